@@ -1,0 +1,338 @@
+"""Pins of the oracle's crack filter (c), blend (d), weights and hole fill (e),
+and of the whole pipeline against an analytic FP64 ray-cast (Sec. VI)."""
+import math
+
+import numpy as np
+import pytest
+
+import synthetic as S
+
+E = np.uint64(0xFFFFFFFFFFFFFFFF)
+
+
+def key(z, cam=0, src=0):
+    zb = int(np.array([z], np.float32).view(np.uint32)[0])
+    return np.uint64((zb << 32) | (cam << 26) | src)
+
+
+def grid(vals):
+    """Build a key grid from depths (None = empty); src = flat index."""
+    H, W = len(vals), len(vals[0])
+    g = np.full((H, W), E, np.uint64)
+    for y in range(H):
+        for x in range(W):
+            if vals[y][x] is not None:
+                g[y, x] = key(vals[y][x], 1, y * W + x)
+    return g
+
+
+# ------------------------------------------------------------------ crack filter
+
+def test_crack_fills_empty_between_consistent_pair(oracle_mod):
+    g = grid([[1000, 1000, 1000],
+              [1000, None, 1010],
+              [1000, 1000, 1000]])
+    out = oracle_mod.crack_filter(g, 0.05)
+    assert out[1, 1] == min(g[1, 0], g[1, 2])          # first pair (L, R)
+    others = np.ones_like(g, bool)
+    others[1, 1] = False
+    assert np.array_equal(out[others], g[others])
+
+
+def test_crack_pair_order_and_consistency(oracle_mod):
+    # (L, R) inconsistent (1000 vs 2000): the (U, D) pair is taken
+    g = grid([[None, 1500, None],
+              [1000, None, 2000],
+              [None, 1520, None]])
+    out = oracle_mod.crack_filter(g, 0.05)
+    assert out[1, 1] == min(g[0, 1], g[2, 1])
+    # no consistent pair at all: stays empty
+    g2 = grid([[None, 1500, None],
+               [1000, None, 2000],
+               [None, 3000, None]])
+    assert oracle_mod.crack_filter(g2, 0.05)[1, 1] == E
+    # only a diagonal pair (UR, DL) is consistent
+    g3 = grid([[None, None, 800],
+               [None, None, None],
+               [810, None, None]])
+    assert oracle_mod.crack_filter(g3, 0.05)[1, 1] == min(g3[0, 2], g3[2, 0])
+    # the (UL, DR) pair comes before (UR, DL)
+    g4 = grid([[700, None, 800],
+               [None, None, None],
+               [810, None, 701]])
+    assert oracle_mod.crack_filter(g4, 0.05)[1, 1] == min(g4[0, 0], g4[2, 2])
+
+
+def test_crack_removes_background_through_foreground(oracle_mod):
+    g = grid([[1000, 1000, 1000],
+              [1000, 2000, 1000],
+              [1000, 1000, 1000]])
+    out = oracle_mod.crack_filter(g, 0.05)
+    assert out[1, 1] == min(g[1, 0], g[1, 2])
+    # a point only slightly behind (within tau) is kept
+    g2 = grid([[1000, 1000, 1000],
+               [1000, 1040, 1000],
+               [1000, 1000, 1000]])
+    assert oracle_mod.crack_filter(g2, 0.05)[1, 1] == g2[1, 1]
+    # the threshold is (1 + tau) * zmax of the pair, not zmin: pair (1000, 1040),
+    # 1060 lies between 1.05 * 1000 and 1.05 * 1040 and is kept
+    g4 = grid([[None, None, None],
+               [1000, 1060, 1040],
+               [None, None, None]])
+    assert oracle_mod.crack_filter(g4, 0.05)[1, 1] == g4[1, 1]
+    g4[1, 1] = key(1093.0, 1, 4)
+    assert oracle_mod.crack_filter(g4, 0.05)[1, 1] == g4[1, 0]
+    # a foreground point on background is kept (the rule only pulls forward)
+    g3 = grid([[2000, 2000, 2000],
+               [2000, 1000, 2000],
+               [2000, 2000, 2000]])
+    assert oracle_mod.crack_filter(g3, 0.05)[1, 1] == g3[1, 1]
+
+
+def test_crack_off_image_neighbours_are_empty(oracle_mod):
+    g = grid([[None, 1000],
+              [1000, 1000]])
+    out = oracle_mod.crack_filter(g, 0.05)
+    # (0,0): L, U, UL, UR, DL off-image; only none of the pairs complete
+    assert out[0, 0] == E
+    assert np.array_equal(out[1], g[1])
+
+
+def test_crack_filter_is_out_of_place(oracle_mod):
+    # a row of two adjacent empties: neither is filled from the other's fill
+    g = grid([[1000, None, None, 1000]])
+    out = oracle_mod.crack_filter(g, 0.05)
+    assert out[0, 1] == E and out[0, 2] == E
+
+
+def test_magnification_cracks_closed(oracle_mod):
+    """Zooming onto a plane opens cracks in the forward warp (Sec. VI); one
+    filter pass closes every interior crack."""
+    W, H = 120, 90
+    src = S.Camera(W, H, 100.0, 100.0, (W - 1) / 2, (H - 1) / 2, np.eye(3), np.zeros(3))
+    view = S.Camera(W, H, 160.0, 160.0, (W - 1) / 2, (H - 1) / 2, np.eye(3), np.zeros(3))
+    dep = np.full((H, W), 2000, np.uint16)
+    M, _, _ = oracle_mod.compose([src], view, [0, 0, 2])
+    raw = oracle_mod.warp_splat([src], [dep], M, np.ones(1, np.float32), W, H)
+    assert (raw == E).sum() > 1000
+    out = oracle_mod.crack_filter(raw, 0.05)
+    # interior: every crack closed; the 1-px border lacks off-image partners
+    assert (out[1:-1, 1:-1] == E).sum() == 0
+    assert (out[1:-1, 1:-1] != raw[1:-1, 1:-1]).sum() == (raw[1:-1, 1:-1] == E).sum()
+
+
+# ------------------------------------------------------------------ weights
+
+def _theta(Cv, Ck, O):
+    a, b = Cv - O, Ck - O
+    return math.atan2(np.linalg.norm(np.cross(a, b)), float(a @ b))
+
+
+def test_weights_angular_distance(oracle_mod):
+    cams = S.rig_arc(9, 90.0, 1.5, 64, 36, 50.0)
+    view = S.arc_view(13.0, 1.7, 64, 36, 50.0)
+    _, _, w = oracle_mod.compose(cams, view, [0, 0, 0])
+    exp = np.array([1.0 / (_theta(view.center, c.center, np.zeros(3)) + 1e-3) for c in cams])
+    assert np.allclose(w, exp.astype(np.float32), rtol=1e-6)
+    # nearer cameras weigh more
+    order = np.argsort(-w, kind="stable")
+    assert abs(13.0 - (-45 + 11.25 * order[0])) <= 11.25 / 2 + 1e-9
+
+
+def test_weights_n_ref_and_onehot(oracle_mod):
+    cams = S.rig_arc(9, 90.0, 1.5, 64, 36, 50.0)
+    view = S.arc_view(-20.0, 1.5, 64, 36, 50.0)
+    _, _, w3 = oracle_mod.compose(cams, view, [0, 0, 0], n_ref=3)
+    th = [_theta(view.center, c.center, np.zeros(3)) for c in cams]
+    assert set(np.nonzero(w3)[0]) == set(np.argsort(th, kind="stable")[:3])
+    _, _, w1 = oracle_mod.compose(cams, cams[6].copy(), [0, 0, 0])
+    assert list(w1) == [0, 0, 0, 0, 0, 0, 1, 0, 0]
+    # midway between two cameras: equal weights
+    mid = S.arc_view(-45 + 11.25 * 2.5, 1.5, 64, 36, 50.0)
+    _, _, wm = oracle_mod.compose(cams, mid, [0, 0, 0], n_ref=2)
+    assert set(np.nonzero(wm)[0]) == {2, 3}
+    assert abs(wm[2] - wm[3]) <= 1e-6 * wm[2]
+
+
+# ------------------------------------------------------------------ blend
+
+def _two_cam_plane(frac, colours=((200, 20, 40), (10, 100, 250))):
+    W, H, f = 96, 64, 120.0
+    cams = S.rig_parallel(2, W, H, f, 0.1)
+    view = S.Camera(W, H, f, f, (W - 1) / 2, (H - 1) / 2, np.eye(3),
+                    -np.array([-0.05 + frac * 0.1, 0.0, 0.0]))
+    rgb = np.stack([np.broadcast_to(np.array(c, np.uint8), (H, W, 3)) for c in colours]).copy()
+    dep = np.full((2, H, W), 2000, np.uint16)
+    return cams, view, rgb, dep
+
+
+def test_blend_weighted_mean_of_visible_cameras(oracle_mod):
+    """Where both cameras see the plane, the output is the weight-normalised
+    mean of their colours; where one does, its colour."""
+    cams, view, rgb, dep = _two_cam_plane(1.0 / 3.0)
+    O = np.array([0, 0, 2.0])
+    out = oracle_mod.synthesize(cams, rgb, dep, view, O, hole_fill=0)
+    w0 = 1.0 / (_theta(view.center, cams[0].center, O) + 1e-3)
+    w1 = 1.0 / (_theta(view.center, cams[1].center, O) + 1e-3)
+    mix = (w0 * rgb[0, 0, 0].astype(float) + w1 * rgb[1, 0, 0]) / (w0 + w1)
+    z, cam, src = oracle_mod.key_fields(out["keys"])
+    xs = np.arange(view.width)[None, :]
+    # camera 1 sits 2/3 B to the right: it sees view columns x >= f (2/3 B) / Z = 4
+    both = (cam == 0) & (xs >= 4) & (xs < view.width - 12)
+    assert np.all(out["rgb"][(cam == 0) & (xs < 4)] == rgb[0, 0, 0])
+    assert both.sum() > 1000
+    assert np.all(np.abs(out["rgb"][both].astype(float) - mix) <= 0.5 + 1e-3)
+    # top-3 aux: two contributions, descending, summing to one
+    t3 = out["top3"][both]
+    assert np.allclose(t3[:, 0], max(w0, w1) / (w0 + w1), rtol=1e-5)
+    assert np.allclose(t3[:, 1], min(w0, w1) / (w0 + w1), rtol=1e-5)
+    assert np.all(t3[:, 2] == 0)
+    # right edge: only camera 1 sees it (camera 0's image ends)
+    only1 = cam == 1
+    assert only1.sum() > 0
+    assert np.all(out["rgb"][only1] == rgb[1, 0, 0])
+
+
+def test_blend_visibility_rejects_inconsistent_fetch(oracle_mod):
+    """A camera whose depth at the back-projected pixel disagrees with the
+    point's depth there by more than tau_vis does not contribute; within
+    tau_vis it does."""
+    cams, view, rgb, dep = _two_cam_plane(0.25)
+    dep[1, :, :] = 2500                      # 25 % off: rejected
+    out = oracle_mod.synthesize(cams, rgb, dep, view, [0, 0, 2.0], hole_fill=0)
+    z, cam, src = oracle_mod.key_fields(out["keys"])
+    from0 = (cam == 0)
+    assert from0.sum() > 1000
+    assert np.all(out["rgb"][from0] == rgb[0, 0, 0])
+    assert np.all(out["top3"][from0][:, 0] == 1.0)
+    dep[1, :, :] = 2080                      # 4 % off: rejected (tau_vis = 3 %)
+    out = oracle_mod.synthesize(cams, rgb, dep, view, [0, 0, 2.0], hole_fill=0)
+    z, cam, src = oracle_mod.key_fields(out["keys"])
+    assert np.all(out["rgb"][cam == 0] == rgb[0, 0, 0])
+    dep[1, :, :] = 2050                      # 2.5 % off: accepted
+    out = oracle_mod.synthesize(cams, rgb, dep, view, [0, 0, 2.0], hole_fill=0)
+    z, cam, src = oracle_mod.key_fields(out["keys"])
+    xs = np.arange(view.width)[None, :]
+    mixed = (cam == 0) & (xs >= 8) & (xs < view.width - 12)
+    assert mixed.sum() > 1000
+    assert np.all(out["rgb"][mixed] != rgb[0, 0, 0])
+    assert np.all(out["top3"][mixed][:, 1] > 0)
+
+
+def test_blend_rounding_and_single_camera(oracle_mod):
+    """One active camera: the blend returns its colour exactly (acc / w)."""
+    cams, view, rgb, dep = _two_cam_plane(0.0)
+    rng = np.random.default_rng(0)
+    rgb = rng.integers(0, 256, rgb.shape).astype(np.uint8)
+    out = oracle_mod.synthesize(cams, rgb, dep, cams[0].copy(), [0, 0, 2.0])
+    assert np.array_equal(out["rgb"], rgb[0])
+
+
+# ------------------------------------------------------------------ hole fill
+
+def test_hole_fill_rows(oracle_mod):
+    hole = np.array([[0, 1, 1, 0, 1, 0, 1],
+                     [1, 1, 1, 1, 1, 1, 1],
+                     [0, 1, 0, 1, 1, 1, 1],
+                     [1, 1, 0, 1, 0, 0, 1]], np.uint8)
+    dep = np.array([[5, 0, 0, 9, 0, 2, 0],
+                    [0, 0, 0, 0, 0, 0, 0],
+                    [4, 0, 4, 0, 0, 0, 0],
+                    [0, 0, 3, 0, 7, 1, 0]], np.float32)
+    rgb = np.zeros((4, 7, 3), np.uint8)
+    rgb[..., 0] = np.arange(7)[None, :] * 10 + np.arange(4)[:, None]
+    rgb[hole == 1] = 0                       # the blend leaves holes black
+    r, d = oracle_mod.hole_fill(hole, rgb, dep)
+    # row 0: x1,x2 between A(5) and B(9) -> B; x4 between B(9) and C(2) -> B;
+    #        x6 only C on its left -> C
+    assert list(r[0, :, 0]) == [0, 30, 30, 30, 30, 50, 50]
+    assert list(d[0]) == [5, 9, 9, 9, 9, 2, 2]
+    # row 1: all holes stay black
+    assert not r[1].any() and not d[1].any()
+    # row 2: equal depths -> left; trailing holes -> nearest left
+    assert list(r[2, :, 0]) == [2, 2, 22, 22, 22, 22, 22]
+    # row 3: x0,x1 only right -> x2; x3 between 3 and 7 -> x4; x6 -> x5
+    assert list(r[3, :, 0]) == [23, 23, 23, 43, 43, 53, 53]
+
+
+# ------------------------------------------------------------------ analytic ground truth
+
+def _gt_mask(cams, view, scene, gt, margin=2):
+    """Pixels whose surface point is seen by at least one reference camera
+    (FP64 shadow-ray test against that camera's exact depth) and which lie at
+    least ``margin`` px from a depth discontinuity of the ground truth."""
+    H, W = view.height, view.width
+    z = gt["z"] * 1000.0
+    P = gt["point"].reshape(-1, 3)
+    seen = np.zeros(H * W, bool)
+    for c in cams:
+        r = S.render(scene, c)
+        q = P @ c.R.T + c.t
+        with np.errstate(divide="ignore", invalid="ignore"):
+            u = np.floor(c.fx * q[:, 0] / q[:, 2] + c.cx + 0.5)
+            v = np.floor(c.fy * q[:, 1] / q[:, 2] + c.cy + 0.5)
+        ok = (q[:, 2] > 0) & (u >= 0) & (u < c.width) & (v >= 0) & (v < c.height)
+        ui = np.where(ok, u, 0).astype(int)
+        vi = np.where(ok, v, 0).astype(int)
+        zc = r["z"][vi, ui]
+        seen |= ok & (np.abs(zc - q[:, 2]) <= 2e-3 * q[:, 2])
+    seen = seen.reshape(H, W)
+    jump = np.zeros((H, W), bool)
+    dz = np.abs(np.diff(z, axis=1)) > 0.02 * z[:, 1:]
+    jump[:, 1:] |= dz
+    jump[:, :-1] |= dz
+    dz = np.abs(np.diff(z, axis=0)) > 0.02 * z[1:, :]
+    jump[1:, :] |= dz
+    jump[:-1, :] |= dz
+    obj = gt["obj"]
+    d = obj[:, 1:] != obj[:, :-1]
+    jump[:, 1:] |= d
+    jump[:, :-1] |= d
+    d = obj[1:, :] != obj[:-1, :]
+    jump[1:, :] |= d
+    jump[:-1, :] |= d
+    grow = jump.copy()
+    for _ in range(margin):
+        g = grow.copy()
+        g[1:, :] |= grow[:-1, :]
+        g[:-1, :] |= grow[1:, :]
+        g[:, 1:] |= grow[:, :-1]
+        g[:, :-1] |= grow[:, 1:]
+        grow = g
+    return seen & ~grow & np.isfinite(z)
+
+
+def _psnr(a, b):
+    mse = np.mean((a.astype(float) - b.astype(float)) ** 2)
+    return float("inf") if mse == 0 else 10 * math.log10(255.0 ** 2 / mse)
+
+
+@pytest.mark.parametrize("name,scale,view_idx", [("plain_2cam_320x240", 1.0, 0),
+                                                 ("plain_9cam_1280x720", 0.25, 40)])
+def test_analytic_ground_truth(oracle_mod, name, scale, view_idx):
+    """Against an FP64 ray-cast of the same analytic scene at the virtual pose
+    (noise-free frames), on pixels seen by a reference camera and 2 px away
+    from depth discontinuities: depth within 1 %; colour PSNR >= 30 dB away
+    from texture edges (nearest-neighbour sampling at a sub-pixel offset picks
+    either side of an edge) and >= 20 dB including them."""
+    wl = S.workload(name, scale=scale)
+    cams, scene, view = wl["cams"], wl["scene"], wl["views"][view_idx]
+    rgb, dep = S.frames_for(scene, cams)
+    out = oracle_mod.synthesize(cams, rgb, dep, view, wl["look_at"])
+    gt = S.render(scene, view)
+    gt_rgb, _ = S.quantise(gt)
+    m = _gt_mask(cams, view, scene, gt)
+    assert m.mean() > 0.5
+    zgt = gt["z"][m] * 1000.0
+    assert np.all(np.abs(out["depth"][m] - zgt) <= 0.01 * zgt)
+    g = gt_rgb.astype(int)
+    edge = np.zeros(m.shape, bool)
+    dx = np.abs(np.diff(g, axis=1)).max(-1) > 24
+    edge[:, 1:] |= dx
+    edge[:, :-1] |= dx
+    dy = np.abs(np.diff(g, axis=0)).max(-1) > 24
+    edge[1:, :] |= dy
+    edge[:-1, :] |= dy
+    assert (m & ~edge).mean() > 0.4
+    assert _psnr(out["rgb"][m & ~edge], gt_rgb[m & ~edge]) >= 30.0
+    assert _psnr(out["rgb"][m], gt_rgb[m]) >= 20.0
