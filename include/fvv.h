@@ -1,0 +1,172 @@
+/*
+ * fvv.h -- C ABI of the GB300 view-synthesis library (libfvv.so).
+ *
+ * The library implements the real-time view-synthesis stage of FVV Live
+ * (Sec. VI "View synthesis"): depth-image-based rendering (DIBR) of a
+ * virtual camera, chosen by the viewer, from calibrated multiview colour
+ * plus depth frames.  Every step runs in the library's CUDA kernels for
+ * sm_103a:
+ *   (a) per-camera unproject/reproject warp of every pixel with depth
+ *       (Sec. VI: "each pixel ... corresponds to a line in 3D space, and
+ *       depth information constrains that line to a single point");
+ *   (b) z-buffer splat with 64-bit atomicMin on packed keys
+ *       bits(Z) << 32 | camera << 26 | source pixel;
+ *   (c) crack / outlier filter on the key image (Sec. VI: cracks from
+ *       magnification, handled by backward warping plus filtering);
+ *   (d) backward fetch and blend weighted by the angular distance of each
+ *       reference camera to the virtual camera (Sec. VI: contributions are
+ *       mixed according to that distance);
+ *   (e) row-wise hole filling from the background side (Sec. VI names
+ *       disocclusions; the paper leaves them black, Sec. IX, fig. of test
+ *       screenshots -- the fill can be switched off).
+ *
+ * Conventions
+ *   - Cameras: pinhole, pixel (u, v) has its centre at integer (u, v);
+ *     x right, y down, z forward; R, t map world -> camera; t in metres.
+ *   - Depth frames: uint16 codes, 0 = no depth; code * depth_unit_m metres
+ *     of camera-space z.  Colour frames: RGB8 interleaved.
+ *   - Every call returns an fvv_status; on failure fvv_last_error() holds a
+ *     message for the calling thread.
+ *   - Buffers passed in may be host memory (pageable or pinned) or device
+ *     memory of the current device; the kind is detected per pointer.
+ *     The library keeps no pointer to a caller buffer after a call returns.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the library's own
+ *     stream).  Calls enqueue their GPU work on that stream; a call that
+ *     writes host memory returns after that data is written.  Calls on one
+ *     context must not be made from several threads at once.
+ */
+#ifndef FVV_H
+#define FVV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t fvv_status;
+#define FVV_OK                0
+#define FVV_ERR_INVALID_ARG   1   /* bad pointer, size, index or option */
+#define FVV_ERR_OUT_OF_MEMORY 2   /* a device or pinned allocation failed */
+#define FVV_ERR_BUDGET        3   /* the request exceeds the memory budget */
+#define FVV_ERR_CUDA          4   /* a CUDA call failed (message has the name) */
+#define FVV_ERR_TIMEOUT       5   /* a bounded wait ran out */
+#define FVV_ERR_BUSY          6   /* no free slot right now */
+#define FVV_ERR_NOT_READY     7   /* no complete frame tick / result not ready */
+#define FVV_ERR_STATE         8   /* call not valid in the context's state */
+
+#define FVV_MAX_CAMS       64          /* 6-bit camera field of a key */
+#define FVV_MAX_SRC_PIXELS (1u << 26)  /* 26-bit source-pixel field of a key */
+#define FVV_KEY_EMPTY      (~(uint64_t)0)
+
+typedef struct fvv_ctx fvv_ctx;
+
+/* One calibrated pinhole camera, or the virtual camera of a view. */
+typedef struct fvv_camera {
+    int32_t width, height;      /* pixels, >= 1; width * height <= FVV_MAX_SRC_PIXELS */
+    double fx, fy, cx, cy;      /* intrinsics, pixels */
+    double R[9];                /* world -> camera rotation, row-major */
+    double t[3];                /* world -> camera translation, metres */
+} fvv_camera;
+
+typedef fvv_camera fvv_view;
+
+/* The reference-camera rig (Sec. III/IX: cameras on an arc around the scene). */
+typedef struct fvv_rig {
+    int32_t n_cams;             /* 1 .. FVV_MAX_CAMS */
+    const fvv_camera* cams;     /* n_cams entries, copied by fvv_create */
+    double look_at[3];          /* point the rig faces; centre of the angular weights */
+    double depth_unit_m;        /* metres per depth code (0.001 = millimetres) */
+} fvv_rig;
+
+/* Options.  Initialise with fvv_default_options, then override fields. */
+typedef struct fvv_options {
+    int32_t n_ref;              /* active reference cameras: the n_ref of smallest angle
+                                   to the view (Sec. VI: typically three); 0 = all */
+    int32_t crack_filter;       /* 1 = apply step (c) */
+    int32_t hole_fill;          /* 1 = apply step (e) */
+    float tau_crack;            /* (c) relative depth tolerance, default 0.05 */
+    float tau_vis;              /* (d) visibility tolerance |d - Z| <= tau_vis Z, default 0.03 */
+    float z_min;                /* smallest accepted projected depth (depth units), default 1 */
+    uint32_t d_lo, d_hi;        /* accepted depth codes, default [1, 65535] */
+    int32_t frame_slots;        /* device-resident frame ticks kept (ring), default 2 */
+    int32_t max_batch;          /* most views per batched call, default 64 */
+    uint64_t memory_budget;     /* device bytes the context may hold, 0 = unlimited */
+} fvv_options;
+
+/* Optional per-view outputs (device or host pointers; NULL = not wanted).
+ * Each is dense row-major over the view's height x width. */
+typedef struct fvv_aux {
+    float* depth;               /* [H][W] virtual-camera depth Z (depth units); 0 where no fill */
+    uint8_t* hole;              /* [H][W] 1 = no reference camera contributed (before fill) */
+    float* top3;                /* [H][W][3] three largest normalised blend weights, descending */
+    uint64_t* keys;             /* [H][W] z-buffer keys after the crack filter */
+    uint64_t* keys_raw;         /* [H][W] z-buffer keys before the crack filter */
+} fvv_aux;
+
+/* Fill `opt` with the defaults listed above. */
+fvv_status fvv_default_options(fvv_options* opt);
+
+/* Message of the last failing call on this thread ("" if none).  The
+ * pointer stays valid until the next failing call on this thread. */
+const char* fvv_last_error(void);
+
+/* Create a context on the current CUDA device: copies the rig, allocates the
+ * frame ring (frame_slots ticks of every camera: RGBA8 + uint16 depth) and
+ * scratch.  Errors: INVALID_ARG (rig/options), BUDGET, OUT_OF_MEMORY, CUDA. */
+fvv_status fvv_create(const fvv_rig* rig, const fvv_options* opt, fvv_ctx** out);
+
+/* Release every resource of `ctx` (waits for its work).  NULL is a no-op. */
+fvv_status fvv_destroy(fvv_ctx* ctx);
+
+/* Upload one camera's frame for capture tick `tick` (the per-tick input of
+ * Sec. VI: decoded colour + depth of a reference camera).
+ *   rgb:   height rows of width*3 bytes, row pitch `rgb_pitch` bytes
+ *   depth: height rows of width uint16, row pitch `depth_pitch` bytes
+ * Tick t lives in slot t % frame_slots.  A tick is complete once all cameras
+ * have been uploaded for it; later syntheses see it.  Uploading into a slot
+ * waits on the GPU for syntheses still reading that slot.  Errors:
+ * INVALID_ARG, STATE (tick older than the one held by the slot), CUDA. */
+fvv_status fvv_upload_frame(fvv_ctx* ctx, int32_t cam, const uint8_t* rgb,
+                            size_t rgb_pitch, const uint16_t* depth,
+                            size_t depth_pitch, uint64_t tick, void* stream);
+
+/* Upload all cameras of one tick.  Camera k's rows start at
+ * rgb + k * rgb_cam_stride and depth + k * depth_cam_stride (bytes). */
+fvv_status fvv_upload_frames(fvv_ctx* ctx, const uint8_t* rgb, size_t rgb_cam_stride,
+                             size_t rgb_pitch, const uint16_t* depth,
+                             size_t depth_cam_stride, size_t depth_pitch,
+                             uint64_t tick, void* stream);
+
+/* Newest complete tick, or NOT_READY if none. */
+fvv_status fvv_latest_tick(fvv_ctx* ctx, uint64_t* tick);
+
+/* Synthesise one virtual view from the newest complete tick: steps (a)-(e).
+ *   out_rgb: height rows of width*3 bytes, row pitch `out_pitch` >= 3*width
+ *   aux:     optional extra outputs (NULL = none)
+ * Errors: INVALID_ARG, NOT_READY (no complete tick), BUDGET, CUDA. */
+fvv_status fvv_synthesize(fvv_ctx* ctx, const fvv_view* view, uint8_t* out_rgb,
+                          size_t out_pitch, const fvv_aux* aux, void* stream);
+
+/* Synthesise n views in one batched pass (three kernel launches for the
+ * whole batch).  ticks[i] selects view i's frame tick (must be complete and
+ * still resident); ticks = NULL uses the newest complete tick for all.
+ * aux may be NULL or an array of n entries.  Views may differ in size. */
+fvv_status fvv_synthesize_batch(fvv_ctx* ctx, int32_t n, const fvv_view* views,
+                                const uint64_t* ticks, uint8_t* const* out_rgb,
+                                const size_t* out_pitch, const fvv_aux* aux,
+                                void* stream);
+
+/* Host-only: the per-camera quantities the kernels use for `view`, composed
+ * in FP64 and rounded to FP32 once.  M: n_cams x 12 forward maps (camera ->
+ * view, acting on (u z, v z, z, 1)); N: n_cams x 12 backward maps (view ->
+ * camera); w: n_cams blend weights (0 = inactive).  Any output may be NULL.
+ * Needs no GPU. */
+fvv_status fvv_view_params(const fvv_rig* rig, const fvv_options* opt,
+                           const fvv_view* view, float* M, float* N, float* w);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FVV_H */

@@ -1,0 +1,781 @@
+// fvv_api.cu -- host runtime behind the C ABI of include/fvv.h.
+//
+// Owns the device-resident frame ring (every camera's RGBA8 + depth for
+// `frame_slots` capture ticks), the per-view z-buffer scratch, a ring of
+// pinned/device parameter blocks for batched launches, and the FP64 pose
+// composition (Sec. VI geometry) whose FP32-rounded results the kernels use.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "fvv.h"
+#include "fvv_internal.h"
+
+using fvv::CamGeom;
+using fvv::FrameRef;
+using fvv::ViewDesc;
+
+namespace {
+
+thread_local std::string g_err;
+
+fvv_status fail(fvv_status code, const std::string& msg)
+{
+    g_err = msg;
+    return code;
+}
+
+#define FVV_CUDA(call)                                                                   \
+    do {                                                                                 \
+        cudaError_t e_ = (call);                                                         \
+        if (e_ != cudaSuccess) {                                                         \
+            cudaGetLastError();                                                          \
+            return fail(e_ == cudaErrorMemoryAllocation ? FVV_ERR_OUT_OF_MEMORY           \
+                                                        : FVV_ERR_CUDA,                   \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));             \
+        }                                                                                \
+    } while (0)
+
+#define FVV_TRY(expr)                      \
+    do {                                   \
+        fvv_status s_ = (expr);            \
+        if (s_ != FVV_OK) return s_;       \
+    } while (0)
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+bool finite_all(const double* v, int n)
+{
+    for (int i = 0; i < n; ++i)
+        if (!std::isfinite(v[i])) return false;
+    return true;
+}
+
+bool camera_ok(const fvv_camera& c, std::string* why)
+{
+    if (c.width < 1 || c.height < 1 || c.width > 65535 || c.height > 65535) {
+        *why = "width/height must be in [1, 65535]";
+        return false;
+    }
+    if (uint64_t(c.width) * uint64_t(c.height) > FVV_MAX_SRC_PIXELS) {
+        *why = "width*height exceeds the 26-bit source-pixel field of a key";
+        return false;
+    }
+    const double k[4] = {c.fx, c.fy, c.cx, c.cy};
+    if (!finite_all(k, 4) || c.fx == 0.0 || c.fy == 0.0) {
+        *why = "intrinsics must be finite with fx, fy != 0";
+        return false;
+    }
+    if (!finite_all(c.R, 9) || !finite_all(c.t, 3)) {
+        *why = "R and t must be finite";
+        return false;
+    }
+    return true;
+}
+
+bool options_ok(const fvv_options& o, int n_cams, std::string* why)
+{
+    if (o.n_ref < 0 || o.n_ref > n_cams) { *why = "n_ref must be in [0, n_cams]"; return false; }
+    if (!(o.tau_crack >= 0.0f) || !std::isfinite(o.tau_crack)) { *why = "tau_crack must be >= 0"; return false; }
+    if (!(o.tau_vis >= 0.0f) || !std::isfinite(o.tau_vis)) { *why = "tau_vis must be >= 0"; return false; }
+    if (!std::isfinite(o.z_min)) { *why = "z_min must be finite"; return false; }
+    if (o.d_lo < 1 || o.d_hi > 65535 || o.d_lo > o.d_hi) { *why = "need 1 <= d_lo <= d_hi <= 65535"; return false; }
+    if (o.frame_slots < 1 || o.frame_slots > 1024) { *why = "frame_slots must be in [1, 1024]"; return false; }
+    if (o.max_batch < 1 || o.max_batch > 4096) { *why = "max_batch must be in [1, 4096]"; return false; }
+    return true;
+}
+
+// ---------------------------------------------------------------------------
+// Sec. VI geometry, FP64.  Maps (u z, v z, z, 1) of camera s to (X, Y, Z) of
+// camera d: [A | b] with A = K_d R_rel K_s^-1 and b = K_d t_rel, where
+// R_rel = R_d R_s^T and t_rel = (t_d - R_rel t_s) / depth_unit_m.  A's columns
+// are KR[:,0] / fx_s, KR[:,1] / fy_s and KR[:,2] - KR[:,0] cx_s / fx_s -
+// KR[:,1] cy_s / fy_s (exact when the cameras share intrinsics and
+// orientation).  Rounded to FP32 once.
+// ---------------------------------------------------------------------------
+void compose_map(const fvv_camera& s, const fvv_camera& d, double scale, float out[12])
+{
+    double Rrel[3][3], trel[3], KR[3][3], Kt[3];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double acc = 0.0;
+            for (int m = 0; m < 3; ++m) acc += d.R[3 * i + m] * s.R[3 * j + m];
+            Rrel[i][j] = acc;
+        }
+    for (int i = 0; i < 3; ++i) {
+        double acc = 0.0;
+        for (int j = 0; j < 3; ++j) acc += Rrel[i][j] * s.t[j];
+        trel[i] = (d.t[i] - acc) * scale;
+    }
+    for (int j = 0; j < 3; ++j) {
+        KR[0][j] = d.fx * Rrel[0][j] + d.cx * Rrel[2][j];
+        KR[1][j] = d.fy * Rrel[1][j] + d.cy * Rrel[2][j];
+        KR[2][j] = Rrel[2][j];
+    }
+    Kt[0] = d.fx * trel[0] + d.cx * trel[2];
+    Kt[1] = d.fy * trel[1] + d.cy * trel[2];
+    Kt[2] = trel[2];
+    for (int i = 0; i < 3; ++i) {
+        const double c0 = KR[i][0] / s.fx;
+        const double c1 = KR[i][1] / s.fy;
+        const double c2 = (KR[i][2] - (KR[i][0] * s.cx) / s.fx) - (KR[i][1] * s.cy) / s.fy;
+        out[4 * i + 0] = float(c0);
+        out[4 * i + 1] = float(c1);
+        out[4 * i + 2] = float(c2);
+        out[4 * i + 3] = float(Kt[i]);
+    }
+}
+
+void centre_of(const fvv_camera& c, double C[3])
+{
+    for (int j = 0; j < 3; ++j)
+        C[j] = -(c.R[0 + j] * c.t[0] + c.R[3 + j] * c.t[1] + c.R[6 + j] * c.t[2]);
+}
+
+// Mixing by "the distance of each reference camera to the virtual camera"
+// (Sec. VI), read as the angle between the two viewing directions from the
+// rig's look-at point: theta = atan2(|a x b|, a . b).
+double angle_about(const double Cv[3], const double Ck[3], const double O[3])
+{
+    double a[3], b[3], c[3];
+    for (int j = 0; j < 3; ++j) {
+        a[j] = Cv[j] - O[j];
+        b[j] = Ck[j] - O[j];
+    }
+    c[0] = a[1] * b[2] - a[2] * b[1];
+    c[1] = a[2] * b[0] - a[0] * b[2];
+    c[2] = a[0] * b[1] - a[1] * b[0];
+    const double cn = std::sqrt(c[0] * c[0] + c[1] * c[1] + c[2] * c[2]);
+    const double dt = a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
+    return std::atan2(cn, dt);
+}
+
+// Per-camera maps and weights of one view: the n_ref cameras of smallest
+// angle get w = 1 / (theta + 1e-3), the rest 0; a view sitting on a camera
+// (same centre within 1e-9 m, same optical axis) is one-hot on it.
+void compose_view(int n_cams, const fvv_camera* cams, const double look_at[3],
+                  double depth_unit_m, int n_ref, const fvv_camera& view, CamGeom* g)
+{
+    const double scale = 1.0 / depth_unit_m;
+    double Cv[3], theta[fvv::kMaxCams];
+    bool chosen[fvv::kMaxCams];
+    centre_of(view, Cv);
+    int onehot = -1;
+    for (int k = 0; k < n_cams; ++k) {
+        compose_map(cams[k], view, scale, g[k].M);
+        compose_map(view, cams[k], scale, g[k].N);
+        g[k].pad[0] = g[k].pad[1] = g[k].pad[2] = 0.0f;
+        double Ck[3];
+        centre_of(cams[k], Ck);
+        theta[k] = angle_about(Cv, Ck, look_at);
+        chosen[k] = false;
+        const double dx = Cv[0] - Ck[0], dy = Cv[1] - Ck[1], dz = Cv[2] - Ck[2];
+        const double dist = std::sqrt(dx * dx + dy * dy + dz * dz);
+        const double axis = view.R[6] * cams[k].R[6] + view.R[7] * cams[k].R[7] +
+                            view.R[8] * cams[k].R[8];
+        if (onehot < 0 && dist < 1e-9 && axis > 1.0 - 1e-12) onehot = k;
+    }
+    if (n_ref <= 0 || n_ref > n_cams) n_ref = n_cams;
+    if (onehot >= 0) {
+        for (int k = 0; k < n_cams; ++k) g[k].w = k == onehot ? 1.0f : 0.0f;
+        return;
+    }
+    for (int r = 0; r < n_ref; ++r) {
+        int best = -1;
+        for (int k = 0; k < n_cams; ++k)
+            if (!chosen[k] && (best < 0 || theta[k] < theta[best])) best = k;
+        chosen[best] = true;
+    }
+    for (int k = 0; k < n_cams; ++k)
+        g[k].w = chosen[k] ? float(1.0 / (theta[k] + 1e-3)) : 0.0f;
+}
+
+enum class MemKind { Device, Host };
+
+MemKind mem_kind(const void* p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return MemKind::Host;
+    }
+    return (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) ? MemKind::Device
+                                                                               : MemKind::Host;
+}
+
+struct ParamBlock {
+    uint8_t* host = nullptr;    // pinned
+    uint8_t* dev = nullptr;
+    size_t cap = 0;
+    cudaEvent_t done = nullptr;
+    bool pending = false;
+};
+
+struct SlotState {
+    uint64_t tick = 0;
+    uint64_t mask = 0;
+    bool any = false;
+    cudaEvent_t uploaded = nullptr;   // after the last upload into this slot
+    cudaEvent_t read = nullptr;       // after the last synthesis reading it
+    bool read_pending = false;
+};
+
+}  // namespace
+
+struct fvv_ctx {
+    int device = 0;
+    int n_cams = 0;
+    std::vector<fvv_camera> cams;
+    double look_at[3] = {0, 0, 0};
+    double depth_unit_m = 0.001;
+    fvv_options opt{};
+    cudaStream_t own = nullptr;
+    size_t smem_optin = 0;
+
+    int slots = 0;
+    std::vector<int> dpitch, rpitch;            // elements
+    std::vector<size_t> off_depth, off_rgba;    // within a slot
+    size_t slot_bytes = 0;
+    uint8_t* arena = nullptr;
+    size_t arena_bytes = 0;
+    FrameRef* frames_dev = nullptr;
+    std::vector<SlotState> slot;
+    uint64_t full_mask = 0;
+    uint64_t latest = 0;
+    bool have_latest = false;
+
+    std::vector<uint8_t*> stage_rgb;            // per camera, for host uploads
+    unsigned long long* keys = nullptr;
+    size_t keys_cap = 0;                        // elements
+    uint8_t* out_stage = nullptr;
+    size_t out_stage_cap = 0;
+
+    std::vector<ParamBlock> pring;
+    int pnext = 0;
+    cudaEvent_t scratch_done = nullptr;         // after the last batch's use of keys / out_stage
+    bool scratch_pending = false;
+    size_t held = 0;                            // device bytes held
+};
+
+namespace {
+
+fvv_status dev_alloc(fvv_ctx* c, void** p, size_t bytes)
+{
+    *p = nullptr;
+    if (bytes == 0) return FVV_OK;
+    if (c->opt.memory_budget && c->held + bytes > c->opt.memory_budget)
+        return fail(FVV_ERR_BUDGET, "device memory budget exceeded (" + std::to_string(c->held + bytes) +
+                                        " > " + std::to_string(c->opt.memory_budget) + " bytes)");
+    FVV_CUDA(cudaMalloc(p, bytes));
+    c->held += bytes;
+    return FVV_OK;
+}
+
+void dev_free(fvv_ctx* c, void* p, size_t bytes)
+{
+    if (p) {
+        cudaFree(p);
+        c->held -= bytes;
+    }
+}
+
+size_t param_bytes(int n, int n_cams)
+{
+    return align_up(size_t(n) * sizeof(ViewDesc), 256) + size_t(n) * n_cams * sizeof(CamGeom);
+}
+
+fvv_status ensure_keys(fvv_ctx* c, size_t n)
+{
+    if (n <= c->keys_cap) return FVV_OK;
+    if (c->keys) {
+        FVV_CUDA(cudaDeviceSynchronize());
+        dev_free(c, c->keys, c->keys_cap * 8);
+        c->keys = nullptr;
+        c->keys_cap = 0;
+    }
+    const size_t cap = align_up(n, 1 << 16);
+    FVV_TRY(dev_alloc(c, reinterpret_cast<void**>(&c->keys), cap * 8));
+    c->keys_cap = cap;
+    return FVV_OK;
+}
+
+fvv_status ensure_out_stage(fvv_ctx* c, size_t bytes)
+{
+    if (bytes <= c->out_stage_cap) return FVV_OK;
+    if (c->out_stage) {
+        FVV_CUDA(cudaDeviceSynchronize());
+        dev_free(c, c->out_stage, c->out_stage_cap);
+        c->out_stage = nullptr;
+        c->out_stage_cap = 0;
+    }
+    const size_t cap = align_up(bytes, 1 << 20);
+    FVV_TRY(dev_alloc(c, reinterpret_cast<void**>(&c->out_stage), cap));
+    c->out_stage_cap = cap;
+    return FVV_OK;
+}
+
+fvv_status upload_one(fvv_ctx* c, int cam, const uint8_t* rgb, size_t rgb_pitch,
+                      const uint16_t* depth, size_t depth_pitch, uint64_t tick, cudaStream_t s)
+{
+    const fvv_camera& C = c->cams[cam];
+    if (!rgb || !depth) return fail(FVV_ERR_INVALID_ARG, "rgb and depth must be non-NULL");
+    if (rgb_pitch < size_t(C.width) * 3) return fail(FVV_ERR_INVALID_ARG, "rgb_pitch < 3 * width");
+    if (depth_pitch < size_t(C.width) * 2) return fail(FVV_ERR_INVALID_ARG, "depth_pitch < 2 * width");
+    const int si = int(tick % uint64_t(c->slots));
+    SlotState& S = c->slot[si];
+    if (S.any && tick < S.tick)
+        return fail(FVV_ERR_STATE, "tick " + std::to_string(tick) + " is older than tick " +
+                                       std::to_string(S.tick) + " held by its slot");
+    if (!S.any || tick > S.tick) {
+        S.any = true;
+        S.tick = tick;
+        S.mask = 0;
+    }
+    if (S.read_pending) FVV_CUDA(cudaStreamWaitEvent(s, S.read, 0));
+    uint8_t* base = c->arena + size_t(si) * c->slot_bytes;
+    uint16_t* ddst = reinterpret_cast<uint16_t*>(base + c->off_depth[cam]);
+    uint32_t* rdst = reinterpret_cast<uint32_t*>(base + c->off_rgba[cam]);
+    FVV_CUDA(cudaMemcpy2DAsync(ddst, size_t(c->dpitch[cam]) * 2, depth, depth_pitch,
+                               size_t(C.width) * 2, size_t(C.height), cudaMemcpyDefault, s));
+    const uint8_t* src = rgb;
+    size_t spitch = rgb_pitch;
+    if (mem_kind(rgb) == MemKind::Host) {
+        if (!c->stage_rgb[cam]) {
+            void* p = nullptr;
+            FVV_TRY(dev_alloc(c, &p, size_t(C.width) * 3 * size_t(C.height)));
+            c->stage_rgb[cam] = static_cast<uint8_t*>(p);
+        }
+        FVV_CUDA(cudaMemcpy2DAsync(c->stage_rgb[cam], size_t(C.width) * 3, rgb, rgb_pitch,
+                                   size_t(C.width) * 3, size_t(C.height), cudaMemcpyHostToDevice, s));
+        src = c->stage_rgb[cam];
+        spitch = size_t(C.width) * 3;
+    }
+    FVV_CUDA(fvv::launch_pack_rgba(src, spitch, rdst, c->rpitch[cam], C.width, C.height, s));
+    FVV_CUDA(cudaEventRecord(S.uploaded, s));
+    S.mask |= uint64_t(1) << cam;
+    if (S.mask == c->full_mask && (!c->have_latest || tick > c->latest)) {
+        c->latest = tick;
+        c->have_latest = true;
+    }
+    return FVV_OK;
+}
+
+struct OutPlan {
+    uint8_t* rgb_dev;
+    size_t rgb_pitch_dev;
+    bool rgb_host;
+    float* depth_dev; bool depth_host;
+    uint8_t* hole_dev; bool hole_host;
+    float* top3_dev; bool top3_host;
+    unsigned long long* keys_dev; bool keys_host;
+};
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+fvv_status fvv_default_options(fvv_options* o)
+{
+    if (!o) return fail(FVV_ERR_INVALID_ARG, "options pointer is NULL");
+    std::memset(o, 0, sizeof *o);
+    o->n_ref = 0;
+    o->crack_filter = 1;
+    o->hole_fill = 1;
+    o->tau_crack = 0.05f;
+    o->tau_vis = 0.03f;
+    o->z_min = 1.0f;
+    o->d_lo = 1;
+    o->d_hi = 65535;
+    o->frame_slots = 2;
+    o->max_batch = 64;
+    o->memory_budget = 0;
+    return FVV_OK;
+}
+
+const char* fvv_last_error(void) { return g_err.c_str(); }
+
+static fvv_status check_rig(const fvv_rig* rig)
+{
+    if (!rig) return fail(FVV_ERR_INVALID_ARG, "rig is NULL");
+    if (rig->n_cams < 1 || rig->n_cams > FVV_MAX_CAMS)
+        return fail(FVV_ERR_INVALID_ARG, "n_cams must be in [1, 64]");
+    if (!rig->cams) return fail(FVV_ERR_INVALID_ARG, "rig->cams is NULL");
+    if (!(rig->depth_unit_m > 0.0) || !std::isfinite(rig->depth_unit_m))
+        return fail(FVV_ERR_INVALID_ARG, "depth_unit_m must be > 0");
+    if (!finite_all(rig->look_at, 3)) return fail(FVV_ERR_INVALID_ARG, "look_at must be finite");
+    std::string why;
+    for (int k = 0; k < rig->n_cams; ++k)
+        if (!camera_ok(rig->cams[k], &why))
+            return fail(FVV_ERR_INVALID_ARG, "camera " + std::to_string(k) + ": " + why);
+    return FVV_OK;
+}
+
+fvv_status fvv_view_params(const fvv_rig* rig, const fvv_options* opt, const fvv_view* view,
+                           float* M, float* N, float* w)
+{
+    FVV_TRY(check_rig(rig));
+    fvv_options o;
+    if (opt) o = *opt; else fvv_default_options(&o);
+    std::string why;
+    if (!options_ok(o, rig->n_cams, &why)) return fail(FVV_ERR_INVALID_ARG, why);
+    if (!view || !camera_ok(*view, &why)) return fail(FVV_ERR_INVALID_ARG, "view: " + why);
+    std::vector<CamGeom> g(rig->n_cams);
+    compose_view(rig->n_cams, rig->cams, rig->look_at, rig->depth_unit_m, o.n_ref, *view, g.data());
+    for (int k = 0; k < rig->n_cams; ++k) {
+        if (M) std::memcpy(M + 12 * k, g[k].M, 12 * sizeof(float));
+        if (N) std::memcpy(N + 12 * k, g[k].N, 12 * sizeof(float));
+        if (w) w[k] = g[k].w;
+    }
+    return FVV_OK;
+}
+
+fvv_status fvv_destroy(fvv_ctx* c)
+{
+    if (!c) return FVV_OK;
+    int cur = 0;
+    cudaGetDevice(&cur);
+    cudaSetDevice(c->device);
+    if (c->own) cudaStreamSynchronize(c->own);
+    cudaDeviceSynchronize();
+    for (auto& p : c->pring) {
+        if (p.host) cudaFreeHost(p.host);
+        dev_free(c, p.dev, p.cap);
+        if (p.done) cudaEventDestroy(p.done);
+    }
+    for (auto& S : c->slot) {
+        if (S.uploaded) cudaEventDestroy(S.uploaded);
+        if (S.read) cudaEventDestroy(S.read);
+    }
+    if (c->scratch_done) cudaEventDestroy(c->scratch_done);
+    for (int k = 0; k < c->n_cams; ++k)
+        if (c->stage_rgb[k])
+            dev_free(c, c->stage_rgb[k], size_t(c->cams[k].width) * 3 * size_t(c->cams[k].height));
+    dev_free(c, c->keys, c->keys_cap * 8);
+    dev_free(c, c->out_stage, c->out_stage_cap);
+    dev_free(c, c->frames_dev, sizeof(FrameRef) * size_t(c->slots) * c->n_cams);
+    dev_free(c, c->arena, c->arena_bytes);
+    if (c->own) cudaStreamDestroy(c->own);
+    cudaGetLastError();
+    cudaSetDevice(cur);
+    delete c;
+    return FVV_OK;
+}
+
+fvv_status fvv_create(const fvv_rig* rig, const fvv_options* opt, fvv_ctx** out)
+{
+    if (!out) return fail(FVV_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    FVV_TRY(check_rig(rig));
+    fvv_options o;
+    if (opt) o = *opt; else fvv_default_options(&o);
+    std::string why;
+    if (!options_ok(o, rig->n_cams, &why)) return fail(FVV_ERR_INVALID_ARG, why);
+
+    fvv_ctx* c = new fvv_ctx();
+    c->n_cams = rig->n_cams;
+    c->cams.assign(rig->cams, rig->cams + rig->n_cams);
+    std::memcpy(c->look_at, rig->look_at, sizeof c->look_at);
+    c->depth_unit_m = rig->depth_unit_m;
+    c->opt = o;
+    c->slots = o.frame_slots;
+    c->full_mask = c->n_cams == 64 ? ~uint64_t(0) : ((uint64_t(1) << c->n_cams) - 1);
+    c->stage_rgb.assign(c->n_cams, nullptr);
+
+    auto bail = [&](fvv_status s) {
+        std::string msg = g_err;
+        fvv_destroy(c);
+        g_err = msg;
+        return s;
+    };
+#define FVV_CREATE_TRY(expr)                 \
+    do {                                     \
+        fvv_status s_ = (expr);              \
+        if (s_ != FVV_OK) return bail(s_);   \
+    } while (0)
+#define FVV_CREATE_CUDA(call)                                                                      \
+    do {                                                                                           \
+        cudaError_t e_ = (call);                                                                   \
+        if (e_ != cudaSuccess) {                                                                   \
+            cudaGetLastError();                                                                    \
+            return bail(fail(FVV_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)));  \
+        }                                                                                          \
+    } while (0)
+
+    FVV_CREATE_CUDA(cudaGetDevice(&c->device));
+    int optin = 0;
+    FVV_CREATE_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
+    c->smem_optin = size_t(optin);
+    FVV_CREATE_CUDA(cudaStreamCreateWithFlags(&c->own, cudaStreamNonBlocking));
+
+    // frame ring layout: per camera depth then RGBA8, rows padded to 128 B
+    c->dpitch.resize(c->n_cams);
+    c->rpitch.resize(c->n_cams);
+    c->off_depth.resize(c->n_cams);
+    c->off_rgba.resize(c->n_cams);
+    size_t off = 0;
+    for (int k = 0; k < c->n_cams; ++k) {
+        const fvv_camera& C = c->cams[k];
+        c->dpitch[k] = int(align_up(size_t(C.width) * 2, 128) / 2);
+        c->rpitch[k] = int(align_up(size_t(C.width) * 4, 128) / 4);
+        c->off_depth[k] = off;
+        off = align_up(off + size_t(C.height) * c->dpitch[k] * 2, 256);
+        c->off_rgba[k] = off;
+        off = align_up(off + size_t(C.height) * c->rpitch[k] * 4, 256);
+    }
+    c->slot_bytes = off;
+    c->arena_bytes = off * size_t(c->slots);
+    FVV_CREATE_TRY(dev_alloc(c, reinterpret_cast<void**>(&c->arena), c->arena_bytes));
+    FVV_CREATE_CUDA(cudaMemsetAsync(c->arena, 0, c->arena_bytes, c->own));
+
+    std::vector<FrameRef> fr(size_t(c->slots) * c->n_cams);
+    for (int s = 0; s < c->slots; ++s)
+        for (int k = 0; k < c->n_cams; ++k) {
+            FrameRef& F = fr[size_t(s) * c->n_cams + k];
+            uint8_t* base = c->arena + size_t(s) * c->slot_bytes;
+            F.depth = reinterpret_cast<const uint16_t*>(base + c->off_depth[k]);
+            F.rgba = reinterpret_cast<const uint32_t*>(base + c->off_rgba[k]);
+            F.W = c->cams[k].width;
+            F.H = c->cams[k].height;
+            F.dpitch = c->dpitch[k];
+            F.rpitch = c->rpitch[k];
+        }
+    FVV_CREATE_TRY(dev_alloc(c, reinterpret_cast<void**>(&c->frames_dev), sizeof(FrameRef) * fr.size()));
+    FVV_CREATE_CUDA(cudaMemcpyAsync(c->frames_dev, fr.data(), sizeof(FrameRef) * fr.size(),
+                                    cudaMemcpyHostToDevice, c->own));
+
+    c->slot.resize(c->slots);
+    for (auto& S : c->slot) {
+        FVV_CREATE_CUDA(cudaEventCreateWithFlags(&S.uploaded, cudaEventDisableTiming));
+        FVV_CREATE_CUDA(cudaEventCreateWithFlags(&S.read, cudaEventDisableTiming));
+        FVV_CREATE_CUDA(cudaEventRecord(S.uploaded, c->own));
+    }
+    FVV_CREATE_CUDA(cudaEventCreateWithFlags(&c->scratch_done, cudaEventDisableTiming));
+    c->pring.resize(4);
+    const size_t pb = param_bytes(o.max_batch, c->n_cams);
+    for (auto& p : c->pring) {
+        FVV_CREATE_CUDA(cudaHostAlloc(reinterpret_cast<void**>(&p.host), pb, cudaHostAllocDefault));
+        FVV_CREATE_TRY(dev_alloc(c, reinterpret_cast<void**>(&p.dev), pb));
+        p.cap = pb;
+        FVV_CREATE_CUDA(cudaEventCreateWithFlags(&p.done, cudaEventDisableTiming));
+    }
+    FVV_CREATE_CUDA(cudaStreamSynchronize(c->own));
+#undef FVV_CREATE_TRY
+#undef FVV_CREATE_CUDA
+    *out = c;
+    return FVV_OK;
+}
+
+fvv_status fvv_upload_frame(fvv_ctx* c, int32_t cam, const uint8_t* rgb, size_t rgb_pitch,
+                            const uint16_t* depth, size_t depth_pitch, uint64_t tick, void* stream)
+{
+    if (!c) return fail(FVV_ERR_INVALID_ARG, "ctx is NULL");
+    if (cam < 0 || cam >= c->n_cams) return fail(FVV_ERR_INVALID_ARG, "camera index out of range");
+    cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : c->own;
+    return upload_one(c, cam, rgb, rgb_pitch, depth, depth_pitch, tick, s);
+}
+
+fvv_status fvv_upload_frames(fvv_ctx* c, const uint8_t* rgb, size_t rgb_cam_stride, size_t rgb_pitch,
+                             const uint16_t* depth, size_t depth_cam_stride, size_t depth_pitch,
+                             uint64_t tick, void* stream)
+{
+    if (!c) return fail(FVV_ERR_INVALID_ARG, "ctx is NULL");
+    if (!rgb || !depth) return fail(FVV_ERR_INVALID_ARG, "rgb and depth must be non-NULL");
+    cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : c->own;
+    for (int k = 0; k < c->n_cams; ++k) {
+        const uint8_t* r = rgb + size_t(k) * rgb_cam_stride;
+        const uint16_t* d = reinterpret_cast<const uint16_t*>(
+            reinterpret_cast<const uint8_t*>(depth) + size_t(k) * depth_cam_stride);
+        FVV_TRY(upload_one(c, k, r, rgb_pitch, d, depth_pitch, tick, s));
+    }
+    return FVV_OK;
+}
+
+fvv_status fvv_latest_tick(fvv_ctx* c, uint64_t* tick)
+{
+    if (!c || !tick) return fail(FVV_ERR_INVALID_ARG, "NULL argument");
+    if (!c->have_latest) return fail(FVV_ERR_NOT_READY, "no complete frame tick uploaded yet");
+    *tick = c->latest;
+    return FVV_OK;
+}
+
+fvv_status fvv_synthesize_batch(fvv_ctx* c, int32_t n, const fvv_view* views, const uint64_t* ticks,
+                                uint8_t* const* out_rgb, const size_t* out_pitch, const fvv_aux* aux,
+                                void* stream)
+{
+    if (!c) return fail(FVV_ERR_INVALID_ARG, "ctx is NULL");
+    if (n < 1 || n > c->opt.max_batch)
+        return fail(FVV_ERR_INVALID_ARG, "batch size must be in [1, max_batch]");
+    if (!views || !out_rgb || !out_pitch) return fail(FVV_ERR_INVALID_ARG, "NULL views/out_rgb/out_pitch");
+    cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : c->own;
+    FVV_CUDA(cudaSetDevice(c->device));
+
+    // validate views and resolve their frame slots
+    std::string why;
+    std::vector<int> slot_of(n);
+    size_t key_total = 0, stage_total = 0;
+    int max_w = 0, max_h = 0;
+    for (int i = 0; i < n; ++i) {
+        const fvv_view& V = views[i];
+        if (!camera_ok(V, &why)) return fail(FVV_ERR_INVALID_ARG, "view " + std::to_string(i) + ": " + why);
+        if (fvv::resolve_smem_bytes(V.width, c->n_cams) > c->smem_optin)
+            return fail(FVV_ERR_INVALID_ARG, "view " + std::to_string(i) + ": width too large");
+        if (!out_rgb[i]) return fail(FVV_ERR_INVALID_ARG, "out_rgb[" + std::to_string(i) + "] is NULL");
+        if (out_pitch[i] < size_t(V.width) * 3) return fail(FVV_ERR_INVALID_ARG, "out_pitch < 3 * width");
+        uint64_t t;
+        if (ticks) {
+            t = ticks[i];
+            const SlotState& S = c->slot[t % uint64_t(c->slots)];
+            if (!S.any || S.tick != t || S.mask != c->full_mask)
+                return fail(FVV_ERR_NOT_READY, "tick " + std::to_string(t) + " is not complete or no longer resident");
+        } else {
+            if (!c->have_latest) return fail(FVV_ERR_NOT_READY, "no complete frame tick uploaded yet");
+            t = c->latest;
+        }
+        slot_of[i] = int(t % uint64_t(c->slots));
+        const size_t np = size_t(V.width) * V.height;
+        key_total += align_up(np, 16);
+        max_w = std::max(max_w, V.width);
+        max_h = std::max(max_h, V.height);
+        if (mem_kind(out_rgb[i]) == MemKind::Host) stage_total += align_up(np * 3, 256);
+        if (aux) {
+            const fvv_aux& A = aux[i];
+            if (A.depth && mem_kind(A.depth) == MemKind::Host) stage_total += align_up(np * 4, 256);
+            if (A.hole && mem_kind(A.hole) == MemKind::Host) stage_total += align_up(np, 256);
+            if (A.top3 && mem_kind(A.top3) == MemKind::Host) stage_total += align_up(np * 12, 256);
+            if (A.keys && mem_kind(A.keys) == MemKind::Host) stage_total += align_up(np * 8, 256);
+        }
+    }
+    FVV_TRY(ensure_keys(c, key_total));
+    FVV_TRY(ensure_out_stage(c, stage_total));
+
+    // parameter block
+    ParamBlock& P = c->pring[c->pnext];
+    c->pnext = (c->pnext + 1) % int(c->pring.size());
+    if (P.pending) FVV_CUDA(cudaEventSynchronize(P.done));
+    ViewDesc* vd = reinterpret_cast<ViewDesc*>(P.host);
+    const size_t geom_off = align_up(size_t(n) * sizeof(ViewDesc), 256);
+    CamGeom* gh = reinterpret_cast<CamGeom*>(P.host + geom_off);
+    const CamGeom* gd = reinterpret_cast<const CamGeom*>(P.dev + geom_off);
+
+    struct HostCopy { void* dst; size_t dpitch; const void* src; size_t spitch, width, height; };
+    std::vector<HostCopy> d2h;
+    std::vector<std::pair<void*, const void*>> raw_copies;   // keys_raw
+    std::vector<size_t> raw_bytes;
+    size_t koff = 0, soff = 0;
+    int max_chunks = 0;
+    bool any_host = false;
+    for (int i = 0; i < n; ++i) {
+        const fvv_view& V = views[i];
+        ViewDesc& D = vd[i];
+        std::memset(&D, 0, sizeof D);
+        const size_t np = size_t(V.width) * V.height;
+        D.Wv = V.width;
+        D.Hv = V.height;
+        D.n_cams = c->n_cams;
+        D.slot = slot_of[i];
+        D.flags = (c->opt.crack_filter ? fvv::kFlagCrack : 0) | (c->opt.hole_fill ? fvv::kFlagFill : 0);
+        D.tau_crack = c->opt.tau_crack;
+        D.tau_vis = c->opt.tau_vis;
+        D.z_min = c->opt.z_min;
+        D.d_lo = c->opt.d_lo;
+        D.d_hi = c->opt.d_hi;
+        D.keys = c->keys + koff;
+        koff += align_up(np, 16);
+        CamGeom* g = gh + size_t(i) * c->n_cams;
+        compose_view(c->n_cams, c->cams.data(), c->look_at, c->depth_unit_m, c->opt.n_ref, V, g);
+        D.geom = gd + size_t(i) * c->n_cams;
+        int na = 0, chunks = 0;
+        D.chunk_begin[0] = 0;
+        for (int k = 0; k < c->n_cams; ++k)
+            if (g[k].w > 0.0f) {
+                D.active[na] = k;
+                chunks += c->cams[k].height * ((c->cams[k].width + fvv::kSplatPix - 1) / fvv::kSplatPix);
+                D.chunk_begin[++na] = chunks;
+            }
+        D.n_active = na;
+        max_chunks = std::max(max_chunks, chunks);
+        auto stage = [&](size_t bytes) {
+            uint8_t* p = c->out_stage + soff;
+            soff += align_up(bytes, 256);
+            return p;
+        };
+        if (mem_kind(out_rgb[i]) == MemKind::Host) {
+            D.out_rgb = stage(np * 3);
+            D.out_pitch = int64_t(V.width) * 3;
+            d2h.push_back({out_rgb[i], out_pitch[i], D.out_rgb, size_t(V.width) * 3, size_t(V.width) * 3,
+                           size_t(V.height)});
+        } else {
+            D.out_rgb = out_rgb[i];
+            D.out_pitch = int64_t(out_pitch[i]);
+        }
+        if (aux) {
+            const fvv_aux& A = aux[i];
+            auto plan = [&](void* user, size_t elem, void** dev_field) {
+                if (!user) return;
+                if (mem_kind(user) == MemKind::Host) {
+                    uint8_t* p = stage(np * elem);
+                    *dev_field = p;
+                    d2h.push_back({user, np * elem, p, np * elem, np * elem, 1});
+                } else {
+                    *dev_field = user;
+                }
+            };
+            plan(A.depth, 4, reinterpret_cast<void**>(&D.out_depth));
+            plan(A.hole, 1, reinterpret_cast<void**>(&D.out_hole));
+            plan(A.top3, 12, reinterpret_cast<void**>(&D.out_top3));
+            plan(A.keys, 8, reinterpret_cast<void**>(&D.out_keys));
+            if (A.keys_raw) {
+                raw_copies.push_back({A.keys_raw, D.keys});
+                raw_bytes.push_back(np * 8);
+                if (mem_kind(A.keys_raw) == MemKind::Host) any_host = true;
+            }
+        }
+    }
+    if (!d2h.empty()) any_host = true;
+    const size_t pbytes = geom_off + size_t(n) * c->n_cams * sizeof(CamGeom);
+    FVV_CUDA(cudaMemcpyAsync(P.dev, P.host, pbytes, cudaMemcpyHostToDevice, s));
+    const ViewDesc* vdev = reinterpret_cast<const ViewDesc*>(P.dev);
+
+    std::vector<int> used(c->slots, 0);
+    for (int i = 0; i < n; ++i) used[slot_of[i]] = 1;
+    for (int si = 0; si < c->slots; ++si)
+        if (used[si]) FVV_CUDA(cudaStreamWaitEvent(s, c->slot[si].uploaded, 0));
+
+    // the z-buffer scratch and output staging are shared by all batches of
+    // the context: a batch on another stream waits for the previous one
+    if (c->scratch_pending) FVV_CUDA(cudaStreamWaitEvent(s, c->scratch_done, 0));
+    FVV_CUDA(fvv::launch_clear_keys(c->keys, koff, s));
+    FVV_CUDA(fvv::launch_warp_splat(vdev, n, max_chunks, c->frames_dev, s));
+    for (size_t r = 0; r < raw_copies.size(); ++r)
+        FVV_CUDA(cudaMemcpyAsync(raw_copies[r].first, raw_copies[r].second, raw_bytes[r],
+                                 cudaMemcpyDefault, s));
+    FVV_CUDA(fvv::launch_resolve(vdev, n, max_h, max_w, c->n_cams, c->frames_dev, s));
+    for (const HostCopy& h : d2h)
+        FVV_CUDA(cudaMemcpy2DAsync(h.dst, h.dpitch, h.src, h.spitch, h.width, h.height,
+                                   cudaMemcpyDeviceToHost, s));
+    FVV_CUDA(cudaEventRecord(P.done, s));
+    P.pending = true;
+    FVV_CUDA(cudaEventRecord(c->scratch_done, s));
+    c->scratch_pending = true;
+    for (int si = 0; si < c->slots; ++si)
+        if (used[si]) {
+            FVV_CUDA(cudaEventRecord(c->slot[si].read, s));
+            c->slot[si].read_pending = true;
+        }
+    if (any_host) FVV_CUDA(cudaStreamSynchronize(s));
+    return FVV_OK;
+}
+
+fvv_status fvv_synthesize(fvv_ctx* c, const fvv_view* view, uint8_t* out_rgb, size_t out_pitch,
+                          const fvv_aux* aux, void* stream)
+{
+    return fvv_synthesize_batch(c, 1, view, nullptr, &out_rgb, &out_pitch, aux, stream);
+}
+
+}  // extern "C"

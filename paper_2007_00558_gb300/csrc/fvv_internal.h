@@ -1,0 +1,72 @@
+// fvv_internal.h -- device-side descriptors shared by the kernels and the
+// host runtime of libfvv.  Not part of the public ABI (see include/fvv.h).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace fvv {
+
+constexpr int kMaxCams = 64;
+constexpr int kSrcBits = 26;
+constexpr unsigned long long kKeyEmpty = ~0ull;
+constexpr int kSplatPix = 8;         // source pixels per splat thread (one 16-B load)
+constexpr int kSplatThreads = 256;
+constexpr int kResolveThreads = 256;
+
+constexpr int kFlagCrack = 1;
+constexpr int kFlagFill = 2;
+
+// Per (view, camera) quantities, composed on the host in FP64 and rounded
+// to FP32 once (Sec. VI geometry).  M maps (u z, v z, z, 1) of the camera to
+// (X, Y, Z) of the view; N maps (x Z, y Z, Z, 1) of the view to the camera.
+struct alignas(16) CamGeom {
+    float M[12];
+    float N[12];
+    float w;          // blend weight, 0 = inactive
+    float pad[3];
+};
+
+// One camera's frame in one slot of the device-resident frame ring.
+struct alignas(16) FrameRef {
+    const uint16_t* depth;   // [H][dpitch] depth codes, 0 = none
+    const uint32_t* rgba;    // [H][rpitch] R | G << 8 | B << 16
+    int32_t W, H;
+    int32_t dpitch;          // elements; rows 16-B aligned
+    int32_t rpitch;          // elements
+};
+
+// One view of a batched launch.
+struct alignas(16) ViewDesc {
+    int32_t Wv, Hv;
+    int32_t n_cams;
+    int32_t n_active;
+    int32_t slot;
+    int32_t flags;
+    float tau_crack, tau_vis, z_min;
+    uint32_t d_lo, d_hi;
+    int32_t pad0;
+    unsigned long long* keys;        // scratch z-buffer [Hv * Wv]
+    uint8_t* out_rgb;                // [Hv] rows of 3 * Wv bytes
+    int64_t out_pitch;               // bytes
+    float* out_depth;                // nullable [Hv * Wv]
+    uint8_t* out_hole;               // nullable [Hv * Wv]
+    float* out_top3;                 // nullable [Hv * Wv * 3]
+    unsigned long long* out_keys;    // nullable [Hv * Wv], after the crack filter
+    const CamGeom* geom;             // [n_cams]
+    int32_t active[kMaxCams];        // cameras with w > 0, ascending
+    int32_t chunk_begin[kMaxCams + 1];  // prefix of splat chunks over `active`
+};
+
+// Launchers (fvv_kernels.cu).  All asynchronous on `stream`.
+cudaError_t launch_clear_keys(unsigned long long* keys, size_t n, cudaStream_t stream);
+cudaError_t launch_warp_splat(const ViewDesc* views, int n_views, int max_chunks,
+                              const FrameRef* frames, cudaStream_t stream);
+cudaError_t launch_resolve(const ViewDesc* views, int n_views, int max_h, int max_w, int n_cams,
+                           const FrameRef* frames, cudaStream_t stream);
+cudaError_t launch_pack_rgba(const uint8_t* rgb, size_t rgb_pitch, uint32_t* rgba,
+                             int rpitch, int W, int H, cudaStream_t stream);
+size_t resolve_smem_bytes(int max_w, int n_cams);
+
+}  // namespace fvv

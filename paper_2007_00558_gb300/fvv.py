@@ -1,0 +1,251 @@
+"""Thin ctypes binding of libfvv.so (include/fvv.h): same names, argument
+marshalling only.  Every step of view synthesis runs in the library's CUDA
+kernels; there is no Python or CPU fallback, and loading fails loudly when the
+library has not been built.
+
+Pointers may be passed as ints, numpy arrays or torch tensors (host or CUDA);
+``stream`` may be None, an int handle, or a torch.cuda.Stream.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+import threading
+from typing import Optional, Sequence
+
+import numpy as np
+
+from . import build as _build
+
+FVV_OK = 0
+FVV_ERR_INVALID_ARG = 1
+FVV_ERR_OUT_OF_MEMORY = 2
+FVV_ERR_BUDGET = 3
+FVV_ERR_CUDA = 4
+FVV_ERR_TIMEOUT = 5
+FVV_ERR_BUSY = 6
+FVV_ERR_NOT_READY = 7
+FVV_ERR_STATE = 8
+FVV_MAX_CAMS = 64
+FVV_MAX_SRC_PIXELS = 1 << 26
+FVV_KEY_EMPTY = 0xFFFFFFFFFFFFFFFF
+
+_NAMES = {v: k for k, v in list(globals().items()) if k.startswith("FVV_ERR_") or k == "FVV_OK"}
+
+
+class FvvError(RuntimeError):
+    def __init__(self, code: int, func: str, msg: str):
+        super().__init__("%s failed: %s (%s)" % (func, msg, _NAMES.get(code, code)))
+        self.code = code
+
+
+class fvv_camera(C.Structure):
+    _fields_ = [("width", C.c_int32), ("height", C.c_int32),
+                ("fx", C.c_double), ("fy", C.c_double), ("cx", C.c_double), ("cy", C.c_double),
+                ("R", C.c_double * 9), ("t", C.c_double * 3)]
+
+
+fvv_view = fvv_camera
+
+
+class fvv_rig(C.Structure):
+    _fields_ = [("n_cams", C.c_int32), ("cams", C.POINTER(fvv_camera)),
+                ("look_at", C.c_double * 3), ("depth_unit_m", C.c_double)]
+
+
+class fvv_options(C.Structure):
+    _fields_ = [("n_ref", C.c_int32), ("crack_filter", C.c_int32), ("hole_fill", C.c_int32),
+                ("tau_crack", C.c_float), ("tau_vis", C.c_float), ("z_min", C.c_float),
+                ("d_lo", C.c_uint32), ("d_hi", C.c_uint32), ("frame_slots", C.c_int32),
+                ("max_batch", C.c_int32), ("memory_budget", C.c_uint64)]
+
+
+class fvv_aux(C.Structure):
+    _fields_ = [("depth", C.c_void_p), ("hole", C.c_void_p), ("top3", C.c_void_p),
+                ("keys", C.c_void_p), ("keys_raw", C.c_void_p)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load() -> C.CDLL:
+    """Load libfvv.so (built in-tree by ``paper_2007_00558_gb300.build``)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = lib_path()
+        if not os.path.exists(path):
+            raise RuntimeError("libfvv.so is not built (%s); run __graft_entry__.build() or "
+                               "python -m paper_2007_00558_gb300.build" % path)
+        lib = C.CDLL(path)
+        P, S, I, U64 = C.c_void_p, C.c_size_t, C.c_int32, C.c_uint64
+        sig = {
+            "fvv_default_options": [C.POINTER(fvv_options)],
+            "fvv_last_error": [],
+            "fvv_create": [C.POINTER(fvv_rig), C.POINTER(fvv_options), C.POINTER(P)],
+            "fvv_destroy": [P],
+            "fvv_upload_frame": [P, I, P, S, P, S, U64, P],
+            "fvv_upload_frames": [P, P, S, S, P, S, S, U64, P],
+            "fvv_latest_tick": [P, C.POINTER(U64)],
+            "fvv_synthesize": [P, C.POINTER(fvv_camera), P, S, C.POINTER(fvv_aux), P],
+            "fvv_synthesize_batch": [P, I, C.POINTER(fvv_camera), C.POINTER(U64), C.POINTER(P),
+                                     C.POINTER(S), C.POINTER(fvv_aux), P],
+            "fvv_view_params": [C.POINTER(fvv_rig), C.POINTER(fvv_options), C.POINTER(fvv_camera),
+                                P, P, P],
+        }
+        for name, args in sig.items():
+            f = getattr(lib, name)
+            f.argtypes = args
+            f.restype = C.c_char_p if name == "fvv_last_error" else C.c_int32
+        _lib = lib
+        return lib
+
+
+def header_symbols() -> list:
+    """Function names declared in include/fvv.h."""
+    hdr = os.path.join(_build.INCLUDE, "fvv.h")
+    text = open(hdr).read()
+    return sorted(set(re.findall(r"^\s*(?:fvv_status|const char\*)\s+(fvv_\w+)\s*\(", text, re.M)))
+
+
+def _check(code: int, func: str):
+    if code != FVV_OK:
+        msg = load().fvv_last_error()
+        raise FvvError(code, func, msg.decode() if msg else "")
+
+
+def ptr(x) -> Optional[int]:
+    """Data pointer of an int / numpy array / torch tensor (None -> NULL)."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    raise TypeError("cannot take a pointer of %r" % type(x))
+
+
+def stream_handle(stream) -> Optional[int]:
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def camera(c) -> fvv_camera:
+    """fvv_camera from any object with width, height, fx, fy, cx, cy, R, t."""
+    out = fvv_camera()
+    out.width, out.height = int(c.width), int(c.height)
+    out.fx, out.fy, out.cx, out.cy = float(c.fx), float(c.fy), float(c.cx), float(c.cy)
+    R = np.asarray(c.R, dtype=np.float64).reshape(9)
+    t = np.asarray(c.t, dtype=np.float64).reshape(3)
+    out.R[:] = [float(v) for v in R]
+    out.t[:] = [float(v) for v in t]
+    return out
+
+
+def rig(cams: Sequence, look_at, depth_unit_m: float = 0.001) -> fvv_rig:
+    arr = (fvv_camera * len(cams))(*[camera(c) for c in cams])
+    r = fvv_rig()
+    r.n_cams = len(cams)
+    r.cams = C.cast(arr, C.POINTER(fvv_camera))
+    r.look_at[:] = [float(v) for v in np.asarray(look_at, dtype=np.float64).reshape(3)]
+    r.depth_unit_m = float(depth_unit_m)
+    r._keep = arr
+    return r
+
+
+def fvv_default_options(**overrides) -> fvv_options:
+    o = fvv_options()
+    _check(load().fvv_default_options(C.byref(o)), "fvv_default_options")
+    for k, v in overrides.items():
+        if not hasattr(o, k):
+            raise AttributeError(k)
+        setattr(o, k, v)
+    return o
+
+
+def fvv_last_error() -> str:
+    m = load().fvv_last_error()
+    return m.decode() if m else ""
+
+
+def fvv_create(rig_: fvv_rig, opt: Optional[fvv_options] = None) -> int:
+    h = C.c_void_p()
+    _check(load().fvv_create(C.byref(rig_), C.byref(opt) if opt is not None else None,
+                             C.byref(h)), "fvv_create")
+    return h.value
+
+
+def fvv_destroy(ctx: int) -> None:
+    _check(load().fvv_destroy(ctx), "fvv_destroy")
+
+
+def fvv_upload_frame(ctx: int, cam: int, rgb, rgb_pitch: int, depth, depth_pitch: int,
+                     tick: int, stream=None) -> None:
+    _check(load().fvv_upload_frame(ctx, cam, ptr(rgb), rgb_pitch, ptr(depth), depth_pitch,
+                                   tick, stream_handle(stream)), "fvv_upload_frame")
+
+
+def fvv_upload_frames(ctx: int, rgb, rgb_cam_stride: int, rgb_pitch: int, depth,
+                      depth_cam_stride: int, depth_pitch: int, tick: int, stream=None) -> None:
+    _check(load().fvv_upload_frames(ctx, ptr(rgb), rgb_cam_stride, rgb_pitch, ptr(depth),
+                                    depth_cam_stride, depth_pitch, tick, stream_handle(stream)),
+           "fvv_upload_frames")
+
+
+def fvv_latest_tick(ctx: int) -> int:
+    t = C.c_uint64()
+    _check(load().fvv_latest_tick(ctx, C.byref(t)), "fvv_latest_tick")
+    return t.value
+
+
+def aux(depth=None, hole=None, top3=None, keys=None, keys_raw=None) -> fvv_aux:
+    a = fvv_aux()
+    a.depth, a.hole, a.top3, a.keys, a.keys_raw = (ptr(depth), ptr(hole), ptr(top3), ptr(keys),
+                                                   ptr(keys_raw))
+    return a
+
+
+def fvv_synthesize(ctx: int, view, out_rgb, out_pitch: int, aux_: Optional[fvv_aux] = None,
+                   stream=None) -> None:
+    v = view if isinstance(view, fvv_camera) else camera(view)
+    _check(load().fvv_synthesize(ctx, C.byref(v), ptr(out_rgb), out_pitch,
+                                 C.byref(aux_) if aux_ is not None else None,
+                                 stream_handle(stream)), "fvv_synthesize")
+
+
+def fvv_synthesize_batch(ctx: int, views: Sequence, ticks: Optional[Sequence[int]], out_rgb: Sequence,
+                         out_pitch: Sequence[int], aux_: Optional[Sequence[fvv_aux]] = None,
+                         stream=None) -> None:
+    n = len(views)
+    va = (fvv_camera * n)(*[v if isinstance(v, fvv_camera) else camera(v) for v in views])
+    ta = (C.c_uint64 * n)(*ticks) if ticks is not None else None
+    oa = (C.c_void_p * n)(*[ptr(o) for o in out_rgb])
+    pa = (C.c_size_t * n)(*out_pitch)
+    aa = (fvv_aux * n)(*aux_) if aux_ is not None else None
+    _check(load().fvv_synthesize_batch(ctx, n, va, ta, oa, pa, aa, stream_handle(stream)),
+           "fvv_synthesize_batch")
+
+
+def fvv_view_params(rig_: fvv_rig, opt: Optional[fvv_options], view):
+    """Host-only composition: returns M (K,3,4), N (K,3,4), w (K,) as float32."""
+    K = rig_.n_cams
+    M = np.zeros((K, 3, 4), np.float32)
+    N = np.zeros((K, 3, 4), np.float32)
+    w = np.zeros(K, np.float32)
+    v = view if isinstance(view, fvv_camera) else camera(view)
+    _check(load().fvv_view_params(C.byref(rig_), C.byref(opt) if opt is not None else None,
+                                  C.byref(v), M.ctypes.data, N.ctypes.data, w.ctypes.data),
+           "fvv_view_params")
+    return M, N, w

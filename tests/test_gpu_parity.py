@@ -1,0 +1,202 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle on the
+same seeded inputs.  Keys, hole mask and depth bit-exact; colour within 1/255
+on >= 99.9 % of pixels at >= 50 dB (see fvv_helpers.assert_parity)."""
+import numpy as np
+import pytest
+
+import synthetic as S
+from fvv_helpers import KEY_EMPTY, assert_parity, gpu_run, lib
+
+pytestmark = pytest.mark.gpu
+
+
+def _oracle(oracle_mod, cams, rgb, dep, view, O, **kw):
+    return oracle_mod.synthesize(cams, rgb, dep, view, O, **kw)
+
+
+def _opts(**kw):
+    return lib().fvv_default_options(**kw)
+
+
+def test_two_camera_plane_and_spheres(oracle_mod):
+    """Two parallel cameras 320x240, f = 300 px, 100 mm baseline; the view
+    midway between them."""
+    wl = S.workload("plain_2cam_320x240")
+    g = gpu_run(wl["cams"], wl["rgb"], wl["depth"], wl["views"], wl["look_at"])[0]
+    ref = _oracle(oracle_mod, wl["cams"], wl["rgb"], wl["depth"], wl["views"][0], wl["look_at"])
+    info = assert_parity(g, ref, "2cam")
+    assert info["exact_rgb_fraction"] == 1.0
+
+
+@pytest.fixture(scope="module")
+def arc_small():
+    return S.workload("plain_9cam_1280x720", scale=0.26)      # 333 x 187: ragged rows
+
+
+@pytest.fixture(scope="module")
+def arc_full():
+    return S.workload("plain_9cam_1280x720")
+
+
+def test_nine_camera_arc_small_batch(oracle_mod, arc_small):
+    """Nine noisy cameras on the 90 deg arc, three views of the swing
+    trajectory in one batch; 333 x 187 spans many tiles and a ragged tail."""
+    wl = arc_small
+    views = [wl["views"][i] for i in (0, 75, 210)]
+    gs = gpu_run(wl["cams"], wl["rgb"], wl["depth"], views, wl["look_at"])
+    for i, (g, v) in enumerate(zip(gs, views)):
+        ref = _oracle(oracle_mod, wl["cams"], wl["rgb"], wl["depth"], v, wl["look_at"])
+        assert_parity(g, ref, "view %d" % i)
+
+
+def test_nine_camera_arc_full_size(oracle_mod, arc_full):
+    """The 1280x720 nine-camera workload at full size, compared on every pixel."""
+    wl = arc_full
+    views = [wl["views"][i] for i in (37, 150)]
+    gs = gpu_run(wl["cams"], wl["rgb"], wl["depth"], views, wl["look_at"])
+    for i, (g, v) in enumerate(zip(gs, views)):
+        ref = _oracle(oracle_mod, wl["cams"], wl["rgb"], wl["depth"], v, wl["look_at"])
+        info = assert_parity(g, ref, "full view %d" % i)
+        assert info["exact_rgb_fraction"] >= 0.999
+
+
+@pytest.mark.parametrize("kw", [dict(n_ref=3), dict(n_ref=1), dict(crack_filter=0),
+                                dict(hole_fill=0), dict(crack_filter=0, hole_fill=0, n_ref=2),
+                                dict(tau_vis=0.0), dict(d_lo=1500, d_hi=3000)])
+def test_options(oracle_mod, arc_small, kw):
+    wl = arc_small
+    v = wl["views"][40]
+    g = gpu_run(wl["cams"], wl["rgb"], wl["depth"], [v], wl["look_at"], opts=_opts(**kw))[0]
+    ref = _oracle(oracle_mod, wl["cams"], wl["rgb"], wl["depth"], v, wl["look_at"], **kw)
+    assert_parity(g, ref, str(kw))
+
+
+def test_empty_input_all_holes(oracle_mod):
+    cams = S.rig_arc(3, 30.0, 1.5, 40, 30, 40.0)
+    rgb = np.full((3, 30, 40, 3), 200, np.uint8)
+    dep = np.zeros((3, 30, 40), np.uint16)
+    v = S.arc_view(5.0, 1.5, 40, 30, 40.0)
+    g = gpu_run(cams, rgb, dep, [v], [0, 0, 0])[0]
+    assert np.all(g["keys_raw"] == KEY_EMPTY) and np.all(g["keys"] == KEY_EMPTY)
+    assert np.all(g["hole"] == 1) and not g["rgb"].any() and not g["depth"].any()
+    assert_parity(g, _oracle(oracle_mod, cams, rgb, dep, v, [0, 0, 0]), "empty")
+
+
+def test_identity_pose_reproduces_input(arc_small):
+    wl = arc_small
+    k = 4
+    g = gpu_run(wl["cams"], wl["rgb"], wl["depth"], [wl["cams"][k].copy()], wl["look_at"],
+                opts=_opts(crack_filter=0, hole_fill=0))[0]
+    valid = wl["depth"][k] > 0
+    assert np.array_equal(g["rgb"][valid], wl["rgb"][k][valid])
+    assert np.array_equal(g["hole"].astype(bool), ~valid)
+
+
+def test_host_outputs_and_padded_pitches(oracle_mod, arc_small):
+    wl = arc_small
+    v = wl["views"][120]
+    ref = _oracle(oracle_mod, wl["cams"], wl["rgb"], wl["depth"], v, wl["look_at"])
+    g = gpu_run(wl["cams"], wl["rgb"], wl["depth"], [v], wl["look_at"], host_out=True,
+                rgb_pitch_pad=13, depth_pitch_pad=6, out_pitch_pad=5)[0]
+    assert_parity(g, ref, "host outputs")
+
+
+def test_mixed_view_sizes_in_one_batch(oracle_mod, arc_small):
+    wl = arc_small
+    base = wl["views"][60]
+    views = []
+    for (W, H, f) in ((1, 1, 3.0), (64, 48, 60.0), (333, 187, 260.0), (500, 260, 400.0)):
+        c = base.copy()
+        c.width, c.height, c.fx, c.fy, c.cx, c.cy = W, H, f, f, (W - 1) / 2, (H - 1) / 2
+        views.append(c)
+    gs = gpu_run(wl["cams"], wl["rgb"], wl["depth"], views, wl["look_at"])
+    for g, v in zip(gs, views):
+        assert_parity(g, _oracle(oracle_mod, wl["cams"], wl["rgb"], wl["depth"], v, wl["look_at"]),
+                      "%dx%d" % (v.width, v.height))
+
+
+def test_sixty_four_cameras(oracle_mod):
+    """The 6-bit camera field at its limit: 64 cameras on a full circle."""
+    cams = S.rig_arc(64, 354.375, 1.5, 24, 16, 20.0)
+    scene = S.scene_random_objects(11, n_objects=12)
+    rgb, dep = S.frames_for(scene, cams)
+    v = S.arc_view(176.0, 1.4, 48, 32, 40.0)          # next to camera 63 (177.2 deg)
+    g = gpu_run(cams, rgb, dep, [v], [0, 0, 0])[0]
+    ref = _oracle(oracle_mod, cams, rgb, dep, v, [0, 0, 0])
+    assert_parity(g, ref, "64 cams")
+    z, cam, src = oracle_mod.key_fields(g["keys_raw"])
+    assert cam.max() == 63
+
+
+def test_largest_source_image(oracle_mod):
+    """The 26-bit source-pixel field at its limit: one 8192 x 8192 camera."""
+    W = H = 8192
+    cam = S.Camera(W, H, 4000.0, 4000.0, (W - 1) / 2, (H - 1) / 2, np.eye(3), np.zeros(3))
+    rng = np.random.default_rng(5)
+    dep = np.zeros((1, H, W), np.uint16)
+    rows = np.arange(H - 64, H)
+    dep[0, rows, :] = rng.integers(1500, 2500, (64, W)).astype(np.uint16)
+    rgb = np.zeros((1, H, W, 3), np.uint8)
+    rgb[0, rows] = rng.integers(0, 256, (64, W, 3)).astype(np.uint8)
+    view = S.Camera(256, 256, 125.0, 125.0, 127.5, 127.5, np.eye(3), np.zeros(3))
+    g = gpu_run([cam], rgb, dep, [view], [0, 0, 2.0], opts=_opts(crack_filter=0))[0]
+    ref = _oracle(oracle_mod, [cam], rgb, dep, view, [0, 0, 2.0], crack_filter=0)
+    assert_parity(g, ref, "8192^2")
+    z, c, src = oracle_mod.key_fields(g["keys_raw"])
+    assert src.max() > (1 << 26) - 8192 * 4
+
+
+def test_frame_ring_ticks_and_errors(oracle_mod):
+    """Ticks live in slot tick % frame_slots; a view may name any resident
+    complete tick; evicted or incomplete ticks and stale uploads are errors."""
+    import torch
+    F = lib()
+    cams = S.rig_arc(3, 40.0, 1.5, 64, 40, 60.0)
+    frames = []
+    for t in range(4):
+        rgb, dep = S.frames_for(S.scene_random_objects(100 + t, n_objects=6), cams, noise_seed=t)
+        frames.append((rgb, dep))
+    v = S.arc_view(7.0, 1.5, 64, 40, 60.0)
+    ctx = F.fvv_create(F.rig(cams, [0, 0, 0]), F.fvv_default_options(frame_slots=2))
+    try:
+        with pytest.raises(F.FvvError) as e:
+            F.fvv_latest_tick(ctx)
+        assert e.value.code == F.FVV_ERR_NOT_READY
+        for t, (rgb, dep) in enumerate(frames):
+            for k in range(3):
+                F.fvv_upload_frame(ctx, k, np.ascontiguousarray(rgb[k]), 64 * 3,
+                                   np.ascontiguousarray(dep[k]), 64 * 2, t)
+        assert F.fvv_latest_tick(ctx) == 3
+        outs = [torch.zeros((40, 64 * 3), dtype=torch.uint8, device="cuda") for _ in range(2)]
+        F.fvv_synthesize_batch(ctx, [v, v], [2, 3], outs, [192, 192])
+        torch.cuda.synchronize()
+        for t, o in zip((2, 3), outs):
+            ref = oracle_mod.synthesize(cams, frames[t][0], frames[t][1], v, [0, 0, 0])
+            assert np.abs(o.cpu().numpy().reshape(40, 64, 3).astype(int) - ref["rgb"]).max() <= 1
+        with pytest.raises(F.FvvError) as e:
+            F.fvv_synthesize_batch(ctx, [v], [1], outs[:1], [192])
+        assert e.value.code == F.FVV_ERR_NOT_READY
+        with pytest.raises(F.FvvError) as e:
+            F.fvv_upload_frame(ctx, 0, np.ascontiguousarray(frames[0][0][0]), 192,
+                               np.ascontiguousarray(frames[0][1][0]), 128, 1)
+        assert e.value.code == F.FVV_ERR_STATE
+        # a partial tick is not visible
+        F.fvv_upload_frame(ctx, 0, np.ascontiguousarray(frames[0][0][0]), 192,
+                           np.ascontiguousarray(frames[0][1][0]), 128, 4)
+        assert F.fvv_latest_tick(ctx) == 3
+        with pytest.raises(F.FvvError) as e:
+            F.fvv_synthesize_batch(ctx, [v], [4], outs[:1], [192])
+        assert e.value.code == F.FVV_ERR_NOT_READY
+    finally:
+        F.fvv_destroy(ctx)
+
+
+def test_user_stream_and_determinism(oracle_mod, arc_small):
+    import torch
+    wl = arc_small
+    v = wl["views"][200]
+    s = torch.cuda.Stream()
+    a = gpu_run(wl["cams"], wl["rgb"], wl["depth"], [v], wl["look_at"], stream=s)[0]
+    b = gpu_run(wl["cams"], wl["rgb"], wl["depth"], [v], wl["look_at"])[0]
+    for k in ("rgb", "keys", "keys_raw", "depth", "top3", "hole"):
+        assert np.array_equal(a[k], b[k]), k
