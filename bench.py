@@ -1,0 +1,456 @@
+#!/usr/bin/env python3
+"""Throughput of DIBR view synthesis (FVV Live, Sec. VI) on GB300.
+
+Workload: nine cameras 1280x720 (RGB8 + uint16 depth) on a 90 deg arc of
+radius 1.5 m, 1 % depth noise and 5 % dropout discs, one 1280x720 virtual view
+per frame along the swing trajectory phi(t) = 22.5 deg sin(2 pi t / 300).
+Synthetic, seeded inputs (the paper's captured sequences are not available).
+
+A step is one batch of ``--batch`` views synthesised by one
+``fvv_synthesize_batch`` call (steps a-e of the hot path: three kernel
+launches).  Each view of a step reads its own frame tick from a ring of
+``--slots`` device-resident ticks, so consecutive reads of a tick are
+separated by more frame data than the 129 MB L2 holds.
+
+``value``: views/s over all ranks with inputs resident in HBM.
+``e2e``: the same metric through the C ABI with host buffers: every view
+uploads its tick's frames from pinned host memory and the batch writes its
+RGB8 results to pinned host memory, all inside the timed region.
+``--impl reference``: the CPU oracle on the host cores, same workload.
+
+Under torchrun each rank renders its own share of views (replicas: the path
+has no exchange step); timing is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOAD = "plain_9cam_1280x720"
+METRIC = "720p views/s, 9 cams (plain vs +net at stated PSNR); p99 per-view latency ms"
+UNIT = "views/s"
+
+
+def parse_args():
+    p = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=200)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", choices=["fvv", "reference"], default="fvv")
+    p.add_argument("--batch", type=int, default=8, help="views per step (one batched call)")
+    p.add_argument("--slots", type=int, default=16, help="device-resident frame ticks")
+    p.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU-baseline sample length")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-profile", action="store_true",
+                   help="do not bracket kernels with events in the timed region")
+    return p.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# oracle workers (CPU baseline and the reference arm); spawn context only
+# ---------------------------------------------------------------------------
+_W = {}
+
+
+def _worker_init(shm_rgb, shm_dep, shape_rgb, shape_dep):
+    import numpy as np
+    from multiprocessing import shared_memory
+    import oracle
+    import synthetic as S
+    a = shared_memory.SharedMemory(name=shm_rgb)
+    b = shared_memory.SharedMemory(name=shm_dep)
+    _W["shm"] = (a, b)
+    _W["rgb"] = np.ndarray(shape_rgb, np.uint8, buffer=a.buf)
+    _W["dep"] = np.ndarray(shape_dep, np.uint16, buffer=b.buf)
+    K, H, W = shape_dep
+    _W["cams"] = S.rig_arc(K, 90.0, 1.5, W, H, 1000.0)
+    _W["views"] = S.trajectory_arc(300, 22.5, 1.5, W, H, 1000.0)
+    _W["oracle"] = oracle
+    oracle.build()
+
+
+def _worker_views(idx):
+    t0 = time.perf_counter()
+    for i in idx:
+        _W["oracle"].synthesize(_W["cams"], _W["rgb"], _W["dep"], _W["views"][i % 300],
+                                [0.0, 0.0, 0.0])
+    return len(idx), time.perf_counter() - t0
+
+
+def _worker_for(seconds, start):
+    t0 = time.perf_counter()
+    n = 0
+    while time.perf_counter() - t0 < seconds:
+        _W["oracle"].synthesize(_W["cams"], _W["rgb"], _W["dep"], _W["views"][(start + n) % 300],
+                                [0.0, 0.0, 0.0])
+        n += 1
+    return n, time.perf_counter() - t0
+
+
+class OraclePool:
+    """Spawned worker processes, each running the single-threaded C oracle
+    on frames shared through POSIX shared memory."""
+
+    def __init__(self, rgb, dep, procs=None):
+        import multiprocessing as mp
+        from multiprocessing import shared_memory
+        self.procs = procs or max(1, min(16, os.cpu_count() or 1))
+        self.a = shared_memory.SharedMemory(create=True, size=rgb.nbytes)
+        self.b = shared_memory.SharedMemory(create=True, size=dep.nbytes)
+        import numpy as np
+        np.ndarray(rgb.shape, np.uint8, buffer=self.a.buf)[...] = rgb
+        np.ndarray(dep.shape, np.uint16, buffer=self.b.buf)[...] = dep
+        ctx = mp.get_context("spawn")
+        self.pool = ctx.Pool(self.procs, initializer=_worker_init,
+                             initargs=(self.a.name, self.b.name, rgb.shape, dep.shape))
+
+    def run_for(self, seconds):
+        t0 = time.perf_counter()
+        res = self.pool.starmap(_worker_for, [(seconds, 37 * i) for i in range(self.procs)])
+        wall = time.perf_counter() - t0
+        return sum(r[0] for r in res), wall
+
+    def run_views(self, idx_lists):
+        return self.pool.map(_worker_views, idx_lists)
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+        self.a.close()
+        self.a.unlink()
+        self.b.close()
+        self.b.unlink()
+
+
+# ---------------------------------------------------------------------------
+# clocks
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.lines = []
+        self.proc = None
+        self.t_start = self.t_stop = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            threading.Thread(target=self._read, daemon=True).start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append((time.time(), line.strip()))
+
+    def mark(self, which):
+        setattr(self, "t_" + which, time.time())
+
+    def stop(self):
+        if self.proc:
+            time.sleep(0.15)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        for t, line in self.lines:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 10:
+                continue
+            try:
+                rows.append((t, float(parts[2]), float(parts[3]), parts[6:10]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        inside = [r for r in rows if self.t_start and self.t_stop and
+                  self.t_start - 0.1 <= r[0] <= self.t_stop + 0.1]
+        use = inside or rows
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in use for i, v in enumerate(r[3]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[1] for r in use), "sm_max_mhz": max(r[2] for r in use),
+                "reasons": reasons, "samples": len(use)}
+
+
+# ---------------------------------------------------------------------------
+# roofline helpers
+# ---------------------------------------------------------------------------
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_source_sha():
+    h = hashlib.sha256()
+    for f in ("fvv_kernels.cu", "fvv_internal.h"):
+        with open(os.path.join(ROOT, "paper_2007_00558_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel, views_per_launch):
+    """DRAM bytes per launch from the committed ncu summary of this kernel,
+    scaled from its per-view figure; None when the kernel source changed
+    since the counters were taken."""
+    path = os.path.join(ROOT, "profiles", "%s_9cam_1280x720.txt" % kernel)
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    m = re.search(r"^dram_bytes_per_view:\s*([0-9.eE+]+)", text, re.M)
+    s = re.search(r"^kernel_source_sha:\s*([0-9a-f]+)", text, re.M)
+    if not m or not s or s.group(1) != kernel_source_sha():
+        return None
+    return float(m.group(1)) * views_per_launch
+
+
+def algorithmic_bytes(K, Ns, Nd, rho, n_ref):
+    """Per-view algorithmic bytes of each kernel (RGB counted as 3 bytes):
+    clear: 8 Nd; splat: depth 2 K Ns + one 8-byte atomicMin per valid source
+    pixel 8 rho K Ns; resolve: keys 8 Nd + backward depth and colour gathers
+    (2 + 3)(n_ref - 1) Nd + winner colour 3 Nd + output 3 Nd."""
+    return {"clear_keys": 8.0 * Nd,
+            "warp_splat": 2.0 * K * Ns + 8.0 * rho * K * Ns,
+            "resolve": 8.0 * Nd + 5.0 * (n_ref - 1) * Nd + 3.0 * Nd + 3.0 * Nd}
+
+
+# ---------------------------------------------------------------------------
+# arms
+# ---------------------------------------------------------------------------
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import numpy as np
+    import synthetic as S
+    wl = S.workload(WORKLOAD)
+    pool = OraclePool(wl["rgb"], wl["depth"])
+    P = pool.procs
+    try:
+        for i in range(args.warmup):
+            pool.run_views([[i * P + j] for j in range(P)])
+        t0 = time.perf_counter()
+        for i in range(args.steps):
+            pool.run_views([[(args.warmup + i) * P + j] for j in range(P)])
+        el = time.perf_counter() - t0
+    finally:
+        pool.close()
+    value = args.steps * P / el
+    sample = "%d steps x %d views of the 9-camera 1280x720 swing (one view per worker process)" % (
+        args.steps, P)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "cams": 9, "src": "1280x720", "view": "1280x720",
+                   "views_per_step": P, "parallelism": "host processes"},
+        "impl": "reference",
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": P, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def run_fvv(args):
+    import numpy as np
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    import synthetic as S
+    from paper_2007_00558_gb300 import build as B
+    B.build()
+    import paper_2007_00558_gb300.fvv as F
+
+    wl = S.workload(WORKLOAD)
+    cams, views = wl["cams"], wl["views"]
+    K = len(cams)
+    H, W = cams[0].height, cams[0].width
+    Bsz, slots = args.batch, max(args.slots, args.batch)
+    opts = F.fvv_default_options(frame_slots=slots, max_batch=Bsz)
+    ctx = F.fvv_create(F.rig(cams, wl["look_at"]), opts)
+    stream = torch.cuda.current_stream()
+
+    rgb_h = torch.from_numpy(np.ascontiguousarray(wl["rgb"])).pin_memory()
+    dep_h = torch.from_numpy(np.ascontiguousarray(wl["depth"]).view(np.int16)).pin_memory()
+    for t in range(slots):
+        F.fvv_upload_frames(ctx, rgb_h, H * W * 3, W * 3, dep_h, H * W * 2, W * 2, t, stream)
+    torch.cuda.synchronize()
+    out = [torch.empty((H, W, 3), dtype=torch.uint8, device="cuda") for _ in range(Bsz)]
+    pitches = [W * 3] * Bsz
+    off = rank * 7919
+
+    def step(i):
+        vs = [views[(off + i * Bsz + j) % 300] for j in range(Bsz)]
+        ticks = [(i * Bsz + j) % slots for j in range(Bsz)]
+        F.fvv_synthesize_batch(ctx, vs, ticks, out, pitches, None, stream)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize()
+    F.fvv_profile_read(ctx, reset=True)
+    F.fvv_profile_enable(ctx, not args.no_profile)
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks.mark("start")
+    ev0.record(stream)
+    for i in range(args.steps):
+        step(args.warmup + i)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clocks.mark("stop")
+    barrier()
+    clocks.stop()
+    el_ms = ev0.elapsed_time(ev1)
+    stats = F.fvv_profile_read(ctx, reset=True)
+    F.fvv_profile_enable(ctx, False)
+    if world > 1:
+        t = torch.tensor([el_ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        el_ms = float(t.item())
+    n_views = args.steps * Bsz * world
+    value = n_views / (el_ms / 1e3)
+
+    # roofline of the dominant kernel
+    Ns = Nd = H * W
+    rho = float(np.count_nonzero(wl["depth"])) / wl["depth"].size
+    alg = algorithmic_bytes(K, Ns, Nd, rho, K)
+    timed = {k: v for k, v in stats.items() if v[1] > 0}
+    roofline = None
+    launches = sum(v[0] for v in stats.values())
+    if timed:
+        dom = max(timed, key=lambda k: timed[k][2])
+        n_l, n_t, ms = timed[dom]
+        avg_s = ms / n_t / 1e3
+        achieved = alg[dom] * Bsz / avg_s / 1e9
+        peak, src = measured_peaks()
+        roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
+                    "unit": "GB/s", "frac": achieved / peak, "peak_source": src,
+                    "traffic": profiled_traffic(dom, Bsz),
+                    "alg_bytes_per_launch": alg[dom] * Bsz, "avg_launch_us": avg_s * 1e6,
+                    "kernel_share": {k: v[2] / sum(x[2] for x in timed.values()) for k, v in timed.items()},
+                    "step_alg_bytes_per_view": sum(alg.values()),
+                    "step_frac": sum(alg.values()) * n_views / world / (el_ms / 1e3) / 1e9 / peak}
+
+    # end to end through the C ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        out_h = [torch.empty((H, W, 3), dtype=torch.uint8).pin_memory() for _ in range(Bsz)]
+        tick = [slots]
+
+        def e2e_step(i):
+            vs, ticks = [], []
+            for j in range(Bsz):
+                F.fvv_upload_frames(ctx, rgb_h, H * W * 3, W * 3, dep_h, H * W * 2, W * 2,
+                                    tick[0], stream)
+                ticks.append(tick[0])
+                tick[0] += 1
+                vs.append(views[(off + i * Bsz + j) % 300])
+            F.fvv_synthesize_batch(ctx, vs, ticks, out_h, pitches, None, stream)
+
+        for i in range(args.warmup):
+            e2e_step(i)
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        for i in range(args.steps):
+            e2e_step(args.warmup + i)
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([el], device="cuda")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            el = float(t.item())
+        e2e = {"value": n_views / el, "unit": UNIT,
+               "h2d_bytes_per_step": int(Bsz * (rgb_h.numel() + dep_h.numel() * 2)),
+               "d2h_bytes_per_step": int(Bsz * H * W * 3)}
+
+    F.fvv_destroy(ctx)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        pool = OraclePool(wl["rgb"], wl["depth"])
+        try:
+            pool.run_views([[0] for _ in range(pool.procs)])      # warm the workers
+            n, wall = pool.run_for(args.cpu_seconds)
+        finally:
+            pool.close()
+        cpu = {"value": n / wall, "unit": UNIT, "cores": pool.procs, "kind": "oracle",
+               "sample": "%d views of the 9-camera 1280x720 swing in %.1f s on %d worker processes "
+                         "(one single-threaded oracle each)" % (n, wall, pool.procs)}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": el_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "cams": K, "src": "%dx%d" % (W, H),
+                       "view": "%dx%d" % (W, H), "views_per_step": Bsz, "frame_slots": slots,
+                       "l2": "inputs > L2: each view reads its own frame tick, %d ticks x %.1f MB "
+                             "resident" % (slots, K * H * W * 6 / 1e6),
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": int(launches), "clocks": clocks.summary(),
+            "kernel_ms": {k: v[2] for k, v in stats.items()},
+        }
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_fvv(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

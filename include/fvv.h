@@ -166,6 +166,25 @@ fvv_status fvv_synthesize_batch(fvv_ctx* ctx, int32_t n, const fvv_view* views,
 fvv_status fvv_view_params(const fvv_rig* rig, const fvv_options* opt,
                            const fvv_view* view, float* M, float* N, float* w);
 
+/* ---- profiling (per-stage timing, after the paper's per-stage times of
+ * Sec. VIII: decode, synthesis, end-to-end) ------------------------------ */
+
+/* Per-kernel statistics of one context. */
+typedef struct fvv_kernel_stats {
+    char name[32];              /* "clear_keys", "warp_splat", "resolve", "pack_rgba" */
+    uint64_t launches;          /* launches since the last reset */
+    uint64_t timed;             /* of which bracketed by CUDA events */
+    double total_ms;            /* summed event durations of the timed launches */
+} fvv_kernel_stats;
+
+/* on = 1: bracket every kernel launch of `ctx` with CUDA events recorded on
+ * the launching stream (adds two event records per launch); 0: counts only. */
+fvv_status fvv_profile_enable(fvv_ctx* ctx, int32_t on);
+
+/* Copy up to *n entries into `out` (NULL = only return the count in *n);
+ * waits for the recorded events.  reset = 1 clears the statistics. */
+fvv_status fvv_profile_read(fvv_ctx* ctx, fvv_kernel_stats* out, int32_t* n, int32_t reset);
+
 #ifdef __cplusplus
 }
 #endif

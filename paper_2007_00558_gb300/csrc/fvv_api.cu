@@ -214,6 +214,16 @@ struct ParamBlock {
     bool pending = false;
 };
 
+enum Kid { kClear = 0, kSplat, kResolve, kPack, kNumKernels };
+const char* const kKernelName[kNumKernels] = {"clear_keys", "warp_splat", "resolve", "pack_rgba"};
+
+struct KernelStat {
+    uint64_t launches = 0;
+    uint64_t timed = 0;
+    double ms = 0.0;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending;
+};
+
 struct SlotState {
     uint64_t tick = 0;
     uint64_t mask = 0;
@@ -257,6 +267,9 @@ struct fvv_ctx {
     int pnext = 0;
     cudaEvent_t scratch_done = nullptr;         // after the last batch's use of keys / out_stage
     bool scratch_pending = false;
+    bool profiling = false;
+    KernelStat kstat[kNumKernels];
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> event_pool;
     size_t held = 0;                            // device bytes held
 };
 
@@ -280,6 +293,37 @@ void dev_free(fvv_ctx* c, void* p, size_t bytes)
         cudaFree(p);
         c->held -= bytes;
     }
+}
+
+// Launch through `fn` (returns cudaError_t), counting it and, when profiling
+// is on, bracketing it with events on the launching stream.
+template <class Fn>
+fvv_status run_kernel(fvv_ctx* c, Kid id, cudaStream_t s, Fn fn)
+{
+    KernelStat& K = c->kstat[id];
+    std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
+    if (c->profiling) {
+        if (c->event_pool.empty()) {
+            FVV_CUDA(cudaEventCreate(&ev.first));
+            FVV_CUDA(cudaEventCreate(&ev.second));
+        } else {
+            ev = c->event_pool.back();
+            c->event_pool.pop_back();
+        }
+        FVV_CUDA(cudaEventRecord(ev.first, s));
+    }
+    cudaError_t e = fn();
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        if (ev.first) c->event_pool.push_back(ev);
+        return fail(FVV_ERR_CUDA, std::string("launch of ") + kKernelName[id] + ": " + cudaGetErrorString(e));
+    }
+    ++K.launches;
+    if (ev.first) {
+        FVV_CUDA(cudaEventRecord(ev.second, s));
+        K.pending.push_back(ev);
+    }
+    return FVV_OK;
 }
 
 size_t param_bytes(int n, int n_cams)
@@ -353,7 +397,9 @@ fvv_status upload_one(fvv_ctx* c, int cam, const uint8_t* rgb, size_t rgb_pitch,
         src = c->stage_rgb[cam];
         spitch = size_t(C.width) * 3;
     }
-    FVV_CUDA(fvv::launch_pack_rgba(src, spitch, rdst, c->rpitch[cam], C.width, C.height, s));
+    FVV_TRY(run_kernel(c, kPack, s, [&] {
+        return fvv::launch_pack_rgba(src, spitch, rdst, c->rpitch[cam], C.width, C.height, s);
+    }));
     FVV_CUDA(cudaEventRecord(S.uploaded, s));
     S.mask |= uint64_t(1) << cam;
     if (S.mask == c->full_mask && (!c->have_latest || tick > c->latest)) {
@@ -453,6 +499,12 @@ fvv_status fvv_destroy(fvv_ctx* c)
         if (S.read) cudaEventDestroy(S.read);
     }
     if (c->scratch_done) cudaEventDestroy(c->scratch_done);
+    for (auto& K : c->kstat)
+        for (auto& ev : K.pending) c->event_pool.push_back(ev);
+    for (auto& ev : c->event_pool) {
+        cudaEventDestroy(ev.first);
+        cudaEventDestroy(ev.second);
+    }
     for (int k = 0; k < c->n_cams; ++k)
         if (c->stage_rgb[k])
             dev_free(c, c->stage_rgb[k], size_t(c->cams[k].width) * 3 * size_t(c->cams[k].height));
@@ -750,12 +802,16 @@ fvv_status fvv_synthesize_batch(fvv_ctx* c, int32_t n, const fvv_view* views, co
     // the z-buffer scratch and output staging are shared by all batches of
     // the context: a batch on another stream waits for the previous one
     if (c->scratch_pending) FVV_CUDA(cudaStreamWaitEvent(s, c->scratch_done, 0));
-    FVV_CUDA(fvv::launch_clear_keys(c->keys, koff, s));
-    FVV_CUDA(fvv::launch_warp_splat(vdev, n, max_chunks, c->frames_dev, s));
+    FVV_TRY(run_kernel(c, kClear, s, [&] { return fvv::launch_clear_keys(c->keys, koff, s); }));
+    FVV_TRY(run_kernel(c, kSplat, s, [&] {
+        return fvv::launch_warp_splat(vdev, n, max_chunks, c->frames_dev, s);
+    }));
     for (size_t r = 0; r < raw_copies.size(); ++r)
         FVV_CUDA(cudaMemcpyAsync(raw_copies[r].first, raw_copies[r].second, raw_bytes[r],
                                  cudaMemcpyDefault, s));
-    FVV_CUDA(fvv::launch_resolve(vdev, n, max_h, max_w, c->n_cams, c->frames_dev, s));
+    FVV_TRY(run_kernel(c, kResolve, s, [&] {
+        return fvv::launch_resolve(vdev, n, max_h, max_w, c->n_cams, c->frames_dev, s);
+    }));
     for (const HostCopy& h : d2h)
         FVV_CUDA(cudaMemcpy2DAsync(h.dst, h.dpitch, h.src, h.spitch, h.width, h.height,
                                    cudaMemcpyDeviceToHost, s));
@@ -769,6 +825,47 @@ fvv_status fvv_synthesize_batch(fvv_ctx* c, int32_t n, const fvv_view* views, co
             c->slot[si].read_pending = true;
         }
     if (any_host) FVV_CUDA(cudaStreamSynchronize(s));
+    return FVV_OK;
+}
+
+fvv_status fvv_profile_enable(fvv_ctx* c, int32_t on)
+{
+    if (!c) return fail(FVV_ERR_INVALID_ARG, "ctx is NULL");
+    c->profiling = on != 0;
+    return FVV_OK;
+}
+
+fvv_status fvv_profile_read(fvv_ctx* c, fvv_kernel_stats* out, int32_t* n, int32_t reset)
+{
+    if (!c || !n) return fail(FVV_ERR_INVALID_ARG, "NULL argument");
+    for (auto& K : c->kstat) {
+        for (auto& ev : K.pending) {
+            FVV_CUDA(cudaEventSynchronize(ev.second));
+            float ms = 0.0f;
+            FVV_CUDA(cudaEventElapsedTime(&ms, ev.first, ev.second));
+            K.ms += double(ms);
+            ++K.timed;
+            c->event_pool.push_back(ev);
+        }
+        K.pending.clear();
+    }
+    if (out) {
+        const int m = std::min<int>(*n, kNumKernels);
+        for (int i = 0; i < m; ++i) {
+            std::memset(&out[i], 0, sizeof out[i]);
+            std::snprintf(out[i].name, sizeof out[i].name, "%s", kKernelName[i]);
+            out[i].launches = c->kstat[i].launches;
+            out[i].timed = c->kstat[i].timed;
+            out[i].total_ms = c->kstat[i].ms;
+        }
+    }
+    *n = kNumKernels;
+    if (reset)
+        for (auto& K : c->kstat) {
+            K.launches = 0;
+            K.timed = 0;
+            K.ms = 0.0;
+        }
     return FVV_OK;
 }
 

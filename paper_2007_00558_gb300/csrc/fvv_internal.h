@@ -11,7 +11,7 @@ namespace fvv {
 constexpr int kMaxCams = 64;
 constexpr int kSrcBits = 26;
 constexpr unsigned long long kKeyEmpty = ~0ull;
-constexpr int kSplatPix = 8;         // source pixels per splat thread (one 16-B load)
+constexpr int kSplatPix = 16;        // source pixels per splat thread (two 16-B loads)
 constexpr int kSplatThreads = 256;
 constexpr int kResolveThreads = 256;
 
@@ -33,7 +33,7 @@ struct alignas(16) FrameRef {
     const uint16_t* depth;   // [H][dpitch] depth codes, 0 = none
     const uint32_t* rgba;    // [H][rpitch] R | G << 8 | B << 16
     int32_t W, H;
-    int32_t dpitch;          // elements; rows 16-B aligned
+    int32_t dpitch;          // elements; rows 128-B aligned
     int32_t rpitch;          // elements
 };
 

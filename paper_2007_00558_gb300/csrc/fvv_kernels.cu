@@ -60,58 +60,130 @@ __global__ void __launch_bounds__(256) k_clear_keys(unsigned long long* __restri
 {
     const size_t stride = size_t(gridDim.x) * blockDim.x;
     const size_t i0 = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    ulonglong2* k2 = reinterpret_cast<ulonglong2*>(keys);
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
     const size_t npair = n >> 1;
     for (size_t j = i0; j < npair; j += stride)
-        k2[j] = make_ulonglong2(kKeyEmpty, kKeyEmpty);
+        asm volatile("st.global.L2::cache_hint.v2.u64 [%0], {%1, %2}, %3;" ::"l"(keys + 2 * j),
+                     "l"(kKeyEmpty), "l"(kKeyEmpty), "l"(pol)
+                     : "memory");
     if ((n & 1) && i0 == 0)
         keys[n - 1] = kKeyEmpty;
 }
 
 // ---------------------------------------------------------------------------
+// cache-policy helpers (PTX createpolicy / cache_hint forms, sm_80+)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t policy_evict_first()
+{
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
+__device__ __forceinline__ uint64_t policy_evict_last()
+{
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
+// streaming 16-byte load: read once, do not keep in L1, evict first from L2
+__device__ __forceinline__ uint4 ld_stream_u4(const void* ptr, uint64_t pol)
+{
+    uint4 v;
+    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "l"(ptr), "l"(pol));
+    return v;
+}
+
+// z-buffer read at L2 (the value may be stale, but keys only ever decrease,
+// so a stale value is never below the current one)
+__device__ __forceinline__ unsigned long long ld_key(const unsigned long long* ptr, uint64_t pol)
+{
+    unsigned long long v;
+    asm volatile("ld.global.cg.L2::cache_hint.u64 %0, [%1], %2;" : "=l"(v) : "l"(ptr), "l"(pol));
+    return v;
+}
+
+// fire-and-forget 64-bit atomic minimum, kept in L2
+__device__ __forceinline__ void red_min_key(unsigned long long* ptr, unsigned long long v, uint64_t pol)
+{
+    asm volatile("red.global.min.L2::cache_hint.u64 [%0], %1, %2;" ::"l"(ptr), "l"(v), "l"(pol)
+                 : "memory");
+}
+
+// ---------------------------------------------------------------------------
 // (a) + (b): forward warp and z-buffer splat.
-// One thread = 8 consecutive source pixels of one row of one active camera
-// (one 16-byte depth load).  Threads of a view are numbered camera-major
-// over the active cameras: chunk_begin[a] .. chunk_begin[a+1).
+// One thread = 16 consecutive source pixels of one row of one active camera
+// (two 16-byte depth loads).  Threads of a view are numbered camera-major
+// over the active cameras: chunk_begin[a] .. chunk_begin[a+1).  Every CTA
+// belongs to one view, whose maps and frame table it stages in shared memory.
+// A point is splatted only when its key is below the key read at its target
+// pixel first: keys only decrease, so the skipped atomics could not win.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kSplatThreads)
 k_warp_splat(const ViewDesc* __restrict__ views, const FrameRef* __restrict__ frames)
 {
+    __shared__ __align__(16) float s_M[kMaxCams][12];
+    __shared__ __align__(16) FrameRef s_F[kMaxCams];
+    __shared__ int s_cb[kMaxCams + 1];
+    __shared__ int s_act[kMaxCams];
     const ViewDesc* V = views + blockIdx.y;
-    const int chunk = blockIdx.x * kSplatThreads + threadIdx.x;
-    const int n_active = V->n_active;
-    if (chunk >= V->chunk_begin[n_active])
+    const int na = V->n_active;
+    const int first = blockIdx.x * kSplatThreads;
+    if (first >= V->chunk_begin[na])
+        return;                                   // uniform over the CTA
+    for (int i = threadIdx.x; i < na * 12; i += kSplatThreads) {
+        const int a = i / 12;
+        s_M[a][i - a * 12] = V->geom[V->active[a]].M[i - a * 12];
+    }
+    for (int i = threadIdx.x; i < na; i += kSplatThreads) {
+        s_act[i] = V->active[i];
+        s_F[i] = frames[V->slot * V->n_cams + V->active[i]];
+    }
+    for (int i = threadIdx.x; i <= na; i += kSplatThreads)
+        s_cb[i] = V->chunk_begin[i];
+    __syncthreads();
+
+    const int chunk = first + threadIdx.x;
+    if (chunk >= s_cb[na])
         return;
     int a = 0;
-    while (chunk >= V->chunk_begin[a + 1])
+    while (chunk >= s_cb[a + 1])
         ++a;
-    const int k = V->active[a];
-    const FrameRef F = frames[V->slot * V->n_cams + k];
+    const int k = s_act[a];
+    const FrameRef F = s_F[a];
     const int cpr = (F.W + kSplatPix - 1) / kSplatPix;
-    const int local = chunk - V->chunk_begin[a];
+    const int local = chunk - s_cb[a];
     const int v = local / cpr;
     const int u0 = (local - v * cpr) * kSplatPix;
     const uint16_t* row = F.depth + size_t(v) * F.dpitch;
+    const uint64_t pol_stream = policy_evict_first();
+    const uint64_t pol_keys = policy_evict_last();
 
-    uint32_t d[kSplatPix];
+    uint32_t dw[kSplatPix / 2];                   // two depth codes per word
     if (u0 + kSplatPix <= F.W) {
-        const uint4 q = __ldg(reinterpret_cast<const uint4*>(row + u0));
-        d[0] = q.x & 0xFFFFu; d[1] = q.x >> 16;
-        d[2] = q.y & 0xFFFFu; d[3] = q.y >> 16;
-        d[4] = q.z & 0xFFFFu; d[5] = q.z >> 16;
-        d[6] = q.w & 0xFFFFu; d[7] = q.w >> 16;
+        const uint4 q0 = ld_stream_u4(row + u0, pol_stream);
+        const uint4 q1 = ld_stream_u4(row + u0 + 8, pol_stream);
+        dw[0] = q0.x; dw[1] = q0.y; dw[2] = q0.z; dw[3] = q0.w;
+        dw[4] = q1.x; dw[5] = q1.y; dw[6] = q1.z; dw[7] = q1.w;
     } else {
 #pragma unroll
-        for (int i = 0; i < kSplatPix; ++i)
-            d[i] = (u0 + i < F.W) ? uint32_t(__ldg(row + u0 + i)) : 0u;
+        for (int i = 0; i < kSplatPix / 2; ++i) {
+            const uint32_t lo = (u0 + 2 * i < F.W) ? uint32_t(row[u0 + 2 * i]) : 0u;
+            const uint32_t hi = (u0 + 2 * i + 1 < F.W) ? uint32_t(row[u0 + 2 * i + 1]) : 0u;
+            dw[i] = lo | (hi << 16);
+        }
     }
 
-    const float* m = V->geom[k].M;
-    const float m0 = m[0], m1 = m[1], m2 = m[2], m3 = m[3];
-    const float m4 = m[4], m5 = m[5], m6 = m[6], m7 = m[7];
-    const float m8 = m[8], m9 = m[9], m10 = m[10], m11 = m[11];
+    const float* m = s_M[a];
+    const float m0 = m[0], m2 = m[2], m3 = m[3];
+    const float m4 = m[4], m6 = m[6], m7 = m[7];
+    const float m8 = m[8], m10 = m[10], m11 = m[11];
     const float fv = float(v);
-    const float r0 = __fmul_rn(m1, fv), r1 = __fmul_rn(m5, fv), r2 = __fmul_rn(m9, fv);
+    const float r0 = __fmul_rn(m[1], fv), r1 = __fmul_rn(m[5], fv), r2 = __fmul_rn(m[9], fv);
     const float zmin = V->z_min;
     const uint32_t dlo = V->d_lo, dhi = V->d_hi;
     const int Wv = V->Wv;
@@ -121,33 +193,47 @@ k_warp_splat(const ViewDesc* __restrict__ views, const FrameRef* __restrict__ fr
     const uint32_t src0 = uint32_t(v) * uint32_t(F.W) + uint32_t(u0);
 
 #pragma unroll
-    for (int i = 0; i < kSplatPix; ++i) {
-        const uint32_t dd = d[i];
-        if (dd == 0u || dd < dlo || dd > dhi)
-            continue;
-        const float fu = float(u0 + i);
-        const float z = float(dd);
-        const float a0 = __fadd_rn(__fadd_rn(__fmul_rn(m0, fu), r0), m2);
-        const float a1 = __fadd_rn(__fadd_rn(__fmul_rn(m4, fu), r1), m6);
-        const float a2 = __fadd_rn(__fadd_rn(__fmul_rn(m8, fu), r2), m10);
-        const float X = __fadd_rn(__fmul_rn(a0, z), m3);
-        const float Y = __fadd_rn(__fmul_rn(a1, z), m7);
-        const float Z = __fadd_rn(__fmul_rn(a2, z), m11);
-        if (!(Z > zmin))
-            continue;
-        const float up = __fdiv_rn(X, Z);
-        const float vp = __fdiv_rn(Y, Z);
-        if (!isfinite(up) || !isfinite(vp))
-            continue;
-        const float tu = floorf(__fadd_rn(up, 0.5f));
-        const float tv = floorf(__fadd_rn(vp, 0.5f));
-        if (!(tu >= 0.0f && tu <= maxu && tv >= 0.0f && tv <= maxv))
-            continue;
-        const size_t p = size_t(int(tv)) * size_t(Wv) + size_t(int(tu));
-        const unsigned long long key =
-            (static_cast<unsigned long long>(__float_as_uint(Z)) << 32) | khi |
-            static_cast<unsigned long long>(src0 + uint32_t(i));
-        atomicMin(keys + p, key);
+    for (int h = 0; h < kSplatPix; h += 8) {
+        unsigned long long key[8];
+        uint32_t pix[8];
+        bool ok[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int ii = h + i;
+            const uint32_t dd = (dw[ii >> 1] >> (16 * (ii & 1))) & 0xFFFFu;
+            ok[i] = false;
+            key[i] = kKeyEmpty;
+            pix[i] = 0;
+            if (dd == 0u || dd < dlo || dd > dhi)
+                continue;
+            const float fu = float(u0 + ii);
+            const float z = float(dd);
+            const float a0 = __fadd_rn(__fadd_rn(__fmul_rn(m0, fu), r0), m2);
+            const float a1 = __fadd_rn(__fadd_rn(__fmul_rn(m4, fu), r1), m6);
+            const float a2 = __fadd_rn(__fadd_rn(__fmul_rn(m8, fu), r2), m10);
+            const float X = __fadd_rn(__fmul_rn(a0, z), m3);
+            const float Y = __fadd_rn(__fmul_rn(a1, z), m7);
+            const float Z = __fadd_rn(__fmul_rn(a2, z), m11);
+            if (!(Z > zmin))
+                continue;
+            const float tu = floorf(__fadd_rn(__fdiv_rn(X, Z), 0.5f));
+            const float tv = floorf(__fadd_rn(__fdiv_rn(Y, Z), 0.5f));
+            // also rejects NaN and +-inf, as a finiteness test would
+            if (!(tu >= 0.0f && tu <= maxu && tv >= 0.0f && tv <= maxv))
+                continue;
+            ok[i] = true;
+            pix[i] = uint32_t(int(tv)) * uint32_t(Wv) + uint32_t(int(tu));
+            key[i] = (static_cast<unsigned long long>(__float_as_uint(Z)) << 32) | khi |
+                     static_cast<unsigned long long>(src0 + uint32_t(ii));
+        }
+        unsigned long long cur[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+            cur[i] = ok[i] ? ld_key(keys + pix[i], pol_keys) : 0ull;
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+            if (ok[i] && key[i] < cur[i])
+                red_min_key(keys + pix[i], key[i], pol_keys);
     }
 }
 
@@ -241,7 +327,7 @@ __device__ __forceinline__ int block_excl_suffix_min(int v, int* s_scan)
 // ---------------------------------------------------------------------------
 // (c) + (d) + (e), one CTA per output row of one view.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kResolveThreads)
+__global__ void __launch_bounds__(kResolveThreads, 3)
 k_resolve(const ViewDesc* __restrict__ views, const FrameRef* __restrict__ frames)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -263,10 +349,18 @@ k_resolve(const ViewDesc* __restrict__ views, const FrameRef* __restrict__ frame
     const int tid = threadIdx.x;
     constexpr int NT = kResolveThreads;
 
-    // stage the backward maps, weights, frame table and active list
-    for (int i = tid; i < nc * 13; i += NT) {
-        const int k = i / 13, j = i - k * 13;
-        s_geom[k * 16 + j] = j < 12 ? V->geom[k].N[j] : V->geom[k].w;
+    // stage the backward maps, weights, frame table and active list.  Per
+    // camera, 16 floats: N[0..11], then w and the row terms N1 y, N5 y, N9 y
+    // (the products the per-pixel projection would form; same rounding).
+    const float fy = float(y);
+    for (int i = tid; i < nc * 16; i += NT) {
+        const int k = i >> 4, j = i & 15;
+        const float* Nk = V->geom[k].N;
+        float val;
+        if (j < 12) val = Nk[j];
+        else if (j == 12) val = V->geom[k].w;
+        else val = __fmul_rn(Nk[1 + 4 * (j - 13)], fy);
+        s_geom[i] = val;
     }
     for (int i = tid; i < nc; i += NT)
         s_fr[i] = frames[V->slot * nc + i];
@@ -293,7 +387,7 @@ k_resolve(const ViewDesc* __restrict__ views, const FrameRef* __restrict__ frame
     float* __restrict__ top3 = V->out_top3;
     unsigned long long* __restrict__ okeys = V->out_keys;
     const size_t rowbase = size_t(y) * Wv;
-    const float fy = float(y);
+    const float4* g4 = reinterpret_cast<const float4*>(s_geom);
 
     for (int x = tid; x < Wv; x += NT) {
         const unsigned long long kp = s_keys[Wv + x];
@@ -325,47 +419,73 @@ k_resolve(const ViewDesc* __restrict__ views, const FrameRef* __restrict__ frame
         float t0 = ww, t1 = -1.0f, t2 = -1.0f;
         int k0 = w, k1 = INT_MAX, k2 = INT_MAX;
         const float fx = float(x);
-        for (int ai = 0; ai < na; ++ai) {
-            const int k = s_act[ai];
-            if (k == w)
-                continue;
-            const float* g = s_geom + k * 16;
-            const float a0 = __fadd_rn(__fadd_rn(__fmul_rn(g[0], fx), __fmul_rn(g[1], fy)), g[2]);
-            const float a1 = __fadd_rn(__fadd_rn(__fmul_rn(g[4], fx), __fmul_rn(g[5], fy)), g[6]);
-            const float a2 = __fadd_rn(__fadd_rn(__fmul_rn(g[8], fx), __fmul_rn(g[9], fy)), g[10]);
-            const float Xk = __fadd_rn(__fmul_rn(a0, Z), g[3]);
-            const float Yk = __fadd_rn(__fmul_rn(a1, Z), g[7]);
-            const float Zk = __fadd_rn(__fmul_rn(a2, Z), g[11]);
-            if (!(Zk > zmin))
-                continue;
-            const float up = __fdiv_rn(Xk, Zk);
-            const float vp = __fdiv_rn(Yk, Zk);
-            if (!isfinite(up) || !isfinite(vp))
-                continue;
-            const float tu = floorf(__fadd_rn(up, 0.5f));
-            const float tv = floorf(__fadd_rn(vp, 0.5f));
-            const FrameRef& Fk = s_fr[k];
-            if (!(tu >= 0.0f && tu <= float(Fk.W - 1) && tv >= 0.0f && tv <= float(Fk.H - 1)))
-                continue;
-            const int uk = int(tu), vk = int(tv);
-            const uint32_t dk = __ldg(Fk.depth + size_t(vk) * Fk.dpitch + uk);
-            const uint32_t ck = __ldg(Fk.rgba + size_t(vk) * Fk.rpitch + uk);
-            if (dk == 0u || dk < dlo || dk > dhi)
-                continue;
-            const float diff = fabsf(__fsub_rn(float(dk), Zk));
-            if (!(diff <= __fmul_rn(tau_vis, Zk)))
-                continue;
-            const float wk = g[12];
-            acc0 = __fadd_rn(acc0, __fmul_rn(wk, float(ck & 255u)));
-            acc1 = __fadd_rn(acc1, __fmul_rn(wk, float((ck >> 8) & 255u)));
-            acc2 = __fadd_rn(acc2, __fmul_rn(wk, float((ck >> 16) & 255u)));
-            wsum = __fadd_rn(wsum, wk);
-            if (w_before(wk, k, t0, k0)) {
-                t2 = t1; k2 = k1; t1 = t0; k1 = k0; t0 = wk; k0 = k;
-            } else if (w_before(wk, k, t1, k1)) {
-                t2 = t1; k2 = k1; t1 = wk; k1 = k;
-            } else if (w_before(wk, k, t2, k2)) {
-                t2 = wk; k2 = k;
+        // cameras in groups of four: project all four and issue their depth
+        // and colour gathers before any is consumed, then accumulate in
+        // ascending camera order
+        for (int g0 = 0; g0 < na; g0 += 4) {
+            uint32_t dk[4], ck[4];
+            float zk[4];
+            int kk[4];
+            bool ok[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                ok[j] = false;
+                dk[j] = 0u;
+                ck[j] = 0u;
+                zk[j] = 0.0f;
+                kk[j] = 0;
+                const int ai = g0 + j;
+                if (ai >= na)
+                    continue;
+                const int k = s_act[ai];
+                kk[j] = k;
+                if (k == w)
+                    continue;
+                const float4 A = g4[4 * k + 0], Bq = g4[4 * k + 1], Cq = g4[4 * k + 2],
+                             Dq = g4[4 * k + 3];
+                const float a0 = __fadd_rn(__fadd_rn(__fmul_rn(A.x, fx), Dq.y), A.z);
+                const float a1 = __fadd_rn(__fadd_rn(__fmul_rn(Bq.x, fx), Dq.z), Bq.z);
+                const float a2 = __fadd_rn(__fadd_rn(__fmul_rn(Cq.x, fx), Dq.w), Cq.z);
+                const float Xk = __fadd_rn(__fmul_rn(a0, Z), A.w);
+                const float Yk = __fadd_rn(__fmul_rn(a1, Z), Bq.w);
+                const float Zk = __fadd_rn(__fmul_rn(a2, Z), Cq.w);
+                if (!(Zk > zmin))
+                    continue;
+                const float tu = floorf(__fadd_rn(__fdiv_rn(Xk, Zk), 0.5f));
+                const float tv = floorf(__fadd_rn(__fdiv_rn(Yk, Zk), 0.5f));
+                const FrameRef& Fk = s_fr[k];
+                // also rejects NaN and +-inf, as a finiteness test would
+                if (!(tu >= 0.0f && tu <= float(Fk.W - 1) && tv >= 0.0f && tv <= float(Fk.H - 1)))
+                    continue;
+                const int uk = int(tu), vk = int(tv);
+                ok[j] = true;
+                zk[j] = Zk;
+                dk[j] = __ldg(Fk.depth + size_t(vk) * Fk.dpitch + uk);
+                ck[j] = __ldg(Fk.rgba + size_t(vk) * Fk.rpitch + uk);
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                if (!ok[j])
+                    continue;
+                if (dk[j] == 0u || dk[j] < dlo || dk[j] > dhi)
+                    continue;
+                const float diff = fabsf(__fsub_rn(float(dk[j]), zk[j]));
+                if (!(diff <= __fmul_rn(tau_vis, zk[j])))
+                    continue;
+                const int k = kk[j];
+                const float wk = s_geom[16 * k + 12];
+                const uint32_t c = ck[j];
+                acc0 = __fadd_rn(acc0, __fmul_rn(wk, float(c & 255u)));
+                acc1 = __fadd_rn(acc1, __fmul_rn(wk, float((c >> 8) & 255u)));
+                acc2 = __fadd_rn(acc2, __fmul_rn(wk, float((c >> 16) & 255u)));
+                wsum = __fadd_rn(wsum, wk);
+                if (w_before(wk, k, t0, k0)) {
+                    t2 = t1; k2 = k1; t1 = t0; k1 = k0; t0 = wk; k0 = k;
+                } else if (w_before(wk, k, t1, k1)) {
+                    t2 = t1; k2 = k1; t1 = wk; k1 = k;
+                } else if (w_before(wk, k, t2, k2)) {
+                    t2 = wk; k2 = k;
+                }
             }
         }
         s_rgb[x] = blend_channel(acc0, wsum) | (blend_channel(acc1, wsum) << 8) |

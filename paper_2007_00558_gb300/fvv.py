@@ -66,6 +66,11 @@ class fvv_aux(C.Structure):
                 ("keys", C.c_void_p), ("keys_raw", C.c_void_p)]
 
 
+class fvv_kernel_stats(C.Structure):
+    _fields_ = [("name", C.c_char * 32), ("launches", C.c_uint64), ("timed", C.c_uint64),
+                ("total_ms", C.c_double)]
+
+
 _lib = None
 _lock = threading.Lock()
 
@@ -99,6 +104,8 @@ def load() -> C.CDLL:
                                      C.POINTER(S), C.POINTER(fvv_aux), P],
             "fvv_view_params": [C.POINTER(fvv_rig), C.POINTER(fvv_options), C.POINTER(fvv_camera),
                                 P, P, P],
+            "fvv_profile_enable": [P, I],
+            "fvv_profile_read": [P, C.POINTER(fvv_kernel_stats), C.POINTER(I), I],
         }
         for name, args in sig.items():
             f = getattr(lib, name)
@@ -249,3 +256,16 @@ def fvv_view_params(rig_: fvv_rig, opt: Optional[fvv_options], view):
                                   C.byref(v), M.ctypes.data, N.ctypes.data, w.ctypes.data),
            "fvv_view_params")
     return M, N, w
+
+
+def fvv_profile_enable(ctx: int, on: bool = True) -> None:
+    _check(load().fvv_profile_enable(ctx, 1 if on else 0), "fvv_profile_enable")
+
+
+def fvv_profile_read(ctx: int, reset: bool = False) -> dict:
+    """{kernel name: (launches, timed launches, total ms)}."""
+    n = C.c_int32(8)
+    arr = (fvv_kernel_stats * 8)()
+    _check(load().fvv_profile_read(ctx, arr, C.byref(n), 1 if reset else 0), "fvv_profile_read")
+    return {arr[i].name.decode(): (arr[i].launches, arr[i].timed, arr[i].total_ms)
+            for i in range(min(n.value, 8))}
