@@ -747,7 +747,7 @@ fvv_status fvv_synthesize_batch(fvv_ctx* c, int32_t n, const fvv_view* views, co
         for (int k = 0; k < c->n_cams; ++k)
             if (g[k].w > 0.0f) {
                 D.active[na] = k;
-                chunks += c->cams[k].height * ((c->cams[k].width + fvv::kSplatPix - 1) / fvv::kSplatPix);
+                chunks += c->cams[k].height * ((c->cams[k].width + fvv::kSplatSeg - 1) / fvv::kSplatSeg);
                 D.chunk_begin[++na] = chunks;
             }
         D.n_active = na;
@@ -790,6 +790,8 @@ fvv_status fvv_synthesize_batch(fvv_ctx* c, int32_t n, const fvv_view* views, co
         }
     }
     if (!d2h.empty()) any_host = true;
+    bool want_top3 = false;
+    for (int i = 0; aux && i < n; ++i) want_top3 = want_top3 || aux[i].top3 != nullptr;
     const size_t pbytes = geom_off + size_t(n) * c->n_cams * sizeof(CamGeom);
     FVV_CUDA(cudaMemcpyAsync(P.dev, P.host, pbytes, cudaMemcpyHostToDevice, s));
     const ViewDesc* vdev = reinterpret_cast<const ViewDesc*>(P.dev);
@@ -810,7 +812,7 @@ fvv_status fvv_synthesize_batch(fvv_ctx* c, int32_t n, const fvv_view* views, co
         FVV_CUDA(cudaMemcpyAsync(raw_copies[r].first, raw_copies[r].second, raw_bytes[r],
                                  cudaMemcpyDefault, s));
     FVV_TRY(run_kernel(c, kResolve, s, [&] {
-        return fvv::launch_resolve(vdev, n, max_h, max_w, c->n_cams, c->frames_dev, s);
+        return fvv::launch_resolve(vdev, n, max_h, max_w, c->n_cams, want_top3, c->frames_dev, s);
     }));
     for (const HostCopy& h : d2h)
         FVV_CUDA(cudaMemcpy2DAsync(h.dst, h.dpitch, h.src, h.spitch, h.width, h.height,

@@ -11,9 +11,10 @@ namespace fvv {
 constexpr int kMaxCams = 64;
 constexpr int kSrcBits = 26;
 constexpr unsigned long long kKeyEmpty = ~0ull;
-constexpr int kSplatPix = 16;        // source pixels per splat thread (two 16-B loads)
+constexpr int kSplatSeg = 256;       // source pixels per splat warp (8 per lane, stride 32)
 constexpr int kSplatThreads = 256;
 constexpr int kResolveThreads = 256;
+constexpr int kResolveBand = 4;      // output rows per resolve CTA
 
 constexpr int kFlagCrack = 1;
 constexpr int kFlagFill = 2;
@@ -56,7 +57,7 @@ struct alignas(16) ViewDesc {
     unsigned long long* out_keys;    // nullable [Hv * Wv], after the crack filter
     const CamGeom* geom;             // [n_cams]
     int32_t active[kMaxCams];        // cameras with w > 0, ascending
-    int32_t chunk_begin[kMaxCams + 1];  // prefix of splat chunks over `active`
+    int32_t chunk_begin[kMaxCams + 1];  // prefix of splat warp segments over `active`
 };
 
 // Launchers (fvv_kernels.cu).  All asynchronous on `stream`.
@@ -64,7 +65,7 @@ cudaError_t launch_clear_keys(unsigned long long* keys, size_t n, cudaStream_t s
 cudaError_t launch_warp_splat(const ViewDesc* views, int n_views, int max_chunks,
                               const FrameRef* frames, cudaStream_t stream);
 cudaError_t launch_resolve(const ViewDesc* views, int n_views, int max_h, int max_w, int n_cams,
-                           const FrameRef* frames, cudaStream_t stream);
+                           bool top3, const FrameRef* frames, cudaStream_t stream);
 cudaError_t launch_pack_rgba(const uint8_t* rgb, size_t rgb_pitch, uint32_t* rgba,
                              int rpitch, int W, int H, cudaStream_t stream);
 size_t resolve_smem_bytes(int max_w, int n_cams);
