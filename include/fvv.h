@@ -185,6 +185,46 @@ fvv_status fvv_profile_enable(fvv_ctx* ctx, int32_t on);
  * waits for the recorded events.  reset = 1 clears the statistics. */
 fvv_status fvv_profile_read(fvv_ctx* ctx, fvv_kernel_stats* out, int32_t* n, int32_t reset);
 
+/* ---- allocation-free variant ------------------------------------------- */
+
+/* Largest view (width * height) fvv_synthesize_noalloc accepts. */
+#define FVV_NOALLOC_MAX_PIXELS (1u << 21)
+
+/* Synthesise one view (steps a-e, the same kernels and results as
+ * fvv_synthesize) without allocating any memory.  The paper has no
+ * counterpart: this call exists for callers that must not call cudaMalloc --
+ * a process whose device memory is owned by another allocator (a framework's
+ * caching allocator that has reserved the GPU), or a latency-critical render
+ * thread on which cudaMalloc / cudaFree would synchronise the device and
+ * stall other streams.  It needs no context: the caller passes the frames
+ * and the output, all in device memory.
+ *   rig, opt:       as for fvv_create (opt NULL = defaults; frame_slots,
+ *                   max_batch and memory_budget are ignored)
+ *   depth[k]:       camera k's depth codes, uint16 rows of pitch depth_pitch[k]
+ *                   bytes (even), 0 = no depth
+ *   rgba[k]:        camera k's colour, one uint32 per pixel R | G << 8 | B << 16,
+ *                   rows of pitch rgba_pitch[k] bytes (multiple of 4)
+ *   view:           the virtual camera, width * height <= FVV_NOALLOC_MAX_PIXELS
+ *   out_rgb:        height rows of 3 * width bytes, row pitch out_pitch
+ *   stream:         cudaStream_t as void* (NULL = the legacy default stream);
+ *                   the call is asynchronous on it
+ * Scratch: file-scope device arrays (FVV_NOALLOC_MAX_PIXELS 64-bit z-buffer
+ * keys = 16 MiB, plus about 10 KiB of launch parameters), which every GPU that
+ * loads the library holds until the process exits.  Larger views are rejected
+ * with FVV_ERR_INVALID_ARG.  The first call on a device looks up the device
+ * address of that scratch (cudaGetSymbolAddress) with the device current;
+ * make that first call before any stream capture.  Every call shares the
+ * scratch and it keeps the last call's contents (the keys are reset at the
+ * start of each call): calls whose GPU work overlaps, e.g. on two unordered
+ * streams, race -- order them on one stream.  On success nothing is
+ * allocated, on the host or the device.
+ * Errors: INVALID_ARG (NULL, non-device pointer, size, pitch, options), CUDA. */
+fvv_status fvv_synthesize_noalloc(const fvv_rig* rig, const fvv_options* opt,
+                                  const uint16_t* const* depth, const size_t* depth_pitch,
+                                  const uint32_t* const* rgba, const size_t* rgba_pitch,
+                                  const fvv_view* view, uint8_t* out_rgb, size_t out_pitch,
+                                  void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -235,6 +235,19 @@ struct SlotState {
 
 }  // namespace
 
+namespace fvv {
+// Message for fvv_last_error() from code outside this file (failure paths).
+void set_last_error(const char* msg) { g_err = msg; }
+
+// Host-side composition of one view's per-camera maps and weights (the same
+// routine the batched path uses); writes into caller storage only.
+void compose_view_into(int n_cams, const fvv_camera* cams, const double look_at[3],
+                       double depth_unit_m, int n_ref, const fvv_camera& view, CamGeom* g)
+{
+    compose_view(n_cams, cams, look_at, depth_unit_m, n_ref, view, g);
+}
+}  // namespace fvv
+
 struct fvv_ctx {
     int device = 0;
     int n_cams = 0;

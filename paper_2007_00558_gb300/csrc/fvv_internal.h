@@ -71,3 +71,12 @@ cudaError_t launch_pack_rgba(const uint8_t* rgb, size_t rgb_pitch, uint32_t* rgb
 size_t resolve_smem_bytes(int max_w, int n_cams);
 
 }  // namespace fvv
+
+struct fvv_camera;
+namespace fvv {
+// fvv_api.cu: message returned by fvv_last_error() on this thread.
+void set_last_error(const char* msg);
+// fvv_api.cu: FP64 composition of one view (maps M, N and weights w per camera).
+void compose_view_into(int n_cams, const fvv_camera* cams, const double look_at[3],
+                       double depth_unit_m, int n_ref, const fvv_camera& view, CamGeom* g);
+}  // namespace fvv

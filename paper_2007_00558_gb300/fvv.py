@@ -30,6 +30,7 @@ FVV_ERR_STATE = 8
 FVV_MAX_CAMS = 64
 FVV_MAX_SRC_PIXELS = 1 << 26
 FVV_KEY_EMPTY = 0xFFFFFFFFFFFFFFFF
+FVV_NOALLOC_MAX_PIXELS = 1 << 21
 
 _NAMES = {v: k for k, v in list(globals().items()) if k.startswith("FVV_ERR_") or k == "FVV_OK"}
 
@@ -104,6 +105,9 @@ def load() -> C.CDLL:
                                      C.POINTER(S), C.POINTER(fvv_aux), P],
             "fvv_view_params": [C.POINTER(fvv_rig), C.POINTER(fvv_options), C.POINTER(fvv_camera),
                                 P, P, P],
+            "fvv_synthesize_noalloc": [C.POINTER(fvv_rig), C.POINTER(fvv_options), C.POINTER(P),
+                                       C.POINTER(S), C.POINTER(P), C.POINTER(S),
+                                       C.POINTER(fvv_camera), P, S, P],
             "fvv_profile_enable": [P, I],
             "fvv_profile_read": [P, C.POINTER(fvv_kernel_stats), C.POINTER(I), I],
         }
@@ -269,3 +273,18 @@ def fvv_profile_read(ctx: int, reset: bool = False) -> dict:
     _check(load().fvv_profile_read(ctx, arr, C.byref(n), 1 if reset else 0), "fvv_profile_read")
     return {arr[i].name.decode(): (arr[i].launches, arr[i].timed, arr[i].total_ms)
             for i in range(min(n.value, 8))}
+
+
+def fvv_synthesize_noalloc(rig_: fvv_rig, opt: Optional[fvv_options], depth: Sequence,
+                           depth_pitch: Sequence[int], rgba: Sequence, rgba_pitch: Sequence[int],
+                           view, out_rgb, out_pitch: int, stream=None) -> None:
+    """Allocation-free synthesis of one view from device frames (RGBA8 + uint16)."""
+    n = rig_.n_cams
+    dp = (C.c_void_p * n)(*[ptr(d) for d in depth])
+    ds = (C.c_size_t * n)(*depth_pitch)
+    rp = (C.c_void_p * n)(*[ptr(r) for r in rgba])
+    rs = (C.c_size_t * n)(*rgba_pitch)
+    v = view if isinstance(view, fvv_camera) else camera(view)
+    _check(load().fvv_synthesize_noalloc(C.byref(rig_), C.byref(opt) if opt is not None else None,
+                                         dp, ds, rp, rs, C.byref(v), ptr(out_rgb), out_pitch,
+                                         stream_handle(stream)), "fvv_synthesize_noalloc")
