@@ -197,11 +197,11 @@ k_warp_splat(const ViewDesc* __restrict__ views, const FrameRef* __restrict__ fr
         const uint32_t src0 = uint32_t(v) * uint32_t(F.W) + uint32_t(u0 + lane);
         const float fu0 = u23_to_float(uint32_t(u0 + lane));
 
+        // branch-free per point (only the atomic is predicated), so the eight
+        // independent projections and divisions of a lane can interleave
 #pragma unroll
         for (int j = 0; j < kSplatSeg / 32; ++j) {
             const uint32_t dd = d[j];
-            if (dd == 0u || dd < dlo || dd > dhi)
-                continue;
             const float fu = __fadd_rn(fu0, float(32 * j));  // exact: small integers
             const float z = u23_to_float(dd);
             const float a0 = __fadd_rn(__fadd_rn(__fmul_rn(m0, fu), r0), m2);
@@ -210,18 +210,18 @@ k_warp_splat(const ViewDesc* __restrict__ views, const FrameRef* __restrict__ fr
             const float X = __fadd_rn(__fmul_rn(a0, z), m3);
             const float Y = __fadd_rn(__fmul_rn(a1, z), m7);
             const float Z = __fadd_rn(__fmul_rn(a2, z), m11);
-            if (!(Z > zmin))
-                continue;
             const float tu = floorf(__fadd_rn(__fdiv_rn(X, Z), 0.5f));
             const float tv = floorf(__fadd_rn(__fdiv_rn(Y, Z), 0.5f));
-            // also rejects NaN and +-inf, as a finiteness test would
-            if (!(tu >= 0.0f && tu <= maxu && tv >= 0.0f && tv <= maxv))
-                continue;
-            const uint32_t pix = float_to_u23(tv) * Wv + float_to_u23(tu);
-            const unsigned long long key =
-                (static_cast<unsigned long long>(__float_as_uint(Z)) << 32) | khi |
-                static_cast<unsigned long long>(src0 + uint32_t(32 * j));
-            red_min_key(keys + pix, key, pol_keys);
+            // the bounds test also rejects NaN and +-inf, as a finiteness test would
+            const bool ok = dd != 0u && dd >= dlo && dd <= dhi && Z > zmin && tu >= 0.0f &&
+                            tu <= maxu && tv >= 0.0f && tv <= maxv;
+            if (ok) {
+                const uint32_t pix = float_to_u23(tv) * Wv + float_to_u23(tu);
+                const unsigned long long key =
+                    (static_cast<unsigned long long>(__float_as_uint(Z)) << 32) | khi |
+                    static_cast<unsigned long long>(src0 + uint32_t(32 * j));
+                red_min_key(keys + pix, key, pol_keys);
+            }
         }
     }
 }
@@ -462,20 +462,13 @@ k_resolve(const ViewDesc* __restrict__ views, const FrameRef* __restrict__ frame
                 float zk[4];
                 int kk[4];
                 bool ok[4];
+                // branch-free projection of the group (only the gathers are
+                // predicated), so the four chains can interleave
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
-                    ok[j] = false;
-                    dk[j] = 0u;
-                    ck[j] = 0u;
-                    zk[j] = 0.0f;
-                    kk[j] = 0;
-                    const int ai = g0 + j;
-                    if (ai >= na)
-                        continue;
+                    const int ai = min(g0 + j, na - 1);
                     const int k = s_act[ai];
                     kk[j] = k;
-                    if (k == w)
-                        continue;
                     const float4 A = g4[5 * k + 0], Bq = g4[5 * k + 1], Cq = g4[5 * k + 2],
                                  Eq = g4[5 * k + 4];
                     const float4 Rt = reinterpret_cast<const float4*>(s_rowt)[k];
@@ -485,19 +478,20 @@ k_resolve(const ViewDesc* __restrict__ views, const FrameRef* __restrict__ frame
                     const float Xk = __fadd_rn(__fmul_rn(a0, Z), A.w);
                     const float Yk = __fadd_rn(__fmul_rn(a1, Z), Bq.w);
                     const float Zk = __fadd_rn(__fmul_rn(a2, Z), Cq.w);
-                    if (!(Zk > zmin))
-                        continue;
                     const float tu = floorf(__fadd_rn(__fdiv_rn(Xk, Zk), 0.5f));
                     const float tv = floorf(__fadd_rn(__fdiv_rn(Yk, Zk), 0.5f));
-                    // also rejects NaN and +-inf, as a finiteness test would
-                    if (!(tu >= 0.0f && tu <= Eq.x && tv >= 0.0f && tv <= Eq.y))
-                        continue;
-                    const FrameRef& Fk = s_fr[k];
-                    const uint32_t uk = float_to_u23(tu), vk = float_to_u23(tv);
-                    ok[j] = true;
+                    // the bounds test also rejects NaN and +-inf, as a finiteness test would
+                    ok[j] = g0 + j < na && k != w && Zk > zmin && tu >= 0.0f && tu <= Eq.x &&
+                            tv >= 0.0f && tv <= Eq.y;
                     zk[j] = Zk;
-                    dk[j] = __ldg(Fk.depth + vk * uint32_t(Fk.dpitch) + uk);
-                    ck[j] = __ldg(Fk.rgba + vk * uint32_t(Fk.rpitch) + uk);
+                    dk[j] = 0u;
+                    ck[j] = 0u;
+                    if (ok[j]) {
+                        const FrameRef& Fk = s_fr[k];
+                        const uint32_t uk = float_to_u23(tu), vk = float_to_u23(tv);
+                        dk[j] = __ldg(Fk.depth + vk * uint32_t(Fk.dpitch) + uk);
+                        ck[j] = __ldg(Fk.rgba + vk * uint32_t(Fk.rpitch) + uk);
+                    }
                 }
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
