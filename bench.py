@@ -57,6 +57,9 @@ def parse_args():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-profile", action="store_true",
                    help="do not bracket kernels with events in the timed region")
+    p.add_argument("--no-serve", action="store_true", help="skip the serving-loop measurement")
+    p.add_argument("--serve-seconds", type=float, default=3.0,
+                   help="length of the Poisson multi-viewer run")
     return p.parse_args()
 
 
@@ -244,6 +247,112 @@ def algorithmic_bytes(K, Ns, Nd, rho, n_ref):
 
 
 # ---------------------------------------------------------------------------
+# serving loop: many viewers, Poisson arrivals, mixed resolutions
+# ---------------------------------------------------------------------------
+SERVE_RES = [(640, 360, 500.0)] * 2 + [(1280, 720, 1000.0), (1920, 1080, 1500.0)]   # 2:1:1
+
+
+def serve_bench(F, ctx, wl, rgb_h, dep_h, slots, seconds, stream):
+    """16 viewers, Poisson 30 Hz each, resolutions 640x360 : 1280x720 :
+    1920x1080 = 2:1:1 (viewer i takes SERVE_RES[i % 4]), frames re-uploaded
+    at 30 fps on a second stream; then a saturation run of back-to-back
+    submissions.  Latency: submission -> output written (library clock)."""
+    import numpy as np
+    import torch
+    import synthetic as S
+    H, W = wl["cams"][0].height, wl["cams"][0].width
+    n_viewers, rate = 16, 30.0
+    rng = np.random.default_rng(7)
+    arrivals = []
+    for v in range(n_viewers):
+        t = rng.exponential(1.0 / rate)
+        while t < seconds:
+            arrivals.append((t, v))
+            t += rng.exponential(1.0 / rate)
+    arrivals.sort()
+    views = {}
+    for v in range(n_viewers):
+        Wv, Hv, f = SERVE_RES[v % 4]
+        views[v] = [S.arc_view(22.5 * math.sin(2 * math.pi * (i + 19 * v) / 300.0), 1.5, Wv, Hv, f)
+                    for i in range(300)]
+    depth_per_viewer = 8
+    bufs = {v: [torch.empty((SERVE_RES[v % 4][1], SERVE_RES[v % 4][0] * 3), dtype=torch.uint8,
+                            device="cuda") for _ in range(depth_per_viewer)] for v in range(n_viewers)}
+    owner = {}
+    F.fvv_serve_start(ctx, F.fvv_serve_default_cfg(lanes=3, max_batch=16, memory_budget=1 << 30))
+    stop = threading.Event()
+    up_stream = torch.cuda.Stream()
+    tick0 = [10 ** 6]
+
+    def uploader():
+        period = 1.0 / 30.0
+        nxt = time.perf_counter()
+        while not stop.is_set():
+            F.fvv_upload_frames(ctx, rgb_h, H * W * 3, W * 3, dep_h, H * W * 2, W * 2, tick0[0],
+                                up_stream)
+            tick0[0] += 1
+            nxt += period
+            time.sleep(max(0.0, nxt - time.perf_counter()))
+
+    def submit(v, k, i):
+        buf = bufs[v][k % depth_per_viewer]
+        prev = owner.get(id(buf))
+        if prev is not None:
+            F.fvv_serve_poll(ctx, prev, 10_000_000)
+        view = views[v][i % 300]
+        t = F.fvv_serve_submit(ctx, v, view, buf, view.width * 3)
+        owner[id(buf)] = t
+        return t
+
+    th = threading.Thread(target=uploader, daemon=True)
+    th.start()
+    try:
+        F.fvv_serve_stats(ctx, reset=True)
+        t0 = time.perf_counter()
+        count = {v: 0 for v in range(n_viewers)}
+        for at, v in arrivals:
+            dt = t0 + at - time.perf_counter()
+            if dt > 0:
+                time.sleep(dt)
+            submit(v, count[v], count[v] + int(at * 30))
+            count[v] += 1
+        for t in list(owner.values()):
+            F.fvv_serve_poll(ctx, t, 10_000_000)
+        owner.clear()
+        nominal = F.fvv_serve_stats(ctx, reset=True)
+        # saturation: submit as fast as the pending limit allows
+        n_sat = 3000
+        t0 = time.perf_counter()
+        tickets = []
+        for j in range(n_sat):
+            v = j % n_viewers
+            tickets.append(submit(v, j // n_viewers, j))
+        for t in tickets[-n_viewers * depth_per_viewer:]:
+            try:
+                F.fvv_serve_poll(ctx, t, 10_000_000)
+            except F.FvvError:
+                pass
+        sat_wall = time.perf_counter() - t0
+        sat = F.fvv_serve_stats(ctx, reset=True)
+    finally:
+        stop.set()
+        th.join()
+        F.fvv_serve_stop(ctx)
+    mean_px = sum(r[0] * r[1] for r in SERVE_RES) / len(SERVE_RES)
+    return {
+        "viewers": n_viewers, "rate_hz_per_viewer": rate, "resolutions": "640x360:1280x720:1920x1080=2:1:1",
+        "frame_updates_hz": 30, "lanes": 3, "max_batch": 16, "seconds": seconds,
+        "offered_rps": len(arrivals) / seconds, "completed": nominal["completed"],
+        "p50_ms": nominal["p50_ms"], "p99_ms": nominal["p99_ms"], "max_ms": nominal["max_ms"],
+        "views_per_s": nominal["views_per_s"], "mean_batch": nominal["mean_batch"],
+        "saturated": {"requests": n_sat, "views_per_s": sat["views_per_s"],
+                      "views_720p_equiv_per_s": sat["views_per_s"] * mean_px / (1280 * 720),
+                      "p50_ms": sat["p50_ms"], "p99_ms": sat["p99_ms"], "mean_batch": sat["mean_batch"],
+                      "wall_s": sat_wall},
+    }
+
+
+# ---------------------------------------------------------------------------
 # arms
 # ---------------------------------------------------------------------------
 def dist_env():
@@ -411,6 +520,10 @@ def run_fvv(args):
                "h2d_bytes_per_step": int(Bsz * (rgb_h.numel() + dep_h.numel() * 2)),
                "d2h_bytes_per_step": int(Bsz * H * W * 3)}
 
+    serve = None
+    if not args.no_serve and world == 1:
+        serve = serve_bench(F, ctx, wl, rgb_h, dep_h, slots, args.serve_seconds, stream)
+
     F.fvv_destroy(ctx)
 
     cpu = None
@@ -435,7 +548,7 @@ def run_fvv(args):
                        "l2": "inputs > L2: each view reads its own frame tick, %d ticks x %.1f MB "
                              "resident" % (slots, K * H * W * 6 / 1e6),
                        "parallelism": "replicas" if world > 1 else "single"},
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "serve": serve,
             "gpu_launches": int(launches), "clocks": clocks.summary(),
             "kernel_ms": {k: v[2] for k, v in stats.items()},
         }

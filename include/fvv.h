@@ -166,6 +166,62 @@ fvv_status fvv_synthesize_batch(fvv_ctx* ctx, int32_t n, const fvv_view* views,
 fvv_status fvv_view_params(const fvv_rig* rig, const fvv_options* opt,
                            const fvv_view* view, float* M, float* N, float* w);
 
+/* ---- serving loop (continuous batching of many viewers' requests) ------
+ * The paper serves one viewer whose viewpoint commands reach the edge server
+ * and wait for the next synthesised frame (Sec. VIII, motion-to-photon
+ * delay).  Here many viewers submit viewpoint requests of any resolution; a
+ * scheduler thread inside the library packs queued requests, in arrival
+ * order, into batched launches of steps (a)-(e) on `lanes` CUDA streams.
+ * Each lane owns device scratch sized from `memory_budget`; a batch is formed
+ * when a lane is free, from the oldest requests that fit its scratch, so
+ * requests arriving while others run join the next batch (continuous
+ * batching) and batches on different lanes overlap on the GPU.  Every batch
+ * renders from the newest complete frame tick when it is formed; frames keep
+ * being uploaded with fvv_upload_frame(s) meanwhile.  Latency is measured
+ * from fvv_serve_submit to the completion of the request's output write. */
+typedef struct fvv_serve_cfg {
+    int32_t lanes;              /* batches in flight on the GPU, 1..16, default 3 */
+    int32_t max_batch;          /* views per batched launch, default 16 */
+    int32_t max_pending;        /* submitted and not yet polled, default 4096 */
+    uint64_t memory_budget;     /* device bytes of serving scratch (all lanes), default 768 MiB */
+} fvv_serve_cfg;
+
+typedef struct fvv_serve_report {
+    uint64_t submitted, completed, failed;
+    uint64_t batches;           /* batched launches */
+    double mean_batch;          /* views per launch */
+    double p50_ms, p99_ms, max_ms;   /* per-view latency, submission -> output written */
+    double views_per_s;         /* completed / (last completion - first submission) */
+    int32_t in_flight;          /* submitted, not yet finished */
+} fvv_serve_report;
+
+fvv_status fvv_serve_default_cfg(fvv_serve_cfg* cfg);
+
+/* Start the scheduler thread and allocate the lanes' scratch.  Errors:
+ * INVALID_ARG, STATE (already running), BUDGET (budget too small), CUDA. */
+fvv_status fvv_serve_start(fvv_ctx* ctx, const fvv_serve_cfg* cfg);
+
+/* Queue one view for `viewer`; `out` (device or host) receives height rows of
+ * 3 * width bytes with row pitch `pitch` and must stay valid until the
+ * ticket is polled.  Errors: INVALID_ARG, NOT_READY (no complete tick), BUSY
+ * (max_pending outstanding), BUDGET (view larger than a lane's scratch),
+ * STATE (not running / stopping). */
+fvv_status fvv_serve_submit(fvv_ctx* ctx, uint32_t viewer, const fvv_view* view, uint8_t* out,
+                            size_t pitch, uint64_t* ticket);
+
+/* Wait up to timeout_us (0 = do not wait, < 0 = until done) for a ticket.
+ * OK once the result is written (the ticket is then released), NOT_READY /
+ * TIMEOUT if not finished, INVALID_ARG for an unknown ticket, CUDA if the
+ * batch failed. */
+fvv_status fvv_serve_poll(fvv_ctx* ctx, uint64_t ticket, int64_t timeout_us);
+
+/* Throughput and latency percentiles since start or the last reset. */
+fvv_status fvv_serve_stats(fvv_ctx* ctx, fvv_serve_report* out, int32_t reset);
+
+/* Finish every queued and running request, then stop the thread and free
+ * the lanes.  fvv_destroy stops a running loop too. */
+fvv_status fvv_serve_stop(fvv_ctx* ctx);
+
 /* ---- profiling (per-stage timing, after the paper's per-stage times of
  * Sec. VIII: decode, synthesis, end-to-end) ------------------------------ */
 

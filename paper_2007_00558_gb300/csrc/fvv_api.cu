@@ -13,39 +13,54 @@
 
 #include "fvv.h"
 #include "fvv_internal.h"
+#include "fvv_runtime.h"
 
+using fvv::BatchScratch;
 using fvv::CamGeom;
 using fvv::FrameRef;
+using fvv::MemKind;
+using fvv::ParamBlock;
+using fvv::SlotState;
 using fvv::ViewDesc;
+using fvv::align_up;
+using fvv::camera_ok;
+using fvv::dev_alloc;
+using fvv::dev_free;
+using fvv::fail;
+using fvv::mem_kind;
+using fvv::run_kernel;
+using fvv::kClear;
+using fvv::kPack;
+using fvv::kResolve;
+using fvv::kSplat;
+using fvv::kNumKernels;
+using fvv::kKernelName;
 
 namespace {
-
 thread_local std::string g_err;
+}  // namespace
 
-fvv_status fail(fvv_status code, const std::string& msg)
+fvv_status fvv::fail(fvv_status code, const std::string& msg)
 {
     g_err = msg;
     return code;
 }
 
-#define FVV_CUDA(call)                                                                   \
-    do {                                                                                 \
-        cudaError_t e_ = (call);                                                         \
-        if (e_ != cudaSuccess) {                                                         \
-            cudaGetLastError();                                                          \
-            return fail(e_ == cudaErrorMemoryAllocation ? FVV_ERR_OUT_OF_MEMORY           \
-                                                        : FVV_ERR_CUDA,                   \
-                        std::string(#call) + ": " + cudaGetErrorString(e_));             \
-        }                                                                                \
-    } while (0)
+const char* const fvv::kKernelName[fvv::kNumKernels] = {"clear_keys", "warp_splat", "resolve",
+                                                        "pack_rgba"};
 
-#define FVV_TRY(expr)                      \
-    do {                                   \
-        fvv_status s_ = (expr);            \
-        if (s_ != FVV_OK) return s_;       \
-    } while (0)
+fvv::MemKind fvv::mem_kind(const void* p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return MemKind::Host;
+    }
+    return (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) ? MemKind::Device
+                                                                               : MemKind::Host;
+}
 
-size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+namespace {
 
 bool finite_all(const double* v, int n)
 {
@@ -54,7 +69,9 @@ bool finite_all(const double* v, int n)
     return true;
 }
 
-bool camera_ok(const fvv_camera& c, std::string* why)
+}  // namespace
+
+bool fvv::camera_ok(const fvv_camera& c, std::string* why)
 {
     if (c.width < 1 || c.height < 1 || c.width > 65535 || c.height > 65535) {
         *why = "width/height must be in [1, 65535]";
@@ -75,6 +92,8 @@ bool camera_ok(const fvv_camera& c, std::string* why)
     }
     return true;
 }
+
+namespace {
 
 bool options_ok(const fvv_options& o, int n_cams, std::string* why)
 {
@@ -193,46 +212,6 @@ void compose_view(int n_cams, const fvv_camera* cams, const double look_at[3],
         g[k].w = chosen[k] ? float(1.0 / (theta[k] + 1e-3)) : 0.0f;
 }
 
-enum class MemKind { Device, Host };
-
-MemKind mem_kind(const void* p)
-{
-    cudaPointerAttributes a;
-    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-        cudaGetLastError();
-        return MemKind::Host;
-    }
-    return (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) ? MemKind::Device
-                                                                               : MemKind::Host;
-}
-
-struct ParamBlock {
-    uint8_t* host = nullptr;    // pinned
-    uint8_t* dev = nullptr;
-    size_t cap = 0;
-    cudaEvent_t done = nullptr;
-    bool pending = false;
-};
-
-enum Kid { kClear = 0, kSplat, kResolve, kPack, kNumKernels };
-const char* const kKernelName[kNumKernels] = {"clear_keys", "warp_splat", "resolve", "pack_rgba"};
-
-struct KernelStat {
-    uint64_t launches = 0;
-    uint64_t timed = 0;
-    double ms = 0.0;
-    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending;
-};
-
-struct SlotState {
-    uint64_t tick = 0;
-    uint64_t mask = 0;
-    bool any = false;
-    cudaEvent_t uploaded = nullptr;   // after the last upload into this slot
-    cudaEvent_t read = nullptr;       // after the last synthesis reading it
-    bool read_pending = false;
-};
-
 }  // namespace
 
 namespace fvv {
@@ -248,47 +227,7 @@ void compose_view_into(int n_cams, const fvv_camera* cams, const double look_at[
 }
 }  // namespace fvv
 
-struct fvv_ctx {
-    int device = 0;
-    int n_cams = 0;
-    std::vector<fvv_camera> cams;
-    double look_at[3] = {0, 0, 0};
-    double depth_unit_m = 0.001;
-    fvv_options opt{};
-    cudaStream_t own = nullptr;
-    size_t smem_optin = 0;
-
-    int slots = 0;
-    std::vector<int> dpitch, rpitch;            // elements
-    std::vector<size_t> off_depth, off_rgba;    // within a slot
-    size_t slot_bytes = 0;
-    uint8_t* arena = nullptr;
-    size_t arena_bytes = 0;
-    FrameRef* frames_dev = nullptr;
-    std::vector<SlotState> slot;
-    uint64_t full_mask = 0;
-    uint64_t latest = 0;
-    bool have_latest = false;
-
-    std::vector<uint8_t*> stage_rgb;            // per camera, for host uploads
-    unsigned long long* keys = nullptr;
-    size_t keys_cap = 0;                        // elements
-    uint8_t* out_stage = nullptr;
-    size_t out_stage_cap = 0;
-
-    std::vector<ParamBlock> pring;
-    int pnext = 0;
-    cudaEvent_t scratch_done = nullptr;         // after the last batch's use of keys / out_stage
-    bool scratch_pending = false;
-    bool profiling = false;
-    KernelStat kstat[kNumKernels];
-    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> event_pool;
-    size_t held = 0;                            // device bytes held
-};
-
-namespace {
-
-fvv_status dev_alloc(fvv_ctx* c, void** p, size_t bytes)
+fvv_status fvv::dev_alloc(fvv_ctx* c, void** p, size_t bytes)
 {
     *p = nullptr;
     if (bytes == 0) return FVV_OK;
@@ -300,7 +239,7 @@ fvv_status dev_alloc(fvv_ctx* c, void** p, size_t bytes)
     return FVV_OK;
 }
 
-void dev_free(fvv_ctx* c, void* p, size_t bytes)
+void fvv::dev_free(fvv_ctx* c, void* p, size_t bytes)
 {
     if (p) {
         cudaFree(p);
@@ -308,69 +247,47 @@ void dev_free(fvv_ctx* c, void* p, size_t bytes)
     }
 }
 
-// Launch through `fn` (returns cudaError_t), counting it and, when profiling
-// is on, bracketing it with events on the launching stream.
-template <class Fn>
-fvv_status run_kernel(fvv_ctx* c, Kid id, cudaStream_t s, Fn fn)
-{
-    KernelStat& K = c->kstat[id];
-    std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
-    if (c->profiling) {
-        if (c->event_pool.empty()) {
-            FVV_CUDA(cudaEventCreate(&ev.first));
-            FVV_CUDA(cudaEventCreate(&ev.second));
-        } else {
-            ev = c->event_pool.back();
-            c->event_pool.pop_back();
-        }
-        FVV_CUDA(cudaEventRecord(ev.first, s));
-    }
-    cudaError_t e = fn();
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        if (ev.first) c->event_pool.push_back(ev);
-        return fail(FVV_ERR_CUDA, std::string("launch of ") + kKernelName[id] + ": " + cudaGetErrorString(e));
-    }
-    ++K.launches;
-    if (ev.first) {
-        FVV_CUDA(cudaEventRecord(ev.second, s));
-        K.pending.push_back(ev);
-    }
-    return FVV_OK;
-}
+namespace {
 
 size_t param_bytes(int n, int n_cams)
 {
     return align_up(size_t(n) * sizeof(ViewDesc), 256) + size_t(n) * n_cams * sizeof(CamGeom);
 }
 
-fvv_status ensure_keys(fvv_ctx* c, size_t n)
+fvv_status ensure_keys(fvv_ctx* c, BatchScratch& S, size_t n)
 {
-    if (n <= c->keys_cap) return FVV_OK;
-    if (c->keys) {
+    if (n <= S.keys_cap) return FVV_OK;
+    if (!S.growable)
+        return fail(FVV_ERR_BUDGET, "batch needs " + std::to_string(n) + " z-buffer keys; the scratch holds " +
+                                        std::to_string(S.keys_cap));
+    if (S.keys) {
         FVV_CUDA(cudaDeviceSynchronize());
-        dev_free(c, c->keys, c->keys_cap * 8);
-        c->keys = nullptr;
-        c->keys_cap = 0;
+        dev_free(c, S.keys, S.keys_cap * 8);
+        S.keys = nullptr;
+        S.keys_cap = 0;
     }
     const size_t cap = align_up(n, 1 << 16);
-    FVV_TRY(dev_alloc(c, reinterpret_cast<void**>(&c->keys), cap * 8));
-    c->keys_cap = cap;
+    FVV_TRY(dev_alloc(c, reinterpret_cast<void**>(&S.keys), cap * 8));
+    S.keys_cap = cap;
     return FVV_OK;
 }
 
-fvv_status ensure_out_stage(fvv_ctx* c, size_t bytes)
+fvv_status ensure_out_stage(fvv_ctx* c, BatchScratch& S, size_t bytes)
 {
-    if (bytes <= c->out_stage_cap) return FVV_OK;
-    if (c->out_stage) {
+    if (bytes <= S.out_stage_cap) return FVV_OK;
+    if (!S.growable)
+        return fail(FVV_ERR_BUDGET, "batch needs " + std::to_string(bytes) +
+                                        " bytes of output staging; the scratch holds " +
+                                        std::to_string(S.out_stage_cap));
+    if (S.out_stage) {
         FVV_CUDA(cudaDeviceSynchronize());
-        dev_free(c, c->out_stage, c->out_stage_cap);
-        c->out_stage = nullptr;
-        c->out_stage_cap = 0;
+        dev_free(c, S.out_stage, S.out_stage_cap);
+        S.out_stage = nullptr;
+        S.out_stage_cap = 0;
     }
     const size_t cap = align_up(bytes, 1 << 20);
-    FVV_TRY(dev_alloc(c, reinterpret_cast<void**>(&c->out_stage), cap));
-    c->out_stage_cap = cap;
+    FVV_TRY(dev_alloc(c, reinterpret_cast<void**>(&S.out_stage), cap));
+    S.out_stage_cap = cap;
     return FVV_OK;
 }
 
@@ -391,7 +308,8 @@ fvv_status upload_one(fvv_ctx* c, int cam, const uint8_t* rgb, size_t rgb_pitch,
         S.tick = tick;
         S.mask = 0;
     }
-    if (S.read_pending) FVV_CUDA(cudaStreamWaitEvent(s, S.read, 0));
+    for (int r = 0; r < fvv::kMaxReaders; ++r)
+        if (S.read_pending[r]) FVV_CUDA(cudaStreamWaitEvent(s, S.read[r], 0));
     uint8_t* base = c->arena + size_t(si) * c->slot_bytes;
     uint16_t* ddst = reinterpret_cast<uint16_t*>(base + c->off_depth[cam]);
     uint32_t* rdst = reinterpret_cast<uint32_t*>(base + c->off_rgba[cam]);
@@ -422,17 +340,252 @@ fvv_status upload_one(fvv_ctx* c, int cam, const uint8_t* rgb, size_t rgb_pitch,
     return FVV_OK;
 }
 
-struct OutPlan {
-    uint8_t* rgb_dev;
-    size_t rgb_pitch_dev;
-    bool rgb_host;
-    float* depth_dev; bool depth_host;
-    uint8_t* hole_dev; bool hole_host;
-    float* top3_dev; bool top3_host;
-    unsigned long long* keys_dev; bool keys_host;
-};
-
 }  // namespace
+
+fvv_status fvv::scratch_alloc(fvv_ctx* c, BatchScratch& S, size_t keys, size_t stage, int max_batch,
+                              int n_blocks)
+{
+    S.growable = false;
+    if (keys) {
+        FVV_TRY(dev_alloc(c, reinterpret_cast<void**>(&S.keys), keys * 8));
+        S.keys_cap = keys;
+    }
+    if (stage) {
+        FVV_TRY(dev_alloc(c, reinterpret_cast<void**>(&S.out_stage), stage));
+        S.out_stage_cap = stage;
+    }
+    const size_t pb = param_bytes(max_batch, c->n_cams);
+    S.max_batch = max_batch;
+    S.pring.resize(n_blocks);
+    for (auto& p : S.pring) {
+        FVV_CUDA(cudaHostAlloc(reinterpret_cast<void**>(&p.host), pb, cudaHostAllocDefault));
+        FVV_TRY(dev_alloc(c, reinterpret_cast<void**>(&p.dev), pb));
+        p.cap = pb;
+        FVV_CUDA(cudaEventCreateWithFlags(&p.done, cudaEventDisableTiming));
+    }
+    FVV_CUDA(cudaEventCreateWithFlags(&S.done, cudaEventDisableTiming));
+    return FVV_OK;
+}
+
+void fvv::scratch_free(fvv_ctx* c, BatchScratch& S)
+{
+    for (auto& p : S.pring) {
+        if (p.host) cudaFreeHost(p.host);
+        dev_free(c, p.dev, p.cap);
+        if (p.done) cudaEventDestroy(p.done);
+    }
+    S.pring.clear();
+    dev_free(c, S.keys, S.keys_cap * 8);
+    dev_free(c, S.out_stage, S.out_stage_cap);
+    S.keys = nullptr;
+    S.out_stage = nullptr;
+    S.keys_cap = S.out_stage_cap = 0;
+    if (S.done) cudaEventDestroy(S.done);
+    S.done = nullptr;
+}
+
+size_t fvv::view_keys(const fvv_view& v) { return align_up(size_t(v.width) * v.height, 16); }
+
+size_t fvv::view_stage_bytes(const fvv_view& v, uint8_t* out_rgb, const fvv_aux* aux)
+{
+    const size_t np = size_t(v.width) * v.height;
+    size_t b = 0;
+    if (mem_kind(out_rgb) == MemKind::Host) b += align_up(np * 3, 256);
+    if (aux) {
+        if (aux->depth && mem_kind(aux->depth) == MemKind::Host) b += align_up(np * 4, 256);
+        if (aux->hole && mem_kind(aux->hole) == MemKind::Host) b += align_up(np, 256);
+        if (aux->top3 && mem_kind(aux->top3) == MemKind::Host) b += align_up(np * 12, 256);
+        if (aux->keys && mem_kind(aux->keys) == MemKind::Host) b += align_up(np * 8, 256);
+    }
+    return b;
+}
+
+fvv_status fvv::run_batch(fvv_ctx* c, BatchScratch& S, int n, const fvv_view* views,
+                          const uint64_t* ticks, uint8_t* const* out_rgb, const size_t* out_pitch,
+                          const fvv_aux* aux, cudaStream_t s, bool sync_host)
+{
+    if (n < 1 || n > S.max_batch)
+        return fail(FVV_ERR_INVALID_ARG, "batch size must be in [1, max_batch]");
+    if (!views || !out_rgb || !out_pitch) return fail(FVV_ERR_INVALID_ARG, "NULL views/out_rgb/out_pitch");
+    FVV_CUDA(cudaSetDevice(c->device));
+
+    // validate views and resolve their frame slots
+    std::string why;
+    std::vector<int> slot_of(n);
+    size_t key_total = 0, stage_total = 0;
+    int max_w = 0, max_h = 0;
+    for (int i = 0; i < n; ++i) {
+        const fvv_view& V = views[i];
+        if (!camera_ok(V, &why)) return fail(FVV_ERR_INVALID_ARG, "view " + std::to_string(i) + ": " + why);
+        if (fvv::resolve_smem_bytes(V.width, c->n_cams) > c->smem_optin)
+            return fail(FVV_ERR_INVALID_ARG, "view " + std::to_string(i) + ": width too large");
+        if (!out_rgb[i]) return fail(FVV_ERR_INVALID_ARG, "out_rgb[" + std::to_string(i) + "] is NULL");
+        if (out_pitch[i] < size_t(V.width) * 3) return fail(FVV_ERR_INVALID_ARG, "out_pitch < 3 * width");
+        uint64_t t;
+        if (ticks) {
+            t = ticks[i];
+            const SlotState& T = c->slot[t % uint64_t(c->slots)];
+            if (!T.any || T.tick != t || T.mask != c->full_mask)
+                return fail(FVV_ERR_NOT_READY, "tick " + std::to_string(t) + " is not complete or no longer resident");
+        } else {
+            if (!c->have_latest) return fail(FVV_ERR_NOT_READY, "no complete frame tick uploaded yet");
+            t = c->latest;
+        }
+        slot_of[i] = int(t % uint64_t(c->slots));
+        const size_t np = size_t(V.width) * V.height;
+        key_total += align_up(np, 16);
+        max_w = std::max(max_w, V.width);
+        max_h = std::max(max_h, V.height);
+        if (mem_kind(out_rgb[i]) == MemKind::Host) stage_total += align_up(np * 3, 256);
+        if (aux) {
+            const fvv_aux& A = aux[i];
+            if (A.depth && mem_kind(A.depth) == MemKind::Host) stage_total += align_up(np * 4, 256);
+            if (A.hole && mem_kind(A.hole) == MemKind::Host) stage_total += align_up(np, 256);
+            if (A.top3 && mem_kind(A.top3) == MemKind::Host) stage_total += align_up(np * 12, 256);
+            if (A.keys && mem_kind(A.keys) == MemKind::Host) stage_total += align_up(np * 8, 256);
+        }
+    }
+    FVV_TRY(ensure_keys(c, S, key_total));
+    FVV_TRY(ensure_out_stage(c, S, stage_total));
+
+    // parameter block
+    ParamBlock& P = S.pring[S.pnext];
+    S.pnext = (S.pnext + 1) % int(S.pring.size());
+    if (P.pending) FVV_CUDA(cudaEventSynchronize(P.done));
+    ViewDesc* vd = reinterpret_cast<ViewDesc*>(P.host);
+    const size_t geom_off = align_up(size_t(n) * sizeof(ViewDesc), 256);
+    CamGeom* gh = reinterpret_cast<CamGeom*>(P.host + geom_off);
+    const CamGeom* gd = reinterpret_cast<const CamGeom*>(P.dev + geom_off);
+
+    struct HostCopy { void* dst; size_t dpitch; const void* src; size_t spitch, width, height; };
+    std::vector<HostCopy> d2h;
+    std::vector<std::pair<void*, const void*>> raw_copies;   // keys_raw
+    std::vector<size_t> raw_bytes;
+    size_t koff = 0, soff = 0;
+    int max_chunks = 0;
+    bool any_host = false;
+    for (int i = 0; i < n; ++i) {
+        const fvv_view& V = views[i];
+        ViewDesc& D = vd[i];
+        std::memset(&D, 0, sizeof D);
+        const size_t np = size_t(V.width) * V.height;
+        D.Wv = V.width;
+        D.Hv = V.height;
+        D.n_cams = c->n_cams;
+        D.slot = slot_of[i];
+        D.flags = (c->opt.crack_filter ? fvv::kFlagCrack : 0) | (c->opt.hole_fill ? fvv::kFlagFill : 0);
+        D.tau_crack = c->opt.tau_crack;
+        D.tau_vis = c->opt.tau_vis;
+        D.z_min = c->opt.z_min;
+        D.d_lo = c->opt.d_lo;
+        D.d_hi = c->opt.d_hi;
+        D.keys = S.keys + koff;
+        koff += align_up(np, 16);
+        CamGeom* g = gh + size_t(i) * c->n_cams;
+        compose_view(c->n_cams, c->cams.data(), c->look_at, c->depth_unit_m, c->opt.n_ref, V, g);
+        D.geom = gd + size_t(i) * c->n_cams;
+        int na = 0, chunks = 0;
+        D.chunk_begin[0] = 0;
+        for (int k = 0; k < c->n_cams; ++k)
+            if (g[k].w > 0.0f) {
+                D.active[na] = k;
+                chunks += c->cams[k].height * ((c->cams[k].width + fvv::kSplatSeg - 1) / fvv::kSplatSeg);
+                D.chunk_begin[++na] = chunks;
+            }
+        D.n_active = na;
+        max_chunks = std::max(max_chunks, chunks);
+        auto stage = [&](size_t bytes) {
+            uint8_t* p = S.out_stage + soff;
+            soff += align_up(bytes, 256);
+            return p;
+        };
+        if (mem_kind(out_rgb[i]) == MemKind::Host) {
+            D.out_rgb = stage(np * 3);
+            D.out_pitch = int64_t(V.width) * 3;
+            d2h.push_back({out_rgb[i], out_pitch[i], D.out_rgb, size_t(V.width) * 3, size_t(V.width) * 3,
+                           size_t(V.height)});
+        } else {
+            D.out_rgb = out_rgb[i];
+            D.out_pitch = int64_t(out_pitch[i]);
+        }
+        if (aux) {
+            const fvv_aux& A = aux[i];
+            auto plan = [&](void* user, size_t elem, void** dev_field) {
+                if (!user) return;
+                if (mem_kind(user) == MemKind::Host) {
+                    uint8_t* p = stage(np * elem);
+                    *dev_field = p;
+                    d2h.push_back({user, np * elem, p, np * elem, np * elem, 1});
+                } else {
+                    *dev_field = user;
+                }
+            };
+            plan(A.depth, 4, reinterpret_cast<void**>(&D.out_depth));
+            plan(A.hole, 1, reinterpret_cast<void**>(&D.out_hole));
+            plan(A.top3, 12, reinterpret_cast<void**>(&D.out_top3));
+            plan(A.keys, 8, reinterpret_cast<void**>(&D.out_keys));
+            if (A.keys_raw) {
+                raw_copies.push_back({A.keys_raw, D.keys});
+                raw_bytes.push_back(np * 8);
+                if (mem_kind(A.keys_raw) == MemKind::Host) any_host = true;
+            }
+        }
+    }
+    if (!d2h.empty()) any_host = true;
+    bool want_top3 = false;
+    for (int i = 0; aux && i < n; ++i) want_top3 = want_top3 || aux[i].top3 != nullptr;
+    const size_t pbytes = geom_off + size_t(n) * c->n_cams * sizeof(CamGeom);
+    FVV_CUDA(cudaMemcpyAsync(P.dev, P.host, pbytes, cudaMemcpyHostToDevice, s));
+    const ViewDesc* vdev = reinterpret_cast<const ViewDesc*>(P.dev);
+
+    std::vector<int> used(c->slots, 0);
+    for (int i = 0; i < n; ++i) used[slot_of[i]] = 1;
+    for (int si = 0; si < c->slots; ++si)
+        if (used[si]) FVV_CUDA(cudaStreamWaitEvent(s, c->slot[si].uploaded, 0));
+
+    // the z-buffer scratch and output staging are shared by all batches using
+    // S: a batch on another stream waits for the previous one
+    if (S.pending) FVV_CUDA(cudaStreamWaitEvent(s, S.done, 0));
+    FVV_TRY(run_kernel(c, kClear, s, [&] { return fvv::launch_clear_keys(S.keys, koff, s); }));
+    FVV_TRY(run_kernel(c, kSplat, s, [&] {
+        return fvv::launch_warp_splat(vdev, n, max_chunks, c->frames_dev, s);
+    }));
+    for (size_t r = 0; r < raw_copies.size(); ++r)
+        FVV_CUDA(cudaMemcpyAsync(raw_copies[r].first, raw_copies[r].second, raw_bytes[r],
+                                 cudaMemcpyDefault, s));
+    FVV_TRY(run_kernel(c, kResolve, s, [&] {
+        return fvv::launch_resolve(vdev, n, max_h, max_w, c->n_cams, want_top3, c->frames_dev, s);
+    }));
+    for (const HostCopy& h : d2h)
+        FVV_CUDA(cudaMemcpy2DAsync(h.dst, h.dpitch, h.src, h.spitch, h.width, h.height,
+                                   cudaMemcpyDeviceToHost, s));
+    FVV_CUDA(cudaEventRecord(P.done, s));
+    P.pending = true;
+    FVV_CUDA(cudaEventRecord(S.done, s));
+    S.pending = true;
+    for (int si = 0; si < c->slots; ++si)
+        if (used[si]) {
+            SlotState& T = c->slot[si];
+            if (!T.read[S.reader])
+                FVV_CUDA(cudaEventCreateWithFlags(&T.read[S.reader], cudaEventDisableTiming));
+            FVV_CUDA(cudaEventRecord(T.read[S.reader], s));
+            T.read_pending[S.reader] = true;
+        }
+    if (any_host && sync_host) FVV_CUDA(cudaStreamSynchronize(s));
+    return FVV_OK;
+}
+
+fvv_status fvv_synthesize_batch(fvv_ctx* c, int32_t n, const fvv_view* views, const uint64_t* ticks,
+                                uint8_t* const* out_rgb, const size_t* out_pitch, const fvv_aux* aux,
+                                void* stream)
+{
+    if (!c) return fail(FVV_ERR_INVALID_ARG, "ctx is NULL");
+    if (n < 1 || n > c->opt.max_batch)
+        return fail(FVV_ERR_INVALID_ARG, "batch size must be in [1, max_batch]");
+    cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : c->own;
+    std::lock_guard<std::recursive_mutex> lock(c->mu);
+    return fvv::run_batch(c, c->main, n, views, ticks, out_rgb, out_pitch, aux, s, true);
+}
 
 // ===========================================================================
 // C ABI
@@ -497,21 +650,18 @@ fvv_status fvv_view_params(const fvv_rig* rig, const fvv_options* opt, const fvv
 fvv_status fvv_destroy(fvv_ctx* c)
 {
     if (!c) return FVV_OK;
+    fvv::serve_shutdown(c);
     int cur = 0;
     cudaGetDevice(&cur);
     cudaSetDevice(c->device);
     if (c->own) cudaStreamSynchronize(c->own);
     cudaDeviceSynchronize();
-    for (auto& p : c->pring) {
-        if (p.host) cudaFreeHost(p.host);
-        dev_free(c, p.dev, p.cap);
-        if (p.done) cudaEventDestroy(p.done);
-    }
+    fvv::scratch_free(c, c->main);
     for (auto& S : c->slot) {
         if (S.uploaded) cudaEventDestroy(S.uploaded);
-        if (S.read) cudaEventDestroy(S.read);
+        for (cudaEvent_t e : S.read)
+            if (e) cudaEventDestroy(e);
     }
-    if (c->scratch_done) cudaEventDestroy(c->scratch_done);
     for (auto& K : c->kstat)
         for (auto& ev : K.pending) c->event_pool.push_back(ev);
     for (auto& ev : c->event_pool) {
@@ -521,8 +671,6 @@ fvv_status fvv_destroy(fvv_ctx* c)
     for (int k = 0; k < c->n_cams; ++k)
         if (c->stage_rgb[k])
             dev_free(c, c->stage_rgb[k], size_t(c->cams[k].width) * 3 * size_t(c->cams[k].height));
-    dev_free(c, c->keys, c->keys_cap * 8);
-    dev_free(c, c->out_stage, c->out_stage_cap);
     dev_free(c, c->frames_dev, sizeof(FrameRef) * size_t(c->slots) * c->n_cams);
     dev_free(c, c->arena, c->arena_bytes);
     if (c->own) cudaStreamDestroy(c->own);
@@ -617,18 +765,10 @@ fvv_status fvv_create(const fvv_rig* rig, const fvv_options* opt, fvv_ctx** out)
     c->slot.resize(c->slots);
     for (auto& S : c->slot) {
         FVV_CREATE_CUDA(cudaEventCreateWithFlags(&S.uploaded, cudaEventDisableTiming));
-        FVV_CREATE_CUDA(cudaEventCreateWithFlags(&S.read, cudaEventDisableTiming));
         FVV_CREATE_CUDA(cudaEventRecord(S.uploaded, c->own));
     }
-    FVV_CREATE_CUDA(cudaEventCreateWithFlags(&c->scratch_done, cudaEventDisableTiming));
-    c->pring.resize(4);
-    const size_t pb = param_bytes(o.max_batch, c->n_cams);
-    for (auto& p : c->pring) {
-        FVV_CREATE_CUDA(cudaHostAlloc(reinterpret_cast<void**>(&p.host), pb, cudaHostAllocDefault));
-        FVV_CREATE_TRY(dev_alloc(c, reinterpret_cast<void**>(&p.dev), pb));
-        p.cap = pb;
-        FVV_CREATE_CUDA(cudaEventCreateWithFlags(&p.done, cudaEventDisableTiming));
-    }
+    FVV_CREATE_TRY(fvv::scratch_alloc(c, c->main, 0, 0, o.max_batch, 4));
+    c->main.growable = true;
     FVV_CREATE_CUDA(cudaStreamSynchronize(c->own));
 #undef FVV_CREATE_TRY
 #undef FVV_CREATE_CUDA
@@ -642,6 +782,7 @@ fvv_status fvv_upload_frame(fvv_ctx* c, int32_t cam, const uint8_t* rgb, size_t 
     if (!c) return fail(FVV_ERR_INVALID_ARG, "ctx is NULL");
     if (cam < 0 || cam >= c->n_cams) return fail(FVV_ERR_INVALID_ARG, "camera index out of range");
     cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : c->own;
+    std::lock_guard<std::recursive_mutex> lock(c->mu);
     return upload_one(c, cam, rgb, rgb_pitch, depth, depth_pitch, tick, s);
 }
 
@@ -652,6 +793,7 @@ fvv_status fvv_upload_frames(fvv_ctx* c, const uint8_t* rgb, size_t rgb_cam_stri
     if (!c) return fail(FVV_ERR_INVALID_ARG, "ctx is NULL");
     if (!rgb || !depth) return fail(FVV_ERR_INVALID_ARG, "rgb and depth must be non-NULL");
     cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : c->own;
+    std::lock_guard<std::recursive_mutex> lock(c->mu);
     for (int k = 0; k < c->n_cams; ++k) {
         const uint8_t* r = rgb + size_t(k) * rgb_cam_stride;
         const uint16_t* d = reinterpret_cast<const uint16_t*>(
@@ -664,188 +806,16 @@ fvv_status fvv_upload_frames(fvv_ctx* c, const uint8_t* rgb, size_t rgb_cam_stri
 fvv_status fvv_latest_tick(fvv_ctx* c, uint64_t* tick)
 {
     if (!c || !tick) return fail(FVV_ERR_INVALID_ARG, "NULL argument");
+    std::lock_guard<std::recursive_mutex> lock(c->mu);
     if (!c->have_latest) return fail(FVV_ERR_NOT_READY, "no complete frame tick uploaded yet");
     *tick = c->latest;
-    return FVV_OK;
-}
-
-fvv_status fvv_synthesize_batch(fvv_ctx* c, int32_t n, const fvv_view* views, const uint64_t* ticks,
-                                uint8_t* const* out_rgb, const size_t* out_pitch, const fvv_aux* aux,
-                                void* stream)
-{
-    if (!c) return fail(FVV_ERR_INVALID_ARG, "ctx is NULL");
-    if (n < 1 || n > c->opt.max_batch)
-        return fail(FVV_ERR_INVALID_ARG, "batch size must be in [1, max_batch]");
-    if (!views || !out_rgb || !out_pitch) return fail(FVV_ERR_INVALID_ARG, "NULL views/out_rgb/out_pitch");
-    cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : c->own;
-    FVV_CUDA(cudaSetDevice(c->device));
-
-    // validate views and resolve their frame slots
-    std::string why;
-    std::vector<int> slot_of(n);
-    size_t key_total = 0, stage_total = 0;
-    int max_w = 0, max_h = 0;
-    for (int i = 0; i < n; ++i) {
-        const fvv_view& V = views[i];
-        if (!camera_ok(V, &why)) return fail(FVV_ERR_INVALID_ARG, "view " + std::to_string(i) + ": " + why);
-        if (fvv::resolve_smem_bytes(V.width, c->n_cams) > c->smem_optin)
-            return fail(FVV_ERR_INVALID_ARG, "view " + std::to_string(i) + ": width too large");
-        if (!out_rgb[i]) return fail(FVV_ERR_INVALID_ARG, "out_rgb[" + std::to_string(i) + "] is NULL");
-        if (out_pitch[i] < size_t(V.width) * 3) return fail(FVV_ERR_INVALID_ARG, "out_pitch < 3 * width");
-        uint64_t t;
-        if (ticks) {
-            t = ticks[i];
-            const SlotState& S = c->slot[t % uint64_t(c->slots)];
-            if (!S.any || S.tick != t || S.mask != c->full_mask)
-                return fail(FVV_ERR_NOT_READY, "tick " + std::to_string(t) + " is not complete or no longer resident");
-        } else {
-            if (!c->have_latest) return fail(FVV_ERR_NOT_READY, "no complete frame tick uploaded yet");
-            t = c->latest;
-        }
-        slot_of[i] = int(t % uint64_t(c->slots));
-        const size_t np = size_t(V.width) * V.height;
-        key_total += align_up(np, 16);
-        max_w = std::max(max_w, V.width);
-        max_h = std::max(max_h, V.height);
-        if (mem_kind(out_rgb[i]) == MemKind::Host) stage_total += align_up(np * 3, 256);
-        if (aux) {
-            const fvv_aux& A = aux[i];
-            if (A.depth && mem_kind(A.depth) == MemKind::Host) stage_total += align_up(np * 4, 256);
-            if (A.hole && mem_kind(A.hole) == MemKind::Host) stage_total += align_up(np, 256);
-            if (A.top3 && mem_kind(A.top3) == MemKind::Host) stage_total += align_up(np * 12, 256);
-            if (A.keys && mem_kind(A.keys) == MemKind::Host) stage_total += align_up(np * 8, 256);
-        }
-    }
-    FVV_TRY(ensure_keys(c, key_total));
-    FVV_TRY(ensure_out_stage(c, stage_total));
-
-    // parameter block
-    ParamBlock& P = c->pring[c->pnext];
-    c->pnext = (c->pnext + 1) % int(c->pring.size());
-    if (P.pending) FVV_CUDA(cudaEventSynchronize(P.done));
-    ViewDesc* vd = reinterpret_cast<ViewDesc*>(P.host);
-    const size_t geom_off = align_up(size_t(n) * sizeof(ViewDesc), 256);
-    CamGeom* gh = reinterpret_cast<CamGeom*>(P.host + geom_off);
-    const CamGeom* gd = reinterpret_cast<const CamGeom*>(P.dev + geom_off);
-
-    struct HostCopy { void* dst; size_t dpitch; const void* src; size_t spitch, width, height; };
-    std::vector<HostCopy> d2h;
-    std::vector<std::pair<void*, const void*>> raw_copies;   // keys_raw
-    std::vector<size_t> raw_bytes;
-    size_t koff = 0, soff = 0;
-    int max_chunks = 0;
-    bool any_host = false;
-    for (int i = 0; i < n; ++i) {
-        const fvv_view& V = views[i];
-        ViewDesc& D = vd[i];
-        std::memset(&D, 0, sizeof D);
-        const size_t np = size_t(V.width) * V.height;
-        D.Wv = V.width;
-        D.Hv = V.height;
-        D.n_cams = c->n_cams;
-        D.slot = slot_of[i];
-        D.flags = (c->opt.crack_filter ? fvv::kFlagCrack : 0) | (c->opt.hole_fill ? fvv::kFlagFill : 0);
-        D.tau_crack = c->opt.tau_crack;
-        D.tau_vis = c->opt.tau_vis;
-        D.z_min = c->opt.z_min;
-        D.d_lo = c->opt.d_lo;
-        D.d_hi = c->opt.d_hi;
-        D.keys = c->keys + koff;
-        koff += align_up(np, 16);
-        CamGeom* g = gh + size_t(i) * c->n_cams;
-        compose_view(c->n_cams, c->cams.data(), c->look_at, c->depth_unit_m, c->opt.n_ref, V, g);
-        D.geom = gd + size_t(i) * c->n_cams;
-        int na = 0, chunks = 0;
-        D.chunk_begin[0] = 0;
-        for (int k = 0; k < c->n_cams; ++k)
-            if (g[k].w > 0.0f) {
-                D.active[na] = k;
-                chunks += c->cams[k].height * ((c->cams[k].width + fvv::kSplatSeg - 1) / fvv::kSplatSeg);
-                D.chunk_begin[++na] = chunks;
-            }
-        D.n_active = na;
-        max_chunks = std::max(max_chunks, chunks);
-        auto stage = [&](size_t bytes) {
-            uint8_t* p = c->out_stage + soff;
-            soff += align_up(bytes, 256);
-            return p;
-        };
-        if (mem_kind(out_rgb[i]) == MemKind::Host) {
-            D.out_rgb = stage(np * 3);
-            D.out_pitch = int64_t(V.width) * 3;
-            d2h.push_back({out_rgb[i], out_pitch[i], D.out_rgb, size_t(V.width) * 3, size_t(V.width) * 3,
-                           size_t(V.height)});
-        } else {
-            D.out_rgb = out_rgb[i];
-            D.out_pitch = int64_t(out_pitch[i]);
-        }
-        if (aux) {
-            const fvv_aux& A = aux[i];
-            auto plan = [&](void* user, size_t elem, void** dev_field) {
-                if (!user) return;
-                if (mem_kind(user) == MemKind::Host) {
-                    uint8_t* p = stage(np * elem);
-                    *dev_field = p;
-                    d2h.push_back({user, np * elem, p, np * elem, np * elem, 1});
-                } else {
-                    *dev_field = user;
-                }
-            };
-            plan(A.depth, 4, reinterpret_cast<void**>(&D.out_depth));
-            plan(A.hole, 1, reinterpret_cast<void**>(&D.out_hole));
-            plan(A.top3, 12, reinterpret_cast<void**>(&D.out_top3));
-            plan(A.keys, 8, reinterpret_cast<void**>(&D.out_keys));
-            if (A.keys_raw) {
-                raw_copies.push_back({A.keys_raw, D.keys});
-                raw_bytes.push_back(np * 8);
-                if (mem_kind(A.keys_raw) == MemKind::Host) any_host = true;
-            }
-        }
-    }
-    if (!d2h.empty()) any_host = true;
-    bool want_top3 = false;
-    for (int i = 0; aux && i < n; ++i) want_top3 = want_top3 || aux[i].top3 != nullptr;
-    const size_t pbytes = geom_off + size_t(n) * c->n_cams * sizeof(CamGeom);
-    FVV_CUDA(cudaMemcpyAsync(P.dev, P.host, pbytes, cudaMemcpyHostToDevice, s));
-    const ViewDesc* vdev = reinterpret_cast<const ViewDesc*>(P.dev);
-
-    std::vector<int> used(c->slots, 0);
-    for (int i = 0; i < n; ++i) used[slot_of[i]] = 1;
-    for (int si = 0; si < c->slots; ++si)
-        if (used[si]) FVV_CUDA(cudaStreamWaitEvent(s, c->slot[si].uploaded, 0));
-
-    // the z-buffer scratch and output staging are shared by all batches of
-    // the context: a batch on another stream waits for the previous one
-    if (c->scratch_pending) FVV_CUDA(cudaStreamWaitEvent(s, c->scratch_done, 0));
-    FVV_TRY(run_kernel(c, kClear, s, [&] { return fvv::launch_clear_keys(c->keys, koff, s); }));
-    FVV_TRY(run_kernel(c, kSplat, s, [&] {
-        return fvv::launch_warp_splat(vdev, n, max_chunks, c->frames_dev, s);
-    }));
-    for (size_t r = 0; r < raw_copies.size(); ++r)
-        FVV_CUDA(cudaMemcpyAsync(raw_copies[r].first, raw_copies[r].second, raw_bytes[r],
-                                 cudaMemcpyDefault, s));
-    FVV_TRY(run_kernel(c, kResolve, s, [&] {
-        return fvv::launch_resolve(vdev, n, max_h, max_w, c->n_cams, want_top3, c->frames_dev, s);
-    }));
-    for (const HostCopy& h : d2h)
-        FVV_CUDA(cudaMemcpy2DAsync(h.dst, h.dpitch, h.src, h.spitch, h.width, h.height,
-                                   cudaMemcpyDeviceToHost, s));
-    FVV_CUDA(cudaEventRecord(P.done, s));
-    P.pending = true;
-    FVV_CUDA(cudaEventRecord(c->scratch_done, s));
-    c->scratch_pending = true;
-    for (int si = 0; si < c->slots; ++si)
-        if (used[si]) {
-            FVV_CUDA(cudaEventRecord(c->slot[si].read, s));
-            c->slot[si].read_pending = true;
-        }
-    if (any_host) FVV_CUDA(cudaStreamSynchronize(s));
     return FVV_OK;
 }
 
 fvv_status fvv_profile_enable(fvv_ctx* c, int32_t on)
 {
     if (!c) return fail(FVV_ERR_INVALID_ARG, "ctx is NULL");
+    std::lock_guard<std::recursive_mutex> lock(c->mu);
     c->profiling = on != 0;
     return FVV_OK;
 }
@@ -853,6 +823,7 @@ fvv_status fvv_profile_enable(fvv_ctx* c, int32_t on)
 fvv_status fvv_profile_read(fvv_ctx* c, fvv_kernel_stats* out, int32_t* n, int32_t reset)
 {
     if (!c || !n) return fail(FVV_ERR_INVALID_ARG, "NULL argument");
+    std::lock_guard<std::recursive_mutex> lock(c->mu);
     for (auto& K : c->kstat) {
         for (auto& ev : K.pending) {
             FVV_CUDA(cudaEventSynchronize(ev.second));

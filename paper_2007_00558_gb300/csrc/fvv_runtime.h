@@ -1,0 +1,191 @@
+// fvv_runtime.h -- host runtime internals shared by fvv_api.cu (context,
+// uploads, batched synthesis) and fvv_serve.cu (the serving loop).  Not part
+// of the public ABI.
+#pragma once
+
+#include <cstdint>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "fvv.h"
+#include "fvv_internal.h"
+
+namespace fvv {
+
+// Records `msg` for fvv_last_error() on this thread and returns `code`.
+fvv_status fail(fvv_status code, const std::string& msg);
+
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+#define FVV_CUDA(call)                                                                   \
+    do {                                                                                 \
+        cudaError_t e_ = (call);                                                         \
+        if (e_ != cudaSuccess) {                                                         \
+            cudaGetLastError();                                                          \
+            return ::fvv::fail(e_ == cudaErrorMemoryAllocation ? FVV_ERR_OUT_OF_MEMORY    \
+                                                               : FVV_ERR_CUDA,            \
+                               std::string(#call) + ": " + cudaGetErrorString(e_));      \
+        }                                                                                \
+    } while (0)
+
+#define FVV_TRY(expr)                      \
+    do {                                   \
+        fvv_status s_ = (expr);            \
+        if (s_ != FVV_OK) return s_;       \
+    } while (0)
+
+enum class MemKind { Device, Host };
+MemKind mem_kind(const void* p);
+
+// Valid pinhole camera (also used for views); `why` gets the reason.
+bool camera_ok(const fvv_camera& c, std::string* why);
+
+struct ParamBlock {
+    uint8_t* host = nullptr;    // pinned
+    uint8_t* dev = nullptr;
+    size_t cap = 0;
+    cudaEvent_t done = nullptr;
+    bool pending = false;
+};
+
+enum Kid { kClear = 0, kSplat, kResolve, kPack, kNumKernels };
+extern const char* const kKernelName[kNumKernels];
+
+struct KernelStat {
+    uint64_t launches = 0;
+    uint64_t timed = 0;
+    double ms = 0.0;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending;
+};
+
+// Readers of the frame ring: the context's own scratch (0) and up to 16
+// serving lanes; each records its own "last read" event per slot.
+constexpr int kMaxReaders = 17;
+
+struct SlotState {
+    uint64_t tick = 0;
+    uint64_t mask = 0;
+    bool any = false;
+    cudaEvent_t uploaded = nullptr;            // after the last upload into this slot
+    cudaEvent_t read[kMaxReaders] = {};        // after each reader's last synthesis of it
+    bool read_pending[kMaxReaders] = {};
+};
+
+// Device scratch of batched launches: the z-buffer keys, the staging area
+// for host outputs and a ring of parameter blocks.  The context's own
+// scratch grows on demand; a serving lane's is sized once from its budget.
+struct BatchScratch {
+    unsigned long long* keys = nullptr;
+    size_t keys_cap = 0;                  // elements
+    uint8_t* out_stage = nullptr;
+    size_t out_stage_cap = 0;             // bytes
+    std::vector<ParamBlock> pring;
+    int pnext = 0;
+    cudaEvent_t done = nullptr;           // after the last batch using this scratch
+    bool pending = false;
+    bool growable = true;
+    int reader = 0;                       // index into SlotState::read
+    int max_batch = 0;                    // views per launch the parameter blocks hold
+};
+
+struct ServeState;                        // fvv_serve.cu
+
+}  // namespace fvv
+
+struct fvv_ctx {
+    int device = 0;
+    int n_cams = 0;
+    std::vector<fvv_camera> cams;
+    double look_at[3] = {0, 0, 0};
+    double depth_unit_m = 0.001;
+    fvv_options opt{};
+    cudaStream_t own = nullptr;
+    size_t smem_optin = 0;
+
+    int slots = 0;
+    std::vector<int> dpitch, rpitch;            // elements
+    std::vector<size_t> off_depth, off_rgba;    // within a slot
+    size_t slot_bytes = 0;
+    uint8_t* arena = nullptr;
+    size_t arena_bytes = 0;
+    fvv::FrameRef* frames_dev = nullptr;
+    std::vector<fvv::SlotState> slot;
+    uint64_t full_mask = 0;
+    uint64_t latest = 0;
+    bool have_latest = false;
+
+    std::vector<uint8_t*> stage_rgb;            // per camera, for host uploads
+    fvv::BatchScratch main;                     // scratch of fvv_synthesize(_batch)
+
+    bool profiling = false;
+    fvv::KernelStat kstat[fvv::kNumKernels];
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> event_pool;
+    size_t held = 0;                            // device bytes held
+
+    // Guards the frame-ring state, the kernel statistics and the scratch
+    // against the serving thread.
+    std::recursive_mutex mu;
+    fvv::ServeState* serve = nullptr;
+};
+
+namespace fvv {
+
+fvv_status dev_alloc(fvv_ctx* c, void** p, size_t bytes);
+void dev_free(fvv_ctx* c, void* p, size_t bytes);
+
+// Launch through `fn` (returns cudaError_t), counting it and, when profiling
+// is on, bracketing it with events on the launching stream.
+template <class Fn>
+fvv_status run_kernel(fvv_ctx* c, Kid id, cudaStream_t s, Fn fn)
+{
+    KernelStat& K = c->kstat[id];
+    std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
+    if (c->profiling) {
+        if (c->event_pool.empty()) {
+            FVV_CUDA(cudaEventCreate(&ev.first));
+            FVV_CUDA(cudaEventCreate(&ev.second));
+        } else {
+            ev = c->event_pool.back();
+            c->event_pool.pop_back();
+        }
+        FVV_CUDA(cudaEventRecord(ev.first, s));
+    }
+    cudaError_t e = fn();
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        if (ev.first) c->event_pool.push_back(ev);
+        return fail(FVV_ERR_CUDA, std::string("launch of ") + kKernelName[id] + ": " + cudaGetErrorString(e));
+    }
+    ++K.launches;
+    if (ev.first) {
+        FVV_CUDA(cudaEventRecord(ev.second, s));
+        K.pending.push_back(ev);
+    }
+    return FVV_OK;
+}
+
+// Allocate `S` with room for `keys` z-buffer entries, `stage` staging bytes
+// and `n_blocks` parameter blocks of `max_batch` views; growable = false.
+fvv_status scratch_alloc(fvv_ctx* c, BatchScratch& S, size_t keys, size_t stage, int max_batch,
+                         int n_blocks);
+void scratch_free(fvv_ctx* c, BatchScratch& S);
+
+// Keys (elements) and host-output staging bytes one view needs.
+size_t view_keys(const fvv_view& v);
+size_t view_stage_bytes(const fvv_view& v, uint8_t* out_rgb, const fvv_aux* aux);
+
+// One batched launch of steps a-e for n views on stream s, with scratch S.
+// ticks[i] selects view i's tick (NULL = newest complete).  With sync_host
+// the call waits for host outputs; without, the caller orders on the stream.
+// The caller holds c->mu.
+fvv_status run_batch(fvv_ctx* c, BatchScratch& S, int n, const fvv_view* views,
+                     const uint64_t* ticks, uint8_t* const* out_rgb, const size_t* out_pitch,
+                     const fvv_aux* aux, cudaStream_t s, bool sync_host);
+
+// fvv_serve.cu: stop a running serving loop (fvv_destroy calls it).
+void serve_shutdown(fvv_ctx* c);
+
+}  // namespace fvv

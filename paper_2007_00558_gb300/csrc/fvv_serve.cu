@@ -1,0 +1,388 @@
+// fvv_serve.cu -- continuous-batching serving loop over the view-synthesis
+// path.
+//
+// Many viewers each request their own virtual viewpoint (the paper's
+// interactive use: a viewer moves the virtual camera and waits for the new
+// view, Sec. VIII motion-to-photon delay).  Requests of any resolution are
+// admitted into a queue; a scheduler thread packs them, in arrival order,
+// into batched launches of steps a-e on `lanes` CUDA streams.  Each lane owns
+// device scratch sized from the memory budget, so a batch is admitted only
+// when a lane and its memory are free, and batches on different lanes overlap
+// on the GPU.  Requests that arrive while batches run join the next batch as
+// soon as a lane frees up (continuous batching).  Every batch renders from
+// the newest complete frame tick at the moment it is formed.  A host callback
+// on the lane's stream stamps each request's completion; latency is
+// submission to completion of its output write.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <condition_variable>
+#include <deque>
+#include <memory>
+#include <thread>
+#include <unordered_map>
+
+#include "fvv_runtime.h"
+
+namespace fvv {
+
+namespace {
+
+double now_s()
+{
+    using namespace std::chrono;
+    return duration<double>(steady_clock::now().time_since_epoch()).count();
+}
+
+enum class ReqState { Queued, Running, Done, Failed };
+
+struct Req {
+    uint64_t ticket;
+    uint32_t viewer;
+    fvv_view view;
+    uint8_t* out;
+    size_t pitch;
+};
+
+struct Rec {
+    ReqState state = ReqState::Queued;
+    double t_submit = 0.0;
+    double t_done = 0.0;
+};
+
+}  // namespace
+
+struct ServeLane {
+    ServeState* owner = nullptr;
+    int index = 0;
+    cudaStream_t stream = nullptr;
+    BatchScratch S;
+    bool busy = false;
+    std::vector<uint64_t> tickets;
+};
+
+struct ServeState {
+    fvv_ctx* ctx = nullptr;
+    fvv_serve_cfg cfg{};
+    std::thread thread;
+    std::mutex mu;
+    std::condition_variable cv;
+    std::deque<Req> queue;
+    std::unordered_map<uint64_t, Rec> recs;
+    std::vector<std::unique_ptr<ServeLane>> lanes;
+    size_t lane_keys = 0, lane_stage = 0;
+    bool stopping = false;
+    uint64_t next_ticket = 1;
+    uint64_t submitted = 0, completed = 0, failed = 0, batches = 0, batch_views = 0;
+    std::vector<double> lat_ms;
+    double t_first = -1.0, t_last = -1.0;
+    std::string error;
+};
+
+namespace {
+
+void CUDART_CB lane_done(void* p)
+{
+    // runs on a CUDA callback thread: no CUDA calls here
+    ServeLane* L = static_cast<ServeLane*>(p);
+    ServeState* st = L->owner;
+    const double t = now_s();
+    {
+        std::lock_guard<std::mutex> lk(st->mu);
+        for (uint64_t tk : L->tickets) {
+            auto it = st->recs.find(tk);
+            if (it == st->recs.end()) continue;
+            it->second.state = ReqState::Done;
+            it->second.t_done = t;
+            st->lat_ms.push_back(1e3 * (t - it->second.t_submit));
+            ++st->completed;
+        }
+        st->t_last = t;
+        L->tickets.clear();
+        L->busy = false;
+    }
+    st->cv.notify_all();
+}
+
+void scheduler(ServeState* st)
+{
+    fvv_ctx* c = st->ctx;
+    cudaSetDevice(c->device);
+    std::vector<fvv_view> views;
+    std::vector<uint8_t*> outs;
+    std::vector<size_t> pitches;
+    std::unique_lock<std::mutex> lk(st->mu);
+    for (;;) {
+        auto free_lane = [&]() -> ServeLane* {
+            for (auto& L : st->lanes)
+                if (!L->busy) return L.get();
+            return nullptr;
+        };
+        auto idle = [&]() {
+            for (auto& L : st->lanes)
+                if (L->busy) return false;
+            return true;
+        };
+        st->cv.wait_for(lk, std::chrono::milliseconds(5), [&] {
+            return (st->stopping && st->queue.empty() && idle()) ||
+                   (!st->queue.empty() && free_lane() != nullptr);
+        });
+        if (st->stopping && st->queue.empty() && idle()) break;
+        ServeLane* L;
+        while (!st->queue.empty() && (L = free_lane()) != nullptr) {
+            // pack the oldest requests that fit this lane's scratch
+            views.clear();
+            outs.clear();
+            pitches.clear();
+            L->tickets.clear();
+            size_t keys = 0, stage = 0;
+            while (!st->queue.empty() && int(views.size()) < st->cfg.max_batch) {
+                const Req& r = st->queue.front();
+                const size_t k = view_keys(r.view), b = view_stage_bytes(r.view, r.out, nullptr);
+                if (keys + k > L->S.keys_cap || stage + b > L->S.out_stage_cap) break;
+                keys += k;
+                stage += b;
+                views.push_back(r.view);
+                outs.push_back(r.out);
+                pitches.push_back(r.pitch);
+                L->tickets.push_back(r.ticket);
+                st->recs[r.ticket].state = ReqState::Running;
+                st->queue.pop_front();
+            }
+            L->busy = true;
+            ++st->batches;
+            st->batch_views += views.size();
+            lk.unlock();
+            fvv_status rc;
+            std::string err;
+            {
+                std::lock_guard<std::recursive_mutex> g(c->mu);
+                rc = run_batch(c, L->S, int(views.size()), views.data(), nullptr, outs.data(),
+                               pitches.data(), nullptr, L->stream, false);
+                if (rc == FVV_OK) {
+                    cudaError_t e = cudaLaunchHostFunc(L->stream, lane_done, L);
+                    if (e != cudaSuccess) {
+                        cudaGetLastError();
+                        rc = FVV_ERR_CUDA;
+                        err = std::string("cudaLaunchHostFunc: ") + cudaGetErrorString(e);
+                    }
+                } else {
+                    err = fvv_last_error();
+                }
+            }
+            lk.lock();
+            if (rc != FVV_OK) {
+                for (uint64_t tk : L->tickets) {
+                    st->recs[tk].state = ReqState::Failed;
+                    ++st->failed;
+                }
+                L->tickets.clear();
+                L->busy = false;
+                st->error = err;
+                st->cv.notify_all();
+            }
+        }
+    }
+}
+
+}  // namespace
+
+void serve_shutdown(fvv_ctx* c)
+{
+    ServeState* st = c->serve;
+    if (!st) return;
+    {
+        std::lock_guard<std::mutex> lk(st->mu);
+        st->stopping = true;
+    }
+    st->cv.notify_all();
+    if (st->thread.joinable()) st->thread.join();
+    {
+        std::lock_guard<std::recursive_mutex> g(c->mu);
+        for (auto& L : st->lanes) {
+            if (L->stream) cudaStreamSynchronize(L->stream);
+            scratch_free(c, L->S);
+            if (L->stream) cudaStreamDestroy(L->stream);
+        }
+    }
+    c->serve = nullptr;
+    delete st;
+}
+
+}  // namespace fvv
+
+using fvv::ReqState;
+using fvv::ServeState;
+using fvv::fail;
+
+extern "C" {
+
+fvv_status fvv_serve_default_cfg(fvv_serve_cfg* cfg)
+{
+    if (!cfg) return fail(FVV_ERR_INVALID_ARG, "cfg is NULL");
+    cfg->lanes = 3;
+    cfg->max_batch = 16;
+    cfg->max_pending = 4096;
+    cfg->memory_budget = uint64_t(768) << 20;
+    return FVV_OK;
+}
+
+fvv_status fvv_serve_start(fvv_ctx* c, const fvv_serve_cfg* cfg_in)
+{
+    if (!c) return fail(FVV_ERR_INVALID_ARG, "ctx is NULL");
+    fvv_serve_cfg cfg;
+    if (cfg_in) cfg = *cfg_in; else fvv_serve_default_cfg(&cfg);
+    if (cfg.lanes < 1 || cfg.lanes > fvv::kMaxReaders - 1)
+        return fail(FVV_ERR_INVALID_ARG, "lanes must be in [1, 16]");
+    if (cfg.max_batch < 1 || cfg.max_batch > 4096 || cfg.max_pending < 1)
+        return fail(FVV_ERR_INVALID_ARG, "max_batch must be in [1, 4096], max_pending >= 1");
+    if (c->serve) return fail(FVV_ERR_STATE, "serving loop already running");
+    std::lock_guard<std::recursive_mutex> g(c->mu);
+    FVV_CUDA(cudaSetDevice(c->device));
+    auto st = std::make_unique<ServeState>();
+    st->ctx = c;
+    st->cfg = cfg;
+    // per lane: 8 bytes of keys and 3 bytes of host-output staging per pixel
+    const size_t per_lane = size_t(cfg.memory_budget) / size_t(cfg.lanes);
+    const size_t pb = fvv::align_up(size_t(cfg.max_batch) * sizeof(fvv::ViewDesc), 256) +
+                      size_t(cfg.max_batch) * c->n_cams * sizeof(fvv::CamGeom);
+    if (per_lane < 2 * pb + (size_t(1) << 20))
+        return fail(FVV_ERR_BUDGET, "memory_budget too small for the lanes");
+    const size_t room = per_lane - 2 * pb;
+    st->lane_keys = fvv::align_up(room / 11, 16) - 16;
+    st->lane_stage = fvv::align_up((room - st->lane_keys * 8) & ~size_t(255), 256) - 256;
+    for (int i = 0; i < cfg.lanes; ++i) {
+        auto L = std::make_unique<fvv::ServeLane>();
+        L->owner = st.get();
+        L->index = i;
+        cudaError_t e = cudaStreamCreateWithFlags(&L->stream, cudaStreamNonBlocking);
+        fvv_status rc = e == cudaSuccess ? FVV_OK : FVV_ERR_CUDA;
+        if (rc == FVV_OK)
+            rc = fvv::scratch_alloc(c, L->S, st->lane_keys, st->lane_stage, cfg.max_batch, 2);
+        L->S.reader = 1 + i;
+        st->lanes.push_back(std::move(L));
+        if (rc != FVV_OK) {
+            std::string msg = e != cudaSuccess ? std::string("cudaStreamCreate: ") + cudaGetErrorString(e)
+                                               : std::string(fvv_last_error());
+            for (auto& l : st->lanes) {
+                fvv::scratch_free(c, l->S);
+                if (l->stream) cudaStreamDestroy(l->stream);
+            }
+            return fail(rc, msg);
+        }
+    }
+    ServeState* raw = st.release();
+    c->serve = raw;
+    raw->thread = std::thread(fvv::scheduler, raw);
+    return FVV_OK;
+}
+
+fvv_status fvv_serve_submit(fvv_ctx* c, uint32_t viewer, const fvv_view* view, uint8_t* out,
+                            size_t pitch, uint64_t* ticket)
+{
+    if (!c || !view || !out || !ticket) return fail(FVV_ERR_INVALID_ARG, "NULL argument");
+    ServeState* st = c->serve;
+    if (!st) return fail(FVV_ERR_STATE, "serving loop not running");
+    std::string why;
+    if (!fvv::camera_ok(*view, &why)) return fail(FVV_ERR_INVALID_ARG, "view: " + why);
+    if (fvv::resolve_smem_bytes(view->width, c->n_cams) > c->smem_optin)
+        return fail(FVV_ERR_INVALID_ARG, "view: width too large");
+    if (pitch < size_t(view->width) * 3) return fail(FVV_ERR_INVALID_ARG, "pitch < 3 * width");
+    if (fvv::view_keys(*view) > st->lane_keys ||
+        fvv::view_stage_bytes(*view, out, nullptr) > st->lane_stage)
+        return fail(FVV_ERR_BUDGET, "view does not fit one lane's share of the serving memory budget");
+    {
+        std::lock_guard<std::recursive_mutex> g(c->mu);
+        if (!c->have_latest) return fail(FVV_ERR_NOT_READY, "no complete frame tick uploaded yet");
+    }
+    {
+        std::lock_guard<std::mutex> lk(st->mu);
+        if (st->stopping) return fail(FVV_ERR_STATE, "serving loop is stopping");
+        if (st->recs.size() >= size_t(st->cfg.max_pending))
+            return fail(FVV_ERR_BUSY, "max_pending requests outstanding; poll some first");
+        const uint64_t t = st->next_ticket++;
+        fvv::Rec r;
+        r.t_submit = fvv::now_s();
+        st->recs.emplace(t, r);
+        st->queue.push_back(fvv::Req{t, viewer, *view, out, pitch});
+        ++st->submitted;
+        if (st->t_first < 0.0) st->t_first = r.t_submit;
+        *ticket = t;
+    }
+    st->cv.notify_all();
+    return FVV_OK;
+}
+
+fvv_status fvv_serve_poll(fvv_ctx* c, uint64_t ticket, int64_t timeout_us)
+{
+    if (!c) return fail(FVV_ERR_INVALID_ARG, "ctx is NULL");
+    ServeState* st = c->serve;
+    if (!st) return fail(FVV_ERR_STATE, "serving loop not running");
+    std::unique_lock<std::mutex> lk(st->mu);
+    auto it = st->recs.find(ticket);
+    if (it == st->recs.end()) return fail(FVV_ERR_INVALID_ARG, "unknown or already collected ticket");
+    auto finished = [&] {
+        auto i = st->recs.find(ticket);
+        return i->second.state == ReqState::Done || i->second.state == ReqState::Failed;
+    };
+    if (!finished()) {
+        if (timeout_us == 0) return fail(FVV_ERR_NOT_READY, "request not finished");
+        if (timeout_us < 0)
+            st->cv.wait(lk, finished);
+        else if (!st->cv.wait_for(lk, std::chrono::microseconds(timeout_us), finished))
+            return fail(FVV_ERR_TIMEOUT, "request not finished within the timeout");
+    }
+    it = st->recs.find(ticket);
+    const bool ok = it->second.state == ReqState::Done;
+    st->recs.erase(it);
+    if (!ok) return fail(FVV_ERR_CUDA, "request failed: " + st->error);
+    return FVV_OK;
+}
+
+fvv_status fvv_serve_stats(fvv_ctx* c, fvv_serve_report* out, int32_t reset)
+{
+    if (!c || !out) return fail(FVV_ERR_INVALID_ARG, "NULL argument");
+    ServeState* st = c->serve;
+    if (!st) return fail(FVV_ERR_STATE, "serving loop not running");
+    std::lock_guard<std::mutex> lk(st->mu);
+    std::memset(out, 0, sizeof *out);
+    out->submitted = st->submitted;
+    out->completed = st->completed;
+    out->failed = st->failed;
+    out->batches = st->batches;
+    out->mean_batch = st->batches ? double(st->batch_views) / double(st->batches) : 0.0;
+    int running = 0;
+    for (auto& kv : st->recs)
+        if (kv.second.state == ReqState::Queued || kv.second.state == ReqState::Running) ++running;
+    out->in_flight = running;
+    if (!st->lat_ms.empty()) {
+        std::vector<double> v = st->lat_ms;
+        std::sort(v.begin(), v.end());
+        auto pct = [&](double q) {
+            const size_t i = size_t(std::ceil(q * double(v.size()))) - 1;
+            return v[std::min(i, v.size() - 1)];
+        };
+        out->p50_ms = pct(0.50);
+        out->p99_ms = pct(0.99);
+        out->max_ms = v.back();
+    }
+    if (st->completed && st->t_last > st->t_first)
+        out->views_per_s = double(st->completed) / (st->t_last - st->t_first);
+    if (reset) {
+        st->submitted = st->completed = st->failed = st->batches = st->batch_views = 0;
+        st->lat_ms.clear();
+        st->t_first = st->t_last = -1.0;
+    }
+    return FVV_OK;
+}
+
+fvv_status fvv_serve_stop(fvv_ctx* c)
+{
+    if (!c) return fail(FVV_ERR_INVALID_ARG, "ctx is NULL");
+    if (!c->serve) return fail(FVV_ERR_STATE, "serving loop not running");
+    fvv::serve_shutdown(c);
+    return FVV_OK;
+}
+
+}  // extern "C"

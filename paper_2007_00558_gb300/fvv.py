@@ -67,6 +67,18 @@ class fvv_aux(C.Structure):
                 ("keys", C.c_void_p), ("keys_raw", C.c_void_p)]
 
 
+class fvv_serve_cfg(C.Structure):
+    _fields_ = [("lanes", C.c_int32), ("max_batch", C.c_int32), ("max_pending", C.c_int32),
+                ("memory_budget", C.c_uint64)]
+
+
+class fvv_serve_report(C.Structure):
+    _fields_ = [("submitted", C.c_uint64), ("completed", C.c_uint64), ("failed", C.c_uint64),
+                ("batches", C.c_uint64), ("mean_batch", C.c_double), ("p50_ms", C.c_double),
+                ("p99_ms", C.c_double), ("max_ms", C.c_double), ("views_per_s", C.c_double),
+                ("in_flight", C.c_int32)]
+
+
 class fvv_kernel_stats(C.Structure):
     _fields_ = [("name", C.c_char * 32), ("launches", C.c_uint64), ("timed", C.c_uint64),
                 ("total_ms", C.c_double)]
@@ -108,6 +120,12 @@ def load() -> C.CDLL:
             "fvv_synthesize_noalloc": [C.POINTER(fvv_rig), C.POINTER(fvv_options), C.POINTER(P),
                                        C.POINTER(S), C.POINTER(P), C.POINTER(S),
                                        C.POINTER(fvv_camera), P, S, P],
+            "fvv_serve_default_cfg": [C.POINTER(fvv_serve_cfg)],
+            "fvv_serve_start": [P, C.POINTER(fvv_serve_cfg)],
+            "fvv_serve_submit": [P, C.c_uint32, C.POINTER(fvv_camera), P, S, C.POINTER(U64)],
+            "fvv_serve_poll": [P, U64, C.c_int64],
+            "fvv_serve_stats": [P, C.POINTER(fvv_serve_report), I],
+            "fvv_serve_stop": [P],
             "fvv_profile_enable": [P, I],
             "fvv_profile_read": [P, C.POINTER(fvv_kernel_stats), C.POINTER(I), I],
         }
@@ -288,3 +306,39 @@ def fvv_synthesize_noalloc(rig_: fvv_rig, opt: Optional[fvv_options], depth: Seq
     _check(load().fvv_synthesize_noalloc(C.byref(rig_), C.byref(opt) if opt is not None else None,
                                          dp, ds, rp, rs, C.byref(v), ptr(out_rgb), out_pitch,
                                          stream_handle(stream)), "fvv_synthesize_noalloc")
+
+
+def fvv_serve_default_cfg(**overrides) -> fvv_serve_cfg:
+    cfg = fvv_serve_cfg()
+    _check(load().fvv_serve_default_cfg(C.byref(cfg)), "fvv_serve_default_cfg")
+    for k, v in overrides.items():
+        if not hasattr(cfg, k):
+            raise AttributeError(k)
+        setattr(cfg, k, v)
+    return cfg
+
+
+def fvv_serve_start(ctx: int, cfg: Optional[fvv_serve_cfg] = None) -> None:
+    _check(load().fvv_serve_start(ctx, C.byref(cfg) if cfg is not None else None), "fvv_serve_start")
+
+
+def fvv_serve_submit(ctx: int, viewer: int, view, out, pitch: int) -> int:
+    v = view if isinstance(view, fvv_camera) else camera(view)
+    t = C.c_uint64()
+    _check(load().fvv_serve_submit(ctx, viewer, C.byref(v), ptr(out), pitch, C.byref(t)),
+           "fvv_serve_submit")
+    return t.value
+
+
+def fvv_serve_poll(ctx: int, ticket: int, timeout_us: int = -1) -> None:
+    _check(load().fvv_serve_poll(ctx, ticket, timeout_us), "fvv_serve_poll")
+
+
+def fvv_serve_stats(ctx: int, reset: bool = False) -> dict:
+    r = fvv_serve_report()
+    _check(load().fvv_serve_stats(ctx, C.byref(r), 1 if reset else 0), "fvv_serve_stats")
+    return {f: getattr(r, f) for f, _ in fvv_serve_report._fields_}
+
+
+def fvv_serve_stop(ctx: int) -> None:
+    _check(load().fvv_serve_stop(ctx), "fvv_serve_stop")
