@@ -1,0 +1,128 @@
+"""Pins of the FP64 refinement-network oracle (oracle/unet.py): forward
+against an independent library routine and hand cases, backward against
+finite differences and adjoint identities."""
+import numpy as np
+import pytest
+
+from oracle import unet as U
+
+scipy_signal = pytest.importorskip("scipy.signal")
+
+
+def test_conv3x3_matches_scipy_correlate():
+    rng = np.random.default_rng(0)
+    x = rng.standard_normal((2, 6, 5, 3))
+    w = rng.standard_normal((4, 3, 3, 3))
+    b = rng.standard_normal(4)
+    y = U.conv3x3(x, w, b)
+    for n in range(2):
+        xp = np.pad(x[n], ((1, 1), (1, 1), (0, 0)))
+        for co in range(4):
+            ref = sum(scipy_signal.correlate2d(xp[..., ci], w[co, :, :, ci], mode="valid")
+                      for ci in range(3)) + b[co]
+            assert np.allclose(y[n, ..., co], ref, rtol=1e-12, atol=1e-12)
+
+
+def test_conv1x1_is_channel_matmul():
+    rng = np.random.default_rng(1)
+    x = rng.standard_normal((1, 3, 4, 5))
+    w = rng.standard_normal((2, 5))
+    b = rng.standard_normal(2)
+    y = U.conv1x1(x, w, b)
+    for i in range(3):
+        for j in range(4):
+            assert np.allclose(y[0, i, j], w @ x[0, i, j] + b)
+
+
+def _fd(f, arr, idx, eps=1e-6):
+    old = arr[idx]
+    arr[idx] = old + eps
+    fp = f()
+    arr[idx] = old - eps
+    fm = f()
+    arr[idx] = old
+    return (fp - fm) / (2 * eps)
+
+
+def test_conv3x3_backward_finite_differences_and_adjoint():
+    rng = np.random.default_rng(2)
+    x = rng.standard_normal((1, 5, 4, 3))
+    w = rng.standard_normal((2, 3, 3, 3))
+    b = rng.standard_normal(2)
+    r = rng.standard_normal((1, 5, 4, 2))
+    f = lambda: float(np.sum(U.conv3x3(x, w, b) * r))
+    dx, dw, db = U.conv3x3_backward(x, w, r)
+    for idx in [(0, 0, 0, 0), (0, 4, 3, 2), (0, 2, 1, 1), (0, 0, 3, 1)]:
+        assert abs(_fd(f, x, idx) - dx[idx]) < 1e-7
+    for idx in [(0, 0, 0, 0), (1, 2, 2, 2), (1, 1, 0, 1)]:
+        assert abs(_fd(f, w, idx) - dw[idx]) < 1e-7
+    assert abs(_fd(f, b, (1,)) - db[1]) < 1e-7
+    # adjoint: <conv(x), r> = <x, conv^T(r)> with zero bias
+    y0 = U.conv3x3(x, w, np.zeros(2))
+    assert np.isclose(np.sum(y0 * r), np.sum(x * dx))
+
+
+def test_maxpool_and_upsample():
+    x = np.array([[1, 5, 2, 2], [3, 4, 2, 1], [0, 0, 7, 8], [0, 9, 6, 8]], float)[None, :, :, None]
+    y, arg = U.maxpool2(x)
+    assert y[0, :, :, 0].tolist() == [[5, 2], [9, 8]]
+    # ties (2, 2 in the top-right block; 8, 8 bottom-right): first in scan order
+    assert arg[0, :, :, 0].tolist() == [[1, 0], [3, 1]]
+    d = U.maxpool2_backward(arg, np.array([[10, 20], [30, 40]], float)[None, :, :, None])
+    assert d[0, :, :, 0].tolist() == [[0, 10, 20, 0], [0, 0, 0, 0], [0, 0, 0, 40], [0, 30, 0, 0]]
+    u = U.up2(np.arange(4.0).reshape(1, 2, 2, 1))
+    assert u[0, :, :, 0].tolist() == [[0, 0, 1, 1], [0, 0, 1, 1], [2, 2, 3, 3], [2, 2, 3, 3]]
+    rng = np.random.default_rng(3)
+    a, r = rng.standard_normal((1, 3, 2, 4)), rng.standard_normal((1, 6, 4, 4))
+    assert np.isclose(np.sum(U.up2(a) * r), np.sum(a * U.up2_backward(r)))
+
+
+def test_network_gradient_finite_differences():
+    rng = np.random.default_rng(4)
+    p = U.init_params(widths=(3, 4, 5), seed=5, out_scale=0.1)
+    for k in p:
+        if k.endswith(".b"):
+            p[k] = rng.standard_normal(p[k].shape) * 0.1
+    x = rng.standard_normal((2, 8, 8, 8))
+    rgb = 0.5 + 0.05 * rng.standard_normal((2, 8, 8, 3))
+    target = rng.uniform(0.3, 0.7, (2, 8, 8, 3))
+
+    def loss():
+        pred, _ = U.forward(p, x, rgb)
+        return U.mse(pred, target)[0]
+
+    pred, cache = U.forward(p, x, rgb)
+    assert np.all((cache["s"] > 0) & (cache["s"] < 1))
+    _, dpred = U.mse(pred, target)
+    g = U.backward(p, cache, dpred)
+    checked = 0
+    for k in p:
+        flat = p[k].reshape(-1)
+        for j in rng.choice(flat.size, min(3, flat.size), replace=False):
+            idx = np.unravel_index(j, p[k].shape)
+            num = _fd(loss, p[k], idx, eps=1e-6)
+            assert abs(num - g[k][idx]) <= 1e-6 * max(1e-3, abs(num)) + 1e-9, (k, idx, num, g[k][idx])
+            checked += 1
+    assert checked >= 50
+
+
+def test_clamp_blocks_gradient_and_zero_net_is_identity():
+    p = U.init_params(widths=(2, 2, 2), seed=1)
+    for k in p:
+        p[k] = np.zeros_like(p[k])
+    rgb = np.linspace(-0.2, 1.2, 2 * 4 * 4 * 3).reshape(2, 4, 4, 3)
+    x = np.zeros((2, 4, 4, 8))
+    pred, cache = U.forward(p, x, rgb)
+    assert np.allclose(pred, np.clip(rgb, 0, 1))
+    g = U.backward(p, cache, np.ones_like(pred))
+    inside = ((rgb > 0) & (rgb < 1)).sum(axis=(0, 1, 2))
+    assert np.allclose(g["out.b"], inside)
+
+
+def test_adam_single_step_closed_form():
+    p = {"a": np.array([1.0, -2.0])}
+    g = {"a": np.array([0.5, -0.25])}
+    st = {}
+    U.adam_step(p, g, st, lr=0.1)
+    # first bias-corrected step moves by lr * g / (|g| + eps) = lr * sign(g)
+    assert np.allclose(p["a"], [1.0 - 0.1, -2.0 + 0.1], atol=1e-6)
