@@ -241,6 +241,24 @@ fvv_status fvv_profile_enable(fvv_ctx* ctx, int32_t on);
  * waits for the recorded events.  reset = 1 clears the statistics. */
 fvv_status fvv_profile_read(fvv_ctx* ctx, fvv_kernel_stats* out, int32_t* n, int32_t reset);
 
+/* ---- refinement network: layer operations -------------------------------
+ * The learned refinement (a U-Net; the paper has none) runs on the sm_103a
+ * tensor cores.  Its layers are exposed for tests and custom pipelines.
+ * Tensors are device memory, NHWC, bf16 unless stated. */
+
+/* y = relu?(conv3x3(x, w) + bias), pad 1, stride 1, then optionally zeroed
+ * where mask <= 0 (the ReLU derivative of a previous layer, for backward
+ * passes).  Implicit GEMM on tcgen05 with fp32 accumulation in TMEM.
+ *   x: [n][h][w][cin], cin a multiple of 32
+ *   wt: [cout][3][3][cin]; bias: float [cout] or NULL
+ *   cout: 32, 64, 96, 128 or 192; mask: [n][h][w][cout] or NULL
+ *   y: [n][h][w][cout]
+ * Waits for completion on `stream`.  Errors: INVALID_ARG, TIMEOUT (a bounded
+ * wait inside the kernel ran out), CUDA. */
+fvv_status fvv_unet_conv3x3(const void* x, int32_t n, int32_t h, int32_t w, int32_t cin,
+                            const void* wt, const float* bias, int32_t cout, int32_t relu,
+                            const void* mask, void* y, void* stream);
+
 /* ---- allocation-free variant ------------------------------------------- */
 
 /* Largest view (width * height) fvv_synthesize_noalloc accepts. */

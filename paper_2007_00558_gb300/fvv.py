@@ -126,6 +126,7 @@ def load() -> C.CDLL:
             "fvv_serve_poll": [P, U64, C.c_int64],
             "fvv_serve_stats": [P, C.POINTER(fvv_serve_report), I],
             "fvv_serve_stop": [P],
+            "fvv_unet_conv3x3": [P, I, I, I, I, P, P, I, I, P, P, P],
             "fvv_profile_enable": [P, I],
             "fvv_profile_read": [P, C.POINTER(fvv_kernel_stats), C.POINTER(I), I],
         }
@@ -342,3 +343,9 @@ def fvv_serve_stats(ctx: int, reset: bool = False) -> dict:
 
 def fvv_serve_stop(ctx: int) -> None:
     _check(load().fvv_serve_stop(ctx), "fvv_serve_stop")
+
+
+def fvv_unet_conv3x3(x, n: int, h: int, w: int, cin: int, wt, bias, cout: int, relu: bool, mask, y,
+                     stream=None) -> None:
+    _check(load().fvv_unet_conv3x3(ptr(x), n, h, w, cin, ptr(wt), ptr(bias), cout, 1 if relu else 0,
+                                   ptr(mask), ptr(y), stream_handle(stream)), "fvv_unet_conv3x3")
