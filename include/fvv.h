@@ -259,6 +259,64 @@ fvv_status fvv_unet_conv3x3(const void* x, int32_t n, int32_t h, int32_t w, int3
                             const void* wt, const float* bias, int32_t cout, int32_t relu,
                             const void* mask, void* y, void* stream);
 
+/* ---- refinement network ---------------------------------------------------
+ * A 3-level U-Net refines a plain synthesis (the paper has none; it leaves
+ * disocclusions black, Sec. IX).  Input: the blended RGB / 255, depth / z_far,
+ * the hole mask and the three largest blend weights; output: clamp(RGB +
+ * residual, 0, 1).  3x3 convolutions (pad 1) + ReLU at widths w1/w2/w3, 2x2
+ * max pooling, nearest 2x upsampling with channel-concatenated skips, a 1x1
+ * head; trained with mean-squared error against a held-out camera and Adam.
+ * The 3x3 convolutions and their input gradients run on the tcgen05 tensor
+ * cores (bf16 operands, fp32 accumulation); master weights are fp32. */
+typedef struct fvv_unet_cfg {
+    int32_t widths[3];          /* default 32, 64, 128 (multiples of 32) */
+    uint64_t seed;              /* weight initialisation */
+    float z_far;                /* depth normalisation (depth units), default 8000 */
+} fvv_unet_cfg;
+
+/* One batch of plain-synthesis outputs (device memory, dense). */
+typedef struct fvv_refine_batch {
+    int32_t n, height, width;   /* height and width multiples of 4 */
+    const uint8_t* rgb;         /* [n][h][w][3] blended colour */
+    const float* depth;         /* [n][h][w] virtual depth (fvv_aux.depth) */
+    const uint8_t* hole;        /* [n][h][w] hole mask (fvv_aux.hole) */
+    const float* top3;          /* [n][h][w][3] top-3 blend weights (fvv_aux.top3) */
+    const uint8_t* target;      /* [n][h][w][3] held-out camera colour (training only) */
+} fvv_refine_batch;
+
+/* Buffers addressable by fvv_refine_get / fvv_refine_set, each a flat fp32
+ * vector of fvv_refine_param_count entries: per 3x3 layer (e1a, e1b, e2a,
+ * e2b, ba, bb, d2a, d2b, d1a, d1b) W[cout][3][3][cin] then b[cout], then the
+ * head W[3][w1] and b[3]. */
+#define FVV_REFINE_PARAMS 0
+#define FVV_REFINE_GRADS  1
+#define FVV_REFINE_ADAM_M 2
+#define FVV_REFINE_ADAM_V 3
+
+fvv_status fvv_refine_default_cfg(fvv_unet_cfg* cfg);
+/* (Re)create the network of `ctx` with fresh weights. */
+fvv_status fvv_refine_init(fvv_ctx* ctx, const fvv_unet_cfg* cfg);
+fvv_status fvv_refine_param_count(fvv_ctx* ctx, uint64_t* n);
+/* Copy a buffer to / from host memory (waits for the device). */
+fvv_status fvv_refine_get(fvv_ctx* ctx, int32_t which, float* out);
+fvv_status fvv_refine_set(fvv_ctx* ctx, int32_t which, const float* in);
+/* Forward pass: out_rgb [n][h][w][3] uint8 and/or out_f32 (clamped
+ * prediction in [0, 1]); device memory, either may be NULL.  Waits. */
+fvv_status fvv_refine_forward(fvv_ctx* ctx, const fvv_refine_batch* batch, uint8_t* out_rgb,
+                              float* out_f32, void* stream);
+/* Forward, backward and (lr > 0) one Adam step; *loss = mean squared error
+ * of the batch before the update.  lr = 0 leaves the gradients readable with
+ * FVV_REFINE_GRADS and changes nothing else.  Waits. */
+fvv_status fvv_refine_train_step(fvv_ctx* ctx, const fvv_refine_batch* batch, float lr, float* loss,
+                                 void* stream);
+/* Checkpoint: widths, step, z_far, weights and Adam moments. */
+fvv_status fvv_refine_save(fvv_ctx* ctx, const char* path);
+fvv_status fvv_refine_load(fvv_ctx* ctx, const char* path);
+/* Plain synthesis of `view` from the newest complete tick, then the
+ * network; out_rgb device or host.  Width and height multiples of 4. */
+fvv_status fvv_synthesize_refined(fvv_ctx* ctx, const fvv_view* view, uint8_t* out_rgb,
+                                  size_t out_pitch, void* stream);
+
 /* ---- allocation-free variant ------------------------------------------- */
 
 /* Largest view (width * height) fvv_synthesize_noalloc accepts. */

@@ -651,6 +651,7 @@ fvv_status fvv_destroy(fvv_ctx* c)
 {
     if (!c) return FVV_OK;
     fvv::serve_shutdown(c);
+    fvv::refine_destroy(c);
     int cur = 0;
     cudaGetDevice(&cur);
     cudaSetDevice(c->device);

@@ -1,6 +1,24 @@
-// fvv_refine.cu -- C ABI of the refinement network's layer operations.
+// fvv_refine.cu -- the learned refinement of synthesised views: a 3-level
+// U-Net trained and run with the library's own kernels (the 3x3
+// convolutions and their input gradients on the tcgen05 tensor cores, the
+// rest on CUDA cores).  The paper has no learned stage; the network refines
+// the plain synthesis (blended RGB, depth, hole mask, top-3 blend weights)
+// into a residual added to the blended colour.
+//
+// Network (widths w1/w2/w3): e1 = conv(conv(x)) [w1]; e2 = conv(conv(pool e1))
+// [w2]; bt = conv(conv(pool e2)) [w3]; d2 = conv(conv([up bt | e2])) [w2];
+// d1 = conv(conv([up d2 | e1])) [w1]; out = clamp(rgb + W d1 + b, 0, 1).
+// 3x3 convolutions with pad 1 and ReLU; 2x2 max pooling; nearest 2x
+// upsampling; mean-squared error against the held-out camera; Adam.
+// Master weights, gradients and Adam moments are fp32; activations and
+// activation gradients are bf16 (NHWC); GEMM accumulation is fp32.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
 #include <mutex>
+#include <random>
 #include <string>
+#include <vector>
 
 #include "fvv_runtime.h"
 #include "fvv_unet.h"
@@ -43,11 +61,333 @@ fvv_status check_flag(int* flag, cudaStream_t s, const char* what)
 
 bool on_device(const void* p) { return p && mem_kind(p) == MemKind::Device; }
 
+int round32(int c) { return (c + 31) / 32 * 32; }
+
 }  // namespace
+
+struct ConvLayer {
+    int cin_true = 0, cin = 0, cout = 0;
+    float *w = nullptr, *b = nullptr, *gw = nullptr, *gb = nullptr;
+    float *mw = nullptr, *vw = nullptr, *mb = nullptr, *vb = nullptr;
+    __nv_bfloat16 *wbf = nullptr, *wt = nullptr;
+    size_t nw() const { return size_t(cout) * 9 * cin; }
+};
+
+struct RefineNet {
+    int w1 = 32, w2 = 64, w3 = 128;
+    float z_far = 8000.0f;
+    ConvLayer L[10];
+    float *wout = nullptr, *bout = nullptr, *gwout = nullptr, *gbout = nullptr;
+    float *mwo = nullptr, *vwo = nullptr, *mbo = nullptr, *vbo = nullptr;
+    int step = 0;
+    std::vector<std::pair<void*, size_t>> params;     // device allocations of parameters
+    int B = 0, H = 0, W = 0;
+    std::vector<std::pair<void*, size_t>> acts;       // activations for (B, H, W)
+    __nv_bfloat16 *x0, *e1a, *e1, *p1, *e2a, *e2, *p2, *ba, *bt, *cat2, *d2a, *d2, *cat1, *d1a, *d1;
+    uint8_t *arg1, *arg2;
+    float* s;
+    __nv_bfloat16 *g_d1b, *g_d1a, *g_cat1, *g_skip1, *g_d2b, *g_d2a, *g_cat2, *g_skip2, *g_bb, *g_ba, *g_p2,
+        *g_e2b, *g_e2a, *g_p1, *g_e1b, *g_e1a;
+    float* loss = nullptr;
+    // plain-synthesis outputs feeding fvv_synthesize_refined
+    int sH = 0, sW = 0;
+    std::vector<std::pair<void*, size_t>> syn;
+    uint8_t *syn_rgb = nullptr, *syn_hole = nullptr, *syn_out = nullptr;
+    float *syn_depth = nullptr, *syn_top3 = nullptr;
+};
+
+namespace {
+
+const char* const kLayerName[10] = {"e1a", "e1b", "e2a", "e2b", "ba", "bb", "d2a", "d2b", "d1a", "d1b"};
+
+fvv_status alloc_into(fvv_ctx* c, std::vector<std::pair<void*, size_t>>& list, void** p, size_t bytes)
+{
+    FVV_TRY(dev_alloc(c, p, bytes));
+    list.push_back({*p, bytes});
+    return FVV_OK;
+}
+
+void free_list(fvv_ctx* c, std::vector<std::pair<void*, size_t>>& list)
+{
+    for (auto& a : list) dev_free(c, a.first, a.second);
+    list.clear();
+}
+
+template <class T>
+fvv_status alloc_t(fvv_ctx* c, std::vector<std::pair<void*, size_t>>& list, T** p, size_t n)
+{
+    void* v = nullptr;
+    FVV_TRY(alloc_into(c, list, &v, n * sizeof(T)));
+    *p = static_cast<T*>(v);
+    return FVV_OK;
+}
+
+// parameters in the flat host layout: per 3x3 layer W[cout][3][3][cin_true]
+// then b[cout]; then the head W[3][w1] and b[3]
+size_t flat_count(const RefineNet& N)
+{
+    size_t n = 0;
+    for (const ConvLayer& l : N.L) n += size_t(l.cout) * 9 * l.cin_true + l.cout;
+    return n + 3 * size_t(N.w1) + 3;
+}
+
+enum class Buf { Param, Grad, M, V };
+
+void layer_bufs(ConvLayer& l, Buf b, float** w, float** bias)
+{
+    switch (b) {
+    case Buf::Param: *w = l.w; *bias = l.b; break;
+    case Buf::Grad: *w = l.gw; *bias = l.gb; break;
+    case Buf::M: *w = l.mw; *bias = l.mb; break;
+    case Buf::V: *w = l.vw; *bias = l.vb; break;
+    }
+}
+
+void head_bufs(RefineNet& N, Buf b, float** w, float** bias)
+{
+    switch (b) {
+    case Buf::Param: *w = N.wout; *bias = N.bout; break;
+    case Buf::Grad: *w = N.gwout; *bias = N.gbout; break;
+    case Buf::M: *w = N.mwo; *bias = N.mbo; break;
+    case Buf::V: *w = N.vwo; *bias = N.vbo; break;
+    }
+}
+
+fvv_status get_flat(RefineNet& N, Buf which, float* out)
+{
+    size_t o = 0;
+    std::vector<float> tmp;
+    for (ConvLayer& l : N.L) {
+        float *w, *b;
+        layer_bufs(l, which, &w, &b);
+        tmp.resize(l.nw());
+        FVV_CUDA(cudaMemcpy(tmp.data(), w, l.nw() * 4, cudaMemcpyDeviceToHost));
+        for (int co = 0; co < l.cout; ++co)
+            for (int t = 0; t < 9; ++t)
+                for (int ci = 0; ci < l.cin_true; ++ci)
+                    out[o++] = tmp[(size_t(co) * 9 + t) * l.cin + ci];
+        FVV_CUDA(cudaMemcpy(out + o, b, size_t(l.cout) * 4, cudaMemcpyDeviceToHost));
+        o += l.cout;
+    }
+    float *w, *b;
+    head_bufs(N, which, &w, &b);
+    FVV_CUDA(cudaMemcpy(out + o, w, size_t(3) * N.w1 * 4, cudaMemcpyDeviceToHost));
+    o += 3 * size_t(N.w1);
+    FVV_CUDA(cudaMemcpy(out + o, b, 3 * 4, cudaMemcpyDeviceToHost));
+    return FVV_OK;
+}
+
+fvv_status refresh_weights(RefineNet& N, cudaStream_t s)
+{
+    for (ConvLayer& l : N.L)
+        FVV_CUDA(launch_flip_weights(l.cout, l.cin, l.w, l.wbf, l.wt, s));
+    return FVV_OK;
+}
+
+fvv_status set_flat(RefineNet& N, Buf which, const float* in, cudaStream_t s)
+{
+    size_t o = 0;
+    std::vector<float> tmp;
+    for (ConvLayer& l : N.L) {
+        float *w, *b;
+        layer_bufs(l, which, &w, &b);
+        tmp.assign(l.nw(), 0.0f);
+        for (int co = 0; co < l.cout; ++co)
+            for (int t = 0; t < 9; ++t)
+                for (int ci = 0; ci < l.cin_true; ++ci)
+                    tmp[(size_t(co) * 9 + t) * l.cin + ci] = in[o++];
+        FVV_CUDA(cudaMemcpy(w, tmp.data(), l.nw() * 4, cudaMemcpyHostToDevice));
+        FVV_CUDA(cudaMemcpy(b, in + o, size_t(l.cout) * 4, cudaMemcpyHostToDevice));
+        o += l.cout;
+    }
+    float *w, *b;
+    head_bufs(N, which, &w, &b);
+    FVV_CUDA(cudaMemcpy(w, in + o, size_t(3) * N.w1 * 4, cudaMemcpyHostToDevice));
+    o += 3 * size_t(N.w1);
+    FVV_CUDA(cudaMemcpy(b, in + o, 3 * 4, cudaMemcpyHostToDevice));
+    if (which == Buf::Param) FVV_TRY(refresh_weights(N, s));
+    return FVV_OK;
+}
+
+fvv_status ensure_acts(fvv_ctx* c, RefineNet& N, int B, int H, int W)
+{
+    if (N.B == B && N.H == H && N.W == W) return FVV_OK;
+    FVV_CUDA(cudaDeviceSynchronize());
+    free_list(c, N.acts);
+    N.B = N.H = N.W = 0;
+    const size_t p1 = size_t(B) * H * W, p2 = p1 / 4, p3 = p1 / 16;
+    const int w1 = N.L[1].cout, w2 = N.L[3].cout, w3 = N.L[5].cout;
+    auto A = [&](__nv_bfloat16** p, size_t n) { return alloc_t(c, N.acts, p, n); };
+    FVV_TRY(A(&N.x0, p1 * 32));
+    FVV_TRY(A(&N.e1a, p1 * w1));
+    FVV_TRY(A(&N.e1, p1 * w1));
+    FVV_TRY(A(&N.p1, p2 * w1));
+    FVV_TRY(A(&N.e2a, p2 * w2));
+    FVV_TRY(A(&N.e2, p2 * w2));
+    FVV_TRY(A(&N.p2, p3 * w2));
+    FVV_TRY(A(&N.ba, p3 * w3));
+    FVV_TRY(A(&N.bt, p3 * w3));
+    FVV_TRY(A(&N.cat2, p2 * (w3 + w2)));
+    FVV_TRY(A(&N.d2a, p2 * w2));
+    FVV_TRY(A(&N.d2, p2 * w2));
+    FVV_TRY(A(&N.cat1, p1 * (w2 + w1)));
+    FVV_TRY(A(&N.d1a, p1 * w1));
+    FVV_TRY(A(&N.d1, p1 * w1));
+    FVV_TRY(A(&N.g_d1b, p1 * w1));
+    FVV_TRY(A(&N.g_d1a, p1 * w1));
+    FVV_TRY(A(&N.g_cat1, p1 * (w2 + w1)));
+    FVV_TRY(A(&N.g_skip1, p1 * w1));
+    FVV_TRY(A(&N.g_d2b, p2 * w2));
+    FVV_TRY(A(&N.g_d2a, p2 * w2));
+    FVV_TRY(A(&N.g_cat2, p2 * (w3 + w2)));
+    FVV_TRY(A(&N.g_skip2, p2 * w2));
+    FVV_TRY(A(&N.g_bb, p3 * w3));
+    FVV_TRY(A(&N.g_ba, p3 * w3));
+    FVV_TRY(A(&N.g_p2, p3 * w2));
+    FVV_TRY(A(&N.g_e2b, p2 * w2));
+    FVV_TRY(A(&N.g_e2a, p2 * w2));
+    FVV_TRY(A(&N.g_p1, p2 * w1));
+    FVV_TRY(A(&N.g_e1b, p1 * w1));
+    FVV_TRY(A(&N.g_e1a, p1 * w1));
+    FVV_TRY(alloc_t(c, N.acts, &N.arg1, p2 * w1));
+    FVV_TRY(alloc_t(c, N.acts, &N.arg2, p3 * w2));
+    FVV_TRY(alloc_t(c, N.acts, &N.s, p1 * 3));
+    N.B = B;
+    N.H = H;
+    N.W = W;
+    return FVV_OK;
+}
+
+fvv_status conv(const ConvLayer& l, const __nv_bfloat16* x, int B, int H, int W, __nv_bfloat16* y, int* err,
+                cudaStream_t s)
+{
+    ConvArgs a{};
+    a.bias = l.b;
+    a.y = y;
+    a.relu = 1;
+    a.err = err;
+    FVV_CUDA(launch_conv3x3(x, B, H, W, l.cin, l.wbf, l.cout, a, s));
+    return FVV_OK;
+}
+
+// weight and bias gradients of layer l, and its input gradient (masked)
+fvv_status conv_bwd(const ConvLayer& l, const __nv_bfloat16* x, const __nv_bfloat16* dz, int B, int H, int W,
+                    __nv_bfloat16* dx, const __nv_bfloat16* mask, int* err, cudaStream_t s)
+{
+    FVV_CUDA(launch_wgrad3x3(B, H, W, l.cin, l.cout, x, dz, l.gw, s));
+    FVV_CUDA(launch_bias_grad(size_t(B) * H * W, l.cout, dz, l.gb, s));
+    if (dx) {
+        ConvArgs a{};
+        a.y = dx;
+        a.relu = 0;
+        a.mask = mask;
+        a.err = err;
+        FVV_CUDA(launch_conv3x3(dz, B, H, W, l.cout, l.wt, l.cin, a, s));
+    }
+    return FVV_OK;
+}
+
+fvv_status forward(RefineNet& N, const fvv_refine_batch& b, int* err, cudaStream_t s, uint8_t* out,
+                   size_t out_pitch, float* out_f32)
+{
+    const int B = b.n, H = b.height, W = b.width;
+    const size_t npx = size_t(B) * H * W;
+    const int H2 = H / 2, W2 = W / 2, H4 = H / 4, W4 = W / 4;
+    const int w1 = N.L[1].cout, w2 = N.L[3].cout, w3 = N.L[5].cout;
+    FVV_CUDA(launch_pack_features(npx, b.rgb, b.depth, b.hole, b.top3, N.z_far, N.x0, s));
+    FVV_TRY(conv(N.L[0], N.x0, B, H, W, N.e1a, err, s));
+    FVV_TRY(conv(N.L[1], N.e1a, B, H, W, N.e1, err, s));
+    FVV_CUDA(launch_maxpool2(B, H, W, w1, N.e1, N.p1, N.arg1, s));
+    FVV_TRY(conv(N.L[2], N.p1, B, H2, W2, N.e2a, err, s));
+    FVV_TRY(conv(N.L[3], N.e2a, B, H2, W2, N.e2, err, s));
+    FVV_CUDA(launch_maxpool2(B, H2, W2, w2, N.e2, N.p2, N.arg2, s));
+    FVV_TRY(conv(N.L[4], N.p2, B, H4, W4, N.ba, err, s));
+    FVV_TRY(conv(N.L[5], N.ba, B, H4, W4, N.bt, err, s));
+    FVV_CUDA(launch_up2_concat(B, H2, W2, w3, w2, N.bt, N.e2, N.cat2, s));
+    FVV_TRY(conv(N.L[6], N.cat2, B, H2, W2, N.d2a, err, s));
+    FVV_TRY(conv(N.L[7], N.d2a, B, H2, W2, N.d2, err, s));
+    FVV_CUDA(launch_up2_concat(B, H, W, w2, w1, N.d2, N.e1, N.cat1, s));
+    FVV_TRY(conv(N.L[8], N.cat1, B, H, W, N.d1a, err, s));
+    FVV_TRY(conv(N.L[9], N.d1a, B, H, W, N.d1, err, s));
+    FVV_CUDA(launch_head_fwd(npx, N.d1, N.wout, N.bout, b.rgb, N.s, out, W, out_pitch, out_f32, s));
+    return FVV_OK;
+}
+
+fvv_status backward(RefineNet& N, const fvv_refine_batch& b, int* err, cudaStream_t s)
+{
+    const int B = b.n, H = b.height, W = b.width;
+    const size_t npx = size_t(B) * H * W;
+    const int H2 = H / 2, W2 = W / 2, H4 = H / 4, W4 = W / 4;
+    const int w1 = N.L[1].cout, w2 = N.L[3].cout, w3 = N.L[5].cout;
+    for (ConvLayer& l : N.L) {
+        FVV_CUDA(cudaMemsetAsync(l.gw, 0, l.nw() * 4, s));
+        FVV_CUDA(cudaMemsetAsync(l.gb, 0, size_t(l.cout) * 4, s));
+    }
+    FVV_CUDA(cudaMemsetAsync(N.gwout, 0, size_t(3) * N.w1 * 4, s));
+    FVV_CUDA(cudaMemsetAsync(N.gbout, 0, 3 * 4, s));
+    FVV_CUDA(cudaMemsetAsync(N.loss, 0, 4, s));
+    FVV_CUDA(launch_head_bwd(npx, N.d1, N.wout, N.s, b.target, N.loss, N.gwout, N.gbout, N.g_d1b, s));
+    FVV_TRY(conv_bwd(N.L[9], N.d1a, N.g_d1b, B, H, W, N.g_d1a, N.d1a, err, s));
+    FVV_TRY(conv_bwd(N.L[8], N.cat1, N.g_d1a, B, H, W, N.g_cat1, nullptr, err, s));
+    FVV_CUDA(launch_up2_concat_bwd(B, H, W, w2, w1, N.g_cat1, N.d2, N.g_d2b, N.g_skip1, s));
+    FVV_TRY(conv_bwd(N.L[7], N.d2a, N.g_d2b, B, H2, W2, N.g_d2a, N.d2a, err, s));
+    FVV_TRY(conv_bwd(N.L[6], N.cat2, N.g_d2a, B, H2, W2, N.g_cat2, nullptr, err, s));
+    FVV_CUDA(launch_up2_concat_bwd(B, H2, W2, w3, w2, N.g_cat2, N.bt, N.g_bb, N.g_skip2, s));
+    FVV_TRY(conv_bwd(N.L[5], N.ba, N.g_bb, B, H4, W4, N.g_ba, N.ba, err, s));
+    FVV_TRY(conv_bwd(N.L[4], N.p2, N.g_ba, B, H4, W4, N.g_p2, nullptr, err, s));
+    FVV_CUDA(launch_maxpool2_bwd(B, H2, W2, w2, N.g_p2, N.arg2, N.g_skip2, N.e2, N.g_e2b, s));
+    FVV_TRY(conv_bwd(N.L[3], N.e2a, N.g_e2b, B, H2, W2, N.g_e2a, N.e2a, err, s));
+    FVV_TRY(conv_bwd(N.L[2], N.p1, N.g_e2a, B, H2, W2, N.g_p1, nullptr, err, s));
+    FVV_CUDA(launch_maxpool2_bwd(B, H, W, w1, N.g_p1, N.arg1, N.g_skip1, N.e1, N.g_e1b, s));
+    FVV_TRY(conv_bwd(N.L[1], N.e1a, N.g_e1b, B, H, W, N.g_e1a, N.e1a, err, s));
+    FVV_TRY(conv_bwd(N.L[0], N.x0, N.g_e1a, B, H, W, nullptr, nullptr, err, s));
+    return FVV_OK;
+}
+
+fvv_status adam(RefineNet& N, float lr, cudaStream_t s)
+{
+    const int t = ++N.step;
+    for (ConvLayer& l : N.L) {
+        FVV_CUDA(launch_adam(l.nw(), l.w, l.gw, l.mw, l.vw, lr, t, s));
+        FVV_CUDA(launch_adam(size_t(l.cout), l.b, l.gb, l.mb, l.vb, lr, t, s));
+    }
+    FVV_CUDA(launch_adam(size_t(3) * N.w1, N.wout, N.gwout, N.mwo, N.vwo, lr, t, s));
+    FVV_CUDA(launch_adam(3, N.bout, N.gbout, N.mbo, N.vbo, lr, t, s));
+    return refresh_weights(N, s);
+}
+
+fvv_status check_batch(const RefineNet& N, const fvv_refine_batch* b, bool need_target)
+{
+    if (!b) return fail(FVV_ERR_INVALID_ARG, "batch is NULL");
+    if (b->n < 1 || b->height < 4 || b->width < 4 || b->height % 4 || b->width % 4)
+        return fail(FVV_ERR_INVALID_ARG, "batch size >= 1, height and width multiples of 4");
+    if (!on_device(b->rgb) || !on_device(b->depth) || !on_device(b->hole) || !on_device(b->top3))
+        return fail(FVV_ERR_INVALID_ARG, "batch inputs must be device memory");
+    if (need_target && !on_device(b->target)) return fail(FVV_ERR_INVALID_ARG, "target must be device memory");
+    (void)N;
+    return FVV_OK;
+}
+
+RefineNet* net_of(fvv_ctx* c) { return c ? c->refine : nullptr; }
+
+}  // namespace
+
+void refine_destroy(fvv_ctx* c)
+{
+    RefineNet* N = c->refine;
+    if (!N) return;
+    cudaDeviceSynchronize();
+    free_list(c, N->acts);
+    free_list(c, N->syn);
+    free_list(c, N->params);
+    delete N;
+    c->refine = nullptr;
+}
 
 }  // namespace fvv
 
 using fvv::fail;
+using fvv::RefineNet;
 
 extern "C" {
 
@@ -76,6 +416,271 @@ fvv_status fvv_unet_conv3x3(const void* x, int32_t n, int32_t h, int32_t w, int3
     a.err = flag;
     FVV_CUDA(fvv::launch_conv3x3(x, n, h, w, cin, wt, cout, a, s));
     return fvv::check_flag(flag, s, "fvv_unet_conv3x3");
+}
+
+fvv_status fvv_refine_default_cfg(fvv_unet_cfg* cfg)
+{
+    if (!cfg) return fail(FVV_ERR_INVALID_ARG, "cfg is NULL");
+    cfg->widths[0] = 32;
+    cfg->widths[1] = 64;
+    cfg->widths[2] = 128;
+    cfg->seed = 0;
+    cfg->z_far = 8000.0f;
+    return FVV_OK;
+}
+
+fvv_status fvv_refine_init(fvv_ctx* c, const fvv_unet_cfg* cfg_in)
+{
+    if (!c) return fail(FVV_ERR_INVALID_ARG, "ctx is NULL");
+    fvv_unet_cfg cfg;
+    if (cfg_in) cfg = *cfg_in; else fvv_refine_default_cfg(&cfg);
+    for (int i = 0; i < 3; ++i)
+        if (cfg.widths[i] < 32 || cfg.widths[i] % 32 || cfg.widths[i] > 128)
+            return fail(FVV_ERR_INVALID_ARG, "widths must be multiples of 32 in [32, 128]");
+    if (!(cfg.z_far > 0.0f)) return fail(FVV_ERR_INVALID_ARG, "z_far must be > 0");
+    {
+        // every input-gradient convolution has N = that layer's input width
+        const int a = cfg.widths[0], b = cfg.widths[1], d = cfg.widths[2];
+        const int dg[9] = {a, a, b, b, d, d + b, b, b + a, a};
+        for (int v : dg)
+            if (!fvv::conv_cout_supported(v))
+                return fail(FVV_ERR_INVALID_ARG, "unsupported widths (layer inputs must be 32, 64, 96, 128 or 192)");
+    }
+    std::lock_guard<std::recursive_mutex> g(c->mu);
+    FVV_CUDA(cudaSetDevice(c->device));
+    fvv::refine_destroy(c);
+    auto* N = new RefineNet();
+    c->refine = N;
+    N->w1 = cfg.widths[0];
+    N->w2 = cfg.widths[1];
+    N->w3 = cfg.widths[2];
+    N->z_far = cfg.z_far;
+    const int w1 = N->w1, w2 = N->w2, w3 = N->w3;
+    const int cins[10] = {8, w1, w1, w2, w2, w3, w3 + w2, w2, w2 + w1, w1};
+    const int couts[10] = {w1, w1, w2, w2, w3, w3, w2, w2, w1, w1};
+    auto P = [&](float** p, size_t n) { return fvv::alloc_t(c, N->params, p, n); };
+    auto PB = [&](__nv_bfloat16** p, size_t n) { return fvv::alloc_t(c, N->params, p, n); };
+    fvv_status rc = FVV_OK;
+    for (int i = 0; i < 10 && rc == FVV_OK; ++i) {
+        fvv::ConvLayer& l = N->L[i];
+        l.cin_true = cins[i];
+        l.cin = fvv::round32(cins[i]);
+        l.cout = couts[i];
+        const size_t nw = l.nw();
+        if ((rc = P(&l.w, nw)) || (rc = P(&l.gw, nw)) || (rc = P(&l.mw, nw)) || (rc = P(&l.vw, nw)) ||
+            (rc = P(&l.b, l.cout)) || (rc = P(&l.gb, l.cout)) || (rc = P(&l.mb, l.cout)) ||
+            (rc = P(&l.vb, l.cout)) || (rc = PB(&l.wbf, nw)) || (rc = PB(&l.wt, nw)))
+            break;
+    }
+    if (rc == FVV_OK) {
+        float** hp[9] = {&N->wout, &N->bout, &N->gwout, &N->gbout, &N->mwo, &N->vwo, &N->mbo, &N->vbo, &N->loss};
+        const size_t hn[9] = {3 * size_t(w1), 3, 3 * size_t(w1), 3, 3 * size_t(w1), 3 * size_t(w1), 3, 3, 1};
+        for (int i = 0; i < 9 && rc == FVV_OK; ++i) rc = P(hp[i], hn[i]);
+    }
+    if (rc != FVV_OK) {
+        std::string msg = fvv_last_error();
+        fvv::refine_destroy(c);
+        return fail(rc, msg);
+    }
+    for (auto& a : N->params) FVV_CUDA(cudaMemset(a.first, 0, a.second));
+    // He-normal 3x3 weights, zero biases, a small head
+    std::mt19937_64 rng(cfg.seed);
+    std::normal_distribution<float> nd(0.0f, 1.0f);
+    std::vector<float> flat(fvv::flat_count(*N));
+    size_t o = 0;
+    for (fvv::ConvLayer& l : N->L) {
+        const float sd = std::sqrt(2.0f / (9.0f * float(l.cin_true)));
+        for (size_t k = 0; k < size_t(l.cout) * 9 * l.cin_true; ++k) flat[o++] = sd * nd(rng);
+        for (int k = 0; k < l.cout; ++k) flat[o++] = 0.0f;
+    }
+    const float sd = 0.1f * std::sqrt(1.0f / float(w1));
+    for (int k = 0; k < 3 * w1; ++k) flat[o++] = sd * nd(rng);
+    for (int k = 0; k < 3; ++k) flat[o++] = 0.0f;
+    FVV_TRY(fvv::set_flat(*N, fvv::Buf::Param, flat.data(), c->own));
+    FVV_CUDA(cudaStreamSynchronize(c->own));
+    return FVV_OK;
+}
+
+fvv_status fvv_refine_param_count(fvv_ctx* c, uint64_t* n)
+{
+    RefineNet* N = fvv::net_of(c);
+    if (!N || !n) return fail(FVV_ERR_STATE, "refinement network not initialised");
+    *n = fvv::flat_count(*N);
+    return FVV_OK;
+}
+
+fvv_status fvv_refine_get(fvv_ctx* c, int32_t which, float* out)
+{
+    RefineNet* N = fvv::net_of(c);
+    if (!N) return fail(FVV_ERR_STATE, "refinement network not initialised");
+    if (!out || which < 0 || which > 3) return fail(FVV_ERR_INVALID_ARG, "bad buffer selector or NULL");
+    std::lock_guard<std::recursive_mutex> g(c->mu);
+    FVV_CUDA(cudaDeviceSynchronize());
+    return fvv::get_flat(*N, fvv::Buf(which), out);
+}
+
+fvv_status fvv_refine_set(fvv_ctx* c, int32_t which, const float* in)
+{
+    RefineNet* N = fvv::net_of(c);
+    if (!N) return fail(FVV_ERR_STATE, "refinement network not initialised");
+    if (!in || which < 0 || which > 3) return fail(FVV_ERR_INVALID_ARG, "bad buffer selector or NULL");
+    std::lock_guard<std::recursive_mutex> g(c->mu);
+    FVV_CUDA(cudaDeviceSynchronize());
+    FVV_TRY(fvv::set_flat(*N, fvv::Buf(which), in, c->own));
+    FVV_CUDA(cudaStreamSynchronize(c->own));
+    return FVV_OK;
+}
+
+fvv_status fvv_refine_forward(fvv_ctx* c, const fvv_refine_batch* b, uint8_t* out_rgb, float* out_f32,
+                              void* stream)
+{
+    RefineNet* N = fvv::net_of(c);
+    if (!N) return fail(FVV_ERR_STATE, "refinement network not initialised");
+    FVV_TRY(fvv::check_batch(*N, b, false));
+    if ((out_rgb && !fvv::on_device(out_rgb)) || (out_f32 && !fvv::on_device(out_f32)))
+        return fail(FVV_ERR_INVALID_ARG, "outputs must be device memory");
+    cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : c->own;
+    std::lock_guard<std::recursive_mutex> g(c->mu);
+    int* err = nullptr;
+    FVV_TRY(fvv::device_flag(&err));
+    FVV_TRY(fvv::ensure_acts(c, *N, b->n, b->height, b->width));
+    FVV_TRY(fvv::forward(*N, *b, err, s, out_rgb, size_t(b->width) * 3, out_f32));
+    return fvv::check_flag(err, s, "fvv_refine_forward");
+}
+
+fvv_status fvv_refine_train_step(fvv_ctx* c, const fvv_refine_batch* b, float lr, float* loss, void* stream)
+{
+    RefineNet* N = fvv::net_of(c);
+    if (!N) return fail(FVV_ERR_STATE, "refinement network not initialised");
+    FVV_TRY(fvv::check_batch(*N, b, true));
+    if (!(lr >= 0.0f) || !std::isfinite(lr)) return fail(FVV_ERR_INVALID_ARG, "lr must be >= 0");
+    cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : c->own;
+    std::lock_guard<std::recursive_mutex> g(c->mu);
+    int* err = nullptr;
+    FVV_TRY(fvv::device_flag(&err));
+    FVV_TRY(fvv::ensure_acts(c, *N, b->n, b->height, b->width));
+    FVV_TRY(fvv::forward(*N, *b, err, s, nullptr, 0, nullptr));
+    FVV_TRY(fvv::backward(*N, *b, err, s));
+    if (lr > 0.0f) FVV_TRY(fvv::adam(*N, lr, s));
+    float h = 0.0f;
+    FVV_CUDA(cudaMemcpyAsync(&h, N->loss, 4, cudaMemcpyDeviceToHost, s));
+    FVV_TRY(fvv::check_flag(err, s, "fvv_refine_train_step"));
+    if (loss) *loss = h;
+    return FVV_OK;
+}
+
+fvv_status fvv_refine_save(fvv_ctx* c, const char* path)
+{
+    RefineNet* N = fvv::net_of(c);
+    if (!N) return fail(FVV_ERR_STATE, "refinement network not initialised");
+    if (!path) return fail(FVV_ERR_INVALID_ARG, "path is NULL");
+    std::lock_guard<std::recursive_mutex> g(c->mu);
+    FVV_CUDA(cudaDeviceSynchronize());
+    const size_t n = fvv::flat_count(*N);
+    std::vector<float> buf(3 * n);
+    FVV_TRY(fvv::get_flat(*N, fvv::Buf::Param, buf.data()));
+    FVV_TRY(fvv::get_flat(*N, fvv::Buf::M, buf.data() + n));
+    FVV_TRY(fvv::get_flat(*N, fvv::Buf::V, buf.data() + 2 * n));
+    FILE* f = std::fopen(path, "wb");
+    if (!f) return fail(FVV_ERR_INVALID_ARG, std::string("cannot open ") + path);
+    const char magic[8] = {'F', 'V', 'V', 'U', 'N', 'E', 'T', '1'};
+    const int32_t hdr[5] = {N->w1, N->w2, N->w3, N->step, 0};
+    const uint64_t cnt = n;
+    bool ok = std::fwrite(magic, 1, 8, f) == 8 && std::fwrite(hdr, 4, 5, f) == 5 &&
+              std::fwrite(&N->z_far, 4, 1, f) == 1 && std::fwrite(&cnt, 8, 1, f) == 1 &&
+              std::fwrite(buf.data(), 4, buf.size(), f) == buf.size();
+    ok = (std::fclose(f) == 0) && ok;
+    if (!ok) return fail(FVV_ERR_INVALID_ARG, std::string("write failed: ") + path);
+    return FVV_OK;
+}
+
+fvv_status fvv_refine_load(fvv_ctx* c, const char* path)
+{
+    if (!c || !path) return fail(FVV_ERR_INVALID_ARG, "NULL argument");
+    FILE* f = std::fopen(path, "rb");
+    if (!f) return fail(FVV_ERR_INVALID_ARG, std::string("cannot open ") + path);
+    char magic[8];
+    int32_t hdr[5];
+    float z_far = 0.0f;
+    uint64_t cnt = 0;
+    bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, "FVVUNET1", 8) == 0 &&
+              std::fread(hdr, 4, 5, f) == 5 && std::fread(&z_far, 4, 1, f) == 1 && std::fread(&cnt, 8, 1, f) == 1;
+    std::vector<float> buf;
+    if (ok && cnt < (uint64_t(1) << 32)) {
+        buf.resize(3 * cnt);
+        ok = std::fread(buf.data(), 4, buf.size(), f) == buf.size();
+    } else {
+        ok = false;
+    }
+    std::fclose(f);
+    if (!ok) return fail(FVV_ERR_INVALID_ARG, std::string("not a refinement checkpoint: ") + path);
+    fvv_unet_cfg cfg;
+    fvv_refine_default_cfg(&cfg);
+    cfg.widths[0] = hdr[0];
+    cfg.widths[1] = hdr[1];
+    cfg.widths[2] = hdr[2];
+    cfg.z_far = z_far;
+    FVV_TRY(fvv_refine_init(c, &cfg));
+    RefineNet* N = fvv::net_of(c);
+    if (fvv::flat_count(*N) != cnt) return fail(FVV_ERR_INVALID_ARG, "checkpoint size mismatch");
+    std::lock_guard<std::recursive_mutex> g(c->mu);
+    FVV_TRY(fvv::set_flat(*N, fvv::Buf::Param, buf.data(), c->own));
+    FVV_TRY(fvv::set_flat(*N, fvv::Buf::M, buf.data() + cnt, c->own));
+    FVV_TRY(fvv::set_flat(*N, fvv::Buf::V, buf.data() + 2 * cnt, c->own));
+    N->step = hdr[3];
+    FVV_CUDA(cudaStreamSynchronize(c->own));
+    return FVV_OK;
+}
+
+fvv_status fvv_synthesize_refined(fvv_ctx* c, const fvv_view* view, uint8_t* out_rgb, size_t out_pitch,
+                                  void* stream)
+{
+    RefineNet* N = fvv::net_of(c);
+    if (!N) return fail(FVV_ERR_STATE, "refinement network not initialised");
+    if (!view || !out_rgb) return fail(FVV_ERR_INVALID_ARG, "NULL argument");
+    const int H = view->height, W = view->width;
+    if (H % 4 || W % 4) return fail(FVV_ERR_INVALID_ARG, "refined views need width and height multiples of 4");
+    if (out_pitch < size_t(W) * 3) return fail(FVV_ERR_INVALID_ARG, "out_pitch < 3 * width");
+    cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : c->own;
+    std::lock_guard<std::recursive_mutex> g(c->mu);
+    if (N->sH != H || N->sW != W) {
+        FVV_CUDA(cudaDeviceSynchronize());
+        fvv::free_list(c, N->syn);
+        N->sH = N->sW = 0;
+        const size_t np = size_t(H) * W;
+        FVV_TRY(fvv::alloc_t(c, N->syn, &N->syn_rgb, np * 3));
+        FVV_TRY(fvv::alloc_t(c, N->syn, &N->syn_out, np * 3));
+        FVV_TRY(fvv::alloc_t(c, N->syn, &N->syn_hole, np));
+        FVV_TRY(fvv::alloc_t(c, N->syn, &N->syn_depth, np));
+        FVV_TRY(fvv::alloc_t(c, N->syn, &N->syn_top3, np * 3));
+        N->sH = H;
+        N->sW = W;
+    }
+    fvv_aux aux{};
+    aux.depth = N->syn_depth;
+    aux.hole = N->syn_hole;
+    aux.top3 = N->syn_top3;
+    uint8_t* outs[1] = {N->syn_rgb};
+    const size_t pitches[1] = {size_t(W) * 3};
+    FVV_TRY(fvv::run_batch(c, c->main, 1, view, nullptr, outs, pitches, &aux, s, true));
+    fvv_refine_batch b{};
+    b.n = 1;
+    b.height = H;
+    b.width = W;
+    b.rgb = N->syn_rgb;
+    b.depth = N->syn_depth;
+    b.hole = N->syn_hole;
+    b.top3 = N->syn_top3;
+    int* err = nullptr;
+    FVV_TRY(fvv::device_flag(&err));
+    FVV_TRY(fvv::ensure_acts(c, *N, 1, H, W));
+    const bool dev_out = fvv::mem_kind(out_rgb) == fvv::MemKind::Device;
+    FVV_TRY(fvv::forward(*N, b, err, s, dev_out ? out_rgb : N->syn_out, dev_out ? out_pitch : size_t(W) * 3,
+                         nullptr));
+    if (!dev_out)
+        FVV_CUDA(cudaMemcpy2DAsync(out_rgb, out_pitch, N->syn_out, size_t(W) * 3, size_t(W) * 3, size_t(H),
+                                   cudaMemcpyDeviceToHost, s));
+    return fvv::check_flag(err, s, "fvv_synthesize_refined");
 }
 
 }  // extern "C"

@@ -92,6 +92,7 @@ struct BatchScratch {
 };
 
 struct ServeState;                        // fvv_serve.cu
+struct RefineNet;                         // fvv_refine.cu
 
 }  // namespace fvv
 
@@ -129,6 +130,7 @@ struct fvv_ctx {
     // against the serving thread.
     std::recursive_mutex mu;
     fvv::ServeState* serve = nullptr;
+    fvv::RefineNet* refine = nullptr;
 };
 
 namespace fvv {
@@ -187,5 +189,7 @@ fvv_status run_batch(fvv_ctx* c, BatchScratch& S, int n, const fvv_view* views,
 
 // fvv_serve.cu: stop a running serving loop (fvv_destroy calls it).
 void serve_shutdown(fvv_ctx* c);
+// fvv_refine.cu: free the refinement network (fvv_destroy calls it).
+void refine_destroy(fvv_ctx* c);
 
 }  // namespace fvv

@@ -26,3 +26,33 @@ cudaError_t launch_conv3x3(const void* x, int NB, int H, int W, int Cin, const v
                            cudaStream_t s);
 
 }  // namespace fvv
+
+namespace fvv {
+
+// fvv_unet_ops.cu (CUDA-core layers)
+cudaError_t launch_pack_features(size_t npx, const uint8_t* rgb, const float* depth, const uint8_t* hole,
+                                 const float* top3, float z_far, __nv_bfloat16* out, cudaStream_t s);
+cudaError_t launch_maxpool2(int B, int H, int W, int C, const __nv_bfloat16* x, __nv_bfloat16* y, uint8_t* arg,
+                            cudaStream_t s);
+cudaError_t launch_maxpool2_bwd(int B, int H, int W, int C, const __nv_bfloat16* dy, const uint8_t* arg,
+                                const __nv_bfloat16* add, const __nv_bfloat16* mask, __nv_bfloat16* dx,
+                                cudaStream_t s);
+cudaError_t launch_up2_concat(int B, int H, int W, int C1, int C2, const __nv_bfloat16* lo,
+                              const __nv_bfloat16* skip, __nv_bfloat16* cat, cudaStream_t s);
+cudaError_t launch_up2_concat_bwd(int B, int H, int W, int C1, int C2, const __nv_bfloat16* dcat,
+                                  const __nv_bfloat16* lo_act, __nv_bfloat16* dlo, __nv_bfloat16* dskip,
+                                  cudaStream_t s);
+cudaError_t launch_head_fwd(size_t npx, const __nv_bfloat16* d1, const float* wout, const float* bout,
+                            const uint8_t* rgb, float* sbuf, uint8_t* out, int W, size_t out_pitch,
+                            float* out_f32, cudaStream_t s);
+cudaError_t launch_head_bwd(size_t npx, const __nv_bfloat16* d1, const float* wout, const float* sbuf,
+                            const uint8_t* target, float* loss, float* dwout, float* dbout, __nv_bfloat16* dd1,
+                            cudaStream_t s);
+cudaError_t launch_wgrad3x3(int B, int H, int W, int Cin, int Cout, const __nv_bfloat16* x,
+                            const __nv_bfloat16* dz, float* dw, cudaStream_t s);
+cudaError_t launch_bias_grad(size_t npx, int C, const __nv_bfloat16* dz, float* db, cudaStream_t s);
+cudaError_t launch_flip_weights(int Cout, int Cin, const float* w, __nv_bfloat16* wbf, __nv_bfloat16* wt,
+                                cudaStream_t s);
+cudaError_t launch_adam(size_t n, float* w, const float* g, float* m, float* v, float lr, int t, cudaStream_t s);
+
+}  // namespace fvv

@@ -1,0 +1,473 @@
+// fvv_unet_ops.cu -- the refinement network's non-GEMM layers (CUDA cores):
+// input packing, 2x2 max pooling, nearest 2x upsampling + channel concat,
+// the 1x1 output head with clamp and the mean-squared-error loss, weight and
+// bias gradients of the 3x3 convolutions, the weight flip used by the
+// transposed (data-gradient) convolution, and Adam.
+// All activations are NHWC bf16; gradients of weights and biases are fp32.
+#include <cuda_bf16.h>
+
+#include "fvv_unet.h"
+
+namespace fvv {
+
+namespace {
+
+__device__ __forceinline__ float bf(const __nv_bfloat16 v) { return __bfloat162float(v); }
+
+__device__ __forceinline__ float block_sum(float v, float* red)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[wid] = v;
+    __syncthreads();
+    float s = 0.0f;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < int(blockDim.x >> 5); ++i) s += red[i];
+    return s;                                   // valid in thread 0
+}
+
+// ---- input features ----------------------------------------------------------
+// 8 channels (RGB / 255, depth / z_far, hole, top-3 weights) + zeros to 32.
+__global__ void k_pack_features(size_t npx, const uint8_t* __restrict__ rgb, const float* __restrict__ depth,
+                                const uint8_t* __restrict__ hole, const float* __restrict__ top3, float inv_zfar,
+                                __nv_bfloat16* __restrict__ out)
+{
+    const size_t p = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (p >= npx) return;
+    float f[8];
+    f[0] = float(rgb[3 * p + 0]) * (1.0f / 255.0f);
+    f[1] = float(rgb[3 * p + 1]) * (1.0f / 255.0f);
+    f[2] = float(rgb[3 * p + 2]) * (1.0f / 255.0f);
+    f[3] = depth[p] * inv_zfar;
+    f[4] = float(hole[p]);
+    f[5] = top3[3 * p + 0];
+    f[6] = top3[3 * p + 1];
+    f[7] = top3[3 * p + 2];
+    uint32_t w[16];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(f[2 * i], f[2 * i + 1]);
+        w[i] = *reinterpret_cast<const uint32_t*>(&h);
+    }
+#pragma unroll
+    for (int i = 4; i < 16; ++i) w[i] = 0u;
+    uint4* dst = reinterpret_cast<uint4*>(out + 32 * p);
+#pragma unroll
+    for (int v = 0; v < 4; ++v) dst[v] = make_uint4(w[4 * v], w[4 * v + 1], w[4 * v + 2], w[4 * v + 3]);
+}
+
+// ---- pooling -----------------------------------------------------------------
+__global__ void k_maxpool2(int B, int H, int W, int C, const __nv_bfloat16* __restrict__ x,
+                           __nv_bfloat16* __restrict__ y, uint8_t* __restrict__ arg)
+{
+    const size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    const int h2 = H / 2, w2 = W / 2;
+    const size_t n_out = size_t(B) * h2 * w2 * C;
+    if (i >= n_out) return;
+    const int c = int(i % C);
+    size_t r = i / C;
+    const int ox = int(r % w2);
+    r /= w2;
+    const int oy = int(r % h2);
+    const int b = int(r / h2);
+    const size_t base = ((size_t(b) * H + 2 * oy) * W + 2 * ox) * C + c;
+    const float v[4] = {bf(x[base]), bf(x[base + C]), bf(x[base + size_t(W) * C]),
+                        bf(x[base + size_t(W) * C + C])};
+    int a = 0;
+    for (int k = 1; k < 4; ++k)
+        if (v[k] > v[a]) a = k;                   // first maximum wins
+    y[i] = x[base + (a & 1) * size_t(C) + (a >> 1) * size_t(W) * C];
+    arg[i] = uint8_t(a);
+}
+
+// dx = route(dy by arg) + add, then zero where mask <= 0 (add, mask nullable)
+__global__ void k_maxpool2_bwd(int B, int H, int W, int C, const __nv_bfloat16* __restrict__ dy,
+                               const uint8_t* __restrict__ arg, const __nv_bfloat16* __restrict__ add,
+                               const __nv_bfloat16* __restrict__ mask, __nv_bfloat16* __restrict__ dx)
+{
+    const size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    const size_t n = size_t(B) * H * W * C;
+    if (i >= n) return;
+    const int c = int(i % C);
+    size_t r = i / C;
+    const int x = int(r % W);
+    r /= W;
+    const int yy = int(r % H);
+    const int b = int(r / H);
+    const int h2 = H / 2, w2 = W / 2;
+    const size_t j = ((size_t(b) * h2 + yy / 2) * w2 + x / 2) * C + c;
+    const int k = (yy & 1) * 2 + (x & 1);
+    float v = arg[j] == k ? bf(dy[j]) : 0.0f;
+    if (add) v += bf(add[i]);
+    if (mask && !(bf(mask[i]) > 0.0f)) v = 0.0f;
+    dx[i] = __float2bfloat16_rn(v);
+}
+
+// ---- upsampling + concat ------------------------------------------------------
+// cat[b, y, x] = [ up(lo)[b, y, x, 0:C1] | skip[b, y, x, 0:C2] ]
+__global__ void k_up2_concat(int B, int H, int W, int C1, int C2, const __nv_bfloat16* __restrict__ lo,
+                             const __nv_bfloat16* __restrict__ skip, __nv_bfloat16* __restrict__ cat)
+{
+    const int C = C1 + C2;
+    const size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    const size_t n = size_t(B) * H * W * C;
+    if (i >= n) return;
+    const int c = int(i % C);
+    const size_t p = i / C;
+    const int x = int(p % W);
+    const int yy = int((p / W) % H);
+    const int b = int(p / (size_t(W) * H));
+    if (c < C1)
+        cat[i] = lo[((size_t(b) * (H / 2) + yy / 2) * (W / 2) + x / 2) * C1 + c];
+    else
+        cat[i] = skip[p * C2 + (c - C1)];
+}
+
+// dlo = (sum over each 2x2 block of dcat[..., 0:C1]) * (lo_act > 0); dskip = dcat[..., C1:]
+__global__ void k_up2_concat_bwd(int B, int H, int W, int C1, int C2, const __nv_bfloat16* __restrict__ dcat,
+                                 const __nv_bfloat16* __restrict__ lo_act, __nv_bfloat16* __restrict__ dlo,
+                                 __nv_bfloat16* __restrict__ dskip)
+{
+    const int C = C1 + C2;
+    const size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    const int h2 = H / 2, w2 = W / 2;
+    const size_t n_lo = size_t(B) * h2 * w2 * C1;
+    const size_t n_sk = size_t(B) * H * W * C2;
+    if (i < n_lo) {
+        const int c = int(i % C1);
+        size_t r = i / C1;
+        const int x = int(r % w2);
+        r /= w2;
+        const int yy = int(r % h2);
+        const int b = int(r / h2);
+        const size_t p00 = (size_t(b) * H + 2 * yy) * W + 2 * x;
+        float v = bf(dcat[p00 * C + c]) + bf(dcat[(p00 + 1) * C + c]) + bf(dcat[(p00 + W) * C + c]) +
+                  bf(dcat[(p00 + W + 1) * C + c]);
+        if (!(bf(lo_act[i]) > 0.0f)) v = 0.0f;
+        dlo[i] = __float2bfloat16_rn(v);
+    }
+    if (i < n_sk) {
+        const int c = int(i % C2);
+        const size_t p = i / C2;
+        dskip[i] = dcat[p * C + C1 + c];
+    }
+}
+
+// ---- 1x1 head ---------------------------------------------------------------
+// s = rgb / 255 + (W d1 + b); out = round(255 clamp(s, 0, 1))
+__global__ void k_head_fwd(size_t npx, const __nv_bfloat16* __restrict__ d1, const float* __restrict__ wout,
+                           const float* __restrict__ bout, const uint8_t* __restrict__ rgb, float* __restrict__ s,
+                           uint8_t* __restrict__ out, int W, size_t out_pitch, float* __restrict__ out_f32)
+{
+    __shared__ float sw[3 * 32 + 3];
+    for (int i = threadIdx.x; i < 99; i += blockDim.x) sw[i] = i < 96 ? wout[i] : bout[i - 96];
+    __syncthreads();
+    const size_t p = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (p >= npx) return;
+    float a[32];
+    const uint4* src = reinterpret_cast<const uint4*>(d1 + 32 * p);
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+        const uint4 q = src[v];
+        const uint32_t w4[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const __nv_bfloat162 h = *reinterpret_cast<const __nv_bfloat162*>(&w4[j]);
+            a[8 * v + 2 * j] = __bfloat162float(h.x);
+            a[8 * v + 2 * j + 1] = __bfloat162float(h.y);
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        float r = sw[96 + c];
+#pragma unroll
+        for (int k = 0; k < 32; ++k) r += sw[32 * c + k] * a[k];
+        const float sv = float(rgb[3 * p + c]) * (1.0f / 255.0f) + r;
+        if (s) s[3 * p + c] = sv;
+        const float pr = fminf(fmaxf(sv, 0.0f), 1.0f);
+        if (out_f32) out_f32[3 * p + c] = pr;
+        if (out) {
+            const size_t y = p / W, x = p % W;
+            out[y * out_pitch + 3 * x + c] = uint8_t(floorf(pr * 255.0f + 0.5f));
+        }
+    }
+}
+
+// Loss and the head's backward pass.  diff = clamp(s) - target / 255;
+// loss += sum diff^2 (scaled by inv_count); ds = 2 diff inv_count on 0 < s < 1;
+// dW += ds d1^T; db += ds; dd1 = (W^T ds) * (d1 > 0).
+__global__ void k_head_bwd(size_t npx, const __nv_bfloat16* __restrict__ d1, const float* __restrict__ wout,
+                           const float* __restrict__ s, const uint8_t* __restrict__ target, float inv_count,
+                           float* __restrict__ loss, float* __restrict__ dwout, float* __restrict__ dbout,
+                           __nv_bfloat16* __restrict__ dd1)
+{
+    __shared__ float sw[96];
+    __shared__ float acc[96 + 3 + 1];
+    __shared__ float red[32];
+    for (int i = threadIdx.x; i < 96; i += blockDim.x) sw[i] = wout[i];
+    for (int i = threadIdx.x; i < 100; i += blockDim.x) acc[i] = 0.0f;
+    __syncthreads();
+    const size_t p = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    float l = 0.0f;
+    if (p < npx) {
+        float a[32];
+        const uint4* src = reinterpret_cast<const uint4*>(d1 + 32 * p);
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const uint4 q = src[v];
+            const uint32_t w4[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const __nv_bfloat162 h = *reinterpret_cast<const __nv_bfloat162*>(&w4[j]);
+                a[8 * v + 2 * j] = __bfloat162float(h.x);
+                a[8 * v + 2 * j + 1] = __bfloat162float(h.y);
+            }
+        }
+        float ds[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float sv = s[3 * p + c];
+            const float d = fminf(fmaxf(sv, 0.0f), 1.0f) - float(target[3 * p + c]) * (1.0f / 255.0f);
+            l += d * d;
+            ds[c] = (sv > 0.0f && sv < 1.0f) ? 2.0f * d * inv_count : 0.0f;
+            atomicAdd(&acc[96 + c], ds[c]);
+        }
+        uint32_t out[16];
+#pragma unroll
+        for (int k = 0; k < 32; k += 2) {
+            float g0 = sw[k] * ds[0] + sw[32 + k] * ds[1] + sw[64 + k] * ds[2];
+            float g1 = sw[k + 1] * ds[0] + sw[33 + k] * ds[1] + sw[65 + k] * ds[2];
+            if (!(a[k] > 0.0f)) g0 = 0.0f;
+            if (!(a[k + 1] > 0.0f)) g1 = 0.0f;
+            const __nv_bfloat162 h = __floats2bfloat162_rn(g0, g1);
+            out[k >> 1] = *reinterpret_cast<const uint32_t*>(&h);
+        }
+        uint4* dst = reinterpret_cast<uint4*>(dd1 + 32 * p);
+#pragma unroll
+        for (int v = 0; v < 4; ++v) dst[v] = make_uint4(out[4 * v], out[4 * v + 1], out[4 * v + 2], out[4 * v + 3]);
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            if (ds[c] != 0.0f)
+#pragma unroll 4
+                for (int k = 0; k < 32; ++k) atomicAdd(&acc[32 * c + k], ds[c] * a[k]);
+    }
+    const float bl = block_sum(l, red);
+    __syncthreads();
+    if (threadIdx.x == 0) atomicAdd(loss, bl * inv_count);
+    for (int i = threadIdx.x; i < 99; i += blockDim.x) {
+        const float v = acc[i];
+        if (v != 0.0f) atomicAdd(i < 96 ? &dwout[i] : &dbout[i - 96], v);
+    }
+}
+
+// ---- weight gradients of a 3x3 convolution --------------------------------------
+// dw[co][ky][kx][ci] += sum_p dz[p][co] * x[p + (ky-1, kx-1)][ci]  (zero outside).
+// CTA = a 32 (co) x 32 (ci) block of one tap over a slice of pixel rows; each
+// thread owns 2 x 2 outputs; 64 pixels are staged in shared memory at a time.
+constexpr int kWgPix = 64;
+__global__ void __launch_bounds__(256) k_wgrad3x3(int B, int H, int W, int Cin, int Cout,
+                                                  const __nv_bfloat16* __restrict__ x,
+                                                  const __nv_bfloat16* __restrict__ dz, float* __restrict__ dw,
+                                                  int rows_per_cta)
+{
+    __shared__ float sz[kWgPix][33];
+    __shared__ float sx[kWgPix][33];
+    const int co_blocks = Cout / 32, ci_blocks = Cin / 32;
+    int t = blockIdx.x;
+    const int cib = t % ci_blocks;
+    t /= ci_blocks;
+    const int cob = t % co_blocks;
+    const int tap = t / co_blocks;
+    const int ky = tap / 3, kx = tap - 3 * ky;
+    const int tid = threadIdx.x;
+    const int tco = (tid >> 4) * 2, tci = (tid & 15) * 2;
+    float a00 = 0.f, a01 = 0.f, a10 = 0.f, a11 = 0.f;
+    const long total_rows = long(B) * H;
+    const long r0 = long(blockIdx.y) * rows_per_cta;
+    const long r1 = min(total_rows, r0 + rows_per_cta);
+    for (long r = r0; r < r1; ++r) {
+        const int b = int(r / H), yy = int(r % H);
+        const int ys = yy + ky - 1;
+        for (int x0 = 0; x0 < W; x0 += kWgPix) {
+            __syncthreads();
+            for (int i = tid; i < kWgPix * 32; i += 256) {
+                const int pp = i >> 5, c = i & 31;
+                const int xx = x0 + pp;
+                float zv = 0.0f, xv = 0.0f;
+                if (xx < W) {
+                    zv = bf(dz[((size_t(b) * H + yy) * W + xx) * Cout + cob * 32 + c]);
+                    const int xs = xx + kx - 1;
+                    if (ys >= 0 && ys < H && xs >= 0 && xs < W)
+                        xv = bf(x[((size_t(b) * H + ys) * W + xs) * Cin + cib * 32 + c]);
+                }
+                sz[pp][c] = zv;
+                sx[pp][c] = xv;
+            }
+            __syncthreads();
+#pragma unroll 8
+            for (int pp = 0; pp < kWgPix; ++pp) {
+                const float z0 = sz[pp][tco], z1 = sz[pp][tco + 1];
+                const float x0v = sx[pp][tci], x1v = sx[pp][tci + 1];
+                a00 += z0 * x0v;
+                a01 += z0 * x1v;
+                a10 += z1 * x0v;
+                a11 += z1 * x1v;
+            }
+        }
+    }
+    const size_t K = size_t(9) * Cin;
+    const size_t o0 = size_t(cob * 32 + tco) * K + size_t(tap) * Cin + cib * 32 + tci;
+    atomicAdd(&dw[o0], a00);
+    atomicAdd(&dw[o0 + 1], a01);
+    atomicAdd(&dw[o0 + K], a10);
+    atomicAdd(&dw[o0 + K + 1], a11);
+}
+
+// db[co] += sum_p dz[p][co]
+__global__ void k_bias_grad(size_t npx, int C, const __nv_bfloat16* __restrict__ dz, float* __restrict__ db,
+                            size_t px_per_cta)
+{
+    const int c = threadIdx.x % C;
+    const int lanes = blockDim.x / C;
+    const int l = threadIdx.x / C;
+    if (l >= lanes) return;
+    const size_t p0 = size_t(blockIdx.x) * px_per_cta;
+    const size_t p1 = p0 + px_per_cta < npx ? p0 + px_per_cta : npx;
+    float a = 0.0f;
+    for (size_t p = p0 + l; p < p1; p += lanes) a += bf(dz[p * C + c]);
+    atomicAdd(&db[c], a);
+}
+
+// wt[ci][ky][kx][co] = w[co][2-ky][2-kx][ci] (bf16), the weights of the
+// transposed convolution that gives the input gradient.
+__global__ void k_flip_weights(int Cout, int Cin, const float* __restrict__ w, __nv_bfloat16* __restrict__ wbf,
+                               __nv_bfloat16* __restrict__ wt)
+{
+    const size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    const size_t n = size_t(Cout) * 9 * Cin;
+    if (i >= n) return;
+    const int ci = int(i % Cin);
+    const int tap = int((i / Cin) % 9);
+    const int co = int(i / (size_t(9) * Cin));
+    const __nv_bfloat16 v = __float2bfloat16_rn(w[i]);
+    wbf[i] = v;
+    if (wt) wt[(size_t(ci) * 9 + (8 - tap)) * Cout + co] = v;
+}
+
+__global__ void k_adam(size_t n, float* __restrict__ w, const float* __restrict__ g, float* __restrict__ m,
+                       float* __restrict__ v, float lr, float b1, float b2, float eps, float c1, float c2)
+{
+    const size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.0f - b1) * gi;
+    const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    w[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+}
+
+unsigned blocks(size_t n, int t) { return unsigned((n + t - 1) / t); }
+
+}  // namespace
+
+cudaError_t launch_pack_features(size_t npx, const uint8_t* rgb, const float* depth, const uint8_t* hole,
+                                 const float* top3, float z_far, __nv_bfloat16* out, cudaStream_t s)
+{
+    k_pack_features<<<blocks(npx, 256), 256, 0, s>>>(npx, rgb, depth, hole, top3, 1.0f / z_far, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_maxpool2(int B, int H, int W, int C, const __nv_bfloat16* x, __nv_bfloat16* y, uint8_t* arg,
+                            cudaStream_t s)
+{
+    const size_t n = size_t(B) * (H / 2) * (W / 2) * C;
+    k_maxpool2<<<blocks(n, 256), 256, 0, s>>>(B, H, W, C, x, y, arg);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_maxpool2_bwd(int B, int H, int W, int C, const __nv_bfloat16* dy, const uint8_t* arg,
+                                const __nv_bfloat16* add, const __nv_bfloat16* mask, __nv_bfloat16* dx,
+                                cudaStream_t s)
+{
+    const size_t n = size_t(B) * H * W * C;
+    k_maxpool2_bwd<<<blocks(n, 256), 256, 0, s>>>(B, H, W, C, dy, arg, add, mask, dx);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_up2_concat(int B, int H, int W, int C1, int C2, const __nv_bfloat16* lo,
+                              const __nv_bfloat16* skip, __nv_bfloat16* cat, cudaStream_t s)
+{
+    const size_t n = size_t(B) * H * W * (C1 + C2);
+    k_up2_concat<<<blocks(n, 256), 256, 0, s>>>(B, H, W, C1, C2, lo, skip, cat);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_up2_concat_bwd(int B, int H, int W, int C1, int C2, const __nv_bfloat16* dcat,
+                                  const __nv_bfloat16* lo_act, __nv_bfloat16* dlo, __nv_bfloat16* dskip,
+                                  cudaStream_t s)
+{
+    const size_t n = size_t(B) * H * W * C2 > size_t(B) * (H / 2) * (W / 2) * C1
+                         ? size_t(B) * H * W * C2
+                         : size_t(B) * (H / 2) * (W / 2) * C1;
+    k_up2_concat_bwd<<<blocks(n, 256), 256, 0, s>>>(B, H, W, C1, C2, dcat, lo_act, dlo, dskip);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_head_fwd(size_t npx, const __nv_bfloat16* d1, const float* wout, const float* bout,
+                            const uint8_t* rgb, float* sbuf, uint8_t* out, int W, size_t out_pitch,
+                            float* out_f32, cudaStream_t s)
+{
+    k_head_fwd<<<blocks(npx, 128), 128, 0, s>>>(npx, d1, wout, bout, rgb, sbuf, out, W, out_pitch, out_f32);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_head_bwd(size_t npx, const __nv_bfloat16* d1, const float* wout, const float* sbuf,
+                            const uint8_t* target, float* loss, float* dwout, float* dbout, __nv_bfloat16* dd1,
+                            cudaStream_t s)
+{
+    const float inv = 1.0f / float(npx * 3);
+    k_head_bwd<<<blocks(npx, 128), 128, 0, s>>>(npx, d1, wout, sbuf, target, inv, loss, dwout, dbout, dd1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_wgrad3x3(int B, int H, int W, int Cin, int Cout, const __nv_bfloat16* x,
+                            const __nv_bfloat16* dz, float* dw, cudaStream_t s)
+{
+    const int tiles = 9 * (Cout / 32) * (Cin / 32);
+    const long rows = long(B) * H;
+    // split the rows so that about 4 waves of CTAs cover the GPU
+    long splits = (4L * 152 * 4 + tiles - 1) / tiles;
+    if (splits > rows) splits = rows;
+    if (splits < 1) splits = 1;
+    const int rpc = int((rows + splits - 1) / splits);
+    dim3 grid(unsigned(tiles), unsigned((rows + rpc - 1) / rpc));
+    k_wgrad3x3<<<grid, 256, 0, s>>>(B, H, W, Cin, Cout, x, dz, dw, rpc);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bias_grad(size_t npx, int C, const __nv_bfloat16* dz, float* db, cudaStream_t s)
+{
+    const size_t per = 4096;
+    k_bias_grad<<<blocks(npx, int(per)), 256, 0, s>>>(npx, C, dz, db, per);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_flip_weights(int Cout, int Cin, const float* w, __nv_bfloat16* wbf, __nv_bfloat16* wt,
+                                cudaStream_t s)
+{
+    const size_t n = size_t(Cout) * 9 * Cin;
+    k_flip_weights<<<blocks(n, 256), 256, 0, s>>>(Cout, Cin, w, wbf, wt);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adam(size_t n, float* w, const float* g, float* m, float* v, float lr, int t, cudaStream_t s)
+{
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float c1 = 1.0f - powf(b1, float(t)), c2 = 1.0f - powf(b2, float(t));
+    k_adam<<<blocks(n, 256), 256, 0, s>>>(n, w, g, m, v, lr, b1, b2, 1e-8f, c1, c2);
+    return cudaGetLastError();
+}
+
+}  // namespace fvv

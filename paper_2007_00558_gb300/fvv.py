@@ -79,6 +79,19 @@ class fvv_serve_report(C.Structure):
                 ("in_flight", C.c_int32)]
 
 
+class fvv_unet_cfg(C.Structure):
+    _fields_ = [("widths", C.c_int32 * 3), ("seed", C.c_uint64), ("z_far", C.c_float)]
+
+
+class fvv_refine_batch(C.Structure):
+    _fields_ = [("n", C.c_int32), ("height", C.c_int32), ("width", C.c_int32),
+                ("rgb", C.c_void_p), ("depth", C.c_void_p), ("hole", C.c_void_p),
+                ("top3", C.c_void_p), ("target", C.c_void_p)]
+
+
+FVV_REFINE_PARAMS, FVV_REFINE_GRADS, FVV_REFINE_ADAM_M, FVV_REFINE_ADAM_V = 0, 1, 2, 3
+
+
 class fvv_kernel_stats(C.Structure):
     _fields_ = [("name", C.c_char * 32), ("launches", C.c_uint64), ("timed", C.c_uint64),
                 ("total_ms", C.c_double)]
@@ -127,6 +140,16 @@ def load() -> C.CDLL:
             "fvv_serve_stats": [P, C.POINTER(fvv_serve_report), I],
             "fvv_serve_stop": [P],
             "fvv_unet_conv3x3": [P, I, I, I, I, P, P, I, I, P, P, P],
+            "fvv_refine_default_cfg": [C.POINTER(fvv_unet_cfg)],
+            "fvv_refine_init": [P, C.POINTER(fvv_unet_cfg)],
+            "fvv_refine_param_count": [P, C.POINTER(U64)],
+            "fvv_refine_get": [P, I, P],
+            "fvv_refine_set": [P, I, P],
+            "fvv_refine_forward": [P, C.POINTER(fvv_refine_batch), P, P, P],
+            "fvv_refine_train_step": [P, C.POINTER(fvv_refine_batch), C.c_float, C.POINTER(C.c_float), P],
+            "fvv_refine_save": [P, C.c_char_p],
+            "fvv_refine_load": [P, C.c_char_p],
+            "fvv_synthesize_refined": [P, C.POINTER(fvv_camera), P, S, P],
             "fvv_profile_enable": [P, I],
             "fvv_profile_read": [P, C.POINTER(fvv_kernel_stats), C.POINTER(I), I],
         }
@@ -349,3 +372,68 @@ def fvv_unet_conv3x3(x, n: int, h: int, w: int, cin: int, wt, bias, cout: int, r
                      stream=None) -> None:
     _check(load().fvv_unet_conv3x3(ptr(x), n, h, w, cin, ptr(wt), ptr(bias), cout, 1 if relu else 0,
                                    ptr(mask), ptr(y), stream_handle(stream)), "fvv_unet_conv3x3")
+
+
+def fvv_refine_default_cfg(**overrides) -> fvv_unet_cfg:
+    cfg = fvv_unet_cfg()
+    _check(load().fvv_refine_default_cfg(C.byref(cfg)), "fvv_refine_default_cfg")
+    for k, v in overrides.items():
+        if k == "widths":
+            cfg.widths[:] = list(v)
+        else:
+            setattr(cfg, k, v)
+    return cfg
+
+
+def fvv_refine_init(ctx: int, cfg: Optional[fvv_unet_cfg] = None) -> None:
+    _check(load().fvv_refine_init(ctx, C.byref(cfg) if cfg is not None else None), "fvv_refine_init")
+
+
+def fvv_refine_param_count(ctx: int) -> int:
+    n = C.c_uint64()
+    _check(load().fvv_refine_param_count(ctx, C.byref(n)), "fvv_refine_param_count")
+    return n.value
+
+
+def fvv_refine_get(ctx: int, which: int = FVV_REFINE_PARAMS) -> np.ndarray:
+    out = np.zeros(fvv_refine_param_count(ctx), np.float32)
+    _check(load().fvv_refine_get(ctx, which, out.ctypes.data), "fvv_refine_get")
+    return out
+
+
+def fvv_refine_set(ctx: int, which: int, values) -> None:
+    v = np.ascontiguousarray(values, dtype=np.float32)
+    _check(load().fvv_refine_set(ctx, which, v.ctypes.data), "fvv_refine_set")
+
+
+def refine_batch(n, height, width, rgb, depth, hole, top3, target=None) -> fvv_refine_batch:
+    b = fvv_refine_batch()
+    b.n, b.height, b.width = n, height, width
+    b.rgb, b.depth, b.hole, b.top3, b.target = ptr(rgb), ptr(depth), ptr(hole), ptr(top3), ptr(target)
+    return b
+
+
+def fvv_refine_forward(ctx: int, batch: fvv_refine_batch, out_rgb=None, out_f32=None, stream=None) -> None:
+    _check(load().fvv_refine_forward(ctx, C.byref(batch), ptr(out_rgb), ptr(out_f32),
+                                     stream_handle(stream)), "fvv_refine_forward")
+
+
+def fvv_refine_train_step(ctx: int, batch: fvv_refine_batch, lr: float, stream=None) -> float:
+    loss = C.c_float()
+    _check(load().fvv_refine_train_step(ctx, C.byref(batch), lr, C.byref(loss), stream_handle(stream)),
+           "fvv_refine_train_step")
+    return loss.value
+
+
+def fvv_refine_save(ctx: int, path: str) -> None:
+    _check(load().fvv_refine_save(ctx, path.encode()), "fvv_refine_save")
+
+
+def fvv_refine_load(ctx: int, path: str) -> None:
+    _check(load().fvv_refine_load(ctx, path.encode()), "fvv_refine_load")
+
+
+def fvv_synthesize_refined(ctx: int, view, out_rgb, out_pitch: int, stream=None) -> None:
+    v = view if isinstance(view, fvv_camera) else camera(view)
+    _check(load().fvv_synthesize_refined(ctx, C.byref(v), ptr(out_rgb), out_pitch, stream_handle(stream)),
+           "fvv_synthesize_refined")
