@@ -60,6 +60,8 @@ def parse_args():
     p.add_argument("--no-serve", action="store_true", help="skip the serving-loop measurement")
     p.add_argument("--serve-seconds", type=float, default=3.0,
                    help="length of the Poisson multi-viewer run")
+    p.add_argument("--no-refine", action="store_true", help="skip the refinement-network measurement")
+    p.add_argument("--refine-steps", type=int, default=600, help="LOO training steps before measuring")
     return p.parse_args()
 
 
@@ -212,6 +214,15 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
+def bf16_peak():
+    """Measured dense bf16 tensor throughput (TFLOP/s): burst figure."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["bf16_tflops"]), "measured"
+    except Exception:
+        return 1900.0, "fallback"
+
+
 def kernel_source_sha():
     h = hashlib.sha256()
     for f in ("fvv_kernels.cu", "fvv_internal.h"):
@@ -353,11 +364,117 @@ def serve_bench(F, ctx, wl, rgb_h, dep_h, slots, seconds, stream):
 
 
 # ---------------------------------------------------------------------------
+# refinement network: LOO training (stated PSNR), refined 720p throughput
+# ---------------------------------------------------------------------------
+def unet_flops(H, W, widths=(32, 64, 128), c_in=8):
+    """Algorithmic multiply-adds x 2 of the U-Net forward on an H x W view."""
+    w1, w2, w3 = widths
+    l1 = 9 * (c_in * w1 + w1 * w1 + (w2 + w1) * w1 + w1 * w1) + 3 * w1
+    l2 = 9 * (w1 * w2 + w2 * w2 + (w3 + w2) * w2 + w2 * w2)
+    l3 = 9 * (w2 * w3 + w3 * w3)
+    return 2.0 * (H * W * l1 + H * W / 4 * l2 + H * W / 16 * l3)
+
+
+def refine_bench(F, ctx, wl, steps, stream):
+    import numpy as np
+    import torch
+    import synthetic as S
+    from paper_2007_00558_gb300 import refine_train as RT
+    # 1. stated PSNR: LOO renders at 1/4 scale, 6 training + 2 unseen scenes
+    cams_s = S.rig_arc(9, 90.0, 1.5, 320, 180, 250.0)
+    loo = RT.LooRig(cams_s, [0.0, 0.0, 0.0])
+    try:
+        def scene(seed):
+            rgb, dep = S.frames_for(S.scene_random_objects(seed), cams_s, noise_seed=seed + 7)
+            return loo.samples(rgb, dep)
+        train = RT.concat([scene(s) for s in range(100, 106)])
+        test = RT.concat([scene(s) for s in (200, 201)])
+    finally:
+        loo.close()
+    F.fvv_refine_init(ctx, F.fvv_refine_default_cfg(seed=1))
+    t0 = time.perf_counter()
+    losses = RT.train(ctx, train, steps=steps, batch=8, crop=128, lr=2e-3)
+    train_s = time.perf_counter() - t0
+    ev = RT.evaluate(ctx, test)
+    # 2. throughput: plain synthesis + network on 1280x720 views
+    H, W = wl["cams"][0].height, wl["cams"][0].width
+    views = wl["views"]
+    out = torch.empty((H, W * 3), dtype=torch.uint8, device="cuda")
+    for i in range(3):
+        F.fvv_synthesize_refined(ctx, views[i], out, W * 3, stream)
+    torch.cuda.synchronize()
+    n = 40
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(n):
+        F.fvv_synthesize_refined(ctx, views[i % 300], out, W * 3, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    per_view = e0.elapsed_time(e1) / n / 1e3
+    # network alone on a batch of 4 plain 720p outputs
+    B = 4
+    plain = {"rgb": torch.empty((B, H, W, 3), dtype=torch.uint8, device="cuda"),
+             "depth": torch.empty((B, H, W), dtype=torch.float32, device="cuda"),
+             "hole": torch.empty((B, H, W), dtype=torch.uint8, device="cuda"),
+             "top3": torch.empty((B, H, W, 3), dtype=torch.float32, device="cuda")}
+    F.fvv_synthesize_batch(ctx, views[:B], None, [plain["rgb"][i] for i in range(B)], [W * 3] * B,
+                           [F.aux(depth=plain["depth"][i], hole=plain["hole"][i], top3=plain["top3"][i])
+                            for i in range(B)], stream)
+    fb = F.refine_batch(B, H, W, plain["rgb"], plain["depth"], plain["hole"], plain["top3"])
+    outb = torch.empty((B, H, W, 3), dtype=torch.uint8, device="cuda")
+    F.fvv_refine_forward(ctx, fb, outb, None, stream)
+    m = 10
+    e0.record(stream)
+    for i in range(m):
+        F.fvv_refine_forward(ctx, fb, outb, None, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    net_s = e0.elapsed_time(e1) / m / 1e3 / B
+    flops = unet_flops(H, W)
+    peak, src = bf16_peak()
+    return {
+        "views_per_s": 1.0 / per_view, "ms_per_view": per_view * 1e3,
+        "net_ms_per_view": net_s * 1e3, "net_tflops": flops / net_s / 1e12,
+        "tensor_peak_tflops": peak, "tensor_frac": flops / net_s / 1e12 / peak, "peak_source": src,
+        "gflop_per_view": flops / 1e9, "dtype": "bf16 x bf16 -> fp32",
+        "psnr": {"plain_db": ev["psnr_plain"], "refined_db": ev["psnr_refined"],
+                 "eval": "leave-one-camera-out, 2 unseen synthetic scenes x 9 cameras, %s" % ev["size"]},
+        "train": {"steps": steps, "batch": 8, "crop": 128, "seconds": train_s,
+                  "loss_first": float(np.mean(losses[:20])), "loss_last": float(np.mean(losses[-20:])),
+                  "samples": int(train["depth"].shape[0])},
+    }
+
+
+# ---------------------------------------------------------------------------
 # arms
 # ---------------------------------------------------------------------------
 def dist_env():
     return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
             int(os.environ.get("LOCAL_RANK", 0)))
+
+
+def view_schedule(rank, step, batch, slots, n_traj=300):
+    """Replicas: (trajectory index, frame tick) of each view a rank renders in
+    one step.  Every rank walks the trajectory from its own offset; there is
+    no exchange between ranks."""
+    off = rank * 7919
+    return [((off + step * batch + j) % n_traj, (step * batch + j) % slots) for j in range(batch)]
+
+
+def max_over_ranks(value, device):
+    """Max of a float over all ranks (NCCL for cuda tensors, gloo for cpu)."""
+    import torch
+    import torch.distributed as dist
+    if not dist.is_available() or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_views_per_s(steps, batch, world, max_elapsed_s):
+    """Whole-job throughput: views of all ranks over the slowest rank's time."""
+    return steps * batch * world / max_elapsed_s
 
 
 def run_reference(args):
@@ -428,9 +545,9 @@ def run_fvv(args):
     off = rank * 7919
 
     def step(i):
-        vs = [views[(off + i * Bsz + j) % 300] for j in range(Bsz)]
-        ticks = [(i * Bsz + j) % slots for j in range(Bsz)]
-        F.fvv_synthesize_batch(ctx, vs, ticks, out, pitches, None, stream)
+        sched = view_schedule(rank, i, Bsz, slots)
+        F.fvv_synthesize_batch(ctx, [views[v] for v, _ in sched], [t for _, t in sched], out, pitches,
+                               None, stream)
 
     def barrier():
         if world > 1:
@@ -459,12 +576,9 @@ def run_fvv(args):
     el_ms = ev0.elapsed_time(ev1)
     stats = F.fvv_profile_read(ctx, reset=True)
     F.fvv_profile_enable(ctx, False)
-    if world > 1:
-        t = torch.tensor([el_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        el_ms = float(t.item())
+    el_ms = max_over_ranks(el_ms, "cuda")
     n_views = args.steps * Bsz * world
-    value = n_views / (el_ms / 1e3)
+    value = aggregate_views_per_s(args.steps, Bsz, world, el_ms / 1e3)
 
     # roofline of the dominant kernel
     Ns = Nd = H * W
@@ -511,18 +625,18 @@ def run_fvv(args):
         for i in range(args.steps):
             e2e_step(args.warmup + i)
         torch.cuda.synchronize()
-        el = time.perf_counter() - t0
-        if world > 1:
-            t = torch.tensor([el], device="cuda")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            el = float(t.item())
-        e2e = {"value": n_views / el, "unit": UNIT,
+        el = max_over_ranks(time.perf_counter() - t0, "cuda")
+        e2e = {"value": aggregate_views_per_s(args.steps, Bsz, world, el), "unit": UNIT,
                "h2d_bytes_per_step": int(Bsz * (rgb_h.numel() + dep_h.numel() * 2)),
                "d2h_bytes_per_step": int(Bsz * H * W * 3)}
 
     serve = None
     if not args.no_serve and world == 1:
         serve = serve_bench(F, ctx, wl, rgb_h, dep_h, slots, args.serve_seconds, stream)
+
+    refine = None
+    if not args.no_refine and world == 1:
+        refine = refine_bench(F, ctx, wl, args.refine_steps, stream)
 
     F.fvv_destroy(ctx)
 
@@ -548,7 +662,7 @@ def run_fvv(args):
                        "l2": "inputs > L2: each view reads its own frame tick, %d ticks x %.1f MB "
                              "resident" % (slots, K * H * W * 6 / 1e6),
                        "parallelism": "replicas" if world > 1 else "single"},
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "serve": serve,
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "serve": serve, "refine": refine,
             "gpu_launches": int(launches), "clocks": clocks.summary(),
             "kernel_ms": {k: v[2] for k, v in stats.items()},
         }
