@@ -241,6 +241,19 @@ fvv_status fvv_profile_enable(fvv_ctx* ctx, int32_t on);
  * waits for the recorded events.  reset = 1 clears the statistics. */
 fvv_status fvv_profile_read(fvv_ctx* ctx, fvv_kernel_stats* out, int32_t* n, int32_t reset);
 
+/* ---- diagnostics ----------------------------------------------------------
+ * Self-test of the bounded waits that every tensor-core kernel of this
+ * library uses (the paper has no counterpart).  One CTA initialises an
+ * mbarrier expecting one arrival; if `arrive` != 0 a thread arrives on it;
+ * then a thread waits for the phase to complete, giving up after limit_us
+ * microseconds (1 .. 2,000,000).  A wait that gives up records an error code
+ * in a device flag and the kernel exits normally, so the context stays
+ * usable.  Allocates and frees one device int; waits for completion on
+ * `stream` (NULL = the legacy default stream).
+ * Returns OK when the phase completed, TIMEOUT when the wait ran out,
+ * INVALID_ARG for a limit outside the range, CUDA on a launch failure. */
+fvv_status fvv_selftest_bounded_wait(int32_t arrive, uint32_t limit_us, void* stream);
+
 /* ---- refinement network: layer operations -------------------------------
  * The learned refinement (a U-Net; the paper has none) runs on the sm_103a
  * tensor cores.  Its layers are exposed for tests and custom pipelines.

@@ -140,6 +140,7 @@ def load() -> C.CDLL:
             "fvv_serve_stats": [P, C.POINTER(fvv_serve_report), I],
             "fvv_serve_stop": [P],
             "fvv_unet_conv3x3": [P, I, I, I, I, P, P, I, I, P, P, P],
+            "fvv_selftest_bounded_wait": [I, C.c_uint32, P],
             "fvv_refine_default_cfg": [C.POINTER(fvv_unet_cfg)],
             "fvv_refine_init": [P, C.POINTER(fvv_unet_cfg)],
             "fvv_refine_param_count": [P, C.POINTER(U64)],
@@ -372,6 +373,15 @@ def fvv_unet_conv3x3(x, n: int, h: int, w: int, cin: int, wt, bias, cout: int, r
                      stream=None) -> None:
     _check(load().fvv_unet_conv3x3(ptr(x), n, h, w, cin, ptr(wt), ptr(bias), cout, 1 if relu else 0,
                                    ptr(mask), ptr(y), stream_handle(stream)), "fvv_unet_conv3x3")
+
+
+def fvv_selftest_bounded_wait(arrive: bool, limit_us: int, stream=None) -> int:
+    """Returns the raw status (FVV_OK or FVV_ERR_TIMEOUT are both expected
+    outcomes); other failures raise."""
+    st = load().fvv_selftest_bounded_wait(1 if arrive else 0, limit_us, stream_handle(stream))
+    if st not in (FVV_OK, FVV_ERR_TIMEOUT):
+        _check(st, "fvv_selftest_bounded_wait")
+    return st
 
 
 def fvv_refine_default_cfg(**overrides) -> fvv_unet_cfg:

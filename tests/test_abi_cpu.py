@@ -99,3 +99,9 @@ def test_invalid_arguments_rejected_on_host(F):
     # NULL context
     assert _code(F, F.fvv_destroy, None) == 0
     assert _code(F, F.fvv_latest_tick, None) == F.FVV_ERR_INVALID_ARG
+
+
+def test_selftest_limit_checked_on_host(F):
+    so = F.load()
+    for lim in (0, 2000001):
+        assert so.fvv_selftest_bounded_wait(0, lim, None) == F.FVV_ERR_INVALID_ARG
