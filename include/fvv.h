@@ -262,15 +262,31 @@ fvv_status fvv_selftest_bounded_wait(int32_t arrive, uint32_t limit_us, void* st
 /* y = relu?(conv3x3(x, w) + bias), pad 1, stride 1, then optionally zeroed
  * where mask <= 0 (the ReLU derivative of a previous layer, for backward
  * passes).  Implicit GEMM on tcgen05 with fp32 accumulation in TMEM.
- *   x: [n][h][w][cin], cin a multiple of 32
+ *   x: [n][h][w][cin], cin a multiple of 8 (at most 4096)
  *   wt: [cout][3][3][cin]; bias: float [cout] or NULL
- *   cout: 32, 64, 96, 128 or 192; mask: [n][h][w][cout] or NULL
+ *   cout: 32, 48, 64, 96, 128 or 192; mask: [n][h][w][cout] or NULL
+ *   every pointer 16-byte aligned
  *   y: [n][h][w][cout]
  * Waits for completion on `stream`.  Errors: INVALID_ARG, TIMEOUT (a bounded
  * wait inside the kernel ran out), CUDA. */
 fvv_status fvv_unet_conv3x3(const void* x, int32_t n, int32_t h, int32_t w, int32_t cin,
                             const void* wt, const float* bias, int32_t cout, int32_t relu,
                             const void* mask, void* y, void* stream);
+
+/* FP8 form of the same convolution.  x, wt and y hold OCP E4M3 bytes (1
+ * sign, 4 exponent bits with bias 7, 3 mantissa bits; largest finite 448).
+ * With per-tensor scales s_x, s_w, s_y (x = s_x X, w = s_w W, y = s_y Y for
+ * the stored codes X, W, Y):
+ *   Y = e4m3(relu?(acc_scale * sum X W + bias) * out_inv_scale),
+ * acc_scale = s_x s_w, out_inv_scale = 1 / s_y; e4m3() rounds to nearest
+ * even and saturates to +-448.  Products accumulate in fp32 (tcgen05
+ * kind::f8f6f4).  x: [n][h][w][cin], cin a multiple of 16; wt:
+ * [cout][3][3][cin]; bias: float [cout] or NULL; y: [n][h][w][cout]; every
+ * pointer 16-byte aligned.  Waits for completion on `stream`.
+ * Errors: INVALID_ARG, TIMEOUT, CUDA. */
+fvv_status fvv_unet_conv3x3_e4m3(const void* x, int32_t n, int32_t h, int32_t w, int32_t cin, const void* wt,
+                                 const float* bias, int32_t cout, int32_t relu, float acc_scale,
+                                 float out_inv_scale, void* y, void* stream);
 
 /* ---- refinement network ---------------------------------------------------
  * A 3-level U-Net refines a plain synthesis (the paper has none; it leaves

@@ -204,3 +204,48 @@ def features(rgb8, depth, hole, top3, z_far):
                            (depth.astype(np.float64) / z_far)[..., None],
                            hole.astype(np.float64)[..., None],
                            top3.astype(np.float64)], axis=-1)
+
+
+# ---------------------------------------------------------------------------
+# FP8 form: OCP E4M3 (1 sign bit, 4 exponent bits with bias 7, 3 mantissa
+# bits; normal numbers 2^(e-7) (1 + m/8) for e = 1..15, except e = 15, m = 7
+# which is NaN, so the largest finite value is 448; subnormals (m/8) 2^-6;
+# no infinities).  Conversions round to nearest, ties to even mantissa, and
+# saturate to +-448.
+# ---------------------------------------------------------------------------
+E4M3_MAX = 448.0
+
+
+def e4m3_round(x):
+    """The E4M3 value nearest to x (ties to even), saturated to [-448, 448]."""
+    x = np.asarray(x, np.float64)
+    a = np.abs(x)
+    _, ex = np.frexp(a)                       # a = f 2^ex with f in [0.5, 1): binade 2^(ex-1)
+    e = np.clip(ex - 1, -6, 8)                # below 2^-6 the spacing stays 2^-9 (subnormals)
+    step = np.ldexp(1.0, e - 3)               # 3 mantissa bits
+    q = np.minimum(np.round(a / step) * step, E4M3_MAX)   # np.round: half to even
+    return np.where(np.signbit(x), -q, q)
+
+
+def e4m3_encode(q):
+    """Bytes of E4M3-representable values (as returned by e4m3_round)."""
+    q = np.asarray(q, np.float64)
+    a = np.abs(q)
+    sign = np.signbit(q).astype(np.uint8)
+    _, ex = np.frexp(a)
+    e = ex - 1
+    sub = a < 2.0 ** -6
+    E = np.where(sub, 0, e + 7)
+    M = np.where(sub, a / 2.0 ** -9, (np.ldexp(a, -np.where(sub, 0, e)) - 1.0) * 8.0)
+    return ((sign << 7) | (E.astype(np.uint8) << 3) | M.astype(np.uint8)).astype(np.uint8)
+
+
+def e4m3_decode(b):
+    """Values of E4M3 bytes (the NaN codes 0x7f / 0xff decode to NaN)."""
+    b = np.asarray(b, np.uint8).astype(np.int64)
+    s = np.where(b >> 7, -1.0, 1.0)
+    E = (b >> 3) & 15
+    M = b & 7
+    v = np.where(E == 0, M / 8.0 * 2.0 ** -6, (1.0 + M / 8.0) * np.ldexp(1.0, E - 7))
+    v = np.where((E == 15) & (M == 7), np.nan, v)
+    return s * v

@@ -399,10 +399,13 @@ fvv_status fvv_unet_conv3x3(const void* x, int32_t n, int32_t h, int32_t w, int3
         return fail(FVV_ERR_INVALID_ARG, "x, w and y must be device memory");
     if ((bias && !fvv::on_device(bias)) || (mask && !fvv::on_device(mask)))
         return fail(FVV_ERR_INVALID_ARG, "bias and mask must be device memory");
-    if (n < 1 || h < 1 || w < 1 || cin < 32 || cin % 32 || cin > 4096)
-        return fail(FVV_ERR_INVALID_ARG, "need n, h, w >= 1 and cin a multiple of 32");
+    if ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(wt) | reinterpret_cast<uintptr_t>(y) |
+         reinterpret_cast<uintptr_t>(bias) | reinterpret_cast<uintptr_t>(mask)) & 15u)
+        return fail(FVV_ERR_INVALID_ARG, "x, w, bias, mask and y must be 16-byte aligned");
+    if (n < 1 || h < 1 || w < 1 || cin < 8 || cin % 8 || cin > 4096)
+        return fail(FVV_ERR_INVALID_ARG, "need n, h, w >= 1 and cin a multiple of 8");
     if (!fvv::conv_cout_supported(cout))
-        return fail(FVV_ERR_INVALID_ARG, "cout must be 32, 64, 96, 128 or 192");
+        return fail(FVV_ERR_INVALID_ARG, "cout must be 32, 48, 64, 96, 128 or 192");
     if (uint64_t(n) * h * ((w + 127) / 128) >= (uint64_t(1) << 31))
         return fail(FVV_ERR_INVALID_ARG, "too many pixel tiles");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -416,6 +419,39 @@ fvv_status fvv_unet_conv3x3(const void* x, int32_t n, int32_t h, int32_t w, int3
     a.err = flag;
     FVV_CUDA(fvv::launch_conv3x3(x, n, h, w, cin, wt, cout, a, s));
     return fvv::check_flag(flag, s, "fvv_unet_conv3x3");
+}
+
+fvv_status fvv_unet_conv3x3_e4m3(const void* x, int32_t n, int32_t h, int32_t w, int32_t cin, const void* wt,
+                                 const float* bias, int32_t cout, int32_t relu, float acc_scale, float out_inv_scale,
+                                 void* y, void* stream)
+{
+    if (!fvv::on_device(x) || !fvv::on_device(wt) || !fvv::on_device(y))
+        return fail(FVV_ERR_INVALID_ARG, "x, w and y must be device memory");
+    if (bias && !fvv::on_device(bias)) return fail(FVV_ERR_INVALID_ARG, "bias must be device memory");
+    if ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(wt) | reinterpret_cast<uintptr_t>(y) |
+         reinterpret_cast<uintptr_t>(bias)) & 15u)
+        return fail(FVV_ERR_INVALID_ARG, "x, w, bias and y must be 16-byte aligned");
+    if (n < 1 || h < 1 || w < 1 || cin < 16 || cin % 16 || cin > 4096)
+        return fail(FVV_ERR_INVALID_ARG, "need n, h, w >= 1 and cin a multiple of 16");
+    if (!fvv::conv_cout_supported(cout))
+        return fail(FVV_ERR_INVALID_ARG, "cout must be 32, 48, 64, 96, 128 or 192");
+    if (!(acc_scale > 0.0f) || !(out_inv_scale > 0.0f) || !std::isfinite(acc_scale) || !std::isfinite(out_inv_scale))
+        return fail(FVV_ERR_INVALID_ARG, "scales must be finite and > 0");
+    if (uint64_t(n) * h * ((w + 127) / 128) >= (uint64_t(1) << 31))
+        return fail(FVV_ERR_INVALID_ARG, "too many pixel tiles");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int* flag = nullptr;
+    FVV_TRY(fvv::device_flag(&flag));
+    fvv::ConvArgs a{};
+    a.bias = bias;
+    a.y = static_cast<__nv_bfloat16*>(y);
+    a.relu = relu;
+    a.fp8 = 1;
+    a.acc_scale = acc_scale;
+    a.out_inv_scale = out_inv_scale;
+    a.err = flag;
+    FVV_CUDA(fvv::launch_conv3x3(x, n, h, w, cin, wt, cout, a, s));
+    return fvv::check_flag(flag, s, "fvv_unet_conv3x3_e4m3");
 }
 
 fvv_status fvv_refine_default_cfg(fvv_unet_cfg* cfg)

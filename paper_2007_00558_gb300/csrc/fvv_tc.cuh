@@ -70,8 +70,9 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* e
 {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = globaltimer();
-    for (;;) {
+    for (uint32_t i = 1;; ++i) {
         if (mbar_try_wait(bar, parity)) return true;
+        if ((i & 15u) != 0) continue;            // the flag and the clock every 16 polls
         if (*reinterpret_cast<volatile int*>(err) != 0) return false;   // another thread gave up
         if (globaltimer() - t0 > limit_ns) {
             atomicCAS(err, 0, code);
@@ -104,6 +105,14 @@ __device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, u
     asm volatile(
         "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];"
         ::"r"(smem_u32(dst)), "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1, int c2)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+        ::"r"(smem_u32(dst)), "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
         : "memory");
 }
 
@@ -151,6 +160,20 @@ __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64
         : "memory");
 }
 
+// D[tmem] (+)= A[smem] * B[smem]^T, e4m3 inputs, fp32 accumulators (K = 32 per instruction).
+__device__ __forceinline__ void mma_e4m3(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate)
+{
+    asm volatile(
+        "{\n"
+        ".reg .pred p;\n"
+        "setp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n"
+        "}\n" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
 // Arrive on `bar` when every MMA issued so far by this thread has completed.
 __device__ __forceinline__ void mma_commit(uint64_t* bar)
 {
@@ -180,8 +203,11 @@ __device__ __forceinline__ void tmem_ld_wait()
 }
 
 // Shared-memory matrix descriptor of a K-major operand tile stored as rows
-// of 64 bytes (32 bf16) with the 64-byte swizzle that TMA writes: 8-row
-// groups 512 bytes apart.  The tile base must be 512-byte aligned.
+// of 64 bytes with the 64-byte swizzle that TMA writes: 8-row groups 512
+// bytes apart.  The swizzle follows absolute shared-memory address bits (the
+// base-offset field stays 0), so a start moved by whole 64-byte rows selects
+// the shifted window of a tile that TMA wrote, and +32 bytes the second half
+// of each row.
 __device__ __forceinline__ uint64_t desc_kmajor_sw64(uint32_t saddr)
 {
     uint64_t d = 0;
@@ -191,6 +217,58 @@ __device__ __forceinline__ uint64_t desc_kmajor_sw64(uint32_t saddr)
     d |= uint64_t(1) << 46;                          // descriptor version
     d |= uint64_t(4) << 61;                          // 64-byte swizzle
     return d;
+}
+
+// Descriptor of a K-major operand in the no-swizzle core-matrix layout:
+// each core matrix is 8 rows x 16 bytes stored contiguously (row r at
+// +16 r); core matrices adjacent in K are `lbo` bytes apart, those adjacent
+// in M (or N) `sbo` bytes apart.  Any 16-byte aligned start is valid, so a
+// start moved by whole rows selects a shifted window of the same tile.
+__device__ __forceinline__ uint64_t desc_kmajor_plain(uint32_t saddr, uint32_t lbo, uint32_t sbo)
+{
+    uint64_t d = 0;
+    d |= uint64_t((saddr >> 4) & 0x3FFFu);
+    d |= uint64_t((lbo >> 4) & 0x3FFFu) << 16;
+    d |= uint64_t((sbo >> 4) & 0x3FFFu) << 32;
+    d |= uint64_t(1) << 46;                          // descriptor version; swizzle bits 0 = none
+    return d;
+}
+
+// 16 consecutive fp32 columns of this warp's 32 TMEM lanes.
+__device__ __forceinline__ void tmem_ld_x16(uint32_t taddr, uint32_t (&r)[16])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+          "=r"(r[15])
+        : "r"(taddr));
+}
+
+// ---- cp.async (16 bytes, L2 only); src_bytes = 0 writes zeros -------------------
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, uint32_t src_bytes)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(src_bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// Make this thread's completed generic-proxy shared-memory writes visible to
+// the async proxy (the tensor cores read shared memory through it).
+__device__ __forceinline__ void fence_proxy_async_smem()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// Instruction descriptor: kind::f8f6f4 with e4m3 A and B (format code 0), fp32 D, both K-major.
+__host__ __device__ constexpr uint32_t idesc_e4m3(int M, int N)
+{
+    return (1u << 4) | (uint32_t(N >> 3) << 17) | (uint32_t(M >> 4) << 24);
 }
 
 // Instruction descriptor: kind::f16 with bf16 A and B, fp32 D, both K-major.

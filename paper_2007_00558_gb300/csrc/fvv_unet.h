@@ -7,21 +7,24 @@
 
 namespace fvv {
 
-// Arguments of one tensor-core 3x3 convolution (pad 1), NHWC bf16.
+// Arguments of one tensor-core 3x3 convolution (pad 1), NHWC.
 struct ConvArgs {
-    int NB, H, W, Cin;              // input; Cin % 32 == 0
+    int NB, H, W, Cin;              // input; Cin a multiple of 8 (bf16) or 16 (e4m3)
     int tiles_x;                    // ceil(W / 128), set by the launcher
-    const float* bias;              // [Cout] or null
-    __nv_bfloat16* y;               // [NB][H][W][Cout]
+    const float* bias;              // [Cout] or null (16-byte aligned)
+    __nv_bfloat16* y;               // output pixel p, channel c at y[p * ldy + coff + c] (e4m3: bytes)
+    int ldy, coff;                  // output channel stride (0: Cout) and offset
     int relu;                       // 1: max(0, .)
-    const __nv_bfloat16* mask;      // optional [NB][H][W][Cout]: zero where mask <= 0
+    const __nv_bfloat16* mask;      // optional [NB][H][W][Cout] (bf16 only): zero where mask <= 0
+    int fp8;                        // 1: x, w and y are e4m3
+    float acc_scale;                // accumulator multiplier before the bias (0: 1)
+    float out_inv_scale;            // e4m3 output = value * out_inv_scale (0: 1)
     int* err;                       // device flag: a bounded wait ran out (never reset here)
 };
 
 bool conv_cout_supported(int cout);
-cudaError_t make_act_map(CUtensorMap* m, const void* x, int NB, int H, int W, int C);
-cudaError_t make_weight_map(CUtensorMap* m, const void* w, int cout, int K);
-// y = relu?(conv3x3(x, w) + bias) [* (mask > 0)]; w is bf16 [Cout][3][3][Cin].
+// y = relu?(acc_scale conv3x3(x, w) + bias) [* (mask > 0)]; w is [Cout][3][3][Cin]
+// in the element type of x, Cout one of conv_cout_supported.
 cudaError_t launch_conv3x3(const void* x, int NB, int H, int W, int Cin, const void* w, int Cout, ConvArgs a,
                            cudaStream_t s);
 

@@ -2,19 +2,28 @@
 // an implicit GEMM on the sm_103a tensor cores (tcgen05, TMEM, TMA).
 //
 // GEMM view: M = 128 consecutive output pixels of one image row, N = the
-// output channels, K = 9 taps x input channels.  For tap (ky, kx) and a
-// 32-channel block, TMA loads the 128 x 32 input patch at pixel offset
-// (kx - 1, ky - 1) straight from the NHWC activation tensor (zero fill
-// outside the image is the convolution's padding) and the matching
-// COUT x 32 block of the weights [cout][ky][kx][cin].  A 4-stage mbarrier
-// ring feeds one MMA-issuing thread; the fp32 accumulators live in TMEM and
-// four epilogue warps add the bias, apply ReLU and an optional ReLU-derivative
-// mask, round to bf16 and store NHWC.
+// output channels, K = 9 taps x input channels.  A persistent CTA (one per
+// SM) walks the pixel tiles.  Input channels are taken in groups of one
+// 64-byte row (32 bf16 or 64 e4m3 channels).  For each tile and group, ONE
+// TMA copy brings the halo -- rows y-1..y+1, pixels x0-1..x0+128, zero
+// outside the image (the convolution's padding) and beyond the last channel
+// -- into shared memory as 3 x 130 rows of 64 bytes with the 64-byte swizzle.
+// Operand A of tap (ky, kx) is that same halo seen through a descriptor
+// whose start lies 130 ky + kx rows further on: nine taps cost nine
+// descriptors, not nine copies.  The weights [cout][ky][kx][cin] stay
+// resident in shared memory when they fit; otherwise they stream through a
+// ring of one-ky slices (three taps).  The fp32 accumulators live in TMEM,
+// double-buffered: four epilogue warps drain tile i (scale, bias, ReLU,
+// optional ReLU-derivative mask, rounding to bf16 or e4m3, NHWC store) while
+// the MMA thread accumulates tile i+1.
 //
-// Warp roles (192 threads): 0 = TMA producer, 1 = TMEM owner + MMA issuer,
+// Warp roles (192 threads): 0 = TMA producer, 1 = TMEM owner and MMA issuer,
 // 2..5 = epilogue (warp w reads TMEM lanes 32 (w mod 4) .. +31).
+#include <algorithm>
+
 #include <cuda.h>
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 #include <cudaTypedefs.h>
 
 #include "fvv_internal.h"
@@ -25,53 +34,109 @@ namespace fvv {
 
 namespace {
 
-constexpr int kStages = 4;
 constexpr int kTileM = 128;
-constexpr int kBlockK = 32;                       // channels per stage (64-byte rows)
-constexpr int kABytes = kTileM * kBlockK * 2;     // 8 KiB
+constexpr int kHaloPx = kTileM + 2;                    // 130 halo pixels per row
+constexpr int kRow = 64;                               // bytes of one pixel row of a channel group
+constexpr int kHaloBytes = 3 * kHaloPx * kRow;         // 24,960
+constexpr int kHaloStage = 25 * 1024;                  // halo slot, 1024-aligned
+constexpr int kThreads = 192;
+constexpr int kMaxStages = 8;
+constexpr int kSmemLimit = 227 * 1024;
+constexpr int kSmemFixed = 1024 + 1024;                // alignment slack + barriers
 
 template <int COUT>
 struct ConvCfg {
-    static constexpr int kBBytes = COUT * kBlockK * 2;
-    static constexpr int kBStride = (kBBytes + 1023) / 1024 * 1024;
-    static constexpr int kTmemCols = COUT <= 32 ? 32 : COUT <= 64 ? 64 : COUT <= 128 ? 128 : 256;
-    static constexpr int kSmem = 1024 + kStages * (kABytes + kBStride) + 256;
+    static constexpr int kTap = COUT * kRow;           // B tile of one tap (COUT rows of 64 bytes)
+    static constexpr int kSlice = 3 * kTap;            // the three taps of one ky
+    static constexpr int kGroup = 9 * kTap;            // all taps of one channel group
+    static constexpr int kAcc = (COUT + 31) / 32 * 32; // TMEM columns between the two accumulators
+    static constexpr int kTmemCols = 2 * kAcc <= 64 ? 64 : 2 * kAcc <= 128 ? 128 : 2 * kAcc <= 256 ? 256 : 512;
+    static_assert(kTap % 1024 == 0, "tap tiles stay 1024-byte aligned");
+};
+
+struct Plan {
+    int hs, ws, resident, smem;
 };
 
 template <int COUT>
-__global__ void __launch_bounds__(192, 1)
-k_conv3x3_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUtensorMap tmw, ConvArgs P)
+Plan make_plan(int groups)
+{
+    using C = ConvCfg<COUT>;
+    Plan p{};
+    const int res = groups * C::kGroup;
+    if (kSmemFixed + res + 3 * kHaloStage <= kSmemLimit) {
+        p.resident = 1;
+        p.hs = std::min(kMaxStages, (kSmemLimit - kSmemFixed - res) / kHaloStage);
+        p.ws = 0;
+        p.smem = kSmemFixed + res + p.hs * kHaloStage;
+    } else {
+        p.resident = 0;
+        p.hs = 3;
+        p.ws = std::min(kMaxStages, (kSmemLimit - kSmemFixed - p.hs * kHaloStage) / C::kSlice);
+        p.smem = kSmemFixed + p.hs * kHaloStage + p.ws * C::kSlice;
+    }
+    return p;
+}
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float a, float b)
+{
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<const uint32_t*>(&h);
+}
+
+__device__ __forceinline__ uint32_t pack_e4m3x4(float a, float b, float c, float d)
+{
+    const __nv_fp8x2_storage_t lo = __nv_cvt_float2_to_fp8x2(make_float2(a, b), __NV_SATFINITE, __NV_E4M3);
+    const __nv_fp8x2_storage_t hi = __nv_cvt_float2_to_fp8x2(make_float2(c, d), __NV_SATFINITE, __NV_E4M3);
+    return uint32_t(lo) | (uint32_t(hi) << 16);
+}
+
+// FP8: e4m3 operands and output (K = 32 channels per MMA, 64 per group);
+// otherwise bf16 (K = 16, 32 per group).
+template <int COUT, bool FP8>
+__global__ void __launch_bounds__(kThreads, 1)
+k_conv3x3_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUtensorMap tmw, ConvArgs P,
+             int n_tiles, int HS, int WS, int resident)
 {
     using Cfg = ConvCfg<COUT>;
+    constexpr int kPerGroup = FP8 ? 64 : 32;           // channels in one 64-byte row
+    constexpr int kEsize = FP8 ? 1 : 2;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    uint8_t* sA = base;
-    uint8_t* sB = base + kStages * kABytes;
-    uint64_t* full = reinterpret_cast<uint64_t*>(sB + kStages * Cfg::kBStride);
-    uint64_t* empty = full + kStages;
-    uint64_t* done = empty + kStages;
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+    uint64_t* full_h = reinterpret_cast<uint64_t*>(base);
+    uint64_t* empty_h = full_h + kMaxStages;
+    uint64_t* full_w = empty_h + kMaxStages;
+    uint64_t* empty_w = full_w + kMaxStages;
+    uint64_t* acc_full = empty_w + kMaxStages;         // [2]
+    uint64_t* acc_empty = acc_full + 2;                // [2]
+    uint64_t* wready = acc_empty + 2;
+    uint64_t* drain = wready + 1;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
     int* skip = reinterpret_cast<int*>(tmem_slot + 1);
+    uint8_t* sHalo = base + 1024;
+    uint8_t* sW = sHalo + HS * kHaloStage;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) *skip = *reinterpret_cast<volatile int*>(P.err);
     __syncthreads();
-    if (*skip) return;                             // an earlier CTA gave up: do nothing
+    if (*skip) return;                                 // an earlier CTA gave up
 
-    const int tile = blockIdx.x;
-    const int xt = tile % P.tiles_x;
-    const int row = tile / P.tiles_x;             // n * H + y
-    const int yy = row % P.H, n = row / P.H;
-    const int x0 = xt * kTileM;
-    const int cblocks = P.Cin / kBlockK;
-    const int n_k = 9 * cblocks;
+    const int Cin = P.Cin, H = P.H, Wd = P.W;
+    const int G = (Cin + kPerGroup - 1) / kPerGroup;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < kStages; ++s) {
-            tc::mbar_init(&full[s], 1);
-            tc::mbar_init(&empty[s], 1);
+        for (int s = 0; s < kMaxStages; ++s) {
+            tc::mbar_init(&full_h[s], 1);
+            tc::mbar_init(&empty_h[s], 1);
+            tc::mbar_init(&full_w[s], 1);
+            tc::mbar_init(&empty_w[s], 1);
         }
-        tc::mbar_init(done, 1);
+        for (int b = 0; b < 2; ++b) {
+            tc::mbar_init(&acc_full[b], 1);
+            tc::mbar_init(&acc_empty[b], 4);
+        }
+        tc::mbar_init(wready, 1);
+        tc::mbar_init(drain, 1);
         tc::fence_mbar_init();
         tc::prefetch_tensormap(&tmx);
         tc::prefetch_tensormap(&tmw);
@@ -83,86 +148,174 @@ k_conv3x3_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CU
     const uint32_t tmem = *tmem_slot;
 
     if (warp == 0) {
-        if (lane == 0) {                          // TMA producer
-            int issued = 0;
-            for (int it = 0; it < n_k; ++it) {
-                const int s = it % kStages;
-                const uint32_t ph = (it / kStages) & 1;
-                if (!tc::mbar_wait(&empty[s], ph ^ 1, P.err, 1)) break;
-                const int tap = it / cblocks, cb = it - tap * cblocks;
-                const int ky = tap / 3, kx = tap - 3 * ky;
-                tc::mbar_arrive_expect_tx(&full[s], kABytes + Cfg::kBBytes);
-                tc::tma_load_4d(sA + s * kABytes, &tmx, &full[s], cb * kBlockK, x0 + kx - 1, yy + ky - 1, n);
-                tc::tma_load_2d(sB + s * Cfg::kBStride, &tmw, &full[s], tap * P.Cin + cb * kBlockK, 0);
-                ++issued;
+        // ------------------------------------------------------------ TMA producer
+        if (lane == 0) {
+            if (resident) {
+                tc::mbar_arrive_expect_tx(wready, uint32_t(G * Cfg::kGroup));
+                for (int g = 0; g < G; ++g)
+                    for (int ky = 0; ky < 3; ++ky)
+                        tc::tma_load_3d(sW + g * Cfg::kGroup + ky * Cfg::kSlice, &tmw, wready, g * kPerGroup, 0,
+                                        3 * ky);
             }
-            if (issued < n_k) {
-                // gave up: let the copies still in flight land before exiting
-                for (int it = (issued > kStages ? issued - kStages : 0); it < issued; ++it)
-                    tc::mbar_wait_drain(&full[it % kStages], (it / kStages) & 1);
-            }
-        }
-    } else if (warp == 1) {
-        if (lane == 0) {                          // MMA issuer
-            constexpr uint32_t idesc = tc::idesc_bf16(kTileM, COUT);
-            for (int it = 0; it < n_k; ++it) {
-                const int s = it % kStages;
-                const uint32_t ph = (it / kStages) & 1;
-                if (!tc::mbar_wait(&full[s], ph, P.err, 2)) break;
-                tc::fence_after_sync();
-                const uint32_t a = tc::smem_u32(sA + s * kABytes);
-                const uint32_t b = tc::smem_u32(sB + s * Cfg::kBStride);
-#pragma unroll
-                for (int ks = 0; ks < kBlockK / 16; ++ks)
-                    tc::mma_bf16(tmem, tc::desc_kmajor_sw64(a + 32 * ks), tc::desc_kmajor_sw64(b + 32 * ks),
-                                 idesc, (it | ks) != 0);
-                tc::mma_commit(&empty[s]);        // the stage is free once these MMAs finish
-            }
-            tc::mma_commit(done);                 // every issued MMA has finished
-        }
-    } else {                                      // epilogue
-        const int q = warp & 3;
-        const bool ok = tc::mbar_wait(done, 0, P.err, 3);
-        tc::fence_after_sync();
-        const int px = q * 32 + lane;
-        const int x = x0 + px;
-        const size_t obase = ((size_t(n) * P.H + yy) * P.W + x) * COUT;
-        if (ok) {
-#pragma unroll 1
-            for (int c0 = 0; c0 < COUT; c0 += 32) {
-                uint32_t r[32];
-                tc::tmem_ld_x32(tmem + (uint32_t(q * 32) << 16) + uint32_t(c0), r);
-                tc::tmem_ld_wait();
-                if (x < P.W) {
-                    uint32_t packed[16];
-#pragma unroll
-                    for (int j = 0; j < 32; j += 2) {
-                        float v0 = __uint_as_float(r[j]), v1 = __uint_as_float(r[j + 1]);
-                        if (P.bias) {
-                            v0 += P.bias[c0 + j];
-                            v1 += P.bias[c0 + j + 1];
-                        }
-                        if (P.relu) {
-                            v0 = fmaxf(v0, 0.0f);
-                            v1 = fmaxf(v1, 0.0f);
-                        }
-                        if (P.mask) {
-                            const __nv_bfloat162 m =
-                                *reinterpret_cast<const __nv_bfloat162*>(P.mask + obase + c0 + j);
-                            if (!(__bfloat162float(m.x) > 0.0f)) v0 = 0.0f;
-                            if (!(__bfloat162float(m.y) > 0.0f)) v1 = 0.0f;
-                        }
-                        const __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
-                        packed[j >> 1] = *reinterpret_cast<const uint32_t*>(&h);
+            uint32_t qh = 0, qw = 0;
+            bool ok = true;
+            for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
+                const int xt = tile % P.tiles_x, row = tile / P.tiles_x;
+                const int y = row % H, n = row / H;
+                const int x0 = xt * kTileM;
+                for (int g = 0; g < G && ok; ++g) {
+                    const int sh = int(qh % uint32_t(HS));
+                    if (!tc::mbar_wait(&empty_h[sh], ((qh / uint32_t(HS)) & 1u) ^ 1u, P.err, 1)) {
+                        ok = false;
+                        break;
                     }
-                    uint4* dst = reinterpret_cast<uint4*>(P.y + obase + c0);
-#pragma unroll
-                    for (int v = 0; v < 4; ++v)
-                        dst[v] = make_uint4(packed[4 * v], packed[4 * v + 1], packed[4 * v + 2], packed[4 * v + 3]);
+                    tc::mbar_arrive_expect_tx(&full_h[sh], kHaloBytes);
+                    tc::tma_load_4d(sHalo + sh * kHaloStage, &tmx, &full_h[sh], g * kPerGroup, x0 - 1, y - 1, n);
+                    ++qh;
+                    if (!resident) {
+                        for (int ky = 0; ky < 3; ++ky, ++qw) {
+                            const int sw = int(qw % uint32_t(WS));
+                            if (!tc::mbar_wait(&empty_w[sw], ((qw / uint32_t(WS)) & 1u) ^ 1u, P.err, 2)) {
+                                ok = false;
+                                break;
+                            }
+                            tc::mbar_arrive_expect_tx(&full_w[sw], Cfg::kSlice);
+                            tc::tma_load_3d(sW + sw * Cfg::kSlice, &tmw, &full_w[sw], g * kPerGroup, 0, 3 * ky);
+                        }
+                    }
                 }
             }
         }
+    } else if (warp == 1) {
+        // ------------------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            constexpr uint32_t idesc = FP8 ? tc::idesc_e4m3(kTileM, COUT) : tc::idesc_bf16(kTileM, COUT);
+            bool ok = !resident || tc::mbar_wait(wready, 0, P.err, 3);
+            uint32_t qh = 0, qw = 0;
+            int tl = 0;
+            for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x, ++tl) {
+                const int b = tl & 1;
+                if (!tc::mbar_wait(&acc_empty[b], ((tl >> 1) & 1) ^ 1, P.err, 4)) {
+                    ok = false;
+                    break;
+                }
+                tc::fence_after_sync();
+                const uint32_t d = tmem + uint32_t(b * Cfg::kAcc);
+                for (int g = 0; g < G && ok; ++g, ++qh) {
+                    const int sh = int(qh % uint32_t(HS));
+                    if (!tc::mbar_wait(&full_h[sh], (qh / uint32_t(HS)) & 1u, P.err, 5)) {
+                        ok = false;
+                        break;
+                    }
+                    tc::fence_after_sync();
+                    // K-steps of 32 bytes holding channels of this group (1 or 2)
+                    const int bytes = min(kPerGroup, Cin - g * kPerGroup) * kEsize;
+                    const int nks = (bytes + 31) / 32;
+                    const uint64_t da = tc::desc_kmajor_sw64(tc::smem_u32(sHalo + sh * kHaloStage));
+                    for (int ky = 0; ky < 3 && ok; ++ky) {
+                        uint8_t* slice;
+                        int sw = 0;
+                        if (resident) {
+                            slice = sW + g * Cfg::kGroup + ky * Cfg::kSlice;
+                        } else {
+                            sw = int(qw % uint32_t(WS));
+                            if (!tc::mbar_wait(&full_w[sw], (qw / uint32_t(WS)) & 1u, P.err, 6)) {
+                                ok = false;
+                                break;
+                            }
+                            tc::fence_after_sync();
+                            slice = sW + sw * Cfg::kSlice;
+                        }
+                        const uint64_t db = tc::desc_kmajor_sw64(tc::smem_u32(slice));
+#pragma unroll
+                        for (int kx = 0; kx < 3; ++kx) {
+                            const uint64_t a = da + uint64_t(((ky * kHaloPx + kx) * kRow) >> 4);
+                            const uint64_t bb = db + uint64_t((kx * Cfg::kTap) >> 4);
+                            const uint32_t acc0 = (g | ky | kx) != 0 ? 1u : 0u;
+                            if (FP8) {
+                                tc::mma_e4m3(d, a, bb, idesc, acc0);
+                                if (nks > 1) tc::mma_e4m3(d, a + 2, bb + 2, idesc, 1u);
+                            } else {
+                                tc::mma_bf16(d, a, bb, idesc, acc0);
+                                if (nks > 1) tc::mma_bf16(d, a + 2, bb + 2, idesc, 1u);
+                            }
+                        }
+                        if (!resident) {
+                            tc::mma_commit(&empty_w[sw]);      // the slice is free once these finish
+                            ++qw;
+                        }
+                    }
+                    tc::mma_commit(&empty_h[sh]);              // the halo slot is free once these finish
+                }
+                if (!ok) break;
+                tc::mma_commit(&acc_full[b]);                  // the tile's accumulator is complete
+            }
+            tc::mma_commit(drain);                             // every issued MMA has finished
+        }
+    } else {
+        // ------------------------------------------------------------ epilogue
+        const int qd = warp & 3;
+        int tl = 0;
+        for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++tl) {
+            const int b = tl & 1;
+            if (!tc::mbar_wait(&acc_full[b], (tl >> 1) & 1, P.err, 7)) break;
+            tc::fence_after_sync();
+            const int xt = tile % P.tiles_x, row = tile / P.tiles_x;
+            const int x = xt * kTileM + qd * 32 + lane;
+            const size_t opix = size_t(row) * Wd + x;
+            const uint32_t taddr = tmem + (uint32_t(qd * 32) << 16) + uint32_t(b * Cfg::kAcc);
+#pragma unroll 1
+            for (int c0 = 0; c0 < COUT; c0 += 16) {
+                uint32_t r[16];
+                tc::tmem_ld_x16(taddr + uint32_t(c0), r);
+                tc::tmem_ld_wait();
+                if (x < Wd) {
+                    float v[16];
+#pragma unroll
+                    for (int j = 0; j < 16; j += 4) {
+                        const float4 b4 = P.bias ? __ldg(reinterpret_cast<const float4*>(P.bias + c0 + j))
+                                                 : make_float4(0.f, 0.f, 0.f, 0.f);
+                        v[j] = __uint_as_float(r[j]) * P.acc_scale + b4.x;
+                        v[j + 1] = __uint_as_float(r[j + 1]) * P.acc_scale + b4.y;
+                        v[j + 2] = __uint_as_float(r[j + 2]) * P.acc_scale + b4.z;
+                        v[j + 3] = __uint_as_float(r[j + 3]) * P.acc_scale + b4.w;
+                    }
+                    if (P.relu) {
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) v[j] = fmaxf(v[j], 0.0f);
+                    }
+                    if (FP8) {
+                        uint8_t* dst = reinterpret_cast<uint8_t*>(P.y) + opix * P.ldy + P.coff + c0;
+                        const float s = P.out_inv_scale;
+                        *reinterpret_cast<uint4*>(dst) =
+                            make_uint4(pack_e4m3x4(v[0] * s, v[1] * s, v[2] * s, v[3] * s),
+                                       pack_e4m3x4(v[4] * s, v[5] * s, v[6] * s, v[7] * s),
+                                       pack_e4m3x4(v[8] * s, v[9] * s, v[10] * s, v[11] * s),
+                                       pack_e4m3x4(v[12] * s, v[13] * s, v[14] * s, v[15] * s));
+                    } else {
+                        if (P.mask) {
+                            const __nv_bfloat16* m = P.mask + opix * COUT + c0;
+#pragma unroll
+                            for (int j = 0; j < 16; j += 2) {
+                                const __nv_bfloat162 mm = *reinterpret_cast<const __nv_bfloat162*>(m + j);
+                                if (!(__bfloat162float(mm.x) > 0.0f)) v[j] = 0.0f;
+                                if (!(__bfloat162float(mm.y) > 0.0f)) v[j + 1] = 0.0f;
+                            }
+                        }
+                        uint4* dst = reinterpret_cast<uint4*>(P.y + opix * P.ldy + P.coff + c0);
+                        dst[0] = make_uint4(pack_bf16x2(v[0], v[1]), pack_bf16x2(v[2], v[3]), pack_bf16x2(v[4], v[5]),
+                                            pack_bf16x2(v[6], v[7]));
+                        dst[1] = make_uint4(pack_bf16x2(v[8], v[9]), pack_bf16x2(v[10], v[11]),
+                                            pack_bf16x2(v[12], v[13]), pack_bf16x2(v[14], v[15]));
+                    }
+                }
+            }
+            tc::fence_before_sync();
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(&acc_empty[b]);
+        }
     }
+    if (warp == 1 && lane == 0) tc::mbar_wait_drain(drain, 0);  // before TMEM is released
     tc::fence_before_sync();
     __syncthreads();
     if (warp == 1) tc::tmem_dealloc(tmem, Cfg::kTmemCols);
@@ -184,74 +337,108 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
     return fn;
 }
 
-template <int COUT>
-cudaError_t launch_conv(const CUtensorMap& mx, const CUtensorMap& mw, const ConvArgs& a, cudaStream_t s)
+// x: [NB][H][W][C], halo box {one 64-byte channel group, 130 pixels, 3 rows, 1 image}
+cudaError_t make_halo_map(CUtensorMap* m, const void* x, int NB, int H, int W, int C, bool fp8)
 {
-    using Cfg = ConvCfg<COUT>;
-    cudaError_t e = cudaFuncSetAttribute(k_conv3x3_tc<COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         Cfg::kSmem);
+    auto enc = encode_fn();
+    if (!enc) return cudaErrorNotSupported;
+    const cuuint64_t es = fp8 ? 1 : 2;
+    const cuuint64_t dims[4] = {cuuint64_t(C), cuuint64_t(W), cuuint64_t(H), cuuint64_t(NB)};
+    const cuuint64_t strides[3] = {cuuint64_t(C) * es, cuuint64_t(W) * C * es, cuuint64_t(H) * W * C * es};
+    const cuuint32_t box[4] = {cuuint32_t(kRow / es), cuuint32_t(kHaloPx), 3, 1};
+    const cuuint32_t el[4] = {1, 1, 1, 1};
+    CUresult r = enc(m, fp8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4,
+                     const_cast<void*>(x), dims, strides, box, el, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                     CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+// w: [cout][9][cin] seen as (cin, cout, tap); box {one channel group, cout, 3 taps}
+cudaError_t make_weight_map(CUtensorMap* m, const void* w, int cout, int cin, bool fp8)
+{
+    auto enc = encode_fn();
+    if (!enc) return cudaErrorNotSupported;
+    const cuuint64_t es = fp8 ? 1 : 2;
+    const cuuint64_t dims[3] = {cuuint64_t(cin), cuuint64_t(cout), 9};
+    const cuuint64_t strides[2] = {cuuint64_t(9) * cin * es, cuuint64_t(cin) * es};
+    const cuuint32_t box[3] = {cuuint32_t(kRow / es), cuuint32_t(cout), 3};
+    const cuuint32_t el[3] = {1, 1, 1};
+    CUresult r = enc(m, fp8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3,
+                     const_cast<void*>(w), dims, strides, box, el, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                     CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+int num_sms()
+{
+    static int n = 0;
+    if (!n) {
+        int dev = 0, v = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0)
+            n = v;
+        else
+            n = 1;
+    }
+    return n;
+}
+
+template <int COUT, bool FP8>
+cudaError_t launch_conv(const void* x, const void* w, const ConvArgs& a, cudaStream_t s)
+{
+    constexpr int kPerGroup = FP8 ? 64 : 32;
+    const int G = (a.Cin + kPerGroup - 1) / kPerGroup;
+    const Plan p = make_plan<COUT>(G);
+    if (p.hs < 2 || (!p.resident && p.ws < 2)) return cudaErrorInvalidValue;
+    CUtensorMap mx, mw;
+    cudaError_t e = make_halo_map(&mx, x, a.NB, a.H, a.W, a.Cin, FP8);
     if (e != cudaSuccess) return e;
-    const unsigned tiles = unsigned(a.tiles_x) * unsigned(a.NB) * unsigned(a.H);
-    k_conv3x3_tc<COUT><<<tiles, 192, Cfg::kSmem, s>>>(mx, mw, a);
+    e = make_weight_map(&mw, w, COUT, a.Cin, FP8);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_conv3x3_tc<COUT, FP8>, cudaFuncAttributeMaxDynamicSharedMemorySize, p.smem);
+    if (e != cudaSuccess) return e;
+    const long long tiles = (long long)a.tiles_x * a.NB * a.H;
+    const int grid = int(std::min<long long>(tiles, num_sms()));
+    k_conv3x3_tc<COUT, FP8><<<grid, kThreads, p.smem, s>>>(mx, mw, a, int(tiles), p.hs, p.ws, p.resident);
     return cudaGetLastError();
+}
+
+template <bool FP8>
+cudaError_t dispatch(const void* x, const void* w, int Cout, const ConvArgs& a, cudaStream_t s)
+{
+    switch (Cout) {
+    case 32: return launch_conv<32, FP8>(x, w, a, s);
+    case 48: return launch_conv<48, FP8>(x, w, a, s);
+    case 64: return launch_conv<64, FP8>(x, w, a, s);
+    case 96: return launch_conv<96, FP8>(x, w, a, s);
+    case 128: return launch_conv<128, FP8>(x, w, a, s);
+    case 192: return launch_conv<192, FP8>(x, w, a, s);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 }  // namespace
 
-cudaError_t make_act_map(CUtensorMap* m, const void* x, int NB, int H, int W, int C)
-{
-    auto enc = encode_fn();
-    if (!enc) return cudaErrorNotSupported;
-    const cuuint64_t dims[4] = {cuuint64_t(C), cuuint64_t(W), cuuint64_t(H), cuuint64_t(NB)};
-    const cuuint64_t strides[3] = {cuuint64_t(C) * 2, cuuint64_t(W) * C * 2, cuuint64_t(H) * W * C * 2};
-    const cuuint32_t box[4] = {cuuint32_t(kBlockK), cuuint32_t(kTileM), 1, 1};
-    const cuuint32_t es[4] = {1, 1, 1, 1};
-    CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(x), dims, strides, box, es,
-                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
-}
-
-cudaError_t make_weight_map(CUtensorMap* m, const void* w, int cout, int K)
-{
-    auto enc = encode_fn();
-    if (!enc) return cudaErrorNotSupported;
-    const cuuint64_t dims[2] = {cuuint64_t(K), cuuint64_t(cout)};
-    const cuuint64_t strides[1] = {cuuint64_t(K) * 2};
-    const cuuint32_t box[2] = {cuuint32_t(kBlockK), cuuint32_t(cout)};
-    const cuuint32_t es[2] = {1, 1};
-    CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(w), dims, strides, box, es,
-                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
-}
-
 bool conv_cout_supported(int cout)
 {
-    return cout == 32 || cout == 64 || cout == 96 || cout == 128 || cout == 192;
+    return cout == 32 || cout == 48 || cout == 64 || cout == 96 || cout == 128 || cout == 192;
 }
 
 cudaError_t launch_conv3x3(const void* x, int NB, int H, int W, int Cin, const void* w, int Cout, ConvArgs a,
                            cudaStream_t s)
 {
-    CUtensorMap mx, mw;
-    cudaError_t e = make_act_map(&mx, x, NB, H, W, Cin);
-    if (e != cudaSuccess) return e;
-    e = make_weight_map(&mw, w, Cout, 9 * Cin);
-    if (e != cudaSuccess) return e;
+    const bool fp8 = a.fp8 != 0;
+    if (Cin < 1 || Cin % (fp8 ? 16 : 8) || NB < 1 || H < 1 || W < 1 || !conv_cout_supported(Cout))
+        return cudaErrorInvalidValue;
     a.NB = NB;
     a.H = H;
     a.W = W;
     a.Cin = Cin;
     a.tiles_x = (W + kTileM - 1) / kTileM;
-    switch (Cout) {
-    case 32: return launch_conv<32>(mx, mw, a, s);
-    case 64: return launch_conv<64>(mx, mw, a, s);
-    case 96: return launch_conv<96>(mx, mw, a, s);
-    case 128: return launch_conv<128>(mx, mw, a, s);
-    case 192: return launch_conv<192>(mx, mw, a, s);
-    default: return cudaErrorInvalidValue;
-    }
+    if (a.ldy == 0) a.ldy = Cout;
+    if (a.acc_scale == 0.0f) a.acc_scale = 1.0f;
+    if (a.out_inv_scale == 0.0f) a.out_inv_scale = 1.0f;
+    return fp8 ? dispatch<true>(x, w, Cout, a, s) : dispatch<false>(x, w, Cout, a, s);
 }
 
 }  // namespace fvv

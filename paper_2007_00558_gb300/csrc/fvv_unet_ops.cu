@@ -57,40 +57,84 @@ __global__ void k_pack_features(size_t npx, const uint8_t* __restrict__ rgb, con
     for (int v = 0; v < 4; ++v) dst[v] = make_uint4(w[4 * v], w[4 * v + 1], w[4 * v + 2], w[4 * v + 3]);
 }
 
+// ---- 8-channel vectors: every channel count here is a multiple of 8 ---------
+__device__ __forceinline__ void unpack8(const uint4 q, float f[8])
+{
+    const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const __nv_bfloat162 h = *reinterpret_cast<const __nv_bfloat162*>(&w[j]);
+        f[2 * j] = __bfloat162float(h.x);
+        f[2 * j + 1] = __bfloat162float(h.y);
+    }
+}
+
+__device__ __forceinline__ uint4 pack8(const float f[8])
+{
+    uint32_t w[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(f[2 * j], f[2 * j + 1]);
+        w[j] = *reinterpret_cast<const uint32_t*>(&h);
+    }
+    return make_uint4(w[0], w[1], w[2], w[3]);
+}
+
+__device__ __forceinline__ uint4 ld8(const __nv_bfloat16* p) { return *reinterpret_cast<const uint4*>(p); }
+__device__ __forceinline__ void st8(__nv_bfloat16* p, const uint4 v) { *reinterpret_cast<uint4*>(p) = v; }
+
 // ---- pooling -----------------------------------------------------------------
+// One thread per output pixel and 8 channels.  The first maximum of the 2x2
+// window, in the order (0,0), (0,1), (1,0), (1,1), wins; its position is kept.
 __global__ void k_maxpool2(int B, int H, int W, int C, const __nv_bfloat16* __restrict__ x,
                            __nv_bfloat16* __restrict__ y, uint8_t* __restrict__ arg)
 {
     const size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    const int h2 = H / 2, w2 = W / 2;
-    const size_t n_out = size_t(B) * h2 * w2 * C;
+    const int h2 = H / 2, w2 = W / 2, cv = C >> 3;
+    const size_t n_out = size_t(B) * h2 * w2 * cv;
     if (i >= n_out) return;
-    const int c = int(i % C);
-    size_t r = i / C;
+    const int c = int(i % cv) * 8;
+    size_t r = i / cv;
     const int ox = int(r % w2);
     r /= w2;
     const int oy = int(r % h2);
     const int b = int(r / h2);
     const size_t base = ((size_t(b) * H + 2 * oy) * W + 2 * ox) * C + c;
-    const float v[4] = {bf(x[base]), bf(x[base + C]), bf(x[base + size_t(W) * C]),
-                        bf(x[base + size_t(W) * C + C])};
-    int a = 0;
-    for (int k = 1; k < 4; ++k)
-        if (v[k] > v[a]) a = k;                   // first maximum wins
-    y[i] = x[base + (a & 1) * size_t(C) + (a >> 1) * size_t(W) * C];
-    arg[i] = uint8_t(a);
+    const uint4 q[4] = {ld8(x + base), ld8(x + base + C), ld8(x + base + size_t(W) * C),
+                        ld8(x + base + size_t(W) * C + C)};
+    float v[4][8];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) unpack8(q[k], v[k]);
+    const uint16_t* raw[4] = {reinterpret_cast<const uint16_t*>(&q[0]), reinterpret_cast<const uint16_t*>(&q[1]),
+                              reinterpret_cast<const uint16_t*>(&q[2]), reinterpret_cast<const uint16_t*>(&q[3])};
+    uint16_t outv[8];
+    uint8_t outa[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        int a = 0;
+#pragma unroll
+        for (int k = 1; k < 4; ++k)
+            if (v[k][j] > v[a][j]) a = k;
+        outa[j] = uint8_t(a);
+        outv[j] = a == 0 ? raw[0][j] : a == 1 ? raw[1][j] : a == 2 ? raw[2][j] : raw[3][j];
+    }
+    const size_t o = i * 8;
+    *reinterpret_cast<uint4*>(y + o) = *reinterpret_cast<const uint4*>(outv);
+    *reinterpret_cast<uint2*>(arg + o) = *reinterpret_cast<const uint2*>(outa);
 }
 
-// dx = route(dy by arg) + add, then zero where mask <= 0 (add, mask nullable)
+// dx = route(dy by arg) + add, then zero where mask <= 0 (add, mask nullable);
+// one thread per input pixel and 8 channels
 __global__ void k_maxpool2_bwd(int B, int H, int W, int C, const __nv_bfloat16* __restrict__ dy,
                                const uint8_t* __restrict__ arg, const __nv_bfloat16* __restrict__ add,
                                const __nv_bfloat16* __restrict__ mask, __nv_bfloat16* __restrict__ dx)
 {
     const size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    const size_t n = size_t(B) * H * W * C;
+    const int cv = C >> 3;
+    const size_t n = size_t(B) * H * W * cv;
     if (i >= n) return;
-    const int c = int(i % C);
-    size_t r = i / C;
+    const int c = int(i % cv) * 8;
+    size_t r = i / cv;
     const int x = int(r % W);
     r /= W;
     const int yy = int(r % H);
@@ -98,30 +142,45 @@ __global__ void k_maxpool2_bwd(int B, int H, int W, int C, const __nv_bfloat16* 
     const int h2 = H / 2, w2 = W / 2;
     const size_t j = ((size_t(b) * h2 + yy / 2) * w2 + x / 2) * C + c;
     const int k = (yy & 1) * 2 + (x & 1);
-    float v = arg[j] == k ? bf(dy[j]) : 0.0f;
-    if (add) v += bf(add[i]);
-    if (mask && !(bf(mask[i]) > 0.0f)) v = 0.0f;
-    dx[i] = __float2bfloat16_rn(v);
+    float g[8], ad[8], m[8];
+    unpack8(ld8(dy + j), g);
+    const uint2 av = *reinterpret_cast<const uint2*>(arg + j);
+    const uint8_t* a8 = reinterpret_cast<const uint8_t*>(&av);
+    if (add) unpack8(ld8(add + i * 8), ad);
+    if (mask) unpack8(ld8(mask + i * 8), m);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        float v = a8[q] == k ? g[q] : 0.0f;
+        if (add) v += ad[q];
+        if (mask && !(m[q] > 0.0f)) v = 0.0f;
+        g[q] = v;
+    }
+    st8(dx + i * 8, pack8(g));
 }
 
 // ---- upsampling + concat ------------------------------------------------------
-// cat[b, y, x] = [ up(lo)[b, y, x, 0:C1] | skip[b, y, x, 0:C2] ]
+// cat[b, y, x] = [ up(lo)[b, y, x, 0:C1] | skip[b, y, x, 0:C2] ]; one thread
+// per pixel and 8 channels
 __global__ void k_up2_concat(int B, int H, int W, int C1, int C2, const __nv_bfloat16* __restrict__ lo,
                              const __nv_bfloat16* __restrict__ skip, __nv_bfloat16* __restrict__ cat)
 {
-    const int C = C1 + C2;
+    const int cv = (C1 + C2) >> 3, cv1 = C1 >> 3;
     const size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    const size_t n = size_t(B) * H * W * C;
+    const size_t n = size_t(B) * H * W * cv;
     if (i >= n) return;
-    const int c = int(i % C);
-    const size_t p = i / C;
-    const int x = int(p % W);
-    const int yy = int((p / W) % H);
-    const int b = int(p / (size_t(W) * H));
-    if (c < C1)
-        cat[i] = lo[((size_t(b) * (H / 2) + yy / 2) * (W / 2) + x / 2) * C1 + c];
-    else
-        cat[i] = skip[p * C2 + (c - C1)];
+    const int c = int(i % cv);
+    const size_t p = i / cv;
+    uint4 v;
+    if (c < cv1) {
+        const int x = int(p % W);
+        const size_t r = p / W;
+        const int yy = int(r % H);
+        const int b = int(r / H);
+        v = ld8(lo + ((size_t(b) * (H / 2) + yy / 2) * (W / 2) + x / 2) * C1 + 8 * c);
+    } else {
+        v = ld8(skip + p * C2 + 8 * (c - cv1));
+    }
+    st8(cat + i * 8, v);
 }
 
 // dlo = (sum over each 2x2 block of dcat[..., 0:C1]) * (lo_act > 0); dskip = dcat[..., C1:]
@@ -129,28 +188,36 @@ __global__ void k_up2_concat_bwd(int B, int H, int W, int C1, int C2, const __nv
                                  const __nv_bfloat16* __restrict__ lo_act, __nv_bfloat16* __restrict__ dlo,
                                  __nv_bfloat16* __restrict__ dskip)
 {
-    const int C = C1 + C2;
+    const int C = C1 + C2, cv1 = C1 >> 3, cv2 = C2 >> 3;
     const size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
     const int h2 = H / 2, w2 = W / 2;
-    const size_t n_lo = size_t(B) * h2 * w2 * C1;
-    const size_t n_sk = size_t(B) * H * W * C2;
+    const size_t n_lo = size_t(B) * h2 * w2 * cv1;
+    const size_t n_sk = size_t(B) * H * W * cv2;
     if (i < n_lo) {
-        const int c = int(i % C1);
-        size_t r = i / C1;
+        const int c = int(i % cv1) * 8;
+        size_t r = i / cv1;
         const int x = int(r % w2);
         r /= w2;
         const int yy = int(r % h2);
         const int b = int(r / h2);
         const size_t p00 = (size_t(b) * H + 2 * yy) * W + 2 * x;
-        float v = bf(dcat[p00 * C + c]) + bf(dcat[(p00 + 1) * C + c]) + bf(dcat[(p00 + W) * C + c]) +
-                  bf(dcat[(p00 + W + 1) * C + c]);
-        if (!(bf(lo_act[i]) > 0.0f)) v = 0.0f;
-        dlo[i] = __float2bfloat16_rn(v);
+        float s0[8], s1[8], s2[8], s3[8], a[8];
+        unpack8(ld8(dcat + p00 * C + c), s0);
+        unpack8(ld8(dcat + (p00 + 1) * C + c), s1);
+        unpack8(ld8(dcat + (p00 + W) * C + c), s2);
+        unpack8(ld8(dcat + (p00 + W + 1) * C + c), s3);
+        unpack8(ld8(lo_act + i * 8), a);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const float v = s0[q] + s1[q] + s2[q] + s3[q];
+            s0[q] = a[q] > 0.0f ? v : 0.0f;
+        }
+        st8(dlo + i * 8, pack8(s0));
     }
     if (i < n_sk) {
-        const int c = int(i % C2);
-        const size_t p = i / C2;
-        dskip[i] = dcat[p * C + C1 + c];
+        const int c = int(i % cv2);
+        const size_t p = i / cv2;
+        st8(dskip + i * 8, ld8(dcat + p * C + C1 + 8 * c));
     }
 }
 
@@ -382,7 +449,7 @@ cudaError_t launch_pack_features(size_t npx, const uint8_t* rgb, const float* de
 cudaError_t launch_maxpool2(int B, int H, int W, int C, const __nv_bfloat16* x, __nv_bfloat16* y, uint8_t* arg,
                             cudaStream_t s)
 {
-    const size_t n = size_t(B) * (H / 2) * (W / 2) * C;
+    const size_t n = size_t(B) * (H / 2) * (W / 2) * (C / 8);
     k_maxpool2<<<blocks(n, 256), 256, 0, s>>>(B, H, W, C, x, y, arg);
     return cudaGetLastError();
 }
@@ -391,7 +458,7 @@ cudaError_t launch_maxpool2_bwd(int B, int H, int W, int C, const __nv_bfloat16*
                                 const __nv_bfloat16* add, const __nv_bfloat16* mask, __nv_bfloat16* dx,
                                 cudaStream_t s)
 {
-    const size_t n = size_t(B) * H * W * C;
+    const size_t n = size_t(B) * H * W * (C / 8);
     k_maxpool2_bwd<<<blocks(n, 256), 256, 0, s>>>(B, H, W, C, dy, arg, add, mask, dx);
     return cudaGetLastError();
 }
@@ -399,7 +466,7 @@ cudaError_t launch_maxpool2_bwd(int B, int H, int W, int C, const __nv_bfloat16*
 cudaError_t launch_up2_concat(int B, int H, int W, int C1, int C2, const __nv_bfloat16* lo,
                               const __nv_bfloat16* skip, __nv_bfloat16* cat, cudaStream_t s)
 {
-    const size_t n = size_t(B) * H * W * (C1 + C2);
+    const size_t n = size_t(B) * H * W * ((C1 + C2) / 8);
     k_up2_concat<<<blocks(n, 256), 256, 0, s>>>(B, H, W, C1, C2, lo, skip, cat);
     return cudaGetLastError();
 }
@@ -408,9 +475,8 @@ cudaError_t launch_up2_concat_bwd(int B, int H, int W, int C1, int C2, const __n
                                   const __nv_bfloat16* lo_act, __nv_bfloat16* dlo, __nv_bfloat16* dskip,
                                   cudaStream_t s)
 {
-    const size_t n = size_t(B) * H * W * C2 > size_t(B) * (H / 2) * (W / 2) * C1
-                         ? size_t(B) * H * W * C2
-                         : size_t(B) * (H / 2) * (W / 2) * C1;
+    const size_t n_sk = size_t(B) * H * W * (C2 / 8), n_lo = size_t(B) * (H / 2) * (W / 2) * (C1 / 8);
+    const size_t n = n_sk > n_lo ? n_sk : n_lo;
     k_up2_concat_bwd<<<blocks(n, 256), 256, 0, s>>>(B, H, W, C1, C2, dcat, lo_act, dlo, dskip);
     return cudaGetLastError();
 }

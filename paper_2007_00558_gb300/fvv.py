@@ -141,6 +141,7 @@ def load() -> C.CDLL:
             "fvv_serve_stop": [P],
             "fvv_unet_conv3x3": [P, I, I, I, I, P, P, I, I, P, P, P],
             "fvv_selftest_bounded_wait": [I, C.c_uint32, P],
+            "fvv_unet_conv3x3_e4m3": [P, I, I, I, I, P, P, I, I, C.c_float, C.c_float, P, P],
             "fvv_refine_default_cfg": [C.POINTER(fvv_unet_cfg)],
             "fvv_refine_init": [P, C.POINTER(fvv_unet_cfg)],
             "fvv_refine_param_count": [P, C.POINTER(U64)],
@@ -373,6 +374,13 @@ def fvv_unet_conv3x3(x, n: int, h: int, w: int, cin: int, wt, bias, cout: int, r
                      stream=None) -> None:
     _check(load().fvv_unet_conv3x3(ptr(x), n, h, w, cin, ptr(wt), ptr(bias), cout, 1 if relu else 0,
                                    ptr(mask), ptr(y), stream_handle(stream)), "fvv_unet_conv3x3")
+
+
+def fvv_unet_conv3x3_e4m3(x, n: int, h: int, w: int, cin: int, wt, bias, cout: int, relu: bool,
+                          acc_scale: float, out_inv_scale: float, y, stream=None) -> None:
+    _check(load().fvv_unet_conv3x3_e4m3(ptr(x), n, h, w, cin, ptr(wt), ptr(bias), cout, 1 if relu else 0,
+                                        acc_scale, out_inv_scale, ptr(y), stream_handle(stream)),
+           "fvv_unet_conv3x3_e4m3")
 
 
 def fvv_selftest_bounded_wait(arrive: bool, limit_us: int, stream=None) -> int:

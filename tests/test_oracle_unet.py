@@ -126,3 +126,40 @@ def test_adam_single_step_closed_form():
     U.adam_step(p, g, st, lr=0.1)
     # first bias-corrected step moves by lr * g / (|g| + eps) = lr * sign(g)
     assert np.allclose(p["a"], [1.0 - 0.1, -2.0 + 0.1], atol=1e-6)
+
+
+def test_e4m3_closed_forms():
+    """Values fixed by the format: largest finite 448, smallest subnormal
+    2^-9, ties to the even mantissa, saturation, exact round trip of all 254
+    finite codes."""
+    r = U.e4m3_round
+    assert r(448.0) == 448.0 and r(1e6) == 448.0 and r(-1e6) == -448.0
+    assert r(464.0) == 448.0                       # tie between 448 (m=6) and 480 (not finite): even m=6
+    assert r(2.0 ** -9) == 2.0 ** -9 and r(2.0 ** -10) == 0.0 and r(1.5 * 2.0 ** -9) == 2.0 ** -8
+    assert r(1.0625) == 1.0 and r(1.1875) == 1.25  # ties between mantissas 0|1 and 1|2
+    assert r(1.0624) == 1.0 and r(1.0626) == 1.125
+    assert r(2.0 ** -6) == 2.0 ** -6 and r(0.875 * 2.0 ** -6) == 0.875 * 2.0 ** -6   # normal / subnormal edge
+    assert np.signbit(r(-0.0))
+    codes = np.array([c for c in range(256) if c not in (0x7F, 0xFF)], np.uint8)
+    vals = U.e4m3_decode(codes)
+    assert np.all(np.isfinite(vals)) and vals.max() == 448.0
+    assert np.array_equal(U.e4m3_round(vals), vals)
+    assert np.array_equal(U.e4m3_encode(vals), codes)
+
+
+def test_e4m3_matches_torch_float8():
+    """Rounding and encoding agree byte for byte with PyTorch's float8_e4m3fn
+    conversion (round to nearest even; values beyond 448 are saturated first,
+    since that conversion does not saturate)."""
+    torch = pytest.importorskip("torch")
+    if not hasattr(torch, "float8_e4m3fn"):
+        pytest.skip("no float8_e4m3fn")
+    rng = np.random.default_rng(5)
+    x = np.concatenate([rng.standard_normal(20000) * 10.0, rng.standard_normal(20000) * 0.01,
+                        np.ldexp(rng.random(20000) + 1.0, rng.integers(-12, 9, 20000)) *
+                        np.where(rng.random(20000) < 0.5, -1, 1),
+                        np.arange(-480.0, 480.0, 0.125)])
+    x = np.clip(x, -448.0, 448.0)
+    ref = torch.from_numpy(x.astype(np.float32)).to(torch.float8_e4m3fn)
+    ours = U.e4m3_encode(U.e4m3_round(x.astype(np.float32).astype(np.float64)))
+    assert np.array_equal(ours, ref.view(torch.uint8).numpy())
