@@ -298,7 +298,8 @@ fvv_status fvv_unet_conv3x3_e4m3(const void* x, int32_t n, int32_t h, int32_t w,
  * The 3x3 convolutions and their input gradients run on the tcgen05 tensor
  * cores (bf16 operands, fp32 accumulation); master weights are fp32. */
 typedef struct fvv_unet_cfg {
-    int32_t widths[3];          /* default 32, 64, 128 (multiples of 32) */
+    int32_t widths[3];          /* default 32, 64, 128; each one of 32, 48, 64, 96, 128, 192,
+                                   widths[0] one of 32, 48, 64 */
     uint64_t seed;              /* weight initialisation */
     float z_far;                /* depth normalisation (depth units), default 8000 */
 } fvv_unet_cfg;
@@ -341,6 +342,31 @@ fvv_status fvv_refine_train_step(fvv_ctx* ctx, const fvv_refine_batch* batch, fl
 /* Checkpoint: widths, step, z_far, weights and Adam moments. */
 fvv_status fvv_refine_save(fvv_ctx* ctx, const char* path);
 fvv_status fvv_refine_load(fvv_ctx* ctx, const char* path);
+/* ---- FP8 (E4M3) inference ------------------------------------------------
+ * Post-training quantisation of the trained network.  Every activation
+ * tensor is stored as E4M3 codes with one scale per tensor: the input
+ * features with 2^-8, each 3x3 conv output t with s_t = amax_t / 448, where
+ * amax_t is the largest |value| of t in a bf16 forward pass over `calib`
+ * (act_scales NULL), or s_t = act_scales[t] for the ten conv outputs in layer
+ * order (e1a ... d1b).  Weights get one scale per layer, s_w = amax(W') / 448,
+ * where W' folds the scale ratio of a concatenated input's two parts into the
+ * weights (W' = W s_part / s_first_part per input channel), so one fp32
+ * accumulator multiplier per layer restores real units.  The 3x3 convs run
+ * as fvv_unet_conv3x3_e4m3; pooling and upsampling move codes; the head
+ * dequantises.  After this call fvv_refine_forward and fvv_synthesize_refined
+ * run in E4M3 until fvv_refine_set_precision(FVV_PREC_BF16) or any change of
+ * the weights (init, set, load, a training step), which returns to bf16.
+ * calib: device memory as for fvv_refine_forward (ignored when act_scales is
+ * given).  Waits.  Errors: STATE (no network), INVALID_ARG, TIMEOUT, CUDA. */
+#define FVV_PREC_BF16 0
+#define FVV_PREC_E4M3 1
+fvv_status fvv_refine_quantize(fvv_ctx* ctx, const fvv_refine_batch* calib, const float* act_scales,
+                               void* stream);
+/* FVV_PREC_E4M3 needs quantised weights that are current (else STATE). */
+fvv_status fvv_refine_set_precision(fvv_ctx* ctx, int32_t precision);
+/* *precision, and (if not NULL) the ten activation scales in use. */
+fvv_status fvv_refine_get_precision(fvv_ctx* ctx, int32_t* precision, float* act_scales);
+
 /* Plain synthesis of `view` from the newest complete tick, then the
  * network; out_rgb device or host.  Width and height multiples of 4. */
 fvv_status fvv_synthesize_refined(fvv_ctx* ctx, const fvv_view* view, uint8_t* out_rgb,

@@ -249,3 +249,56 @@ def e4m3_decode(b):
     v = np.where(E == 0, M / 8.0 * 2.0 ** -6, (1.0 + M / 8.0) * np.ldexp(1.0, E - 7))
     v = np.where((E == 15) & (M == 7), np.nan, v)
     return s * v
+
+
+# ---------------------------------------------------------------------------
+# FP8 inference form of the network (post-training quantisation)
+# ---------------------------------------------------------------------------
+CONV_OUTPUTS = ["e1a", "e1b", "e2a", "e2b", "ba", "bb", "d2a", "d2b", "d1a", "d1b"]
+
+
+def activation_scales(cache):
+    """Per-tensor scales amax / 448 of the ten conv outputs of a forward pass
+    (ReLU outputs; a tensor that is all zero gets scale 1)."""
+    out = []
+    for name in CONV_OUTPUTS:
+        a = np.abs(relu(cache[name + ".z"])).max()
+        out.append(a / E4M3_MAX if a > 0 else 1.0)
+    return np.array(out)
+
+
+def forward_e4m3(p, x, rgb, act_scales, s0=2.0 ** -8):
+    """The network with every activation stored as E4M3 codes of one
+    per-tensor scale: the input features at s0, conv output t at
+    act_scales[t].  Layer l with input parts (codes X_j, scale s_j) takes
+    weights W' = W s_j / s_1 on part j's channels, one weight scale
+    s_w = max|W'| / 448 and codes Q = e4m3(W' / s_w); its output codes are
+    e4m3(relu(s_1 s_w conv(X, Q) + b) / s_out).  Max pooling and upsampling
+    move codes; the head uses the dequantised last activation.
+    Returns the clamped prediction."""
+    S = dict(zip(CONV_OUTPUTS, act_scales))
+
+    def layer(name, parts, s_out):
+        xq = np.concatenate([c for c, _ in parts], axis=3)
+        f = np.concatenate([np.full(c.shape[3], s / parts[0][1]) for c, s in parts])
+        wp = p[name + ".w"] * f
+        s_w = np.abs(wp).max() / E4M3_MAX
+        s_w = s_w if s_w > 0 else 1.0
+        acc = conv3x3(xq, e4m3_round(wp / s_w), np.zeros(wp.shape[0]))
+        return e4m3_round(relu(acc * (parts[0][1] * s_w) + p[name + ".b"]) / s_out)
+
+    X0 = e4m3_round(x / s0)
+    e1a = layer("e1a", [(X0, s0)], S["e1a"])
+    e1 = layer("e1b", [(e1a, S["e1a"])], S["e1b"])
+    p1, _ = maxpool2(e1)
+    e2a = layer("e2a", [(p1, S["e1b"])], S["e2a"])
+    e2 = layer("e2b", [(e2a, S["e2a"])], S["e2b"])
+    p2, _ = maxpool2(e2)
+    ba = layer("ba", [(p2, S["e2b"])], S["ba"])
+    bt = layer("bb", [(ba, S["ba"])], S["bb"])
+    d2a = layer("d2a", [(up2(bt), S["bb"]), (e2, S["e2b"])], S["d2a"])
+    d2 = layer("d2b", [(d2a, S["d2a"])], S["d2b"])
+    d1a = layer("d1a", [(up2(d2), S["d2b"]), (e1, S["e1b"])], S["d1a"])
+    d1 = layer("d1b", [(d1a, S["d1a"])], S["d1b"])
+    res = conv1x1(d1 * S["d1b"], p["out.w"], p["out.b"])
+    return np.clip(rgb + res, 0.0, 1.0)

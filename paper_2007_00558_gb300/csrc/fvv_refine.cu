@@ -12,6 +12,7 @@
 // upsampling; mean-squared error against the held-out camera; Adam.
 // Master weights, gradients and Adam moments are fp32; activations and
 // activation gradients are bf16 (NHWC); GEMM accumulation is fp32.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -19,6 +20,8 @@
 #include <random>
 #include <string>
 #include <vector>
+
+#include <cuda_fp8.h>
 
 #include "fvv_runtime.h"
 #include "fvv_unet.h"
@@ -61,7 +64,6 @@ fvv_status check_flag(int* flag, cudaStream_t s, const char* what)
 
 bool on_device(const void* p) { return p && mem_kind(p) == MemKind::Device; }
 
-int round32(int c) { return (c + 31) / 32 * 32; }
 
 }  // namespace
 
@@ -70,6 +72,10 @@ struct ConvLayer {
     float *w = nullptr, *b = nullptr, *gw = nullptr, *gb = nullptr;
     float *mw = nullptr, *vw = nullptr, *mb = nullptr, *vb = nullptr;
     __nv_bfloat16 *wbf = nullptr, *wt = nullptr;
+    // e4m3 inference: codes [cout][9][cin_q] (cin_q = cin rounded up to 16), scales
+    uint8_t* wq = nullptr;
+    int cin_q = 0;
+    float acc_scale = 1.0f, out_inv_scale = 1.0f;
     size_t nw() const { return size_t(cout) * 9 * cin; }
 };
 
@@ -89,6 +95,17 @@ struct RefineNet {
     __nv_bfloat16 *g_d1b, *g_d1a, *g_cat1, *g_skip1, *g_d2b, *g_d2a, *g_cat2, *g_skip2, *g_bb, *g_ba, *g_p2,
         *g_e2b, *g_e2a, *g_p1, *g_e1b, *g_e1a;
     float* loss = nullptr;
+    // e4m3 inference: per-tensor scales of the ten conv outputs, the input
+    // scale, and e4m3 activations for (qB, qH, qW)
+    int precision = FVV_PREC_BF16;
+    bool q_ready = false;
+    float s_act[10] = {};
+    float s0 = 1.0f / 256.0f;
+    float* amax = nullptr;
+    int qB = 0, qH = 0, qW = 0;
+    std::vector<std::pair<void*, size_t>> acts8;
+    uint8_t *q_x0, *q_e1a, *q_e1, *q_p1, *q_e2a, *q_e2, *q_p2, *q_ba, *q_bt, *q_cat2, *q_d2a, *q_d2, *q_cat1, *q_d1a,
+        *q_d1;
     // plain-synthesis outputs feeding fvv_synthesize_refined
     int sH = 0, sW = 0;
     std::vector<std::pair<void*, size_t>> syn;
@@ -97,8 +114,6 @@ struct RefineNet {
 };
 
 namespace {
-
-const char* const kLayerName[10] = {"e1a", "e1b", "e2a", "e2b", "ba", "bb", "d2a", "d2b", "d1a", "d1b"};
 
 fvv_status alloc_into(fvv_ctx* c, std::vector<std::pair<void*, size_t>>& list, void** p, size_t bytes)
 {
@@ -179,6 +194,8 @@ fvv_status get_flat(RefineNet& N, Buf which, float* out)
 
 fvv_status refresh_weights(RefineNet& N, cudaStream_t s)
 {
+    N.q_ready = false;                        // e4m3 weights are stale
+    N.precision = FVV_PREC_BF16;
     for (ConvLayer& l : N.L)
         FVV_CUDA(launch_flip_weights(l.cout, l.cin, l.w, l.wbf, l.wt, s));
     return FVV_OK;
@@ -218,7 +235,7 @@ fvv_status ensure_acts(fvv_ctx* c, RefineNet& N, int B, int H, int W)
     const size_t p1 = size_t(B) * H * W, p2 = p1 / 4, p3 = p1 / 16;
     const int w1 = N.L[1].cout, w2 = N.L[3].cout, w3 = N.L[5].cout;
     auto A = [&](__nv_bfloat16** p, size_t n) { return alloc_t(c, N.acts, p, n); };
-    FVV_TRY(A(&N.x0, p1 * 32));
+    FVV_TRY(A(&N.x0, p1 * 8));
     FVV_TRY(A(&N.e1a, p1 * w1));
     FVV_TRY(A(&N.e1, p1 * w1));
     FVV_TRY(A(&N.p1, p2 * w1));
@@ -270,19 +287,29 @@ fvv_status conv(const ConvLayer& l, const __nv_bfloat16* x, int B, int H, int W,
     return FVV_OK;
 }
 
-// weight and bias gradients of layer l, and its input gradient (masked)
+// weight and bias gradients of layer l, and its input gradient (masked).  The
+// input gradient is the convolution of dz with the flipped weights
+// wt[ci][ky][kx][co]; for a concatenated input (split > 0) it runs once per
+// part, ci in [0, split) and [split, cin), into channel slices of dx.
 fvv_status conv_bwd(const ConvLayer& l, const __nv_bfloat16* x, const __nv_bfloat16* dz, int B, int H, int W,
-                    __nv_bfloat16* dx, const __nv_bfloat16* mask, int* err, cudaStream_t s)
+                    __nv_bfloat16* dx, const __nv_bfloat16* mask, int* err, cudaStream_t s, int split = 0)
 {
     FVV_CUDA(launch_wgrad3x3(B, H, W, l.cin, l.cout, x, dz, l.gw, s));
     FVV_CUDA(launch_bias_grad(size_t(B) * H * W, l.cout, dz, l.gb, s));
     if (dx) {
-        ConvArgs a{};
-        a.y = dx;
-        a.relu = 0;
-        a.mask = mask;
-        a.err = err;
-        FVV_CUDA(launch_conv3x3(dz, B, H, W, l.cout, l.wt, l.cin, a, s));
+        const int parts = split > 0 ? 2 : 1;
+        for (int p = 0; p < parts; ++p) {
+            const int c0 = p == 0 ? 0 : split;
+            const int n = parts == 1 ? l.cin : (p == 0 ? split : l.cin - split);
+            ConvArgs a{};
+            a.y = dx;
+            a.ldy = l.cin;
+            a.coff = c0;
+            a.relu = 0;
+            a.mask = parts == 1 ? mask : nullptr;
+            a.err = err;
+            FVV_CUDA(launch_conv3x3(dz, B, H, W, l.cout, l.wt + size_t(c0) * 9 * l.cout, n, a, s));
+        }
     }
     return FVV_OK;
 }
@@ -309,7 +336,7 @@ fvv_status forward(RefineNet& N, const fvv_refine_batch& b, int* err, cudaStream
     FVV_CUDA(launch_up2_concat(B, H, W, w2, w1, N.d2, N.e1, N.cat1, s));
     FVV_TRY(conv(N.L[8], N.cat1, B, H, W, N.d1a, err, s));
     FVV_TRY(conv(N.L[9], N.d1a, B, H, W, N.d1, err, s));
-    FVV_CUDA(launch_head_fwd(npx, N.d1, N.wout, N.bout, b.rgb, N.s, out, W, out_pitch, out_f32, s));
+    FVV_CUDA(launch_head_fwd(npx, w1, N.d1, N.wout, N.bout, b.rgb, N.s, out, W, out_pitch, out_f32, s));
     return FVV_OK;
 }
 
@@ -326,12 +353,12 @@ fvv_status backward(RefineNet& N, const fvv_refine_batch& b, int* err, cudaStrea
     FVV_CUDA(cudaMemsetAsync(N.gwout, 0, size_t(3) * N.w1 * 4, s));
     FVV_CUDA(cudaMemsetAsync(N.gbout, 0, 3 * 4, s));
     FVV_CUDA(cudaMemsetAsync(N.loss, 0, 4, s));
-    FVV_CUDA(launch_head_bwd(npx, N.d1, N.wout, N.s, b.target, N.loss, N.gwout, N.gbout, N.g_d1b, s));
+    FVV_CUDA(launch_head_bwd(npx, w1, N.d1, N.wout, N.s, b.target, N.loss, N.gwout, N.gbout, N.g_d1b, s));
     FVV_TRY(conv_bwd(N.L[9], N.d1a, N.g_d1b, B, H, W, N.g_d1a, N.d1a, err, s));
-    FVV_TRY(conv_bwd(N.L[8], N.cat1, N.g_d1a, B, H, W, N.g_cat1, nullptr, err, s));
+    FVV_TRY(conv_bwd(N.L[8], N.cat1, N.g_d1a, B, H, W, N.g_cat1, nullptr, err, s, w2));
     FVV_CUDA(launch_up2_concat_bwd(B, H, W, w2, w1, N.g_cat1, N.d2, N.g_d2b, N.g_skip1, s));
     FVV_TRY(conv_bwd(N.L[7], N.d2a, N.g_d2b, B, H2, W2, N.g_d2a, N.d2a, err, s));
-    FVV_TRY(conv_bwd(N.L[6], N.cat2, N.g_d2a, B, H2, W2, N.g_cat2, nullptr, err, s));
+    FVV_TRY(conv_bwd(N.L[6], N.cat2, N.g_d2a, B, H2, W2, N.g_cat2, nullptr, err, s, w3));
     FVV_CUDA(launch_up2_concat_bwd(B, H2, W2, w3, w2, N.g_cat2, N.bt, N.g_bb, N.g_skip2, s));
     FVV_TRY(conv_bwd(N.L[5], N.ba, N.g_bb, B, H4, W4, N.g_ba, N.ba, err, s));
     FVV_TRY(conv_bwd(N.L[4], N.p2, N.g_ba, B, H4, W4, N.g_p2, nullptr, err, s));
@@ -341,6 +368,134 @@ fvv_status backward(RefineNet& N, const fvv_refine_batch& b, int* err, cudaStrea
     FVV_CUDA(launch_maxpool2_bwd(B, H, W, w1, N.g_p1, N.arg1, N.g_skip1, N.e1, N.g_e1b, s));
     FVV_TRY(conv_bwd(N.L[1], N.e1a, N.g_e1b, B, H, W, N.g_e1a, N.e1a, err, s));
     FVV_TRY(conv_bwd(N.L[0], N.x0, N.g_e1a, B, H, W, nullptr, nullptr, err, s));
+    return FVV_OK;
+}
+
+fvv_status ensure_acts8(fvv_ctx* c, RefineNet& N, int B, int H, int W)
+{
+    if (N.qB == B && N.qH == H && N.qW == W) return FVV_OK;
+    FVV_CUDA(cudaDeviceSynchronize());
+    free_list(c, N.acts8);
+    N.qB = N.qH = N.qW = 0;
+    const size_t p1 = size_t(B) * H * W, p2 = p1 / 4, p3 = p1 / 16;
+    const int w1 = N.L[1].cout, w2 = N.L[3].cout, w3 = N.L[5].cout;
+    auto A = [&](uint8_t** p, size_t n) { return alloc_t(c, N.acts8, p, n); };
+    FVV_TRY(A(&N.q_x0, p1 * 16));
+    FVV_TRY(A(&N.q_e1a, p1 * w1));
+    FVV_TRY(A(&N.q_e1, p1 * w1));
+    FVV_TRY(A(&N.q_p1, p2 * w1));
+    FVV_TRY(A(&N.q_e2a, p2 * w2));
+    FVV_TRY(A(&N.q_e2, p2 * w2));
+    FVV_TRY(A(&N.q_p2, p3 * w2));
+    FVV_TRY(A(&N.q_ba, p3 * w3));
+    FVV_TRY(A(&N.q_bt, p3 * w3));
+    FVV_TRY(A(&N.q_cat2, p2 * (w3 + w2)));
+    FVV_TRY(A(&N.q_d2a, p2 * w2));
+    FVV_TRY(A(&N.q_d2, p2 * w2));
+    FVV_TRY(A(&N.q_cat1, p1 * (w2 + w1)));
+    FVV_TRY(A(&N.q_d1a, p1 * w1));
+    FVV_TRY(A(&N.q_d1, p1 * w1));
+    N.qB = B;
+    N.qH = H;
+    N.qW = W;
+    return FVV_OK;
+}
+
+fvv_status conv_e4m3(const ConvLayer& l, const uint8_t* x, int B, int H, int W, uint8_t* y, int* err,
+                     cudaStream_t s)
+{
+    ConvArgs a{};
+    a.bias = l.b;
+    a.y = reinterpret_cast<__nv_bfloat16*>(y);
+    a.relu = 1;
+    a.fp8 = 1;
+    a.acc_scale = l.acc_scale;
+    a.out_inv_scale = l.out_inv_scale;
+    a.err = err;
+    FVV_CUDA(launch_conv3x3(x, B, H, W, l.cin_q, l.wq, l.cout, a, s));
+    return FVV_OK;
+}
+
+// The forward pass on e4m3 codes (weights and scales from quantize()).
+fvv_status forward_e4m3(RefineNet& N, const fvv_refine_batch& b, int* err, cudaStream_t s, uint8_t* out,
+                        size_t out_pitch, float* out_f32)
+{
+    const int B = b.n, H = b.height, W = b.width;
+    const size_t npx = size_t(B) * H * W;
+    const int H2 = H / 2, W2 = W / 2, H4 = H / 4, W4 = W / 4;
+    const int w1 = N.L[1].cout, w2 = N.L[3].cout, w3 = N.L[5].cout;
+    FVV_CUDA(launch_pack_features_e4m3(npx, b.rgb, b.depth, b.hole, b.top3, N.z_far, N.s0, N.q_x0, s));
+    FVV_TRY(conv_e4m3(N.L[0], N.q_x0, B, H, W, N.q_e1a, err, s));
+    FVV_TRY(conv_e4m3(N.L[1], N.q_e1a, B, H, W, N.q_e1, err, s));
+    FVV_CUDA(launch_maxpool2_e4m3(B, H, W, w1, N.q_e1, N.q_p1, s));
+    FVV_TRY(conv_e4m3(N.L[2], N.q_p1, B, H2, W2, N.q_e2a, err, s));
+    FVV_TRY(conv_e4m3(N.L[3], N.q_e2a, B, H2, W2, N.q_e2, err, s));
+    FVV_CUDA(launch_maxpool2_e4m3(B, H2, W2, w2, N.q_e2, N.q_p2, s));
+    FVV_TRY(conv_e4m3(N.L[4], N.q_p2, B, H4, W4, N.q_ba, err, s));
+    FVV_TRY(conv_e4m3(N.L[5], N.q_ba, B, H4, W4, N.q_bt, err, s));
+    FVV_CUDA(launch_up2_concat_e4m3(B, H2, W2, w3, w2, N.q_bt, N.q_e2, N.q_cat2, s));
+    FVV_TRY(conv_e4m3(N.L[6], N.q_cat2, B, H2, W2, N.q_d2a, err, s));
+    FVV_TRY(conv_e4m3(N.L[7], N.q_d2a, B, H2, W2, N.q_d2, err, s));
+    FVV_CUDA(launch_up2_concat_e4m3(B, H, W, w2, w1, N.q_d2, N.q_e1, N.q_cat1, s));
+    FVV_TRY(conv_e4m3(N.L[8], N.q_cat1, B, H, W, N.q_d1a, err, s));
+    FVV_TRY(conv_e4m3(N.L[9], N.q_d1a, B, H, W, N.q_d1, err, s));
+    FVV_CUDA(launch_head_fwd_e4m3(npx, w1, N.q_d1, N.s_act[9], N.wout, N.bout, b.rgb, out, W, out_pitch, out_f32,
+                                  s));
+    return FVV_OK;
+}
+
+// Scales of the input parts of layer i: {scale, channels} in channel order.
+int input_parts(const RefineNet& N, int i, float sc[2], int ch[2])
+{
+    const int w1 = N.L[1].cout, w2 = N.L[3].cout, w3 = N.L[5].cout;
+    const float* a = N.s_act;
+    switch (i) {
+    case 0: sc[0] = N.s0; ch[0] = 8; return 1;
+    case 1: sc[0] = a[0]; ch[0] = w1; return 1;
+    case 2: sc[0] = a[1]; ch[0] = w1; return 1;       // max pooling keeps e1b's scale
+    case 3: sc[0] = a[2]; ch[0] = w2; return 1;
+    case 4: sc[0] = a[3]; ch[0] = w2; return 1;
+    case 5: sc[0] = a[4]; ch[0] = w3; return 1;
+    case 6: sc[0] = a[5]; ch[0] = w3; sc[1] = a[3]; ch[1] = w2; return 2;    // [up(bb) | e2b]
+    case 7: sc[0] = a[6]; ch[0] = w2; return 1;
+    case 8: sc[0] = a[7]; ch[0] = w2; sc[1] = a[1]; ch[1] = w1; return 2;    // [up(d2b) | e1b]
+    default: sc[0] = a[8]; ch[0] = w1; return 1;
+    }
+}
+
+// e4m3 weight codes and multipliers of every layer from the fp32 masters and
+// the activation scales in N.s_act (host arithmetic, one pass per quantisation).
+fvv_status quantize_weights(RefineNet& N, cudaStream_t s)
+{
+    std::vector<float> w;
+    std::vector<uint8_t> q;
+    for (int i = 0; i < 10; ++i) {
+        ConvLayer& l = N.L[i];
+        w.resize(l.nw());
+        FVV_CUDA(cudaMemcpy(w.data(), l.w, l.nw() * 4, cudaMemcpyDeviceToHost));
+        float sc[2] = {1.0f, 1.0f};
+        int ch[2] = {l.cin, 0};
+        const int np = input_parts(N, i, sc, ch);
+        std::vector<float> f(l.cin, 1.0f);            // per input channel: s_part / s_first_part
+        if (np == 2)
+            for (int c = ch[0]; c < l.cin; ++c) f[c] = sc[1] / sc[0];
+        float amax = 0.0f;
+        for (int co = 0; co < l.cout; ++co)
+            for (int t = 0; t < 9; ++t)
+                for (int ci = 0; ci < l.cin; ++ci)
+                    amax = std::max(amax, std::fabs(w[(size_t(co) * 9 + t) * l.cin + ci] * f[ci]));
+        const float sw = amax > 0.0f ? amax / 448.0f : 1.0f;
+        q.assign(size_t(l.cout) * 9 * l.cin_q, 0);
+        for (int co = 0; co < l.cout; ++co)
+            for (int t = 0; t < 9; ++t)
+                for (int ci = 0; ci < l.cin; ++ci)
+                    q[(size_t(co) * 9 + t) * l.cin_q + ci] = uint8_t(__nv_cvt_float_to_fp8(
+                        w[(size_t(co) * 9 + t) * l.cin + ci] * f[ci] / sw, __NV_SATFINITE, __NV_E4M3));
+        FVV_CUDA(cudaMemcpyAsync(l.wq, q.data(), q.size(), cudaMemcpyHostToDevice, s));
+        FVV_CUDA(cudaStreamSynchronize(s));
+        l.acc_scale = sc[0] * sw;
+        l.out_inv_scale = 1.0f / N.s_act[i];
+    }
     return FVV_OK;
 }
 
@@ -378,6 +533,7 @@ void refine_destroy(fvv_ctx* c)
     if (!N) return;
     cudaDeviceSynchronize();
     free_list(c, N->acts);
+    free_list(c, N->acts8);
     free_list(c, N->syn);
     free_list(c, N->params);
     delete N;
@@ -470,18 +626,14 @@ fvv_status fvv_refine_init(fvv_ctx* c, const fvv_unet_cfg* cfg_in)
     if (!c) return fail(FVV_ERR_INVALID_ARG, "ctx is NULL");
     fvv_unet_cfg cfg;
     if (cfg_in) cfg = *cfg_in; else fvv_refine_default_cfg(&cfg);
+    // every forward output width and every part of every input gradient is a
+    // supported conv width; the head takes w1 in {32, 48, 64}
     for (int i = 0; i < 3; ++i)
-        if (cfg.widths[i] < 32 || cfg.widths[i] % 32 || cfg.widths[i] > 128)
-            return fail(FVV_ERR_INVALID_ARG, "widths must be multiples of 32 in [32, 128]");
+        if (!fvv::conv_cout_supported(cfg.widths[i]))
+            return fail(FVV_ERR_INVALID_ARG, "widths must each be 32, 48, 64, 96, 128 or 192");
+    if (!fvv::head_width_supported(cfg.widths[0]))
+        return fail(FVV_ERR_INVALID_ARG, "the first width must be 32, 48 or 64");
     if (!(cfg.z_far > 0.0f)) return fail(FVV_ERR_INVALID_ARG, "z_far must be > 0");
-    {
-        // every input-gradient convolution has N = that layer's input width
-        const int a = cfg.widths[0], b = cfg.widths[1], d = cfg.widths[2];
-        const int dg[9] = {a, a, b, b, d, d + b, b, b + a, a};
-        for (int v : dg)
-            if (!fvv::conv_cout_supported(v))
-                return fail(FVV_ERR_INVALID_ARG, "unsupported widths (layer inputs must be 32, 64, 96, 128 or 192)");
-    }
     std::lock_guard<std::recursive_mutex> g(c->mu);
     FVV_CUDA(cudaSetDevice(c->device));
     fvv::refine_destroy(c);
@@ -500,18 +652,21 @@ fvv_status fvv_refine_init(fvv_ctx* c, const fvv_unet_cfg* cfg_in)
     for (int i = 0; i < 10 && rc == FVV_OK; ++i) {
         fvv::ConvLayer& l = N->L[i];
         l.cin_true = cins[i];
-        l.cin = fvv::round32(cins[i]);
+        l.cin = cins[i];
+        l.cin_q = (cins[i] + 15) / 16 * 16;
         l.cout = couts[i];
         const size_t nw = l.nw();
         if ((rc = P(&l.w, nw)) || (rc = P(&l.gw, nw)) || (rc = P(&l.mw, nw)) || (rc = P(&l.vw, nw)) ||
             (rc = P(&l.b, l.cout)) || (rc = P(&l.gb, l.cout)) || (rc = P(&l.mb, l.cout)) ||
-            (rc = P(&l.vb, l.cout)) || (rc = PB(&l.wbf, nw)) || (rc = PB(&l.wt, nw)))
+            (rc = P(&l.vb, l.cout)) || (rc = PB(&l.wbf, nw)) || (rc = PB(&l.wt, nw)) ||
+            (rc = fvv::alloc_t(c, N->params, &l.wq, size_t(l.cout) * 9 * l.cin_q)))
             break;
     }
     if (rc == FVV_OK) {
-        float** hp[9] = {&N->wout, &N->bout, &N->gwout, &N->gbout, &N->mwo, &N->vwo, &N->mbo, &N->vbo, &N->loss};
-        const size_t hn[9] = {3 * size_t(w1), 3, 3 * size_t(w1), 3, 3 * size_t(w1), 3 * size_t(w1), 3, 3, 1};
-        for (int i = 0; i < 9 && rc == FVV_OK; ++i) rc = P(hp[i], hn[i]);
+        float** hp[10] = {&N->wout, &N->bout, &N->gwout, &N->gbout, &N->mwo,
+                          &N->vwo,  &N->mbo,  &N->vbo,   &N->loss,  &N->amax};
+        const size_t hn[10] = {3 * size_t(w1), 3, 3 * size_t(w1), 3, 3 * size_t(w1), 3 * size_t(w1), 3, 3, 1, 10};
+        for (int i = 0; i < 10 && rc == FVV_OK; ++i) rc = P(hp[i], hn[i]);
     }
     if (rc != FVV_OK) {
         std::string msg = fvv_last_error();
@@ -579,9 +734,77 @@ fvv_status fvv_refine_forward(fvv_ctx* c, const fvv_refine_batch* b, uint8_t* ou
     std::lock_guard<std::recursive_mutex> g(c->mu);
     int* err = nullptr;
     FVV_TRY(fvv::device_flag(&err));
-    FVV_TRY(fvv::ensure_acts(c, *N, b->n, b->height, b->width));
-    FVV_TRY(fvv::forward(*N, *b, err, s, out_rgb, size_t(b->width) * 3, out_f32));
+    if (N->precision == FVV_PREC_E4M3) {
+        FVV_TRY(fvv::ensure_acts8(c, *N, b->n, b->height, b->width));
+        FVV_TRY(fvv::forward_e4m3(*N, *b, err, s, out_rgb, size_t(b->width) * 3, out_f32));
+    } else {
+        FVV_TRY(fvv::ensure_acts(c, *N, b->n, b->height, b->width));
+        FVV_TRY(fvv::forward(*N, *b, err, s, out_rgb, size_t(b->width) * 3, out_f32));
+    }
     return fvv::check_flag(err, s, "fvv_refine_forward");
+}
+
+fvv_status fvv_refine_quantize(fvv_ctx* c, const fvv_refine_batch* calib, const float* act_scales, void* stream)
+{
+    RefineNet* N = fvv::net_of(c);
+    if (!N) return fail(FVV_ERR_STATE, "refinement network not initialised");
+    cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : c->own;
+    std::lock_guard<std::recursive_mutex> g(c->mu);
+    float sc[10];
+    if (act_scales) {
+        for (int i = 0; i < 10; ++i) {
+            if (!(act_scales[i] > 0.0f) || !std::isfinite(act_scales[i]))
+                return fail(FVV_ERR_INVALID_ARG, "activation scales must be finite and > 0");
+            sc[i] = act_scales[i];
+        }
+    } else {
+        FVV_TRY(fvv::check_batch(*N, calib, false));
+        int* err = nullptr;
+        FVV_TRY(fvv::device_flag(&err));
+        FVV_TRY(fvv::ensure_acts(c, *N, calib->n, calib->height, calib->width));
+        FVV_TRY(fvv::forward(*N, *calib, err, s, nullptr, 0, nullptr));
+        FVV_TRY(fvv::check_flag(err, s, "fvv_refine_quantize"));
+        const size_t p1 = size_t(calib->n) * calib->height * calib->width, p2 = p1 / 4, p3 = p1 / 16;
+        const __nv_bfloat16* t[10] = {N->e1a, N->e1, N->e2a, N->e2, N->ba, N->bt, N->d2a, N->d2, N->d1a, N->d1};
+        const size_t np[10] = {p1, p1, p2, p2, p3, p3, p2, p2, p1, p1};
+        FVV_CUDA(cudaMemsetAsync(N->amax, 0, 10 * sizeof(float), s));
+        for (int i = 0; i < 10; ++i)
+            FVV_CUDA(fvv::launch_amax(np[i] * N->L[i].cout, t[i], N->amax + i, s));
+        float am[10];
+        FVV_CUDA(cudaMemcpyAsync(am, N->amax, sizeof am, cudaMemcpyDeviceToHost, s));
+        FVV_CUDA(cudaStreamSynchronize(s));
+        for (int i = 0; i < 10; ++i) sc[i] = am[i] > 0.0f && std::isfinite(am[i]) ? am[i] / 448.0f : 1.0f;
+    }
+    for (int i = 0; i < 10; ++i) N->s_act[i] = sc[i];
+    FVV_TRY(fvv::quantize_weights(*N, s));
+    N->q_ready = true;
+    N->precision = FVV_PREC_E4M3;
+    return FVV_OK;
+}
+
+fvv_status fvv_refine_set_precision(fvv_ctx* c, int32_t precision)
+{
+    RefineNet* N = fvv::net_of(c);
+    if (!N) return fail(FVV_ERR_STATE, "refinement network not initialised");
+    if (precision != FVV_PREC_BF16 && precision != FVV_PREC_E4M3)
+        return fail(FVV_ERR_INVALID_ARG, "precision must be FVV_PREC_BF16 or FVV_PREC_E4M3");
+    std::lock_guard<std::recursive_mutex> g(c->mu);
+    if (precision == FVV_PREC_E4M3 && !N->q_ready)
+        return fail(FVV_ERR_STATE, "no current e4m3 weights: call fvv_refine_quantize");
+    N->precision = precision;
+    return FVV_OK;
+}
+
+fvv_status fvv_refine_get_precision(fvv_ctx* c, int32_t* precision, float* act_scales)
+{
+    RefineNet* N = fvv::net_of(c);
+    if (!N) return fail(FVV_ERR_STATE, "refinement network not initialised");
+    if (!precision) return fail(FVV_ERR_INVALID_ARG, "precision is NULL");
+    std::lock_guard<std::recursive_mutex> g(c->mu);
+    *precision = N->precision;
+    if (act_scales)
+        for (int i = 0; i < 10; ++i) act_scales[i] = N->s_act[i];
+    return FVV_OK;
 }
 
 fvv_status fvv_refine_train_step(fvv_ctx* c, const fvv_refine_batch* b, float lr, float* loss, void* stream)
@@ -709,10 +932,16 @@ fvv_status fvv_synthesize_refined(fvv_ctx* c, const fvv_view* view, uint8_t* out
     b.top3 = N->syn_top3;
     int* err = nullptr;
     FVV_TRY(fvv::device_flag(&err));
-    FVV_TRY(fvv::ensure_acts(c, *N, 1, H, W));
     const bool dev_out = fvv::mem_kind(out_rgb) == fvv::MemKind::Device;
-    FVV_TRY(fvv::forward(*N, b, err, s, dev_out ? out_rgb : N->syn_out, dev_out ? out_pitch : size_t(W) * 3,
-                         nullptr));
+    if (N->precision == FVV_PREC_E4M3) {
+        FVV_TRY(fvv::ensure_acts8(c, *N, 1, H, W));
+        FVV_TRY(fvv::forward_e4m3(*N, b, err, s, dev_out ? out_rgb : N->syn_out,
+                                  dev_out ? out_pitch : size_t(W) * 3, nullptr));
+    } else {
+        FVV_TRY(fvv::ensure_acts(c, *N, 1, H, W));
+        FVV_TRY(fvv::forward(*N, b, err, s, dev_out ? out_rgb : N->syn_out, dev_out ? out_pitch : size_t(W) * 3,
+                             nullptr));
+    }
     if (!dev_out)
         FVV_CUDA(cudaMemcpy2DAsync(out_rgb, out_pitch, N->syn_out, size_t(W) * 3, size_t(W) * 3, size_t(H),
                                    cudaMemcpyDeviceToHost, s));

@@ -45,12 +45,23 @@ cudaError_t launch_up2_concat(int B, int H, int W, int C1, int C2, const __nv_bf
 cudaError_t launch_up2_concat_bwd(int B, int H, int W, int C1, int C2, const __nv_bfloat16* dcat,
                                   const __nv_bfloat16* lo_act, __nv_bfloat16* dlo, __nv_bfloat16* dskip,
                                   cudaStream_t s);
-cudaError_t launch_head_fwd(size_t npx, const __nv_bfloat16* d1, const float* wout, const float* bout,
+bool head_width_supported(int c1);              // w1 of the 1x1 head: 32, 48 or 64
+cudaError_t launch_head_fwd(size_t npx, int C1, const __nv_bfloat16* d1, const float* wout, const float* bout,
                             const uint8_t* rgb, float* sbuf, uint8_t* out, int W, size_t out_pitch,
                             float* out_f32, cudaStream_t s);
-cudaError_t launch_head_bwd(size_t npx, const __nv_bfloat16* d1, const float* wout, const float* sbuf,
+cudaError_t launch_head_bwd(size_t npx, int C1, const __nv_bfloat16* d1, const float* wout, const float* sbuf,
                             const uint8_t* target, float* loss, float* dwout, float* dbout, __nv_bfloat16* dd1,
                             cudaStream_t s);
+// e4m3 inference forms: activations are e4m3 codes with per-tensor scales
+cudaError_t launch_pack_features_e4m3(size_t npx, const uint8_t* rgb, const float* depth, const uint8_t* hole,
+                                      const float* top3, float z_far, float s0, uint8_t* out, cudaStream_t s);
+cudaError_t launch_maxpool2_e4m3(int B, int H, int W, int C, const uint8_t* x, uint8_t* y, cudaStream_t s);
+cudaError_t launch_up2_concat_e4m3(int B, int H, int W, int C1, int C2, const uint8_t* lo, const uint8_t* skip,
+                                   uint8_t* cat, cudaStream_t s);
+cudaError_t launch_head_fwd_e4m3(size_t npx, int C1, const uint8_t* d1, float s_d1, const float* wout,
+                                 const float* bout, const uint8_t* rgb, uint8_t* out, int W, size_t out_pitch,
+                                 float* out_f32, cudaStream_t s);
+cudaError_t launch_amax(size_t n, const __nv_bfloat16* x, float* out, cudaStream_t s);
 cudaError_t launch_wgrad3x3(int B, int H, int W, int Cin, int Cout, const __nv_bfloat16* x,
                             const __nv_bfloat16* dz, float* dw, cudaStream_t s);
 cudaError_t launch_bias_grad(size_t npx, int C, const __nv_bfloat16* dz, float* db, cudaStream_t s);

@@ -42,15 +42,18 @@ constexpr int kHaloStage = 25 * 1024;                  // halo slot, 1024-aligne
 constexpr int kThreads = 192;
 constexpr int kMaxStages = 8;
 constexpr int kSmemLimit = 227 * 1024;
-constexpr int kSmemFixed = 1024 + 1024;                // alignment slack + barriers
+constexpr int kHeader = 2048;                          // barriers (bytes 0..511) and bias (512..1279)
+constexpr int kSmemFixed = 1024 + kHeader;             // alignment slack + header
 
 template <int COUT>
 struct ConvCfg {
     static constexpr int kTap = COUT * kRow;           // B tile of one tap (COUT rows of 64 bytes)
     static constexpr int kSlice = 3 * kTap;            // the three taps of one ky
     static constexpr int kGroup = 9 * kTap;            // all taps of one channel group
-    static constexpr int kAcc = (COUT + 31) / 32 * 32; // TMEM columns between the two accumulators
-    static constexpr int kTmemCols = 2 * kAcc <= 64 ? 64 : 2 * kAcc <= 128 ? 128 : 2 * kAcc <= 256 ? 256 : 512;
+    static constexpr int kAcc = (COUT + 31) / 32 * 32; // TMEM columns between accumulators
+    static constexpr int kNumAcc = 4 * kAcc <= 512 ? 4 : 2;        // accumulator ring depth
+    static constexpr int kTmemCols = kNumAcc * kAcc <= 64 ? 64 : kNumAcc * kAcc <= 128 ? 128
+                                   : kNumAcc * kAcc <= 256 ? 256 : 512;
     static_assert(kTap % 1024 == 0, "tap tiles stay 1024-byte aligned");
 };
 
@@ -91,6 +94,29 @@ __device__ __forceinline__ uint32_t pack_e4m3x4(float a, float b, float c, float
     return uint32_t(lo) | (uint32_t(hi) << 16);
 }
 
+// The MMAs of one ky row of taps: kx = 0..2, NKS K-steps of 32 bytes each.
+// A of tap kx starts kx halo rows further on; +2 in a descriptor's start
+// field is +32 bytes (the second K-step).  Only the first MMA can start a
+// fresh accumulator (acc0 = 0).
+template <int COUT, bool FP8, int NKS>
+__device__ __forceinline__ void mma_row(uint32_t d, uint64_t da, uint64_t db, uint32_t idesc, uint32_t acc0)
+{
+    using Cfg = ConvCfg<COUT>;
+#pragma unroll
+    for (int kx = 0; kx < 3; ++kx) {
+#pragma unroll
+        for (int ks = 0; ks < NKS; ++ks) {
+            const uint64_t a = da + uint64_t((kx * kRow) >> 4) + 2 * ks;
+            const uint64_t b = db + uint64_t((kx * Cfg::kTap) >> 4) + 2 * ks;
+            const uint32_t acc = (kx | ks) != 0 ? 1u : acc0;
+            if (FP8)
+                tc::mma_e4m3(d, a, b, idesc, acc);
+            else
+                tc::mma_bf16(d, a, b, idesc, acc);
+        }
+    }
+}
+
 // FP8: e4m3 operands and output (K = 32 channels per MMA, 64 per group);
 // otherwise bf16 (K = 16, 32 per group).
 template <int COUT, bool FP8>
@@ -99,6 +125,7 @@ k_conv3x3_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CU
              int n_tiles, int HS, int WS, int resident)
 {
     using Cfg = ConvCfg<COUT>;
+    static_assert(512 + 4 * COUT <= kHeader, "bias fits the header");
     constexpr int kPerGroup = FP8 ? 64 : 32;           // channels in one 64-byte row
     constexpr int kEsize = FP8 ? 1 : 2;
     extern __shared__ uint8_t smem_raw[];
@@ -107,13 +134,14 @@ k_conv3x3_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CU
     uint64_t* empty_h = full_h + kMaxStages;
     uint64_t* full_w = empty_h + kMaxStages;
     uint64_t* empty_w = full_w + kMaxStages;
-    uint64_t* acc_full = empty_w + kMaxStages;         // [2]
-    uint64_t* acc_empty = acc_full + 2;                // [2]
-    uint64_t* wready = acc_empty + 2;
+    uint64_t* acc_full = empty_w + kMaxStages;         // [kNumAcc]
+    uint64_t* acc_empty = acc_full + 4;                // [kNumAcc]
+    uint64_t* wready = acc_empty + 4;
     uint64_t* drain = wready + 1;
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
     int* skip = reinterpret_cast<int*>(tmem_slot + 1);
-    uint8_t* sHalo = base + 1024;
+    float* s_bias = reinterpret_cast<float*>(base + 512);          // [COUT] (<= 192 floats)
+    uint8_t* sHalo = base + kHeader;
     uint8_t* sW = sHalo + HS * kHaloStage;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -131,7 +159,7 @@ k_conv3x3_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CU
             tc::mbar_init(&full_w[s], 1);
             tc::mbar_init(&empty_w[s], 1);
         }
-        for (int b = 0; b < 2; ++b) {
+        for (int b = 0; b < Cfg::kNumAcc; ++b) {
             tc::mbar_init(&acc_full[b], 1);
             tc::mbar_init(&acc_empty[b], 4);
         }
@@ -142,6 +170,7 @@ k_conv3x3_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CU
         tc::prefetch_tensormap(&tmw);
     }
     if (warp == 1) tc::tmem_alloc(tmem_slot, Cfg::kTmemCols);
+    for (int i = threadIdx.x; i < COUT; i += kThreads) s_bias[i] = P.bias ? P.bias[i] : 0.0f;
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
@@ -165,7 +194,7 @@ k_conv3x3_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CU
                 const int x0 = xt * kTileM;
                 for (int g = 0; g < G && ok; ++g) {
                     const int sh = int(qh % uint32_t(HS));
-                    if (!tc::mbar_wait(&empty_h[sh], ((qh / uint32_t(HS)) & 1u) ^ 1u, P.err, 1)) {
+                    if (!tc::mbar_wait_sleep(&empty_h[sh], ((qh / uint32_t(HS)) & 1u) ^ 1u, P.err, 1)) {
                         ok = false;
                         break;
                     }
@@ -175,7 +204,7 @@ k_conv3x3_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CU
                     if (!resident) {
                         for (int ky = 0; ky < 3; ++ky, ++qw) {
                             const int sw = int(qw % uint32_t(WS));
-                            if (!tc::mbar_wait(&empty_w[sw], ((qw / uint32_t(WS)) & 1u) ^ 1u, P.err, 2)) {
+                            if (!tc::mbar_wait_sleep(&empty_w[sw], ((qw / uint32_t(WS)) & 1u) ^ 1u, P.err, 2)) {
                                 ok = false;
                                 break;
                             }
@@ -194,8 +223,8 @@ k_conv3x3_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CU
             uint32_t qh = 0, qw = 0;
             int tl = 0;
             for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x, ++tl) {
-                const int b = tl & 1;
-                if (!tc::mbar_wait(&acc_empty[b], ((tl >> 1) & 1) ^ 1, P.err, 4)) {
+                const int b = tl % Cfg::kNumAcc;
+                if (!tc::mbar_wait(&acc_empty[b], ((tl / Cfg::kNumAcc) & 1) ^ 1, P.err, 4)) {
                     ok = false;
                     break;
                 }
@@ -227,19 +256,11 @@ k_conv3x3_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CU
                             slice = sW + sw * Cfg::kSlice;
                         }
                         const uint64_t db = tc::desc_kmajor_sw64(tc::smem_u32(slice));
-#pragma unroll
-                        for (int kx = 0; kx < 3; ++kx) {
-                            const uint64_t a = da + uint64_t(((ky * kHaloPx + kx) * kRow) >> 4);
-                            const uint64_t bb = db + uint64_t((kx * Cfg::kTap) >> 4);
-                            const uint32_t acc0 = (g | ky | kx) != 0 ? 1u : 0u;
-                            if (FP8) {
-                                tc::mma_e4m3(d, a, bb, idesc, acc0);
-                                if (nks > 1) tc::mma_e4m3(d, a + 2, bb + 2, idesc, 1u);
-                            } else {
-                                tc::mma_bf16(d, a, bb, idesc, acc0);
-                                if (nks > 1) tc::mma_bf16(d, a + 2, bb + 2, idesc, 1u);
-                            }
-                        }
+                        const uint32_t acc0 = (g | ky) != 0 ? 1u : 0u;
+                        if (nks > 1)
+                            mma_row<COUT, FP8, 2>(d, da + uint64_t((ky * kHaloPx * kRow) >> 4), db, idesc, acc0);
+                        else
+                            mma_row<COUT, FP8, 1>(d, da + uint64_t((ky * kHaloPx * kRow) >> 4), db, idesc, acc0);
                         if (!resident) {
                             tc::mma_commit(&empty_w[sw]);      // the slice is free once these finish
                             ++qw;
@@ -257,56 +278,58 @@ k_conv3x3_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CU
         const int qd = warp & 3;
         int tl = 0;
         for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++tl) {
-            const int b = tl & 1;
-            if (!tc::mbar_wait(&acc_full[b], (tl >> 1) & 1, P.err, 7)) break;
+            const int b = tl % Cfg::kNumAcc;
+            if (!tc::mbar_wait_sleep(&acc_full[b], (tl / Cfg::kNumAcc) & 1, P.err, 7)) break;
             tc::fence_after_sync();
             const int xt = tile % P.tiles_x, row = tile / P.tiles_x;
             const int x = xt * kTileM + qd * 32 + lane;
             const size_t opix = size_t(row) * Wd + x;
             const uint32_t taddr = tmem + (uint32_t(qd * 32) << 16) + uint32_t(b * Cfg::kAcc);
+            // up to 64 columns per TMEM round trip, in units of 16
 #pragma unroll 1
-            for (int c0 = 0; c0 < COUT; c0 += 16) {
-                uint32_t r[16];
-                tc::tmem_ld_x16(taddr + uint32_t(c0), r);
+            for (int c0 = 0; c0 < COUT; c0 += 64) {
+                uint32_t r[4][16];
+                const int nu = min(4, (COUT - c0) / 16);
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (u < nu) tc::tmem_ld_x16(taddr + uint32_t(c0 + 16 * u), r[u]);
                 tc::tmem_ld_wait();
                 if (x < Wd) {
-                    float v[16];
 #pragma unroll
-                    for (int j = 0; j < 16; j += 4) {
-                        const float4 b4 = P.bias ? __ldg(reinterpret_cast<const float4*>(P.bias + c0 + j))
-                                                 : make_float4(0.f, 0.f, 0.f, 0.f);
-                        v[j] = __uint_as_float(r[j]) * P.acc_scale + b4.x;
-                        v[j + 1] = __uint_as_float(r[j + 1]) * P.acc_scale + b4.y;
-                        v[j + 2] = __uint_as_float(r[j + 2]) * P.acc_scale + b4.z;
-                        v[j + 3] = __uint_as_float(r[j + 3]) * P.acc_scale + b4.w;
-                    }
-                    if (P.relu) {
+                    for (int u = 0; u < 4; ++u) {
+                        if (u >= nu) break;
+                        const int c = c0 + 16 * u;
+                        float v[16];
 #pragma unroll
-                        for (int j = 0; j < 16; ++j) v[j] = fmaxf(v[j], 0.0f);
-                    }
-                    if (FP8) {
-                        uint8_t* dst = reinterpret_cast<uint8_t*>(P.y) + opix * P.ldy + P.coff + c0;
-                        const float s = P.out_inv_scale;
-                        *reinterpret_cast<uint4*>(dst) =
-                            make_uint4(pack_e4m3x4(v[0] * s, v[1] * s, v[2] * s, v[3] * s),
-                                       pack_e4m3x4(v[4] * s, v[5] * s, v[6] * s, v[7] * s),
-                                       pack_e4m3x4(v[8] * s, v[9] * s, v[10] * s, v[11] * s),
-                                       pack_e4m3x4(v[12] * s, v[13] * s, v[14] * s, v[15] * s));
-                    } else {
-                        if (P.mask) {
-                            const __nv_bfloat16* m = P.mask + opix * COUT + c0;
+                        for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[u][j]) * P.acc_scale + s_bias[c + j];
+                        if (P.relu) {
 #pragma unroll
-                            for (int j = 0; j < 16; j += 2) {
-                                const __nv_bfloat162 mm = *reinterpret_cast<const __nv_bfloat162*>(m + j);
-                                if (!(__bfloat162float(mm.x) > 0.0f)) v[j] = 0.0f;
-                                if (!(__bfloat162float(mm.y) > 0.0f)) v[j + 1] = 0.0f;
-                            }
+                            for (int j = 0; j < 16; ++j) v[j] = fmaxf(v[j], 0.0f);
                         }
-                        uint4* dst = reinterpret_cast<uint4*>(P.y + opix * P.ldy + P.coff + c0);
-                        dst[0] = make_uint4(pack_bf16x2(v[0], v[1]), pack_bf16x2(v[2], v[3]), pack_bf16x2(v[4], v[5]),
-                                            pack_bf16x2(v[6], v[7]));
-                        dst[1] = make_uint4(pack_bf16x2(v[8], v[9]), pack_bf16x2(v[10], v[11]),
-                                            pack_bf16x2(v[12], v[13]), pack_bf16x2(v[14], v[15]));
+                        if (FP8) {
+                            uint8_t* dst = reinterpret_cast<uint8_t*>(P.y) + opix * P.ldy + P.coff + c;
+                            const float sc = P.out_inv_scale;
+                            *reinterpret_cast<uint4*>(dst) =
+                                make_uint4(pack_e4m3x4(v[0] * sc, v[1] * sc, v[2] * sc, v[3] * sc),
+                                           pack_e4m3x4(v[4] * sc, v[5] * sc, v[6] * sc, v[7] * sc),
+                                           pack_e4m3x4(v[8] * sc, v[9] * sc, v[10] * sc, v[11] * sc),
+                                           pack_e4m3x4(v[12] * sc, v[13] * sc, v[14] * sc, v[15] * sc));
+                        } else {
+                            if (P.mask) {
+                                const __nv_bfloat16* m = P.mask + opix * COUT + c;
+#pragma unroll
+                                for (int j = 0; j < 16; j += 2) {
+                                    const __nv_bfloat162 mm = *reinterpret_cast<const __nv_bfloat162*>(m + j);
+                                    if (!(__bfloat162float(mm.x) > 0.0f)) v[j] = 0.0f;
+                                    if (!(__bfloat162float(mm.y) > 0.0f)) v[j + 1] = 0.0f;
+                                }
+                            }
+                            uint4* dst = reinterpret_cast<uint4*>(P.y + opix * P.ldy + P.coff + c);
+                            dst[0] = make_uint4(pack_bf16x2(v[0], v[1]), pack_bf16x2(v[2], v[3]),
+                                                pack_bf16x2(v[4], v[5]), pack_bf16x2(v[6], v[7]));
+                            dst[1] = make_uint4(pack_bf16x2(v[8], v[9]), pack_bf16x2(v[10], v[11]),
+                                                pack_bf16x2(v[12], v[13]), pack_bf16x2(v[14], v[15]));
+                        }
                     }
                 }
             }

@@ -5,6 +5,7 @@
 // transposed (data-gradient) convolution, and Adam.
 // All activations are NHWC bf16; gradients of weights and biases are fp32.
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 
 #include "fvv_unet.h"
 
@@ -28,14 +29,11 @@ __device__ __forceinline__ float block_sum(float v, float* red)
 }
 
 // ---- input features ----------------------------------------------------------
-// 8 channels (RGB / 255, depth / z_far, hole, top-3 weights) + zeros to 32.
-__global__ void k_pack_features(size_t npx, const uint8_t* __restrict__ rgb, const float* __restrict__ depth,
-                                const uint8_t* __restrict__ hole, const float* __restrict__ top3, float inv_zfar,
-                                __nv_bfloat16* __restrict__ out)
+// 8 channels: RGB / 255, depth / z_far, hole, top-3 weights.
+__device__ __forceinline__ void features(size_t p, const uint8_t* __restrict__ rgb, const float* __restrict__ depth,
+                                         const uint8_t* __restrict__ hole, const float* __restrict__ top3,
+                                         float inv_zfar, float f[8])
 {
-    const size_t p = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (p >= npx) return;
-    float f[8];
     f[0] = float(rgb[3 * p + 0]) * (1.0f / 255.0f);
     f[1] = float(rgb[3 * p + 1]) * (1.0f / 255.0f);
     f[2] = float(rgb[3 * p + 2]) * (1.0f / 255.0f);
@@ -44,17 +42,44 @@ __global__ void k_pack_features(size_t npx, const uint8_t* __restrict__ rgb, con
     f[5] = top3[3 * p + 0];
     f[6] = top3[3 * p + 1];
     f[7] = top3[3 * p + 2];
-    uint32_t w[16];
+}
+
+__global__ void k_pack_features(size_t npx, const uint8_t* __restrict__ rgb, const float* __restrict__ depth,
+                                const uint8_t* __restrict__ hole, const float* __restrict__ top3, float inv_zfar,
+                                __nv_bfloat16* __restrict__ out)
+{
+    const size_t p = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (p >= npx) return;
+    float f[8];
+    features(p, rgb, depth, hole, top3, inv_zfar, f);
+    uint32_t w[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
         const __nv_bfloat162 h = __floats2bfloat162_rn(f[2 * i], f[2 * i + 1]);
         w[i] = *reinterpret_cast<const uint32_t*>(&h);
     }
+    reinterpret_cast<uint4*>(out)[p] = make_uint4(w[0], w[1], w[2], w[3]);
+}
+
+// e4m3 codes of feature / s0 in channels 0..7, zero codes in 8..15
+__global__ void k_pack_features_e4m3(size_t npx, const uint8_t* __restrict__ rgb, const float* __restrict__ depth,
+                                     const uint8_t* __restrict__ hole, const float* __restrict__ top3,
+                                     float inv_zfar, float inv_s0, uint8_t* __restrict__ out)
+{
+    const size_t p = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (p >= npx) return;
+    float f[8];
+    features(p, rgb, depth, hole, top3, inv_zfar, f);
+    uint32_t w[2];
 #pragma unroll
-    for (int i = 4; i < 16; ++i) w[i] = 0u;
-    uint4* dst = reinterpret_cast<uint4*>(out + 32 * p);
-#pragma unroll
-    for (int v = 0; v < 4; ++v) dst[v] = make_uint4(w[4 * v], w[4 * v + 1], w[4 * v + 2], w[4 * v + 3]);
+    for (int i = 0; i < 2; ++i) {
+        const __nv_fp8x2_storage_t lo =
+            __nv_cvt_float2_to_fp8x2(make_float2(f[4 * i] * inv_s0, f[4 * i + 1] * inv_s0), __NV_SATFINITE, __NV_E4M3);
+        const __nv_fp8x2_storage_t hi = __nv_cvt_float2_to_fp8x2(
+            make_float2(f[4 * i + 2] * inv_s0, f[4 * i + 3] * inv_s0), __NV_SATFINITE, __NV_E4M3);
+        w[i] = uint32_t(lo) | (uint32_t(hi) << 16);
+    }
+    reinterpret_cast<uint4*>(out)[p] = make_uint4(w[0], w[1], 0u, 0u);
 }
 
 // ---- 8-channel vectors: every channel count here is a multiple of 8 ---------
@@ -221,35 +246,119 @@ __global__ void k_up2_concat_bwd(int B, int H, int W, int C1, int C2, const __nv
     }
 }
 
+// ---- e4m3 forms for inference: 16 channels (16 bytes) per thread -------------
+__device__ __forceinline__ float e4m3_val(uint8_t b)
+{
+    return __half2float(__half(__nv_cvt_fp8_to_halfraw(__nv_fp8_storage_t(b), __NV_E4M3)));
+}
+
+// 2x2 max pooling of e4m3 codes (one scale in and out); the first maximum wins
+__global__ void k_maxpool2_e4m3(int B, int H, int W, int C, const uint8_t* __restrict__ x, uint8_t* __restrict__ y)
+{
+    const size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    const int h2 = H / 2, w2 = W / 2, cv = C >> 4;
+    const size_t n_out = size_t(B) * h2 * w2 * cv;
+    if (i >= n_out) return;
+    const int c = int(i % cv) * 16;
+    size_t r = i / cv;
+    const int ox = int(r % w2);
+    r /= w2;
+    const int oy = int(r % h2);
+    const int b = int(r / h2);
+    const size_t base = ((size_t(b) * H + 2 * oy) * W + 2 * ox) * C + c;
+    uint4 q[4];
+    q[0] = *reinterpret_cast<const uint4*>(x + base);
+    q[1] = *reinterpret_cast<const uint4*>(x + base + C);
+    q[2] = *reinterpret_cast<const uint4*>(x + base + size_t(W) * C);
+    q[3] = *reinterpret_cast<const uint4*>(x + base + size_t(W) * C + C);
+    const uint8_t* v[4] = {reinterpret_cast<const uint8_t*>(&q[0]), reinterpret_cast<const uint8_t*>(&q[1]),
+                           reinterpret_cast<const uint8_t*>(&q[2]), reinterpret_cast<const uint8_t*>(&q[3])};
+    uint8_t o[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+        uint8_t best = v[0][j];
+        float bv = e4m3_val(best);
+#pragma unroll
+        for (int k = 1; k < 4; ++k) {
+            const float f = e4m3_val(v[k][j]);
+            if (f > bv) {
+                bv = f;
+                best = v[k][j];
+            }
+        }
+        o[j] = best;
+    }
+    *reinterpret_cast<uint4*>(y + i * 16) = *reinterpret_cast<const uint4*>(o);
+}
+
+// cat = [ up(lo) | skip ] on e4m3 codes (each part keeps its own scale)
+__global__ void k_up2_concat_e4m3(int B, int H, int W, int C1, int C2, const uint8_t* __restrict__ lo,
+                                  const uint8_t* __restrict__ skip, uint8_t* __restrict__ cat)
+{
+    const int cv = (C1 + C2) >> 4, cv1 = C1 >> 4;
+    const size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    const size_t n = size_t(B) * H * W * cv;
+    if (i >= n) return;
+    const int c = int(i % cv);
+    const size_t p = i / cv;
+    uint4 v;
+    if (c < cv1) {
+        const int x = int(p % W);
+        const size_t r = p / W;
+        const int yy = int(r % H);
+        const int b = int(r / H);
+        v = *reinterpret_cast<const uint4*>(lo + ((size_t(b) * (H / 2) + yy / 2) * (W / 2) + x / 2) * C1 + 16 * c);
+    } else {
+        v = *reinterpret_cast<const uint4*>(skip + p * C2 + 16 * (c - cv1));
+    }
+    *reinterpret_cast<uint4*>(cat + i * 16) = v;
+}
+
 // ---- 1x1 head ---------------------------------------------------------------
-// s = rgb / 255 + (W d1 + b); out = round(255 clamp(s, 0, 1))
-__global__ void k_head_fwd(size_t npx, const __nv_bfloat16* __restrict__ d1, const float* __restrict__ wout,
+// d1 activations of one pixel as floats: bf16, or e4m3 codes times s_d1
+template <int C1>
+__device__ __forceinline__ void load_d1(const __nv_bfloat16* d1, size_t p, float a[C1])
+{
+    const uint4* src = reinterpret_cast<const uint4*>(d1 + size_t(C1) * p);
+#pragma unroll
+    for (int v = 0; v < C1 / 8; ++v) unpack8(src[v], a + 8 * v);
+}
+
+template <int C1>
+__device__ __forceinline__ void load_d1(const uint8_t* d1, size_t p, float a[C1], float s_d1)
+{
+    const uint4* src = reinterpret_cast<const uint4*>(d1 + size_t(C1) * p);
+#pragma unroll
+    for (int v = 0; v < C1 / 16; ++v) {
+        const uint4 q = src[v];
+        const uint8_t* b = reinterpret_cast<const uint8_t*>(&q);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) a[16 * v + j] = e4m3_val(b[j]) * s_d1;
+    }
+}
+
+// s = rgb / 255 + (W d1 + b); out = round(255 clamp(s, 0, 1)).  T = bf16 or
+// e4m3 codes (then scaled by s_d1).
+template <int C1, typename T>
+__global__ void k_head_fwd(size_t npx, const T* __restrict__ d1, float s_d1, const float* __restrict__ wout,
                            const float* __restrict__ bout, const uint8_t* __restrict__ rgb, float* __restrict__ s,
                            uint8_t* __restrict__ out, int W, size_t out_pitch, float* __restrict__ out_f32)
 {
-    __shared__ float sw[3 * 32 + 3];
-    for (int i = threadIdx.x; i < 99; i += blockDim.x) sw[i] = i < 96 ? wout[i] : bout[i - 96];
+    __shared__ float sw[3 * C1 + 3];
+    for (int i = threadIdx.x; i < 3 * C1 + 3; i += blockDim.x) sw[i] = i < 3 * C1 ? wout[i] : bout[i - 3 * C1];
     __syncthreads();
     const size_t p = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (p >= npx) return;
-    float a[32];
-    const uint4* src = reinterpret_cast<const uint4*>(d1 + 32 * p);
-#pragma unroll
-    for (int v = 0; v < 4; ++v) {
-        const uint4 q = src[v];
-        const uint32_t w4[4] = {q.x, q.y, q.z, q.w};
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const __nv_bfloat162 h = *reinterpret_cast<const __nv_bfloat162*>(&w4[j]);
-            a[8 * v + 2 * j] = __bfloat162float(h.x);
-            a[8 * v + 2 * j + 1] = __bfloat162float(h.y);
-        }
-    }
+    float a[C1];
+    if constexpr (sizeof(T) == 1)
+        load_d1<C1>(d1, p, a, s_d1);
+    else
+        load_d1<C1>(d1, p, a);
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        float r = sw[96 + c];
+        float r = sw[3 * C1 + c];
 #pragma unroll
-        for (int k = 0; k < 32; ++k) r += sw[32 * c + k] * a[k];
+        for (int k = 0; k < C1; ++k) r += sw[C1 * c + k] * a[k];
         const float sv = float(rgb[3 * p + c]) * (1.0f / 255.0f) + r;
         if (s) s[3 * p + c] = sv;
         const float pr = fminf(fmaxf(sv, 0.0f), 1.0f);
@@ -264,33 +373,23 @@ __global__ void k_head_fwd(size_t npx, const __nv_bfloat16* __restrict__ d1, con
 // Loss and the head's backward pass.  diff = clamp(s) - target / 255;
 // loss += sum diff^2 (scaled by inv_count); ds = 2 diff inv_count on 0 < s < 1;
 // dW += ds d1^T; db += ds; dd1 = (W^T ds) * (d1 > 0).
+template <int C1>
 __global__ void k_head_bwd(size_t npx, const __nv_bfloat16* __restrict__ d1, const float* __restrict__ wout,
                            const float* __restrict__ s, const uint8_t* __restrict__ target, float inv_count,
                            float* __restrict__ loss, float* __restrict__ dwout, float* __restrict__ dbout,
                            __nv_bfloat16* __restrict__ dd1)
 {
-    __shared__ float sw[96];
-    __shared__ float acc[96 + 3 + 1];
+    __shared__ float sw[3 * C1];
+    __shared__ float acc[3 * C1 + 3 + 1];
     __shared__ float red[32];
-    for (int i = threadIdx.x; i < 96; i += blockDim.x) sw[i] = wout[i];
-    for (int i = threadIdx.x; i < 100; i += blockDim.x) acc[i] = 0.0f;
+    for (int i = threadIdx.x; i < 3 * C1; i += blockDim.x) sw[i] = wout[i];
+    for (int i = threadIdx.x; i < 3 * C1 + 4; i += blockDim.x) acc[i] = 0.0f;
     __syncthreads();
     const size_t p = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
     float l = 0.0f;
     if (p < npx) {
-        float a[32];
-        const uint4* src = reinterpret_cast<const uint4*>(d1 + 32 * p);
-#pragma unroll
-        for (int v = 0; v < 4; ++v) {
-            const uint4 q = src[v];
-            const uint32_t w4[4] = {q.x, q.y, q.z, q.w};
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const __nv_bfloat162 h = *reinterpret_cast<const __nv_bfloat162*>(&w4[j]);
-                a[8 * v + 2 * j] = __bfloat162float(h.x);
-                a[8 * v + 2 * j + 1] = __bfloat162float(h.y);
-            }
-        }
+        float a[C1];
+        load_d1<C1>(d1, p, a);
         float ds[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
@@ -298,49 +397,48 @@ __global__ void k_head_bwd(size_t npx, const __nv_bfloat16* __restrict__ d1, con
             const float d = fminf(fmaxf(sv, 0.0f), 1.0f) - float(target[3 * p + c]) * (1.0f / 255.0f);
             l += d * d;
             ds[c] = (sv > 0.0f && sv < 1.0f) ? 2.0f * d * inv_count : 0.0f;
-            atomicAdd(&acc[96 + c], ds[c]);
+            atomicAdd(&acc[3 * C1 + c], ds[c]);
         }
-        uint32_t out[16];
+        float g[C1];
 #pragma unroll
-        for (int k = 0; k < 32; k += 2) {
-            float g0 = sw[k] * ds[0] + sw[32 + k] * ds[1] + sw[64 + k] * ds[2];
-            float g1 = sw[k + 1] * ds[0] + sw[33 + k] * ds[1] + sw[65 + k] * ds[2];
-            if (!(a[k] > 0.0f)) g0 = 0.0f;
-            if (!(a[k + 1] > 0.0f)) g1 = 0.0f;
-            const __nv_bfloat162 h = __floats2bfloat162_rn(g0, g1);
-            out[k >> 1] = *reinterpret_cast<const uint32_t*>(&h);
+        for (int k = 0; k < C1; ++k) {
+            const float v = sw[k] * ds[0] + sw[C1 + k] * ds[1] + sw[2 * C1 + k] * ds[2];
+            g[k] = a[k] > 0.0f ? v : 0.0f;
         }
-        uint4* dst = reinterpret_cast<uint4*>(dd1 + 32 * p);
+        uint4* dst = reinterpret_cast<uint4*>(dd1 + size_t(C1) * p);
 #pragma unroll
-        for (int v = 0; v < 4; ++v) dst[v] = make_uint4(out[4 * v], out[4 * v + 1], out[4 * v + 2], out[4 * v + 3]);
+        for (int v = 0; v < C1 / 8; ++v) dst[v] = pack8(g + 8 * v);
 #pragma unroll
         for (int c = 0; c < 3; ++c)
             if (ds[c] != 0.0f)
 #pragma unroll 4
-                for (int k = 0; k < 32; ++k) atomicAdd(&acc[32 * c + k], ds[c] * a[k]);
+                for (int k = 0; k < C1; ++k) atomicAdd(&acc[C1 * c + k], ds[c] * a[k]);
     }
     const float bl = block_sum(l, red);
     __syncthreads();
     if (threadIdx.x == 0) atomicAdd(loss, bl * inv_count);
-    for (int i = threadIdx.x; i < 99; i += blockDim.x) {
+    for (int i = threadIdx.x; i < 3 * C1 + 3; i += blockDim.x) {
         const float v = acc[i];
-        if (v != 0.0f) atomicAdd(i < 96 ? &dwout[i] : &dbout[i - 96], v);
+        if (v != 0.0f) atomicAdd(i < 3 * C1 ? &dwout[i] : &dbout[i - 3 * C1], v);
     }
 }
 
 // ---- weight gradients of a 3x3 convolution --------------------------------------
 // dw[co][ky][kx][ci] += sum_p dz[p][co] * x[p + (ky-1, kx-1)][ci]  (zero outside).
-// CTA = a 32 (co) x 32 (ci) block of one tap over a slice of pixel rows; each
-// thread owns 2 x 2 outputs; 64 pixels are staged in shared memory at a time.
+// CTA = a BCO (co) x BCI (ci) block of one tap over a slice of pixel rows;
+// each thread owns 2 x 2 outputs; 64 pixels are staged in shared memory at a
+// time.  BCO, BCI in {32, 16, 8} divide Cout and Cin.
 constexpr int kWgPix = 64;
-__global__ void __launch_bounds__(256) k_wgrad3x3(int B, int H, int W, int Cin, int Cout,
-                                                  const __nv_bfloat16* __restrict__ x,
-                                                  const __nv_bfloat16* __restrict__ dz, float* __restrict__ dw,
-                                                  int rows_per_cta)
+template <int BCO, int BCI>
+__global__ void __launch_bounds__(BCO * BCI / 4) k_wgrad3x3(int B, int H, int W, int Cin, int Cout,
+                                                           const __nv_bfloat16* __restrict__ x,
+                                                           const __nv_bfloat16* __restrict__ dz,
+                                                           float* __restrict__ dw, int rows_per_cta)
 {
-    __shared__ float sz[kWgPix][33];
-    __shared__ float sx[kWgPix][33];
-    const int co_blocks = Cout / 32, ci_blocks = Cin / 32;
+    constexpr int NT = BCO * BCI / 4;
+    __shared__ float sz[kWgPix][BCO + 1];
+    __shared__ float sx[kWgPix][BCI + 1];
+    const int co_blocks = Cout / BCO, ci_blocks = Cin / BCI;
     int t = blockIdx.x;
     const int cib = t % ci_blocks;
     t /= ci_blocks;
@@ -348,7 +446,7 @@ __global__ void __launch_bounds__(256) k_wgrad3x3(int B, int H, int W, int Cin, 
     const int tap = t / co_blocks;
     const int ky = tap / 3, kx = tap - 3 * ky;
     const int tid = threadIdx.x;
-    const int tco = (tid >> 4) * 2, tci = (tid & 15) * 2;
+    const int tco = (tid / (BCI / 2)) * 2, tci = (tid % (BCI / 2)) * 2;
     float a00 = 0.f, a01 = 0.f, a10 = 0.f, a11 = 0.f;
     const long total_rows = long(B) * H;
     const long r0 = long(blockIdx.y) * rows_per_cta;
@@ -358,17 +456,17 @@ __global__ void __launch_bounds__(256) k_wgrad3x3(int B, int H, int W, int Cin, 
         const int ys = yy + ky - 1;
         for (int x0 = 0; x0 < W; x0 += kWgPix) {
             __syncthreads();
-            for (int i = tid; i < kWgPix * 32; i += 256) {
-                const int pp = i >> 5, c = i & 31;
+            for (int i = tid; i < kWgPix * BCO; i += NT) {
+                const int pp = i / BCO, c = i % BCO;
                 const int xx = x0 + pp;
-                float zv = 0.0f, xv = 0.0f;
-                if (xx < W) {
-                    zv = bf(dz[((size_t(b) * H + yy) * W + xx) * Cout + cob * 32 + c]);
-                    const int xs = xx + kx - 1;
-                    if (ys >= 0 && ys < H && xs >= 0 && xs < W)
-                        xv = bf(x[((size_t(b) * H + ys) * W + xs) * Cin + cib * 32 + c]);
-                }
-                sz[pp][c] = zv;
+                sz[pp][c] = xx < W ? bf(dz[((size_t(b) * H + yy) * W + xx) * Cout + cob * BCO + c]) : 0.0f;
+            }
+            for (int i = tid; i < kWgPix * BCI; i += NT) {
+                const int pp = i / BCI, c = i % BCI;
+                const int xx = x0 + pp, xs = xx + kx - 1;
+                float xv = 0.0f;
+                if (xx < W && ys >= 0 && ys < H && xs >= 0 && xs < W)
+                    xv = bf(x[((size_t(b) * H + ys) * W + xs) * Cin + cib * BCI + c]);
                 sx[pp][c] = xv;
             }
             __syncthreads();
@@ -384,7 +482,7 @@ __global__ void __launch_bounds__(256) k_wgrad3x3(int B, int H, int W, int Cin, 
         }
     }
     const size_t K = size_t(9) * Cin;
-    const size_t o0 = size_t(cob * 32 + tco) * K + size_t(tap) * Cin + cib * 32 + tci;
+    const size_t o0 = size_t(cob * BCO + tco) * K + size_t(tap) * Cin + cib * BCI + tci;
     atomicAdd(&dw[o0], a00);
     atomicAdd(&dw[o0 + 1], a01);
     atomicAdd(&dw[o0 + K], a10);
@@ -435,6 +533,20 @@ __global__ void k_adam(size_t n, float* __restrict__ w, const float* __restrict_
     w[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
 }
 
+// out = max(out, max |x|) (out >= 0 on entry; non-negative floats order like their bits)
+__global__ void k_amax(size_t n8, const __nv_bfloat16* __restrict__ x, float* __restrict__ out)
+{
+    float m = 0.0f;
+    for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n8; i += size_t(gridDim.x) * blockDim.x) {
+        float f[8];
+        unpack8(ld8(x + 8 * i), f);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) m = fmaxf(m, fabsf(f[j]));
+    }
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(reinterpret_cast<unsigned int*>(out), __float_as_uint(m));
+}
+
 unsigned blocks(size_t n, int t) { return unsigned((n + t - 1) / t); }
 
 }  // namespace
@@ -481,36 +593,108 @@ cudaError_t launch_up2_concat_bwd(int B, int H, int W, int C1, int C2, const __n
     return cudaGetLastError();
 }
 
-cudaError_t launch_head_fwd(size_t npx, const __nv_bfloat16* d1, const float* wout, const float* bout,
+bool head_width_supported(int c1) { return c1 == 32 || c1 == 48 || c1 == 64; }
+
+cudaError_t launch_head_fwd(size_t npx, int C1, const __nv_bfloat16* d1, const float* wout, const float* bout,
                             const uint8_t* rgb, float* sbuf, uint8_t* out, int W, size_t out_pitch,
                             float* out_f32, cudaStream_t s)
 {
-    k_head_fwd<<<blocks(npx, 128), 128, 0, s>>>(npx, d1, wout, bout, rgb, sbuf, out, W, out_pitch, out_f32);
+    switch (C1) {
+    case 32: k_head_fwd<32><<<blocks(npx, 128), 128, 0, s>>>(npx, d1, 1.0f, wout, bout, rgb, sbuf, out, W, out_pitch, out_f32); break;
+    case 48: k_head_fwd<48><<<blocks(npx, 128), 128, 0, s>>>(npx, d1, 1.0f, wout, bout, rgb, sbuf, out, W, out_pitch, out_f32); break;
+    case 64: k_head_fwd<64><<<blocks(npx, 128), 128, 0, s>>>(npx, d1, 1.0f, wout, bout, rgb, sbuf, out, W, out_pitch, out_f32); break;
+    default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 
-cudaError_t launch_head_bwd(size_t npx, const __nv_bfloat16* d1, const float* wout, const float* sbuf,
+cudaError_t launch_head_fwd_e4m3(size_t npx, int C1, const uint8_t* d1, float s_d1, const float* wout,
+                                 const float* bout, const uint8_t* rgb, uint8_t* out, int W, size_t out_pitch,
+                                 float* out_f32, cudaStream_t s)
+{
+    switch (C1) {
+    case 32: k_head_fwd<32><<<blocks(npx, 128), 128, 0, s>>>(npx, d1, s_d1, wout, bout, rgb, nullptr, out, W, out_pitch, out_f32); break;
+    case 48: k_head_fwd<48><<<blocks(npx, 128), 128, 0, s>>>(npx, d1, s_d1, wout, bout, rgb, nullptr, out, W, out_pitch, out_f32); break;
+    case 64: k_head_fwd<64><<<blocks(npx, 128), 128, 0, s>>>(npx, d1, s_d1, wout, bout, rgb, nullptr, out, W, out_pitch, out_f32); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_head_bwd(size_t npx, int C1, const __nv_bfloat16* d1, const float* wout, const float* sbuf,
                             const uint8_t* target, float* loss, float* dwout, float* dbout, __nv_bfloat16* dd1,
                             cudaStream_t s)
 {
     const float inv = 1.0f / float(npx * 3);
-    k_head_bwd<<<blocks(npx, 128), 128, 0, s>>>(npx, d1, wout, sbuf, target, inv, loss, dwout, dbout, dd1);
+    switch (C1) {
+    case 32: k_head_bwd<32><<<blocks(npx, 128), 128, 0, s>>>(npx, d1, wout, sbuf, target, inv, loss, dwout, dbout, dd1); break;
+    case 48: k_head_bwd<48><<<blocks(npx, 128), 128, 0, s>>>(npx, d1, wout, sbuf, target, inv, loss, dwout, dbout, dd1); break;
+    case 64: k_head_bwd<64><<<blocks(npx, 128), 128, 0, s>>>(npx, d1, wout, sbuf, target, inv, loss, dwout, dbout, dd1); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_amax(size_t n, const __nv_bfloat16* x, float* out, cudaStream_t s)
+{
+    const size_t n8 = n / 8;                                    // n is a multiple of 8
+    unsigned g = blocks(n8, 256);
+    if (g > 152 * 8) g = 152 * 8;
+    if (g == 0) g = 1;
+    k_amax<<<g, 256, 0, s>>>(n8, x, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack_features_e4m3(size_t npx, const uint8_t* rgb, const float* depth, const uint8_t* hole,
+                                      const float* top3, float z_far, float s0, uint8_t* out, cudaStream_t s)
+{
+    k_pack_features_e4m3<<<blocks(npx, 256), 256, 0, s>>>(npx, rgb, depth, hole, top3, 1.0f / z_far, 1.0f / s0, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_maxpool2_e4m3(int B, int H, int W, int C, const uint8_t* x, uint8_t* y, cudaStream_t s)
+{
+    const size_t n = size_t(B) * (H / 2) * (W / 2) * (C / 16);
+    k_maxpool2_e4m3<<<blocks(n, 256), 256, 0, s>>>(B, H, W, C, x, y);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_up2_concat_e4m3(int B, int H, int W, int C1, int C2, const uint8_t* lo, const uint8_t* skip,
+                                   uint8_t* cat, cudaStream_t s)
+{
+    const size_t n = size_t(B) * H * W * ((C1 + C2) / 16);
+    k_up2_concat_e4m3<<<blocks(n, 256), 256, 0, s>>>(B, H, W, C1, C2, lo, skip, cat);
+    return cudaGetLastError();
+}
+
+template <int BCO, int BCI>
+cudaError_t wgrad_blocks(int B, int H, int W, int Cin, int Cout, const __nv_bfloat16* x, const __nv_bfloat16* dz,
+                         float* dw, cudaStream_t s)
+{
+    const int tiles = 9 * (Cout / BCO) * (Cin / BCI);
+    const long rows = long(B) * H;
+    // split the rows so that about 4 waves of CTAs cover the GPU
+    long splits = (4L * 152 * 4 * (1024 / (BCO * BCI)) + tiles - 1) / tiles;
+    if (splits > rows) splits = rows;
+    if (splits < 1) splits = 1;
+    const int rpc = int((rows + splits - 1) / splits);
+    dim3 grid(unsigned(tiles), unsigned((rows + rpc - 1) / rpc));
+    k_wgrad3x3<BCO, BCI><<<grid, BCO * BCI / 4, 0, s>>>(B, H, W, Cin, Cout, x, dz, dw, rpc);
     return cudaGetLastError();
 }
 
 cudaError_t launch_wgrad3x3(int B, int H, int W, int Cin, int Cout, const __nv_bfloat16* x,
                             const __nv_bfloat16* dz, float* dw, cudaStream_t s)
 {
-    const int tiles = 9 * (Cout / 32) * (Cin / 32);
-    const long rows = long(B) * H;
-    // split the rows so that about 4 waves of CTAs cover the GPU
-    long splits = (4L * 152 * 4 + tiles - 1) / tiles;
-    if (splits > rows) splits = rows;
-    if (splits < 1) splits = 1;
-    const int rpc = int((rows + splits - 1) / splits);
-    dim3 grid(unsigned(tiles), unsigned((rows + rpc - 1) / rpc));
-    k_wgrad3x3<<<grid, 256, 0, s>>>(B, H, W, Cin, Cout, x, dz, dw, rpc);
-    return cudaGetLastError();
+    if (Cout % 16 || Cin % 8) return cudaErrorInvalidValue;
+    if (Cout % 32 == 0) {
+        if (Cin % 32 == 0) return wgrad_blocks<32, 32>(B, H, W, Cin, Cout, x, dz, dw, s);
+        if (Cin % 16 == 0) return wgrad_blocks<32, 16>(B, H, W, Cin, Cout, x, dz, dw, s);
+        return wgrad_blocks<32, 8>(B, H, W, Cin, Cout, x, dz, dw, s);
+    }
+    if (Cin % 32 == 0) return wgrad_blocks<16, 32>(B, H, W, Cin, Cout, x, dz, dw, s);
+    if (Cin % 16 == 0) return wgrad_blocks<16, 16>(B, H, W, Cin, Cout, x, dz, dw, s);
+    return wgrad_blocks<16, 8>(B, H, W, Cin, Cout, x, dz, dw, s);
 }
 
 cudaError_t launch_bias_grad(size_t npx, int C, const __nv_bfloat16* dz, float* db, cudaStream_t s)

@@ -142,6 +142,9 @@ def load() -> C.CDLL:
             "fvv_unet_conv3x3": [P, I, I, I, I, P, P, I, I, P, P, P],
             "fvv_selftest_bounded_wait": [I, C.c_uint32, P],
             "fvv_unet_conv3x3_e4m3": [P, I, I, I, I, P, P, I, I, C.c_float, C.c_float, P, P],
+            "fvv_refine_quantize": [P, C.POINTER(fvv_refine_batch), P, P],
+            "fvv_refine_set_precision": [P, I],
+            "fvv_refine_get_precision": [P, C.POINTER(I), P],
             "fvv_refine_default_cfg": [C.POINTER(fvv_unet_cfg)],
             "fvv_refine_init": [P, C.POINTER(fvv_unet_cfg)],
             "fvv_refine_param_count": [P, C.POINTER(U64)],
@@ -381,6 +384,33 @@ def fvv_unet_conv3x3_e4m3(x, n: int, h: int, w: int, cin: int, wt, bias, cout: i
     _check(load().fvv_unet_conv3x3_e4m3(ptr(x), n, h, w, cin, ptr(wt), ptr(bias), cout, 1 if relu else 0,
                                         acc_scale, out_inv_scale, ptr(y), stream_handle(stream)),
            "fvv_unet_conv3x3_e4m3")
+
+
+FVV_PREC_BF16 = 0
+FVV_PREC_E4M3 = 1
+
+
+def fvv_refine_quantize(ctx: int, calib=None, act_scales=None, stream=None) -> None:
+    """E4M3 inference from now on: scales from a bf16 pass over `calib`
+    (a refine_batch), or the ten given activation scales."""
+    sc = None
+    if act_scales is not None:
+        sc = np.ascontiguousarray(act_scales, np.float32)
+        assert sc.size == 10
+    _check(load().fvv_refine_quantize(ctx, C.byref(calib) if calib is not None else None,
+                                      sc.ctypes.data if sc is not None else None, stream_handle(stream)),
+           "fvv_refine_quantize")
+
+
+def fvv_refine_set_precision(ctx: int, precision: int) -> None:
+    _check(load().fvv_refine_set_precision(ctx, precision), "fvv_refine_set_precision")
+
+
+def fvv_refine_get_precision(ctx: int):
+    p = C.c_int32()
+    sc = np.zeros(10, np.float32)
+    _check(load().fvv_refine_get_precision(ctx, C.byref(p), sc.ctypes.data), "fvv_refine_get_precision")
+    return p.value, sc
 
 
 def fvv_selftest_bounded_wait(arrive: bool, limit_us: int, stream=None) -> int:

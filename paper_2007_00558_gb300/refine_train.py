@@ -87,6 +87,17 @@ def train(ctx: int, data: dict, steps: int, batch: int = 8, crop: int = 128, lr:
     return losses
 
 
+def quantize(ctx: int, data: dict, n: int = 8) -> None:
+    """E4M3 inference for `ctx`: activation scales from a bf16 pass over the
+    first n samples of `data` (full frames, cropped to multiples of 4)."""
+    _, H, W = data["depth"].shape
+    h4, w4 = H // 4 * 4, W // 4 * 4
+    n = min(n, data["depth"].shape[0])
+    b = {k: v[:n, :h4, :w4].contiguous() for k, v in data.items()}
+    fb = F.refine_batch(n, h4, w4, b["rgb"], b["depth"], b["hole"], b["top3"])
+    F.fvv_refine_quantize(ctx, fb)
+
+
 def psnr(a, b) -> float:
     d = (a.float() - b.float())
     mse = float((d * d).mean())

@@ -163,3 +163,27 @@ def test_e4m3_matches_torch_float8():
     ref = torch.from_numpy(x.astype(np.float32)).to(torch.float8_e4m3fn)
     ours = U.e4m3_encode(U.e4m3_round(x.astype(np.float32).astype(np.float64)))
     assert np.array_equal(ours, ref.view(torch.uint8).numpy())
+
+
+def test_forward_e4m3_without_rounding_is_the_network(monkeypatch):
+    """With the E4M3 rounding replaced by the identity, the quantised form's
+    scale bookkeeping (input and output scales, the concat parts' ratios
+    folded into the weights, the accumulator multiplier) must cancel exactly:
+    it then equals the plain forward pass."""
+    rng = np.random.default_rng(2)
+    for widths in ((32, 64, 128), (48, 96, 192)):
+        p = U.init_params(widths, seed=4, out_scale=0.5)
+        for k in p:
+            if k.endswith(".b"):
+                p[k] = rng.standard_normal(p[k].shape) * 0.05
+        x = rng.random((1, 8, 8, 8))
+        rgb = rng.random((1, 8, 8, 3)) * 0.6 + 0.2
+        pred, cache = U.forward(p, x, rgb)
+        scales = U.activation_scales(cache) * rng.uniform(0.5, 2.0, 10)    # any positive scales
+        monkeypatch.setattr(U, "e4m3_round", lambda v: np.asarray(v, np.float64))
+        q = U.forward_e4m3(p, x, rgb, scales)
+        monkeypatch.undo()
+        assert np.allclose(q, pred, rtol=0, atol=1e-12)
+        # and with rounding it stays close (3 mantissa bits per tensor)
+        q8 = U.forward_e4m3(p, x, rgb, U.activation_scales(cache))
+        assert np.abs(q8 - pred).max() < 0.1
