@@ -375,12 +375,10 @@ def unet_flops(H, W, widths=(32, 64, 128), c_in=8):
     return 2.0 * (H * W * l1 + H * W / 4 * l2 + H * W / 16 * l3)
 
 
-def refine_bench(F, ctx, wl, steps, stream):
-    import numpy as np
-    import torch
+def loo_data():
+    """Leave-one-camera-out renders at 1/4 scale: 6 training + 2 unseen scenes."""
     import synthetic as S
     from paper_2007_00558_gb300 import refine_train as RT
-    # 1. stated PSNR: LOO renders at 1/4 scale, 6 training + 2 unseen scenes
     cams_s = S.rig_arc(9, 90.0, 1.5, 320, 180, 250.0)
     loo = RT.LooRig(cams_s, [0.0, 0.0, 0.0])
     try:
@@ -391,27 +389,28 @@ def refine_bench(F, ctx, wl, steps, stream):
         test = RT.concat([scene(s) for s in (200, 201)])
     finally:
         loo.close()
-    F.fvv_refine_init(ctx, F.fvv_refine_default_cfg(seed=1))
+    return train, test
+
+
+def refine_bench(F, ctx, wl, steps, stream, data, widths=(32, 64, 128), fp8=False):
+    """Train the net of `widths` in bf16 on LOO data, state its PSNR, time it
+    at 1280x720; fp8: also quantise to E4M3 and report that form."""
+    import numpy as np
+    import torch
+    from paper_2007_00558_gb300 import refine_train as RT
+    train, test = data
+    F.fvv_refine_init(ctx, F.fvv_refine_default_cfg(seed=1, widths=widths))
     t0 = time.perf_counter()
     losses = RT.train(ctx, train, steps=steps, batch=8, crop=128, lr=2e-3)
     train_s = time.perf_counter() - t0
     ev = RT.evaluate(ctx, test)
-    # 2. throughput: plain synthesis + network on 1280x720 views
+    ev_q = None
+    if fp8:
+        RT.quantize(ctx, train, n=8)
+        ev_q = RT.evaluate(ctx, test)
+    # 2. throughput at 1280x720: plain synthesis + network, and the network alone
     H, W = wl["cams"][0].height, wl["cams"][0].width
     views = wl["views"]
-    out = torch.empty((H, W * 3), dtype=torch.uint8, device="cuda")
-    for i in range(3):
-        F.fvv_synthesize_refined(ctx, views[i], out, W * 3, stream)
-    torch.cuda.synchronize()
-    n = 40
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for i in range(n):
-        F.fvv_synthesize_refined(ctx, views[i % 300], out, W * 3, stream)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    per_view = e0.elapsed_time(e1) / n / 1e3
-    # network alone on a batch of 4 plain 720p outputs
     B = 4
     plain = {"rgb": torch.empty((B, H, W, 3), dtype=torch.uint8, device="cuda"),
              "depth": torch.empty((B, H, W), dtype=torch.float32, device="cuda"),
@@ -422,27 +421,52 @@ def refine_bench(F, ctx, wl, steps, stream):
                             for i in range(B)], stream)
     fb = F.refine_batch(B, H, W, plain["rgb"], plain["depth"], plain["hole"], plain["top3"])
     outb = torch.empty((B, H, W, 3), dtype=torch.uint8, device="cuda")
-    F.fvv_refine_forward(ctx, fb, outb, None, stream)
-    m = 10
-    e0.record(stream)
-    for i in range(m):
+    out = torch.empty((H, W * 3), dtype=torch.uint8, device="cuda")
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed():
+        for i in range(3):
+            F.fvv_synthesize_refined(ctx, views[i], out, W * 3, stream)
+        torch.cuda.synchronize()
+        n = 40
+        e0.record(stream)
+        for i in range(n):
+            F.fvv_synthesize_refined(ctx, views[i % 300], out, W * 3, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        per_view = e0.elapsed_time(e1) / n / 1e3
         F.fvv_refine_forward(ctx, fb, outb, None, stream)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    net_s = e0.elapsed_time(e1) / m / 1e3 / B
-    flops = unet_flops(H, W)
+        m = 10
+        e0.record(stream)
+        for i in range(m):
+            F.fvv_refine_forward(ctx, fb, outb, None, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return per_view, e0.elapsed_time(e1) / m / 1e3 / B
+
+    flops = unet_flops(H, W, widths)
     peak, src = bf16_peak()
-    return {
-        "views_per_s": 1.0 / per_view, "ms_per_view": per_view * 1e3,
-        "net_ms_per_view": net_s * 1e3, "net_tflops": flops / net_s / 1e12,
-        "tensor_peak_tflops": peak, "tensor_frac": flops / net_s / 1e12 / peak, "peak_source": src,
-        "gflop_per_view": flops / 1e9, "dtype": "bf16 x bf16 -> fp32",
-        "psnr": {"plain_db": ev["psnr_plain"], "refined_db": ev["psnr_refined"],
-                 "eval": "leave-one-camera-out, 2 unseen synthetic scenes x 9 cameras, %s" % ev["size"]},
-        "train": {"steps": steps, "batch": 8, "crop": 128, "seconds": train_s,
-                  "loss_first": float(np.mean(losses[:20])), "loss_last": float(np.mean(losses[-20:])),
-                  "samples": int(train["depth"].shape[0])},
-    }
+    psnr_eval = "leave-one-camera-out, 2 unseen synthetic scenes x 9 cameras, %s" % ev["size"]
+
+    def entry(per_view, net_s, ev_, dtype, pk, pk_src):
+        return {"views_per_s": 1.0 / per_view, "ms_per_view": per_view * 1e3,
+                "net_ms_per_view": net_s * 1e3, "net_tflops": flops / net_s / 1e12,
+                "tensor_peak_tflops": pk, "tensor_frac": flops / net_s / 1e12 / pk, "peak_source": pk_src,
+                "dtype": dtype, "psnr": {"plain_db": ev_["psnr_plain"], "refined_db": ev_["psnr_refined"],
+                                         "eval": psnr_eval}}
+
+    res = {"widths": list(widths), "gflop_per_view": flops / 1e9,
+           "train": {"steps": steps, "batch": 8, "crop": 128, "seconds": train_s,
+                     "loss_first": float(np.mean(losses[:20])), "loss_last": float(np.mean(losses[-20:])),
+                     "samples": int(train["depth"].shape[0])}}
+    if fp8:
+        pv, ns = timed()
+        res["e4m3"] = entry(pv, ns, ev_q, "e4m3 x e4m3 -> fp32, per-tensor scales", 2.0 * peak,
+                            src + " bf16 x 2 (the e4m3 / bf16 dense rate ratio)")
+        F.fvv_refine_set_precision(ctx, F.FVV_PREC_BF16)
+    pv, ns = timed()
+    res["bf16"] = entry(pv, ns, ev, "bf16 x bf16 -> fp32", peak, src)
+    return res
 
 
 # ---------------------------------------------------------------------------
@@ -636,7 +660,10 @@ def run_fvv(args):
 
     refine = None
     if not args.no_refine and world == 1:
-        refine = refine_bench(F, ctx, wl, args.refine_steps, stream)
+        data = loo_data()
+        refine = {"net_32_64_128": refine_bench(F, ctx, wl, args.refine_steps, stream, data),
+                  "net_48_96_192": refine_bench(F, ctx, wl, args.refine_steps, stream, data, (48, 96, 192),
+                                                fp8=True)}
 
     F.fvv_destroy(ctx)
 

@@ -64,6 +64,10 @@ fvv_status check_flag(int* flag, cudaStream_t s, const char* what)
 
 bool on_device(const void* p) { return p && mem_kind(p) == MemKind::Device; }
 
+// the 8 input features occupy one 64-byte row per pixel (zeros after them)
+constexpr int kX0Stride = 32;     // bf16 channels
+constexpr int kX0StrideQ = 64;    // e4m3 bytes
+
 
 }  // namespace
 
@@ -89,7 +93,7 @@ struct RefineNet {
     std::vector<std::pair<void*, size_t>> params;     // device allocations of parameters
     int B = 0, H = 0, W = 0;
     std::vector<std::pair<void*, size_t>> acts;       // activations for (B, H, W)
-    __nv_bfloat16 *x0, *e1a, *e1, *p1, *e2a, *e2, *p2, *ba, *bt, *cat2, *d2a, *d2, *cat1, *d1a, *d1;
+    __nv_bfloat16 *x0, *e1a, *p1, *e2a, *p2, *ba, *cat2, *d2a, *cat1, *d1a, *d1;
     uint8_t *arg1, *arg2;
     float* s;
     __nv_bfloat16 *g_d1b, *g_d1a, *g_cat1, *g_skip1, *g_d2b, *g_d2a, *g_cat2, *g_skip2, *g_bb, *g_ba, *g_p2,
@@ -104,8 +108,7 @@ struct RefineNet {
     float* amax = nullptr;
     int qB = 0, qH = 0, qW = 0;
     std::vector<std::pair<void*, size_t>> acts8;
-    uint8_t *q_x0, *q_e1a, *q_e1, *q_p1, *q_e2a, *q_e2, *q_p2, *q_ba, *q_bt, *q_cat2, *q_d2a, *q_d2, *q_cat1, *q_d1a,
-        *q_d1;
+    uint8_t *q_x0, *q_e1a, *q_p1, *q_e2a, *q_p2, *q_ba, *q_cat2, *q_d2a, *q_cat1, *q_d1a, *q_d1;
     // plain-synthesis outputs feeding fvv_synthesize_refined
     int sH = 0, sW = 0;
     std::vector<std::pair<void*, size_t>> syn;
@@ -235,18 +238,14 @@ fvv_status ensure_acts(fvv_ctx* c, RefineNet& N, int B, int H, int W)
     const size_t p1 = size_t(B) * H * W, p2 = p1 / 4, p3 = p1 / 16;
     const int w1 = N.L[1].cout, w2 = N.L[3].cout, w3 = N.L[5].cout;
     auto A = [&](__nv_bfloat16** p, size_t n) { return alloc_t(c, N.acts, p, n); };
-    FVV_TRY(A(&N.x0, p1 * 8));
+    FVV_TRY(A(&N.x0, p1 * kX0Stride));
     FVV_TRY(A(&N.e1a, p1 * w1));
-    FVV_TRY(A(&N.e1, p1 * w1));
     FVV_TRY(A(&N.p1, p2 * w1));
     FVV_TRY(A(&N.e2a, p2 * w2));
-    FVV_TRY(A(&N.e2, p2 * w2));
     FVV_TRY(A(&N.p2, p3 * w2));
     FVV_TRY(A(&N.ba, p3 * w3));
-    FVV_TRY(A(&N.bt, p3 * w3));
     FVV_TRY(A(&N.cat2, p2 * (w3 + w2)));
     FVV_TRY(A(&N.d2a, p2 * w2));
-    FVV_TRY(A(&N.d2, p2 * w2));
     FVV_TRY(A(&N.cat1, p1 * (w2 + w1)));
     FVV_TRY(A(&N.d1a, p1 * w1));
     FVV_TRY(A(&N.d1, p1 * w1));
@@ -275,14 +274,24 @@ fvv_status ensure_acts(fvv_ctx* c, RefineNet& N, int B, int H, int W)
     return FVV_OK;
 }
 
+// Where a conv writes: channel stride and offset of the output, and whether
+// it stores the 2x nearest upsampling (into a concatenation's first part).
+struct Out {
+    int ldy = 0, coff = 0, up2 = 0;
+};
+
 fvv_status conv(const ConvLayer& l, const __nv_bfloat16* x, int B, int H, int W, __nv_bfloat16* y, int* err,
-                cudaStream_t s)
+                cudaStream_t s, int xstride = 0, Out o = Out())
 {
     ConvArgs a{};
+    a.ldy = o.ldy;
+    a.coff = o.coff;
+    a.up2 = o.up2;
     a.bias = l.b;
     a.y = y;
     a.relu = 1;
     a.err = err;
+    a.xstride = xstride;
     FVV_CUDA(launch_conv3x3(x, B, H, W, l.cin, l.wbf, l.cout, a, s));
     return FVV_OK;
 }
@@ -292,9 +301,10 @@ fvv_status conv(const ConvLayer& l, const __nv_bfloat16* x, int B, int H, int W,
 // wt[ci][ky][kx][co]; for a concatenated input (split > 0) it runs once per
 // part, ci in [0, split) and [split, cin), into channel slices of dx.
 fvv_status conv_bwd(const ConvLayer& l, const __nv_bfloat16* x, const __nv_bfloat16* dz, int B, int H, int W,
-                    __nv_bfloat16* dx, const __nv_bfloat16* mask, int* err, cudaStream_t s, int split = 0)
+                    __nv_bfloat16* dx, const __nv_bfloat16* mask, int* err, cudaStream_t s, int split = 0,
+                    int xstride = 0)
 {
-    FVV_CUDA(launch_wgrad3x3(B, H, W, l.cin, l.cout, x, dz, l.gw, s));
+    FVV_CUDA(launch_wgrad3x3(B, H, W, l.cin, xstride ? xstride : l.cin, l.cout, x, dz, l.gw, s));
     FVV_CUDA(launch_bias_grad(size_t(B) * H * W, l.cout, dz, l.gb, s));
     if (dx) {
         const int parts = split > 0 ? 2 : 1;
@@ -321,19 +331,22 @@ fvv_status forward(RefineNet& N, const fvv_refine_batch& b, int* err, cudaStream
     const size_t npx = size_t(B) * H * W;
     const int H2 = H / 2, W2 = W / 2, H4 = H / 4, W4 = W / 4;
     const int w1 = N.L[1].cout, w2 = N.L[3].cout, w3 = N.L[5].cout;
+    // e1b and e2b write straight into the second part of the concatenations
+    // cat1 = [up2(d2b) | e1b] and cat2 = [up2(bb) | e2b]; bb and d2b write their
+    // 2x upsampling into the first parts.  No separate copies of e1b, e2b,
+    // bb or d2b exist.
+    const int l1 = w2 + w1, l2 = w3 + w2;
     FVV_CUDA(launch_pack_features(npx, b.rgb, b.depth, b.hole, b.top3, N.z_far, N.x0, s));
-    FVV_TRY(conv(N.L[0], N.x0, B, H, W, N.e1a, err, s));
-    FVV_TRY(conv(N.L[1], N.e1a, B, H, W, N.e1, err, s));
-    FVV_CUDA(launch_maxpool2(B, H, W, w1, N.e1, N.p1, N.arg1, s));
+    FVV_TRY(conv(N.L[0], N.x0, B, H, W, N.e1a, err, s, kX0Stride));
+    FVV_TRY(conv(N.L[1], N.e1a, B, H, W, N.cat1, err, s, 0, Out{l1, w2, 0}));
+    FVV_CUDA(launch_maxpool2(B, H, W, w1, N.cat1 + w2, l1, N.p1, N.arg1, s));
     FVV_TRY(conv(N.L[2], N.p1, B, H2, W2, N.e2a, err, s));
-    FVV_TRY(conv(N.L[3], N.e2a, B, H2, W2, N.e2, err, s));
-    FVV_CUDA(launch_maxpool2(B, H2, W2, w2, N.e2, N.p2, N.arg2, s));
+    FVV_TRY(conv(N.L[3], N.e2a, B, H2, W2, N.cat2, err, s, 0, Out{l2, w3, 0}));
+    FVV_CUDA(launch_maxpool2(B, H2, W2, w2, N.cat2 + w3, l2, N.p2, N.arg2, s));
     FVV_TRY(conv(N.L[4], N.p2, B, H4, W4, N.ba, err, s));
-    FVV_TRY(conv(N.L[5], N.ba, B, H4, W4, N.bt, err, s));
-    FVV_CUDA(launch_up2_concat(B, H2, W2, w3, w2, N.bt, N.e2, N.cat2, s));
+    FVV_TRY(conv(N.L[5], N.ba, B, H4, W4, N.cat2, err, s, 0, Out{l2, 0, 1}));
     FVV_TRY(conv(N.L[6], N.cat2, B, H2, W2, N.d2a, err, s));
-    FVV_TRY(conv(N.L[7], N.d2a, B, H2, W2, N.d2, err, s));
-    FVV_CUDA(launch_up2_concat(B, H, W, w2, w1, N.d2, N.e1, N.cat1, s));
+    FVV_TRY(conv(N.L[7], N.d2a, B, H2, W2, N.cat1, err, s, 0, Out{l1, 0, 1}));
     FVV_TRY(conv(N.L[8], N.cat1, B, H, W, N.d1a, err, s));
     FVV_TRY(conv(N.L[9], N.d1a, B, H, W, N.d1, err, s));
     FVV_CUDA(launch_head_fwd(npx, w1, N.d1, N.wout, N.bout, b.rgb, N.s, out, W, out_pitch, out_f32, s));
@@ -356,18 +369,18 @@ fvv_status backward(RefineNet& N, const fvv_refine_batch& b, int* err, cudaStrea
     FVV_CUDA(launch_head_bwd(npx, w1, N.d1, N.wout, N.s, b.target, N.loss, N.gwout, N.gbout, N.g_d1b, s));
     FVV_TRY(conv_bwd(N.L[9], N.d1a, N.g_d1b, B, H, W, N.g_d1a, N.d1a, err, s));
     FVV_TRY(conv_bwd(N.L[8], N.cat1, N.g_d1a, B, H, W, N.g_cat1, nullptr, err, s, w2));
-    FVV_CUDA(launch_up2_concat_bwd(B, H, W, w2, w1, N.g_cat1, N.d2, N.g_d2b, N.g_skip1, s));
+    FVV_CUDA(launch_up2_concat_bwd(B, H, W, w2, w1, N.g_cat1, N.cat1, w2 + w1, N.g_d2b, N.g_skip1, s));
     FVV_TRY(conv_bwd(N.L[7], N.d2a, N.g_d2b, B, H2, W2, N.g_d2a, N.d2a, err, s));
     FVV_TRY(conv_bwd(N.L[6], N.cat2, N.g_d2a, B, H2, W2, N.g_cat2, nullptr, err, s, w3));
-    FVV_CUDA(launch_up2_concat_bwd(B, H2, W2, w3, w2, N.g_cat2, N.bt, N.g_bb, N.g_skip2, s));
+    FVV_CUDA(launch_up2_concat_bwd(B, H2, W2, w3, w2, N.g_cat2, N.cat2, w3 + w2, N.g_bb, N.g_skip2, s));
     FVV_TRY(conv_bwd(N.L[5], N.ba, N.g_bb, B, H4, W4, N.g_ba, N.ba, err, s));
     FVV_TRY(conv_bwd(N.L[4], N.p2, N.g_ba, B, H4, W4, N.g_p2, nullptr, err, s));
-    FVV_CUDA(launch_maxpool2_bwd(B, H2, W2, w2, N.g_p2, N.arg2, N.g_skip2, N.e2, N.g_e2b, s));
+    FVV_CUDA(launch_maxpool2_bwd(B, H2, W2, w2, N.g_p2, N.arg2, N.g_skip2, N.cat2 + w3, w3 + w2, N.g_e2b, s));
     FVV_TRY(conv_bwd(N.L[3], N.e2a, N.g_e2b, B, H2, W2, N.g_e2a, N.e2a, err, s));
     FVV_TRY(conv_bwd(N.L[2], N.p1, N.g_e2a, B, H2, W2, N.g_p1, nullptr, err, s));
-    FVV_CUDA(launch_maxpool2_bwd(B, H, W, w1, N.g_p1, N.arg1, N.g_skip1, N.e1, N.g_e1b, s));
+    FVV_CUDA(launch_maxpool2_bwd(B, H, W, w1, N.g_p1, N.arg1, N.g_skip1, N.cat1 + w2, w2 + w1, N.g_e1b, s));
     FVV_TRY(conv_bwd(N.L[1], N.e1a, N.g_e1b, B, H, W, N.g_e1a, N.e1a, err, s));
-    FVV_TRY(conv_bwd(N.L[0], N.x0, N.g_e1a, B, H, W, nullptr, nullptr, err, s));
+    FVV_TRY(conv_bwd(N.L[0], N.x0, N.g_e1a, B, H, W, nullptr, nullptr, err, s, 0, kX0Stride));
     return FVV_OK;
 }
 
@@ -380,18 +393,14 @@ fvv_status ensure_acts8(fvv_ctx* c, RefineNet& N, int B, int H, int W)
     const size_t p1 = size_t(B) * H * W, p2 = p1 / 4, p3 = p1 / 16;
     const int w1 = N.L[1].cout, w2 = N.L[3].cout, w3 = N.L[5].cout;
     auto A = [&](uint8_t** p, size_t n) { return alloc_t(c, N.acts8, p, n); };
-    FVV_TRY(A(&N.q_x0, p1 * 16));
+    FVV_TRY(A(&N.q_x0, p1 * kX0StrideQ));
     FVV_TRY(A(&N.q_e1a, p1 * w1));
-    FVV_TRY(A(&N.q_e1, p1 * w1));
     FVV_TRY(A(&N.q_p1, p2 * w1));
     FVV_TRY(A(&N.q_e2a, p2 * w2));
-    FVV_TRY(A(&N.q_e2, p2 * w2));
     FVV_TRY(A(&N.q_p2, p3 * w2));
     FVV_TRY(A(&N.q_ba, p3 * w3));
-    FVV_TRY(A(&N.q_bt, p3 * w3));
     FVV_TRY(A(&N.q_cat2, p2 * (w3 + w2)));
     FVV_TRY(A(&N.q_d2a, p2 * w2));
-    FVV_TRY(A(&N.q_d2, p2 * w2));
     FVV_TRY(A(&N.q_cat1, p1 * (w2 + w1)));
     FVV_TRY(A(&N.q_d1a, p1 * w1));
     FVV_TRY(A(&N.q_d1, p1 * w1));
@@ -402,9 +411,12 @@ fvv_status ensure_acts8(fvv_ctx* c, RefineNet& N, int B, int H, int W)
 }
 
 fvv_status conv_e4m3(const ConvLayer& l, const uint8_t* x, int B, int H, int W, uint8_t* y, int* err,
-                     cudaStream_t s)
+                     cudaStream_t s, int xstride = 0, Out o = Out())
 {
     ConvArgs a{};
+    a.ldy = o.ldy;
+    a.coff = o.coff;
+    a.up2 = o.up2;
     a.bias = l.b;
     a.y = reinterpret_cast<__nv_bfloat16*>(y);
     a.relu = 1;
@@ -412,6 +424,7 @@ fvv_status conv_e4m3(const ConvLayer& l, const uint8_t* x, int B, int H, int W, 
     a.acc_scale = l.acc_scale;
     a.out_inv_scale = l.out_inv_scale;
     a.err = err;
+    a.xstride = xstride;
     FVV_CUDA(launch_conv3x3(x, B, H, W, l.cin_q, l.wq, l.cout, a, s));
     return FVV_OK;
 }
@@ -425,18 +438,17 @@ fvv_status forward_e4m3(RefineNet& N, const fvv_refine_batch& b, int* err, cudaS
     const int H2 = H / 2, W2 = W / 2, H4 = H / 4, W4 = W / 4;
     const int w1 = N.L[1].cout, w2 = N.L[3].cout, w3 = N.L[5].cout;
     FVV_CUDA(launch_pack_features_e4m3(npx, b.rgb, b.depth, b.hole, b.top3, N.z_far, N.s0, N.q_x0, s));
-    FVV_TRY(conv_e4m3(N.L[0], N.q_x0, B, H, W, N.q_e1a, err, s));
-    FVV_TRY(conv_e4m3(N.L[1], N.q_e1a, B, H, W, N.q_e1, err, s));
-    FVV_CUDA(launch_maxpool2_e4m3(B, H, W, w1, N.q_e1, N.q_p1, s));
+    const int l1 = w2 + w1, l2 = w3 + w2;                 // concatenations written in place
+    FVV_TRY(conv_e4m3(N.L[0], N.q_x0, B, H, W, N.q_e1a, err, s, kX0StrideQ));
+    FVV_TRY(conv_e4m3(N.L[1], N.q_e1a, B, H, W, N.q_cat1, err, s, 0, Out{l1, w2, 0}));
+    FVV_CUDA(launch_maxpool2_e4m3(B, H, W, w1, N.q_cat1 + w2, l1, N.q_p1, s));
     FVV_TRY(conv_e4m3(N.L[2], N.q_p1, B, H2, W2, N.q_e2a, err, s));
-    FVV_TRY(conv_e4m3(N.L[3], N.q_e2a, B, H2, W2, N.q_e2, err, s));
-    FVV_CUDA(launch_maxpool2_e4m3(B, H2, W2, w2, N.q_e2, N.q_p2, s));
+    FVV_TRY(conv_e4m3(N.L[3], N.q_e2a, B, H2, W2, N.q_cat2, err, s, 0, Out{l2, w3, 0}));
+    FVV_CUDA(launch_maxpool2_e4m3(B, H2, W2, w2, N.q_cat2 + w3, l2, N.q_p2, s));
     FVV_TRY(conv_e4m3(N.L[4], N.q_p2, B, H4, W4, N.q_ba, err, s));
-    FVV_TRY(conv_e4m3(N.L[5], N.q_ba, B, H4, W4, N.q_bt, err, s));
-    FVV_CUDA(launch_up2_concat_e4m3(B, H2, W2, w3, w2, N.q_bt, N.q_e2, N.q_cat2, s));
+    FVV_TRY(conv_e4m3(N.L[5], N.q_ba, B, H4, W4, N.q_cat2, err, s, 0, Out{l2, 0, 1}));
     FVV_TRY(conv_e4m3(N.L[6], N.q_cat2, B, H2, W2, N.q_d2a, err, s));
-    FVV_TRY(conv_e4m3(N.L[7], N.q_d2a, B, H2, W2, N.q_d2, err, s));
-    FVV_CUDA(launch_up2_concat_e4m3(B, H, W, w2, w1, N.q_d2, N.q_e1, N.q_cat1, s));
+    FVV_TRY(conv_e4m3(N.L[7], N.q_d2a, B, H2, W2, N.q_cat1, err, s, 0, Out{l1, 0, 1}));
     FVV_TRY(conv_e4m3(N.L[8], N.q_cat1, B, H, W, N.q_d1a, err, s));
     FVV_TRY(conv_e4m3(N.L[9], N.q_d1a, B, H, W, N.q_d1, err, s));
     FVV_CUDA(launch_head_fwd_e4m3(npx, w1, N.q_d1, N.s_act[9], N.wout, N.bout, b.rgb, out, W, out_pitch, out_f32,
@@ -765,11 +777,16 @@ fvv_status fvv_refine_quantize(fvv_ctx* c, const fvv_refine_batch* calib, const 
         FVV_TRY(fvv::forward(*N, *calib, err, s, nullptr, 0, nullptr));
         FVV_TRY(fvv::check_flag(err, s, "fvv_refine_quantize"));
         const size_t p1 = size_t(calib->n) * calib->height * calib->width, p2 = p1 / 4, p3 = p1 / 16;
-        const __nv_bfloat16* t[10] = {N->e1a, N->e1, N->e2a, N->e2, N->ba, N->bt, N->d2a, N->d2, N->d1a, N->d1};
-        const size_t np[10] = {p1, p1, p2, p2, p3, p3, p2, p2, p1, p1};
+        const int w1 = N->L[1].cout, w2 = N->L[3].cout, w3 = N->L[5].cout;
+        // e1b, e2b, bb, d2b live inside the concatenations (bb and d2b upsampled:
+        // the same maximum)
+        const __nv_bfloat16* t[10] = {N->e1a, N->cat1 + w2, N->e2a, N->cat2 + w3, N->ba,
+                                      N->cat2, N->d2a, N->cat1, N->d1a, N->d1};
+        const size_t np[10] = {p1, p1, p2, p2, p3, p2, p2, p1, p1, p1};
+        const int ld[10] = {w1, w2 + w1, w2, w3 + w2, w3, w3 + w2, w2, w2 + w1, w1, w1};
         FVV_CUDA(cudaMemsetAsync(N->amax, 0, 10 * sizeof(float), s));
         for (int i = 0; i < 10; ++i)
-            FVV_CUDA(fvv::launch_amax(np[i] * N->L[i].cout, t[i], N->amax + i, s));
+            FVV_CUDA(fvv::launch_amax(np[i], N->L[i].cout, t[i], ld[i], N->amax + i, s));
         float am[10];
         FVV_CUDA(cudaMemcpyAsync(am, N->amax, sizeof am, cudaMemcpyDeviceToHost, s));
         FVV_CUDA(cudaStreamSynchronize(s));

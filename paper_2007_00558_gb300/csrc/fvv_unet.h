@@ -10,10 +10,14 @@ namespace fvv {
 // Arguments of one tensor-core 3x3 convolution (pad 1), NHWC.
 struct ConvArgs {
     int NB, H, W, Cin;              // input; Cin a multiple of 8 (bf16) or 16 (e4m3)
+    int xstride;                    // input channels per pixel in memory (0: Cin); channels
+                                    // Cin..xstride-1 are read but must hold zeros
     int tiles_x;                    // ceil(W / 128), set by the launcher
     const float* bias;              // [Cout] or null (16-byte aligned)
     __nv_bfloat16* y;               // output pixel p, channel c at y[p * ldy + coff + c] (e4m3: bytes)
     int ldy, coff;                  // output channel stride (0: Cout) and offset
+    int up2;                        // 1: store each output pixel (y, x) at the four pixels
+                                    // (2y + dy, 2x + dx) of a [NB][2H][2W][ldy] tensor
     int relu;                       // 1: max(0, .)
     const __nv_bfloat16* mask;      // optional [NB][H][W][Cout] (bf16 only): zero where mask <= 0
     int fp8;                        // 1: x, w and y are e4m3
@@ -35,15 +39,17 @@ namespace fvv {
 // fvv_unet_ops.cu (CUDA-core layers)
 cudaError_t launch_pack_features(size_t npx, const uint8_t* rgb, const float* depth, const uint8_t* hole,
                                  const float* top3, float z_far, __nv_bfloat16* out, cudaStream_t s);
-cudaError_t launch_maxpool2(int B, int H, int W, int C, const __nv_bfloat16* x, __nv_bfloat16* y, uint8_t* arg,
-                            cudaStream_t s);
+// x (pixel stride ldx channels) -> y [B][H/2][W/2][C] and the window position
+cudaError_t launch_maxpool2(int B, int H, int W, int C, const __nv_bfloat16* x, int ldx, __nv_bfloat16* y,
+                            uint8_t* arg, cudaStream_t s);
+// dx = route(dy by arg) + add, zeroed where mask (pixel stride ldm) <= 0
 cudaError_t launch_maxpool2_bwd(int B, int H, int W, int C, const __nv_bfloat16* dy, const uint8_t* arg,
-                                const __nv_bfloat16* add, const __nv_bfloat16* mask, __nv_bfloat16* dx,
+                                const __nv_bfloat16* add, const __nv_bfloat16* mask, int ldm, __nv_bfloat16* dx,
                                 cudaStream_t s);
-cudaError_t launch_up2_concat(int B, int H, int W, int C1, int C2, const __nv_bfloat16* lo,
-                              const __nv_bfloat16* skip, __nv_bfloat16* cat, cudaStream_t s);
+// backward of cat = [up2(lo) | skip]: up_act is up2(lo) inside a full-resolution
+// tensor of pixel stride ldu (lo's ReLU mask)
 cudaError_t launch_up2_concat_bwd(int B, int H, int W, int C1, int C2, const __nv_bfloat16* dcat,
-                                  const __nv_bfloat16* lo_act, __nv_bfloat16* dlo, __nv_bfloat16* dskip,
+                                  const __nv_bfloat16* up_act, int ldu, __nv_bfloat16* dlo, __nv_bfloat16* dskip,
                                   cudaStream_t s);
 bool head_width_supported(int c1);              // w1 of the 1x1 head: 32, 48 or 64
 cudaError_t launch_head_fwd(size_t npx, int C1, const __nv_bfloat16* d1, const float* wout, const float* bout,
@@ -55,14 +61,13 @@ cudaError_t launch_head_bwd(size_t npx, int C1, const __nv_bfloat16* d1, const f
 // e4m3 inference forms: activations are e4m3 codes with per-tensor scales
 cudaError_t launch_pack_features_e4m3(size_t npx, const uint8_t* rgb, const float* depth, const uint8_t* hole,
                                       const float* top3, float z_far, float s0, uint8_t* out, cudaStream_t s);
-cudaError_t launch_maxpool2_e4m3(int B, int H, int W, int C, const uint8_t* x, uint8_t* y, cudaStream_t s);
-cudaError_t launch_up2_concat_e4m3(int B, int H, int W, int C1, int C2, const uint8_t* lo, const uint8_t* skip,
-                                   uint8_t* cat, cudaStream_t s);
+cudaError_t launch_maxpool2_e4m3(int B, int H, int W, int C, const uint8_t* x, int ldx, uint8_t* y, cudaStream_t s);
 cudaError_t launch_head_fwd_e4m3(size_t npx, int C1, const uint8_t* d1, float s_d1, const float* wout,
                                  const float* bout, const uint8_t* rgb, uint8_t* out, int W, size_t out_pitch,
                                  float* out_f32, cudaStream_t s);
-cudaError_t launch_amax(size_t n, const __nv_bfloat16* x, float* out, cudaStream_t s);
-cudaError_t launch_wgrad3x3(int B, int H, int W, int Cin, int Cout, const __nv_bfloat16* x,
+// out = max(out, max |x|) over npix pixels of C channels, pixel stride ld
+cudaError_t launch_amax(size_t npix, int C, const __nv_bfloat16* x, int ld, float* out, cudaStream_t s);
+cudaError_t launch_wgrad3x3(int B, int H, int W, int Cin, int xstride, int Cout, const __nv_bfloat16* x,
                             const __nv_bfloat16* dz, float* dw, cudaStream_t s);
 cudaError_t launch_bias_grad(size_t npx, int C, const __nv_bfloat16* dz, float* db, cudaStream_t s);
 cudaError_t launch_flip_weights(int Cout, int Cin, const float* w, __nv_bfloat16* wbf, __nv_bfloat16* wt,

@@ -117,6 +117,28 @@ __device__ __forceinline__ void mma_row(uint32_t d, uint64_t da, uint64_t db, ui
     }
 }
 
+// All MMAs of one channel group with resident weights: taps (ky, kx), NKS
+// K-steps each, every descriptor offset a compile-time constant.
+template <int COUT, bool FP8, int NKS>
+__device__ __forceinline__ void mma_group(uint32_t d, uint64_t da, uint64_t db, uint32_t idesc, uint32_t acc0)
+{
+    using Cfg = ConvCfg<COUT>;
+#pragma unroll
+    for (int ky = 0; ky < 3; ++ky)
+#pragma unroll
+        for (int kx = 0; kx < 3; ++kx)
+#pragma unroll
+            for (int ks = 0; ks < NKS; ++ks) {
+                const uint64_t a = da + uint64_t(((ky * kHaloPx + kx) * kRow) >> 4) + 2 * ks;
+                const uint64_t b = db + uint64_t((ky * Cfg::kSlice + kx * Cfg::kTap) >> 4) + 2 * ks;
+                const uint32_t acc = (ky | kx | ks) != 0 ? 1u : acc0;
+                if (FP8)
+                    tc::mma_e4m3(d, a, b, idesc, acc);
+                else
+                    tc::mma_bf16(d, a, b, idesc, acc);
+            }
+}
+
 // FP8: e4m3 operands and output (K = 32 channels per MMA, 64 per group);
 // otherwise bf16 (K = 16, 32 per group).
 template <int COUT, bool FP8>
@@ -217,59 +239,74 @@ k_conv3x3_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CU
         }
     } else if (warp == 1) {
         // ------------------------------------------------------------ MMA issuer
+        // Ring slots and phase parities are running counters; every channel
+        // group but the last holds two K-steps.  With resident weights a
+        // group is one straight run of MMAs with compile-time descriptor
+        // offsets (the issue loop is the critical path of the kernel).
         if (lane == 0) {
             constexpr uint32_t idesc = FP8 ? tc::idesc_e4m3(kTileM, COUT) : tc::idesc_bf16(kTileM, COUT);
             bool ok = !resident || tc::mbar_wait(wready, 0, P.err, 3);
-            uint32_t qh = 0, qw = 0;
-            int tl = 0;
-            for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x, ++tl) {
-                const int b = tl % Cfg::kNumAcc;
-                if (!tc::mbar_wait(&acc_empty[b], ((tl / Cfg::kNumAcc) & 1) ^ 1, P.err, 4)) {
+            const int nks_last = (min(kPerGroup, Cin - (G - 1) * kPerGroup) * kEsize + 31) / 32;
+            const uint64_t dh0 = tc::desc_kmajor_sw64(tc::smem_u32(sHalo));
+            const uint64_t dw0 = tc::desc_kmajor_sw64(tc::smem_u32(sW));
+            int sh = 0, sw = 0, b = 0;
+            uint32_t ph = 0, pw = 0, pb = 0;
+            for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
+                if (!tc::mbar_wait(&acc_empty[b], pb ^ 1u, P.err, 4)) {
                     ok = false;
                     break;
                 }
                 tc::fence_after_sync();
                 const uint32_t d = tmem + uint32_t(b * Cfg::kAcc);
-                for (int g = 0; g < G && ok; ++g, ++qh) {
-                    const int sh = int(qh % uint32_t(HS));
-                    if (!tc::mbar_wait(&full_h[sh], (qh / uint32_t(HS)) & 1u, P.err, 5)) {
+                for (int g = 0; g < G; ++g) {
+                    // TMA completion on the mbarrier orders the halo for the tensor
+                    // cores (both async proxy): no tcgen05 fence here
+                    if (!tc::mbar_wait(&full_h[sh], ph, P.err, 5)) {
                         ok = false;
                         break;
                     }
-                    tc::fence_after_sync();
-                    // K-steps of 32 bytes holding channels of this group (1 or 2)
-                    const int bytes = min(kPerGroup, Cin - g * kPerGroup) * kEsize;
-                    const int nks = (bytes + 31) / 32;
-                    const uint64_t da = tc::desc_kmajor_sw64(tc::smem_u32(sHalo + sh * kHaloStage));
-                    for (int ky = 0; ky < 3 && ok; ++ky) {
-                        uint8_t* slice;
-                        int sw = 0;
-                        if (resident) {
-                            slice = sW + g * Cfg::kGroup + ky * Cfg::kSlice;
-                        } else {
-                            sw = int(qw % uint32_t(WS));
-                            if (!tc::mbar_wait(&full_w[sw], (qw / uint32_t(WS)) & 1u, P.err, 6)) {
+                    const uint64_t da = dh0 + uint64_t((sh * kHaloStage) >> 4);
+                    const bool two = g < G - 1 || nks_last == 2;
+                    const uint32_t acc0 = g != 0 ? 1u : 0u;
+                    if (resident) {
+                        const uint64_t db = dw0 + uint64_t((g * Cfg::kGroup) >> 4);
+                        if (two)
+                            mma_group<COUT, FP8, 2>(d, da, db, idesc, acc0);
+                        else
+                            mma_group<COUT, FP8, 1>(d, da, db, idesc, acc0);
+                    } else {
+                        for (int ky = 0; ky < 3; ++ky) {
+                            if (!tc::mbar_wait(&full_w[sw], pw, P.err, 6)) {
                                 ok = false;
                                 break;
                             }
-                            tc::fence_after_sync();
-                            slice = sW + sw * Cfg::kSlice;
-                        }
-                        const uint64_t db = tc::desc_kmajor_sw64(tc::smem_u32(slice));
-                        const uint32_t acc0 = (g | ky) != 0 ? 1u : 0u;
-                        if (nks > 1)
-                            mma_row<COUT, FP8, 2>(d, da + uint64_t((ky * kHaloPx * kRow) >> 4), db, idesc, acc0);
-                        else
-                            mma_row<COUT, FP8, 1>(d, da + uint64_t((ky * kHaloPx * kRow) >> 4), db, idesc, acc0);
-                        if (!resident) {
+                            const uint64_t db = dw0 + uint64_t((sw * Cfg::kSlice) >> 4);
+                            const uint64_t dak = da + uint64_t((ky * kHaloPx * kRow) >> 4);
+                            const uint32_t a0 = acc0 | (ky != 0 ? 1u : 0u);
+                            if (two)
+                                mma_row<COUT, FP8, 2>(d, dak, db, idesc, a0);
+                            else
+                                mma_row<COUT, FP8, 1>(d, dak, db, idesc, a0);
                             tc::mma_commit(&empty_w[sw]);      // the slice is free once these finish
-                            ++qw;
+                            if (++sw == WS) {
+                                sw = 0;
+                                pw ^= 1u;
+                            }
                         }
+                        if (!ok) break;
                     }
                     tc::mma_commit(&empty_h[sh]);              // the halo slot is free once these finish
+                    if (++sh == HS) {
+                        sh = 0;
+                        ph ^= 1u;
+                    }
                 }
                 if (!ok) break;
                 tc::mma_commit(&acc_full[b]);                  // the tile's accumulator is complete
+                if (++b == Cfg::kNumAcc) {
+                    b = 0;
+                    pb ^= 1u;
+                }
             }
             tc::mma_commit(drain);                             // every issued MMA has finished
         }
@@ -283,7 +320,12 @@ k_conv3x3_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CU
             tc::fence_after_sync();
             const int xt = tile % P.tiles_x, row = tile / P.tiles_x;
             const int x = xt * kTileM + qd * 32 + lane;
-            const size_t opix = size_t(row) * Wd + x;
+            size_t opix = size_t(row) * Wd + x;
+            if (P.up2) {                                       // top-left of the 2 x 2 block
+                const int n = row / H, y = row - n * H;
+                opix = (size_t(n) * 2 * H + 2 * y) * (2 * size_t(Wd)) + 2 * size_t(x);
+            }
+            const size_t rowstep = 2 * size_t(Wd);            // up2: the next output row
             const uint32_t taddr = tmem + (uint32_t(qd * 32) << 16) + uint32_t(b * Cfg::kAcc);
             // up to 64 columns per TMEM round trip, in units of 16
 #pragma unroll 1
@@ -309,11 +351,18 @@ k_conv3x3_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CU
                         if (FP8) {
                             uint8_t* dst = reinterpret_cast<uint8_t*>(P.y) + opix * P.ldy + P.coff + c;
                             const float sc = P.out_inv_scale;
-                            *reinterpret_cast<uint4*>(dst) =
+                            const uint4 q =
                                 make_uint4(pack_e4m3x4(v[0] * sc, v[1] * sc, v[2] * sc, v[3] * sc),
                                            pack_e4m3x4(v[4] * sc, v[5] * sc, v[6] * sc, v[7] * sc),
                                            pack_e4m3x4(v[8] * sc, v[9] * sc, v[10] * sc, v[11] * sc),
                                            pack_e4m3x4(v[12] * sc, v[13] * sc, v[14] * sc, v[15] * sc));
+                            *reinterpret_cast<uint4*>(dst) = q;
+                            if (P.up2) {
+                                const size_t ld = size_t(P.ldy);
+                                *reinterpret_cast<uint4*>(dst + ld) = q;
+                                *reinterpret_cast<uint4*>(dst + rowstep * ld) = q;
+                                *reinterpret_cast<uint4*>(dst + (rowstep + 1) * ld) = q;
+                            }
                         } else {
                             if (P.mask) {
                                 const __nv_bfloat16* m = P.mask + opix * COUT + c;
@@ -324,11 +373,18 @@ k_conv3x3_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CU
                                     if (!(__bfloat162float(mm.y) > 0.0f)) v[j + 1] = 0.0f;
                                 }
                             }
-                            uint4* dst = reinterpret_cast<uint4*>(P.y + opix * P.ldy + P.coff + c);
-                            dst[0] = make_uint4(pack_bf16x2(v[0], v[1]), pack_bf16x2(v[2], v[3]),
-                                                pack_bf16x2(v[4], v[5]), pack_bf16x2(v[6], v[7]));
-                            dst[1] = make_uint4(pack_bf16x2(v[8], v[9]), pack_bf16x2(v[10], v[11]),
-                                                pack_bf16x2(v[12], v[13]), pack_bf16x2(v[14], v[15]));
+                            __nv_bfloat16* dst = P.y + opix * P.ldy + P.coff + c;
+                            const uint4 q0 = make_uint4(pack_bf16x2(v[0], v[1]), pack_bf16x2(v[2], v[3]),
+                                                        pack_bf16x2(v[4], v[5]), pack_bf16x2(v[6], v[7]));
+                            const uint4 q1 = make_uint4(pack_bf16x2(v[8], v[9]), pack_bf16x2(v[10], v[11]),
+                                                        pack_bf16x2(v[12], v[13]), pack_bf16x2(v[14], v[15]));
+                            const int nst = P.up2 ? 4 : 1;
+                            for (int k = 0; k < nst; ++k) {
+                                const size_t off = (k >> 1) * rowstep + (k & 1);     // pixels from the first
+                                uint4* d4 = reinterpret_cast<uint4*>(dst + off * P.ldy);
+                                d4[0] = q0;
+                                d4[1] = q1;
+                            }
                         }
                     }
                 }
@@ -414,7 +470,7 @@ cudaError_t launch_conv(const void* x, const void* w, const ConvArgs& a, cudaStr
     const Plan p = make_plan<COUT>(G);
     if (p.hs < 2 || (!p.resident && p.ws < 2)) return cudaErrorInvalidValue;
     CUtensorMap mx, mw;
-    cudaError_t e = make_halo_map(&mx, x, a.NB, a.H, a.W, a.Cin, FP8);
+    cudaError_t e = make_halo_map(&mx, x, a.NB, a.H, a.W, a.xstride, FP8);
     if (e != cudaSuccess) return e;
     e = make_weight_map(&mw, w, COUT, a.Cin, FP8);
     if (e != cudaSuccess) return e;
@@ -457,6 +513,9 @@ cudaError_t launch_conv3x3(const void* x, int NB, int H, int W, int Cin, const v
     a.H = H;
     a.W = W;
     a.Cin = Cin;
+    if (a.xstride == 0) a.xstride = Cin;
+    if (a.mask && (a.up2 || a.coff || (a.ldy && a.ldy != Cout))) return cudaErrorInvalidValue;
+    if (a.xstride < Cin || a.xstride % (fp8 ? 16 : 8)) return cudaErrorInvalidValue;
     a.tiles_x = (W + kTileM - 1) / kTileM;
     if (a.ldy == 0) a.ldy = Cout;
     if (a.acc_scale == 0.0f) a.acc_scale = 1.0f;

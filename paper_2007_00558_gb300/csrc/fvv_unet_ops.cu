@@ -29,7 +29,9 @@ __device__ __forceinline__ float block_sum(float v, float* red)
 }
 
 // ---- input features ----------------------------------------------------------
-// 8 channels: RGB / 255, depth / z_far, hole, top-3 weights.
+// 8 channels: RGB / 255, depth / z_far, hole, top-3 weights, stored in one
+// 64-byte row per pixel (bf16: channels 8..31 zero; e4m3: bytes 8..63 zero) so
+// that the convolution's halo copies move whole contiguous rows.
 __device__ __forceinline__ void features(size_t p, const uint8_t* __restrict__ rgb, const float* __restrict__ depth,
                                          const uint8_t* __restrict__ hole, const float* __restrict__ top3,
                                          float inv_zfar, float f[8])
@@ -58,10 +60,12 @@ __global__ void k_pack_features(size_t npx, const uint8_t* __restrict__ rgb, con
         const __nv_bfloat162 h = __floats2bfloat162_rn(f[2 * i], f[2 * i + 1]);
         w[i] = *reinterpret_cast<const uint32_t*>(&h);
     }
-    reinterpret_cast<uint4*>(out)[p] = make_uint4(w[0], w[1], w[2], w[3]);
+    uint4* dst = reinterpret_cast<uint4*>(out) + 4 * p;          // 32 channels per pixel
+    dst[0] = make_uint4(w[0], w[1], w[2], w[3]);
+    dst[1] = dst[2] = dst[3] = make_uint4(0u, 0u, 0u, 0u);
 }
 
-// e4m3 codes of feature / s0 in channels 0..7, zero codes in 8..15
+// e4m3 codes of feature / s0 in bytes 0..7, zero in 8..63
 __global__ void k_pack_features_e4m3(size_t npx, const uint8_t* __restrict__ rgb, const float* __restrict__ depth,
                                      const uint8_t* __restrict__ hole, const float* __restrict__ top3,
                                      float inv_zfar, float inv_s0, uint8_t* __restrict__ out)
@@ -79,7 +83,9 @@ __global__ void k_pack_features_e4m3(size_t npx, const uint8_t* __restrict__ rgb
             make_float2(f[4 * i + 2] * inv_s0, f[4 * i + 3] * inv_s0), __NV_SATFINITE, __NV_E4M3);
         w[i] = uint32_t(lo) | (uint32_t(hi) << 16);
     }
-    reinterpret_cast<uint4*>(out)[p] = make_uint4(w[0], w[1], 0u, 0u);
+    uint4* dst = reinterpret_cast<uint4*>(out) + 4 * p;          // 64 bytes per pixel
+    dst[0] = make_uint4(w[0], w[1], 0u, 0u);
+    dst[1] = dst[2] = dst[3] = make_uint4(0u, 0u, 0u, 0u);
 }
 
 // ---- 8-channel vectors: every channel count here is a multiple of 8 ---------
@@ -111,7 +117,7 @@ __device__ __forceinline__ void st8(__nv_bfloat16* p, const uint4 v) { *reinterp
 // ---- pooling -----------------------------------------------------------------
 // One thread per output pixel and 8 channels.  The first maximum of the 2x2
 // window, in the order (0,0), (0,1), (1,0), (1,1), wins; its position is kept.
-__global__ void k_maxpool2(int B, int H, int W, int C, const __nv_bfloat16* __restrict__ x,
+__global__ void k_maxpool2(int B, int H, int W, int C, const __nv_bfloat16* __restrict__ x, int ldx,
                            __nv_bfloat16* __restrict__ y, uint8_t* __restrict__ arg)
 {
     const size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -124,9 +130,9 @@ __global__ void k_maxpool2(int B, int H, int W, int C, const __nv_bfloat16* __re
     r /= w2;
     const int oy = int(r % h2);
     const int b = int(r / h2);
-    const size_t base = ((size_t(b) * H + 2 * oy) * W + 2 * ox) * C + c;
-    const uint4 q[4] = {ld8(x + base), ld8(x + base + C), ld8(x + base + size_t(W) * C),
-                        ld8(x + base + size_t(W) * C + C)};
+    const size_t base = ((size_t(b) * H + 2 * oy) * W + 2 * ox) * ldx + c;
+    const uint4 q[4] = {ld8(x + base), ld8(x + base + ldx), ld8(x + base + size_t(W) * ldx),
+                        ld8(x + base + size_t(W) * ldx + ldx)};
     float v[4][8];
 #pragma unroll
     for (int k = 0; k < 4; ++k) unpack8(q[k], v[k]);
@@ -152,7 +158,7 @@ __global__ void k_maxpool2(int B, int H, int W, int C, const __nv_bfloat16* __re
 // one thread per input pixel and 8 channels
 __global__ void k_maxpool2_bwd(int B, int H, int W, int C, const __nv_bfloat16* __restrict__ dy,
                                const uint8_t* __restrict__ arg, const __nv_bfloat16* __restrict__ add,
-                               const __nv_bfloat16* __restrict__ mask, __nv_bfloat16* __restrict__ dx)
+                               const __nv_bfloat16* __restrict__ mask, int ldm, __nv_bfloat16* __restrict__ dx)
 {
     const size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
     const int cv = C >> 3;
@@ -160,6 +166,7 @@ __global__ void k_maxpool2_bwd(int B, int H, int W, int C, const __nv_bfloat16* 
     if (i >= n) return;
     const int c = int(i % cv) * 8;
     size_t r = i / cv;
+    const size_t r0 = r;                                  // input pixel index
     const int x = int(r % W);
     r /= W;
     const int yy = int(r % H);
@@ -172,7 +179,7 @@ __global__ void k_maxpool2_bwd(int B, int H, int W, int C, const __nv_bfloat16* 
     const uint2 av = *reinterpret_cast<const uint2*>(arg + j);
     const uint8_t* a8 = reinterpret_cast<const uint8_t*>(&av);
     if (add) unpack8(ld8(add + i * 8), ad);
-    if (mask) unpack8(ld8(mask + i * 8), m);
+    if (mask) unpack8(ld8(mask + r0 * ldm + c), m);
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
         float v = a8[q] == k ? g[q] : 0.0f;
@@ -183,34 +190,11 @@ __global__ void k_maxpool2_bwd(int B, int H, int W, int C, const __nv_bfloat16* 
     st8(dx + i * 8, pack8(g));
 }
 
-// ---- upsampling + concat ------------------------------------------------------
-// cat[b, y, x] = [ up(lo)[b, y, x, 0:C1] | skip[b, y, x, 0:C2] ]; one thread
-// per pixel and 8 channels
-__global__ void k_up2_concat(int B, int H, int W, int C1, int C2, const __nv_bfloat16* __restrict__ lo,
-                             const __nv_bfloat16* __restrict__ skip, __nv_bfloat16* __restrict__ cat)
-{
-    const int cv = (C1 + C2) >> 3, cv1 = C1 >> 3;
-    const size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    const size_t n = size_t(B) * H * W * cv;
-    if (i >= n) return;
-    const int c = int(i % cv);
-    const size_t p = i / cv;
-    uint4 v;
-    if (c < cv1) {
-        const int x = int(p % W);
-        const size_t r = p / W;
-        const int yy = int(r % H);
-        const int b = int(r / H);
-        v = ld8(lo + ((size_t(b) * (H / 2) + yy / 2) * (W / 2) + x / 2) * C1 + 8 * c);
-    } else {
-        v = ld8(skip + p * C2 + 8 * (c - cv1));
-    }
-    st8(cat + i * 8, v);
-}
-
-// dlo = (sum over each 2x2 block of dcat[..., 0:C1]) * (lo_act > 0); dskip = dcat[..., C1:]
+// ---- upsampling + concat (backward) -----------------------------------------
+// dlo = (sum over each 2x2 block of dcat[..., 0:C1]) * (lo > 0), lo read from its
+// upsampled copy up_act (full resolution, pixel stride ldu); dskip = dcat[..., C1:]
 __global__ void k_up2_concat_bwd(int B, int H, int W, int C1, int C2, const __nv_bfloat16* __restrict__ dcat,
-                                 const __nv_bfloat16* __restrict__ lo_act, __nv_bfloat16* __restrict__ dlo,
+                                 const __nv_bfloat16* __restrict__ up_act, int ldu, __nv_bfloat16* __restrict__ dlo,
                                  __nv_bfloat16* __restrict__ dskip)
 {
     const int C = C1 + C2, cv1 = C1 >> 3, cv2 = C2 >> 3;
@@ -231,7 +215,7 @@ __global__ void k_up2_concat_bwd(int B, int H, int W, int C1, int C2, const __nv
         unpack8(ld8(dcat + (p00 + 1) * C + c), s1);
         unpack8(ld8(dcat + (p00 + W) * C + c), s2);
         unpack8(ld8(dcat + (p00 + W + 1) * C + c), s3);
-        unpack8(ld8(lo_act + i * 8), a);
+        unpack8(ld8(up_act + p00 * ldu + c), a);
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
             const float v = s0[q] + s1[q] + s2[q] + s3[q];
@@ -253,7 +237,8 @@ __device__ __forceinline__ float e4m3_val(uint8_t b)
 }
 
 // 2x2 max pooling of e4m3 codes (one scale in and out); the first maximum wins
-__global__ void k_maxpool2_e4m3(int B, int H, int W, int C, const uint8_t* __restrict__ x, uint8_t* __restrict__ y)
+__global__ void k_maxpool2_e4m3(int B, int H, int W, int C, const uint8_t* __restrict__ x, int ldx,
+                                uint8_t* __restrict__ y)
 {
     const size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
     const int h2 = H / 2, w2 = W / 2, cv = C >> 4;
@@ -265,12 +250,12 @@ __global__ void k_maxpool2_e4m3(int B, int H, int W, int C, const uint8_t* __res
     r /= w2;
     const int oy = int(r % h2);
     const int b = int(r / h2);
-    const size_t base = ((size_t(b) * H + 2 * oy) * W + 2 * ox) * C + c;
+    const size_t base = ((size_t(b) * H + 2 * oy) * W + 2 * ox) * ldx + c;
     uint4 q[4];
     q[0] = *reinterpret_cast<const uint4*>(x + base);
-    q[1] = *reinterpret_cast<const uint4*>(x + base + C);
-    q[2] = *reinterpret_cast<const uint4*>(x + base + size_t(W) * C);
-    q[3] = *reinterpret_cast<const uint4*>(x + base + size_t(W) * C + C);
+    q[1] = *reinterpret_cast<const uint4*>(x + base + ldx);
+    q[2] = *reinterpret_cast<const uint4*>(x + base + size_t(W) * ldx);
+    q[3] = *reinterpret_cast<const uint4*>(x + base + size_t(W) * ldx + ldx);
     const uint8_t* v[4] = {reinterpret_cast<const uint8_t*>(&q[0]), reinterpret_cast<const uint8_t*>(&q[1]),
                            reinterpret_cast<const uint8_t*>(&q[2]), reinterpret_cast<const uint8_t*>(&q[3])};
     uint8_t o[16];
@@ -289,29 +274,6 @@ __global__ void k_maxpool2_e4m3(int B, int H, int W, int C, const uint8_t* __res
         o[j] = best;
     }
     *reinterpret_cast<uint4*>(y + i * 16) = *reinterpret_cast<const uint4*>(o);
-}
-
-// cat = [ up(lo) | skip ] on e4m3 codes (each part keeps its own scale)
-__global__ void k_up2_concat_e4m3(int B, int H, int W, int C1, int C2, const uint8_t* __restrict__ lo,
-                                  const uint8_t* __restrict__ skip, uint8_t* __restrict__ cat)
-{
-    const int cv = (C1 + C2) >> 4, cv1 = C1 >> 4;
-    const size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    const size_t n = size_t(B) * H * W * cv;
-    if (i >= n) return;
-    const int c = int(i % cv);
-    const size_t p = i / cv;
-    uint4 v;
-    if (c < cv1) {
-        const int x = int(p % W);
-        const size_t r = p / W;
-        const int yy = int(r % H);
-        const int b = int(r / H);
-        v = *reinterpret_cast<const uint4*>(lo + ((size_t(b) * (H / 2) + yy / 2) * (W / 2) + x / 2) * C1 + 16 * c);
-    } else {
-        v = *reinterpret_cast<const uint4*>(skip + p * C2 + 16 * (c - cv1));
-    }
-    *reinterpret_cast<uint4*>(cat + i * 16) = v;
 }
 
 // ---- 1x1 head ---------------------------------------------------------------
@@ -430,7 +392,7 @@ __global__ void k_head_bwd(size_t npx, const __nv_bfloat16* __restrict__ d1, con
 // time.  BCO, BCI in {32, 16, 8} divide Cout and Cin.
 constexpr int kWgPix = 64;
 template <int BCO, int BCI>
-__global__ void __launch_bounds__(BCO * BCI / 4) k_wgrad3x3(int B, int H, int W, int Cin, int Cout,
+__global__ void __launch_bounds__(BCO * BCI / 4) k_wgrad3x3(int B, int H, int W, int Cin, int xs_, int Cout,
                                                            const __nv_bfloat16* __restrict__ x,
                                                            const __nv_bfloat16* __restrict__ dz,
                                                            float* __restrict__ dw, int rows_per_cta)
@@ -466,7 +428,7 @@ __global__ void __launch_bounds__(BCO * BCI / 4) k_wgrad3x3(int B, int H, int W,
                 const int xx = x0 + pp, xs = xx + kx - 1;
                 float xv = 0.0f;
                 if (xx < W && ys >= 0 && ys < H && xs >= 0 && xs < W)
-                    xv = bf(x[((size_t(b) * H + ys) * W + xs) * Cin + cib * BCI + c]);
+                    xv = bf(x[((size_t(b) * H + ys) * W + xs) * xs_ + cib * BCI + c]);
                 sx[pp][c] = xv;
             }
             __syncthreads();
@@ -533,13 +495,16 @@ __global__ void k_adam(size_t n, float* __restrict__ w, const float* __restrict_
     w[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
 }
 
-// out = max(out, max |x|) (out >= 0 on entry; non-negative floats order like their bits)
-__global__ void k_amax(size_t n8, const __nv_bfloat16* __restrict__ x, float* __restrict__ out)
+// out = max(out, max |x|) over npix pixels of C channels at pixel stride ld
+// (out >= 0 on entry; non-negative floats order like their bits)
+__global__ void k_amax(size_t npix, int C, const __nv_bfloat16* __restrict__ x, int ld, float* __restrict__ out)
 {
+    const int cv = C >> 3;
+    const size_t n8 = npix * cv;
     float m = 0.0f;
     for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n8; i += size_t(gridDim.x) * blockDim.x) {
         float f[8];
-        unpack8(ld8(x + 8 * i), f);
+        unpack8(ld8(x + (i / cv) * ld + 8 * (i % cv)), f);
 #pragma unroll
         for (int j = 0; j < 8; ++j) m = fmaxf(m, fabsf(f[j]));
     }
@@ -558,38 +523,30 @@ cudaError_t launch_pack_features(size_t npx, const uint8_t* rgb, const float* de
     return cudaGetLastError();
 }
 
-cudaError_t launch_maxpool2(int B, int H, int W, int C, const __nv_bfloat16* x, __nv_bfloat16* y, uint8_t* arg,
-                            cudaStream_t s)
+cudaError_t launch_maxpool2(int B, int H, int W, int C, const __nv_bfloat16* x, int ldx, __nv_bfloat16* y,
+                            uint8_t* arg, cudaStream_t s)
 {
     const size_t n = size_t(B) * (H / 2) * (W / 2) * (C / 8);
-    k_maxpool2<<<blocks(n, 256), 256, 0, s>>>(B, H, W, C, x, y, arg);
+    k_maxpool2<<<blocks(n, 256), 256, 0, s>>>(B, H, W, C, x, ldx, y, arg);
     return cudaGetLastError();
 }
 
 cudaError_t launch_maxpool2_bwd(int B, int H, int W, int C, const __nv_bfloat16* dy, const uint8_t* arg,
-                                const __nv_bfloat16* add, const __nv_bfloat16* mask, __nv_bfloat16* dx,
+                                const __nv_bfloat16* add, const __nv_bfloat16* mask, int ldm, __nv_bfloat16* dx,
                                 cudaStream_t s)
 {
     const size_t n = size_t(B) * H * W * (C / 8);
-    k_maxpool2_bwd<<<blocks(n, 256), 256, 0, s>>>(B, H, W, C, dy, arg, add, mask, dx);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_up2_concat(int B, int H, int W, int C1, int C2, const __nv_bfloat16* lo,
-                              const __nv_bfloat16* skip, __nv_bfloat16* cat, cudaStream_t s)
-{
-    const size_t n = size_t(B) * H * W * ((C1 + C2) / 8);
-    k_up2_concat<<<blocks(n, 256), 256, 0, s>>>(B, H, W, C1, C2, lo, skip, cat);
+    k_maxpool2_bwd<<<blocks(n, 256), 256, 0, s>>>(B, H, W, C, dy, arg, add, mask, ldm, dx);
     return cudaGetLastError();
 }
 
 cudaError_t launch_up2_concat_bwd(int B, int H, int W, int C1, int C2, const __nv_bfloat16* dcat,
-                                  const __nv_bfloat16* lo_act, __nv_bfloat16* dlo, __nv_bfloat16* dskip,
+                                  const __nv_bfloat16* up_act, int ldu, __nv_bfloat16* dlo, __nv_bfloat16* dskip,
                                   cudaStream_t s)
 {
     const size_t n_sk = size_t(B) * H * W * (C2 / 8), n_lo = size_t(B) * (H / 2) * (W / 2) * (C1 / 8);
     const size_t n = n_sk > n_lo ? n_sk : n_lo;
-    k_up2_concat_bwd<<<blocks(n, 256), 256, 0, s>>>(B, H, W, C1, C2, dcat, lo_act, dlo, dskip);
+    k_up2_concat_bwd<<<blocks(n, 256), 256, 0, s>>>(B, H, W, C1, C2, dcat, up_act, ldu, dlo, dskip);
     return cudaGetLastError();
 }
 
@@ -635,13 +592,12 @@ cudaError_t launch_head_bwd(size_t npx, int C1, const __nv_bfloat16* d1, const f
     return cudaGetLastError();
 }
 
-cudaError_t launch_amax(size_t n, const __nv_bfloat16* x, float* out, cudaStream_t s)
+cudaError_t launch_amax(size_t npix, int C, const __nv_bfloat16* x, int ld, float* out, cudaStream_t s)
 {
-    const size_t n8 = n / 8;                                    // n is a multiple of 8
-    unsigned g = blocks(n8, 256);
+    unsigned g = blocks(npix * (C / 8), 256);
     if (g > 152 * 8) g = 152 * 8;
     if (g == 0) g = 1;
-    k_amax<<<g, 256, 0, s>>>(n8, x, out);
+    k_amax<<<g, 256, 0, s>>>(npix, C, x, ld, out);
     return cudaGetLastError();
 }
 
@@ -652,24 +608,16 @@ cudaError_t launch_pack_features_e4m3(size_t npx, const uint8_t* rgb, const floa
     return cudaGetLastError();
 }
 
-cudaError_t launch_maxpool2_e4m3(int B, int H, int W, int C, const uint8_t* x, uint8_t* y, cudaStream_t s)
+cudaError_t launch_maxpool2_e4m3(int B, int H, int W, int C, const uint8_t* x, int ldx, uint8_t* y, cudaStream_t s)
 {
     const size_t n = size_t(B) * (H / 2) * (W / 2) * (C / 16);
-    k_maxpool2_e4m3<<<blocks(n, 256), 256, 0, s>>>(B, H, W, C, x, y);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_up2_concat_e4m3(int B, int H, int W, int C1, int C2, const uint8_t* lo, const uint8_t* skip,
-                                   uint8_t* cat, cudaStream_t s)
-{
-    const size_t n = size_t(B) * H * W * ((C1 + C2) / 16);
-    k_up2_concat_e4m3<<<blocks(n, 256), 256, 0, s>>>(B, H, W, C1, C2, lo, skip, cat);
+    k_maxpool2_e4m3<<<blocks(n, 256), 256, 0, s>>>(B, H, W, C, x, ldx, y);
     return cudaGetLastError();
 }
 
 template <int BCO, int BCI>
-cudaError_t wgrad_blocks(int B, int H, int W, int Cin, int Cout, const __nv_bfloat16* x, const __nv_bfloat16* dz,
-                         float* dw, cudaStream_t s)
+cudaError_t wgrad_blocks(int B, int H, int W, int Cin, int xst, int Cout, const __nv_bfloat16* x,
+                         const __nv_bfloat16* dz, float* dw, cudaStream_t s)
 {
     const int tiles = 9 * (Cout / BCO) * (Cin / BCI);
     const long rows = long(B) * H;
@@ -679,22 +627,22 @@ cudaError_t wgrad_blocks(int B, int H, int W, int Cin, int Cout, const __nv_bflo
     if (splits < 1) splits = 1;
     const int rpc = int((rows + splits - 1) / splits);
     dim3 grid(unsigned(tiles), unsigned((rows + rpc - 1) / rpc));
-    k_wgrad3x3<BCO, BCI><<<grid, BCO * BCI / 4, 0, s>>>(B, H, W, Cin, Cout, x, dz, dw, rpc);
+    k_wgrad3x3<BCO, BCI><<<grid, BCO * BCI / 4, 0, s>>>(B, H, W, Cin, xst, Cout, x, dz, dw, rpc);
     return cudaGetLastError();
 }
 
-cudaError_t launch_wgrad3x3(int B, int H, int W, int Cin, int Cout, const __nv_bfloat16* x,
+cudaError_t launch_wgrad3x3(int B, int H, int W, int Cin, int xstride, int Cout, const __nv_bfloat16* x,
                             const __nv_bfloat16* dz, float* dw, cudaStream_t s)
 {
-    if (Cout % 16 || Cin % 8) return cudaErrorInvalidValue;
+    if (Cout % 16 || Cin % 8 || xstride < Cin) return cudaErrorInvalidValue;
     if (Cout % 32 == 0) {
-        if (Cin % 32 == 0) return wgrad_blocks<32, 32>(B, H, W, Cin, Cout, x, dz, dw, s);
-        if (Cin % 16 == 0) return wgrad_blocks<32, 16>(B, H, W, Cin, Cout, x, dz, dw, s);
-        return wgrad_blocks<32, 8>(B, H, W, Cin, Cout, x, dz, dw, s);
+        if (Cin % 32 == 0) return wgrad_blocks<32, 32>(B, H, W, Cin, xstride, Cout, x, dz, dw, s);
+        if (Cin % 16 == 0) return wgrad_blocks<32, 16>(B, H, W, Cin, xstride, Cout, x, dz, dw, s);
+        return wgrad_blocks<32, 8>(B, H, W, Cin, xstride, Cout, x, dz, dw, s);
     }
-    if (Cin % 32 == 0) return wgrad_blocks<16, 32>(B, H, W, Cin, Cout, x, dz, dw, s);
-    if (Cin % 16 == 0) return wgrad_blocks<16, 16>(B, H, W, Cin, Cout, x, dz, dw, s);
-    return wgrad_blocks<16, 8>(B, H, W, Cin, Cout, x, dz, dw, s);
+    if (Cin % 32 == 0) return wgrad_blocks<16, 32>(B, H, W, Cin, xstride, Cout, x, dz, dw, s);
+    if (Cin % 16 == 0) return wgrad_blocks<16, 16>(B, H, W, Cin, xstride, Cout, x, dz, dw, s);
+    return wgrad_blocks<16, 8>(B, H, W, Cin, xstride, Cout, x, dz, dw, s);
 }
 
 cudaError_t launch_bias_grad(size_t npx, int C, const __nv_bfloat16* dz, float* db, cudaStream_t s)

@@ -122,6 +122,7 @@ def test_training_reduces_loss_and_checkpoint_round_trip(net):
     dev["target"] = (255 - dev["rgb"]).contiguous()
     b = F.refine_batch(n, h, w, dev["rgb"], dev["depth"], dev["hole"], dev["top3"], dev["target"])
     losses = [F.fvv_refine_train_step(ctx, b, 2e-3) for _ in range(80)]
+    print("training losses", losses[0], losses[20], losses[40], losses[-1])
     assert losses[-1] < 0.25 * losses[0], (losses[0], losses[-1])
     with tempfile.TemporaryDirectory() as d:
         path = os.path.join(d, "unet.bin")
