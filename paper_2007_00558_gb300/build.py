@@ -19,7 +19,8 @@ INCLUDE = os.path.join(ROOT, "include")
 OUTDIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(OUTDIR, "libfvv.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2,-Wall",
+# host FP64 (pose composition, codec tables) is never contracted into FMAs
+NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2,-Wall,-ffp-contract=off",
                      "-I", INCLUDE, "-I", CSRC, "--expt-relaxed-constexpr"]
 
 
