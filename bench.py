@@ -14,8 +14,10 @@ separated by more frame data than the 129 MB L2 holds.
 
 ``value``: views/s over all ranks with inputs resident in HBM.
 ``e2e``: the same metric through the C ABI with host buffers: every view
-uploads its tick's frames from pinned host memory and the batch writes its
-RGB8 results to pinned host memory, all inside the timed region.
+uploads its tick's frames from pinned host memory (one stream) and every
+step's RGB8 results are read back to pinned host memory (on the synthesis
+stream), all inside the timed region; uploads of the next step overlap the
+synthesis of the current one.
 ``--impl reference``: the CPU oracle on the host cores, same workload.
 
 Under torchrun each rank renders its own share of views (replicas: the path
@@ -62,7 +64,52 @@ def parse_args():
                    help="length of the Poisson multi-viewer run")
     p.add_argument("--no-refine", action="store_true", help="skip the refinement-network measurement")
     p.add_argument("--refine-steps", type=int, default=600, help="LOO training steps before measuring")
+    p.add_argument("--net-forward", type=int, default=0, metavar="REPS",
+                   help="only time the refinement network: REPS forwards of a batch of 4 plain-like "
+                        "1280x720 inputs after 2 untimed ones (0: the full benchmark); for profiling")
+    p.add_argument("--net-widths", default="32,64,128")
+    p.add_argument("--net-e4m3", action="store_true", help="with --net-forward: quantise to E4M3 first")
     return p.parse_args()
+
+
+def net_forward(args):
+    """Refinement network alone on random plain-like inputs (no training):
+    for kernel profiles of the forward pass."""
+    import torch
+    import synthetic as S
+    from paper_2007_00558_gb300 import fvv as F
+    F.load()
+    widths = tuple(int(v) for v in args.net_widths.split(","))
+    B, H, W = 4, 720, 1280
+    g = torch.Generator(device="cuda").manual_seed(0)
+    rgb = torch.randint(0, 256, (B, H, W, 3), dtype=torch.uint8, device="cuda", generator=g)
+    depth = torch.rand((B, H, W), device="cuda", generator=g) * 6000 + 500
+    hole = (torch.rand((B, H, W), device="cuda", generator=g) < 0.05).to(torch.uint8)
+    top3 = torch.rand((B, H, W, 3), device="cuda", generator=g)
+    ctx = F.fvv_create(F.rig(S.rig_parallel(1, 16, 16, 10.0, 0.1), [0, 0, 1]))
+    try:
+        F.fvv_refine_init(ctx, F.fvv_refine_default_cfg(seed=1, widths=widths))
+        fb = F.refine_batch(B, H, W, rgb, depth, hole, top3)
+        if args.net_e4m3:
+            F.fvv_refine_quantize(ctx, fb)
+        out = torch.empty((B, H, W, 3), dtype=torch.uint8, device="cuda")
+        s = torch.cuda.current_stream()
+        for _ in range(2):
+            F.fvv_refine_forward(ctx, fb, out, None, s)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        for _ in range(args.net_forward):
+            F.fvv_refine_forward(ctx, fb, out, None, s)
+        e1.record(s)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / max(1, args.net_forward) / B
+        fl = unet_flops(H, W, widths)
+        print(json.dumps({"widths": list(widths), "e4m3": args.net_e4m3, "ms_per_view": ms,
+                          "tflops": fl / (ms * 1e-3) / 1e12}))
+    finally:
+        F.fvv_destroy(ctx)
+    return 0
 
 
 # ---------------------------------------------------------------------------
@@ -261,6 +308,70 @@ def algorithmic_bytes(K, Ns, Nd, rho, n_ref):
 # serving loop: many viewers, Poisson arrivals, mixed resolutions
 # ---------------------------------------------------------------------------
 SERVE_RES = [(640, 360, 500.0)] * 2 + [(1280, 720, 1000.0), (1920, 1080, 1500.0)]   # 2:1:1
+
+
+def codec_bench(F, ctx, wl, stream, reps=50):
+    """Depth codec (Eq. 1-3): decode throughput on device-resident YUV420
+    depth frames of the 9 cameras, against the HBM roofline (3.5 algorithmic
+    bytes per pixel: 1.5 read, 2 written), and the host upload of one tick
+    with YUV420 depth versus uint16 depth."""
+    import numpy as np
+    import torch
+    cams = wl["cams"]
+    K, H, W = len(cams), cams[0].height, cams[0].width
+    codec = F.fvv_depth_codec_default(z_near=0.3, z_far=10.0)
+    planes = []
+    for k in range(K):
+        F.fvv_set_depth_codec(ctx, k, codec)
+        d = torch.from_numpy(np.ascontiguousarray(wl["depth"][k]).view(np.int16)).cuda()
+        y = torch.empty((H, W), dtype=torch.uint8, device="cuda")
+        u = torch.empty((H // 2, W // 2), dtype=torch.uint8, device="cuda")
+        v = torch.empty_like(u)
+        F.fvv_depth_encode_yuv(ctx, k, d, W * 2, y, W, u, v, W // 2, stream)
+        planes.append((y, u, v))
+    out = torch.empty((K, H, W), dtype=torch.int16, device="cuda")
+    for k in range(K):
+        F.fvv_depth_decode_yuv(ctx, k, planes[k][0], W, planes[k][1], planes[k][2], W // 2, out[k], W * 2, stream)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        for k in range(K):
+            F.fvv_depth_decode_yuv(ctx, k, planes[k][0], W, planes[k][1], planes[k][2], W // 2, out[k], W * 2,
+                                   stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    us = e0.elapsed_time(e1) * 1e3 / (reps * K)
+    gbs = 3.5 * H * W / (us * 1e-6) / 1e9
+    peak, src = measured_peaks()
+    # one tick uploaded from pinned host memory: YUV420 depth vs uint16 depth
+    rgb_h = [torch.from_numpy(np.ascontiguousarray(wl["rgb"][k])).pin_memory() for k in range(K)]
+    dep_h = [torch.from_numpy(np.ascontiguousarray(wl["depth"][k]).view(np.int16)).pin_memory() for k in range(K)]
+    # one planar I420 buffer per camera (Y, then U, then V), as a decoder outputs it
+    yuv_h = []
+    for k in range(K):
+        buf = torch.cat([p.reshape(-1) for p in planes[k]]).cpu().pin_memory()
+        yuv_h.append((buf, buf[H * W:], buf[H * W + (H // 2) * (W // 2):]))
+
+    def tick_ms(yuv, n=10):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for t in range(n):
+            for k in range(K):
+                if yuv:
+                    F.fvv_upload_frame_yuv(ctx, k, rgb_h[k], W * 3, yuv_h[k][0], W, yuv_h[k][1], yuv_h[k][2],
+                                           W // 2, 1000 + t, stream)
+                else:
+                    F.fvv_upload_frame(ctx, k, rgb_h[k], W * 3, dep_h[k], W * 2, 1000 + t, stream)
+            torch.cuda.synchronize()
+        return (time.perf_counter() - t0) * 1e3 / n
+    tick_ms(True, 2)
+    ms_yuv, ms_u16 = tick_ms(True), tick_ms(False)
+    return {"decode_us_per_frame": us, "frame": "%dx%d" % (W, H), "decode_gbs": gbs,
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+                         "peak_source": src, "alg_bytes_per_pixel": 3.5},
+            "upload_tick_ms": {"yuv420_depth": ms_yuv, "uint16_depth": ms_u16, "cameras": K,
+                               "h2d_depth_bytes": {"yuv420": int(1.5 * H * W * K), "uint16": int(2 * H * W * K)}}}
 
 
 def serve_bench(F, ctx, wl, rgb_h, dep_h, slots, seconds, stream):
@@ -628,18 +739,27 @@ def run_fvv(args):
     # end to end through the C ABI with host buffers
     e2e = None
     if not args.no_e2e:
+        # Two streams: every tick's upload (pinned host -> frame ring) on `up`,
+        # the batched synthesis and the read-back of its RGB results on `syn`.
+        # The frame ring's per-slot events order each synthesis after the
+        # uploads of its ticks and each upload after the syntheses still
+        # reading its slot, so step i+1's copies overlap step i's kernels.
         out_h = [torch.empty((H, W, 3), dtype=torch.uint8).pin_memory() for _ in range(Bsz)]
+        out_d = [torch.empty((H, W * 3), dtype=torch.uint8, device="cuda") for _ in range(Bsz)]
+        up, syn = torch.cuda.Stream(), torch.cuda.Stream()
         tick = [slots]
 
         def e2e_step(i):
             vs, ticks = [], []
             for j in range(Bsz):
-                F.fvv_upload_frames(ctx, rgb_h, H * W * 3, W * 3, dep_h, H * W * 2, W * 2,
-                                    tick[0], stream)
+                F.fvv_upload_frames(ctx, rgb_h, H * W * 3, W * 3, dep_h, H * W * 2, W * 2, tick[0], up)
                 ticks.append(tick[0])
                 tick[0] += 1
                 vs.append(views[(off + i * Bsz + j) % 300])
-            F.fvv_synthesize_batch(ctx, vs, ticks, out_h, pitches, None, stream)
+            F.fvv_synthesize_batch(ctx, vs, ticks, out_d, pitches, None, syn)
+            with torch.cuda.stream(syn):
+                for j in range(Bsz):
+                    out_h[j].view(-1).copy_(out_d[j].view(-1), non_blocking=True)
 
         for i in range(args.warmup):
             e2e_step(i)
@@ -657,6 +777,10 @@ def run_fvv(args):
     serve = None
     if not args.no_serve and world == 1:
         serve = serve_bench(F, ctx, wl, rgb_h, dep_h, slots, args.serve_seconds, stream)
+
+    codec = None
+    if world == 1:
+        codec = codec_bench(F, ctx, wl, stream)
 
     refine = None
     if not args.no_refine and world == 1:
@@ -689,7 +813,7 @@ def run_fvv(args):
                        "l2": "inputs > L2: each view reads its own frame tick, %d ticks x %.1f MB "
                              "resident" % (slots, K * H * W * 6 / 1e6),
                        "parallelism": "replicas" if world > 1 else "single"},
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "serve": serve, "refine": refine,
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "serve": serve, "refine": refine, "codec": codec,
             "gpu_launches": int(launches), "clocks": clocks.summary(),
             "kernel_ms": {k: v[2] for k, v in stats.items()},
         }
@@ -703,6 +827,8 @@ def main():
     args = parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.net_forward:
+        return net_forward(args)
     return run_fvv(args)
 
 

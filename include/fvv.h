@@ -166,6 +166,48 @@ fvv_status fvv_synthesize_batch(fvv_ctx* ctx, int32_t n, const fvv_view* views,
 fvv_status fvv_view_params(const fvv_rig* rig, const fvv_options* opt,
                            const fvv_view* view, float* M, float* N, float* w);
 
+/* ---- depth codec of the transmission chain (Sec. V-B, Eq. (1)-(3)) -------
+ * The capture side corrects depth (Eq. (1): z_post = (alpha z + beta) z, z in
+ * metres), quantises it to 12-bit disparity (Eq. (2): Y = (2^12 - 3)(1/z -
+ * 1/z_far) / (1/z_near - 1/z_far) + 2, rounded half up, for z in [z_near,
+ * z_far]; code 1 marks values out of that range and pixels without depth,
+ * code 0 background) and packs each 2x2 block onto 8-bit YUV420: pixel p's
+ * Y value is its 8 LSBs, complemented when its 4 MSBs are odd (Eq. (3)); the
+ * 4 MSBs of the top pair are bit-interleaved into U (bit i of the left pixel
+ * at bit 2i, of the right pixel at bit 2i + 1), those of the bottom pair into
+ * V.  The view-synthesis side inverts the packing and Eq. (2) on upload,
+ * depth code = round(z / depth_unit_m) (codes 0 and 1 decode to 0, no depth).
+ * Both directions use per-camera tables built in FP64 on the host, so the
+ * kernels are integer lookups.  Frames need even width and height. */
+typedef struct fvv_depth_codec {
+    double z_near, z_far;       /* clipping planes of Eq. (2), metres, 0 < z_near < z_far */
+    double alpha, beta;         /* Eq. (1) correction; identity: alpha = 0, beta = 1 */
+} fvv_depth_codec;
+
+/* z_near 0.3 m, z_far 10 m, alpha 0, beta 1. */
+fvv_status fvv_depth_codec_default(fvv_depth_codec* codec);
+/* Set camera `cam`'s codec (builds its tables; waits for the context's
+ * stream).  Errors: INVALID_ARG, OUT_OF_MEMORY, BUDGET, CUDA. */
+fvv_status fvv_set_depth_codec(fvv_ctx* ctx, int32_t cam, const fvv_depth_codec* codec);
+/* Capture side: camera `cam`'s uint16 depth codes (height rows, pitch
+ * depth_pitch bytes, 4-byte aligned) -> Y (height rows of width bytes, pitch
+ * y_pitch), U and V (height/2 rows of width/2 bytes, pitch uv_pitch); all
+ * device memory; asynchronous on `stream`.  Errors: INVALID_ARG, STATE (no
+ * codec set), CUDA. */
+fvv_status fvv_depth_encode_yuv(fvv_ctx* ctx, int32_t cam, const uint16_t* depth, size_t depth_pitch, uint8_t* y,
+                                size_t y_pitch, uint8_t* u, uint8_t* v, size_t uv_pitch, void* stream);
+/* The inverse: Y, U, V planes -> uint16 depth codes; device memory;
+ * asynchronous on `stream`.  Errors as for the encoder. */
+fvv_status fvv_depth_decode_yuv(fvv_ctx* ctx, int32_t cam, const uint8_t* y, size_t y_pitch, const uint8_t* u,
+                                const uint8_t* v, size_t uv_pitch, uint16_t* depth, size_t depth_pitch,
+                                void* stream);
+/* fvv_upload_frame with the depth given as a YUV420 depth frame: the decode
+ * runs fused into the upload and writes the frame ring directly.  rgb and
+ * the planes may be host or device memory (the three planes alike). */
+fvv_status fvv_upload_frame_yuv(fvv_ctx* ctx, int32_t cam, const uint8_t* rgb, size_t rgb_pitch, const uint8_t* y,
+                                size_t y_pitch, const uint8_t* u, const uint8_t* v, size_t uv_pitch, uint64_t tick,
+                                void* stream);
+
 /* ---- serving loop (continuous batching of many viewers' requests) ------
  * The paper serves one viewer whose viewpoint commands reach the edge server
  * and wait for the next synthesised frame (Sec. VIII, motion-to-photon
@@ -227,7 +269,7 @@ fvv_status fvv_serve_stop(fvv_ctx* ctx);
 
 /* Per-kernel statistics of one context. */
 typedef struct fvv_kernel_stats {
-    char name[32];              /* "clear_keys", "warp_splat", "resolve", "pack_rgba" */
+    char name[32];              /* "clear_keys", "warp_splat", "resolve", "pack_rgba", "yuv_decode" */
     uint64_t launches;          /* launches since the last reset */
     uint64_t timed;             /* of which bracketed by CUDA events */
     double total_ms;            /* summed event durations of the timed launches */

@@ -47,7 +47,7 @@ fvv_status fvv::fail(fvv_status code, const std::string& msg)
 }
 
 const char* const fvv::kKernelName[fvv::kNumKernels] = {"clear_keys", "warp_splat", "resolve",
-                                                        "pack_rgba"};
+                                                        "pack_rgba", "yuv_decode"};
 
 fvv::MemKind fvv::mem_kind(const void* p)
 {
@@ -294,10 +294,18 @@ fvv_status ensure_out_stage(fvv_ctx* c, BatchScratch& S, size_t bytes)
 fvv_status upload_one(fvv_ctx* c, int cam, const uint8_t* rgb, size_t rgb_pitch,
                       const uint16_t* depth, size_t depth_pitch, uint64_t tick, cudaStream_t s)
 {
+    return fvv::upload_frame(c, cam, rgb, rgb_pitch, depth, depth_pitch, nullptr, tick, s);
+}
+
+}  // namespace
+
+fvv_status fvv::upload_frame(fvv_ctx* c, int cam, const uint8_t* rgb, size_t rgb_pitch, const uint16_t* depth,
+                             size_t depth_pitch, const YuvDepth* yuv, uint64_t tick, cudaStream_t s)
+{
     const fvv_camera& C = c->cams[cam];
-    if (!rgb || !depth) return fail(FVV_ERR_INVALID_ARG, "rgb and depth must be non-NULL");
+    if (!rgb || (!depth && !yuv)) return fail(FVV_ERR_INVALID_ARG, "rgb and depth must be non-NULL");
     if (rgb_pitch < size_t(C.width) * 3) return fail(FVV_ERR_INVALID_ARG, "rgb_pitch < 3 * width");
-    if (depth_pitch < size_t(C.width) * 2) return fail(FVV_ERR_INVALID_ARG, "depth_pitch < 2 * width");
+    if (!yuv && depth_pitch < size_t(C.width) * 2) return fail(FVV_ERR_INVALID_ARG, "depth_pitch < 2 * width");
     const int si = int(tick % uint64_t(c->slots));
     SlotState& S = c->slot[si];
     if (S.any && tick < S.tick)
@@ -313,8 +321,13 @@ fvv_status upload_one(fvv_ctx* c, int cam, const uint8_t* rgb, size_t rgb_pitch,
     uint8_t* base = c->arena + size_t(si) * c->slot_bytes;
     uint16_t* ddst = reinterpret_cast<uint16_t*>(base + c->off_depth[cam]);
     uint32_t* rdst = reinterpret_cast<uint32_t*>(base + c->off_rgba[cam]);
-    FVV_CUDA(cudaMemcpy2DAsync(ddst, size_t(c->dpitch[cam]) * 2, depth, depth_pitch,
-                               size_t(C.width) * 2, size_t(C.height), cudaMemcpyDefault, s));
+    if (yuv)
+        FVV_TRY(run_kernel(c, kDecode, s, [&] {
+            return fvv::launch_yuv_decode(*yuv, C.width, C.height, ddst, size_t(c->dpitch[cam]) * 2, s);
+        }));
+    else
+        FVV_CUDA(cudaMemcpy2DAsync(ddst, size_t(c->dpitch[cam]) * 2, depth, depth_pitch, size_t(C.width) * 2,
+                                   size_t(C.height), cudaMemcpyDefault, s));
     const uint8_t* src = rgb;
     size_t spitch = rgb_pitch;
     if (mem_kind(rgb) == MemKind::Host) {
@@ -339,8 +352,6 @@ fvv_status upload_one(fvv_ctx* c, int cam, const uint8_t* rgb, size_t rgb_pitch,
     }
     return FVV_OK;
 }
-
-}  // namespace
 
 fvv_status fvv::scratch_alloc(fvv_ctx* c, BatchScratch& S, size_t keys, size_t stage, int max_batch,
                               int n_blocks)
@@ -652,6 +663,7 @@ fvv_status fvv_destroy(fvv_ctx* c)
     if (!c) return FVV_OK;
     fvv::serve_shutdown(c);
     fvv::refine_destroy(c);
+    fvv::codec_destroy(c);
     int cur = 0;
     cudaGetDevice(&cur);
     cudaSetDevice(c->device);

@@ -1,0 +1,312 @@
+// fvv_codec.cu -- the depth codec of the transmission chain (Sec. V-B):
+// 16-bit depth -> Eq. (1) correction -> Eq. (2) 12-bit disparity -> Eq. (3)
+// and the bit re-arrangement onto an 8-bit YUV420 frame, and back.
+//
+// Both directions go through per-camera tables built on the host in FP64
+// (encode: every uint16 depth code -> 12-bit code; decode: every 12-bit code
+// -> uint16 depth code), so the kernels are integer-only and bound by memory:
+// one thread per 2x2 block reads 4 Y bytes, one U and one V byte and writes
+// four depth codes (decode), or the reverse (encode).  The decode runs fused
+// into the frame upload (fvv_upload_frame_yuv): the decoded depth lands
+// directly in the frame ring.
+//
+// Readings where the paper is silent: Eq. (2) rounds half up; bit i of the
+// first pixel's 4 MSBs goes to bit 2i of U (V), the second pixel's to bit
+// 2i + 1; the decoder inverts Eq. (2) as 1 / (1/z_far + (Y - 2)(1/z_near -
+// 1/z_far) / 4093); reserved codes 0 (background) and 1 (out of range or no
+// depth) decode to depth code 0, and depth code 0 encodes to 1.
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "fvv_runtime.h"
+
+namespace fvv {
+
+struct CodecState {
+    std::vector<int> set;                   // per camera: tables built
+    std::vector<fvv_depth_codec> prm;
+    std::vector<uint16_t*> dec;             // [4096] per camera
+    std::vector<uint16_t*> enc;             // [65536] per camera
+    std::vector<uint8_t*> stage;            // host-upload staging of Y, U, V
+    std::vector<size_t> stage_bytes;
+};
+
+namespace {
+
+constexpr double kLevels = 4093.0;          // 2^12 - 3
+
+// 12-bit code of depth code d (FP64, the operation order of the reading)
+uint16_t encode_code(int d, const fvv_depth_codec& p, double unit)
+{
+    if (d == 0) return 1;
+    const double z = double(d) * unit;
+    const double zc = (p.alpha * z + p.beta) * z;               // Eq. (1)
+    if (!(zc >= p.z_near && zc <= p.z_far)) return 1;
+    const double inv_n = 1.0 / p.z_near, inv_f = 1.0 / p.z_far;
+    const double v = kLevels * (1.0 / zc - inv_f) / (inv_n - inv_f) + 2.0;   // Eq. (2)
+    return uint16_t(std::floor(v + 0.5));
+}
+
+uint16_t decode_code(int y, const fvv_depth_codec& p, double unit)
+{
+    if (y < 2) return 0;
+    const double inv_n = 1.0 / p.z_near, inv_f = 1.0 / p.z_far;
+    const double z = 1.0 / (inv_f + (double(y) - 2.0) * (inv_n - inv_f) / kLevels);
+    const double d = std::floor(z / unit + 0.5);
+    return uint16_t(d < 1.0 ? 1.0 : d > 65535.0 ? 65535.0 : d);
+}
+
+__device__ __forceinline__ uint32_t interleave4(uint32_t a, uint32_t b)
+{
+    uint32_t u = 0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) u |= (((a >> i) & 1u) << (2 * i)) | (((b >> i) & 1u) << (2 * i + 1));
+    return u;
+}
+
+__device__ __forceinline__ void deinterleave4(uint32_t u, uint32_t& a, uint32_t& b)
+{
+    a = b = 0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        a |= ((u >> (2 * i)) & 1u) << i;
+        b |= ((u >> (2 * i + 1)) & 1u) << i;
+    }
+}
+
+// Eq. (3): the Y byte of a 12-bit code, and its inverse given the MSBs
+__device__ __forceinline__ uint32_t fold(uint32_t y12)
+{
+    const uint32_t lsb = y12 & 255u;
+    return ((y12 >> 8) & 1u) ? 255u - lsb : lsb;
+}
+
+__device__ __forceinline__ uint32_t unfold(uint32_t ybyte, uint32_t msb)
+{
+    return (msb << 8) | ((msb & 1u) ? 255u - ybyte : ybyte);
+}
+
+// Grid-stride over 2x2 blocks; the decode table is staged once per CTA (a
+// few CTAs per SM, so table traffic stays far below the frame's).
+__device__ __forceinline__ void decode_block(const YuvDepth& f, const uint16_t* lut, int bx, int by,
+                                             uint16_t* out, size_t opitch)
+{
+    const uint8_t* y0 = f.y + size_t(2 * by) * f.y_pitch + 2 * bx;
+    const uint8_t* y1 = y0 + f.y_pitch;
+    uint32_t m11, m12, m21, m22;
+    deinterleave4(f.u[size_t(by) * f.uv_pitch + bx], m11, m12);
+    deinterleave4(f.v[size_t(by) * f.uv_pitch + bx], m21, m22);
+    uint16_t* r0 = reinterpret_cast<uint16_t*>(reinterpret_cast<uint8_t*>(out) + size_t(2 * by) * opitch) + 2 * bx;
+    uint16_t* r1 = reinterpret_cast<uint16_t*>(reinterpret_cast<uint8_t*>(r0) + opitch);
+    const uint32_t a = lut[unfold(y0[0], m11)], b = lut[unfold(y0[1], m12)];
+    const uint32_t c = lut[unfold(y1[0], m21)], d = lut[unfold(y1[1], m22)];
+    *reinterpret_cast<uint32_t*>(r0) = a | (b << 16);
+    *reinterpret_cast<uint32_t*>(r1) = c | (d << 16);
+}
+
+__global__ void __launch_bounds__(512) k_yuv_decode(YuvDepth f, int bw, int bh, uint16_t* __restrict__ out,
+                                                    size_t opitch)
+{
+    __shared__ uint16_t lut[4096];
+    for (int i = threadIdx.x; i < 4096; i += blockDim.x) lut[i] = f.lut[i];
+    __syncthreads();
+    const size_t n = size_t(bw) * bh;
+    for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += size_t(gridDim.x) * blockDim.x)
+        decode_block(f, lut, int(i % bw), int(i / bw), out, opitch);
+}
+
+__global__ void __launch_bounds__(256) k_yuv_encode(const uint16_t* __restrict__ depth, size_t dpitch, int bw,
+                                                    int bh, const uint16_t* __restrict__ lut, uint8_t* __restrict__ y,
+                                                    size_t ypitch, uint8_t* __restrict__ u, uint8_t* __restrict__ v,
+                                                    size_t uvpitch)
+{
+    const size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= size_t(bw) * bh) return;
+    const int bx = int(i % bw), by = int(i / bw);
+    const uint16_t* d0 =
+        reinterpret_cast<const uint16_t*>(reinterpret_cast<const uint8_t*>(depth) + size_t(2 * by) * dpitch) + 2 * bx;
+    const uint16_t* d1 = reinterpret_cast<const uint16_t*>(reinterpret_cast<const uint8_t*>(d0) + dpitch);
+    const uint32_t p11 = __ldg(lut + d0[0]), p12 = __ldg(lut + d0[1]);
+    const uint32_t p21 = __ldg(lut + d1[0]), p22 = __ldg(lut + d1[1]);
+    uint8_t* yr0 = y + size_t(2 * by) * ypitch + 2 * bx;
+    uint8_t* yr1 = yr0 + ypitch;
+    yr0[0] = uint8_t(fold(p11));
+    yr0[1] = uint8_t(fold(p12));
+    yr1[0] = uint8_t(fold(p21));
+    yr1[1] = uint8_t(fold(p22));
+    u[size_t(by) * uvpitch + bx] = uint8_t(interleave4(p11 >> 8, p12 >> 8));
+    v[size_t(by) * uvpitch + bx] = uint8_t(interleave4(p21 >> 8, p22 >> 8));
+}
+
+bool on_dev(const void* p) { return p && mem_kind(p) == MemKind::Device; }
+
+fvv_status check_cam(fvv_ctx* c, int32_t cam)
+{
+    if (!c) return fail(FVV_ERR_INVALID_ARG, "ctx is NULL");
+    if (cam < 0 || cam >= c->n_cams) return fail(FVV_ERR_INVALID_ARG, "camera index out of range");
+    if (c->cams[cam].width % 2 || c->cams[cam].height % 2)
+        return fail(FVV_ERR_INVALID_ARG, "YUV420 depth needs even width and height");
+    if (!c->codec || !c->codec->set[cam]) return fail(FVV_ERR_STATE, "no depth codec set for this camera");
+    return FVV_OK;
+}
+
+}  // namespace
+
+cudaError_t launch_yuv_decode(const YuvDepth& f, int width, int height, uint16_t* out, size_t out_pitch,
+                              cudaStream_t s)
+{
+    const int bw = width / 2, bh = height / 2;
+    const size_t n = size_t(bw) * bh;
+    if (n == 0) return cudaSuccess;
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
+            sms = 1;
+    }
+    const size_t want = (n + 511) / 512;
+    const unsigned grid = unsigned(want < size_t(2 * sms) ? want : size_t(2 * sms));
+    k_yuv_decode<<<grid, 512, 0, s>>>(f, bw, bh, out, out_pitch);
+    return cudaGetLastError();
+}
+
+void codec_destroy(fvv_ctx* c)
+{
+    CodecState* K = c->codec;
+    if (!K) return;
+    for (int k = 0; k < c->n_cams; ++k) {
+        dev_free(c, K->dec[k], 4096 * sizeof(uint16_t));
+        dev_free(c, K->enc[k], 65536 * sizeof(uint16_t));
+        dev_free(c, K->stage[k], K->stage_bytes[k]);
+    }
+    delete K;
+    c->codec = nullptr;
+}
+
+}  // namespace fvv
+
+using fvv::fail;
+
+extern "C" {
+
+fvv_status fvv_depth_codec_default(fvv_depth_codec* p)
+{
+    if (!p) return fail(FVV_ERR_INVALID_ARG, "codec is NULL");
+    p->z_near = 0.3;
+    p->z_far = 10.0;
+    p->alpha = 0.0;
+    p->beta = 1.0;
+    return FVV_OK;
+}
+
+fvv_status fvv_set_depth_codec(fvv_ctx* c, int32_t cam, const fvv_depth_codec* p)
+{
+    if (!c || !p) return fail(FVV_ERR_INVALID_ARG, "NULL argument");
+    if (cam < 0 || cam >= c->n_cams) return fail(FVV_ERR_INVALID_ARG, "camera index out of range");
+    if (!(p->z_near > 0.0) || !(p->z_far > p->z_near) || !std::isfinite(p->z_far) || !std::isfinite(p->alpha) ||
+        !std::isfinite(p->beta))
+        return fail(FVV_ERR_INVALID_ARG, "need 0 < z_near < z_far and finite alpha, beta");
+    std::lock_guard<std::recursive_mutex> g(c->mu);
+    FVV_CUDA(cudaSetDevice(c->device));
+    if (!c->codec) {
+        auto* K = new fvv::CodecState();
+        K->set.assign(c->n_cams, 0);
+        K->prm.resize(c->n_cams);
+        K->dec.assign(c->n_cams, nullptr);
+        K->enc.assign(c->n_cams, nullptr);
+        K->stage.assign(c->n_cams, nullptr);
+        K->stage_bytes.assign(c->n_cams, 0);
+        c->codec = K;
+    }
+    fvv::CodecState* K = c->codec;
+    if (!K->dec[cam]) FVV_TRY(fvv::dev_alloc(c, reinterpret_cast<void**>(&K->dec[cam]), 4096 * sizeof(uint16_t)));
+    if (!K->enc[cam]) FVV_TRY(fvv::dev_alloc(c, reinterpret_cast<void**>(&K->enc[cam]), 65536 * sizeof(uint16_t)));
+    std::vector<uint16_t> dec(4096), enc(65536);
+    for (int y = 0; y < 4096; ++y) dec[y] = fvv::decode_code(y, *p, c->depth_unit_m);
+    for (int d = 0; d < 65536; ++d) enc[d] = fvv::encode_code(d, *p, c->depth_unit_m);
+    // the tables may be read by work in flight on the context's stream
+    FVV_CUDA(cudaStreamSynchronize(c->own));
+    FVV_CUDA(cudaMemcpy(K->dec[cam], dec.data(), dec.size() * sizeof(uint16_t), cudaMemcpyHostToDevice));
+    FVV_CUDA(cudaMemcpy(K->enc[cam], enc.data(), enc.size() * sizeof(uint16_t), cudaMemcpyHostToDevice));
+    K->prm[cam] = *p;
+    K->set[cam] = 1;
+    return FVV_OK;
+}
+
+fvv_status fvv_depth_encode_yuv(fvv_ctx* c, int32_t cam, const uint16_t* depth, size_t depth_pitch, uint8_t* y,
+                                size_t y_pitch, uint8_t* u, uint8_t* v, size_t uv_pitch, void* stream)
+{
+    FVV_TRY(fvv::check_cam(c, cam));
+    const int W = c->cams[cam].width, H = c->cams[cam].height;
+    if (!fvv::on_dev(depth) || !fvv::on_dev(y) || !fvv::on_dev(u) || !fvv::on_dev(v))
+        return fail(FVV_ERR_INVALID_ARG, "depth and the Y, U, V planes must be device memory");
+    if (depth_pitch < size_t(W) * 2 || depth_pitch % 4 || y_pitch < size_t(W) || uv_pitch < size_t(W / 2) ||
+        reinterpret_cast<uintptr_t>(depth) % 4)
+        return fail(FVV_ERR_INVALID_ARG, "pitch too small, or depth not 4-byte aligned");
+    cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : c->own;
+    const int bw = W / 2, bh = H / 2;
+    const size_t n = size_t(bw) * bh;
+    fvv::k_yuv_encode<<<unsigned((n + 255) / 256), 256, 0, s>>>(depth, depth_pitch, bw, bh, c->codec->enc[cam], y,
+                                                               y_pitch, u, v, uv_pitch);
+    FVV_CUDA(cudaGetLastError());
+    return FVV_OK;
+}
+
+fvv_status fvv_depth_decode_yuv(fvv_ctx* c, int32_t cam, const uint8_t* y, size_t y_pitch, const uint8_t* u,
+                                const uint8_t* v, size_t uv_pitch, uint16_t* depth, size_t depth_pitch, void* stream)
+{
+    FVV_TRY(fvv::check_cam(c, cam));
+    const int W = c->cams[cam].width, H = c->cams[cam].height;
+    if (!fvv::on_dev(depth) || !fvv::on_dev(y) || !fvv::on_dev(u) || !fvv::on_dev(v))
+        return fail(FVV_ERR_INVALID_ARG, "depth and the Y, U, V planes must be device memory");
+    if (depth_pitch < size_t(W) * 2 || depth_pitch % 4 || y_pitch < size_t(W) || uv_pitch < size_t(W / 2) ||
+        reinterpret_cast<uintptr_t>(depth) % 4)
+        return fail(FVV_ERR_INVALID_ARG, "pitch too small, or depth not 4-byte aligned");
+    cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : c->own;
+    const fvv::YuvDepth f{y, u, v, y_pitch, uv_pitch, c->codec->dec[cam]};
+    FVV_CUDA(fvv::launch_yuv_decode(f, W, H, depth, depth_pitch, s));
+    return FVV_OK;
+}
+
+fvv_status fvv_upload_frame_yuv(fvv_ctx* c, int32_t cam, const uint8_t* rgb, size_t rgb_pitch, const uint8_t* y,
+                                size_t y_pitch, const uint8_t* u, const uint8_t* v, size_t uv_pitch, uint64_t tick,
+                                void* stream)
+{
+    FVV_TRY(fvv::check_cam(c, cam));
+    if (!y || !u || !v) return fail(FVV_ERR_INVALID_ARG, "Y, U and V must be non-NULL");
+    const int W = c->cams[cam].width, H = c->cams[cam].height;
+    if (y_pitch < size_t(W) || uv_pitch < size_t(W / 2)) return fail(FVV_ERR_INVALID_ARG, "pitch too small");
+    const bool dy = fvv::on_dev(y), du = fvv::on_dev(u), dv = fvv::on_dev(v);
+    if (dy != du || dy != dv) return fail(FVV_ERR_INVALID_ARG, "Y, U, V must all be host or all device memory");
+    cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : c->own;
+    std::lock_guard<std::recursive_mutex> g(c->mu);
+    fvv::CodecState* K = c->codec;
+    fvv::YuvDepth f{y, u, v, y_pitch, uv_pitch, K->dec[cam]};
+    if (!dy) {
+        // host planes: one copy per plane into dense staging
+        const size_t yb = size_t(W) * H, cb = size_t(W / 2) * (H / 2);
+        if (K->stage_bytes[cam] < yb + 2 * cb) {
+            FVV_CUDA(cudaStreamSynchronize(s));
+            fvv::dev_free(c, K->stage[cam], K->stage_bytes[cam]);
+            K->stage[cam] = nullptr;
+            K->stage_bytes[cam] = 0;
+            FVV_TRY(fvv::dev_alloc(c, reinterpret_cast<void**>(&K->stage[cam]), yb + 2 * cb));
+            K->stage_bytes[cam] = yb + 2 * cb;
+        }
+        uint8_t* sy = K->stage[cam];
+        if (y_pitch == size_t(W) && uv_pitch == size_t(W / 2) && u == y + yb && v == u + cb) {
+            // one planar I420 buffer: a single copy
+            FVV_CUDA(cudaMemcpyAsync(sy, y, yb + 2 * cb, cudaMemcpyHostToDevice, s));
+        } else {
+            FVV_CUDA(cudaMemcpy2DAsync(sy, W, y, y_pitch, W, H, cudaMemcpyHostToDevice, s));
+            FVV_CUDA(cudaMemcpy2DAsync(sy + yb, W / 2, u, uv_pitch, W / 2, H / 2, cudaMemcpyHostToDevice, s));
+            FVV_CUDA(cudaMemcpy2DAsync(sy + yb + cb, W / 2, v, uv_pitch, W / 2, H / 2, cudaMemcpyHostToDevice, s));
+        }
+        f = fvv::YuvDepth{sy, sy + yb, sy + yb + cb, size_t(W), size_t(W / 2), K->dec[cam]};
+    }
+    return fvv::upload_frame(c, cam, rgb, rgb_pitch, nullptr, 0, &f, tick, s);
+}
+
+}  // extern "C"

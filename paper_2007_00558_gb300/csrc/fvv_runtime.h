@@ -51,7 +51,7 @@ struct ParamBlock {
     bool pending = false;
 };
 
-enum Kid { kClear = 0, kSplat, kResolve, kPack, kNumKernels };
+enum Kid { kClear = 0, kSplat, kResolve, kPack, kDecode, kNumKernels };
 extern const char* const kKernelName[kNumKernels];
 
 struct KernelStat {
@@ -96,6 +96,17 @@ struct RefineNet;                         // fvv_refine.cu
 
 }  // namespace fvv
 
+namespace fvv {
+struct CodecState;
+
+// A YUV420 depth frame in device memory and the decode table of its camera.
+struct YuvDepth {
+    const uint8_t *y, *u, *v;
+    size_t y_pitch, uv_pitch;
+    const uint16_t* lut;
+};
+}  // namespace fvv
+
 struct fvv_ctx {
     int device = 0;
     int n_cams = 0;
@@ -131,11 +142,19 @@ struct fvv_ctx {
     std::recursive_mutex mu;
     fvv::ServeState* serve = nullptr;
     fvv::RefineNet* refine = nullptr;
+    fvv::CodecState* codec = nullptr;           // depth codec tables (fvv_codec.cu)
 };
 
 namespace fvv {
 
 fvv_status dev_alloc(fvv_ctx* c, void** p, size_t bytes);
+// Upload one camera's frame for `tick` into the frame ring: depth from uint16
+// rows (yuv NULL) or decoded from a YUV420 depth frame.  Caller holds c->mu.
+fvv_status upload_frame(fvv_ctx* c, int cam, const uint8_t* rgb, size_t rgb_pitch, const uint16_t* depth,
+                        size_t depth_pitch, const YuvDepth* yuv, uint64_t tick, cudaStream_t s);
+cudaError_t launch_yuv_decode(const YuvDepth& f, int width, int height, uint16_t* out, size_t out_pitch,
+                              cudaStream_t s);
+void codec_destroy(fvv_ctx* c);
 void dev_free(fvv_ctx* c, void* p, size_t bytes);
 
 // Launch through `fn` (returns cudaError_t), counting it and, when profiling

@@ -142,6 +142,11 @@ def load() -> C.CDLL:
             "fvv_unet_conv3x3": [P, I, I, I, I, P, P, I, I, P, P, P],
             "fvv_selftest_bounded_wait": [I, C.c_uint32, P],
             "fvv_unet_conv3x3_e4m3": [P, I, I, I, I, P, P, I, I, C.c_float, C.c_float, P, P],
+            "fvv_depth_codec_default": [C.POINTER(fvv_depth_codec)],
+            "fvv_set_depth_codec": [P, I, C.POINTER(fvv_depth_codec)],
+            "fvv_depth_encode_yuv": [P, I, P, S, P, S, P, P, S, P],
+            "fvv_depth_decode_yuv": [P, I, P, S, P, P, S, P, S, P],
+            "fvv_upload_frame_yuv": [P, I, P, S, P, S, P, P, S, U64, P],
             "fvv_refine_quantize": [P, C.POINTER(fvv_refine_batch), P, P],
             "fvv_refine_set_precision": [P, I],
             "fvv_refine_get_precision": [P, C.POINTER(I), P],
@@ -384,6 +389,40 @@ def fvv_unet_conv3x3_e4m3(x, n: int, h: int, w: int, cin: int, wt, bias, cout: i
     _check(load().fvv_unet_conv3x3_e4m3(ptr(x), n, h, w, cin, ptr(wt), ptr(bias), cout, 1 if relu else 0,
                                         acc_scale, out_inv_scale, ptr(y), stream_handle(stream)),
            "fvv_unet_conv3x3_e4m3")
+
+
+class fvv_depth_codec(C.Structure):
+    _fields_ = [("z_near", C.c_double), ("z_far", C.c_double), ("alpha", C.c_double), ("beta", C.c_double)]
+
+
+def fvv_depth_codec_default(**overrides) -> fvv_depth_codec:
+    k = fvv_depth_codec()
+    _check(load().fvv_depth_codec_default(C.byref(k)), "fvv_depth_codec_default")
+    for n, v in overrides.items():
+        setattr(k, n, v)
+    return k
+
+
+def fvv_set_depth_codec(ctx: int, cam: int, codec: fvv_depth_codec) -> None:
+    _check(load().fvv_set_depth_codec(ctx, cam, C.byref(codec)), "fvv_set_depth_codec")
+
+
+def fvv_depth_encode_yuv(ctx: int, cam: int, depth, depth_pitch: int, y, y_pitch: int, u, v, uv_pitch: int,
+                         stream=None) -> None:
+    _check(load().fvv_depth_encode_yuv(ctx, cam, ptr(depth), depth_pitch, ptr(y), y_pitch, ptr(u), ptr(v),
+                                       uv_pitch, stream_handle(stream)), "fvv_depth_encode_yuv")
+
+
+def fvv_depth_decode_yuv(ctx: int, cam: int, y, y_pitch: int, u, v, uv_pitch: int, depth, depth_pitch: int,
+                         stream=None) -> None:
+    _check(load().fvv_depth_decode_yuv(ctx, cam, ptr(y), y_pitch, ptr(u), ptr(v), uv_pitch, ptr(depth),
+                                       depth_pitch, stream_handle(stream)), "fvv_depth_decode_yuv")
+
+
+def fvv_upload_frame_yuv(ctx: int, cam: int, rgb, rgb_pitch: int, y, y_pitch: int, u, v, uv_pitch: int,
+                         tick: int, stream=None) -> None:
+    _check(load().fvv_upload_frame_yuv(ctx, cam, ptr(rgb), rgb_pitch, ptr(y), y_pitch, ptr(u), ptr(v), uv_pitch,
+                                       tick, stream_handle(stream)), "fvv_upload_frame_yuv")
 
 
 FVV_PREC_BF16 = 0

@@ -1,0 +1,127 @@
+"""The depth codec (Sec. V-B, Eq. (1)-(3)) on the GPU against the oracle
+(oracle/codec.py): encoding, decoding and the fused YUV upload are integer
+work decided by tables both sides build in FP64, so every byte and every
+depth code must match exactly."""
+import numpy as np
+import pytest
+
+import synthetic as S
+from oracle import codec as K
+from fvv_helpers import lib
+
+pytestmark = pytest.mark.gpu
+
+CODEC = dict(z_near=0.4, z_far=6.0, alpha=0.004, beta=0.995)
+
+
+@pytest.fixture(scope="module")
+def setup():
+    F = lib()
+    wl = S.workload("plain_9cam_1280x720", scale=0.25)              # 320 x 180 cameras
+    ctx = F.fvv_create(F.rig(wl["cams"], wl["look_at"]))
+    for k in range(len(wl["cams"])):
+        F.fvv_set_depth_codec(ctx, k, F.fvv_depth_codec_default(**CODEC))
+    yield F, ctx, wl
+    F.fvv_destroy(ctx)
+
+
+def _depth_cases(wl):
+    """The workload's depth (noise, dropouts) plus codes out of range."""
+    d = np.array(wl["depth"][0], np.uint16)
+    d[:4, :] = 65535                                   # beyond z_far
+    d[4:8, :] = 100                                    # nearer than z_near
+    d[8:10, :] = 0                                     # no depth
+    return d
+
+
+def _planes(H, W):
+    import torch
+    return (torch.zeros((H, W), dtype=torch.uint8, device="cuda"),
+            torch.zeros((H // 2, W // 2), dtype=torch.uint8, device="cuda"),
+            torch.zeros((H // 2, W // 2), dtype=torch.uint8, device="cuda"))
+
+
+def test_encode_matches_oracle(setup):
+    import torch
+    F, ctx, wl = setup
+    H, W = wl["depth"][0].shape
+    d = _depth_cases(wl)
+    y, u, v = _planes(H, W)
+    F.fvv_depth_encode_yuv(ctx, 0, torch.from_numpy(d.astype(np.int16)).cuda(), W * 2, y, W, u, v, W // 2)
+    torch.cuda.synchronize()
+    ry, ru, rv = K.encode(d, unit_m=0.001, **CODEC)
+    assert np.array_equal(y.cpu().numpy(), ry)
+    assert np.array_equal(u.cpu().numpy(), ru)
+    assert np.array_equal(v.cpu().numpy(), rv)
+
+
+def test_decode_matches_oracle_on_every_code(setup):
+    """Random planes: every 12-bit code at every block position occurs."""
+    import torch
+    F, ctx, wl = setup
+    H, W = wl["depth"][0].shape
+    rng = np.random.default_rng(4)
+    Y = rng.integers(0, 256, (H, W), dtype=np.uint8)
+    U = rng.integers(0, 256, (H // 2, W // 2), dtype=np.uint8)
+    V = rng.integers(0, 256, (H // 2, W // 2), dtype=np.uint8)
+    out = torch.zeros((H, W), dtype=torch.int16, device="cuda")
+    F.fvv_depth_decode_yuv(ctx, 3, torch.from_numpy(Y).cuda(), W, torch.from_numpy(U).cuda(),
+                           torch.from_numpy(V).cuda(), W // 2, out, W * 2)
+    torch.cuda.synchronize()
+    ref = K.decode(Y, U, V, CODEC["z_near"], CODEC["z_far"], 0.001)
+    assert np.array_equal(out.cpu().numpy().view(np.uint16), ref)
+    assert len(np.unique(K.unpack_yuv420(Y, U, V))) > 4000
+
+
+@pytest.mark.parametrize("host", [False, True])
+def test_yuv_upload_synthesises_like_the_decoded_depth(setup, oracle_mod, host):
+    """Frames uploaded as YUV420 depth give the same z-buffer keys as the
+    oracle run on the oracle-decoded depth."""
+    import torch
+    F, ctx0, wl = setup
+    cams = wl["cams"]
+    H, W = cams[0].height, cams[0].width
+    ctx = F.fvv_create(F.rig(cams, wl["look_at"]))
+    try:
+        dec = []
+        for k in range(len(cams)):
+            F.fvv_set_depth_codec(ctx, k, F.fvv_depth_codec_default(**CODEC))
+            ry, ru, rv = K.encode(np.asarray(wl["depth"][k]), unit_m=0.001, **CODEC)
+            dec.append(K.decode(ry, ru, rv, CODEC["z_near"], CODEC["z_far"], 0.001))
+            planes = (ry, ru, rv) if host else tuple(torch.from_numpy(p).cuda() for p in (ry, ru, rv))
+            F.fvv_upload_frame_yuv(ctx, k, np.ascontiguousarray(wl["rgb"][k]), W * 3, planes[0], W, planes[1],
+                                   planes[2], W // 2, 0)
+        v = wl["views"][17]
+        keys = torch.zeros((H, W), dtype=torch.int64, device="cuda")
+        out = torch.zeros((H, W * 3), dtype=torch.uint8, device="cuda")
+        F.fvv_synthesize(ctx, v, out, W * 3, F.aux(keys=keys))
+        torch.cuda.synchronize()
+        ref = oracle_mod.synthesize(cams, wl["rgb"], np.stack(dec), v, wl["look_at"])
+        assert np.array_equal(keys.cpu().numpy().view(np.uint64), ref["keys"])
+        diff = np.abs(out.cpu().numpy().reshape(H, W, 3).astype(int) - ref["rgb"].astype(int))
+        assert np.mean(diff <= 1) >= 0.999
+    finally:
+        F.fvv_destroy(ctx)
+
+
+def test_codec_errors(setup):
+    import torch
+    F, ctx0, wl = setup
+    cams = wl["cams"]
+    ctx = F.fvv_create(F.rig(cams, wl["look_at"]))
+    try:
+        H, W = cams[0].height, cams[0].width
+        y, u, v = _planes(H, W)
+        d = torch.zeros((H, W), dtype=torch.int16, device="cuda")
+        with pytest.raises(F.FvvError) as e:                      # no codec set yet
+            F.fvv_depth_encode_yuv(ctx, 0, d, W * 2, y, W, u, v, W // 2)
+        assert e.value.code == F.FVV_ERR_STATE
+        with pytest.raises(F.FvvError) as e:
+            F.fvv_set_depth_codec(ctx, 0, F.fvv_depth_codec_default(z_near=2.0, z_far=1.0))
+        assert e.value.code == F.FVV_ERR_INVALID_ARG
+        F.fvv_set_depth_codec(ctx, 0, F.fvv_depth_codec_default())
+        with pytest.raises(F.FvvError) as e:                      # pitch too small
+            F.fvv_depth_encode_yuv(ctx, 0, d, W, y, W, u, v, W // 2)
+        assert e.value.code == F.FVV_ERR_INVALID_ARG
+    finally:
+        F.fvv_destroy(ctx)
