@@ -294,6 +294,35 @@ def profiled_traffic(kernel, views_per_launch):
     return float(m.group(1)) * views_per_launch
 
 
+def profiled_instructions(kernel):
+    """Warp instructions per view from the committed ncu summary of this
+    kernel; None when the kernel source changed since."""
+    path = os.path.join(ROOT, "profiles", "%s_9cam_1280x720.txt" % kernel)
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    m = re.search(r"^warp_instructions_per_view:\s*([0-9.eE+]+)", text, re.M)
+    sh = re.search(r"^kernel_source_sha:\s*([0-9a-f]+)", text, re.M)
+    if not m or not sh or sh.group(1) != kernel_source_sha():
+        return None
+    return float(m.group(1))
+
+
+def issue_roofline(kernel, views_per_launch, avg_launch_s, sm_mhz, n_sms):
+    """Instruction-issue roofline of an issue-bound kernel: warp instructions
+    per launch / launch time against n_sms x 4 schedulers x 1 warp
+    instruction per cycle at the SM clock sampled during the run."""
+    wi = profiled_instructions(kernel)
+    if wi is None or not sm_mhz:
+        return None
+    achieved = wi * views_per_launch / avg_launch_s
+    peak = n_sms * 4 * sm_mhz * 1e6
+    return {"bound": "issue", "achieved": achieved, "peak": peak, "unit": "warp instructions/s",
+            "frac": achieved / peak, "warp_instructions_per_view": wi,
+            "peak_source": "%d SMs x 4 schedulers x %.0f MHz (sampled)" % (n_sms, sm_mhz)}
+
+
 def algorithmic_bytes(K, Ns, Nd, rho, n_ref):
     """Per-view algorithmic bytes of each kernel (RGB counted as 3 bytes):
     clear: 8 Nd; splat: depth 2 K Ns + one 8-byte atomicMin per valid source
@@ -333,15 +362,17 @@ def codec_bench(F, ctx, wl, stream, reps=50):
     for k in range(K):
         F.fvv_depth_decode_yuv(ctx, k, planes[k][0], W, planes[k][1], planes[k][2], W // 2, out[k], W * 2, stream)
     torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
+    # kernel time from the library's per-launch CUDA events on the launching stream
+    F.fvv_profile_enable(ctx, 1)
+    F.fvv_profile_read(ctx, reset=True)
     for _ in range(reps):
         for k in range(K):
             F.fvv_depth_decode_yuv(ctx, k, planes[k][0], W, planes[k][1], planes[k][2], W // 2, out[k], W * 2,
                                    stream)
-    e1.record(stream)
     torch.cuda.synchronize()
-    us = e0.elapsed_time(e1) * 1e3 / (reps * K)
+    st = F.fvv_profile_read(ctx, reset=True)["yuv_decode"]
+    F.fvv_profile_enable(ctx, 0)
+    us = st[2] * 1e3 / max(1, st[1])
     gbs = 3.5 * H * W / (us * 1e-6) / 1e9
     peak, src = measured_peaks()
     # one tick uploaded from pinned host memory: YUV420 depth vs uint16 depth
@@ -355,14 +386,15 @@ def codec_bench(F, ctx, wl, stream, reps=50):
 
     def tick_ms(yuv, n=10):
         torch.cuda.synchronize()
+        base = F.fvv_latest_tick(ctx) + 1
         t0 = time.perf_counter()
         for t in range(n):
             for k in range(K):
                 if yuv:
                     F.fvv_upload_frame_yuv(ctx, k, rgb_h[k], W * 3, yuv_h[k][0], W, yuv_h[k][1], yuv_h[k][2],
-                                           W // 2, 1000 + t, stream)
+                                           W // 2, base + t, stream)
                 else:
-                    F.fvv_upload_frame(ctx, k, rgb_h[k], W * 3, dep_h[k], W * 2, 1000 + t, stream)
+                    F.fvv_upload_frame(ctx, k, rgb_h[k], W * 3, dep_h[k], W * 2, base + t, stream)
             torch.cuda.synchronize()
         return (time.perf_counter() - t0) * 1e3 / n
     tick_ms(True, 2)
@@ -802,6 +834,12 @@ def run_fvv(args):
         cpu = {"value": n / wall, "unit": UNIT, "cores": pool.procs, "kind": "oracle",
                "sample": "%d views of the 9-camera 1280x720 swing in %.1f s on %d worker processes "
                          "(one single-threaded oracle each)" % (n, wall, pool.procs)}
+
+    if roofline is not None:
+        clk = clocks.summary() or {}
+        n_sms = torch.cuda.get_device_properties(local).multi_processor_count
+        roofline["issue"] = {k: issue_roofline(k, Bsz, timed[k][2] / timed[k][1] / 1e3, clk.get("sm_mhz"), n_sms)
+                             for k in ("resolve", "warp_splat") if k in timed}
 
     if rank == 0:
         line = {

@@ -330,7 +330,9 @@ fvv_status fvv::upload_frame(fvv_ctx* c, int cam, const uint8_t* rgb, size_t rgb
                                    size_t(C.height), cudaMemcpyDefault, s));
     const uint8_t* src = rgb;
     size_t spitch = rgb_pitch;
-    if (mem_kind(rgb) == MemKind::Host) {
+    const bool staged = mem_kind(rgb) == MemKind::Host;
+    if (staged) {
+        FVV_CUDA(cudaStreamWaitEvent(s, c->stage_free, 0));   // a previous upload may still read it
         if (!c->stage_rgb[cam]) {
             void* p = nullptr;
             FVV_TRY(dev_alloc(c, &p, size_t(C.width) * 3 * size_t(C.height)));
@@ -344,9 +346,82 @@ fvv_status fvv::upload_frame(fvv_ctx* c, int cam, const uint8_t* rgb, size_t rgb
     FVV_TRY(run_kernel(c, kPack, s, [&] {
         return fvv::launch_pack_rgba(src, spitch, rdst, c->rpitch[cam], C.width, C.height, s);
     }));
+    if (staged) FVV_CUDA(cudaEventRecord(c->stage_free, s));
     FVV_CUDA(cudaEventRecord(S.uploaded, s));
     S.mask |= uint64_t(1) << cam;
     if (S.mask == c->full_mask && (!c->have_latest || tick > c->latest)) {
+        c->latest = tick;
+        c->have_latest = true;
+    }
+    return FVV_OK;
+}
+
+// Every camera of one tick (all of one size) in one launch, after at most
+// two bulk host-to-device copies into the context's staging buffer.
+static fvv_status upload_all(fvv_ctx* c, const uint8_t* rgb, size_t rcs, size_t rp, const uint8_t* depth,
+                             size_t dcs, size_t dp, uint64_t tick, cudaStream_t s, bool host)
+{
+    using namespace fvv;
+    const int K = c->n_cams, W = c->cams[0].width, H = c->cams[0].height;
+    if (rp < size_t(W) * 3) return fail(FVV_ERR_INVALID_ARG, "rgb_pitch < 3 * width");
+    if (dp < size_t(W) * 2 || dp % 2) return fail(FVV_ERR_INVALID_ARG, "depth_pitch < 2 * width or odd");
+    if (dcs % 2) return fail(FVV_ERR_INVALID_ARG, "depth camera stride must be even");
+    const int si = int(tick % uint64_t(c->slots));
+    SlotState& S = c->slot[si];
+    if (S.any && tick < S.tick)
+        return fail(FVV_ERR_STATE, "tick " + std::to_string(tick) + " is older than tick " +
+                                       std::to_string(S.tick) + " held by its slot");
+    if (!S.any || tick > S.tick) {
+        S.any = true;
+        S.tick = tick;
+        S.mask = 0;
+    }
+    for (int r = 0; r < kMaxReaders; ++r)
+        if (S.read_pending[r]) FVV_CUDA(cudaStreamWaitEvent(s, S.read[r], 0));
+    const uint8_t* r = rgb;
+    const uint8_t* d = depth;
+    if (host) {
+        const size_t rspan = size_t(K - 1) * rcs + size_t(H - 1) * rp + size_t(W) * 3;
+        const size_t dspan = size_t(K - 1) * dcs + size_t(H - 1) * dp + size_t(W) * 2;
+        const size_t doff = align_up(rspan, 256);
+        if (c->stage_all_bytes < doff + dspan) {
+            FVV_CUDA(cudaEventSynchronize(c->stage_free));
+            dev_free(c, c->stage_all, c->stage_all_bytes);
+            c->stage_all = nullptr;
+            c->stage_all_bytes = 0;
+            void* p = nullptr;
+            FVV_TRY(dev_alloc(c, &p, doff + dspan));
+            c->stage_all = static_cast<uint8_t*>(p);
+            c->stage_all_bytes = doff + dspan;
+        }
+        FVV_CUDA(cudaStreamWaitEvent(s, c->stage_free, 0));    // a previous upload may still read it
+        FVV_CUDA(cudaMemcpyAsync(c->stage_all, rgb, rspan, cudaMemcpyHostToDevice, s));
+        FVV_CUDA(cudaMemcpyAsync(c->stage_all + doff, depth, dspan, cudaMemcpyHostToDevice, s));
+        r = c->stage_all;
+        d = c->stage_all + doff;
+    }
+    UploadAll u{};
+    u.rgb = r;
+    u.rgb_cam_stride = rcs;
+    u.rgb_pitch = rp;
+    u.depth = d;
+    u.depth_cam_stride = dcs;
+    u.depth_pitch = dp;
+    u.slot = c->arena + size_t(si) * c->slot_bytes;
+    u.W = W;
+    u.H = H;
+    u.n_cams = K;
+    u.dpitch = c->dpitch[0];
+    u.rpitch = c->rpitch[0];
+    for (int k = 0; k < K; ++k) {
+        u.off_depth[k] = c->off_depth[k];
+        u.off_rgba[k] = c->off_rgba[k];
+    }
+    FVV_TRY(run_kernel(c, kPack, s, [&] { return launch_upload_all(u, s); }));
+    if (host) FVV_CUDA(cudaEventRecord(c->stage_free, s));
+    FVV_CUDA(cudaEventRecord(S.uploaded, s));
+    S.mask = c->full_mask;
+    if (!c->have_latest || tick > c->latest) {
         c->latest = tick;
         c->have_latest = true;
     }
@@ -686,6 +761,8 @@ fvv_status fvv_destroy(fvv_ctx* c)
             dev_free(c, c->stage_rgb[k], size_t(c->cams[k].width) * 3 * size_t(c->cams[k].height));
     dev_free(c, c->frames_dev, sizeof(FrameRef) * size_t(c->slots) * c->n_cams);
     dev_free(c, c->arena, c->arena_bytes);
+    if (c->stage_all) dev_free(c, c->stage_all, c->stage_all_bytes);
+    if (c->stage_free) cudaEventDestroy(c->stage_free);
     if (c->own) cudaStreamDestroy(c->own);
     cudaGetLastError();
     cudaSetDevice(cur);
@@ -780,6 +857,8 @@ fvv_status fvv_create(const fvv_rig* rig, const fvv_options* opt, fvv_ctx** out)
         FVV_CREATE_CUDA(cudaEventCreateWithFlags(&S.uploaded, cudaEventDisableTiming));
         FVV_CREATE_CUDA(cudaEventRecord(S.uploaded, c->own));
     }
+    FVV_CREATE_CUDA(cudaEventCreateWithFlags(&c->stage_free, cudaEventDisableTiming));
+    FVV_CREATE_CUDA(cudaEventRecord(c->stage_free, c->own));
     FVV_CREATE_TRY(fvv::scratch_alloc(c, c->main, 0, 0, o.max_batch, 4));
     c->main.growable = true;
     FVV_CREATE_CUDA(cudaStreamSynchronize(c->own));
@@ -807,6 +886,13 @@ fvv_status fvv_upload_frames(fvv_ctx* c, const uint8_t* rgb, size_t rgb_cam_stri
     if (!rgb || !depth) return fail(FVV_ERR_INVALID_ARG, "rgb and depth must be non-NULL");
     cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : c->own;
     std::lock_guard<std::recursive_mutex> lock(c->mu);
+    bool uniform = true;
+    for (int k = 1; k < c->n_cams; ++k)
+        uniform = uniform && c->cams[k].width == c->cams[0].width && c->cams[k].height == c->cams[0].height;
+    const fvv::MemKind kr = fvv::mem_kind(rgb), kd = fvv::mem_kind(depth);
+    if (uniform && kr == kd)
+        return upload_all(c, rgb, rgb_cam_stride, rgb_pitch, reinterpret_cast<const uint8_t*>(depth),
+                          depth_cam_stride, depth_pitch, tick, s, kr == fvv::MemKind::Host);
     for (int k = 0; k < c->n_cams; ++k) {
         const uint8_t* r = rgb + size_t(k) * rgb_cam_stride;
         const uint16_t* d = reinterpret_cast<const uint16_t*>(

@@ -266,8 +266,8 @@ fvv_status fvv_depth_decode_yuv(fvv_ctx* c, int32_t cam, const uint8_t* y, size_
         return fail(FVV_ERR_INVALID_ARG, "pitch too small, or depth not 4-byte aligned");
     cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : c->own;
     const fvv::YuvDepth f{y, u, v, y_pitch, uv_pitch, c->codec->dec[cam]};
-    FVV_CUDA(fvv::launch_yuv_decode(f, W, H, depth, depth_pitch, s));
-    return FVV_OK;
+    std::lock_guard<std::recursive_mutex> g(c->mu);
+    return fvv::run_kernel(c, fvv::kDecode, s, [&] { return fvv::launch_yuv_decode(f, W, H, depth, depth_pitch, s); });
 }
 
 fvv_status fvv_upload_frame_yuv(fvv_ctx* c, int32_t cam, const uint8_t* rgb, size_t rgb_pitch, const uint8_t* y,

@@ -30,7 +30,7 @@ constexpr int kGeomFloats = 20;   // per-camera record of the resolve kernel
 constexpr int kRing = 4;          // key rows kept in shared memory (3 in use + 1 in flight)
 
 struct SmemLayout {
-    size_t ring, rgb, dep, hole, left, right, geom, rowt, frames, active, scan, total;
+    size_t ring, rgb, dep, hole, left, right, geom, rowt, frames, active, pos, scan, total;
 };
 
 __host__ __device__ inline SmemLayout resolve_layout(int W, int n_cams)
@@ -47,6 +47,7 @@ __host__ __device__ inline SmemLayout resolve_layout(int W, int n_cams)
     L.rowt = o;   o = align16(o + size_t(n_cams) * 4 * sizeof(float));
     L.frames = o; o = align16(o + size_t(n_cams) * sizeof(FrameRef));
     L.active = o; o = align16(o + size_t(kMaxCams) * sizeof(int));
+    L.pos = o;    o = align16(o + size_t(kMaxCams) * sizeof(int));
     L.scan = o;   o = align16(o + 64 * sizeof(int));
     L.total = o;
     return L;
@@ -358,6 +359,7 @@ k_resolve(const ViewDesc* __restrict__ views, const FrameRef* __restrict__ frame
     float* s_rowt = reinterpret_cast<float*>(smem + L.rowt);
     FrameRef* s_fr = reinterpret_cast<FrameRef*>(smem + L.frames);
     int* s_act = reinterpret_cast<int*>(smem + L.active);
+    int* s_pos = reinterpret_cast<int*>(smem + L.pos);        // camera -> position in s_act
     int* s_scan = reinterpret_cast<int*>(smem + L.scan);
     const int tid = threadIdx.x;
     constexpr int NT = kResolveThreads;
@@ -392,6 +394,12 @@ k_resolve(const ViewDesc* __restrict__ views, const FrameRef* __restrict__ frame
         s_fr[i] = frames[V->slot * nc + i];
     for (int i = tid; i < na; i += NT)
         s_act[i] = V->active[i];
+    for (int k = tid; k < kMaxCams; k += NT) {     // 0 for inactive cameras keeps every index in range
+        int p = 0;
+        for (int i = 0; i < na; ++i)
+            if (V->active[i] == k) p = i;
+        s_pos[k] = p;
+    }
 
     const bool crack = (V->flags & kFlagCrack) != 0;
     const bool fill = (V->flags & kFlagFill) != 0;
@@ -454,10 +462,12 @@ k_resolve(const ViewDesc* __restrict__ views, const FrameRef* __restrict__ frame
             float t0 = ww, t1 = -1.0f, t2 = -1.0f;
             int k0 = w, k1 = INT_MAX, k2 = INT_MAX;
             const float fx = u23_to_float(uint32_t(x));
-            // cameras in groups of four: project all four and issue their
-            // depth and colour gathers before any is consumed, then
-            // accumulate in ascending camera order
-            for (int g0 = 0; g0 < na; g0 += 4) {
+            // the other active cameras (the winner is always active: only
+            // active cameras splat), in ascending order, in groups of four:
+            // project all four and issue their depth and colour gathers
+            // before any is consumed, then accumulate in order
+            const int pw = s_pos[w], nother = na - 1;
+            for (int g0 = 0; g0 < nother; g0 += 4) {
                 uint32_t dk[4], ck[4];
                 float zk[4];
                 int kk[4];
@@ -466,8 +476,8 @@ k_resolve(const ViewDesc* __restrict__ views, const FrameRef* __restrict__ frame
                 // predicated), so the four chains can interleave
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
-                    const int ai = min(g0 + j, na - 1);
-                    const int k = s_act[ai];
+                    const int ii = min(g0 + j, nother - 1);
+                    const int k = s_act[ii + (ii >= pw ? 1 : 0)];
                     kk[j] = k;
                     const float4 A = g4[5 * k + 0], Bq = g4[5 * k + 1], Cq = g4[5 * k + 2],
                                  Eq = g4[5 * k + 4];
@@ -481,7 +491,7 @@ k_resolve(const ViewDesc* __restrict__ views, const FrameRef* __restrict__ frame
                     const float tu = floorf(__fadd_rn(__fdiv_rn(Xk, Zk), 0.5f));
                     const float tv = floorf(__fadd_rn(__fdiv_rn(Yk, Zk), 0.5f));
                     // the bounds test also rejects NaN and +-inf, as a finiteness test would
-                    ok[j] = g0 + j < na && k != w && Zk > zmin && tu >= 0.0f && tu <= Eq.x &&
+                    ok[j] = g0 + j < nother && Zk > zmin && tu >= 0.0f && tu <= Eq.x &&
                             tv >= 0.0f && tv <= Eq.y;
                     zk[j] = Zk;
                     dk[j] = 0u;

@@ -99,6 +99,22 @@ struct RefineNet;                         // fvv_refine.cu
 namespace fvv {
 struct CodecState;
 
+// One tick of every camera (all W x H) into a frame-ring slot: camera k's RGB8
+// rows at rgb + k * rgb_cam_stride (pitch rgb_pitch) become RGBA8 rows at
+// slot + off_rgba[k] (pitch rpitch texels), its uint16 depth rows at
+// depth + k * depth_cam_stride (pitch depth_pitch bytes) are copied to
+// slot + off_depth[k] (pitch dpitch elements).
+struct UploadAll {
+    const uint8_t* rgb;
+    size_t rgb_cam_stride, rgb_pitch;
+    const uint8_t* depth;
+    size_t depth_cam_stride, depth_pitch;
+    uint8_t* slot;
+    int W, H, n_cams, dpitch, rpitch;
+    uint64_t off_depth[kMaxCams], off_rgba[kMaxCams];
+};
+cudaError_t launch_upload_all(const UploadAll& u, cudaStream_t stream);
+
 // A YUV420 depth frame in device memory and the decode table of its camera.
 struct YuvDepth {
     const uint8_t *y, *u, *v;
@@ -130,6 +146,9 @@ struct fvv_ctx {
     bool have_latest = false;
 
     std::vector<uint8_t*> stage_rgb;            // per camera, for host uploads
+    uint8_t* stage_all = nullptr;               // batched host uploads (all cameras)
+    size_t stage_all_bytes = 0;
+    cudaEvent_t stage_free = nullptr;           // last reader of the staging buffers
     fvv::BatchScratch main;                     // scratch of fvv_synthesize(_batch)
 
     bool profiling = false;

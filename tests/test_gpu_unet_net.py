@@ -121,8 +121,10 @@ def test_training_reduces_loss_and_checkpoint_round_trip(net):
     # a learnable target: the inverted colour (a linear function of the input)
     dev["target"] = (255 - dev["rgb"]).contiguous()
     b = F.refine_batch(n, h, w, dev["rgb"], dev["depth"], dev["hole"], dev["top3"], dev["target"])
-    losses = [F.fvv_refine_train_step(ctx, b, 2e-3) for _ in range(80)]
-    print("training losses", losses[0], losses[20], losses[40], losses[-1])
+    # the weight gradients accumulate with fp32 atomics in no fixed order, so
+    # trajectories differ from run to run; 160 steps leave a wide margin
+    losses = [F.fvv_refine_train_step(ctx, b, 2e-3) for _ in range(160)]
+    print("training losses", losses[0], losses[40], losses[80], losses[-1])
     assert losses[-1] < 0.25 * losses[0], (losses[0], losses[-1])
     with tempfile.TemporaryDirectory() as d:
         path = os.path.join(d, "unet.bin")
