@@ -87,8 +87,8 @@ __device__ __forceinline__ uint32_t unfold(uint32_t ybyte, uint32_t msb)
     return (msb << 8) | ((msb & 1u) ? 255u - ybyte : ybyte);
 }
 
-// Grid-stride over 2x2 blocks; the decode table is staged once per CTA (a
-// few CTAs per SM, so table traffic stays far below the frame's).
+// Grid-stride over 2x2 blocks; the 8 KB decode table is read through the L1
+// (it stays cached: staging a copy per CTA cost more traffic than the frame).
 __device__ __forceinline__ void decode_block(const YuvDepth& f, const uint16_t* lut, int bx, int by,
                                              uint16_t* out, size_t opitch)
 {
@@ -99,8 +99,8 @@ __device__ __forceinline__ void decode_block(const YuvDepth& f, const uint16_t* 
     deinterleave4(f.v[size_t(by) * f.uv_pitch + bx], m21, m22);
     uint16_t* r0 = reinterpret_cast<uint16_t*>(reinterpret_cast<uint8_t*>(out) + size_t(2 * by) * opitch) + 2 * bx;
     uint16_t* r1 = reinterpret_cast<uint16_t*>(reinterpret_cast<uint8_t*>(r0) + opitch);
-    const uint32_t a = lut[unfold(y0[0], m11)], b = lut[unfold(y0[1], m12)];
-    const uint32_t c = lut[unfold(y1[0], m21)], d = lut[unfold(y1[1], m22)];
+    const uint32_t a = __ldg(lut + unfold(y0[0], m11)), b = __ldg(lut + unfold(y0[1], m12));
+    const uint32_t c = __ldg(lut + unfold(y1[0], m21)), d = __ldg(lut + unfold(y1[1], m22));
     *reinterpret_cast<uint32_t*>(r0) = a | (b << 16);
     *reinterpret_cast<uint32_t*>(r1) = c | (d << 16);
 }
@@ -108,12 +108,9 @@ __device__ __forceinline__ void decode_block(const YuvDepth& f, const uint16_t* 
 __global__ void __launch_bounds__(512) k_yuv_decode(YuvDepth f, int bw, int bh, uint16_t* __restrict__ out,
                                                     size_t opitch)
 {
-    __shared__ uint16_t lut[4096];
-    for (int i = threadIdx.x; i < 4096; i += blockDim.x) lut[i] = f.lut[i];
-    __syncthreads();
     const size_t n = size_t(bw) * bh;
     for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += size_t(gridDim.x) * blockDim.x)
-        decode_block(f, lut, int(i % bw), int(i / bw), out, opitch);
+        decode_block(f, f.lut, int(i % bw), int(i / bw), out, opitch);
 }
 
 __global__ void __launch_bounds__(256) k_yuv_encode(const uint16_t* __restrict__ depth, size_t dpitch, int bw,
