@@ -221,11 +221,20 @@ fvv_status fvv_upload_frame_yuv(fvv_ctx* ctx, int32_t cam, const uint8_t* rgb, s
  * renders from the newest complete frame tick when it is formed; frames keep
  * being uploaded with fvv_upload_frame(s) meanwhile.  Latency is measured
  * from fvv_serve_submit to the completion of the request's output write. */
+/* With refine = 1 (fvv_refine_init first) each batch renders the plain views
+ * into lane scratch, then the refinement network (in its current precision,
+ * bf16 or E4M3) runs on one refinement stream shared by the lanes and writes
+ * the requests' outputs.  A batch then holds requests of one size: the
+ * oldest queued request and later ones of its width and height.  Views need
+ * width and height multiples of 4.  The network's own activations are not
+ * part of memory_budget.  While such a session runs, the fvv_refine_* calls
+ * that use or change the network return FVV_ERR_BUSY. */
 typedef struct fvv_serve_cfg {
     int32_t lanes;              /* batches in flight on the GPU, 1..16, default 3 */
     int32_t max_batch;          /* views per batched launch, default 16 */
     int32_t max_pending;        /* submitted and not yet polled, default 4096 */
     uint64_t memory_budget;     /* device bytes of serving scratch (all lanes), default 768 MiB */
+    int32_t refine;             /* 1: every view also runs the refinement network (see below) */
 } fvv_serve_cfg;
 
 typedef struct fvv_serve_report {

@@ -91,8 +91,11 @@ struct RefineNet {
     float *mwo = nullptr, *vwo = nullptr, *mbo = nullptr, *vbo = nullptr;
     int step = 0;
     std::vector<std::pair<void*, size_t>> params;     // device allocations of parameters
-    int B = 0, H = 0, W = 0;
-    std::vector<std::pair<void*, size_t>> acts;       // activations for (B, H, W)
+    // activations (and their gradients) for up to `cap` pixels: every buffer
+    // is dense NHWC over the batch, so any (B, H, W) with B*H*W <= cap and H, W
+    // multiples of 4 fits at the full, half and quarter resolutions
+    size_t cap = 0, gcap = 0;
+    std::vector<std::pair<void*, size_t>> acts, grads;
     __nv_bfloat16 *x0, *e1a, *p1, *e2a, *p2, *ba, *cat2, *d2a, *cat1, *d1a, *d1;
     uint8_t *arg1, *arg2;
     float* s;
@@ -106,7 +109,7 @@ struct RefineNet {
     float s_act[10] = {};
     float s0 = 1.0f / 256.0f;
     float* amax = nullptr;
-    int qB = 0, qH = 0, qW = 0;
+    size_t qcap = 0;                                  // e4m3 activations, pixels
     std::vector<std::pair<void*, size_t>> acts8;
     uint8_t *q_x0, *q_e1a, *q_p1, *q_e2a, *q_p2, *q_ba, *q_cat2, *q_d2a, *q_cat1, *q_d1a, *q_d1;
     // plain-synthesis outputs feeding fvv_synthesize_refined
@@ -229,13 +232,13 @@ fvv_status set_flat(RefineNet& N, Buf which, const float* in, cudaStream_t s)
     return FVV_OK;
 }
 
-fvv_status ensure_acts(fvv_ctx* c, RefineNet& N, int B, int H, int W)
+fvv_status ensure_acts(fvv_ctx* c, RefineNet& N, size_t pixels)
 {
-    if (N.B == B && N.H == H && N.W == W) return FVV_OK;
+    if (pixels <= N.cap) return FVV_OK;
     FVV_CUDA(cudaDeviceSynchronize());
     free_list(c, N.acts);
-    N.B = N.H = N.W = 0;
-    const size_t p1 = size_t(B) * H * W, p2 = p1 / 4, p3 = p1 / 16;
+    N.cap = 0;
+    const size_t p1 = pixels, p2 = p1 / 4, p3 = p1 / 16;
     const int w1 = N.L[1].cout, w2 = N.L[3].cout, w3 = N.L[5].cout;
     auto A = [&](__nv_bfloat16** p, size_t n) { return alloc_t(c, N.acts, p, n); };
     FVV_TRY(A(&N.x0, p1 * kX0Stride));
@@ -249,6 +252,23 @@ fvv_status ensure_acts(fvv_ctx* c, RefineNet& N, int B, int H, int W)
     FVV_TRY(A(&N.cat1, p1 * (w2 + w1)));
     FVV_TRY(A(&N.d1a, p1 * w1));
     FVV_TRY(A(&N.d1, p1 * w1));
+    FVV_TRY(alloc_t(c, N.acts, &N.arg1, p2 * w1));
+    FVV_TRY(alloc_t(c, N.acts, &N.arg2, p3 * w2));
+    FVV_TRY(alloc_t(c, N.acts, &N.s, p1 * 3));
+    N.cap = pixels;
+    return FVV_OK;
+}
+
+// Activation gradients (training) for up to `pixels` pixels.
+fvv_status ensure_grads(fvv_ctx* c, RefineNet& N, size_t pixels)
+{
+    if (pixels <= N.gcap) return FVV_OK;
+    FVV_CUDA(cudaDeviceSynchronize());
+    free_list(c, N.grads);
+    N.gcap = 0;
+    const size_t p1 = pixels, p2 = p1 / 4, p3 = p1 / 16;
+    const int w1 = N.L[1].cout, w2 = N.L[3].cout, w3 = N.L[5].cout;
+    auto A = [&](__nv_bfloat16** p, size_t n) { return alloc_t(c, N.grads, p, n); };
     FVV_TRY(A(&N.g_d1b, p1 * w1));
     FVV_TRY(A(&N.g_d1a, p1 * w1));
     FVV_TRY(A(&N.g_cat1, p1 * (w2 + w1)));
@@ -265,12 +285,7 @@ fvv_status ensure_acts(fvv_ctx* c, RefineNet& N, int B, int H, int W)
     FVV_TRY(A(&N.g_p1, p2 * w1));
     FVV_TRY(A(&N.g_e1b, p1 * w1));
     FVV_TRY(A(&N.g_e1a, p1 * w1));
-    FVV_TRY(alloc_t(c, N.acts, &N.arg1, p2 * w1));
-    FVV_TRY(alloc_t(c, N.acts, &N.arg2, p3 * w2));
-    FVV_TRY(alloc_t(c, N.acts, &N.s, p1 * 3));
-    N.B = B;
-    N.H = H;
-    N.W = W;
+    N.gcap = pixels;
     return FVV_OK;
 }
 
@@ -384,13 +399,13 @@ fvv_status backward(RefineNet& N, const fvv_refine_batch& b, int* err, cudaStrea
     return FVV_OK;
 }
 
-fvv_status ensure_acts8(fvv_ctx* c, RefineNet& N, int B, int H, int W)
+fvv_status ensure_acts8(fvv_ctx* c, RefineNet& N, size_t pixels)
 {
-    if (N.qB == B && N.qH == H && N.qW == W) return FVV_OK;
+    if (pixels <= N.qcap) return FVV_OK;
     FVV_CUDA(cudaDeviceSynchronize());
     free_list(c, N.acts8);
-    N.qB = N.qH = N.qW = 0;
-    const size_t p1 = size_t(B) * H * W, p2 = p1 / 4, p3 = p1 / 16;
+    N.qcap = 0;
+    const size_t p1 = pixels, p2 = p1 / 4, p3 = p1 / 16;
     const int w1 = N.L[1].cout, w2 = N.L[3].cout, w3 = N.L[5].cout;
     auto A = [&](uint8_t** p, size_t n) { return alloc_t(c, N.acts8, p, n); };
     FVV_TRY(A(&N.q_x0, p1 * kX0StrideQ));
@@ -404,9 +419,7 @@ fvv_status ensure_acts8(fvv_ctx* c, RefineNet& N, int B, int H, int W)
     FVV_TRY(A(&N.q_cat1, p1 * (w2 + w1)));
     FVV_TRY(A(&N.q_d1a, p1 * w1));
     FVV_TRY(A(&N.q_d1, p1 * w1));
-    N.qB = B;
-    N.qH = H;
-    N.qW = W;
+    N.qcap = pixels;
     return FVV_OK;
 }
 
@@ -545,12 +558,39 @@ void refine_destroy(fvv_ctx* c)
     if (!N) return;
     cudaDeviceSynchronize();
     free_list(c, N->acts);
+    free_list(c, N->grads);
     free_list(c, N->acts8);
     free_list(c, N->syn);
     free_list(c, N->params);
     delete N;
     c->refine = nullptr;
 }
+
+bool refine_ready(fvv_ctx* c) { return c && c->refine; }
+
+fvv_status refine_reserve(fvv_ctx* c, size_t pixels)
+{
+    RefineNet* N = c->refine;
+    if (!N) return fail(FVV_ERR_STATE, "refinement network not initialised");
+    return N->precision == FVV_PREC_E4M3 ? ensure_acts8(c, *N, pixels) : ensure_acts(c, *N, pixels);
+}
+
+fvv_status refine_forward_async(fvv_ctx* c, const fvv_refine_batch& b, uint8_t* out_rgb, cudaStream_t s)
+{
+    RefineNet* N = c->refine;
+    if (!N) return fail(FVV_ERR_STATE, "refinement network not initialised");
+    int* err = nullptr;
+    FVV_TRY(device_flag(&err));
+    const size_t px = size_t(b.n) * b.height * b.width;
+    if (N->precision == FVV_PREC_E4M3) {
+        FVV_TRY(ensure_acts8(c, *N, px));
+        return forward_e4m3(*N, b, err, s, out_rgb, size_t(b.width) * 3, nullptr);
+    }
+    FVV_TRY(ensure_acts(c, *N, px));
+    return forward(*N, b, err, s, out_rgb, size_t(b.width) * 3, nullptr);
+}
+
+fvv_status refine_error_flag(int** flag) { return device_flag(flag); }
 
 }  // namespace fvv
 
@@ -647,6 +687,7 @@ fvv_status fvv_refine_init(fvv_ctx* c, const fvv_unet_cfg* cfg_in)
         return fail(FVV_ERR_INVALID_ARG, "the first width must be 32, 48 or 64");
     if (!(cfg.z_far > 0.0f)) return fail(FVV_ERR_INVALID_ARG, "z_far must be > 0");
     std::lock_guard<std::recursive_mutex> g(c->mu);
+    if (fvv::serve_refining(c)) return fail(FVV_ERR_BUSY, "the serving loop is running the refinement network");
     FVV_CUDA(cudaSetDevice(c->device));
     fvv::refine_destroy(c);
     auto* N = new RefineNet();
@@ -728,6 +769,7 @@ fvv_status fvv_refine_set(fvv_ctx* c, int32_t which, const float* in)
     if (!N) return fail(FVV_ERR_STATE, "refinement network not initialised");
     if (!in || which < 0 || which > 3) return fail(FVV_ERR_INVALID_ARG, "bad buffer selector or NULL");
     std::lock_guard<std::recursive_mutex> g(c->mu);
+    if (fvv::serve_refining(c)) return fail(FVV_ERR_BUSY, "the serving loop is running the refinement network");
     FVV_CUDA(cudaDeviceSynchronize());
     FVV_TRY(fvv::set_flat(*N, fvv::Buf(which), in, c->own));
     FVV_CUDA(cudaStreamSynchronize(c->own));
@@ -744,13 +786,14 @@ fvv_status fvv_refine_forward(fvv_ctx* c, const fvv_refine_batch* b, uint8_t* ou
         return fail(FVV_ERR_INVALID_ARG, "outputs must be device memory");
     cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : c->own;
     std::lock_guard<std::recursive_mutex> g(c->mu);
+    if (fvv::serve_refining(c)) return fail(FVV_ERR_BUSY, "the serving loop is running the refinement network");
     int* err = nullptr;
     FVV_TRY(fvv::device_flag(&err));
     if (N->precision == FVV_PREC_E4M3) {
-        FVV_TRY(fvv::ensure_acts8(c, *N, b->n, b->height, b->width));
+        FVV_TRY(fvv::ensure_acts8(c, *N, size_t(b->n) * b->height * b->width));
         FVV_TRY(fvv::forward_e4m3(*N, *b, err, s, out_rgb, size_t(b->width) * 3, out_f32));
     } else {
-        FVV_TRY(fvv::ensure_acts(c, *N, b->n, b->height, b->width));
+        FVV_TRY(fvv::ensure_acts(c, *N, size_t(b->n) * b->height * b->width));
         FVV_TRY(fvv::forward(*N, *b, err, s, out_rgb, size_t(b->width) * 3, out_f32));
     }
     return fvv::check_flag(err, s, "fvv_refine_forward");
@@ -762,6 +805,7 @@ fvv_status fvv_refine_quantize(fvv_ctx* c, const fvv_refine_batch* calib, const 
     if (!N) return fail(FVV_ERR_STATE, "refinement network not initialised");
     cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : c->own;
     std::lock_guard<std::recursive_mutex> g(c->mu);
+    if (fvv::serve_refining(c)) return fail(FVV_ERR_BUSY, "the serving loop is running the refinement network");
     float sc[10];
     if (act_scales) {
         for (int i = 0; i < 10; ++i) {
@@ -773,7 +817,7 @@ fvv_status fvv_refine_quantize(fvv_ctx* c, const fvv_refine_batch* calib, const 
         FVV_TRY(fvv::check_batch(*N, calib, false));
         int* err = nullptr;
         FVV_TRY(fvv::device_flag(&err));
-        FVV_TRY(fvv::ensure_acts(c, *N, calib->n, calib->height, calib->width));
+        FVV_TRY(fvv::ensure_acts(c, *N, size_t(calib->n) * calib->height * calib->width));
         FVV_TRY(fvv::forward(*N, *calib, err, s, nullptr, 0, nullptr));
         FVV_TRY(fvv::check_flag(err, s, "fvv_refine_quantize"));
         const size_t p1 = size_t(calib->n) * calib->height * calib->width, p2 = p1 / 4, p3 = p1 / 16;
@@ -806,6 +850,7 @@ fvv_status fvv_refine_set_precision(fvv_ctx* c, int32_t precision)
     if (precision != FVV_PREC_BF16 && precision != FVV_PREC_E4M3)
         return fail(FVV_ERR_INVALID_ARG, "precision must be FVV_PREC_BF16 or FVV_PREC_E4M3");
     std::lock_guard<std::recursive_mutex> g(c->mu);
+    if (fvv::serve_refining(c)) return fail(FVV_ERR_BUSY, "the serving loop is running the refinement network");
     if (precision == FVV_PREC_E4M3 && !N->q_ready)
         return fail(FVV_ERR_STATE, "no current e4m3 weights: call fvv_refine_quantize");
     N->precision = precision;
@@ -832,9 +877,11 @@ fvv_status fvv_refine_train_step(fvv_ctx* c, const fvv_refine_batch* b, float lr
     if (!(lr >= 0.0f) || !std::isfinite(lr)) return fail(FVV_ERR_INVALID_ARG, "lr must be >= 0");
     cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : c->own;
     std::lock_guard<std::recursive_mutex> g(c->mu);
+    if (fvv::serve_refining(c)) return fail(FVV_ERR_BUSY, "the serving loop is running the refinement network");
     int* err = nullptr;
     FVV_TRY(fvv::device_flag(&err));
-    FVV_TRY(fvv::ensure_acts(c, *N, b->n, b->height, b->width));
+    FVV_TRY(fvv::ensure_acts(c, *N, size_t(b->n) * b->height * b->width));
+    FVV_TRY(fvv::ensure_grads(c, *N, size_t(b->n) * b->height * b->width));
     FVV_TRY(fvv::forward(*N, *b, err, s, nullptr, 0, nullptr));
     FVV_TRY(fvv::backward(*N, *b, err, s));
     if (lr > 0.0f) FVV_TRY(fvv::adam(*N, lr, s));
@@ -900,6 +947,7 @@ fvv_status fvv_refine_load(fvv_ctx* c, const char* path)
     RefineNet* N = fvv::net_of(c);
     if (fvv::flat_count(*N) != cnt) return fail(FVV_ERR_INVALID_ARG, "checkpoint size mismatch");
     std::lock_guard<std::recursive_mutex> g(c->mu);
+    if (fvv::serve_refining(c)) return fail(FVV_ERR_BUSY, "the serving loop is running the refinement network");
     FVV_TRY(fvv::set_flat(*N, fvv::Buf::Param, buf.data(), c->own));
     FVV_TRY(fvv::set_flat(*N, fvv::Buf::M, buf.data() + cnt, c->own));
     FVV_TRY(fvv::set_flat(*N, fvv::Buf::V, buf.data() + 2 * cnt, c->own));
@@ -919,6 +967,7 @@ fvv_status fvv_synthesize_refined(fvv_ctx* c, const fvv_view* view, uint8_t* out
     if (out_pitch < size_t(W) * 3) return fail(FVV_ERR_INVALID_ARG, "out_pitch < 3 * width");
     cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : c->own;
     std::lock_guard<std::recursive_mutex> g(c->mu);
+    if (fvv::serve_refining(c)) return fail(FVV_ERR_BUSY, "the serving loop is running the refinement network");
     if (N->sH != H || N->sW != W) {
         FVV_CUDA(cudaDeviceSynchronize());
         fvv::free_list(c, N->syn);
@@ -951,11 +1000,11 @@ fvv_status fvv_synthesize_refined(fvv_ctx* c, const fvv_view* view, uint8_t* out
     FVV_TRY(fvv::device_flag(&err));
     const bool dev_out = fvv::mem_kind(out_rgb) == fvv::MemKind::Device;
     if (N->precision == FVV_PREC_E4M3) {
-        FVV_TRY(fvv::ensure_acts8(c, *N, 1, H, W));
+        FVV_TRY(fvv::ensure_acts8(c, *N, size_t(H) * W));
         FVV_TRY(fvv::forward_e4m3(*N, b, err, s, dev_out ? out_rgb : N->syn_out,
                                   dev_out ? out_pitch : size_t(W) * 3, nullptr));
     } else {
-        FVV_TRY(fvv::ensure_acts(c, *N, 1, H, W));
+        FVV_TRY(fvv::ensure_acts(c, *N, size_t(H) * W));
         FVV_TRY(fvv::forward(*N, b, err, s, dev_out ? out_rgb : N->syn_out, dev_out ? out_pitch : size_t(W) * 3,
                              nullptr));
     }

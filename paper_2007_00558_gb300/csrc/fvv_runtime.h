@@ -174,6 +174,18 @@ fvv_status upload_frame(fvv_ctx* c, int cam, const uint8_t* rgb, size_t rgb_pitc
 cudaError_t launch_yuv_decode(const YuvDepth& f, int width, int height, uint16_t* out, size_t out_pitch,
                               cudaStream_t s);
 void codec_destroy(fvv_ctx* c);
+// The refinement network for the serving loop: whether it is initialised, and
+// its forward pass on `s` without waiting (device batch; out_rgb is
+// [n][h][w][3] uint8).  A bounded-wait timeout leaves the device flag raised
+// for the next synchronous refinement call to report.
+bool refine_ready(fvv_ctx* c);
+fvv_status refine_forward_async(fvv_ctx* c, const fvv_refine_batch& b, uint8_t* out_rgb, cudaStream_t s);
+// Grow the network's activations (current precision) to `pixels` per batch.
+fvv_status refine_reserve(fvv_ctx* c, size_t pixels);
+// The device int the network's kernels raise when a bounded wait runs out.
+fvv_status refine_error_flag(int** flag);
+// True while a serving loop with refinement runs (the network is in use).
+bool serve_refining(fvv_ctx* c);
 void dev_free(fvv_ctx* c, void* p, size_t bytes);
 
 // Launch through `fn` (returns cudaError_t), counting it and, when profiling

@@ -13,6 +13,14 @@
 // the newest complete frame tick at the moment it is formed.  A host callback
 // on the lane's stream stamps each request's completion; latency is
 // submission to completion of its output write.
+//
+// With refinement on, a lane renders its batch (all requests of one size)
+// into its own device buffers of network inputs (colour, depth, hole mask,
+// top-3 weights); the network then runs on one refinement stream shared by
+// the lanes, ordered after the plain batch by an event, writes the refined
+// colour into the lane and copies each request's view out.  The plain pass
+// of one lane overlaps the network pass of another.  The network's
+// activations are sized once, at start, for the largest batch a lane holds.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -60,6 +68,14 @@ struct ServeLane {
     BatchScratch S;
     bool busy = false;
     std::vector<uint64_t> tickets;
+    // refinement: network inputs and refined colour for `px` pixels, one
+    // allocation of kRefineBytesPerPixel * px bytes
+    uint8_t* feat = nullptr;
+    size_t px = 0;
+    float *depth = nullptr, *top3 = nullptr;
+    uint8_t *rgb = nullptr, *hole = nullptr, *refined = nullptr;
+    cudaEvent_t plain_done = nullptr;
+    int* flag_host = nullptr;             // pinned copy of the network's error flag
 };
 
 struct ServeState {
@@ -72,6 +88,8 @@ struct ServeState {
     std::unordered_map<uint64_t, Rec> recs;
     std::vector<std::unique_ptr<ServeLane>> lanes;
     size_t lane_keys = 0, lane_stage = 0;
+    cudaStream_t refine_stream = nullptr;
+    bool reset_flag = false;              // a batch saw the network's error flag raised
     bool stopping = false;
     uint64_t next_ticket = 1;
     uint64_t submitted = 0, completed = 0, failed = 0, batches = 0, batch_views = 0;
@@ -82,6 +100,10 @@ struct ServeState {
 
 namespace {
 
+// network inputs (depth 4 + top-3 weights 12 + colour 3 + hole 1) and the
+// refined colour (3), bytes per pixel of a lane
+constexpr size_t kRefineBytesPerPixel = 23;
+
 void CUDART_CB lane_done(void* p)
 {
     // runs on a CUDA callback thread: no CUDA calls here
@@ -90,9 +112,19 @@ void CUDART_CB lane_done(void* p)
     const double t = now_s();
     {
         std::lock_guard<std::mutex> lk(st->mu);
+        const bool timed_out = L->flag_host && *L->flag_host != 0;
+        if (timed_out) {
+            st->reset_flag = true;
+            st->error = "a bounded wait of the refinement network ran out";
+        }
         for (uint64_t tk : L->tickets) {
             auto it = st->recs.find(tk);
             if (it == st->recs.end()) continue;
+            if (timed_out) {
+                it->second.state = ReqState::Failed;
+                ++st->failed;
+                continue;
+            }
             it->second.state = ReqState::Done;
             it->second.t_done = t;
             st->lat_ms.push_back(1e3 * (t - it->second.t_submit));
@@ -105,6 +137,46 @@ void CUDART_CB lane_done(void* p)
     st->cv.notify_all();
 }
 
+// One refined batch of same-size views on lane L: plain steps a-e into the
+// lane's network inputs on the lane's stream, then, on the refinement
+// stream, the network into the lane's refined colour, each request's copy
+// out and a copy of the network's error flag.  The caller holds c->mu.
+fvv_status run_refined(fvv_ctx* c, ServeState* st, ServeLane* L, const std::vector<fvv_view>& views,
+                       const std::vector<Req>& reqs, std::vector<fvv_aux>& aux, std::vector<uint8_t*>& outs,
+                       std::vector<size_t>& pitches)
+{
+    const int n = int(views.size()), W = views[0].width, H = views[0].height;
+    const size_t np = size_t(W) * H;
+    aux.assign(n, fvv_aux{});
+    for (int i = 0; i < n; ++i) {
+        outs[i] = L->rgb + size_t(i) * np * 3;
+        pitches[i] = size_t(W) * 3;
+        aux[i].depth = L->depth + size_t(i) * np;
+        aux[i].hole = L->hole + size_t(i) * np;
+        aux[i].top3 = L->top3 + size_t(i) * np * 3;
+    }
+    FVV_TRY(run_batch(c, L->S, n, views.data(), nullptr, outs.data(), pitches.data(), aux.data(), L->stream,
+                      false));
+    FVV_CUDA(cudaEventRecord(L->plain_done, L->stream));
+    FVV_CUDA(cudaStreamWaitEvent(st->refine_stream, L->plain_done, 0));
+    fvv_refine_batch b{};
+    b.n = n;
+    b.height = H;
+    b.width = W;
+    b.rgb = L->rgb;
+    b.depth = L->depth;
+    b.hole = L->hole;
+    b.top3 = L->top3;
+    FVV_TRY(refine_forward_async(c, b, L->refined, st->refine_stream));
+    for (int i = 0; i < n; ++i)
+        FVV_CUDA(cudaMemcpy2DAsync(reqs[i].out, reqs[i].pitch, L->refined + size_t(i) * np * 3, size_t(W) * 3,
+                                   size_t(W) * 3, size_t(H), cudaMemcpyDefault, st->refine_stream));
+    int* flag = nullptr;
+    FVV_TRY(refine_error_flag(&flag));
+    FVV_CUDA(cudaMemcpyAsync(L->flag_host, flag, sizeof(int), cudaMemcpyDeviceToHost, st->refine_stream));
+    return FVV_OK;
+}
+
 void scheduler(ServeState* st)
 {
     fvv_ctx* c = st->ctx;
@@ -112,6 +184,8 @@ void scheduler(ServeState* st)
     std::vector<fvv_view> views;
     std::vector<uint8_t*> outs;
     std::vector<size_t> pitches;
+    std::vector<Req> reqs;
+    std::vector<fvv_aux> aux;
     std::unique_lock<std::mutex> lk(st->mu);
     for (;;) {
         auto free_lane = [&]() -> ServeLane* {
@@ -129,26 +203,61 @@ void scheduler(ServeState* st)
                    (!st->queue.empty() && free_lane() != nullptr);
         });
         if (st->stopping && st->queue.empty() && idle()) break;
+        if (st->reset_flag) {
+            // a network wait ran out: clear the flag before the next batch
+            st->reset_flag = false;
+            lk.unlock();
+            int* flag = nullptr;
+            {
+                std::lock_guard<std::recursive_mutex> g(c->mu);
+                if (refine_error_flag(&flag) == FVV_OK)
+                    cudaMemsetAsync(flag, 0, sizeof(int), st->refine_stream);
+            }
+            lk.lock();
+        }
         ServeLane* L;
         while (!st->queue.empty() && (L = free_lane()) != nullptr) {
-            // pack the oldest requests that fit this lane's scratch
             views.clear();
             outs.clear();
             pitches.clear();
+            reqs.clear();
             L->tickets.clear();
-            size_t keys = 0, stage = 0;
-            while (!st->queue.empty() && int(views.size()) < st->cfg.max_batch) {
-                const Req& r = st->queue.front();
-                const size_t k = view_keys(r.view), b = view_stage_bytes(r.view, r.out, nullptr);
-                if (keys + k > L->S.keys_cap || stage + b > L->S.out_stage_cap) break;
-                keys += k;
-                stage += b;
+            auto take = [&](const Req& r) {
                 views.push_back(r.view);
                 outs.push_back(r.out);
                 pitches.push_back(r.pitch);
+                reqs.push_back(r);
                 L->tickets.push_back(r.ticket);
                 st->recs[r.ticket].state = ReqState::Running;
-                st->queue.pop_front();
+            };
+            if (st->cfg.refine) {
+                // the oldest request and later ones of its size, up to the
+                // lane's pixels (one network batch is one size)
+                const int W = st->queue.front().view.width, H = st->queue.front().view.height;
+                const size_t np = size_t(W) * H;
+                size_t px = 0;
+                for (auto it = st->queue.begin();
+                     it != st->queue.end() && int(views.size()) < st->cfg.max_batch;) {
+                    if (it->view.width == W && it->view.height == H && px + np <= L->px) {
+                        px += np;
+                        take(*it);
+                        it = st->queue.erase(it);
+                    } else {
+                        ++it;
+                    }
+                }
+            } else {
+                // the oldest requests that fit this lane's scratch
+                size_t keys = 0, stage = 0;
+                while (!st->queue.empty() && int(views.size()) < st->cfg.max_batch) {
+                    const Req& r = st->queue.front();
+                    const size_t k = view_keys(r.view), b = view_stage_bytes(r.view, r.out, nullptr);
+                    if (keys + k > L->S.keys_cap || stage + b > L->S.out_stage_cap) break;
+                    keys += k;
+                    stage += b;
+                    take(r);
+                    st->queue.pop_front();
+                }
             }
             L->busy = true;
             ++st->batches;
@@ -158,10 +267,16 @@ void scheduler(ServeState* st)
             std::string err;
             {
                 std::lock_guard<std::recursive_mutex> g(c->mu);
-                rc = run_batch(c, L->S, int(views.size()), views.data(), nullptr, outs.data(),
-                               pitches.data(), nullptr, L->stream, false);
+                cudaStream_t done_on = L->stream;
+                if (st->cfg.refine) {
+                    rc = run_refined(c, st, L, views, reqs, aux, outs, pitches);
+                    done_on = st->refine_stream;
+                } else {
+                    rc = run_batch(c, L->S, int(views.size()), views.data(), nullptr, outs.data(),
+                                   pitches.data(), nullptr, L->stream, false);
+                }
                 if (rc == FVV_OK) {
-                    cudaError_t e = cudaLaunchHostFunc(L->stream, lane_done, L);
+                    cudaError_t e = cudaLaunchHostFunc(done_on, lane_done, L);
                     if (e != cudaSuccess) {
                         cudaGetLastError();
                         rc = FVV_ERR_CUDA;
@@ -169,6 +284,12 @@ void scheduler(ServeState* st)
                     }
                 } else {
                     err = fvv_last_error();
+                }
+                if (rc != FVV_OK) {
+                    // work of this batch may be queued: let it drain before
+                    // the lane's buffers are reused
+                    cudaStreamSynchronize(L->stream);
+                    if (st->refine_stream) cudaStreamSynchronize(st->refine_stream);
                 }
             }
             lk.lock();
@@ -186,7 +307,40 @@ void scheduler(ServeState* st)
     }
 }
 
+// Release a lane's stream, scratch and refinement buffers (work drained).
+void lane_free(fvv_ctx* c, ServeLane& L)
+{
+    if (L.stream) cudaStreamSynchronize(L.stream);
+    scratch_free(c, L.S);
+    dev_free(c, L.feat, L.px * kRefineBytesPerPixel);
+    L.feat = nullptr;
+    if (L.flag_host) cudaFreeHost(L.flag_host);
+    L.flag_host = nullptr;
+    if (L.plain_done) cudaEventDestroy(L.plain_done);
+    L.plain_done = nullptr;
+    if (L.stream) cudaStreamDestroy(L.stream);
+    L.stream = nullptr;
+}
+
+// The lane's refinement buffers for `px` pixels (a multiple of 64).
+fvv_status lane_refine_alloc(fvv_ctx* c, ServeLane& L, size_t px)
+{
+    FVV_TRY(dev_alloc(c, reinterpret_cast<void**>(&L.feat), px * kRefineBytesPerPixel));
+    L.px = px;
+    L.depth = reinterpret_cast<float*>(L.feat);
+    L.top3 = reinterpret_cast<float*>(L.feat + px * 4);
+    L.rgb = L.feat + px * 16;
+    L.refined = L.feat + px * 19;
+    L.hole = L.feat + px * 22;
+    FVV_CUDA(cudaHostAlloc(reinterpret_cast<void**>(&L.flag_host), sizeof(int), cudaHostAllocDefault));
+    *L.flag_host = 0;
+    FVV_CUDA(cudaEventCreateWithFlags(&L.plain_done, cudaEventDisableTiming));
+    return FVV_OK;
+}
+
 }  // namespace
+
+bool serve_refining(fvv_ctx* c) { return c && c->serve && c->serve->cfg.refine; }
 
 void serve_shutdown(fvv_ctx* c)
 {
@@ -200,11 +354,9 @@ void serve_shutdown(fvv_ctx* c)
     if (st->thread.joinable()) st->thread.join();
     {
         std::lock_guard<std::recursive_mutex> g(c->mu);
-        for (auto& L : st->lanes) {
-            if (L->stream) cudaStreamSynchronize(L->stream);
-            scratch_free(c, L->S);
-            if (L->stream) cudaStreamDestroy(L->stream);
-        }
+        if (st->refine_stream) cudaStreamSynchronize(st->refine_stream);
+        for (auto& L : st->lanes) lane_free(c, *L);
+        if (st->refine_stream) cudaStreamDestroy(st->refine_stream);
     }
     c->serve = nullptr;
     delete st;
@@ -225,6 +377,7 @@ fvv_status fvv_serve_default_cfg(fvv_serve_cfg* cfg)
     cfg->max_batch = 16;
     cfg->max_pending = 4096;
     cfg->memory_budget = uint64_t(768) << 20;
+    cfg->refine = 0;
     return FVV_OK;
 }
 
@@ -237,21 +390,44 @@ fvv_status fvv_serve_start(fvv_ctx* c, const fvv_serve_cfg* cfg_in)
         return fail(FVV_ERR_INVALID_ARG, "lanes must be in [1, 16]");
     if (cfg.max_batch < 1 || cfg.max_batch > 4096 || cfg.max_pending < 1)
         return fail(FVV_ERR_INVALID_ARG, "max_batch must be in [1, 4096], max_pending >= 1");
+    if (cfg.refine != 0 && cfg.refine != 1) return fail(FVV_ERR_INVALID_ARG, "refine must be 0 or 1");
     if (c->serve) return fail(FVV_ERR_STATE, "serving loop already running");
     std::lock_guard<std::recursive_mutex> g(c->mu);
+    if (cfg.refine && !fvv::refine_ready(c))
+        return fail(FVV_ERR_STATE, "refine = 1 needs fvv_refine_init first");
     FVV_CUDA(cudaSetDevice(c->device));
     auto st = std::make_unique<ServeState>();
     st->ctx = c;
     st->cfg = cfg;
-    // per lane: 8 bytes of keys and 3 bytes of host-output staging per pixel
     const size_t per_lane = size_t(cfg.memory_budget) / size_t(cfg.lanes);
     const size_t pb = fvv::align_up(size_t(cfg.max_batch) * sizeof(fvv::ViewDesc), 256) +
                       size_t(cfg.max_batch) * c->n_cams * sizeof(fvv::CamGeom);
     if (per_lane < 2 * pb + (size_t(1) << 20))
         return fail(FVV_ERR_BUDGET, "memory_budget too small for the lanes");
     const size_t room = per_lane - 2 * pb;
-    st->lane_keys = fvv::align_up(room / 11, 16) - 16;
-    st->lane_stage = fvv::align_up((room - st->lane_keys * 8) & ~size_t(255), 256) - 256;
+    size_t lane_px = 0;
+    if (cfg.refine) {
+        // per lane and pixel: 8 bytes of keys and the refinement buffers
+        lane_px = room / (8 + fvv::kRefineBytesPerPixel) / 64 * 64;
+        st->lane_keys = lane_px;
+        st->lane_stage = 0;
+    } else {
+        // per lane: 8 bytes of keys and 3 bytes of host-output staging per pixel
+        st->lane_keys = fvv::align_up(room / 11, 16) - 16;
+        st->lane_stage = fvv::align_up((room - st->lane_keys * 8) & ~size_t(255), 256) - 256;
+    }
+    auto unwind = [&](fvv_status rc, const std::string& msg) {
+        if (st->refine_stream) cudaStreamSynchronize(st->refine_stream);
+        for (auto& l : st->lanes) fvv::lane_free(c, *l);
+        if (st->refine_stream) cudaStreamDestroy(st->refine_stream);
+        return fail(rc, msg);
+    };
+    if (cfg.refine) {
+        cudaError_t e = cudaStreamCreateWithFlags(&st->refine_stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return unwind(FVV_ERR_CUDA, std::string("cudaStreamCreate: ") + cudaGetErrorString(e));
+        // the network's activations for the largest batch a lane holds
+        if (fvv::refine_reserve(c, lane_px) != FVV_OK) return unwind(FVV_ERR_BUDGET, fvv_last_error());
+    }
     for (int i = 0; i < cfg.lanes; ++i) {
         auto L = std::make_unique<fvv::ServeLane>();
         L->owner = st.get();
@@ -260,17 +436,12 @@ fvv_status fvv_serve_start(fvv_ctx* c, const fvv_serve_cfg* cfg_in)
         fvv_status rc = e == cudaSuccess ? FVV_OK : FVV_ERR_CUDA;
         if (rc == FVV_OK)
             rc = fvv::scratch_alloc(c, L->S, st->lane_keys, st->lane_stage, cfg.max_batch, 2);
+        if (rc == FVV_OK && cfg.refine) rc = fvv::lane_refine_alloc(c, *L, lane_px);
         L->S.reader = 1 + i;
         st->lanes.push_back(std::move(L));
-        if (rc != FVV_OK) {
-            std::string msg = e != cudaSuccess ? std::string("cudaStreamCreate: ") + cudaGetErrorString(e)
-                                               : std::string(fvv_last_error());
-            for (auto& l : st->lanes) {
-                fvv::scratch_free(c, l->S);
-                if (l->stream) cudaStreamDestroy(l->stream);
-            }
-            return fail(rc, msg);
-        }
+        if (rc != FVV_OK)
+            return unwind(rc, e != cudaSuccess ? std::string("cudaStreamCreate: ") + cudaGetErrorString(e)
+                                               : std::string(fvv_last_error()));
     }
     ServeState* raw = st.release();
     c->serve = raw;
@@ -289,9 +460,15 @@ fvv_status fvv_serve_submit(fvv_ctx* c, uint32_t viewer, const fvv_view* view, u
     if (fvv::resolve_smem_bytes(view->width, c->n_cams) > c->smem_optin)
         return fail(FVV_ERR_INVALID_ARG, "view: width too large");
     if (pitch < size_t(view->width) * 3) return fail(FVV_ERR_INVALID_ARG, "pitch < 3 * width");
-    if (fvv::view_keys(*view) > st->lane_keys ||
-        fvv::view_stage_bytes(*view, out, nullptr) > st->lane_stage)
+    if (st->cfg.refine) {
+        if (view->width % 4 || view->height % 4)
+            return fail(FVV_ERR_INVALID_ARG, "refined views need width and height multiples of 4");
+        if (size_t(view->width) * view->height > st->lanes[0]->px)
+            return fail(FVV_ERR_BUDGET, "view does not fit one lane's share of the serving memory budget");
+    } else if (fvv::view_keys(*view) > st->lane_keys ||
+               fvv::view_stage_bytes(*view, out, nullptr) > st->lane_stage) {
         return fail(FVV_ERR_BUDGET, "view does not fit one lane's share of the serving memory budget");
+    }
     {
         std::lock_guard<std::recursive_mutex> g(c->mu);
         if (!c->have_latest) return fail(FVV_ERR_NOT_READY, "no complete frame tick uploaded yet");

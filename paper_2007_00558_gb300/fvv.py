@@ -69,7 +69,7 @@ class fvv_aux(C.Structure):
 
 class fvv_serve_cfg(C.Structure):
     _fields_ = [("lanes", C.c_int32), ("max_batch", C.c_int32), ("max_pending", C.c_int32),
-                ("memory_budget", C.c_uint64)]
+                ("memory_budget", C.c_uint64), ("refine", C.c_int32)]
 
 
 class fvv_serve_report(C.Structure):

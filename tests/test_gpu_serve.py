@@ -174,3 +174,68 @@ def test_serve_while_frames_update(rig_small):
             assert np.array_equal(a, refs[0]) or np.array_equal(a, refs[1])
     finally:
         F.fvv_destroy(ctx)
+
+
+@pytest.mark.parametrize("precision", ["bf16", "e4m3"])
+def test_serve_refined_equals_alone(rig_small, precision):
+    """Refinement on: requests of two sizes are served in same-size batches
+    through the network; every result equals fvv_synthesize_refined of the
+    view alone, byte for byte (the same kernels on the same inputs; no
+    reduction in the forward pass depends on the batch)."""
+    import torch
+    F = lib()
+    wl = rig_small
+    rng = np.random.default_rng(11)
+    sizes = [(320, 180, 125.0), (640, 360, 250.0)]
+    reqs = []
+    for i in range(20):
+        W, H, f = sizes[int(rng.integers(0, 2))]
+        reqs.append(_view(wl["views"][int(rng.integers(0, 300))], W, H, f))
+    ctx = _ctx_with_frames(F, wl)
+    try:
+        with pytest.raises(F.FvvError) as e:                     # no network yet
+            F.fvv_serve_start(ctx, F.fvv_serve_default_cfg(refine=1))
+        assert e.value.code == F.FVV_ERR_STATE
+        F.fvv_refine_init(ctx, None)
+        if precision == "e4m3":
+            F.fvv_refine_quantize(ctx, None, np.full(10, 0.02, np.float32))
+        F.fvv_serve_start(ctx, F.fvv_serve_default_cfg(lanes=2, max_batch=4, memory_budget=128 << 20,
+                                                        refine=1))
+        probe = torch.zeros((180, 960), dtype=torch.uint8, device="cuda")
+        with pytest.raises(F.FvvError) as e:                     # the network is in use
+            F.fvv_synthesize_refined(ctx, reqs[0], probe, 960)
+        assert e.value.code == F.FVV_ERR_BUSY
+        with pytest.raises(F.FvvError) as e:
+            F.fvv_refine_set_precision(ctx, F.FVV_PREC_BF16)
+        assert e.value.code == F.FVV_ERR_BUSY
+        with pytest.raises(F.FvvError) as e:                     # not a multiple of 4
+            F.fvv_serve_submit(ctx, 0, _view(wl["views"][3], 322, 180, 125.0), probe, 966)
+        assert e.value.code == F.FVV_ERR_INVALID_ARG
+        outs = []
+        for i, v in enumerate(reqs):
+            if i % 3 == 0:
+                outs.append(np.zeros((v.height, v.width * 3), np.uint8))
+            else:
+                outs.append(torch.zeros((v.height, v.width * 3), dtype=torch.uint8, device="cuda"))
+        torch.cuda.synchronize()
+        tickets = [F.fvv_serve_submit(ctx, i % 4, F.camera(v), o, v.width * 3)
+                   for i, (v, o) in enumerate(zip(reqs, outs))]
+        for t in tickets:
+            F.fvv_serve_poll(ctx, t, 10_000_000)
+        st = F.fvv_serve_stats(ctx)
+        assert st["completed"] == 20 and st["failed"] == 0
+        assert st["batches"] < 20
+        F.fvv_serve_stop(ctx)
+        changed = 0
+        for v, o in zip(reqs, outs):
+            ref = torch.zeros((v.height, v.width * 3), dtype=torch.uint8, device="cuda")
+            F.fvv_synthesize_refined(ctx, v, ref, v.width * 3)
+            plain = torch.zeros_like(ref)
+            F.fvv_synthesize(ctx, v, plain, v.width * 3)
+            torch.cuda.synchronize()
+            a = o.cpu().numpy() if hasattr(o, "cpu") else o
+            assert np.array_equal(a, ref.cpu().numpy())
+            changed += int(not np.array_equal(a, plain.cpu().numpy()))
+        assert changed == len(reqs)                              # the network did run
+    finally:
+        F.fvv_destroy(ctx)
