@@ -28,6 +28,7 @@ _lib = None
 
 KEY_EMPTY = np.uint64(0xFFFFFFFFFFFFFFFF)
 SRC_BITS = 26
+DEPTH_BG = 65535      # depth code signalling a background pixel (Sec. V-B, 12-bit code 0)
 
 CFLAGS = ["-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
           "-shared", "-Wall", "-Wextra"]
@@ -233,6 +234,65 @@ def synthesize(cams: Sequence, rgb, depth, view, look_at, opts: Optional[Options
     if rc != 0:
         raise ValueError("oracle_synthesize: invalid arguments")
     return {"rgb": out, "depth": dep, "hole": hole, "top3": top3, "keys_raw": kr, "keys": kf}
+
+
+def synthesize_layered(cams: Sequence, rgb, depth, bg, view, look_at, opts: Optional[Options] = None,
+                       depth_unit_m: float = 0.001, **kw) -> dict:
+    """Layered FG/BG synthesis of one virtual view (Sec. VI, the per-camera
+    FG and BG layers and their mixing and stacking), composed from steps a-e.
+
+    ``depth[k]`` holds camera k's live codes, ``DEPTH_BG`` where the pixel
+    is background; ``bg[k]`` its static background model (depth codes, 0 =
+    none; ``bg`` or ``bg[k]`` may be None).  Readings taken here:
+
+    * FG layer: every camera's live codes.  A BG-signalled pixel is no FG
+      point because ``d_hi`` <= 65534 keeps ``DEPTH_BG`` out of the accepted
+      codes; a pixel without depth (0) is in neither layer.
+    * BG layer: camera k's model depth where camera k signals BG, 0 (no
+      point) elsewhere -- where camera k sees a foreground object it holds no
+      background colour.  The colour is always the live frame's.
+    * Each layer goes through steps a-d on its own (z-buffer, crack filter,
+      blend whose visibility test reads that layer's depth maps), with the
+      weights of the one composition of the view.
+    * Stacking: the FG layer where its filtered key is present, else the BG
+      layer, else a hole; step e runs on the stacked image.
+
+    Returns dict(rgb, depth, hole, top3, keys (key of the layer shown),
+    keys_raw (the FG layer before the filter), keys_raw_bg, layer (0 FG,
+    1 BG, -1 hole))."""
+    n = len(cams)
+    if opts is None:
+        opts = options(**kw)
+    if opts.d_hi >= DEPTH_BG:
+        raise ValueError("layered synthesis needs d_hi <= 65534")
+    Hv, Wv = int(view.height), int(view.width)
+    M, N, w = compose(cams, view, look_at, depth_unit_m, opts.n_ref)
+    live = [np.ascontiguousarray(depth[k], dtype=np.uint16) for k in range(n)]
+    model = []
+    for k in range(n):
+        m = None if bg is None else bg[k]
+        m = np.zeros_like(live[k]) if m is None else np.asarray(m, dtype=np.uint16)
+        model.append(np.where(live[k] == DEPTH_BG, m, 0).astype(np.uint16))
+    layers = []
+    for dmaps in (live, model):
+        raw = warp_splat(cams, dmaps, M, w, Wv, Hv, opts, N)
+        filt = crack_filter(raw, opts.tau_crack) if opts.crack_filter else raw.copy()
+        layers.append((raw, filt, fetch_blend(cams, rgb, dmaps, M, N, w, filt, opts)))
+    (rf, kf, bf), (rb, kb, bb) = layers
+    on_fg = kf != KEY_EMPTY
+    on_bg = ~on_fg & (kb != KEY_EMPTY)
+    pick = lambda a, b, fill: np.where(on_fg[..., None] if a.ndim == 3 else on_fg, a,
+                                       np.where(on_bg[..., None] if b.ndim == 3 else on_bg, b, fill))
+    out = pick(bf["rgb"], bb["rgb"], 0).astype(np.uint8)
+    dep = pick(bf["depth"], bb["depth"], 0.0).astype(np.float32)
+    top3 = pick(bf["top3"], bb["top3"], 0.0).astype(np.float32)
+    hole = (~on_fg & ~on_bg).astype(np.uint8)
+    if opts.hole_fill:
+        out, dep = hole_fill(hole, out, dep)
+    keys = np.where(on_fg, kf, kb)
+    layer = np.where(on_fg, 0, np.where(on_bg, 1, -1)).astype(np.int8)
+    return {"rgb": out, "depth": dep, "hole": hole, "top3": top3, "keys": keys, "keys_raw": rf,
+            "keys_raw_bg": rb, "layer": layer}
 
 
 def key_fields(keys: np.ndarray):

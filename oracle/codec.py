@@ -19,14 +19,18 @@ the text): Eq. (2) rounds half up, Y = floor(value + 0.5); the interleave
 puts bit i of the first pixel's MSBs at bit 2i and bit i of the second
 pixel's at bit 2i + 1; the decoder inverts Eq. (2) as
 z = 1 / (1/z_far + (Y - 2) (1/z_near - 1/z_far) / 4093), in that order, and
-returns depth codes floor(z / unit + 0.5) clamped to [1, 65535]; codes 0 and
-1 decode to depth code 0 (no depth).  Depth code 0 (no depth) encodes to 1.
+returns depth codes floor(z / unit + 0.5) clamped to [1, 65534]; code 1
+decodes to depth code 0 (no depth) and code 0 to 65535, the 16-bit
+background signal (a BG pixel has no transmitted depth; the view-synthesis
+side takes its depth from the static background model).  Depth code 0 (no
+depth) encodes to 1 and the background signal 65535 to 0.
 """
 from __future__ import annotations
 
 import numpy as np
 
 Y_LEVELS = 2 ** 12 - 3          # 4093: steps between z_far (Y = 2) and z_near (Y = 4095)
+DEPTH_BG = 65535                # 16-bit background signal (12-bit code 0)
 
 
 def correct(z, alpha, beta):
@@ -60,16 +64,20 @@ def encode_table(z_near, z_far, alpha, beta, unit_m):
     d = np.arange(65536, dtype=np.float64)
     y = quantize(correct(d * unit_m, alpha, beta), z_near, z_far)
     y[0] = 1
+    y[DEPTH_BG] = 0
     return y
 
 
 def decode_table(z_near, z_far, unit_m):
-    """uint16 depth code of every 12-bit code (0 for the reserved codes 0, 1)."""
+    """uint16 depth code of every 12-bit code (0 for code 1, the background
+    signal for code 0)."""
     y = np.arange(4096)
     z = dequantize(y, z_near, z_far)
     with np.errstate(invalid="ignore"):
-        d = np.clip(np.floor(z / unit_m + 0.5), 1, 65535)
-    return np.where(y >= 2, d, 0).astype(np.int64)
+        d = np.clip(np.floor(z / unit_m + 0.5), 1, DEPTH_BG - 1)
+    d = np.where(y >= 2, d, 0)
+    d[0] = DEPTH_BG
+    return d.astype(np.int64)
 
 
 def _interleave(a, b):
@@ -118,5 +126,5 @@ def encode(depth, z_near, z_far, alpha, beta, unit_m):
 
 
 def decode(Y, U, V, z_near, z_far, unit_m):
-    """YUV420 planes -> uint16 depth codes (0 = no depth)."""
+    """YUV420 planes -> uint16 depth codes (0 = no depth, 65535 = background)."""
     return decode_table(z_near, z_far, unit_m)[unpack_yuv420(Y, U, V)].astype(np.uint16)

@@ -52,7 +52,7 @@ void oracle_default_options(or_options* o)
     o->tau_vis = 0.03f;
     o->z_min = 1.0f;
     o->d_lo = 1;
-    o->d_hi = 65535;
+    o->d_hi = 65534;   /* 65535 signals a background pixel (Sec. V-B, code 0) */
 }
 
 static float key_depth(uint64_t key)

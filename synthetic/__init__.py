@@ -11,4 +11,5 @@ from .scenes import (  # noqa: F401
     rig_parallel, rig_arc, arc_view, trajectory_arc,
     scene_spheres_plane, scene_random_objects, scene_fronto_plane,
     add_depth_noise, quantise, workload,
+    DEPTH_BG, layered_frames, scene_layered,
 )

@@ -6,7 +6,9 @@ Conventions (shared by every consumer of these frames):
   * pixel (u, v) has its centre at integer (u, v); the ray through it is
     ``R.T @ ((u - cx) / fx, (v - cy) / fy, 1)``, so the ray parameter of a hit
     is the camera-space depth z;
-  * depth frames are uint16 millimetres of camera-space z, 0 = no depth.
+  * depth frames are uint16 millimetres of camera-space z, 0 = no depth;
+    in layered frames 65535 (``DEPTH_BG``) marks a background pixel, whose
+    depth is not sent (a separate static background model holds it).
 
 The rig shapes follow the paper's test set-up (Sec. IX: nine cameras on an
 arc; swing / still trajectories); the scenes stand in for its captured
@@ -21,6 +23,7 @@ from typing import List, Optional, Sequence
 import numpy as np
 
 _EPS_T = 1e-6
+DEPTH_BG = 65535
 
 
 @dataclass
@@ -328,6 +331,73 @@ def frames_for(scene: Scene, cams: Sequence[Camera], noise_seed: Optional[int] =
     return rgb, dep
 
 
+def layered_frames(bg_scene: Scene, actors: Sequence[Sphere], cams: Sequence[Camera],
+                   noise_seed: Optional[int] = None, sigma: float = 0.01, dropout: float = 0.05):
+    """Frames of a static background scene with moving foreground actors.
+
+    The live frames render background + actors: RGB8 colour everywhere;
+    depth (noise model of :func:`add_depth_noise` with ``noise_seed``) where
+    an actor is hit, ``DEPTH_BG`` where the background is hit, 0 where
+    nothing is.  The background model is the exact, noise-free depth of
+    ``bg_scene`` alone (the off-line model of the static set).  The actors
+    must be the scene's only spheres.  Returns rgb (K, H, W, 3) u8, live
+    depth (K, H, W) u16, model depth (K, H, W) u16 and the actor mask
+    (K, H, W) bool.
+    """
+    assert not bg_scene.spheres
+    full = Scene(spheres=list(actors), boxes=bg_scene.boxes, planes=bg_scene.planes,
+                 walls=bg_scene.walls, light_to=bg_scene.light_to, ambient=bg_scene.ambient)
+    first = len(full.walls) + len(full.planes)           # render() numbers walls, planes, spheres, boxes
+    H, W = cams[0].height, cams[0].width
+    K = len(cams)
+    rgb = np.zeros((K, H, W, 3), np.uint8)
+    live = np.zeros((K, H, W), np.uint16)
+    model = np.zeros((K, H, W), np.uint16)
+    fg = np.zeros((K, H, W), bool)
+    rng = np.random.default_rng(noise_seed) if noise_seed is not None else None
+    for k, c in enumerate(cams):
+        assert (c.height, c.width) == (H, W)
+        r = render(full, c)
+        rgb[k], d = quantise(r)
+        if rng is not None:
+            d = add_depth_noise(d, r["z"] * 1000.0, rng, sigma, dropout)
+        fg[k] = (r["obj"] >= first) & (r["obj"] < first + len(actors))
+        hit_bg = (r["obj"] >= 0) & ~fg[k]
+        live[k] = np.where(fg[k], d, np.where(hit_bg, DEPTH_BG, 0))
+        _, model[k] = quantise(render(bg_scene, c), max_mm=DEPTH_BG - 1)
+    return rgb, live, model, fg
+
+
+def scene_layered(seed: int, n_actors: int = 8, n_props: int = 6, half: float = 0.6,
+                  floor_y: float = 0.5, wall_radius: float = 4.0):
+    """A static set (checker floor, cylindrical wall, ``n_props`` yawed boxes
+    with edges 0.2-0.6 m standing on the floor 2.5-3.5 m from the centre,
+    within 60 deg of +z, i.e. behind the centre for cameras on the -z side)
+    and ``n_actors`` spheres (r 0.1-0.3 m) inside a cube of side ``2*half``
+    around the origin, so that from the rig the set is always behind the
+    actors (stacking the FG layer over the BG layer is then exact).
+    Returns (set, actors)."""
+    rng = np.random.default_rng(seed)
+    boxes = []
+    for _ in range(n_props):
+        e = rng.uniform(0.2, 0.6, 3)
+        rr, ph = rng.uniform(2.5, 3.5), math.radians(rng.uniform(-60.0, 60.0))
+        ctr = np.array([rr * math.sin(ph), floor_y - e[1] / 2, rr * math.cos(ph)])
+        boxes.append(Box(ctr, e / 2, rng.uniform(0, math.pi), rng.uniform(0, 255, 3)))
+    actors = []
+    for _ in range(n_actors):
+        r = rng.uniform(0.1, 0.3)
+        ctr = np.array([rng.uniform(-half, half), rng.uniform(-half, floor_y - r),
+                        rng.uniform(-half, half)])
+        actors.append(Sphere(ctr, r, rng.uniform(0, 255, 3)))
+    floor = Plane(np.array([0.0, floor_y, 0.0]), np.array([0.0, -1.0, 0.0]),
+                  rng.uniform(60, 230, 3), rng.uniform(20, 120, 3), 0.25,
+                  u_axis=np.array([1.0, 0.0, 0.0]), v_axis=np.array([0.0, 0.0, 1.0]))
+    wall = CylinderWall(np.zeros(3), wall_radius, rng.uniform(90, 255, 3),
+                        rng.uniform(20, 140, 3), 0.3)
+    return Scene(boxes=boxes, planes=[floor], walls=[wall]), actors
+
+
 # --------------------------------------------------------------------------
 # rigs and trajectories
 # --------------------------------------------------------------------------
@@ -450,6 +520,11 @@ def workload(name: str, seed: Optional[int] = None, scale: float = 1.0) -> dict:
       views along phi(t) = 22.5 deg sin(2 pi t / 300). Seed 2.
     * ``plain_18cam_1920x1080``: 18 cameras 1920x1080 (f = 1500 px) on a 180 deg
       arc of radius 2 m, noise as above, the same swing trajectory. Seed 5.
+    * ``layered_9cam_1280x720``: the 9-camera rig and views of
+      ``plain_9cam_1280x720`` over a static set (floor, wall, 6 boxes) with 8
+      sphere actors; live depth only on the actors (noise as above), the
+      set signalled as background, and an exact background depth model.
+      Seed 3.  Adds ``bg`` (model depth) and ``fg`` (actor mask).
 
     ``scale`` < 1 shrinks every resolution and focal length (for small cases).
     Returns dict(cams, rgb, depth, views, look_at, scene, name).
@@ -463,6 +538,18 @@ def workload(name: str, seed: Optional[int] = None, scale: float = 1.0) -> dict:
         rgb, dep = frames_for(scene, cams)
         views = [view]
         look_at = np.array([0.0, 0.0, 2.0])
+    elif name == "layered_9cam_1280x720":
+        seed = 3 if seed is None else seed
+        W, H, f = int(round(1280 * scale)), int(round(720 * scale)), 1000.0 * scale
+        cams = rig_arc(9, 90.0, 1.5, W, H, f)
+        bg_scene, actors = scene_layered(seed)
+        rgb, dep, bg, fg = layered_frames(bg_scene, actors, cams, noise_seed=seed + 1000)
+        views = trajectory_arc(300, 22.5, 1.5, W, H, f)
+        scene = Scene(spheres=list(actors), boxes=bg_scene.boxes, planes=bg_scene.planes,
+                      walls=bg_scene.walls)
+        return {"name": name, "cams": cams, "rgb": rgb, "depth": dep, "views": views,
+                "look_at": np.zeros(3), "scene": scene, "bg_scene": bg_scene, "actors": actors,
+                "bg": bg, "fg": fg}
     elif name in ("plain_9cam_1280x720", "plain_18cam_1920x1080"):
         if name == "plain_9cam_1280x720":
             seed = 2 if seed is None else seed

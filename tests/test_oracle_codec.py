@@ -74,7 +74,7 @@ def test_pack_round_trip_every_code_every_position(pos):
 def test_depth_round_trip_through_the_codec():
     """encode -> decode returns every in-range depth code to within the
     depth width of half a disparity step; out-of-range and missing depth
-    decode to 0."""
+    decode to 0; the background signal survives as itself."""
     unit = 0.001
     d = np.arange(65536)
     y = K.encode_table(ZN, ZF, 0.0, 1.0, unit)
@@ -84,6 +84,23 @@ def test_depth_round_trip_through_the_codec():
     step = (1.0 / ZN - 1.0 / ZF) / 4093
     tol = 0.5 * step * z * z / unit * 1.0001 + 0.5          # half a step in 1/z, in codes, + rounding
     assert np.all(np.abs(back[inr] - d[inr]) <= tol[inr])
-    assert np.all(back[~inr] == 0) and back[0] == 0
+    sig = d == K.DEPTH_BG
+    assert np.all(back[~inr & ~sig] == 0) and back[0] == 0
+    assert back[K.DEPTH_BG] == K.DEPTH_BG
     Y, U, V = K.encode(d[:4096].reshape(64, 64), ZN, ZF, 0.0, 1.0, unit)
     assert np.array_equal(K.decode(Y, U, V, ZN, ZF, unit), back[:4096].reshape(64, 64))
+
+
+def test_background_signal_is_code_zero():
+    """Eq. (2) reserves code 0 for background pixels and code 1 for pixels
+    out of range or without depth: the 16-bit background signal encodes to
+    0 and code 0 decodes to it; no depth code decodes to the signal."""
+    enc = K.encode_table(ZN, ZF, 0.0, 1.0, 0.001)
+    dec = K.decode_table(ZN, ZF, 0.001)
+    assert enc[K.DEPTH_BG] == 0 and enc[0] == 1
+    assert np.all(enc[1:K.DEPTH_BG] >= 1)
+    assert dec[0] == K.DEPTH_BG and dec[1] == 0
+    assert np.all((dec[2:] >= 1) & (dec[2:] <= K.DEPTH_BG - 1))
+    # a near z_far that reaches the top of the 16-bit range clamps below the signal
+    dec_far = K.decode_table(0.5, 70.0, 0.001)
+    assert dec_far[2] == K.DEPTH_BG - 1
