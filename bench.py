@@ -63,6 +63,7 @@ def parse_args():
     p.add_argument("--serve-seconds", type=float, default=3.0,
                    help="length of the Poisson multi-viewer run")
     p.add_argument("--no-refine", action="store_true", help="skip the refinement-network measurement")
+    p.add_argument("--no-layered", action="store_true", help="skip the layered FG/BG measurement")
     p.add_argument("--refine-steps", type=int, default=600, help="LOO training steps before measuring")
     p.add_argument("--net-forward", type=int, default=0, metavar="REPS",
                    help="only time the refinement network: REPS forwards of a batch of 4 plain-like "
@@ -658,6 +659,57 @@ def dist_env():
             int(os.environ.get("LOCAL_RANK", 0)))
 
 
+def layered_bench(F, steps, warmup, batch, slots, stream):
+    """Layered FG/BG synthesis (Sec. VI per-camera FG and BG layers) on the
+    9-camera 1280x720 rig over a static set with actors: the main
+    measurement's schedule (each view reads its own tick of a 16-tick ring,
+    inputs > L2), views/s from CUDA events over `steps` batched calls, and
+    each kernel's time per view from the library's per-launch events."""
+    import numpy as np
+    import torch
+    import synthetic as S
+    wl = S.workload("layered_9cam_1280x720")
+    cams, views = wl["cams"], wl["views"]
+    K, H, W = len(cams), cams[0].height, cams[0].width
+    ctx = F.fvv_create(F.rig(cams, wl["look_at"]),
+                       F.fvv_default_options(frame_slots=slots, max_batch=batch, layered=1))
+    try:
+        for k in range(K):
+            F.fvv_set_bg_depth(ctx, k, np.ascontiguousarray(wl["bg"][k]), W * 2)
+        rgb_h = torch.from_numpy(np.ascontiguousarray(wl["rgb"])).pin_memory()
+        dep_h = torch.from_numpy(np.ascontiguousarray(wl["depth"]).view(np.int16)).pin_memory()
+        for t in range(slots):
+            F.fvv_upload_frames(ctx, rgb_h, H * W * 3, W * 3, dep_h, H * W * 2, W * 2, t, stream)
+        out = [torch.empty((H, W, 3), dtype=torch.uint8, device="cuda") for _ in range(batch)]
+
+        def step(i):
+            sched = view_schedule(0, i, batch, slots)
+            F.fvv_synthesize_batch(ctx, [views[v] for v, _ in sched], [t for _, t in sched], out,
+                                   [W * 3] * batch, None, stream)
+
+        for i in range(warmup):
+            step(i)
+        torch.cuda.synchronize()
+        F.fvv_profile_read(ctx, reset=True)
+        F.fvv_profile_enable(ctx, True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for i in range(steps):
+            step(warmup + i)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        stats = F.fvv_profile_read(ctx, reset=True)
+        F.fvv_profile_enable(ctx, False)
+    finally:
+        F.fvv_destroy(ctx)
+    return {"workload": "layered_9cam_1280x720", "views_per_s": steps * batch / (ms / 1e3),
+            "ms_per_step": ms / steps, "views_per_step": batch,
+            "kernel_us_per_view": {k: 1e3 * v[2] / v[1] / batch for k, v in stats.items() if v[1] > 0},
+            "actor_pixel_fraction": float(wl["fg"].mean()),
+            "l2": "inputs > L2: each view reads its own tick of %d" % slots}
+
+
 def view_schedule(rank, step, batch, slots, n_traj=300):
     """Replicas: (trajectory index, frame tick) of each view a rank renders in
     one step.  Every rank walks the trajectory from its own offset; there is
@@ -852,6 +904,10 @@ def run_fvv(args):
     if world == 1:
         codec = codec_bench(F, ctx, wl, stream)
 
+    layered = None
+    if not args.no_layered and world == 1:
+        layered = layered_bench(F, args.steps, args.warmup, Bsz, slots, stream)
+
     refine = None
     if not args.no_refine and world == 1:
         data = loo_data()
@@ -890,6 +946,7 @@ def run_fvv(args):
                              "resident" % (slots, K * H * W * 6 / 1e6),
                        "parallelism": "replicas" if world > 1 else "single"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "serve": serve, "refine": refine, "codec": codec,
+            "layered": layered,
             "gpu_launches": int(launches), "clocks": clocks.summary(),
             "kernel_ms": {k: v[2] for k, v in stats.items()},
         }

@@ -23,8 +23,10 @@
  * Conventions
  *   - Cameras: pinhole, pixel (u, v) has its centre at integer (u, v);
  *     x right, y down, z forward; R, t map world -> camera; t in metres.
- *   - Depth frames: uint16 codes, 0 = no depth; code * depth_unit_m metres
- *     of camera-space z.  Colour frames: RGB8 interleaved.
+ *   - Depth frames: uint16 codes, 0 = no depth, FVV_DEPTH_BG = a background
+ *     pixel (Sec. V-B: code 0 of the 12-bit map; BG depth is not sent);
+ *     other codes * depth_unit_m metres of camera-space z.  Colour frames:
+ *     RGB8 interleaved.
  *   - Every call returns an fvv_status; on failure fvv_last_error() holds a
  *     message for the calling thread.
  *   - Buffers passed in may be host memory (pageable or pinned) or device
@@ -59,6 +61,7 @@ typedef int32_t fvv_status;
 #define FVV_MAX_CAMS       64          /* 6-bit camera field of a key */
 #define FVV_MAX_SRC_PIXELS (1u << 26)  /* 26-bit source-pixel field of a key */
 #define FVV_KEY_EMPTY      (~(uint64_t)0)
+#define FVV_DEPTH_BG       65535u      /* depth code signalling a background pixel */
 
 typedef struct fvv_ctx fvv_ctx;
 
@@ -89,10 +92,12 @@ typedef struct fvv_options {
     float tau_crack;            /* (c) relative depth tolerance, default 0.05 */
     float tau_vis;              /* (d) visibility tolerance |d - Z| <= tau_vis Z, default 0.03 */
     float z_min;                /* smallest accepted projected depth (depth units), default 1 */
-    uint32_t d_lo, d_hi;        /* accepted depth codes, default [1, 65535] */
+    uint32_t d_lo, d_hi;        /* accepted depth codes, default [1, 65534] (d_hi <= 65534:
+                                   FVV_DEPTH_BG is never a depth) */
     int32_t frame_slots;        /* device-resident frame ticks kept (ring), default 2 */
     int32_t max_batch;          /* most views per batched call, default 64 */
     uint64_t memory_budget;     /* device bytes the context may hold, 0 = unlimited */
+    int32_t layered;            /* 1 = layered FG/BG synthesis (see fvv_set_bg_depth), default 0 */
 } fvv_options;
 
 /* Optional per-view outputs (device or host pointers; NULL = not wanted).
@@ -139,6 +144,27 @@ fvv_status fvv_upload_frames(fvv_ctx* ctx, const uint8_t* rgb, size_t rgb_cam_st
                              size_t depth_cam_stride, size_t depth_pitch,
                              uint64_t tick, void* stream);
 
+/* ---- layered FG/BG synthesis (Sec. VI: per-camera FG and BG layers) -----
+ * With fvv_options.layered = 1 each camera's pixels split by the depth
+ * signalling.  A depth code in [d_lo, d_hi] is a foreground (FG) point at
+ * that depth.  FVV_DEPTH_BG is a background (BG) point at the depth of the
+ * camera's static BG model, with the live colour (a BG pixel where the model
+ * holds 0, or of a camera without a model, is not warped).  0 is neither.
+ * Steps (a)-(d) run on each layer on its own: its own z-buffer and crack
+ * filter, and in (d) the visibility test against that layer's depth in the
+ * other cameras (FG: their live codes; BG: their model where they signal
+ * BG), with the same angular weights.  The FG layer is then stacked over the
+ * BG layer (a pixel shows FG wherever the filtered FG layer is present) and
+ * (e) fills what neither covers.  aux.keys gives each pixel's key in the
+ * layer shown, aux.keys_raw the FG layer's keys before the filter.  The
+ * z-buffer scratch doubles.  Without layered, BG pixels have no depth. */
+
+/* Set camera `cam`'s static BG depth model: height rows of width uint16
+ * depth codes (0 = no model depth) at row pitch `pitch` bytes, host or device
+ * memory, copied.  Waits for the device's work first.  depth = NULL removes
+ * the model.  Errors: INVALID_ARG, BUDGET, OUT_OF_MEMORY, CUDA. */
+fvv_status fvv_set_bg_depth(fvv_ctx* ctx, int32_t cam, const uint16_t* depth, size_t pitch);
+
 /* Newest complete tick, or NOT_READY if none. */
 fvv_status fvv_latest_tick(fvv_ctx* ctx, uint64_t* tick);
 
@@ -176,7 +202,9 @@ fvv_status fvv_view_params(const fvv_rig* rig, const fvv_options* opt,
  * 4 MSBs of the top pair are bit-interleaved into U (bit i of the left pixel
  * at bit 2i, of the right pixel at bit 2i + 1), those of the bottom pair into
  * V.  The view-synthesis side inverts the packing and Eq. (2) on upload,
- * depth code = round(z / depth_unit_m) (codes 0 and 1 decode to 0, no depth).
+ * depth code = round(z / depth_unit_m) clamped to [1, 65534]; code 1
+ * decodes to 0 (no depth) and code 0 to FVV_DEPTH_BG, which also encodes
+ * back to code 0.
  * Both directions use per-camera tables built in FP64 on the host, so the
  * kernels are integer lookups.  Frames need even width and height. */
 typedef struct fvv_depth_codec {

@@ -101,7 +101,11 @@ bool options_ok(const fvv_options& o, int n_cams, std::string* why)
     if (!(o.tau_crack >= 0.0f) || !std::isfinite(o.tau_crack)) { *why = "tau_crack must be >= 0"; return false; }
     if (!(o.tau_vis >= 0.0f) || !std::isfinite(o.tau_vis)) { *why = "tau_vis must be >= 0"; return false; }
     if (!std::isfinite(o.z_min)) { *why = "z_min must be finite"; return false; }
-    if (o.d_lo < 1 || o.d_hi > 65535 || o.d_lo > o.d_hi) { *why = "need 1 <= d_lo <= d_hi <= 65535"; return false; }
+    if (o.d_lo < 1 || o.d_hi > 65534 || o.d_lo > o.d_hi) {
+        *why = "need 1 <= d_lo <= d_hi <= 65534 (65535 is the background signal)";
+        return false;
+    }
+    if (o.layered != 0 && o.layered != 1) { *why = "layered must be 0 or 1"; return false; }
     if (o.frame_slots < 1 || o.frame_slots > 1024) { *why = "frame_slots must be in [1, 1024]"; return false; }
     if (o.max_batch < 1 || o.max_batch > 4096) { *why = "max_batch must be in [1, 4096]"; return false; }
     return true;
@@ -470,7 +474,10 @@ void fvv::scratch_free(fvv_ctx* c, BatchScratch& S)
     S.done = nullptr;
 }
 
-size_t fvv::view_keys(const fvv_view& v) { return align_up(size_t(v.width) * v.height, 16); }
+size_t fvv::view_keys(const fvv_view& v, bool layered)
+{
+    return align_up(size_t(v.width) * v.height, 16) * (layered ? 2 : 1);
+}
 
 size_t fvv::view_stage_bytes(const fvv_view& v, uint8_t* out_rgb, const fvv_aux* aux)
 {
@@ -503,7 +510,7 @@ fvv_status fvv::run_batch(fvv_ctx* c, BatchScratch& S, int n, const fvv_view* vi
     for (int i = 0; i < n; ++i) {
         const fvv_view& V = views[i];
         if (!camera_ok(V, &why)) return fail(FVV_ERR_INVALID_ARG, "view " + std::to_string(i) + ": " + why);
-        if (fvv::resolve_smem_bytes(V.width, c->n_cams) > c->smem_optin)
+        if (fvv::resolve_smem_bytes(V.width, c->n_cams, c->opt.layered != 0) > c->smem_optin)
             return fail(FVV_ERR_INVALID_ARG, "view " + std::to_string(i) + ": width too large");
         if (!out_rgb[i]) return fail(FVV_ERR_INVALID_ARG, "out_rgb[" + std::to_string(i) + "] is NULL");
         if (out_pitch[i] < size_t(V.width) * 3) return fail(FVV_ERR_INVALID_ARG, "out_pitch < 3 * width");
@@ -519,7 +526,7 @@ fvv_status fvv::run_batch(fvv_ctx* c, BatchScratch& S, int n, const fvv_view* vi
         }
         slot_of[i] = int(t % uint64_t(c->slots));
         const size_t np = size_t(V.width) * V.height;
-        key_total += align_up(np, 16);
+        key_total += view_keys(V, c->opt.layered != 0);
         max_w = std::max(max_w, V.width);
         max_h = std::max(max_h, V.height);
         if (mem_kind(out_rgb[i]) == MemKind::Host) stage_total += align_up(np * 3, 256);
@@ -559,7 +566,8 @@ fvv_status fvv::run_batch(fvv_ctx* c, BatchScratch& S, int n, const fvv_view* vi
         D.Hv = V.height;
         D.n_cams = c->n_cams;
         D.slot = slot_of[i];
-        D.flags = (c->opt.crack_filter ? fvv::kFlagCrack : 0) | (c->opt.hole_fill ? fvv::kFlagFill : 0);
+        D.flags = (c->opt.crack_filter ? fvv::kFlagCrack : 0) | (c->opt.hole_fill ? fvv::kFlagFill : 0) |
+                  (c->opt.layered ? fvv::kFlagLayered : 0);
         D.tau_crack = c->opt.tau_crack;
         D.tau_vis = c->opt.tau_vis;
         D.z_min = c->opt.z_min;
@@ -567,6 +575,11 @@ fvv_status fvv::run_batch(fvv_ctx* c, BatchScratch& S, int n, const fvv_view* vi
         D.d_hi = c->opt.d_hi;
         D.keys = S.keys + koff;
         koff += align_up(np, 16);
+        D.keys_bg = nullptr;
+        if (c->opt.layered) {
+            D.keys_bg = S.keys + koff;
+            koff += align_up(np, 16);
+        }
         CamGeom* g = gh + size_t(i) * c->n_cams;
         compose_view(c->n_cams, c->cams.data(), c->look_at, c->depth_unit_m, c->opt.n_ref, V, g);
         D.geom = gd + size_t(i) * c->n_cams;
@@ -634,13 +647,14 @@ fvv_status fvv::run_batch(fvv_ctx* c, BatchScratch& S, int n, const fvv_view* vi
     if (S.pending) FVV_CUDA(cudaStreamWaitEvent(s, S.done, 0));
     FVV_TRY(run_kernel(c, kClear, s, [&] { return fvv::launch_clear_keys(S.keys, koff, s); }));
     FVV_TRY(run_kernel(c, kSplat, s, [&] {
-        return fvv::launch_warp_splat(vdev, n, max_chunks, c->frames_dev, s);
+        return fvv::launch_warp_splat(vdev, n, max_chunks, c->frames_dev, s, c->opt.layered != 0);
     }));
     for (size_t r = 0; r < raw_copies.size(); ++r)
         FVV_CUDA(cudaMemcpyAsync(raw_copies[r].first, raw_copies[r].second, raw_bytes[r],
                                  cudaMemcpyDefault, s));
     FVV_TRY(run_kernel(c, kResolve, s, [&] {
-        return fvv::launch_resolve(vdev, n, max_h, max_w, c->n_cams, want_top3, c->frames_dev, s);
+        return fvv::launch_resolve(vdev, n, max_h, max_w, c->n_cams, want_top3, c->frames_dev, s,
+                                   c->opt.layered != 0);
     }));
     for (const HostCopy& h : d2h)
         FVV_CUDA(cudaMemcpy2DAsync(h.dst, h.dpitch, h.src, h.spitch, h.width, h.height,
@@ -689,7 +703,7 @@ fvv_status fvv_default_options(fvv_options* o)
     o->tau_vis = 0.03f;
     o->z_min = 1.0f;
     o->d_lo = 1;
-    o->d_hi = 65535;
+    o->d_hi = 65534;
     o->frame_slots = 2;
     o->max_batch = 64;
     o->memory_budget = 0;
@@ -759,6 +773,8 @@ fvv_status fvv_destroy(fvv_ctx* c)
     for (int k = 0; k < c->n_cams; ++k)
         if (c->stage_rgb[k])
             dev_free(c, c->stage_rgb[k], size_t(c->cams[k].width) * 3 * size_t(c->cams[k].height));
+    for (size_t k = 0; k < c->bg.size(); ++k)
+        dev_free(c, c->bg[k], size_t(c->cams[k].height) * c->dpitch[k] * 2);
     dev_free(c, c->frames_dev, sizeof(FrameRef) * size_t(c->slots) * c->n_cams);
     dev_free(c, c->arena, c->arena_bytes);
     if (c->stage_all) dev_free(c, c->stage_all, c->stage_all_bytes);
@@ -789,6 +805,7 @@ fvv_status fvv_create(const fvv_rig* rig, const fvv_options* opt, fvv_ctx** out)
     c->slots = o.frame_slots;
     c->full_mask = c->n_cams == 64 ? ~uint64_t(0) : ((uint64_t(1) << c->n_cams) - 1);
     c->stage_rgb.assign(c->n_cams, nullptr);
+    c->bg.assign(c->n_cams, nullptr);
 
     auto bail = [&](fvv_status s) {
         std::string msg = g_err;
@@ -876,6 +893,37 @@ fvv_status fvv_upload_frame(fvv_ctx* c, int32_t cam, const uint8_t* rgb, size_t 
     cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : c->own;
     std::lock_guard<std::recursive_mutex> lock(c->mu);
     return upload_one(c, cam, rgb, rgb_pitch, depth, depth_pitch, tick, s);
+}
+
+fvv_status fvv_set_bg_depth(fvv_ctx* c, int32_t cam, const uint16_t* depth, size_t pitch)
+{
+    if (!c) return fail(FVV_ERR_INVALID_ARG, "ctx is NULL");
+    if (cam < 0 || cam >= c->n_cams) return fail(FVV_ERR_INVALID_ARG, "camera index out of range");
+    const fvv_camera& C = c->cams[cam];
+    if (depth && (pitch < size_t(C.width) * 2 || pitch % 2))
+        return fail(FVV_ERR_INVALID_ARG, "pitch must be even and >= 2 * width");
+    std::lock_guard<std::recursive_mutex> lock(c->mu);
+    FVV_CUDA(cudaSetDevice(c->device));
+    // kernels in flight may read the model: replace it only when they are done
+    FVV_CUDA(cudaDeviceSynchronize());
+    const size_t bytes = size_t(C.height) * c->dpitch[cam] * 2;
+    uint16_t* m = c->bg[cam];
+    if (!depth) {
+        dev_free(c, m, bytes);
+        m = nullptr;
+    } else {
+        if (!m) FVV_TRY(dev_alloc(c, reinterpret_cast<void**>(&m), bytes));
+        c->bg[cam] = m;
+        FVV_CUDA(cudaMemset(m, 0, bytes));
+        FVV_CUDA(cudaMemcpy2D(m, size_t(c->dpitch[cam]) * 2, depth, pitch, size_t(C.width) * 2, size_t(C.height),
+                              cudaMemcpyDefault));
+    }
+    c->bg[cam] = m;
+    // every slot's frame record of this camera points at the model
+    const uint16_t* p = m;
+    for (int s = 0; s < c->slots; ++s)
+        FVV_CUDA(cudaMemcpy(&c->frames_dev[size_t(s) * c->n_cams + cam].bg, &p, sizeof p, cudaMemcpyHostToDevice));
+    return FVV_OK;
 }
 
 fvv_status fvv_upload_frames(fvv_ctx* c, const uint8_t* rgb, size_t rgb_cam_stride, size_t rgb_pitch,

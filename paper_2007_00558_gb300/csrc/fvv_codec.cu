@@ -39,7 +39,8 @@ constexpr double kLevels = 4093.0;          // 2^12 - 3
 // 12-bit code of depth code d (FP64, the operation order of the reading)
 uint16_t encode_code(int d, const fvv_depth_codec& p, double unit)
 {
-    if (d == 0) return 1;
+    if (d == 0) return 1;                       // no depth
+    if (d == int(kDepthBg)) return 0;           // background signal
     const double z = double(d) * unit;
     const double zc = (p.alpha * z + p.beta) * z;               // Eq. (1)
     if (!(zc >= p.z_near && zc <= p.z_far)) return 1;
@@ -50,11 +51,12 @@ uint16_t encode_code(int d, const fvv_depth_codec& p, double unit)
 
 uint16_t decode_code(int y, const fvv_depth_codec& p, double unit)
 {
-    if (y < 2) return 0;
+    if (y == 0) return kDepthBg;
+    if (y == 1) return 0;
     const double inv_n = 1.0 / p.z_near, inv_f = 1.0 / p.z_far;
     const double z = 1.0 / (inv_f + (double(y) - 2.0) * (inv_n - inv_f) / kLevels);
     const double d = std::floor(z / unit + 0.5);
-    return uint16_t(d < 1.0 ? 1.0 : d > 65535.0 ? 65535.0 : d);
+    return uint16_t(d < 1.0 ? 1.0 : d > 65534.0 ? 65534.0 : d);
 }
 
 __device__ __forceinline__ uint32_t interleave4(uint32_t a, uint32_t b)

@@ -11,6 +11,7 @@ namespace fvv {
 constexpr int kMaxCams = 64;
 constexpr int kSrcBits = 26;
 constexpr unsigned long long kKeyEmpty = ~0ull;
+constexpr uint16_t kDepthBg = 65535;   // depth code of a background pixel
 constexpr int kSplatSeg = 256;       // source pixels per splat warp (8 per lane, stride 32)
 constexpr int kSplatThreads = 256;
 constexpr int kResolveThreads = 256;
@@ -18,6 +19,7 @@ constexpr int kResolveBand = 4;      // output rows per resolve CTA
 
 constexpr int kFlagCrack = 1;
 constexpr int kFlagFill = 2;
+constexpr int kFlagLayered = 4;
 
 // Per (view, camera) quantities, composed on the host in FP64 and rounded
 // to FP32 once (Sec. VI geometry).  M maps (u z, v z, z, 1) of the camera to
@@ -31,8 +33,9 @@ struct alignas(16) CamGeom {
 
 // One camera's frame in one slot of the device-resident frame ring.
 struct alignas(16) FrameRef {
-    const uint16_t* depth;   // [H][dpitch] depth codes, 0 = none
+    const uint16_t* depth;   // [H][dpitch] depth codes, 0 = none, kDepthBg = background
     const uint32_t* rgba;    // [H][rpitch] R | G << 8 | B << 16
+    const uint16_t* bg;      // [H][dpitch] static background depth model, or NULL
     int32_t W, H;
     int32_t dpitch;          // elements; rows 128-B aligned
     int32_t rpitch;          // elements
@@ -48,7 +51,8 @@ struct alignas(16) ViewDesc {
     float tau_crack, tau_vis, z_min;
     uint32_t d_lo, d_hi;
     int32_t pad0;
-    unsigned long long* keys;        // scratch z-buffer [Hv * Wv]
+    unsigned long long* keys;        // scratch z-buffer [Hv * Wv] (the FG layer when layered)
+    unsigned long long* keys_bg;     // layered: the BG layer's z-buffer [Hv * Wv], else NULL
     uint8_t* out_rgb;                // [Hv] rows of 3 * Wv bytes
     int64_t out_pitch;               // bytes
     float* out_depth;                // nullable [Hv * Wv]
@@ -62,13 +66,14 @@ struct alignas(16) ViewDesc {
 
 // Launchers (fvv_kernels.cu).  All asynchronous on `stream`.
 cudaError_t launch_clear_keys(unsigned long long* keys, size_t n, cudaStream_t stream);
+// layered: FG/BG layers (each view's keys_bg set, frames' bg models used).
 cudaError_t launch_warp_splat(const ViewDesc* views, int n_views, int max_chunks,
-                              const FrameRef* frames, cudaStream_t stream);
+                              const FrameRef* frames, cudaStream_t stream, bool layered = false);
 cudaError_t launch_resolve(const ViewDesc* views, int n_views, int max_h, int max_w, int n_cams,
-                           bool top3, const FrameRef* frames, cudaStream_t stream);
+                           bool top3, const FrameRef* frames, cudaStream_t stream, bool layered = false);
 cudaError_t launch_pack_rgba(const uint8_t* rgb, size_t rgb_pitch, uint32_t* rgba,
                              int rpitch, int W, int H, cudaStream_t stream);
-size_t resolve_smem_bytes(int max_w, int n_cams);
+size_t resolve_smem_bytes(int max_w, int n_cams, bool layered = false);
 
 }  // namespace fvv
 

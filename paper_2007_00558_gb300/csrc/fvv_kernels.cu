@@ -12,6 +12,13 @@
 //                  (e) row hole fill, fused: one CTA per output row
 //   k_pack_rgba    upload: RGB8 rows -> RGBA8 (one aligned 32-bit gather per texel)
 //
+// Layered form (Sec. VI, per-camera FG and BG layers): a pixel signalled BG
+// (kDepthBg) is a point of the BG layer at its camera's static model depth,
+// every other valid pixel a point of the FG layer; each layer has its own
+// z-buffer, crack filter and visibility test, and the FG layer is stacked
+// over the BG layer before the hole fill.  The kernels take it as a
+// template parameter, so the single-layer form carries none of it.
+//
 // Every FP32 operation of the warp, the filter and the blend is an explicit
 // round-to-nearest intrinsic (__fmul_rn / __fadd_rn / __fsub_rn / __fdiv_rn)
 // in a fixed order with no FMA contraction, so the results are exactly the
@@ -33,11 +40,12 @@ struct SmemLayout {
     size_t ring, rgb, dep, hole, left, right, geom, rowt, frames, active, pos, scan, total;
 };
 
-__host__ __device__ inline SmemLayout resolve_layout(int W, int n_cams)
+__host__ __device__ inline SmemLayout resolve_layout(int W, int n_cams, bool layered)
 {
     SmemLayout L;
     size_t o = 0;
-    L.ring = o;   o = align16(o + size_t(kRing) * W * sizeof(unsigned long long));
+    // layered: the BG layer's ring follows the FG layer's
+    L.ring = o;   o = align16(o + size_t(layered ? 2 : 1) * kRing * W * sizeof(unsigned long long));
     L.rgb = o;    o = align16(o + size_t(W) * 4);
     L.dep = o;    o = align16(o + size_t(W) * 4);
     L.hole = o;   o = align16(o + size_t(W));
@@ -133,6 +141,7 @@ __device__ __forceinline__ uint32_t float_to_u23(float f)   // f integral, 0 <= 
 // chunk_begin[a] .. chunk_begin[a+1).  Each CTA belongs to one view and
 // stages its maps and frame table in shared memory.
 // ---------------------------------------------------------------------------
+template <bool kLayered>
 __global__ void __launch_bounds__(kSplatThreads, 5)
 k_warp_splat(const ViewDesc* __restrict__ views, const FrameRef* __restrict__ frames)
 {
@@ -165,6 +174,7 @@ k_warp_splat(const ViewDesc* __restrict__ views, const FrameRef* __restrict__ fr
     const uint32_t Wv = uint32_t(V->Wv);
     const float maxu = u23_to_float(Wv - 1), maxv = u23_to_float(uint32_t(V->Hv - 1));
     unsigned long long* __restrict__ keys = V->keys;
+    unsigned long long* __restrict__ keys_bg = V->keys_bg;
     const uint64_t pol_stream = policy_evict_first();
     const uint64_t pol_keys = policy_evict_last();
 
@@ -186,6 +196,18 @@ k_warp_splat(const ViewDesc* __restrict__ views, const FrameRef* __restrict__ fr
         for (int j = 0; j < kSplatSeg / 32; ++j) {
             const int u = u0 + lane + 32 * j;
             d[j] = u < F.W ? ld_stream_u16(row + u, pol_stream) : 0u;
+        }
+        // layered: a BG-signalled pixel takes its depth from the model and
+        // splats into the BG layer (bit j of bgm)
+        uint32_t bgm = 0;
+        if (kLayered) {
+            const uint16_t* brow = F.bg ? F.bg + size_t(v) * F.dpitch : nullptr;
+#pragma unroll
+            for (int j = 0; j < kSplatSeg / 32; ++j)
+                if (d[j] == kDepthBg) {
+                    d[j] = brow ? ld_stream_u16(brow + u0 + lane + 32 * j, pol_stream) : 0u;
+                    bgm |= 1u << j;
+                }
         }
 
         const float* m = s_M[a];
@@ -221,7 +243,8 @@ k_warp_splat(const ViewDesc* __restrict__ views, const FrameRef* __restrict__ fr
                 const unsigned long long key =
                     (static_cast<unsigned long long>(__float_as_uint(Z)) << 32) | khi |
                     static_cast<unsigned long long>(src0 + uint32_t(32 * j));
-                red_min_key(keys + pix, key, pol_keys);
+                unsigned long long* dst = (kLayered && ((bgm >> j) & 1u)) ? keys_bg : keys;
+                red_min_key(dst + pix, key, pol_keys);
             }
         }
     }
@@ -336,7 +359,7 @@ __device__ __forceinline__ int block_excl_suffix_min(int v, int* s_scan)
 // kTop3: also track the three largest contributing weights (only when that
 // output is requested).
 // ---------------------------------------------------------------------------
-template <bool kTop3>
+template <bool kTop3, bool kLayered>
 __global__ void __launch_bounds__(kResolveThreads, 3)
 k_resolve(const ViewDesc* __restrict__ views, const FrameRef* __restrict__ frames, int band)
 {
@@ -348,7 +371,7 @@ k_resolve(const ViewDesc* __restrict__ views, const FrameRef* __restrict__ frame
         return;                                    // uniform over the CTA
     const int y1 = min(Hv, y0 + band);
     const int nc = V->n_cams, na = V->n_active;
-    const SmemLayout L = resolve_layout(Wv, nc);
+    const SmemLayout L = resolve_layout(Wv, nc, kLayered);
     unsigned long long* s_ring = reinterpret_cast<unsigned long long*>(smem + L.ring);
     uint32_t* s_rgb = reinterpret_cast<uint32_t*>(smem + L.rgb);
     float* s_dep = reinterpret_cast<float*>(smem + L.dep);
@@ -365,14 +388,25 @@ k_resolve(const ViewDesc* __restrict__ views, const FrameRef* __restrict__ frame
     constexpr int NT = kResolveThreads;
     const unsigned long long* keys = V->keys;
 
+    const unsigned long long* keys_bg = V->keys_bg;
     auto ring_row = [&](int yy) { return s_ring + size_t((yy + kRing) & (kRing - 1)) * Wv; };
+    auto ring_row_bg = [&](int yy) { return ring_row(yy) + size_t(kRing) * Wv; };
     auto fetch_row = [&](int yy) {           // async copy of key row yy (empty outside)
         unsigned long long* dst = ring_row(yy);
         if (yy >= 0 && yy < Hv) {
             const unsigned long long* src = keys + size_t(yy) * Wv;
             for (int x = tid; x < Wv; x += NT) cp_async8(dst + x, src + x);
+            if (kLayered) {
+                unsigned long long* dstb = ring_row_bg(yy);
+                const unsigned long long* srcb = keys_bg + size_t(yy) * Wv;
+                for (int x = tid; x < Wv; x += NT) cp_async8(dstb + x, srcb + x);
+            }
         } else {
             for (int x = tid; x < Wv; x += NT) dst[x] = kKeyEmpty;
+            if (kLayered) {
+                unsigned long long* dstb = ring_row_bg(yy);
+                for (int x = tid; x < Wv; x += NT) dstb[x] = kKeyEmpty;
+            }
         }
     };
     fetch_row(y0 - 1);
@@ -433,7 +467,18 @@ k_resolve(const ViewDesc* __restrict__ views, const FrameRef* __restrict__ frame
         bool any_hole = false;
         for (int x = tid; x < Wv; x += NT) {
             const unsigned long long kp = rC[x];
-            const unsigned long long key = crack ? crack_rule(rU, rC, rD, Wv, x, kp, f1) : kp;
+            unsigned long long key = crack ? crack_rule(rU, rC, rD, Wv, x, kp, f1) : kp;
+            // layered: the FG layer is stacked over the BG layer, so the BG
+            // layer is resolved only where the filtered FG layer is empty
+            bool bg_layer = false;
+            if (kLayered && key == kKeyEmpty) {
+                const unsigned long long* bU = ring_row_bg(y - 1);
+                const unsigned long long* bC = ring_row_bg(y);
+                const unsigned long long* bD = ring_row_bg(y + 1);
+                const unsigned long long kb = bC[x];
+                key = crack ? crack_rule(bU, bC, bD, Wv, x, kb, f1) : kb;
+                bg_layer = true;
+            }
             if (okeys) okeys[rowbase + x] = key;
             if (key == kKeyEmpty) {
                 s_rgb[x] = 0u;
@@ -468,7 +513,7 @@ k_resolve(const ViewDesc* __restrict__ views, const FrameRef* __restrict__ frame
             // before any is consumed, then accumulate in order
             const int pw = s_pos[w], nother = na - 1;
             for (int g0 = 0; g0 < nother; g0 += 4) {
-                uint32_t dk[4], ck[4];
+                uint32_t dk[4], ck[4], di[4];
                 float zk[4];
                 int kk[4];
                 bool ok[4];
@@ -496,11 +541,24 @@ k_resolve(const ViewDesc* __restrict__ views, const FrameRef* __restrict__ frame
                     zk[j] = Zk;
                     dk[j] = 0u;
                     ck[j] = 0u;
+                    di[j] = 0u;
                     if (ok[j]) {
                         const FrameRef& Fk = s_fr[k];
                         const uint32_t uk = float_to_u23(tu), vk = float_to_u23(tv);
-                        dk[j] = __ldg(Fk.depth + vk * uint32_t(Fk.dpitch) + uk);
+                        di[j] = vk * uint32_t(Fk.dpitch) + uk;
+                        dk[j] = __ldg(Fk.depth + di[j]);
                         ck[j] = __ldg(Fk.rgba + vk * uint32_t(Fk.rpitch) + uk);
+                    }
+                }
+                // the BG layer's depth in camera k: its model where camera k
+                // signals BG, none elsewhere (there camera k sees FG)
+                if (kLayered && bg_layer) {
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        if (!ok[j])
+                            continue;
+                        const FrameRef& Fk = s_fr[kk[j]];
+                        dk[j] = (dk[j] == kDepthBg && Fk.bg) ? uint32_t(__ldg(Fk.bg + di[j])) : 0u;
                     }
                 }
 #pragma unroll
@@ -622,7 +680,10 @@ __global__ void __launch_bounds__(256) k_pack_rgba(const uint8_t* __restrict__ r
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
-size_t resolve_smem_bytes(int max_w, int n_cams) { return resolve_layout(max_w, n_cams).total; }
+size_t resolve_smem_bytes(int max_w, int n_cams, bool layered)
+{
+    return resolve_layout(max_w, n_cams, layered).total;
+}
 
 cudaError_t launch_clear_keys(unsigned long long* keys, size_t n, cudaStream_t stream)
 {
@@ -635,7 +696,7 @@ cudaError_t launch_clear_keys(unsigned long long* keys, size_t n, cudaStream_t s
 }
 
 cudaError_t launch_warp_splat(const ViewDesc* views, int n_views, int max_chunks,
-                              const FrameRef* frames, cudaStream_t stream)
+                              const FrameRef* frames, cudaStream_t stream, bool layered)
 {
     if (n_views <= 0 || max_chunks <= 0) return cudaSuccess;
     constexpr int kWarps = kSplatThreads / 32;      // one warp per segment at a time
@@ -647,31 +708,30 @@ cudaError_t launch_warp_splat(const ViewDesc* views, int n_views, int max_chunks
     const int need = (max_chunks + kWarps - 1) / kWarps;
     const int bx = need < want ? need : (want < 1 ? 1 : want);
     dim3 grid(static_cast<unsigned>(bx), static_cast<unsigned>(n_views));
-    k_warp_splat<<<grid, kSplatThreads, 0, stream>>>(views, frames);
+    if (layered)
+        k_warp_splat<true><<<grid, kSplatThreads, 0, stream>>>(views, frames);
+    else
+        k_warp_splat<false><<<grid, kSplatThreads, 0, stream>>>(views, frames);
     return cudaGetLastError();
 }
 
 cudaError_t launch_resolve(const ViewDesc* views, int n_views, int max_h, int max_w, int n_cams,
-                           bool top3, const FrameRef* frames, cudaStream_t stream)
+                           bool top3, const FrameRef* frames, cudaStream_t stream, bool layered)
 {
     if (n_views <= 0 || max_h <= 0) return cudaSuccess;
     // the layout grows with the width and the camera count, so the widest
     // view of the batch bounds every CTA's shared memory
-    const size_t smem = resolve_smem_bytes(max_w, n_cams);
+    const size_t smem = resolve_smem_bytes(max_w, n_cams, layered);
     const int band = kResolveBand;
     dim3 grid(static_cast<unsigned>((max_h + band - 1) / band), static_cast<unsigned>(n_views));
-    if (top3) {
-        cudaError_t e = cudaFuncSetAttribute(k_resolve<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             int(smem));
+    auto go = [&](auto kernel) {
+        cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
         if (e != cudaSuccess) return e;
-        k_resolve<true><<<grid, kResolveThreads, smem, stream>>>(views, frames, band);
-    } else {
-        cudaError_t e = cudaFuncSetAttribute(k_resolve<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             int(smem));
-        if (e != cudaSuccess) return e;
-        k_resolve<false><<<grid, kResolveThreads, smem, stream>>>(views, frames, band);
-    }
-    return cudaGetLastError();
+        kernel<<<grid, kResolveThreads, smem, stream>>>(views, frames, band);
+        return cudaGetLastError();
+    };
+    if (layered) return top3 ? go(k_resolve<true, true>) : go(k_resolve<false, true>);
+    return top3 ? go(k_resolve<true, false>) : go(k_resolve<false, false>);
 }
 
 cudaError_t launch_pack_rgba(const uint8_t* rgb, size_t rgb_pitch, uint32_t* rgba, int rpitch,

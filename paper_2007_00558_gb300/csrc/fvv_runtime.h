@@ -145,6 +145,7 @@ struct fvv_ctx {
     uint64_t latest = 0;
     bool have_latest = false;
 
+    std::vector<uint16_t*> bg;                  // per camera: static BG depth model [H][dpitch] or NULL
     std::vector<uint8_t*> stage_rgb;            // per camera, for host uploads
     uint8_t* stage_all = nullptr;               // batched host uploads (all cameras)
     size_t stage_all_bytes = 0;
@@ -225,8 +226,9 @@ fvv_status scratch_alloc(fvv_ctx* c, BatchScratch& S, size_t keys, size_t stage,
                          int n_blocks);
 void scratch_free(fvv_ctx* c, BatchScratch& S);
 
-// Keys (elements) and host-output staging bytes one view needs.
-size_t view_keys(const fvv_view& v);
+// Keys (elements) and host-output staging bytes one view needs (layered:
+// two z-buffers).
+size_t view_keys(const fvv_view& v, bool layered = false);
 size_t view_stage_bytes(const fvv_view& v, uint8_t* out_rgb, const fvv_aux* aux);
 
 // One batched launch of steps a-e for n views on stream s, with scratch S.

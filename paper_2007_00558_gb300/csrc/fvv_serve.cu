@@ -251,7 +251,8 @@ void scheduler(ServeState* st)
                 size_t keys = 0, stage = 0;
                 while (!st->queue.empty() && int(views.size()) < st->cfg.max_batch) {
                     const Req& r = st->queue.front();
-                    const size_t k = view_keys(r.view), b = view_stage_bytes(r.view, r.out, nullptr);
+                    const size_t k = view_keys(r.view, c->opt.layered != 0),
+                                 b = view_stage_bytes(r.view, r.out, nullptr);
                     if (keys + k > L->S.keys_cap || stage + b > L->S.out_stage_cap) break;
                     keys += k;
                     stage += b;
@@ -407,9 +408,10 @@ fvv_status fvv_serve_start(fvv_ctx* c, const fvv_serve_cfg* cfg_in)
     const size_t room = per_lane - 2 * pb;
     size_t lane_px = 0;
     if (cfg.refine) {
-        // per lane and pixel: 8 bytes of keys and the refinement buffers
-        lane_px = room / (8 + fvv::kRefineBytesPerPixel) / 64 * 64;
-        st->lane_keys = lane_px;
+        // per lane and pixel: 8 bytes of keys per layer and the refinement buffers
+        const size_t layers = c->opt.layered ? 2 : 1;
+        lane_px = room / (8 * layers + fvv::kRefineBytesPerPixel) / 64 * 64;
+        st->lane_keys = lane_px * layers;
         st->lane_stage = 0;
     } else {
         // per lane: 8 bytes of keys and 3 bytes of host-output staging per pixel
@@ -457,7 +459,7 @@ fvv_status fvv_serve_submit(fvv_ctx* c, uint32_t viewer, const fvv_view* view, u
     if (!st) return fail(FVV_ERR_STATE, "serving loop not running");
     std::string why;
     if (!fvv::camera_ok(*view, &why)) return fail(FVV_ERR_INVALID_ARG, "view: " + why);
-    if (fvv::resolve_smem_bytes(view->width, c->n_cams) > c->smem_optin)
+    if (fvv::resolve_smem_bytes(view->width, c->n_cams, c->opt.layered != 0) > c->smem_optin)
         return fail(FVV_ERR_INVALID_ARG, "view: width too large");
     if (pitch < size_t(view->width) * 3) return fail(FVV_ERR_INVALID_ARG, "pitch < 3 * width");
     if (st->cfg.refine) {
@@ -465,7 +467,7 @@ fvv_status fvv_serve_submit(fvv_ctx* c, uint32_t viewer, const fvv_view* view, u
             return fail(FVV_ERR_INVALID_ARG, "refined views need width and height multiples of 4");
         if (size_t(view->width) * view->height > st->lanes[0]->px)
             return fail(FVV_ERR_BUDGET, "view does not fit one lane's share of the serving memory budget");
-    } else if (fvv::view_keys(*view) > st->lane_keys ||
+    } else if (fvv::view_keys(*view, c->opt.layered != 0) > st->lane_keys ||
                fvv::view_stage_bytes(*view, out, nullptr) > st->lane_stage) {
         return fail(FVV_ERR_BUDGET, "view does not fit one lane's share of the serving memory budget");
     }

@@ -30,6 +30,7 @@ FVV_ERR_STATE = 8
 FVV_MAX_CAMS = 64
 FVV_MAX_SRC_PIXELS = 1 << 26
 FVV_KEY_EMPTY = 0xFFFFFFFFFFFFFFFF
+FVV_DEPTH_BG = 65535
 FVV_NOALLOC_MAX_PIXELS = 1 << 21
 
 _NAMES = {v: k for k, v in list(globals().items()) if k.startswith("FVV_ERR_") or k == "FVV_OK"}
@@ -59,7 +60,7 @@ class fvv_options(C.Structure):
     _fields_ = [("n_ref", C.c_int32), ("crack_filter", C.c_int32), ("hole_fill", C.c_int32),
                 ("tau_crack", C.c_float), ("tau_vis", C.c_float), ("z_min", C.c_float),
                 ("d_lo", C.c_uint32), ("d_hi", C.c_uint32), ("frame_slots", C.c_int32),
-                ("max_batch", C.c_int32), ("memory_budget", C.c_uint64)]
+                ("max_batch", C.c_int32), ("memory_budget", C.c_uint64), ("layered", C.c_int32)]
 
 
 class fvv_aux(C.Structure):
@@ -124,6 +125,7 @@ def load() -> C.CDLL:
             "fvv_destroy": [P],
             "fvv_upload_frame": [P, I, P, S, P, S, U64, P],
             "fvv_upload_frames": [P, P, S, S, P, S, S, U64, P],
+            "fvv_set_bg_depth": [P, I, P, S],
             "fvv_latest_tick": [P, C.POINTER(U64)],
             "fvv_synthesize": [P, C.POINTER(fvv_camera), P, S, C.POINTER(fvv_aux), P],
             "fvv_synthesize_batch": [P, I, C.POINTER(fvv_camera), C.POINTER(U64), C.POINTER(P),
@@ -258,6 +260,12 @@ def fvv_upload_frame(ctx: int, cam: int, rgb, rgb_pitch: int, depth, depth_pitch
                      tick: int, stream=None) -> None:
     _check(load().fvv_upload_frame(ctx, cam, ptr(rgb), rgb_pitch, ptr(depth), depth_pitch,
                                    tick, stream_handle(stream)), "fvv_upload_frame")
+
+
+def fvv_set_bg_depth(ctx: int, cam: int, depth, pitch: int = 0) -> None:
+    """Camera `cam`'s static background depth model (None removes it)."""
+    _check(load().fvv_set_bg_depth(ctx, cam, ptr(depth) if depth is not None else None, pitch),
+           "fvv_set_bg_depth")
 
 
 def fvv_upload_frames(ctx: int, rgb, rgb_cam_stride: int, rgb_pitch: int, depth,

@@ -15,8 +15,9 @@ def lib():
 
 
 def gpu_run(cams, rgb, depth, views, look_at, opts=None, ticks=None, host_out=False,
-            rgb_pitch_pad=0, depth_pitch_pad=0, out_pitch_pad=0, stream=None):
-    """Upload one tick (0) of frames and synthesise ``views`` in one batch.
+            rgb_pitch_pad=0, depth_pitch_pad=0, out_pitch_pad=0, stream=None, bg=None):
+    """Upload one tick (0) of frames (and, with ``bg``, each camera's
+    background depth model) and synthesise ``views`` in one batch.
 
     Returns a list of dicts (rgb, depth, hole, top3, keys, keys_raw) as numpy.
     """
@@ -25,6 +26,9 @@ def gpu_run(cams, rgb, depth, views, look_at, opts=None, ticks=None, host_out=Fa
     r = F.rig(cams, look_at)
     ctx = F.fvv_create(r, opts)
     try:
+        for k, c in enumerate(cams):
+            if bg is not None and bg[k] is not None:
+                F.fvv_set_bg_depth(ctx, k, np.ascontiguousarray(bg[k], np.uint16), c.width * 2)
         for k, c in enumerate(cams):
             H, W = c.height, c.width
             rp = W * 3 + rgb_pitch_pad

@@ -27,7 +27,7 @@ def test_default_options(F):
     o = F.fvv_default_options()
     assert (o.n_ref, o.crack_filter, o.hole_fill) == (0, 1, 1)
     assert o.tau_crack == pytest.approx(0.05) and o.tau_vis == pytest.approx(0.03)
-    assert (o.d_lo, o.d_hi, o.frame_slots) == (1, 65535, 2)
+    assert (o.d_lo, o.d_hi, o.frame_slots, o.layered) == (1, 65534, 2, 0)
 
 
 def _rigs():
@@ -90,7 +90,7 @@ def test_invalid_arguments_rejected_on_host(F):
     assert _code(F, F.fvv_view_params, F.rig(nanc, [0, 0, 1]), None, cams[0]) == F.FVV_ERR_INVALID_ARG
     # options
     for kw in ({"n_ref": 3}, {"tau_vis": -1.0}, {"d_lo": 0}, {"d_lo": 9, "d_hi": 8},
-               {"frame_slots": 0}, {"max_batch": 0}):
+               {"d_hi": 65535}, {"layered": 2}, {"frame_slots": 0}, {"max_batch": 0}):
         assert _code(F, F.fvv_create, good, F.fvv_default_options(**kw)) == F.FVV_ERR_INVALID_ARG
     # bad view
     v = cams[0].copy()

@@ -26,11 +26,13 @@ def setup():
 
 
 def _depth_cases(wl):
-    """The workload's depth (noise, dropouts) plus codes out of range."""
+    """The workload's depth (noise, dropouts) plus codes out of range and
+    background-signalled rows."""
     d = np.array(wl["depth"][0], np.uint16)
-    d[:4, :] = 65535                                   # beyond z_far
+    d[:4, :] = 65534                                   # beyond z_far
     d[4:8, :] = 100                                    # nearer than z_near
     d[8:10, :] = 0                                     # no depth
+    d[10:12, 3:] = 65535                               # background
     return d
 
 
