@@ -64,6 +64,8 @@ def parse_args():
                    help="length of the Poisson multi-viewer run")
     p.add_argument("--no-refine", action="store_true", help="skip the refinement-network measurement")
     p.add_argument("--no-layered", action="store_true", help="skip the layered FG/BG measurement")
+    p.add_argument("--layered-only", action="store_true",
+                   help="only the layered FG/BG measurement (--steps/--warmup/--batch/--slots); for profiling")
     p.add_argument("--refine-steps", type=int, default=600, help="LOO training steps before measuring")
     p.add_argument("--net-forward", type=int, default=0, metavar="REPS",
                    help="only time the refinement network: REPS forwards of a batch of 4 plain-like "
@@ -962,6 +964,13 @@ def main():
         return run_reference(args)
     if args.net_forward:
         return net_forward(args)
+    if args.layered_only:
+        import torch
+        from paper_2007_00558_gb300 import fvv as F
+        F.load()
+        print(json.dumps(layered_bench(F, args.steps, args.warmup, args.batch, max(args.slots, args.batch),
+                                       torch.cuda.current_stream())))
+        return 0
     return run_fvv(args)
 
 
