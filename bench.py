@@ -96,7 +96,11 @@ def net_forward(args):
         if args.net_e4m3:
             F.fvv_refine_quantize(ctx, fb)
         out = torch.empty((B, H, W, 3), dtype=torch.uint8, device="cuda")
-        s = torch.cuda.current_stream()
+        # a stream of its own: the library launches on it and the events
+        # are recorded on it (a NULL handle would send the work to the
+        # library's own stream, unordered with events on the default stream)
+        s = torch.cuda.Stream()
+        torch.cuda.set_stream(s)
         for _ in range(2):
             F.fvv_refine_forward(ctx, fb, out, None, s)
         torch.cuda.synchronize()
@@ -792,7 +796,12 @@ def run_fvv(args):
     Bsz, slots = args.batch, max(args.slots, args.batch)
     opts = F.fvv_default_options(frame_slots=slots, max_batch=Bsz)
     ctx = F.fvv_create(F.rig(cams, wl["look_at"]), opts)
-    stream = torch.cuda.current_stream()
+    # the launching stream: every timed call gets this handle, and the CUDA
+    # events of the timed regions are recorded on it (the legacy default
+    # stream's NULL handle would route the work to the library's own stream,
+    # which those events do not order with)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
 
     rgb_h = torch.from_numpy(np.ascontiguousarray(wl["rgb"])).pin_memory()
     dep_h = torch.from_numpy(np.ascontiguousarray(wl["depth"]).view(np.int16)).pin_memory()
@@ -968,8 +977,10 @@ def main():
         import torch
         from paper_2007_00558_gb300 import fvv as F
         F.load()
+        stream = torch.cuda.Stream()
+        torch.cuda.set_stream(stream)
         print(json.dumps(layered_bench(F, args.steps, args.warmup, args.batch, max(args.slots, args.batch),
-                                       torch.cuda.current_stream())))
+                                       stream)))
         return 0
     return run_fvv(args)
 
