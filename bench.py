@@ -665,6 +665,46 @@ def dist_env():
             int(os.environ.get("LOCAL_RANK", 0)))
 
 
+def jbf_bench(F, wl, stream, reps=20):
+    """Joint bilateral depth pre-filter (Sec. VI) on upload: the 9-camera
+    1280x720 tick from pinned host memory through fvv_upload_frames with the
+    filter on (radius 3) and off, and the filter kernel's time per frame
+    from the library's per-launch events against the HBM roofline at 7
+    algorithmic bytes per pixel (2 B codes + 3 B colour read, 2 B written)."""
+    import numpy as np
+    import torch
+    cams = wl["cams"]
+    K, H, W = len(cams), cams[0].height, cams[0].width
+    rgb_h = torch.from_numpy(np.ascontiguousarray(wl["rgb"])).pin_memory()
+    dep_h = torch.from_numpy(np.ascontiguousarray(wl["depth"]).view(np.int16)).pin_memory()
+    res = {}
+    for radius in (3, 0):
+        ctx = F.fvv_create(F.rig(cams, wl["look_at"]), F.fvv_default_options(frame_slots=4, jbf_radius=radius))
+        try:
+            for t in range(3):
+                F.fvv_upload_frames(ctx, rgb_h, H * W * 3, W * 3, dep_h, H * W * 2, W * 2, t, stream)
+            torch.cuda.synchronize()
+            F.fvv_profile_read(ctx, reset=True)
+            F.fvv_profile_enable(ctx, True)
+            t0 = time.perf_counter()
+            for t in range(reps):
+                F.fvv_upload_frames(ctx, rgb_h, H * W * 3, W * 3, dep_h, H * W * 2, W * 2, 3 + t, stream)
+                torch.cuda.synchronize()
+            res[radius] = ((time.perf_counter() - t0) * 1e3 / reps, F.fvv_profile_read(ctx, reset=True))
+        finally:
+            F.fvv_destroy(ctx)
+    st = res[3][1]["jbf"]
+    us = 1e3 * st[2] / st[1] / K
+    gbs = 7.0 * H * W / (us * 1e-6) / 1e9
+    peak, src = measured_peaks()
+    return {"radius": 3, "sigma_s": 2.0, "sigma_c": 10.0, "min_valid": 3, "frame": "%dx%d" % (W, H),
+            "kernel_us_per_frame": us, "gbs": gbs,
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+                         "peak_source": src, "alg_bytes_per_pixel": 7.0},
+            "upload_tick_ms": {"with_filter": res[3][0], "without": res[0][0], "cameras": K},
+            "holes_before": float((wl["depth"] == 0).mean())}
+
+
 def layered_bench(F, steps, warmup, batch, slots, stream):
     """Layered FG/BG synthesis (Sec. VI per-camera FG and BG layers) on the
     9-camera 1280x720 rig over a static set with actors: the main
@@ -915,6 +955,10 @@ def run_fvv(args):
     if world == 1:
         codec = codec_bench(F, ctx, wl, stream)
 
+    jbf = None
+    if world == 1:
+        jbf = jbf_bench(F, wl, stream)
+
     layered = None
     if not args.no_layered and world == 1:
         layered = layered_bench(F, args.steps, args.warmup, Bsz, slots, stream)
@@ -957,7 +1001,7 @@ def run_fvv(args):
                              "resident" % (slots, K * H * W * 6 / 1e6),
                        "parallelism": "replicas" if world > 1 else "single"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "serve": serve, "refine": refine, "codec": codec,
-            "layered": layered,
+            "layered": layered, "jbf": jbf,
             "gpu_launches": int(launches), "clocks": clocks.summary(),
             "kernel_ms": {k: v[2] for k, v in stats.items()},
         }

@@ -98,6 +98,11 @@ typedef struct fvv_options {
     int32_t max_batch;          /* most views per batched call, default 64 */
     uint64_t memory_budget;     /* device bytes the context may hold, 0 = unlimited */
     int32_t layered;            /* 1 = layered FG/BG synthesis (see fvv_set_bg_depth), default 0 */
+    /* joint bilateral depth pre-filter on upload (see fvv_depth_jbf) */
+    int32_t jbf_radius;         /* window radius 0..7, 0 = off (default) */
+    float jbf_sigma_s;          /* spatial sigma, pixels, default 2 */
+    float jbf_sigma_c;          /* colour sigma per RGB channel, default 10 */
+    int32_t jbf_min_valid;      /* fill only with at least this many valid neighbours, default 3 */
 } fvv_options;
 
 /* Optional per-view outputs (device or host pointers; NULL = not wanted).
@@ -164,6 +169,27 @@ fvv_status fvv_upload_frames(fvv_ctx* ctx, const uint8_t* rgb, size_t rgb_cam_st
  * memory, copied.  Waits for the device's work first.  depth = NULL removes
  * the model.  Errors: INVALID_ARG, BUDGET, OUT_OF_MEMORY, CUDA. */
 fvv_status fvv_set_bg_depth(fvv_ctx* ctx, int32_t cam, const uint16_t* depth, size_t pitch);
+
+/* ---- joint bilateral depth pre-filter (Sec. VI) ------------------------
+ * Live depth is pre-processed to close small holes and gaps around object
+ * edges with a joint bilateral filter guided by the colour frame.  A pixel
+ * without depth (0) takes the weighted mean of the valid codes (in [d_lo,
+ * d_hi], not FVV_DEPTH_BG) of its (2 jbf_radius + 1)^2 window, visited in
+ * row-major order; the weight is s(dx, dy) c(|dR|) c(|dG|) c(|dB|) with
+ * s = exp(-(dx^2 + dy^2) / (2 jbf_sigma_s^2)) and c(t) = exp(-t^2 / (2
+ * jbf_sigma_c^2)), each evaluated in FP64 and rounded to FP32 once, products
+ * and sums in FP32 round-to-nearest in that order.  The code is
+ * floor(sum w d / sum w + 0.5) clamped to [d_lo, d_hi], written when at
+ * least jbf_min_valid neighbours are valid; other pixels keep their code.
+ * With fvv_options.jbf_radius > 0 every uploaded frame (all upload calls)
+ * is filtered before it enters the frame ring.  This call runs the filter
+ * on one frame: rgb (height rows of width*3 bytes), depth and out (height
+ * rows of width uint16, even pitches) in device memory; out must not overlap
+ * depth.  Asynchronous on `stream`.  Errors: INVALID_ARG (options with
+ * jbf_radius = 0 included), CUDA. */
+fvv_status fvv_depth_jbf(const uint8_t* rgb, size_t rgb_pitch, const uint16_t* depth, size_t depth_pitch,
+                         uint16_t* out, size_t out_pitch, int32_t width, int32_t height,
+                         const fvv_options* opt, void* stream);
 
 /* Newest complete tick, or NOT_READY if none. */
 fvv_status fvv_latest_tick(fvv_ctx* ctx, uint64_t* tick);

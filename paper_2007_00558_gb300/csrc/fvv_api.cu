@@ -13,6 +13,7 @@
 
 #include "fvv.h"
 #include "fvv_internal.h"
+#include "fvv_jbf.h"
 #include "fvv_runtime.h"
 
 using fvv::BatchScratch;
@@ -47,7 +48,7 @@ fvv_status fvv::fail(fvv_status code, const std::string& msg)
 }
 
 const char* const fvv::kKernelName[fvv::kNumKernels] = {"clear_keys", "warp_splat", "resolve",
-                                                        "pack_rgba", "yuv_decode"};
+                                                        "pack_rgba", "yuv_decode", "jbf"};
 
 fvv::MemKind fvv::mem_kind(const void* p)
 {
@@ -106,6 +107,7 @@ bool options_ok(const fvv_options& o, int n_cams, std::string* why)
         return false;
     }
     if (o.layered != 0 && o.layered != 1) { *why = "layered must be 0 or 1"; return false; }
+    if (!fvv::jbf_options_ok(o, why)) return false;
     if (o.frame_slots < 1 || o.frame_slots > 1024) { *why = "frame_slots must be in [1, 1024]"; return false; }
     if (o.max_batch < 1 || o.max_batch > 4096) { *why = "max_batch must be in [1, 4096]"; return false; }
     return true;
@@ -325,18 +327,39 @@ fvv_status fvv::upload_frame(fvv_ctx* c, int cam, const uint8_t* rgb, size_t rgb
     uint8_t* base = c->arena + size_t(si) * c->slot_bytes;
     uint16_t* ddst = reinterpret_cast<uint16_t*>(base + c->off_depth[cam]);
     uint32_t* rdst = reinterpret_cast<uint32_t*>(base + c->off_rgba[cam]);
+    const bool staged = mem_kind(rgb) == MemKind::Host;
+    // with the depth pre-filter the unfiltered codes go to a per-camera
+    // buffer (or are read in place from device memory) and the filter
+    // writes the slot
+    const bool jbf = c->opt.jbf_radius > 0;
+    const uint16_t* jsrc = nullptr;
+    int64_t jpitch = 0;
+    uint16_t* dfirst = ddst;
+    if (jbf) {
+        if (!c->jbf_tmp[cam])
+            FVV_TRY(dev_alloc(c, reinterpret_cast<void**>(&c->jbf_tmp[cam]), size_t(C.height) * c->dpitch[cam] * 2));
+        if (!yuv && mem_kind(depth) == MemKind::Device && depth_pitch % 2 == 0 &&
+            (reinterpret_cast<uintptr_t>(depth) & 1) == 0) {
+            jsrc = depth;
+            jpitch = int64_t(depth_pitch / 2);
+            dfirst = nullptr;
+        } else {
+            dfirst = c->jbf_tmp[cam];
+            jsrc = dfirst;
+            jpitch = c->dpitch[cam];
+        }
+    }
+    if (staged || jbf) FVV_CUDA(cudaStreamWaitEvent(s, c->stage_free, 0));   // a previous upload may still read them
     if (yuv)
         FVV_TRY(run_kernel(c, kDecode, s, [&] {
-            return fvv::launch_yuv_decode(*yuv, C.width, C.height, ddst, size_t(c->dpitch[cam]) * 2, s);
+            return fvv::launch_yuv_decode(*yuv, C.width, C.height, dfirst, size_t(c->dpitch[cam]) * 2, s);
         }));
-    else
-        FVV_CUDA(cudaMemcpy2DAsync(ddst, size_t(c->dpitch[cam]) * 2, depth, depth_pitch, size_t(C.width) * 2,
+    else if (dfirst)
+        FVV_CUDA(cudaMemcpy2DAsync(dfirst, size_t(c->dpitch[cam]) * 2, depth, depth_pitch, size_t(C.width) * 2,
                                    size_t(C.height), cudaMemcpyDefault, s));
     const uint8_t* src = rgb;
     size_t spitch = rgb_pitch;
-    const bool staged = mem_kind(rgb) == MemKind::Host;
     if (staged) {
-        FVV_CUDA(cudaStreamWaitEvent(s, c->stage_free, 0));   // a previous upload may still read it
         if (!c->stage_rgb[cam]) {
             void* p = nullptr;
             FVV_TRY(dev_alloc(c, &p, size_t(C.width) * 3 * size_t(C.height)));
@@ -350,7 +373,13 @@ fvv_status fvv::upload_frame(fvv_ctx* c, int cam, const uint8_t* rgb, size_t rgb
     FVV_TRY(run_kernel(c, kPack, s, [&] {
         return fvv::launch_pack_rgba(src, spitch, rdst, c->rpitch[cam], C.width, C.height, s);
     }));
-    if (staged) FVV_CUDA(cudaEventRecord(c->stage_free, s));
+    if (jbf) {
+        JbfParams P;
+        jbf_params(c->opt, C.width, C.height, &P);
+        P.cam[0] = JbfCam{src, int64_t(spitch), jsrc, jpitch, ddst, int64_t(c->dpitch[cam])};
+        FVV_TRY(run_kernel(c, kJbf, s, [&] { return launch_jbf(P, 1, s); }));
+    }
+    if (staged || jbf) FVV_CUDA(cudaEventRecord(c->stage_free, s));
     FVV_CUDA(cudaEventRecord(S.uploaded, s));
     S.mask |= uint64_t(1) << cam;
     if (S.mask == c->full_mask && (!c->have_latest || tick > c->latest)) {
@@ -422,6 +451,17 @@ static fvv_status upload_all(fvv_ctx* c, const uint8_t* rgb, size_t rcs, size_t 
         u.off_rgba[k] = c->off_rgba[k];
     }
     FVV_TRY(run_kernel(c, kPack, s, [&] { return launch_upload_all(u, s); }));
+    if (c->opt.jbf_radius > 0) {
+        // the pre-filter reads the unfiltered codes where they came from and
+        // overwrites the slot's depth rows
+        JbfParams P;
+        jbf_params(c->opt, W, H, &P);
+        for (int k = 0; k < K; ++k)
+            P.cam[k] = JbfCam{r + size_t(k) * rcs, int64_t(rp),
+                              reinterpret_cast<const uint16_t*>(d + size_t(k) * dcs), int64_t(dp / 2),
+                              reinterpret_cast<uint16_t*>(u.slot + c->off_depth[k]), int64_t(c->dpitch[k])};
+        FVV_TRY(run_kernel(c, kJbf, s, [&] { return launch_jbf(P, K, s); }));
+    }
     if (host) FVV_CUDA(cudaEventRecord(c->stage_free, s));
     FVV_CUDA(cudaEventRecord(S.uploaded, s));
     S.mask = c->full_mask;
@@ -707,6 +747,11 @@ fvv_status fvv_default_options(fvv_options* o)
     o->frame_slots = 2;
     o->max_batch = 64;
     o->memory_budget = 0;
+    o->layered = 0;
+    o->jbf_radius = 0;
+    o->jbf_sigma_s = 2.0f;
+    o->jbf_sigma_c = 10.0f;
+    o->jbf_min_valid = 3;
     return FVV_OK;
 }
 
@@ -775,6 +820,8 @@ fvv_status fvv_destroy(fvv_ctx* c)
             dev_free(c, c->stage_rgb[k], size_t(c->cams[k].width) * 3 * size_t(c->cams[k].height));
     for (size_t k = 0; k < c->bg.size(); ++k)
         dev_free(c, c->bg[k], size_t(c->cams[k].height) * c->dpitch[k] * 2);
+    for (size_t k = 0; k < c->jbf_tmp.size(); ++k)
+        dev_free(c, c->jbf_tmp[k], size_t(c->cams[k].height) * c->dpitch[k] * 2);
     dev_free(c, c->frames_dev, sizeof(FrameRef) * size_t(c->slots) * c->n_cams);
     dev_free(c, c->arena, c->arena_bytes);
     if (c->stage_all) dev_free(c, c->stage_all, c->stage_all_bytes);
@@ -806,6 +853,7 @@ fvv_status fvv_create(const fvv_rig* rig, const fvv_options* opt, fvv_ctx** out)
     c->full_mask = c->n_cams == 64 ? ~uint64_t(0) : ((uint64_t(1) << c->n_cams) - 1);
     c->stage_rgb.assign(c->n_cams, nullptr);
     c->bg.assign(c->n_cams, nullptr);
+    c->jbf_tmp.assign(c->n_cams, nullptr);
 
     auto bail = [&](fvv_status s) {
         std::string msg = g_err;
@@ -938,7 +986,10 @@ fvv_status fvv_upload_frames(fvv_ctx* c, const uint8_t* rgb, size_t rgb_cam_stri
     for (int k = 1; k < c->n_cams; ++k)
         uniform = uniform && c->cams[k].width == c->cams[0].width && c->cams[k].height == c->cams[0].height;
     const fvv::MemKind kr = fvv::mem_kind(rgb), kd = fvv::mem_kind(depth);
-    if (uniform && kr == kd)
+    // the batched kernel reads depth as uint16: device rows must be 2-byte aligned
+    const bool aligned = depth_pitch % 2 == 0 && depth_cam_stride % 2 == 0 &&
+                         (kd == fvv::MemKind::Host || (reinterpret_cast<uintptr_t>(depth) & 1) == 0);
+    if (uniform && kr == kd && aligned)
         return upload_all(c, rgb, rgb_cam_stride, rgb_pitch, reinterpret_cast<const uint8_t*>(depth),
                           depth_cam_stride, depth_pitch, tick, s, kr == fvv::MemKind::Host);
     for (int k = 0; k < c->n_cams; ++k) {

@@ -1,0 +1,174 @@
+// fvv_jbf.cu -- joint bilateral depth pre-filter (Sec. VI: live depth is
+// pre-processed to close small holes and gaps around object edges with a
+// joint bilateral filter guided by the colour frame).
+//
+// A pixel without depth (code 0) takes the weighted mean of the valid codes
+// in its (2r+1) x (2r+1) window; every other pixel keeps its code.  The
+// weight of neighbour q is s[dy][dx] * c[|dR|] * c[|dG|] * c[|dB|] with
+// s = exp(-(dx^2 + dy^2) / (2 sigma_s^2)) and c[t] = exp(-t^2 / (2
+// sigma_c^2)), both evaluated on the host in FP64 and rounded to FP32 once.
+// Neighbours are visited in row-major window order and every FP32 operation
+// is an explicit round-to-nearest intrinsic, so the result is exactly that
+// of the stated operation sequence.  The code is floor(acc / wsum + 0.5)
+// clamped to [d_lo, d_hi], written only when at least min_valid neighbours
+// are valid codes; the background signal is neither a source nor filled.
+// One pass, out of place.
+//
+// The filter reads 2 + 3 bytes and writes 2 bytes per pixel: it is bound by
+// HBM bandwidth.  Only the few pixels without depth visit their window, and
+// those reads hit the lines the block's own row loads just brought in.
+#include <cmath>
+#include <cstring>
+
+#include "fvv_jbf.h"
+#include "fvv_runtime.h"
+
+namespace fvv {
+
+namespace {
+
+__device__ __forceinline__ float code_to_float(uint32_t d)   // exact for d < 2^23
+{
+    return __fsub_rn(__uint_as_float(0x4B000000u | d), 8388608.0f);
+}
+
+__device__ __forceinline__ uint32_t absdiff(uint32_t a, uint32_t b) { return a > b ? a - b : b - a; }
+
+// one thread per pixel of a 32 x 8 tile of camera blockIdx.z
+__global__ void __launch_bounds__(256) k_jbf(const JbfParams P)
+{
+    const JbfCam& C = P.cam[blockIdx.z];
+    const int x = blockIdx.x * 32 + threadIdx.x;
+    const int y = blockIdx.y * 8 + threadIdx.y;
+    if (x >= P.width || y >= P.height)
+        return;
+    const uint32_t d = __ldg(C.src + size_t(y) * C.src_pitch + x);
+    uint32_t out = d;
+    if (d == 0u) {
+        const int R = P.radius, side = 2 * R + 1;
+        const uint8_t* cp = C.rgb + size_t(y) * C.rgb_pitch + 3 * size_t(x);
+        const uint32_t r0 = __ldg(cp), g0 = __ldg(cp + 1), b0 = __ldg(cp + 2);
+        float acc = 0.0f, wsum = 0.0f;
+        int n = 0;
+        for (int dy = -R; dy <= R; ++dy) {
+            const int yy = y + dy;
+            if (yy < 0 || yy >= P.height)
+                continue;
+            const uint16_t* drow = C.src + size_t(yy) * C.src_pitch;
+            const uint8_t* crow = C.rgb + size_t(yy) * C.rgb_pitch;
+            for (int dx = -R; dx <= R; ++dx) {
+                const int xx = x + dx;
+                if (xx < 0 || xx >= P.width)
+                    continue;
+                const uint32_t q = __ldg(drow + xx);
+                if (q < P.d_lo || q > P.d_hi || q == kDepthBg)
+                    continue;
+                const uint8_t* cq = crow + 3 * size_t(xx);
+                const float w = __fmul_rn(
+                    __fmul_rn(__fmul_rn(P.s[(dy + R) * side + (dx + R)], P.c[absdiff(r0, __ldg(cq))]),
+                              P.c[absdiff(g0, __ldg(cq + 1))]),
+                    P.c[absdiff(b0, __ldg(cq + 2))]);
+                acc = __fadd_rn(acc, __fmul_rn(w, code_to_float(q)));
+                wsum = __fadd_rn(wsum, w);
+                ++n;
+            }
+        }
+        if (n >= P.min_valid && wsum > 0.0f) {
+            float v = floorf(__fadd_rn(__fdiv_rn(acc, wsum), 0.5f));
+            v = fminf(fmaxf(v, float(P.d_lo)), float(P.d_hi));
+            out = uint32_t(v);
+        }
+    }
+    C.dst[size_t(y) * C.dst_pitch + x] = uint16_t(out);
+}
+
+}  // namespace
+
+bool jbf_options_ok(const fvv_options& o, std::string* why)
+{
+    if (o.jbf_radius < 0 || o.jbf_radius > kJbfMaxRadius) {
+        *why = "jbf_radius must be in [0, 7]";
+        return false;
+    }
+    if (o.jbf_radius == 0) return true;
+    if (!(o.jbf_sigma_s > 0.0f) || !std::isfinite(o.jbf_sigma_s) || !(o.jbf_sigma_c > 0.0f) ||
+        !std::isfinite(o.jbf_sigma_c)) {
+        *why = "jbf_sigma_s and jbf_sigma_c must be finite and > 0";
+        return false;
+    }
+    const int side = 2 * o.jbf_radius + 1;
+    if (o.jbf_min_valid < 1 || o.jbf_min_valid >= side * side) {
+        *why = "jbf_min_valid must be in [1, (2 jbf_radius + 1)^2 - 1]";
+        return false;
+    }
+    return true;
+}
+
+void jbf_params(const fvv_options& o, int width, int height, JbfParams* P)
+{
+    std::memset(P, 0, sizeof *P);
+    P->width = width;
+    P->height = height;
+    P->radius = o.jbf_radius;
+    P->min_valid = o.jbf_min_valid;
+    P->d_lo = o.d_lo;
+    P->d_hi = o.d_hi;
+    const int R = o.jbf_radius, side = 2 * R + 1;
+    const double ss = double(o.jbf_sigma_s), sc = double(o.jbf_sigma_c);
+    for (int dy = -R; dy <= R; ++dy)
+        for (int dx = -R; dx <= R; ++dx)
+            P->s[(dy + R) * side + (dx + R)] = float(std::exp(-double(dx * dx + dy * dy) / (2.0 * ss * ss)));
+    for (int t = 0; t < 256; ++t) P->c[t] = float(std::exp(-double(t * t) / (2.0 * sc * sc)));
+}
+
+cudaError_t launch_jbf(const JbfParams& P, int n_cams, cudaStream_t stream)
+{
+    if (n_cams <= 0 || P.width <= 0 || P.height <= 0) return cudaSuccess;
+    dim3 grid(unsigned((P.width + 31) / 32), unsigned((P.height + 7) / 8), unsigned(n_cams));
+    k_jbf<<<grid, dim3(32, 8), 0, stream>>>(P);
+    return cudaGetLastError();
+}
+
+}  // namespace fvv
+
+using fvv::fail;
+
+extern "C" fvv_status fvv_depth_jbf(const uint8_t* rgb, size_t rgb_pitch, const uint16_t* depth, size_t depth_pitch,
+                                    uint16_t* out, size_t out_pitch, int32_t width, int32_t height,
+                                    const fvv_options* opt, void* stream)
+{
+    if (!rgb || !depth || !out || !opt) return fail(FVV_ERR_INVALID_ARG, "fvv_depth_jbf: NULL argument");
+    if (width < 1 || height < 1) return fail(FVV_ERR_INVALID_ARG, "fvv_depth_jbf: width and height must be >= 1");
+    std::string why;
+    if (!fvv::jbf_options_ok(*opt, &why)) return fail(FVV_ERR_INVALID_ARG, "fvv_depth_jbf: " + why);
+    if (opt->jbf_radius == 0) return fail(FVV_ERR_INVALID_ARG, "fvv_depth_jbf: jbf_radius is 0 (filter off)");
+    if (opt->d_lo < 1 || opt->d_hi > 65534 || opt->d_lo > opt->d_hi)
+        return fail(FVV_ERR_INVALID_ARG, "fvv_depth_jbf: need 1 <= d_lo <= d_hi <= 65534");
+    if (rgb_pitch < size_t(width) * 3 || depth_pitch < size_t(width) * 2 || depth_pitch % 2 ||
+        out_pitch < size_t(width) * 2 || out_pitch % 2 || (reinterpret_cast<uintptr_t>(depth) & 1) ||
+        (reinterpret_cast<uintptr_t>(out) & 1))
+        return fail(FVV_ERR_INVALID_ARG, "fvv_depth_jbf: bad pitch or alignment");
+    const size_t ib = depth_pitch * size_t(height - 1) + size_t(width) * 2;
+    const size_t ob = out_pitch * size_t(height - 1) + size_t(width) * 2;
+    const uintptr_t i0 = reinterpret_cast<uintptr_t>(depth), o0 = reinterpret_cast<uintptr_t>(out);
+    if (i0 < o0 + ob && o0 < i0 + ib)
+        return fail(FVV_ERR_INVALID_ARG, "fvv_depth_jbf: out must not overlap depth (the filter is out of place)");
+    for (const void* p : {static_cast<const void*>(rgb), static_cast<const void*>(depth),
+                          static_cast<const void*>(out)})
+        if (fvv::mem_kind(p) != fvv::MemKind::Device)
+            return fail(FVV_ERR_INVALID_ARG, "fvv_depth_jbf: buffers must be device memory");
+    fvv::JbfParams P;
+    fvv::jbf_params(*opt, width, height, &P);
+    P.cam[0].rgb = rgb;
+    P.cam[0].rgb_pitch = int64_t(rgb_pitch);
+    P.cam[0].src = depth;
+    P.cam[0].src_pitch = int64_t(depth_pitch / 2);
+    P.cam[0].dst = out;
+    P.cam[0].dst_pitch = int64_t(out_pitch / 2);
+    cudaError_t e = fvv::launch_jbf(P, 1, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(FVV_ERR_CUDA, std::string("fvv_depth_jbf: ") + cudaGetErrorString(e));
+    }
+    return FVV_OK;
+}

@@ -51,7 +51,7 @@ struct ParamBlock {
     bool pending = false;
 };
 
-enum Kid { kClear = 0, kSplat, kResolve, kPack, kDecode, kNumKernels };
+enum Kid { kClear = 0, kSplat, kResolve, kPack, kDecode, kJbf, kNumKernels };
 extern const char* const kKernelName[kNumKernels];
 
 struct KernelStat {
@@ -146,6 +146,7 @@ struct fvv_ctx {
     bool have_latest = false;
 
     std::vector<uint16_t*> bg;                  // per camera: static BG depth model [H][dpitch] or NULL
+    std::vector<uint16_t*> jbf_tmp;             // per camera: unfiltered codes [H][dpitch] (depth pre-filter)
     std::vector<uint8_t*> stage_rgb;            // per camera, for host uploads
     uint8_t* stage_all = nullptr;               // batched host uploads (all cameras)
     size_t stage_all_bytes = 0;

@@ -60,7 +60,9 @@ class fvv_options(C.Structure):
     _fields_ = [("n_ref", C.c_int32), ("crack_filter", C.c_int32), ("hole_fill", C.c_int32),
                 ("tau_crack", C.c_float), ("tau_vis", C.c_float), ("z_min", C.c_float),
                 ("d_lo", C.c_uint32), ("d_hi", C.c_uint32), ("frame_slots", C.c_int32),
-                ("max_batch", C.c_int32), ("memory_budget", C.c_uint64), ("layered", C.c_int32)]
+                ("max_batch", C.c_int32), ("memory_budget", C.c_uint64), ("layered", C.c_int32),
+                ("jbf_radius", C.c_int32), ("jbf_sigma_s", C.c_float), ("jbf_sigma_c", C.c_float),
+                ("jbf_min_valid", C.c_int32)]
 
 
 class fvv_aux(C.Structure):
@@ -126,6 +128,7 @@ def load() -> C.CDLL:
             "fvv_upload_frame": [P, I, P, S, P, S, U64, P],
             "fvv_upload_frames": [P, P, S, S, P, S, S, U64, P],
             "fvv_set_bg_depth": [P, I, P, S],
+            "fvv_depth_jbf": [P, S, P, S, P, S, I, I, C.POINTER(fvv_options), P],
             "fvv_latest_tick": [P, C.POINTER(U64)],
             "fvv_synthesize": [P, C.POINTER(fvv_camera), P, S, C.POINTER(fvv_aux), P],
             "fvv_synthesize_batch": [P, I, C.POINTER(fvv_camera), C.POINTER(U64), C.POINTER(P),
@@ -260,6 +263,13 @@ def fvv_upload_frame(ctx: int, cam: int, rgb, rgb_pitch: int, depth, depth_pitch
                      tick: int, stream=None) -> None:
     _check(load().fvv_upload_frame(ctx, cam, ptr(rgb), rgb_pitch, ptr(depth), depth_pitch,
                                    tick, stream_handle(stream)), "fvv_upload_frame")
+
+
+def fvv_depth_jbf(rgb, rgb_pitch: int, depth, depth_pitch: int, out, out_pitch: int, width: int, height: int,
+                  opt: fvv_options, stream=None) -> None:
+    """Joint bilateral depth pre-filter of one frame (device buffers)."""
+    _check(load().fvv_depth_jbf(ptr(rgb), rgb_pitch, ptr(depth), depth_pitch, ptr(out), out_pitch, width, height,
+                                C.byref(opt), stream_handle(stream)), "fvv_depth_jbf")
 
 
 def fvv_set_bg_depth(ctx: int, cam: int, depth, pitch: int = 0) -> None:
