@@ -43,12 +43,15 @@ def _run(F, rgb, depth, **kw):
 def test_filter_matches_oracle(arc, kw):
     F = lib()
     o = F.fvv_default_options(**kw)
+    filled = 0
     for k in (0, 4, 8):
         got = _run(F, arc["rgb"][k], arc["depth"][k], **kw)
         ref = J.jbf(arc["depth"][k], arc["rgb"][k], radius=o.jbf_radius, sigma_s=f32(o.jbf_sigma_s),
                     sigma_c=f32(o.jbf_sigma_c), d_lo=o.d_lo, d_hi=o.d_hi, min_valid=o.jbf_min_valid)
         assert np.array_equal(got, ref), "camera %d: %d codes differ" % (k, int((got != ref).sum()))
-        assert (got != arc["depth"][k]).any()
+        filled += int((got != arc["depth"][k]).sum())
+    if o.jbf_min_valid < 8:                  # the 3x3 case with 8 valid neighbours may fill nothing
+        assert filled > 0
 
 
 def test_filter_edge_cases():
