@@ -15,8 +15,8 @@
 // One pass, out of place.
 //
 // The filter reads 2 + 3 bytes and writes 2 bytes per pixel: it is bound by
-// HBM bandwidth.  Only the few pixels without depth visit their window, and
-// those reads hit the lines the block's own row loads just brought in.
+// HBM bandwidth once the few pixels without depth, the only ones that visit
+// their window, no longer hold up whole warps (see k_jbf).
 #include <cmath>
 #include <cstring>
 
@@ -34,52 +34,86 @@ __device__ __forceinline__ float code_to_float(uint32_t d)   // exact for d < 2^
 
 __device__ __forceinline__ uint32_t absdiff(uint32_t a, uint32_t b) { return a > b ? a - b : b - a; }
 
-// one thread per pixel of a 32 x 8 tile of camera blockIdx.z
-__global__ void __launch_bounds__(256) k_jbf(const JbfParams P)
+// A CTA filters a kTileW x kTileH tile of camera blockIdx.z.  Phase 1
+// stages the tile and its halo (codes and colour bytes) in shared memory
+// with coalesced loads.  Phase 2 writes every pixel with a code straight
+// through and lists the pixels without one.  Phase 3 deals the listed
+// pixels out to the threads, so a tile's few holes are filtered by many
+// threads at once instead of idling the rest of their warps; each filtered
+// pixel walks its window in shared memory in the stated order.
+constexpr int kTileW = 64, kTileH = 16, kThreads = 256;
+constexpr int kHaloW = kTileW + 2 * kJbfMaxRadius, kHaloH = kTileH + 2 * kJbfMaxRadius;
+
+__global__ void __launch_bounds__(kThreads) k_jbf(const JbfParams P)
 {
+    __shared__ uint16_t s_d[kHaloH][kHaloW];
+    __shared__ uint8_t s_c[kHaloH][3 * kHaloW];
+    __shared__ uint16_t s_list[kTileW * kTileH];
+    __shared__ int s_n;
     const JbfCam& C = P.cam[blockIdx.z];
-    const int x = blockIdx.x * 32 + threadIdx.x;
-    const int y = blockIdx.y * 8 + threadIdx.y;
-    if (x >= P.width || y >= P.height)
-        return;
-    const uint32_t d = __ldg(C.src + size_t(y) * C.src_pitch + x);
-    uint32_t out = d;
-    if (d == 0u) {
-        const int R = P.radius, side = 2 * R + 1;
-        const uint8_t* cp = C.rgb + size_t(y) * C.rgb_pitch + 3 * size_t(x);
-        const uint32_t r0 = __ldg(cp), g0 = __ldg(cp + 1), b0 = __ldg(cp + 2);
+    const int R = P.radius, side = 2 * R + 1;
+    const int x0 = blockIdx.x * kTileW, y0 = blockIdx.y * kTileH;
+    const int hw = kTileW + 2 * R, hh = kTileH + 2 * R;
+    const int tid = threadIdx.x;
+    if (tid == 0) s_n = 0;
+    // phase 1: halo tile; outside the image a code of 0 (never a source)
+    for (int i = tid; i < hw * hh; i += kThreads) {
+        const int hy = i / hw, hx = i - hy * hw;
+        const int gx = x0 - R + hx, gy = y0 - R + hy;
+        const bool in = gx >= 0 && gx < P.width && gy >= 0 && gy < P.height;
+        s_d[hy][hx] = in ? __ldg(C.src + size_t(gy) * C.src_pitch + gx) : uint16_t(0);
+    }
+    for (int i = tid; i < 3 * hw * hh; i += kThreads) {
+        const int hy = i / (3 * hw), b = i - hy * 3 * hw;
+        const int gx3 = 3 * (x0 - R) + b, gy = y0 - R + hy;
+        const bool in = gx3 >= 0 && gx3 < 3 * P.width && gy >= 0 && gy < P.height;
+        s_c[hy][b] = in ? __ldg(C.rgb + size_t(gy) * C.rgb_pitch + gx3) : uint8_t(0);
+    }
+    __syncthreads();
+    // phase 2: codes pass through; pixels without one are listed
+    for (int i = tid; i < kTileW * kTileH; i += kThreads) {
+        const int ty = i / kTileW, tx = i - ty * kTileW;
+        const int x = x0 + tx, y = y0 + ty;
+        if (x >= P.width || y >= P.height)
+            continue;
+        const uint16_t d = s_d[ty + R][tx + R];
+        if (d != 0)
+            C.dst[size_t(y) * C.dst_pitch + x] = d;
+        else
+            s_list[atomicAdd(&s_n, 1)] = uint16_t(i);
+    }
+    __syncthreads();
+    // phase 3: one listed pixel per thread at a time
+    const int n_holes = s_n;
+    for (int j = tid; j < n_holes; j += kThreads) {
+        const int i = s_list[j];
+        const int ty = i / kTileW, tx = i - ty * kTileW;
+        const int cy = ty + R, cx = tx + R;                     // centre in the halo tile
+        const uint32_t r0 = s_c[cy][3 * cx], g0 = s_c[cy][3 * cx + 1], b0 = s_c[cy][3 * cx + 2];
         float acc = 0.0f, wsum = 0.0f;
         int n = 0;
         for (int dy = -R; dy <= R; ++dy) {
-            const int yy = y + dy;
-            if (yy < 0 || yy >= P.height)
-                continue;
-            const uint16_t* drow = C.src + size_t(yy) * C.src_pitch;
-            const uint8_t* crow = C.rgb + size_t(yy) * C.rgb_pitch;
             for (int dx = -R; dx <= R; ++dx) {
-                const int xx = x + dx;
-                if (xx < 0 || xx >= P.width)
-                    continue;
-                const uint32_t q = __ldg(drow + xx);
+                const uint32_t q = s_d[cy + dy][cx + dx];
                 if (q < P.d_lo || q > P.d_hi || q == kDepthBg)
                     continue;
-                const uint8_t* cq = crow + 3 * size_t(xx);
-                const float w = __fmul_rn(
-                    __fmul_rn(__fmul_rn(P.s[(dy + R) * side + (dx + R)], P.c[absdiff(r0, __ldg(cq))]),
-                              P.c[absdiff(g0, __ldg(cq + 1))]),
-                    P.c[absdiff(b0, __ldg(cq + 2))]);
+                const uint8_t* cq = &s_c[cy + dy][3 * (cx + dx)];
+                const float w = __fmul_rn(__fmul_rn(__fmul_rn(P.s[(dy + R) * side + (dx + R)], P.c[absdiff(r0, cq[0])]),
+                                                    P.c[absdiff(g0, cq[1])]),
+                                          P.c[absdiff(b0, cq[2])]);
                 acc = __fadd_rn(acc, __fmul_rn(w, code_to_float(q)));
                 wsum = __fadd_rn(wsum, w);
                 ++n;
             }
         }
+        uint32_t out = 0u;
         if (n >= P.min_valid && wsum > 0.0f) {
             float v = floorf(__fadd_rn(__fdiv_rn(acc, wsum), 0.5f));
             v = fminf(fmaxf(v, float(P.d_lo)), float(P.d_hi));
             out = uint32_t(v);
         }
+        C.dst[size_t(y0 + ty) * C.dst_pitch + (x0 + tx)] = uint16_t(out);
     }
-    C.dst[size_t(y) * C.dst_pitch + x] = uint16_t(out);
 }
 
 }  // namespace
@@ -124,8 +158,9 @@ void jbf_params(const fvv_options& o, int width, int height, JbfParams* P)
 cudaError_t launch_jbf(const JbfParams& P, int n_cams, cudaStream_t stream)
 {
     if (n_cams <= 0 || P.width <= 0 || P.height <= 0) return cudaSuccess;
-    dim3 grid(unsigned((P.width + 31) / 32), unsigned((P.height + 7) / 8), unsigned(n_cams));
-    k_jbf<<<grid, dim3(32, 8), 0, stream>>>(P);
+    dim3 grid(unsigned((P.width + kTileW - 1) / kTileW), unsigned((P.height + kTileH - 1) / kTileH),
+              unsigned(n_cams));
+    k_jbf<<<grid, kThreads, 0, stream>>>(P);
     return cudaGetLastError();
 }
 
