@@ -49,6 +49,8 @@ __global__ void __launch_bounds__(kThreads) k_jbf(const JbfParams P)
     __shared__ uint16_t s_d[kHaloH][kHaloW];
     __shared__ uint8_t s_c[kHaloH][3 * kHaloW];
     __shared__ uint16_t s_list[kTileW * kTileH];
+    __shared__ float s_ws[(2 * kJbfMaxRadius + 1) * (2 * kJbfMaxRadius + 1)];
+    __shared__ float s_wc[256];
     __shared__ int s_n;
     const JbfCam& C = P.cam[blockIdx.z];
     const int R = P.radius, side = 2 * R + 1;
@@ -56,18 +58,27 @@ __global__ void __launch_bounds__(kThreads) k_jbf(const JbfParams P)
     const int hw = kTileW + 2 * R, hh = kTileH + 2 * R;
     const int tid = threadIdx.x;
     if (tid == 0) s_n = 0;
-    // phase 1: halo tile; outside the image a code of 0 (never a source)
-    for (int i = tid; i < hw * hh; i += kThreads) {
-        const int hy = i / hw, hx = i - hy * hw;
-        const int gx = x0 - R + hx, gy = y0 - R + hy;
-        const bool in = gx >= 0 && gx < P.width && gy >= 0 && gy < P.height;
-        s_d[hy][hx] = in ? __ldg(C.src + size_t(gy) * C.src_pitch + gx) : uint16_t(0);
-    }
-    for (int i = tid; i < 3 * hw * hh; i += kThreads) {
-        const int hy = i / (3 * hw), b = i - hy * 3 * hw;
-        const int gx3 = 3 * (x0 - R) + b, gy = y0 - R + hy;
-        const bool in = gx3 >= 0 && gx3 < 3 * P.width && gy >= 0 && gy < P.height;
-        s_c[hy][b] = in ? __ldg(C.rgb + size_t(gy) * C.rgb_pitch + gx3) : uint8_t(0);
+    // the weight tables in shared memory: the filtered pixels of a warp
+    // index them at different places, which parameter (constant) memory
+    // would serialise
+    for (int i = tid; i < side * side; i += kThreads) s_ws[i] = P.s[i];
+    for (int i = tid; i < 256; i += kThreads) s_wc[i] = P.c[i];
+    // phase 1: halo tile, a warp per row and its lanes along the row;
+    // outside the image a code of 0 (never a source)
+    const int warp = tid >> 5, lane = tid & 31;
+    for (int hy = warp; hy < hh; hy += kThreads / 32) {
+        const int gy = y0 - R + hy;
+        const bool row_in = gy >= 0 && gy < P.height;
+        const uint16_t* drow = C.src + size_t(row_in ? gy : 0) * C.src_pitch;
+        const uint8_t* crow = C.rgb + size_t(row_in ? gy : 0) * C.rgb_pitch;
+        for (int hx = lane; hx < hw; hx += 32) {
+            const int gx = x0 - R + hx;
+            s_d[hy][hx] = (row_in && gx >= 0 && gx < P.width) ? __ldg(drow + gx) : uint16_t(0);
+        }
+        for (int b = lane; b < 3 * hw; b += 32) {
+            const int gx3 = 3 * (x0 - R) + b;
+            s_c[hy][b] = (row_in && gx3 >= 0 && gx3 < 3 * P.width) ? __ldg(crow + gx3) : uint8_t(0);
+        }
     }
     __syncthreads();
     // phase 2: codes pass through; pixels without one are listed
@@ -98,9 +109,9 @@ __global__ void __launch_bounds__(kThreads) k_jbf(const JbfParams P)
                 if (q < P.d_lo || q > P.d_hi || q == kDepthBg)
                     continue;
                 const uint8_t* cq = &s_c[cy + dy][3 * (cx + dx)];
-                const float w = __fmul_rn(__fmul_rn(__fmul_rn(P.s[(dy + R) * side + (dx + R)], P.c[absdiff(r0, cq[0])]),
-                                                    P.c[absdiff(g0, cq[1])]),
-                                          P.c[absdiff(b0, cq[2])]);
+                const float w = __fmul_rn(__fmul_rn(__fmul_rn(s_ws[(dy + R) * side + (dx + R)], s_wc[absdiff(r0, cq[0])]),
+                                                    s_wc[absdiff(g0, cq[1])]),
+                                          s_wc[absdiff(b0, cq[2])]);
                 acc = __fadd_rn(acc, __fmul_rn(w, code_to_float(q)));
                 wsum = __fadd_rn(wsum, w);
                 ++n;
