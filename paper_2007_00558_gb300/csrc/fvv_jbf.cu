@@ -63,22 +63,42 @@ __global__ void __launch_bounds__(kThreads) k_jbf(const JbfParams P)
     // would serialise
     for (int i = tid; i < side * side; i += kThreads) s_ws[i] = P.s[i];
     for (int i = tid; i < 256; i += kThreads) s_wc[i] = P.c[i];
-    // phase 1: halo tile, a warp per row and its lanes along the row;
-    // outside the image a code of 0 (never a source)
+    // phase 1: halo tile, rows dealt to the warps and each row's elements to
+    // the lanes; every load of a thread is issued before any is stored, so
+    // they are in flight together.  Outside the image a code of 0 (never a
+    // source).
+    constexpr int kRows = (kHaloH + kThreads / 32 - 1) / (kThreads / 32);
+    constexpr int kDIt = (kHaloW + 31) / 32, kCIt = (3 * kHaloW + 31) / 32;
     const int warp = tid >> 5, lane = tid & 31;
-    for (int hy = warp; hy < hh; hy += kThreads / 32) {
-        const int gy = y0 - R + hy;
-        const bool row_in = gy >= 0 && gy < P.height;
+    uint32_t dv[kRows][kDIt], cv[kRows][kCIt];
+#pragma unroll
+    for (int r = 0; r < kRows; ++r) {
+        const int hy = warp + r * (kThreads / 32), gy = y0 - R + hy;
+        const bool row_in = hy < hh && gy >= 0 && gy < P.height;
         const uint16_t* drow = C.src + size_t(row_in ? gy : 0) * C.src_pitch;
         const uint8_t* crow = C.rgb + size_t(row_in ? gy : 0) * C.rgb_pitch;
-        for (int hx = lane; hx < hw; hx += 32) {
-            const int gx = x0 - R + hx;
-            s_d[hy][hx] = (row_in && gx >= 0 && gx < P.width) ? __ldg(drow + gx) : uint16_t(0);
+#pragma unroll
+        for (int j = 0; j < kDIt; ++j) {
+            const int hx = lane + 32 * j, gx = x0 - R + hx;
+            dv[r][j] = (row_in && hx < hw && gx >= 0 && gx < P.width) ? __ldg(drow + gx) : 0u;
         }
-        for (int b = lane; b < 3 * hw; b += 32) {
-            const int gx3 = 3 * (x0 - R) + b;
-            s_c[hy][b] = (row_in && gx3 >= 0 && gx3 < 3 * P.width) ? __ldg(crow + gx3) : uint8_t(0);
+#pragma unroll
+        for (int j = 0; j < kCIt; ++j) {
+            const int b = lane + 32 * j, gx3 = 3 * (x0 - R) + b;
+            cv[r][j] = (row_in && b < 3 * hw && gx3 >= 0 && gx3 < 3 * P.width) ? __ldg(crow + gx3) : 0u;
         }
+    }
+#pragma unroll
+    for (int r = 0; r < kRows; ++r) {
+        const int hy = warp + r * (kThreads / 32);
+        if (hy >= hh)
+            continue;
+#pragma unroll
+        for (int j = 0; j < kDIt; ++j)
+            if (lane + 32 * j < hw) s_d[hy][lane + 32 * j] = uint16_t(dv[r][j]);
+#pragma unroll
+        for (int j = 0; j < kCIt; ++j)
+            if (lane + 32 * j < 3 * hw) s_c[hy][lane + 32 * j] = uint8_t(cv[r][j]);
     }
     __syncthreads();
     // phase 2: codes pass through; pixels without one are listed
