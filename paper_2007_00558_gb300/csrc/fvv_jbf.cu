@@ -41,21 +41,23 @@ __device__ __forceinline__ uint32_t absdiff(uint32_t a, uint32_t b) { return a >
 // pixels out to the threads, so a tile's few holes are filtered by many
 // threads at once instead of idling the rest of their warps; each filtered
 // pixel walks its window in shared memory in the stated order.
+// The radius is a template parameter, so a filtered pixel's window loop
+// unrolls and its shared-memory loads are in flight together.
 constexpr int kTileW = 64, kTileH = 16, kThreads = 256;
-constexpr int kHaloW = kTileW + 2 * kJbfMaxRadius, kHaloH = kTileH + 2 * kJbfMaxRadius;
 
+template <int R>
 __global__ void __launch_bounds__(kThreads) k_jbf(const JbfParams P)
 {
-    __shared__ uint16_t s_d[kHaloH][kHaloW];
-    __shared__ uint8_t s_c[kHaloH][3 * kHaloW];
+    constexpr int side = 2 * R + 1;
+    constexpr int hw = kTileW + 2 * R, hh = kTileH + 2 * R;
+    __shared__ uint16_t s_d[hh][hw];
+    __shared__ uint8_t s_c[hh][3 * hw];
     __shared__ uint16_t s_list[kTileW * kTileH];
-    __shared__ float s_ws[(2 * kJbfMaxRadius + 1) * (2 * kJbfMaxRadius + 1)];
+    __shared__ float s_ws[side * side];
     __shared__ float s_wc[256];
     __shared__ int s_n;
     const JbfCam& C = P.cam[blockIdx.z];
-    const int R = P.radius, side = 2 * R + 1;
     const int x0 = blockIdx.x * kTileW, y0 = blockIdx.y * kTileH;
-    const int hw = kTileW + 2 * R, hh = kTileH + 2 * R;
     const int tid = threadIdx.x;
     if (tid == 0) s_n = 0;
     // the weight tables in shared memory: the filtered pixels of a warp
@@ -67,8 +69,8 @@ __global__ void __launch_bounds__(kThreads) k_jbf(const JbfParams P)
     // the lanes; every load of a thread is issued before any is stored, so
     // they are in flight together.  Outside the image a code of 0 (never a
     // source).
-    constexpr int kRows = (kHaloH + kThreads / 32 - 1) / (kThreads / 32);
-    constexpr int kDIt = (kHaloW + 31) / 32, kCIt = (3 * kHaloW + 31) / 32;
+    constexpr int kRows = (hh + kThreads / 32 - 1) / (kThreads / 32);
+    constexpr int kDIt = (hw + 31) / 32, kCIt = (3 * hw + 31) / 32;
     const int warp = tid >> 5, lane = tid & 31;
     uint32_t dv[kRows][kDIt], cv[kRows][kCIt];
 #pragma unroll
@@ -123,7 +125,9 @@ __global__ void __launch_bounds__(kThreads) k_jbf(const JbfParams P)
         const uint32_t r0 = s_c[cy][3 * cx], g0 = s_c[cy][3 * cx + 1], b0 = s_c[cy][3 * cx + 2];
         float acc = 0.0f, wsum = 0.0f;
         int n = 0;
+#pragma unroll
         for (int dy = -R; dy <= R; ++dy) {
+#pragma unroll
             for (int dx = -R; dx <= R; ++dx) {
                 const uint32_t q = s_d[cy + dy][cx + dx];
                 if (q < P.d_lo || q > P.d_hi || q == kDepthBg)
@@ -191,7 +195,16 @@ cudaError_t launch_jbf(const JbfParams& P, int n_cams, cudaStream_t stream)
     if (n_cams <= 0 || P.width <= 0 || P.height <= 0) return cudaSuccess;
     dim3 grid(unsigned((P.width + kTileW - 1) / kTileW), unsigned((P.height + kTileH - 1) / kTileH),
               unsigned(n_cams));
-    k_jbf<<<grid, kThreads, 0, stream>>>(P);
+    switch (P.radius) {
+    case 1: k_jbf<1><<<grid, kThreads, 0, stream>>>(P); break;
+    case 2: k_jbf<2><<<grid, kThreads, 0, stream>>>(P); break;
+    case 3: k_jbf<3><<<grid, kThreads, 0, stream>>>(P); break;
+    case 4: k_jbf<4><<<grid, kThreads, 0, stream>>>(P); break;
+    case 5: k_jbf<5><<<grid, kThreads, 0, stream>>>(P); break;
+    case 6: k_jbf<6><<<grid, kThreads, 0, stream>>>(P); break;
+    case 7: k_jbf<7><<<grid, kThreads, 0, stream>>>(P); break;
+    default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 
