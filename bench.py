@@ -64,6 +64,8 @@ def parse_args():
                    help="length of the Poisson multi-viewer run")
     p.add_argument("--no-refine", action="store_true", help="skip the refinement-network measurement")
     p.add_argument("--no-layered", action="store_true", help="skip the layered FG/BG measurement")
+    p.add_argument("--jbf-only", action="store_true",
+                   help="only the depth pre-filter measurement; for profiling")
     p.add_argument("--layered-only", action="store_true",
                    help="only the layered FG/BG measurement (--steps/--warmup/--batch/--slots); for profiling")
     p.add_argument("--refine-steps", type=int, default=600, help="LOO training steps before measuring")
@@ -1017,6 +1019,15 @@ def main():
         return run_reference(args)
     if args.net_forward:
         return net_forward(args)
+    if args.jbf_only:
+        import torch
+        import synthetic as S
+        from paper_2007_00558_gb300 import fvv as F
+        F.load()
+        stream = torch.cuda.Stream()
+        torch.cuda.set_stream(stream)
+        print(json.dumps(jbf_bench(F, S.workload(WORKLOAD), stream)))
+        return 0
     if args.layered_only:
         import torch
         from paper_2007_00558_gb300 import fvv as F
