@@ -35,85 +35,105 @@ __device__ __forceinline__ float code_to_float(uint32_t d)   // exact for d < 2^
 __device__ __forceinline__ uint32_t absdiff(uint32_t a, uint32_t b) { return a > b ? a - b : b - a; }
 
 // A CTA filters a kTileW x kTileH tile of camera blockIdx.z.  Phase 1
-// stages the tile and its halo (codes and colour bytes) in shared memory
-// with coalesced loads.  Phase 2 writes every pixel with a code straight
-// through and lists the pixels without one.  Phase 3 deals the listed
-// pixels out to the threads, so a tile's few holes are filtered by many
-// threads at once instead of idling the rest of their warps; each filtered
-// pixel walks its window in shared memory in the stated order.
-// The radius is a template parameter, so a filtered pixel's window loop
-// unrolls and its shared-memory loads are in flight together.
+// stages the tile and its halo (codes and colour bytes) in shared memory:
+// the tile's own columns as 16-byte loads and stores when the rows are
+// 16-byte aligned, the halo columns and ragged edges element by element.
+// Phase 2 writes the tile's codes back out 8 at a time and lists the pixels
+// without one.  Phase 3 deals the listed pixels out to the threads, so a
+// tile's few holes are filtered by many threads at once instead of idling
+// the rest of their warps; each filtered pixel walks its window in shared
+// memory in the stated order (the radius is a template parameter, so the
+// window unrolls and its loads are in flight together) and overwrites its
+// output.
 constexpr int kTileW = 64, kTileH = 16, kThreads = 256;
+constexpr int kDM = 8, kCM = 32;          // left margins of the staged rows: pixels, colour bytes
+constexpr int kDW = kDM + kTileW + kDM;   // staged code row, pixels
+constexpr int kCW = kCM + 3 * kTileW + kCM;   // staged colour row, bytes
+static_assert(kJbfMaxRadius <= kDM && 3 * kJbfMaxRadius <= kCM, "halo wider than the margins");
 
 template <int R>
 __global__ void __launch_bounds__(kThreads) k_jbf(const JbfParams P)
 {
     constexpr int side = 2 * R + 1;
-    constexpr int hw = kTileW + 2 * R, hh = kTileH + 2 * R;
-    __shared__ uint16_t s_d[hh][hw];
-    __shared__ uint8_t s_c[hh][3 * hw];
+    constexpr int hh = kTileH + 2 * R;
+    __shared__ __align__(16) uint16_t s_d[hh][kDW];
+    __shared__ __align__(16) uint8_t s_c[hh][kCW];
     __shared__ uint16_t s_list[kTileW * kTileH];
     __shared__ float s_ws[side * side];
     __shared__ float s_wc[256];
     __shared__ int s_n;
     const JbfCam& C = P.cam[blockIdx.z];
     const int x0 = blockIdx.x * kTileW, y0 = blockIdx.y * kTileH;
-    const int tid = threadIdx.x;
+    const int W = P.width;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const bool vec = C.vec != 0;
     if (tid == 0) s_n = 0;
     // the weight tables in shared memory: the filtered pixels of a warp
     // index them at different places, which parameter (constant) memory
     // would serialise
     for (int i = tid; i < side * side; i += kThreads) s_ws[i] = P.s[i];
     for (int i = tid; i < 256; i += kThreads) s_wc[i] = P.c[i];
-    // phase 1: halo tile, rows dealt to the warps and each row's elements to
-    // the lanes; every load of a thread is issued before any is stored, so
-    // they are in flight together.  Outside the image a code of 0 (never a
-    // source).
-    constexpr int kRows = (hh + kThreads / 32 - 1) / (kThreads / 32);
-    constexpr int kDIt = (hw + 31) / 32, kCIt = (3 * hw + 31) / 32;
-    const int warp = tid >> 5, lane = tid & 31;
-    uint32_t dv[kRows][kDIt], cv[kRows][kCIt];
-#pragma unroll
-    for (int r = 0; r < kRows; ++r) {
-        const int hy = warp + r * (kThreads / 32), gy = y0 - R + hy;
-        const bool row_in = hy < hh && gy >= 0 && gy < P.height;
+    // phase 1: a warp per staged row.  Tasks 0-7: the tile's codes, 8 pixels
+    // each; 8-19: its colour, 16 bytes each; then the halo elements (R codes
+    // and 3R colour bytes on each side).  Outside the image a code of 0
+    // (never a source) and colour 0.
+    constexpr int kTasks = 8 + 12 + 8 * R;
+    for (int hy = warp; hy < hh; hy += kThreads / 32) {
+        const int gy = y0 - R + hy;
+        const bool row_in = gy >= 0 && gy < P.height;
         const uint16_t* drow = C.src + size_t(row_in ? gy : 0) * C.src_pitch;
         const uint8_t* crow = C.rgb + size_t(row_in ? gy : 0) * C.rgb_pitch;
+        for (int t = lane; t < kTasks; t += 32) {
+            if (t < 8) {
+                const int x = x0 + 8 * t;
+                uint16_t* dst = &s_d[hy][kDM + 8 * t];
+                if (row_in && vec && x + 8 <= W) {
+                    *reinterpret_cast<uint4*>(dst) = __ldg(reinterpret_cast<const uint4*>(drow + x));
+                } else {
 #pragma unroll
-        for (int j = 0; j < kDIt; ++j) {
-            const int hx = lane + 32 * j, gx = x0 - R + hx;
-            dv[r][j] = (row_in && hx < hw && gx >= 0 && gx < P.width) ? __ldg(drow + gx) : 0u;
+                    for (int e = 0; e < 8; ++e) dst[e] = (row_in && x + e < W) ? __ldg(drow + x + e) : uint16_t(0);
+                }
+            } else if (t < 20) {
+                const int b = 3 * x0 + 16 * (t - 8);
+                uint8_t* dst = &s_c[hy][kCM + 16 * (t - 8)];
+                if (row_in && vec && b + 16 <= 3 * W) {
+                    *reinterpret_cast<uint4*>(dst) = __ldg(reinterpret_cast<const uint4*>(crow + b));
+                } else {
+#pragma unroll
+                    for (int e = 0; e < 16; ++e) dst[e] = (row_in && b + e < 3 * W) ? __ldg(crow + b + e) : uint8_t(0);
+                }
+            } else if (t < 20 + 2 * R) {
+                const int h = t - 20;                              // left R codes, then right R
+                const int tx = h < R ? h - R : kTileW + (h - R);
+                const int x = x0 + tx;
+                s_d[hy][kDM + tx] = (row_in && x >= 0 && x < W) ? __ldg(drow + x) : uint16_t(0);
+            } else {
+                const int h = t - 20 - 2 * R;                      // left 3R bytes, then right 3R
+                const int tb = h < 3 * R ? h - 3 * R : 3 * kTileW + (h - 3 * R);
+                const int b = 3 * x0 + tb;
+                s_c[hy][kCM + tb] = (row_in && b >= 0 && b < 3 * W) ? __ldg(crow + b) : uint8_t(0);
+            }
         }
-#pragma unroll
-        for (int j = 0; j < kCIt; ++j) {
-            const int b = lane + 32 * j, gx3 = 3 * (x0 - R) + b;
-            cv[r][j] = (row_in && b < 3 * hw && gx3 >= 0 && gx3 < 3 * P.width) ? __ldg(crow + gx3) : 0u;
-        }
-    }
-#pragma unroll
-    for (int r = 0; r < kRows; ++r) {
-        const int hy = warp + r * (kThreads / 32);
-        if (hy >= hh)
-            continue;
-#pragma unroll
-        for (int j = 0; j < kDIt; ++j)
-            if (lane + 32 * j < hw) s_d[hy][lane + 32 * j] = uint16_t(dv[r][j]);
-#pragma unroll
-        for (int j = 0; j < kCIt; ++j)
-            if (lane + 32 * j < 3 * hw) s_c[hy][lane + 32 * j] = uint8_t(cv[r][j]);
     }
     __syncthreads();
-    // phase 2: codes pass through; pixels without one are listed
-    for (int i = tid; i < kTileW * kTileH; i += kThreads) {
-        const int ty = i / kTileW, tx = i - ty * kTileW;
-        const int x = x0 + tx, y = y0 + ty;
-        if (x >= P.width || y >= P.height)
-            continue;
-        const uint16_t d = s_d[ty + R][tx + R];
-        if (d != 0)
-            C.dst[size_t(y) * C.dst_pitch + x] = d;
-        else
-            s_list[atomicAdd(&s_n, 1)] = uint16_t(i);
+    // phase 2: the tile's codes go out 8 at a time (pixels without one as
+    // 0 for now) and those pixels are listed
+    if (tid < kTileH * (kTileW / 8)) {
+        const int ty = tid >> 3, c8 = tid & 7;
+        const int y = y0 + ty, x = x0 + 8 * c8;
+        if (y < P.height && x < W) {
+            const uint4 v = *reinterpret_cast<const uint4*>(&s_d[ty + R][kDM + 8 * c8]);
+            const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+            uint16_t* orow = C.dst + size_t(y) * C.dst_pitch;
+            const int ne = min(8, W - x);
+            if (vec && ne == 8)
+                *reinterpret_cast<uint4*>(orow + x) = v;
+            for (int e = 0; e < ne; ++e) {
+                const uint16_t d = uint16_t(w[e >> 1] >> (16 * (e & 1)));
+                if (!(vec && ne == 8)) orow[x + e] = d;
+                if (d == 0) s_list[atomicAdd(&s_n, 1)] = uint16_t(ty * kTileW + 8 * c8 + e);
+            }
+        }
     }
     __syncthreads();
     // phase 3: one listed pixel per thread at a time
@@ -121,18 +141,19 @@ __global__ void __launch_bounds__(kThreads) k_jbf(const JbfParams P)
     for (int j = tid; j < n_holes; j += kThreads) {
         const int i = s_list[j];
         const int ty = i / kTileW, tx = i - ty * kTileW;
-        const int cy = ty + R, cx = tx + R;                     // centre in the halo tile
-        const uint32_t r0 = s_c[cy][3 * cx], g0 = s_c[cy][3 * cx + 1], b0 = s_c[cy][3 * cx + 2];
+        const int cy = ty + R;                                     // centre row in the staged tile
+        const uint8_t* c0 = &s_c[cy][kCM + 3 * tx];
+        const uint32_t r0 = c0[0], g0 = c0[1], b0 = c0[2];
         float acc = 0.0f, wsum = 0.0f;
         int n = 0;
 #pragma unroll
         for (int dy = -R; dy <= R; ++dy) {
 #pragma unroll
             for (int dx = -R; dx <= R; ++dx) {
-                const uint32_t q = s_d[cy + dy][cx + dx];
+                const uint32_t q = s_d[cy + dy][kDM + tx + dx];
                 if (q < P.d_lo || q > P.d_hi || q == kDepthBg)
                     continue;
-                const uint8_t* cq = &s_c[cy + dy][3 * (cx + dx)];
+                const uint8_t* cq = &s_c[cy + dy][kCM + 3 * (tx + dx)];
                 const float w = __fmul_rn(__fmul_rn(__fmul_rn(s_ws[(dy + R) * side + (dx + R)], s_wc[absdiff(r0, cq[0])]),
                                                     s_wc[absdiff(g0, cq[1])]),
                                           s_wc[absdiff(b0, cq[2])]);
@@ -147,7 +168,8 @@ __global__ void __launch_bounds__(kThreads) k_jbf(const JbfParams P)
             v = fminf(fmaxf(v, float(P.d_lo)), float(P.d_hi));
             out = uint32_t(v);
         }
-        C.dst[size_t(y0 + ty) * C.dst_pitch + (x0 + tx)] = uint16_t(out);
+        if (out != 0u)
+            C.dst[size_t(y0 + ty) * C.dst_pitch + (x0 + tx)] = uint16_t(out);
     }
 }
 
@@ -190,9 +212,20 @@ void jbf_params(const fvv_options& o, int width, int height, JbfParams* P)
     for (int t = 0; t < 256; ++t) P->c[t] = float(std::exp(-double(t * t) / (2.0 * sc * sc)));
 }
 
-cudaError_t launch_jbf(const JbfParams& P, int n_cams, cudaStream_t stream)
+cudaError_t launch_jbf(const JbfParams& P_in, int n_cams, cudaStream_t stream)
 {
-    if (n_cams <= 0 || P.width <= 0 || P.height <= 0) return cudaSuccess;
+    if (n_cams <= 0 || P_in.width <= 0 || P_in.height <= 0) return cudaSuccess;
+    if (n_cams > kJbfMaxCams) return cudaErrorInvalidValue;
+    // 16-byte accesses where every row of a camera starts 16-byte aligned
+    // (a tile's first column sits 128 code bytes and 192 colour bytes on)
+    JbfParams P = P_in;
+    auto a16 = [](const void* p, int64_t pitch_bytes) {
+        return (reinterpret_cast<uintptr_t>(p) & 15u) == 0 && pitch_bytes % 16 == 0;
+    };
+    for (int k = 0; k < n_cams; ++k) {
+        JbfCam& c = P.cam[k];
+        c.vec = a16(c.rgb, c.rgb_pitch) && a16(c.src, c.src_pitch * 2) && a16(c.dst, c.dst_pitch * 2) ? 1 : 0;
+    }
     dim3 grid(unsigned((P.width + kTileW - 1) / kTileW), unsigned((P.height + kTileH - 1) / kTileH),
               unsigned(n_cams));
     switch (P.radius) {

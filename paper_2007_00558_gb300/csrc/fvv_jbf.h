@@ -22,6 +22,8 @@ struct JbfCam {
     int64_t src_pitch;
     uint16_t* dst;
     int64_t dst_pitch;
+    int32_t vec;                // 1: rgb, src and dst rows all start 16-byte aligned (set by launch_jbf)
+    int32_t pad;
 };
 
 // Everything a launch needs, passed by value: the weight tables (FP32,
