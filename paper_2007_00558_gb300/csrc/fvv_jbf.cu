@@ -32,8 +32,6 @@ __device__ __forceinline__ float code_to_float(uint32_t d)   // exact for d < 2^
     return __fsub_rn(__uint_as_float(0x4B000000u | d), 8388608.0f);
 }
 
-__device__ __forceinline__ uint32_t absdiff(uint32_t a, uint32_t b) { return a > b ? a - b : b - a; }
-
 // A CTA filters a kTileW x kTileH tile of camera blockIdx.z.  Phase 1
 // stages the tile and its halo (codes and colour bytes) in shared memory:
 // the tile's own columns as 16-byte loads and stores when the rows are
@@ -58,6 +56,10 @@ __global__ void __launch_bounds__(kThreads) k_jbf(const JbfParams P)
     constexpr int hh = kTileH + 2 * R;
     __shared__ __align__(16) uint16_t s_d[hh][kDW];
     __shared__ __align__(16) uint8_t s_c[hh][kCW];
+    // per staged pixel: the code as FP32 (-1 when it is no source) and the
+    // colour packed R | G << 8 | B << 16, for the window walks of phase 3
+    __shared__ float s_df[hh][kDW];
+    __shared__ uint32_t s_cc[hh][kDW];
     __shared__ uint16_t s_list[kTileW * kTileH];
     __shared__ float s_ws[side * side];
     __shared__ float s_wc[256];
@@ -116,6 +118,16 @@ __global__ void __launch_bounds__(kThreads) k_jbf(const JbfParams P)
         }
     }
     __syncthreads();
+    // phase 1b: sources and packed colour of every staged pixel
+    constexpr int sw = kTileW + 2 * R;
+    for (int i = tid; i < hh * sw; i += kThreads) {
+        const int hy = i / sw, col = kDM - R + (i - hy * sw);
+        const uint32_t q = s_d[hy][col];
+        const bool src = q >= P.d_lo && q <= P.d_hi && q != kDepthBg;
+        s_df[hy][col] = src ? code_to_float(q) : -1.0f;
+        const uint8_t* c = &s_c[hy][kCM + 3 * (col - kDM)];
+        s_cc[hy][col] = uint32_t(c[0]) | (uint32_t(c[1]) << 8) | (uint32_t(c[2]) << 16);
+    }
     // phase 2: the tile's codes go out 8 at a time (pixels without one as
     // 0 for now) and those pixels are listed
     if (tid < kTileH * (kTileW / 8)) {
@@ -141,23 +153,22 @@ __global__ void __launch_bounds__(kThreads) k_jbf(const JbfParams P)
     for (int j = tid; j < n_holes; j += kThreads) {
         const int i = s_list[j];
         const int ty = i / kTileW, tx = i - ty * kTileW;
-        const int cy = ty + R;                                     // centre row in the staged tile
-        const uint8_t* c0 = &s_c[cy][kCM + 3 * tx];
-        const uint32_t r0 = c0[0], g0 = c0[1], b0 = c0[2];
+        const int cy = ty + R, cx = kDM + tx;                      // centre in the staged tile
+        const uint32_t c0 = s_cc[cy][cx];
         float acc = 0.0f, wsum = 0.0f;
         int n = 0;
 #pragma unroll
         for (int dy = -R; dy <= R; ++dy) {
 #pragma unroll
             for (int dx = -R; dx <= R; ++dx) {
-                const uint32_t q = s_d[cy + dy][kDM + tx + dx];
-                if (q < P.d_lo || q > P.d_hi || q == kDepthBg)
+                const float qf = s_df[cy + dy][cx + dx];
+                if (qf < 0.0f)
                     continue;
-                const uint8_t* cq = &s_c[cy + dy][kCM + 3 * (tx + dx)];
-                const float w = __fmul_rn(__fmul_rn(__fmul_rn(s_ws[(dy + R) * side + (dx + R)], s_wc[absdiff(r0, cq[0])]),
-                                                    s_wc[absdiff(g0, cq[1])]),
-                                          s_wc[absdiff(b0, cq[2])]);
-                acc = __fadd_rn(acc, __fmul_rn(w, code_to_float(q)));
+                const uint32_t ad = __vabsdiffu4(c0, s_cc[cy + dy][cx + dx]);   // |dR|, |dG|, |dB| bytes
+                const float w = __fmul_rn(__fmul_rn(__fmul_rn(s_ws[(dy + R) * side + (dx + R)], s_wc[ad & 255u]),
+                                                    s_wc[(ad >> 8) & 255u]),
+                                          s_wc[(ad >> 16) & 255u]);
+                acc = __fadd_rn(acc, __fmul_rn(w, qf));
                 wsum = __fadd_rn(wsum, w);
                 ++n;
             }
