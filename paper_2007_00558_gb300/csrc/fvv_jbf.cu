@@ -50,7 +50,7 @@ constexpr int kCW = kCM + 3 * kTileW + kCM;   // staged colour row, bytes
 static_assert(kJbfMaxRadius <= kDM && 3 * kJbfMaxRadius <= kCM, "halo wider than the margins");
 
 template <int R>
-__global__ void __launch_bounds__(kThreads) k_jbf(const JbfParams P)
+__global__ void __launch_bounds__(kThreads, 4) k_jbf(const JbfParams P)
 {
     constexpr int side = 2 * R + 1;
     constexpr int hh = kTileH + 2 * R;
@@ -161,16 +161,19 @@ __global__ void __launch_bounds__(kThreads) k_jbf(const JbfParams P)
         for (int dy = -R; dy <= R; ++dy) {
 #pragma unroll
             for (int dx = -R; dx <= R; ++dx) {
+                // branch-free: a neighbour that is no source adds +0 to the
+                // non-negative sums, which leaves them unchanged, so the
+                // result equals skipping it, and every iteration's loads can
+                // be issued ahead of the chain of additions
                 const float qf = s_df[cy + dy][cx + dx];
-                if (qf < 0.0f)
-                    continue;
+                const bool ok = qf >= 0.0f;
                 const uint32_t ad = __vabsdiffu4(c0, s_cc[cy + dy][cx + dx]);   // |dR|, |dG|, |dB| bytes
                 const float w = __fmul_rn(__fmul_rn(__fmul_rn(s_ws[(dy + R) * side + (dx + R)], s_wc[ad & 255u]),
                                                     s_wc[(ad >> 8) & 255u]),
                                           s_wc[(ad >> 16) & 255u]);
-                acc = __fadd_rn(acc, __fmul_rn(w, qf));
-                wsum = __fadd_rn(wsum, w);
-                ++n;
+                acc = __fadd_rn(acc, ok ? __fmul_rn(w, qf) : 0.0f);
+                wsum = __fadd_rn(wsum, ok ? w : 0.0f);
+                n += ok ? 1 : 0;
             }
         }
         uint32_t out = 0u;
