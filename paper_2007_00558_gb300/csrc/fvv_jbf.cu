@@ -50,7 +50,7 @@ constexpr int kCW = kCM + 3 * kTileW + kCM;   // staged colour row, bytes
 static_assert(kJbfMaxRadius <= kDM && 3 * kJbfMaxRadius <= kCM, "halo wider than the margins");
 
 template <int R>
-__global__ void __launch_bounds__(kThreads, 4) k_jbf(const JbfParams P)
+__global__ void __launch_bounds__(kThreads) k_jbf(const JbfParams P)
 {
     constexpr int side = 2 * R + 1;
     constexpr int hh = kTileH + 2 * R;
@@ -58,11 +58,15 @@ __global__ void __launch_bounds__(kThreads, 4) k_jbf(const JbfParams P)
     __shared__ __align__(16) uint8_t s_c[hh][kCW];
     // per staged pixel: the code as FP32 (-1 when it is no source) and the
     // colour packed R | G << 8 | B << 16, for the window walks of phase 3
-    __shared__ float s_df[hh][kDW];
-    __shared__ uint32_t s_cc[hh][kDW];
+    // (rows padded by a word so that neighbouring rows fall in other banks)
+    __shared__ float s_df[hh][kDW + 1];
+    __shared__ uint32_t s_cc[hh][kDW + 1];
     __shared__ uint16_t s_list[kTileW * kTileH];
     __shared__ float s_ws[side * side];
-    __shared__ float s_wc[256];
+    // the colour table 8 times over, entry t's copies side by side: a lane
+    // reads copy lane & 7, which spreads a warp's scattered lookups over
+    // the banks
+    __shared__ float s_wc[256 * 8];
     __shared__ int s_n;
     const JbfCam& C = P.cam[blockIdx.z];
     const int x0 = blockIdx.x * kTileW, y0 = blockIdx.y * kTileH;
@@ -74,7 +78,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_jbf(const JbfParams P)
     // index them at different places, which parameter (constant) memory
     // would serialise
     for (int i = tid; i < side * side; i += kThreads) s_ws[i] = P.s[i];
-    for (int i = tid; i < 256; i += kThreads) s_wc[i] = P.c[i];
+    for (int i = tid; i < 256 * 8; i += kThreads) s_wc[i] = P.c[i >> 3];
     // phase 1: a warp per staged row.  Tasks 0-7: the tile's codes, 8 pixels
     // each; 8-19: its colour, 16 bytes each; then the halo elements (R codes
     // and 3R colour bytes on each side).  Outside the image a code of 0
@@ -155,25 +159,23 @@ __global__ void __launch_bounds__(kThreads, 4) k_jbf(const JbfParams P)
         const int ty = i / kTileW, tx = i - ty * kTileW;
         const int cy = ty + R, cx = kDM + tx;                      // centre in the staged tile
         const uint32_t c0 = s_cc[cy][cx];
+        const float* wc = s_wc + (threadIdx.x & 7);
         float acc = 0.0f, wsum = 0.0f;
         int n = 0;
 #pragma unroll
         for (int dy = -R; dy <= R; ++dy) {
 #pragma unroll
             for (int dx = -R; dx <= R; ++dx) {
-                // branch-free: a neighbour that is no source adds +0 to the
-                // non-negative sums, which leaves them unchanged, so the
-                // result equals skipping it, and every iteration's loads can
-                // be issued ahead of the chain of additions
                 const float qf = s_df[cy + dy][cx + dx];
-                const bool ok = qf >= 0.0f;
+                if (qf < 0.0f)
+                    continue;
                 const uint32_t ad = __vabsdiffu4(c0, s_cc[cy + dy][cx + dx]);   // |dR|, |dG|, |dB| bytes
-                const float w = __fmul_rn(__fmul_rn(__fmul_rn(s_ws[(dy + R) * side + (dx + R)], s_wc[ad & 255u]),
-                                                    s_wc[(ad >> 8) & 255u]),
-                                          s_wc[(ad >> 16) & 255u]);
-                acc = __fadd_rn(acc, ok ? __fmul_rn(w, qf) : 0.0f);
-                wsum = __fadd_rn(wsum, ok ? w : 0.0f);
-                n += ok ? 1 : 0;
+                const float w = __fmul_rn(__fmul_rn(__fmul_rn(s_ws[(dy + R) * side + (dx + R)], wc[(ad & 255u) * 8]),
+                                                    wc[((ad >> 8) & 255u) * 8]),
+                                          wc[((ad >> 16) & 255u) * 8]);
+                acc = __fadd_rn(acc, __fmul_rn(w, qf));
+                wsum = __fadd_rn(wsum, w);
+                ++n;
             }
         }
         uint32_t out = 0u;
