@@ -63,10 +63,7 @@ __global__ void __launch_bounds__(kThreads) k_jbf(const JbfParams P)
     __shared__ uint32_t s_cc[hh][kDW + 1];
     __shared__ uint16_t s_list[kTileW * kTileH];
     __shared__ float s_ws[side * side];
-    // the colour table 8 times over, entry t's copies side by side: a lane
-    // reads copy lane & 7, which spreads a warp's scattered lookups over
-    // the banks
-    __shared__ float s_wc[256 * 8];
+    __shared__ float s_wc[256];
     __shared__ int s_n;
     const JbfCam& C = P.cam[blockIdx.z];
     const int x0 = blockIdx.x * kTileW, y0 = blockIdx.y * kTileH;
@@ -78,7 +75,7 @@ __global__ void __launch_bounds__(kThreads) k_jbf(const JbfParams P)
     // index them at different places, which parameter (constant) memory
     // would serialise
     for (int i = tid; i < side * side; i += kThreads) s_ws[i] = P.s[i];
-    for (int i = tid; i < 256 * 8; i += kThreads) s_wc[i] = P.c[i >> 3];
+    for (int i = tid; i < 256; i += kThreads) s_wc[i] = P.c[i];
     // phase 1: a warp per staged row.  Tasks 0-7: the tile's codes, 8 pixels
     // each; 8-19: its colour, 16 bytes each; then the halo elements (R codes
     // and 3R colour bytes on each side).  Outside the image a code of 0
@@ -159,7 +156,6 @@ __global__ void __launch_bounds__(kThreads) k_jbf(const JbfParams P)
         const int ty = i / kTileW, tx = i - ty * kTileW;
         const int cy = ty + R, cx = kDM + tx;                      // centre in the staged tile
         const uint32_t c0 = s_cc[cy][cx];
-        const float* wc = s_wc + (threadIdx.x & 7);
         float acc = 0.0f, wsum = 0.0f;
         int n = 0;
 #pragma unroll
@@ -170,9 +166,9 @@ __global__ void __launch_bounds__(kThreads) k_jbf(const JbfParams P)
                 if (qf < 0.0f)
                     continue;
                 const uint32_t ad = __vabsdiffu4(c0, s_cc[cy + dy][cx + dx]);   // |dR|, |dG|, |dB| bytes
-                const float w = __fmul_rn(__fmul_rn(__fmul_rn(s_ws[(dy + R) * side + (dx + R)], wc[(ad & 255u) * 8]),
-                                                    wc[((ad >> 8) & 255u) * 8]),
-                                          wc[((ad >> 16) & 255u) * 8]);
+                const float w = __fmul_rn(__fmul_rn(__fmul_rn(s_ws[(dy + R) * side + (dx + R)], s_wc[ad & 255u]),
+                                                    s_wc[(ad >> 8) & 255u]),
+                                          s_wc[(ad >> 16) & 255u]);
                 acc = __fadd_rn(acc, __fmul_rn(w, qf));
                 wsum = __fadd_rn(wsum, w);
                 ++n;
