@@ -318,6 +318,29 @@ def profiled_instructions(kernel):
     return float(m.group(1))
 
 
+def jbf_source_sha():
+    h = hashlib.sha256()
+    for f in ("fvv_jbf.cu", "fvv_jbf.h"):
+        with open(os.path.join(ROOT, "paper_2007_00558_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def jbf_profile():
+    """(warp instructions, DRAM bytes) per frame from the committed ncu
+    summary of the pre-filter kernel, or None once its source changed."""
+    try:
+        text = open(os.path.join(ROOT, "profiles", "jbf_9cam_1280x720.txt")).read()
+    except OSError:
+        return None
+    wi = re.search(r"^warp_instructions_per_frame:\s*([0-9.eE+]+)", text, re.M)
+    db = re.search(r"^dram_bytes_per_frame:\s*([0-9.eE+]+)", text, re.M)
+    sh = re.search(r"^kernel_source_sha:\s*([0-9a-f]+)", text, re.M)
+    if not wi or not db or not sh or sh.group(1) != jbf_source_sha():
+        return None
+    return float(wi.group(1)), float(db.group(1))
+
+
 def issue_roofline(kernel, views_per_launch, avg_launch_s, sm_mhz, n_sms):
     """Instruction-issue roofline of an issue-bound kernel: warp instructions
     per launch / launch time against n_sms x 4 schedulers x 1 warp
@@ -680,6 +703,7 @@ def jbf_bench(F, wl, stream, reps=20):
     rgb_h = torch.from_numpy(np.ascontiguousarray(wl["rgb"])).pin_memory()
     dep_h = torch.from_numpy(np.ascontiguousarray(wl["depth"]).view(np.int16)).pin_memory()
     res = {}
+    clocks = ClockSampler(torch.cuda.current_device())
     for radius in (3, 0):
         ctx = F.fvv_create(F.rig(cams, wl["look_at"]), F.fvv_default_options(frame_slots=4, jbf_radius=radius))
         try:
@@ -688,22 +712,44 @@ def jbf_bench(F, wl, stream, reps=20):
             torch.cuda.synchronize()
             F.fvv_profile_read(ctx, reset=True)
             F.fvv_profile_enable(ctx, True)
+            if radius:
+                clocks.start()
+                time.sleep(0.2)
+                clocks.mark("start")
             t0 = time.perf_counter()
             for t in range(reps):
                 F.fvv_upload_frames(ctx, rgb_h, H * W * 3, W * 3, dep_h, H * W * 2, W * 2, 3 + t, stream)
                 torch.cuda.synchronize()
             res[radius] = ((time.perf_counter() - t0) * 1e3 / reps, F.fvv_profile_read(ctx, reset=True))
+            if radius:
+                clocks.mark("stop")
+                clocks.stop()
         finally:
             F.fvv_destroy(ctx)
     st = res[3][1]["jbf"]
     us = 1e3 * st[2] / st[1] / K
     gbs = 7.0 * H * W / (us * 1e-6) / 1e9
     peak, src = measured_peaks()
+    # the filter's bound is instruction issue in the windows of the pixels
+    # without depth (counters from the committed ncu summary)
+    prof = jbf_profile()
+    issue = None
+    if prof is not None:
+        clk = clocks.summary().get("sm_mhz")
+        n_sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+        if clk:
+            ach = prof[0] / (us * 1e-6)
+            pk = n_sms * 4 * clk * 1e6
+            issue = {"bound": "issue", "achieved": ach, "peak": pk, "unit": "warp instructions/s",
+                     "frac": ach / pk, "warp_instructions_per_frame": prof[0],
+                     "peak_source": "%d SMs x 4 schedulers x %.0f MHz (sampled after the run)" % (n_sms, clk)}
     return {"radius": 3, "sigma_s": 2.0, "sigma_c": 10.0, "min_valid": 3, "frame": "%dx%d" % (W, H),
             "kernel_us_per_frame": us, "gbs": gbs,
             "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
-                         "peak_source": src, "alg_bytes_per_pixel": 7.0},
+                         "peak_source": src, "alg_bytes_per_pixel": 7.0,
+                         "traffic_per_frame": prof[1] if prof else None, "issue": issue},
             "upload_tick_ms": {"with_filter": res[3][0], "without": res[0][0], "cameras": K},
+            "clocks": clocks.summary(),
             "holes_before": float((wl["depth"] == 0).mean())}
 
 
