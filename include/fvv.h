@@ -149,6 +149,32 @@ fvv_status fvv_upload_frames(fvv_ctx* ctx, const uint8_t* rgb, size_t rgb_cam_st
                              size_t depth_cam_stride, size_t depth_pitch,
                              uint64_t tick, void* stream);
 
+/* ---- adaptive view transmission (Sec. V-C) -------------------------------
+ * Only the N_Tx cameras nearest the viewers' viewpoints need to be sent for
+ * a tick.  A tick may therefore carry a subset of the cameras: a view is
+ * synthesised from the newest resident tick that holds all of its active
+ * reference cameras (the n_ref of smallest angle), or from the tick named
+ * in fvv_synthesize_batch's ticks if that one holds them (else NOT_READY).
+ * fvv_latest_tick still reports the newest tick holding every camera. */
+
+/* The cameras of cam_mask (bit k = camera k) for one tick; their blocks are
+ * packed in ascending camera order: the i-th selected camera's rows start at
+ * rgb + i * rgb_cam_stride and depth + i * depth_cam_stride.  Errors as
+ * fvv_upload_frame; INVALID_ARG for an empty mask or one naming missing
+ * cameras. */
+fvv_status fvv_upload_frames_subset(fvv_ctx* ctx, uint64_t cam_mask, const uint8_t* rgb,
+                                    size_t rgb_cam_stride, size_t rgb_pitch, const uint16_t* depth,
+                                    size_t depth_cam_stride, size_t depth_pitch, uint64_t tick,
+                                    void* stream);
+
+/* The n_tx cameras of smallest angle to each of the n_views views (the
+ * angle the blend weights use; ties to the lower index), OR-ed over the
+ * views into *mask: the cameras the capture side must send for them.  With
+ * n_tx >= the context's n_ref every view's references are included.  Needs
+ * no GPU.  Errors: INVALID_ARG. */
+fvv_status fvv_select_cameras(const fvv_rig* rig, int32_t n_views, const fvv_view* views, int32_t n_tx,
+                              uint64_t* mask);
+
 /* ---- layered FG/BG synthesis (Sec. VI: per-camera FG and BG layers) -----
  * With fvv_options.layered = 1 each camera's pixels split by the depth
  * signalling.  A depth code in [d_lo, d_hi] is a foreground (FG) point at

@@ -12,6 +12,7 @@ brute-force z-buffer, analytic ray-cast, hand-built filter/blend/fill cases).
 from __future__ import annotations
 
 import ctypes as C
+import math
 import os
 import subprocess
 import threading
@@ -234,6 +235,27 @@ def synthesize(cams: Sequence, rgb, depth, view, look_at, opts: Optional[Options
     if rc != 0:
         raise ValueError("oracle_synthesize: invalid arguments")
     return {"rgb": out, "depth": dep, "hole": hole, "top3": top3, "keys_raw": kr, "keys": kf}
+
+
+def select_cameras(cams: Sequence, views: Sequence, look_at, n_tx: int) -> int:
+    """Adaptive view transmission (Sec. V-C): the n_tx cameras closest to
+    each virtual viewpoint, OR-ed over the views, as a bit mask.  Closeness
+    is the angle the blend weights use, between the directions from the
+    rig's look-at point O to the two camera centres, atan2(|a x b|, a . b)
+    in FP64; ties go to the lower camera index."""
+    O = np.asarray(look_at, dtype=np.float64).reshape(3)
+    centres = [-(np.asarray(c.R, np.float64).T @ np.asarray(c.t, np.float64)) for c in cams]
+    mask = 0
+    for v in views:
+        a = -(np.asarray(v.R, np.float64).T @ np.asarray(v.t, np.float64)) - O
+        th = []
+        for C in centres:
+            b = C - O
+            th.append(math.atan2(float(np.linalg.norm(np.cross(a, b))), float(a @ b)))
+        order = sorted(range(len(cams)), key=lambda k: (th[k], k))
+        for k in order[:n_tx]:
+            mask |= 1 << k
+    return mask
 
 
 def synthesize_layered(cams: Sequence, rgb, depth, bg, view, look_at, opts: Optional[Options] = None,

@@ -178,6 +178,30 @@ double angle_about(const double Cv[3], const double Ck[3], const double O[3])
     return std::atan2(cn, dt);
 }
 
+// The n cameras of smallest angle to the view (ties to the lower index), as
+// a bit mask: the active references of a view (n = n_ref) and the cameras a
+// tick must carry for it (n = N_Tx, Sec. V-C adaptive view transmission).
+uint64_t nearest_cameras(int n_cams, const fvv_camera* cams, const double look_at[3], const fvv_camera& view,
+                         int n)
+{
+    double Cv[3], theta[fvv::kMaxCams];
+    centre_of(view, Cv);
+    for (int k = 0; k < n_cams; ++k) {
+        double Ck[3];
+        centre_of(cams[k], Ck);
+        theta[k] = angle_about(Cv, Ck, look_at);
+    }
+    if (n <= 0 || n > n_cams) n = n_cams;
+    uint64_t m = 0;
+    for (int r = 0; r < n; ++r) {
+        int best = -1;
+        for (int k = 0; k < n_cams; ++k)
+            if (!((m >> k) & 1u) && (best < 0 || theta[k] < theta[best])) best = k;
+        m |= uint64_t(1) << best;
+    }
+    return m;
+}
+
 // Per-camera maps and weights of one view: the n_ref cameras of smallest
 // angle get w = 1 / (theta + 1e-3), the rest 0; a view sitting on a camera
 // (same centre within 1e-9 m, same optical axis) is one-hot on it.
@@ -382,6 +406,7 @@ fvv_status fvv::upload_frame(fvv_ctx* c, int cam, const uint8_t* rgb, size_t rgb
     if (staged || jbf) FVV_CUDA(cudaEventRecord(c->stage_free, s));
     FVV_CUDA(cudaEventRecord(S.uploaded, s));
     S.mask |= uint64_t(1) << cam;
+    c->have_any = true;
     if (S.mask == c->full_mask && (!c->have_latest || tick > c->latest)) {
         c->latest = tick;
         c->have_latest = true;
@@ -389,13 +414,18 @@ fvv_status fvv::upload_frame(fvv_ctx* c, int cam, const uint8_t* rgb, size_t rgb
     return FVV_OK;
 }
 
-// Every camera of one tick (all of one size) in one launch, after at most
-// two bulk host-to-device copies into the context's staging buffer.
-static fvv_status upload_all(fvv_ctx* c, const uint8_t* rgb, size_t rcs, size_t rp, const uint8_t* depth,
-                             size_t dcs, size_t dp, uint64_t tick, cudaStream_t s, bool host)
+// The cameras of `mask` (all of one size) for one tick in one launch, after
+// at most two bulk host-to-device copies into the context's staging buffer;
+// camera blocks are packed in ascending camera order.
+static fvv_status upload_all(fvv_ctx* c, uint64_t mask, const uint8_t* rgb, size_t rcs, size_t rp,
+                             const uint8_t* depth, size_t dcs, size_t dp, uint64_t tick, cudaStream_t s, bool host)
 {
     using namespace fvv;
-    const int K = c->n_cams, W = c->cams[0].width, H = c->cams[0].height;
+    int cams[kMaxCams], K = 0;
+    for (int k = 0; k < c->n_cams; ++k)
+        if ((mask >> k) & 1u) cams[K++] = k;
+    if (K == 0) return fail(FVV_ERR_INVALID_ARG, "camera mask selects no camera");
+    const int W = c->cams[cams[0]].width, H = c->cams[cams[0]].height;
     if (rp < size_t(W) * 3) return fail(FVV_ERR_INVALID_ARG, "rgb_pitch < 3 * width");
     if (dp < size_t(W) * 2 || dp % 2) return fail(FVV_ERR_INVALID_ARG, "depth_pitch < 2 * width or odd");
     if (dcs % 2) return fail(FVV_ERR_INVALID_ARG, "depth camera stride must be even");
@@ -444,11 +474,11 @@ static fvv_status upload_all(fvv_ctx* c, const uint8_t* rgb, size_t rcs, size_t 
     u.W = W;
     u.H = H;
     u.n_cams = K;
-    u.dpitch = c->dpitch[0];
-    u.rpitch = c->rpitch[0];
-    for (int k = 0; k < K; ++k) {
-        u.off_depth[k] = c->off_depth[k];
-        u.off_rgba[k] = c->off_rgba[k];
+    u.dpitch = c->dpitch[cams[0]];
+    u.rpitch = c->rpitch[cams[0]];
+    for (int i = 0; i < K; ++i) {
+        u.off_depth[i] = c->off_depth[cams[i]];
+        u.off_rgba[i] = c->off_rgba[cams[i]];
     }
     FVV_TRY(run_kernel(c, kPack, s, [&] { return launch_upload_all(u, s); }));
     if (c->opt.jbf_radius > 0) {
@@ -456,16 +486,18 @@ static fvv_status upload_all(fvv_ctx* c, const uint8_t* rgb, size_t rcs, size_t 
         // overwrites the slot's depth rows
         JbfParams P;
         jbf_params(c->opt, W, H, &P);
-        for (int k = 0; k < K; ++k)
-            P.cam[k] = JbfCam{r + size_t(k) * rcs, int64_t(rp),
-                              reinterpret_cast<const uint16_t*>(d + size_t(k) * dcs), int64_t(dp / 2),
-                              reinterpret_cast<uint16_t*>(u.slot + c->off_depth[k]), int64_t(c->dpitch[k])};
+        for (int i = 0; i < K; ++i)
+            P.cam[i] = JbfCam{r + size_t(i) * rcs, int64_t(rp),
+                              reinterpret_cast<const uint16_t*>(d + size_t(i) * dcs), int64_t(dp / 2),
+                              reinterpret_cast<uint16_t*>(u.slot + c->off_depth[cams[i]]),
+                              int64_t(c->dpitch[cams[i]])};
         FVV_TRY(run_kernel(c, kJbf, s, [&] { return launch_jbf(P, K, s); }));
     }
     if (host) FVV_CUDA(cudaEventRecord(c->stage_free, s));
     FVV_CUDA(cudaEventRecord(S.uploaded, s));
-    S.mask = c->full_mask;
-    if (!c->have_latest || tick > c->latest) {
+    S.mask |= mask;
+    c->have_any = true;
+    if (S.mask == c->full_mask && (!c->have_latest || tick > c->latest)) {
         c->latest = tick;
         c->have_latest = true;
     }
@@ -542,9 +574,12 @@ fvv_status fvv::run_batch(fvv_ctx* c, BatchScratch& S, int n, const fvv_view* vi
     if (!views || !out_rgb || !out_pitch) return fail(FVV_ERR_INVALID_ARG, "NULL views/out_rgb/out_pitch");
     FVV_CUDA(cudaSetDevice(c->device));
 
-    // validate views and resolve their frame slots
+    // validate views, compose their per-camera maps and weights, and
+    // resolve their frame slots: a view needs the frames of its active
+    // cameras only (a tick may carry a subset of the cameras, Sec. V-C)
     std::string why;
     std::vector<int> slot_of(n);
+    std::vector<CamGeom> geom(size_t(n) * c->n_cams);
     size_t key_total = 0, stage_total = 0;
     int max_w = 0, max_h = 0;
     for (int i = 0; i < n; ++i) {
@@ -554,15 +589,29 @@ fvv_status fvv::run_batch(fvv_ctx* c, BatchScratch& S, int n, const fvv_view* vi
             return fail(FVV_ERR_INVALID_ARG, "view " + std::to_string(i) + ": width too large");
         if (!out_rgb[i]) return fail(FVV_ERR_INVALID_ARG, "out_rgb[" + std::to_string(i) + "] is NULL");
         if (out_pitch[i] < size_t(V.width) * 3) return fail(FVV_ERR_INVALID_ARG, "out_pitch < 3 * width");
-        uint64_t t;
+        CamGeom* g = geom.data() + size_t(i) * c->n_cams;
+        compose_view(c->n_cams, c->cams.data(), c->look_at, c->depth_unit_m, c->opt.n_ref, V, g);
+        uint64_t need = 0;
+        for (int k = 0; k < c->n_cams; ++k)
+            if (g[k].w > 0.0f) need |= uint64_t(1) << k;
+        uint64_t t = 0;
         if (ticks) {
             t = ticks[i];
             const SlotState& T = c->slot[t % uint64_t(c->slots)];
-            if (!T.any || T.tick != t || T.mask != c->full_mask)
-                return fail(FVV_ERR_NOT_READY, "tick " + std::to_string(t) + " is not complete or no longer resident");
+            if (!T.any || T.tick != t || (T.mask & need) != need)
+                return fail(FVV_ERR_NOT_READY, "tick " + std::to_string(t) +
+                                                   " does not hold the view's cameras or is no longer resident");
         } else {
-            if (!c->have_latest) return fail(FVV_ERR_NOT_READY, "no complete frame tick uploaded yet");
-            t = c->latest;
+            // the newest resident tick holding every camera the view uses
+            bool found = false;
+            for (int si = 0; si < c->slots; ++si) {
+                const SlotState& T = c->slot[si];
+                if (T.any && (T.mask & need) == need && (!found || T.tick > t)) {
+                    t = T.tick;
+                    found = true;
+                }
+            }
+            if (!found) return fail(FVV_ERR_NOT_READY, "no resident tick holds the cameras of view " + std::to_string(i));
         }
         slot_of[i] = int(t % uint64_t(c->slots));
         const size_t np = size_t(V.width) * V.height;
@@ -621,7 +670,7 @@ fvv_status fvv::run_batch(fvv_ctx* c, BatchScratch& S, int n, const fvv_view* vi
             koff += align_up(np, 16);
         }
         CamGeom* g = gh + size_t(i) * c->n_cams;
-        compose_view(c->n_cams, c->cams.data(), c->look_at, c->depth_unit_m, c->opt.n_ref, V, g);
+        std::memcpy(g, geom.data() + size_t(i) * c->n_cams, sizeof(CamGeom) * c->n_cams);
         D.geom = gd + size_t(i) * c->n_cams;
         int na = 0, chunks = 0;
         D.chunk_begin[0] = 0;
@@ -974,30 +1023,65 @@ fvv_status fvv_set_bg_depth(fvv_ctx* c, int32_t cam, const uint16_t* depth, size
     return FVV_OK;
 }
 
-fvv_status fvv_upload_frames(fvv_ctx* c, const uint8_t* rgb, size_t rgb_cam_stride, size_t rgb_pitch,
-                             const uint16_t* depth, size_t depth_cam_stride, size_t depth_pitch,
-                             uint64_t tick, void* stream)
+fvv_status fvv_upload_frames_subset(fvv_ctx* c, uint64_t cam_mask, const uint8_t* rgb, size_t rgb_cam_stride,
+                                    size_t rgb_pitch, const uint16_t* depth, size_t depth_cam_stride,
+                                    size_t depth_pitch, uint64_t tick, void* stream)
 {
     if (!c) return fail(FVV_ERR_INVALID_ARG, "ctx is NULL");
     if (!rgb || !depth) return fail(FVV_ERR_INVALID_ARG, "rgb and depth must be non-NULL");
+    if (cam_mask == 0 || (cam_mask & ~c->full_mask) != 0)
+        return fail(FVV_ERR_INVALID_ARG, "camera mask empty or naming cameras the rig does not have");
     cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : c->own;
     std::lock_guard<std::recursive_mutex> lock(c->mu);
+    int first = -1;
     bool uniform = true;
-    for (int k = 1; k < c->n_cams; ++k)
-        uniform = uniform && c->cams[k].width == c->cams[0].width && c->cams[k].height == c->cams[0].height;
+    for (int k = 0; k < c->n_cams; ++k) {
+        if (!((cam_mask >> k) & 1u)) continue;
+        if (first < 0) first = k;
+        uniform = uniform && c->cams[k].width == c->cams[first].width &&
+                  c->cams[k].height == c->cams[first].height;
+    }
     const fvv::MemKind kr = fvv::mem_kind(rgb), kd = fvv::mem_kind(depth);
     // the batched kernel reads depth as uint16: device rows must be 2-byte aligned
     const bool aligned = depth_pitch % 2 == 0 && depth_cam_stride % 2 == 0 &&
                          (kd == fvv::MemKind::Host || (reinterpret_cast<uintptr_t>(depth) & 1) == 0);
     if (uniform && kr == kd && aligned)
-        return upload_all(c, rgb, rgb_cam_stride, rgb_pitch, reinterpret_cast<const uint8_t*>(depth),
+        return upload_all(c, cam_mask, rgb, rgb_cam_stride, rgb_pitch, reinterpret_cast<const uint8_t*>(depth),
                           depth_cam_stride, depth_pitch, tick, s, kr == fvv::MemKind::Host);
+    int i = 0;
     for (int k = 0; k < c->n_cams; ++k) {
-        const uint8_t* r = rgb + size_t(k) * rgb_cam_stride;
+        if (!((cam_mask >> k) & 1u)) continue;
+        const uint8_t* r = rgb + size_t(i) * rgb_cam_stride;
         const uint16_t* d = reinterpret_cast<const uint16_t*>(
-            reinterpret_cast<const uint8_t*>(depth) + size_t(k) * depth_cam_stride);
+            reinterpret_cast<const uint8_t*>(depth) + size_t(i) * depth_cam_stride);
         FVV_TRY(upload_one(c, k, r, rgb_pitch, d, depth_pitch, tick, s));
+        ++i;
     }
+    return FVV_OK;
+}
+
+fvv_status fvv_upload_frames(fvv_ctx* c, const uint8_t* rgb, size_t rgb_cam_stride, size_t rgb_pitch,
+                             const uint16_t* depth, size_t depth_cam_stride, size_t depth_pitch,
+                             uint64_t tick, void* stream)
+{
+    if (!c) return fail(FVV_ERR_INVALID_ARG, "ctx is NULL");
+    return fvv_upload_frames_subset(c, c->full_mask, rgb, rgb_cam_stride, rgb_pitch, depth, depth_cam_stride,
+                                    depth_pitch, tick, stream);
+}
+
+fvv_status fvv_select_cameras(const fvv_rig* rig, int32_t n_views, const fvv_view* views, int32_t n_tx,
+                              uint64_t* mask)
+{
+    FVV_TRY(check_rig(rig));
+    if (n_views < 1 || !views || !mask) return fail(FVV_ERR_INVALID_ARG, "need n_views >= 1, views and mask");
+    if (n_tx < 1 || n_tx > rig->n_cams) return fail(FVV_ERR_INVALID_ARG, "n_tx must be in [1, n_cams]");
+    std::string why;
+    uint64_t m = 0;
+    for (int i = 0; i < n_views; ++i) {
+        if (!camera_ok(views[i], &why)) return fail(FVV_ERR_INVALID_ARG, "view " + std::to_string(i) + ": " + why);
+        m |= nearest_cameras(rig->n_cams, rig->cams, rig->look_at, views[i], n_tx);
+    }
+    *mask = m;
     return FVV_OK;
 }
 

@@ -142,8 +142,9 @@ struct fvv_ctx {
     fvv::FrameRef* frames_dev = nullptr;
     std::vector<fvv::SlotState> slot;
     uint64_t full_mask = 0;
-    uint64_t latest = 0;
+    uint64_t latest = 0;                        // newest tick holding every camera
     bool have_latest = false;
+    bool have_any = false;                      // some camera of some tick uploaded
 
     std::vector<uint16_t*> bg;                  // per camera: static BG depth model [H][dpitch] or NULL
     std::vector<uint16_t*> jbf_tmp;             // per camera: unfiltered codes [H][dpitch] (depth pre-filter)

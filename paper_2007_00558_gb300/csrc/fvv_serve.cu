@@ -473,7 +473,7 @@ fvv_status fvv_serve_submit(fvv_ctx* c, uint32_t viewer, const fvv_view* view, u
     }
     {
         std::lock_guard<std::recursive_mutex> g(c->mu);
-        if (!c->have_latest) return fail(FVV_ERR_NOT_READY, "no complete frame tick uploaded yet");
+        if (!c->have_any) return fail(FVV_ERR_NOT_READY, "no frame uploaded yet");
     }
     {
         std::lock_guard<std::mutex> lk(st->mu);

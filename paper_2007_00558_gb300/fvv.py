@@ -128,6 +128,8 @@ def load() -> C.CDLL:
             "fvv_upload_frame": [P, I, P, S, P, S, U64, P],
             "fvv_upload_frames": [P, P, S, S, P, S, S, U64, P],
             "fvv_set_bg_depth": [P, I, P, S],
+            "fvv_upload_frames_subset": [P, U64, P, S, S, P, S, S, U64, P],
+            "fvv_select_cameras": [C.POINTER(fvv_rig), I, C.POINTER(fvv_camera), I, C.POINTER(U64)],
             "fvv_depth_jbf": [P, S, P, S, P, S, I, I, C.POINTER(fvv_options), P],
             "fvv_latest_tick": [P, C.POINTER(U64)],
             "fvv_synthesize": [P, C.POINTER(fvv_camera), P, S, C.POINTER(fvv_aux), P],
@@ -270,6 +272,23 @@ def fvv_depth_jbf(rgb, rgb_pitch: int, depth, depth_pitch: int, out, out_pitch: 
     """Joint bilateral depth pre-filter of one frame (device buffers)."""
     _check(load().fvv_depth_jbf(ptr(rgb), rgb_pitch, ptr(depth), depth_pitch, ptr(out), out_pitch, width, height,
                                 C.byref(opt), stream_handle(stream)), "fvv_depth_jbf")
+
+
+def fvv_upload_frames_subset(ctx: int, cam_mask: int, rgb, rgb_cam_stride: int, rgb_pitch: int, depth,
+                             depth_cam_stride: int, depth_pitch: int, tick: int, stream=None) -> None:
+    """The cameras of cam_mask for one tick, blocks packed in camera order."""
+    _check(load().fvv_upload_frames_subset(ctx, cam_mask, ptr(rgb), rgb_cam_stride, rgb_pitch, ptr(depth),
+                                           depth_cam_stride, depth_pitch, tick, stream_handle(stream)),
+           "fvv_upload_frames_subset")
+
+
+def fvv_select_cameras(rig_: fvv_rig, views, n_tx: int) -> int:
+    """Bit mask of the n_tx cameras nearest each view, OR-ed over the views."""
+    vs = list(views)
+    arr = (fvv_camera * len(vs))(*[v if isinstance(v, fvv_camera) else camera(v) for v in vs])
+    m = C.c_uint64()
+    _check(load().fvv_select_cameras(C.byref(rig_), len(vs), arr, n_tx, C.byref(m)), "fvv_select_cameras")
+    return m.value
 
 
 def fvv_set_bg_depth(ctx: int, cam: int, depth, pitch: int = 0) -> None:
