@@ -753,6 +753,77 @@ def jbf_bench(F, wl, stream, reps=20):
             "holes_before": float((wl["depth"] == 0).mean())}
 
 
+def adaptive_e2e_bench(F, wl, rgb_h, dep_h, slots, batch, steps, warmup, off=0):
+    """End to end with adaptive view transmission (Sec. V-C) at the paper's
+    settings: each view's tick carries only the N_Tx = 5 cameras nearest it
+    (fvv_select_cameras), uploaded from pinned host memory with
+    fvv_upload_frames_subset, and the view mixes its n_ref = 3 nearest.
+    Same two-stream pipeline and read-back as the main e2e measurement; the
+    same workload with every camera uploaded and n_ref = 3 is timed beside
+    it."""
+    import numpy as np
+    import torch
+    cams, views = wl["cams"], wl["views"]
+    K, H, W = len(cams), cams[0].height, cams[0].width
+    r = F.rig(cams, wl["look_at"])
+    packed = {}
+    masks = []
+    for v in views:
+        m = F.fvv_select_cameras(r, [v], 5)
+        masks.append(m)
+        if m not in packed:
+            idx = torch.tensor([k for k in range(K) if (m >> k) & 1])
+            packed[m] = (rgb_h.index_select(0, idx).pin_memory(), dep_h.index_select(0, idx).pin_memory())
+    out = {}
+    for mode in ("adaptive", "all_cameras"):
+        ctx = F.fvv_create(r, F.fvv_default_options(frame_slots=slots, max_batch=batch, n_ref=3))
+        try:
+            for t in range(slots):
+                F.fvv_upload_frames(ctx, rgb_h, H * W * 3, W * 3, dep_h, H * W * 2, W * 2, t, None)
+            torch.cuda.synchronize()
+            out_h = [torch.empty((H, W, 3), dtype=torch.uint8).pin_memory() for _ in range(batch)]
+            out_d = [torch.empty((H, W * 3), dtype=torch.uint8, device="cuda") for _ in range(batch)]
+            up, syn = torch.cuda.Stream(), torch.cuda.Stream()
+            tick = [slots]
+            h2d = [0]
+
+            def step(i):
+                vs, ticks = [], []
+                for j in range(batch):
+                    vi = (off + i * batch + j) % len(views)
+                    if mode == "adaptive":
+                        m = masks[vi]
+                        rp, dp = packed[m]
+                        F.fvv_upload_frames_subset(ctx, m, rp, H * W * 3, W * 3, dp, H * W * 2, W * 2, tick[0], up)
+                        h2d[0] += rp.numel() + dp.numel() * 2
+                    else:
+                        F.fvv_upload_frames(ctx, rgb_h, H * W * 3, W * 3, dep_h, H * W * 2, W * 2, tick[0], up)
+                        h2d[0] += rgb_h.numel() + dep_h.numel() * 2
+                    ticks.append(tick[0])
+                    tick[0] += 1
+                    vs.append(views[vi])
+                F.fvv_synthesize_batch(ctx, vs, ticks, out_d, [W * 3] * batch, None, syn)
+                with torch.cuda.stream(syn):
+                    for j in range(batch):
+                        out_h[j].view(-1).copy_(out_d[j].view(-1), non_blocking=True)
+
+            for i in range(warmup):
+                step(i)
+            torch.cuda.synchronize()
+            h2d[0] = 0
+            t0 = time.perf_counter()
+            for i in range(steps):
+                step(warmup + i)
+            torch.cuda.synchronize()
+            el = time.perf_counter() - t0
+            out[mode] = {"value": steps * batch / el, "unit": UNIT, "h2d_bytes_per_step": int(h2d[0] / steps),
+                         "d2h_bytes_per_step": int(batch * H * W * 3)}
+        finally:
+            F.fvv_destroy(ctx)
+    out["settings"] = "N_Tx = 5 transmitted cameras per view, n_ref = 3 mixed (Sec. V-C, Sec. VI)"
+    return out
+
+
 def layered_bench(F, steps, warmup, batch, slots, stream):
     """Layered FG/BG synthesis (Sec. VI per-camera FG and BG layers) on the
     9-camera 1280x720 rig over a static set with actors: the main
@@ -995,6 +1066,10 @@ def run_fvv(args):
                "h2d_bytes_per_step": int(Bsz * (rgb_h.numel() + dep_h.numel() * 2)),
                "d2h_bytes_per_step": int(Bsz * H * W * 3)}
 
+    e2e_adaptive = None
+    if not args.no_e2e and world == 1:
+        e2e_adaptive = adaptive_e2e_bench(F, wl, rgb_h, dep_h, slots, Bsz, args.steps, args.warmup)
+
     serve = None
     if not args.no_serve and world == 1:
         serve = serve_bench(F, ctx, wl, rgb_h, dep_h, slots, args.serve_seconds, stream)
@@ -1049,7 +1124,7 @@ def run_fvv(args):
                              "resident" % (slots, K * H * W * 6 / 1e6),
                        "parallelism": "replicas" if world > 1 else "single"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "serve": serve, "refine": refine, "codec": codec,
-            "layered": layered, "jbf": jbf,
+            "layered": layered, "jbf": jbf, "e2e_adaptive": e2e_adaptive,
             "gpu_launches": int(launches), "clocks": clocks.summary(),
             "kernel_ms": {k: v[2] for k, v in stats.items()},
         }
