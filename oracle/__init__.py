@@ -55,11 +55,12 @@ class Camera(C.Structure):
 class Options(C.Structure):
     _fields_ = [("n_ref", C.c_int), ("crack_filter", C.c_int), ("hole_fill", C.c_int),
                 ("tau_crack", C.c_float), ("tau_vis", C.c_float), ("z_min", C.c_float),
-                ("d_lo", C.c_uint32), ("d_hi", C.c_uint32)]
+                ("d_lo", C.c_uint32), ("d_hi", C.c_uint32), ("pixel_weights", C.c_int)]
 
 
 class XForm(C.Structure):
-    _fields_ = [("M", C.c_float * 12), ("N", C.c_float * 12), ("w", C.c_float)]
+    _fields_ = [("M", C.c_float * 12), ("N", C.c_float * 12), ("w", C.c_float),
+                ("cv", C.c_float * 3), ("vk", C.c_float * 4)]
 
 
 def _load():
@@ -143,7 +144,21 @@ def compose(cams, view, look_at, depth_unit_m: float = 0.001, n_ref: int = 0):
     return M, N, w
 
 
-def _xf(M, N, w):
+def compose_pixel(cams, view, look_at, depth_unit_m: float = 0.001):
+    """The per-pixel weight inputs of the composition (R9): each camera's
+    centre in the view's frame (K, 3) and the view's (cx, cy, 1/fx, 1/fy),
+    FP32."""
+    lib = _load()
+    n = len(cams)
+    xf = (XForm * n)()
+    la = np.ascontiguousarray(np.asarray(look_at, dtype=np.float64).reshape(3))
+    vc = _cam(view)
+    lib.oracle_compose(n, _cams(cams), C.byref(vc), _ptr(la), depth_unit_m, 0, xf)
+    cv = np.array([list(x.cv) for x in xf], dtype=np.float32)
+    return cv, np.array(list(xf[0].vk), dtype=np.float32)
+
+
+def _xf(M, N, w, cv=None, vk=None):
     n = len(w)
     xf = (XForm * n)()
     for k in range(n):
@@ -151,6 +166,11 @@ def _xf(M, N, w):
             xf[k].M[i] = float(np.float32(M[k].reshape(12)[i]))
             xf[k].N[i] = float(np.float32(N[k].reshape(12)[i]))
         xf[k].w = float(np.float32(w[k]))
+        if cv is not None:
+            for i in range(3):
+                xf[k].cv[i] = float(cv[k][i])
+            for i in range(4):
+                xf[k].vk[i] = float(vk[i])
     return xf
 
 
@@ -179,8 +199,9 @@ def crack_filter(keys: np.ndarray, tau: float = 0.05) -> np.ndarray:
     return out
 
 
-def fetch_blend(cams, rgb, depth, M, N, w, keys, opts: Optional[Options] = None):
-    """Step d: returns dict(rgb, depth, hole, top3, nvis) before hole fill."""
+def fetch_blend(cams, rgb, depth, M, N, w, keys, opts: Optional[Options] = None, cv=None, vk=None):
+    """Step d: returns dict(rgb, depth, hole, top3, nvis) before hole fill
+    (with opts.pixel_weights, cv and vk from compose_pixel)."""
     lib = _load()
     n = len(cams)
     opts = opts or options()
@@ -192,7 +213,7 @@ def fetch_blend(cams, rgb, depth, M, N, w, keys, opts: Optional[Options] = None)
     hole = np.zeros((Hv, Wv), np.uint8)
     top3 = np.zeros((Hv, Wv, 3), np.float32)
     nvis = np.zeros((Hv, Wv), np.uint8)
-    lib.oracle_fetch_blend(n, _cams(cams), rp, rpitch, dp, dpitch, _xf(M, N, w), _ptr(k),
+    lib.oracle_fetch_blend(n, _cams(cams), rp, rpitch, dp, dpitch, _xf(M, N, w, cv, vk), _ptr(k),
                            Wv, Hv, C.byref(opts), _ptr(out), _ptr(dep), _ptr(hole),
                            _ptr(top3), _ptr(nvis))
     return {"rgb": out, "depth": dep, "hole": hole, "top3": top3, "nvis": nvis}
@@ -289,6 +310,7 @@ def synthesize_layered(cams: Sequence, rgb, depth, bg, view, look_at, opts: Opti
         raise ValueError("layered synthesis needs d_hi <= 65534")
     Hv, Wv = int(view.height), int(view.width)
     M, N, w = compose(cams, view, look_at, depth_unit_m, opts.n_ref)
+    cv, vk = compose_pixel(cams, view, look_at, depth_unit_m)
     live = [np.ascontiguousarray(depth[k], dtype=np.uint16) for k in range(n)]
     model = []
     for k in range(n):
@@ -299,7 +321,7 @@ def synthesize_layered(cams: Sequence, rgb, depth, bg, view, look_at, opts: Opti
     for dmaps in (live, model):
         raw = warp_splat(cams, dmaps, M, w, Wv, Hv, opts, N)
         filt = crack_filter(raw, opts.tau_crack) if opts.crack_filter else raw.copy()
-        layers.append((raw, filt, fetch_blend(cams, rgb, dmaps, M, N, w, filt, opts)))
+        layers.append((raw, filt, fetch_blend(cams, rgb, dmaps, M, N, w, filt, opts, cv, vk)))
     (rf, kf, bf), (rb, kb, bb) = layers
     on_fg = kf != KEY_EMPTY
     on_bg = ~on_fg & (kb != KEY_EMPTY)

@@ -33,6 +33,10 @@
  *   R8  holes (disocclusions, Sec. VI) stay holes (black, as Sec. IX shows)
  *       unless the hole fill is on: a hole takes the nearer-left or
  *       nearer-right non-hole of its row, whichever is deeper (ties: left).
+ *   R9  per-pixel angular weights (option): the n_ref cameras are chosen as
+ *       in R6, but each contribution is weighted by the angle at the
+ *       surface point between the rays to camera k and to the view, as the
+ *       chord between their unit directions: see pixel_weight.
  */
 #include "fvv_oracle.h"
 
@@ -53,6 +57,7 @@ void oracle_default_options(or_options* o)
     o->z_min = 1.0f;
     o->d_lo = 1;
     o->d_hi = 65534;   /* 65535 signals a background pixel (Sec. V-B, code 0) */
+    o->pixel_weights = 0;
 }
 
 static float key_depth(uint64_t key)
@@ -149,6 +154,19 @@ void oracle_compose(int n_cams, const or_camera* cams, const or_camera* view,
     for (int k = 0; k < n_cams; ++k) {
         compose_pair(&cams[k], view, scale, out[k].M);
         compose_pair(view, &cams[k], scale, out[k].N);
+        /* R9: camera k's centre in the view's frame, R_v C_k + t_v, depth units */
+        double Ck0[3];
+        camera_center(&cams[k], Ck0);
+        for (int i = 0; i < 3; ++i) {
+            double acc = 0.0;
+            for (int j = 0; j < 3; ++j)
+                acc += view->R[3 * i + j] * Ck0[j];
+            out[k].cv[i] = (float)((acc + view->t[i]) * scale);
+        }
+        out[k].vk[0] = (float)view->cx;
+        out[k].vk[1] = (float)view->cy;
+        out[k].vk[2] = (float)(1.0 / view->fx);
+        out[k].vk[3] = (float)(1.0 / view->fy);
         double Ck[3];
         camera_center(&cams[k], Ck);
         theta[k] = view_angle(Cv, Ck, look_at);
@@ -279,6 +297,35 @@ void oracle_crack_filter(const uint64_t* keys_in, int Wv, int Hv, float tau,
 }
 
 /* ------------------------------------------------------------------------
+ * R9: per-pixel angular weight of camera k at output pixel (x, y) of depth
+ * Z.  The surface point in the view's frame is P = ((x - cx) / fx Z,
+ * (y - cy) / fy Z, Z); the weight falls with the angle at P between the
+ * rays to camera k's centre c and to the view's centre (the origin),
+ * measured by the chord between the two unit directions,
+ * sqrt(2 (1 - cos)), so w = 1 / (chord + 1e-3).  FP32, in this order:
+ *   px = ((x - cx) * (1/fx)) * Z,  py likewise,  pz = Z
+ *   lb = sqrt((px px + py py) + pz pz)
+ *   a = c - P,  la = sqrt((ax ax + ay ay) + az az)
+ *   q = ((ax px + ay py) + az pz) / (la lb)       (= -cos)
+ *   t = max(1 + q, 0),  chord = sqrt(t + t),  w = 1 / (chord + 0.001f)
+ * ---------------------------------------------------------------------- */
+static float pixel_weight(const or_xform* xk, float x, float y, float Z)
+{
+    const float px = ((x - xk->vk[0]) * xk->vk[2]) * Z;
+    const float py = ((y - xk->vk[1]) * xk->vk[3]) * Z;
+    const float pz = Z;
+    const float lb = sqrtf((px * px + py * py) + pz * pz);
+    const float ax = xk->cv[0] - px, ay = xk->cv[1] - py, az = xk->cv[2] - pz;
+    const float la = sqrtf((ax * ax + ay * ay) + az * az);
+    const float q = ((ax * px + ay * py) + az * pz) / (la * lb);
+    float t = 1.0f + q;
+    if (!(t > 0.0f))
+        t = 0.0f;
+    const float chord = sqrtf(t + t);
+    return 1.0f / (chord + 0.001f);
+}
+
+/* ------------------------------------------------------------------------
  * Step d (R6, R7).  The winning key gives depth Z, camera w and source pixel
  * s.  acc = w_w * rgb_w[s]; then each other active camera k, in ascending
  * order, back-projects (x, y, Z) with N_k (same FMA-free order as R3), takes
@@ -313,14 +360,15 @@ void oracle_fetch_blend(int n_cams, const or_camera* cams,
             const int su = (int)(s % (uint32_t)cams[w].width);
             const int sv = (int)(s / (uint32_t)cams[w].width);
             const uint8_t* c = rgb[w] + (size_t)sv * rgb_pitch[w] + 3 * (size_t)su;
-            float acc[3], wsum = xf[w].w;
+            const float fx = (float)x, fy = (float)y;
+            const float ww = opt->pixel_weights ? pixel_weight(&xf[w], fx, fy, Z) : xf[w].w;
+            float acc[3], wsum = ww;
             float cw[OR_MAX_CAMS];
             int ck[OR_MAX_CAMS], nc = 0;
             for (int ch = 0; ch < 3; ++ch)
-                acc[ch] = xf[w].w * (float)c[ch];
-            cw[nc] = xf[w].w;
+                acc[ch] = ww * (float)c[ch];
+            cw[nc] = ww;
             ck[nc++] = w;
-            const float fx = (float)x, fy = (float)y;
             for (int k = 0; k < n_cams; ++k) {
                 if (k == w || !(xf[k].w > 0.0f))
                     continue;
@@ -351,10 +399,11 @@ void oracle_fetch_blend(int n_cams, const or_camera* cams,
                 if (!(diff <= opt->tau_vis * Zk))
                     continue;
                 const uint8_t* ckp = rgb[k] + (size_t)vk * rgb_pitch[k] + 3 * (size_t)uk;
+                const float wk = opt->pixel_weights ? pixel_weight(&xf[k], fx, fy, Z) : xf[k].w;
                 for (int ch = 0; ch < 3; ++ch)
-                    acc[ch] = acc[ch] + xf[k].w * (float)ckp[ch];
-                wsum = wsum + xf[k].w;
-                cw[nc] = xf[k].w;
+                    acc[ch] = acc[ch] + wk * (float)ckp[ch];
+                wsum = wsum + wk;
+                cw[nc] = wk;
                 ck[nc++] = k;
             }
             for (int ch = 0; ch < 3; ++ch) {

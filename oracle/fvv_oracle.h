@@ -50,6 +50,7 @@ typedef struct {
     float z_min;        /* smallest accepted projected depth, depth units */
     uint32_t d_lo;      /* accepted depth codes [d_lo, d_hi] (d_lo >= 1) */
     uint32_t d_hi;
+    int pixel_weights;  /* 1 = per-pixel angular weights (R9) instead of per-view ones */
 } or_options;
 
 /* Per-camera quantities of one virtual view, composed in FP64 and rounded
@@ -58,6 +59,8 @@ typedef struct {
     float M[12];  /* forward  3x4: (u z, v z, z, 1) of camera k -> virtual (X, Y, Z) */
     float N[12];  /* backward 3x4: (x Z, y Z, Z, 1) of the view  -> camera k (X, Y, Z) */
     float w;      /* blend weight, 0 = camera not among the active references */
+    float cv[3];  /* camera k's centre in the view's camera frame, depth units */
+    float vk[4];  /* the view's cx, cy, 1/fx, 1/fy (the same for every k) */
 } or_xform;
 
 void oracle_default_options(or_options* o);
