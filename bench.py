@@ -64,6 +64,9 @@ def parse_args():
                    help="length of the Poisson multi-viewer run")
     p.add_argument("--no-refine", action="store_true", help="skip the refinement-network measurement")
     p.add_argument("--no-layered", action="store_true", help="skip the layered FG/BG measurement")
+    p.add_argument("--main-only", action="store_true",
+                   help="only the main synthesis measurement (no e2e, serving, codec, pre-filter, layered, "
+                        "per-pixel weights, refinement or CPU baseline); for profiling")
     p.add_argument("--jbf-only", action="store_true",
                    help="only the depth pre-filter measurement; for profiling")
     p.add_argument("--layered-only", action="store_true",
@@ -824,23 +827,21 @@ def adaptive_e2e_bench(F, wl, rgb_h, dep_h, slots, batch, steps, warmup, off=0):
     return out
 
 
-def layered_bench(F, steps, warmup, batch, slots, stream):
-    """Layered FG/BG synthesis (Sec. VI per-camera FG and BG layers) on the
-    9-camera 1280x720 rig over a static set with actors: the main
-    measurement's schedule (each view reads its own tick of a 16-tick ring,
-    inputs > L2), views/s from CUDA events over `steps` batched calls, and
-    each kernel's time per view from the library's per-launch events."""
+def options_bench(F, wl, steps, warmup, batch, slots, stream, bg=None, **opts):
+    """The main measurement's schedule (each view reads its own tick of a
+    16-tick ring, inputs > L2) on workload `wl` with extra options: views/s
+    from CUDA events over `steps` batched calls and each kernel's time per
+    view from the library's per-launch events."""
     import numpy as np
     import torch
-    import synthetic as S
-    wl = S.workload("layered_9cam_1280x720")
     cams, views = wl["cams"], wl["views"]
     K, H, W = len(cams), cams[0].height, cams[0].width
     ctx = F.fvv_create(F.rig(cams, wl["look_at"]),
-                       F.fvv_default_options(frame_slots=slots, max_batch=batch, layered=1))
+                       F.fvv_default_options(frame_slots=slots, max_batch=batch, **opts))
     try:
-        for k in range(K):
-            F.fvv_set_bg_depth(ctx, k, np.ascontiguousarray(wl["bg"][k]), W * 2)
+        if bg is not None:
+            for k in range(K):
+                F.fvv_set_bg_depth(ctx, k, np.ascontiguousarray(bg[k]), W * 2)
         rgb_h = torch.from_numpy(np.ascontiguousarray(wl["rgb"])).pin_memory()
         dep_h = torch.from_numpy(np.ascontiguousarray(wl["depth"]).view(np.int16)).pin_memory()
         for t in range(slots):
@@ -868,11 +869,20 @@ def layered_bench(F, steps, warmup, batch, slots, stream):
         F.fvv_profile_enable(ctx, False)
     finally:
         F.fvv_destroy(ctx)
-    return {"workload": "layered_9cam_1280x720", "views_per_s": steps * batch / (ms / 1e3),
+    return {"workload": wl["name"], "options": opts, "views_per_s": steps * batch / (ms / 1e3),
             "ms_per_step": ms / steps, "views_per_step": batch,
             "kernel_us_per_view": {k: 1e3 * v[2] / v[1] / batch for k, v in stats.items() if v[1] > 0},
-            "actor_pixel_fraction": float(wl["fg"].mean()),
             "l2": "inputs > L2: each view reads its own tick of %d" % slots}
+
+
+def layered_bench(F, steps, warmup, batch, slots, stream):
+    """Layered FG/BG synthesis (Sec. VI per-camera FG and BG layers) on the
+    9-camera 1280x720 rig over a static set with actors."""
+    import synthetic as S
+    wl = S.workload("layered_9cam_1280x720")
+    res = options_bench(F, wl, steps, warmup, batch, slots, stream, bg=wl["bg"], layered=1)
+    res["actor_pixel_fraction"] = float(wl["fg"].mean())
+    return res
 
 
 def view_schedule(rank, step, batch, slots, n_traj=300):
@@ -1030,7 +1040,7 @@ def run_fvv(args):
 
     # end to end through the C ABI with host buffers
     e2e = None
-    if not args.no_e2e:
+    if not args.no_e2e and not args.main_only:
         # Two streams: every tick's upload (pinned host -> frame ring) on `up`,
         # the batched synthesis and the read-back of its RGB results on `syn`.
         # The frame ring's per-slot events order each synthesis after the
@@ -1067,27 +1077,38 @@ def run_fvv(args):
                "d2h_bytes_per_step": int(Bsz * H * W * 3)}
 
     e2e_adaptive = None
-    if not args.no_e2e and world == 1:
+    if not args.no_e2e and world == 1 and not args.main_only:
         e2e_adaptive = adaptive_e2e_bench(F, wl, rgb_h, dep_h, slots, Bsz, args.steps, args.warmup)
 
     serve = None
-    if not args.no_serve and world == 1:
+    if not args.no_serve and world == 1 and not args.main_only:
         serve = serve_bench(F, ctx, wl, rgb_h, dep_h, slots, args.serve_seconds, stream)
 
     codec = None
-    if world == 1:
+    if world == 1 and not args.main_only:
         codec = codec_bench(F, ctx, wl, stream)
 
     jbf = None
-    if world == 1:
+    if world == 1 and not args.main_only:
         jbf = jbf_bench(F, wl, stream)
 
     layered = None
-    if not args.no_layered and world == 1:
+    if not args.no_layered and world == 1 and not args.main_only:
         layered = layered_bench(F, args.steps, args.warmup, Bsz, slots, stream)
 
+    # per-pixel angular weights on the main workload, and the paper's
+    # three-reference setting with them
+    pixel_weights = None
+    if world == 1 and not args.main_only:
+        pixel_weights = {"n_ref_all": options_bench(F, wl, args.steps, args.warmup, Bsz, slots, stream,
+                                                    pixel_weights=1),
+                         "n_ref_3": options_bench(F, wl, args.steps, args.warmup, Bsz, slots, stream,
+                                                  pixel_weights=1, n_ref=3),
+                         "n_ref_3_per_view_weights": options_bench(F, wl, args.steps, args.warmup, Bsz, slots,
+                                                                   stream, n_ref=3)}
+
     refine = None
-    if not args.no_refine and world == 1:
+    if not args.no_refine and world == 1 and not args.main_only:
         data = loo_data()
         refine = {"net_32_64_128": refine_bench(F, ctx, wl, args.refine_steps, stream, data),
                   "net_48_96_192": refine_bench(F, ctx, wl, args.refine_steps, stream, data, (48, 96, 192),
@@ -1096,7 +1117,7 @@ def run_fvv(args):
     F.fvv_destroy(ctx)
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.main_only:
         pool = OraclePool(wl["rgb"], wl["depth"])
         try:
             pool.run_views([[0] for _ in range(pool.procs)])      # warm the workers
@@ -1124,7 +1145,7 @@ def run_fvv(args):
                              "resident" % (slots, K * H * W * 6 / 1e6),
                        "parallelism": "replicas" if world > 1 else "single"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "serve": serve, "refine": refine, "codec": codec,
-            "layered": layered, "jbf": jbf, "e2e_adaptive": e2e_adaptive,
+            "layered": layered, "jbf": jbf, "e2e_adaptive": e2e_adaptive, "pixel_weights": pixel_weights,
             "gpu_launches": int(launches), "clocks": clocks.summary(),
             "kernel_ms": {k: v[2] for k, v in stats.items()},
         }

@@ -103,6 +103,7 @@ typedef struct fvv_options {
     float jbf_sigma_s;          /* spatial sigma, pixels, default 2 */
     float jbf_sigma_c;          /* colour sigma per RGB channel, default 10 */
     int32_t jbf_min_valid;      /* fill only with at least this many valid neighbours, default 3 */
+    int32_t pixel_weights;      /* 1 = per-pixel angular weights in (d), see below; default 0 */
 } fvv_options;
 
 /* Optional per-view outputs (device or host pointers; NULL = not wanted).
@@ -114,6 +115,15 @@ typedef struct fvv_aux {
     uint64_t* keys;             /* [H][W] z-buffer keys after the crack filter */
     uint64_t* keys_raw;         /* [H][W] z-buffer keys before the crack filter */
 } fvv_aux;
+
+/* Per-pixel angular weights (pixel_weights = 1).  The n_ref cameras are
+ * chosen per view as always; each contribution at output pixel (x, y) of
+ * depth Z is then weighted by the angle at its surface point P = ((x - cx) /
+ * fx Z, (y - cy) / fy Z, Z) (view frame) between the rays to camera k's
+ * centre c_k and to the view's centre: w = 1 / (sqrt(2 (1 - cos)) + 0.001),
+ * in FP32 as  lb = |P|, a = c_k - P, la = |a|, q = (a . P) / (la lb),
+ * t = max(1 + q, 0), w = 1 / (sqrt(t + t) + 0.001f), dot products
+ * ((x x + y y) + z z), c_k and 1/fx, 1/fy composed in FP64 and rounded once. */
 
 /* Fill `opt` with the defaults listed above. */
 fvv_status fvv_default_options(fvv_options* opt);

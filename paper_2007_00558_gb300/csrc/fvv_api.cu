@@ -107,6 +107,7 @@ bool options_ok(const fvv_options& o, int n_cams, std::string* why)
         return false;
     }
     if (o.layered != 0 && o.layered != 1) { *why = "layered must be 0 or 1"; return false; }
+    if (o.pixel_weights != 0 && o.pixel_weights != 1) { *why = "pixel_weights must be 0 or 1"; return false; }
     if (!fvv::jbf_options_ok(o, why)) return false;
     if (o.frame_slots < 1 || o.frame_slots > 1024) { *why = "frame_slots must be in [1, 1024]"; return false; }
     if (o.max_batch < 1 || o.max_batch > 4096) { *why = "max_batch must be in [1, 4096]"; return false; }
@@ -216,9 +217,14 @@ void compose_view(int n_cams, const fvv_camera* cams, const double look_at[3],
     for (int k = 0; k < n_cams; ++k) {
         compose_map(cams[k], view, scale, g[k].M);
         compose_map(view, cams[k], scale, g[k].N);
-        g[k].pad[0] = g[k].pad[1] = g[k].pad[2] = 0.0f;
         double Ck[3];
         centre_of(cams[k], Ck);
+        // the camera's centre in the view's frame, R_v C_k + t_v, depth units
+        for (int i = 0; i < 3; ++i) {
+            double acc = 0.0;
+            for (int j = 0; j < 3; ++j) acc += view.R[3 * i + j] * Ck[j];
+            g[k].pad[i] = float((acc + view.t[i]) * scale);
+        }
         theta[k] = angle_about(Cv, Ck, look_at);
         chosen[k] = false;
         const double dx = Cv[0] - Ck[0], dy = Cv[1] - Ck[1], dz = Cv[2] - Ck[2];
@@ -656,7 +662,11 @@ fvv_status fvv::run_batch(fvv_ctx* c, BatchScratch& S, int n, const fvv_view* vi
         D.n_cams = c->n_cams;
         D.slot = slot_of[i];
         D.flags = (c->opt.crack_filter ? fvv::kFlagCrack : 0) | (c->opt.hole_fill ? fvv::kFlagFill : 0) |
-                  (c->opt.layered ? fvv::kFlagLayered : 0);
+                  (c->opt.layered ? fvv::kFlagLayered : 0) | (c->opt.pixel_weights ? fvv::kFlagPixelWeights : 0);
+        D.vk[0] = float(V.cx);
+        D.vk[1] = float(V.cy);
+        D.vk[2] = float(1.0 / V.fx);
+        D.vk[3] = float(1.0 / V.fy);
         D.tau_crack = c->opt.tau_crack;
         D.tau_vis = c->opt.tau_vis;
         D.z_min = c->opt.z_min;
@@ -743,7 +753,7 @@ fvv_status fvv::run_batch(fvv_ctx* c, BatchScratch& S, int n, const fvv_view* vi
                                  cudaMemcpyDefault, s));
     FVV_TRY(run_kernel(c, kResolve, s, [&] {
         return fvv::launch_resolve(vdev, n, max_h, max_w, c->n_cams, want_top3, c->frames_dev, s,
-                                   c->opt.layered != 0);
+                                   c->opt.layered != 0, c->opt.pixel_weights != 0);
     }));
     for (const HostCopy& h : d2h)
         FVV_CUDA(cudaMemcpy2DAsync(h.dst, h.dpitch, h.src, h.spitch, h.width, h.height,
@@ -801,6 +811,7 @@ fvv_status fvv_default_options(fvv_options* o)
     o->jbf_sigma_s = 2.0f;
     o->jbf_sigma_c = 10.0f;
     o->jbf_min_valid = 3;
+    o->pixel_weights = 0;
     return FVV_OK;
 }
 

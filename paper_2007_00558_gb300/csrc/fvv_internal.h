@@ -20,6 +20,7 @@ constexpr int kResolveBand = 4;      // output rows per resolve CTA
 constexpr int kFlagCrack = 1;
 constexpr int kFlagFill = 2;
 constexpr int kFlagLayered = 4;
+constexpr int kFlagPixelWeights = 8;
 
 // Per (view, camera) quantities, composed on the host in FP64 and rounded
 // to FP32 once (Sec. VI geometry).  M maps (u z, v z, z, 1) of the camera to
@@ -28,7 +29,7 @@ struct alignas(16) CamGeom {
     float M[12];
     float N[12];
     float w;          // blend weight, 0 = inactive
-    float pad[3];
+    float pad[3];     // the camera's centre in the view's frame, depth units (per-pixel weights)
 };
 
 // One camera's frame in one slot of the device-resident frame ring.
@@ -51,6 +52,7 @@ struct alignas(16) ViewDesc {
     float tau_crack, tau_vis, z_min;
     uint32_t d_lo, d_hi;
     int32_t pad0;
+    float vk[4];                     // the view's cx, cy, 1/fx, 1/fy (per-pixel weights)
     unsigned long long* keys;        // scratch z-buffer [Hv * Wv] (the FG layer when layered)
     unsigned long long* keys_bg;     // layered: the BG layer's z-buffer [Hv * Wv], else NULL
     uint8_t* out_rgb;                // [Hv] rows of 3 * Wv bytes
@@ -70,7 +72,8 @@ cudaError_t launch_clear_keys(unsigned long long* keys, size_t n, cudaStream_t s
 cudaError_t launch_warp_splat(const ViewDesc* views, int n_views, int max_chunks,
                               const FrameRef* frames, cudaStream_t stream, bool layered = false);
 cudaError_t launch_resolve(const ViewDesc* views, int n_views, int max_h, int max_w, int n_cams,
-                           bool top3, const FrameRef* frames, cudaStream_t stream, bool layered = false);
+                           bool top3, const FrameRef* frames, cudaStream_t stream, bool layered = false,
+                           bool pixel_weights = false);
 cudaError_t launch_pack_rgba(const uint8_t* rgb, size_t rgb_pitch, uint32_t* rgba,
                              int rpitch, int W, int H, cudaStream_t stream);
 size_t resolve_smem_bytes(int max_w, int n_cams, bool layered = false);

@@ -359,7 +359,25 @@ __device__ __forceinline__ int block_excl_suffix_min(int v, int* s_scan)
 // kTop3: also track the three largest contributing weights (only when that
 // output is requested).
 // ---------------------------------------------------------------------------
-template <bool kTop3, bool kLayered>
+// Per-pixel angular weight of a camera whose centre in the view's frame is
+// (cx, cy, cz), at the surface point (px, py, pz) at distance lb from the
+// view's centre: 1 / (chord + 0.001) with chord = sqrt(2 (1 - cos)) of the
+// angle at the point between the rays to the camera and to the view.
+__device__ __forceinline__ float pixel_weight(float cx, float cy, float cz, float px, float py, float pz, float lb)
+{
+    const float ax = __fsub_rn(cx, px), ay = __fsub_rn(cy, py), az = __fsub_rn(cz, pz);
+    const float la = __fsqrt_rn(__fadd_rn(__fadd_rn(__fmul_rn(ax, ax), __fmul_rn(ay, ay)), __fmul_rn(az, az)));
+    const float dot = __fadd_rn(__fadd_rn(__fmul_rn(ax, px), __fmul_rn(ay, py)), __fmul_rn(az, pz));
+    const float q = __fdiv_rn(dot, __fmul_rn(la, lb));
+    float t = __fadd_rn(1.0f, q);
+    t = t > 0.0f ? t : 0.0f;
+    const float chord = __fsqrt_rn(__fadd_rn(t, t));
+    return __fdiv_rn(1.0f, __fadd_rn(chord, 0.001f));
+}
+
+// kPixW: per-pixel angular weights (each contribution weighted by the angle
+// at its surface point) instead of the view's per-camera weights.
+template <bool kTop3, bool kLayered, bool kPixW>
 __global__ void __launch_bounds__(kResolveThreads, 3)
 k_resolve(const ViewDesc* __restrict__ views, const FrameRef* __restrict__ frames, int band)
 {
@@ -420,6 +438,7 @@ k_resolve(const ViewDesc* __restrict__ views, const FrameRef* __restrict__ frame
         float val = 0.0f;
         if (j < 12) val = V->geom[k].N[j];
         else if (j == 12) val = V->geom[k].w;
+        else if (j < 16) val = V->geom[k].pad[j - 13];     // centre in the view's frame (per-pixel weights)
         else if (j == 16) val = float(frames[V->slot * nc + k].W - 1);
         else if (j == 17) val = float(frames[V->slot * nc + k].H - 1);
         s_geom[i] = val;
@@ -499,14 +518,26 @@ k_resolve(const ViewDesc* __restrict__ views, const FrameRef* __restrict__ frame
             const uint32_t sv = s / uint32_t(Fw.W);
             const uint32_t su = s - sv * uint32_t(Fw.W);
             const uint32_t cw = __ldg(Fw.rgba + sv * uint32_t(Fw.rpitch) + su);
-            const float ww = s_geom[w * kGeomFloats + 12];
+            const float fx = u23_to_float(uint32_t(x));
+            // per-pixel weights: the surface point in the view's frame
+            float px = 0.0f, py = 0.0f, lb = 0.0f;
+            if (kPixW) {
+                px = __fmul_rn(__fmul_rn(__fsub_rn(fx, V->vk[0]), V->vk[2]), Z);
+                py = __fmul_rn(__fmul_rn(__fsub_rn(fy, V->vk[1]), V->vk[3]), Z);
+                lb = __fsqrt_rn(__fadd_rn(__fadd_rn(__fmul_rn(px, px), __fmul_rn(py, py)), __fmul_rn(Z, Z)));
+            }
+            auto weight_of = [&](int k) {
+                if (!kPixW) return s_geom[kGeomFloats * k + 12];
+                const float* gk = s_geom + kGeomFloats * k;
+                return pixel_weight(gk[13], gk[14], gk[15], px, py, Z, lb);
+            };
+            const float ww = weight_of(w);
             float acc0 = __fmul_rn(ww, u23_to_float(cw & 255u));
             float acc1 = __fmul_rn(ww, u23_to_float((cw >> 8) & 255u));
             float acc2 = __fmul_rn(ww, u23_to_float((cw >> 16) & 255u));
             float wsum = ww;
             float t0 = ww, t1 = -1.0f, t2 = -1.0f;
             int k0 = w, k1 = INT_MAX, k2 = INT_MAX;
-            const float fx = u23_to_float(uint32_t(x));
             // the other active cameras (the winner is always active: only
             // active cameras splat), in ascending order, in groups of four:
             // project all four and issue their depth and colour gathers
@@ -571,7 +602,7 @@ k_resolve(const ViewDesc* __restrict__ views, const FrameRef* __restrict__ frame
                     if (!(diff <= __fmul_rn(tau_vis, zk[j])))
                         continue;
                     const int k = kk[j];
-                    const float wk = s_geom[kGeomFloats * k + 12];
+                    const float wk = weight_of(k);
                     const uint32_t c = ck[j];
                     acc0 = __fadd_rn(acc0, __fmul_rn(wk, u23_to_float(c & 255u)));
                     acc1 = __fadd_rn(acc1, __fmul_rn(wk, u23_to_float((c >> 8) & 255u)));
@@ -716,7 +747,8 @@ cudaError_t launch_warp_splat(const ViewDesc* views, int n_views, int max_chunks
 }
 
 cudaError_t launch_resolve(const ViewDesc* views, int n_views, int max_h, int max_w, int n_cams,
-                           bool top3, const FrameRef* frames, cudaStream_t stream, bool layered)
+                           bool top3, const FrameRef* frames, cudaStream_t stream, bool layered,
+                           bool pixel_weights)
 {
     if (n_views <= 0 || max_h <= 0) return cudaSuccess;
     // the layout grows with the width and the camera count, so the widest
@@ -730,8 +762,12 @@ cudaError_t launch_resolve(const ViewDesc* views, int n_views, int max_h, int ma
         kernel<<<grid, kResolveThreads, smem, stream>>>(views, frames, band);
         return cudaGetLastError();
     };
-    if (layered) return top3 ? go(k_resolve<true, true>) : go(k_resolve<false, true>);
-    return top3 ? go(k_resolve<true, false>) : go(k_resolve<false, false>);
+    if (pixel_weights) {
+        if (layered) return top3 ? go(k_resolve<true, true, true>) : go(k_resolve<false, true, true>);
+        return top3 ? go(k_resolve<true, false, true>) : go(k_resolve<false, false, true>);
+    }
+    if (layered) return top3 ? go(k_resolve<true, true, false>) : go(k_resolve<false, true, false>);
+    return top3 ? go(k_resolve<true, false, false>) : go(k_resolve<false, false, false>);
 }
 
 cudaError_t launch_pack_rgba(const uint8_t* rgb, size_t rgb_pitch, uint32_t* rgba, int rpitch,

@@ -184,6 +184,10 @@ extern "C" fvv_status fvv_synthesize_noalloc(const fvv_rig* rig, const fvv_optio
     D.z_min = o.z_min;
     D.d_lo = o.d_lo;
     D.d_hi = o.d_hi;
+    D.vk[0] = float(view->cx);
+    D.vk[1] = float(view->cy);
+    D.vk[2] = float(1.0 / view->fx);
+    D.vk[3] = float(1.0 / view->fy);
     D.keys = S.keys;
     D.out_rgb = out_rgb;
     D.out_pitch = int64_t(out_pitch);
@@ -213,7 +217,8 @@ extern "C" fvv_status fvv_synthesize_noalloc(const fvv_rig* rig, const fvv_optio
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = fvv::launch_clear_keys(S.keys, (np + 15) & ~size_t(15), s);
     if (e == cudaSuccess) e = fvv::launch_warp_splat(vdev, 1, segs, fdev, s);
-    if (e == cudaSuccess) e = fvv::launch_resolve(vdev, 1, view->height, view->width, nc, false, fdev, s);
+    if (e == cudaSuccess)
+        e = fvv::launch_resolve(vdev, 1, view->height, view->width, nc, false, fdev, s, false, o.pixel_weights != 0);
     if (e != cudaSuccess) {
         cudaGetLastError();
         char msg[256];

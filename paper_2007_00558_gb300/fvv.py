@@ -62,7 +62,7 @@ class fvv_options(C.Structure):
                 ("d_lo", C.c_uint32), ("d_hi", C.c_uint32), ("frame_slots", C.c_int32),
                 ("max_batch", C.c_int32), ("memory_budget", C.c_uint64), ("layered", C.c_int32),
                 ("jbf_radius", C.c_int32), ("jbf_sigma_s", C.c_float), ("jbf_sigma_c", C.c_float),
-                ("jbf_min_valid", C.c_int32)]
+                ("jbf_min_valid", C.c_int32), ("pixel_weights", C.c_int32)]
 
 
 class fvv_aux(C.Structure):

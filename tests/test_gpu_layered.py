@@ -46,7 +46,7 @@ def test_layered_small_batch(oracle_mod, lay_small):
 
 
 @pytest.mark.parametrize("kw", [dict(crack_filter=0), dict(hole_fill=0), dict(n_ref=3),
-                                dict(crack_filter=0, hole_fill=0, n_ref=2)])
+                                dict(crack_filter=0, hole_fill=0, n_ref=2), dict(pixel_weights=1)])
 def test_layered_options(oracle_mod, lay_small, kw):
     wl = lay_small
     _check(oracle_mod, wl, [wl["views"][40]], **kw)

@@ -62,7 +62,8 @@ def test_nine_camera_arc_full_size(oracle_mod, arc_full):
 
 @pytest.mark.parametrize("kw", [dict(n_ref=3), dict(n_ref=1), dict(crack_filter=0),
                                 dict(hole_fill=0), dict(crack_filter=0, hole_fill=0, n_ref=2),
-                                dict(tau_vis=0.0), dict(d_lo=1500, d_hi=3000)])
+                                dict(tau_vis=0.0), dict(d_lo=1500, d_hi=3000), dict(pixel_weights=1),
+                                dict(pixel_weights=1, n_ref=3, crack_filter=0)])
 def test_options(oracle_mod, arc_small, kw):
     wl = arc_small
     v = wl["views"][40]
