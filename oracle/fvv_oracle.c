@@ -16,8 +16,8 @@
  *       K_v [R_v R_k^T | t_v - R_v R_k^T t_k] and the 3x4 product is rounded
  *       to FP32 once (M_k).  The backward map N_k swaps the roles.
  *   R3  forward projection (FMA-free):  a = ((m0 u + m1 v) + m2);
- *       X = a z + m3, likewise Y, Z; reject !(Z > z_min); u' = X / Z,
- *       v' = Y / Z; target pixel floor(u' + 0.5) (ties round up).
+ *       X = a z + m3, likewise Y, Z; reject !(Z > z_min); r = 1 / Z,
+ *       u' = X r, v' = Y r; target pixel floor(u' + 0.5) (ties round up).
  *   R4  z-buffer: the smallest 64-bit key  bits(Z) << 32 | k << 26 | src
  *       wins; positive floats order like their bit patterns, so the key
  *       orders by depth, then camera, then source pixel.
@@ -231,8 +231,9 @@ void oracle_warp_splat(int n_cams, const or_camera* cams,
                 float Z = (a2 * z) + m[11];
                 if (!(Z > opt->z_min))
                     continue;
-                float up = X / Z;
-                float vp = Y / Z;
+                const float r = 1.0f / Z;
+                float up = X * r;
+                float vp = Y * r;
                 if (!isfinite(up) || !isfinite(vp))
                     continue;
                 float tu = floorf(up + 0.5f);
@@ -330,7 +331,7 @@ static float pixel_weight(const or_xform* xk, float x, float y, float Z)
  * s.  acc = w_w * rgb_w[s]; then each other active camera k, in ascending
  * order, back-projects (x, y, Z) with N_k (same FMA-free order as R3), takes
  * the nearest pixel, and contributes w_k * rgb_k there when visible.
- * Output channel = min(255, floor(acc / wsum + 0.5)).  Aux: Z, hole flag,
+ * Output channel = min(255, floor(acc (1 / wsum) + 0.5)).  Aux: Z, hole flag,
  * the three largest normalised contributing weights (descending, ties by
  * lower camera index), number of contributing cameras.
  * ---------------------------------------------------------------------- */
@@ -381,8 +382,9 @@ void oracle_fetch_blend(int n_cams, const or_camera* cams,
                 float Zk = (a2 * Z) + n[11];
                 if (!(Zk > opt->z_min))
                     continue;
-                float up = Xk / Zk;
-                float vp = Yk / Zk;
+                const float rk = 1.0f / Zk;
+                float up = Xk * rk;
+                float vp = Yk * rk;
                 if (!isfinite(up) || !isfinite(vp))
                     continue;
                 float tu = floorf(up + 0.5f);
@@ -406,8 +408,9 @@ void oracle_fetch_blend(int n_cams, const or_camera* cams,
                 cw[nc] = wk;
                 ck[nc++] = k;
             }
+            const float iw = 1.0f / wsum;
             for (int ch = 0; ch < 3; ++ch) {
-                float val = floorf(acc[ch] / wsum + 0.5f);
+                float val = floorf(acc[ch] * iw + 0.5f);
                 o[ch] = (uint8_t)(val > 255.0f ? 255.0f : val);
             }
             if (out_depth) out_depth[p] = Z;
@@ -425,7 +428,7 @@ void oracle_fetch_blend(int n_cams, const or_camera* cams,
                         out_top3[3 * p + r] = 0.0f;
                     } else {
                         used[best] = 1;
-                        out_top3[3 * p + r] = cw[best] / wsum;
+                        out_top3[3 * p + r] = cw[best] * iw;
                     }
                 }
             }

@@ -233,8 +233,9 @@ k_warp_splat(const ViewDesc* __restrict__ views, const FrameRef* __restrict__ fr
             const float X = __fadd_rn(__fmul_rn(a0, z), m3);
             const float Y = __fadd_rn(__fmul_rn(a1, z), m7);
             const float Z = __fadd_rn(__fmul_rn(a2, z), m11);
-            const float tu = floorf(__fadd_rn(__fdiv_rn(X, Z), 0.5f));
-            const float tv = floorf(__fadd_rn(__fdiv_rn(Y, Z), 0.5f));
+            const float r = __fdiv_rn(1.0f, Z);
+            const float tu = floorf(__fadd_rn(__fmul_rn(X, r), 0.5f));
+            const float tv = floorf(__fadd_rn(__fmul_rn(Y, r), 0.5f));
             // the bounds test also rejects NaN and +-inf, as a finiteness test would
             const bool ok = dd != 0u && dd >= dlo && dd <= dhi && Z > zmin && tu >= 0.0f &&
                             tu <= maxu && tv >= 0.0f && tv <= maxv;
@@ -304,9 +305,9 @@ __device__ __forceinline__ bool w_before(float wa, int ka, float wb, int kb)
     return wa > wb || (wa == wb && ka < kb);
 }
 
-__device__ __forceinline__ uint32_t blend_channel(float acc, float wsum)
+__device__ __forceinline__ uint32_t blend_channel(float acc, float iw)    // iw = 1 / wsum
 {
-    float v = floorf(__fadd_rn(__fdiv_rn(acc, wsum), 0.5f));
+    float v = floorf(__fadd_rn(__fmul_rn(acc, iw), 0.5f));
     v = v > 255.0f ? 255.0f : v;
     return uint32_t(v);
 }
@@ -564,8 +565,9 @@ k_resolve(const ViewDesc* __restrict__ views, const FrameRef* __restrict__ frame
                     const float Xk = __fadd_rn(__fmul_rn(a0, Z), A.w);
                     const float Yk = __fadd_rn(__fmul_rn(a1, Z), Bq.w);
                     const float Zk = __fadd_rn(__fmul_rn(a2, Z), Cq.w);
-                    const float tu = floorf(__fadd_rn(__fdiv_rn(Xk, Zk), 0.5f));
-                    const float tv = floorf(__fadd_rn(__fdiv_rn(Yk, Zk), 0.5f));
+                    const float rk = __fdiv_rn(1.0f, Zk);
+                    const float tu = floorf(__fadd_rn(__fmul_rn(Xk, rk), 0.5f));
+                    const float tv = floorf(__fadd_rn(__fmul_rn(Yk, rk), 0.5f));
                     // the bounds test also rejects NaN and +-inf, as a finiteness test would
                     ok[j] = g0 + j < nother && Zk > zmin && tu >= 0.0f && tu <= Eq.x &&
                             tv >= 0.0f && tv <= Eq.y;
@@ -619,14 +621,14 @@ k_resolve(const ViewDesc* __restrict__ views, const FrameRef* __restrict__ frame
                     }
                 }
             }
-            s_rgb[x] = blend_channel(acc0, wsum) | (blend_channel(acc1, wsum) << 8) |
-                       (blend_channel(acc2, wsum) << 16);
+            const float iw = __fdiv_rn(1.0f, wsum);
+            s_rgb[x] = blend_channel(acc0, iw) | (blend_channel(acc1, iw) << 8) | (blend_channel(acc2, iw) << 16);
             s_dep[x] = Z;
             s_hole[x] = 0;
             if (kTop3 && top3) {
-                top3[3 * (rowbase + x) + 0] = __fdiv_rn(t0, wsum);
-                top3[3 * (rowbase + x) + 1] = t1 >= 0.0f ? __fdiv_rn(t1, wsum) : 0.0f;
-                top3[3 * (rowbase + x) + 2] = t2 >= 0.0f ? __fdiv_rn(t2, wsum) : 0.0f;
+                top3[3 * (rowbase + x) + 0] = __fmul_rn(t0, iw);
+                top3[3 * (rowbase + x) + 1] = t1 >= 0.0f ? __fmul_rn(t1, iw) : 0.0f;
+                top3[3 * (rowbase + x) + 2] = t2 >= 0.0f ? __fmul_rn(t2, iw) : 0.0f;
             }
         }
         // (e) hole fill: nearest non-hole left / right, the deeper one wins
