@@ -170,7 +170,7 @@ k_warp_splat(const ViewDesc* __restrict__ views, const FrameRef* __restrict__ fr
     const int lane = threadIdx.x & 31;
     const int total = s_cb[na];
     const float zmin = V->z_min;
-    const uint32_t dlo = V->d_lo, dhi = V->d_hi;
+    const uint32_t dlo = V->d_lo, dspan = V->d_hi - V->d_lo;
     const uint32_t Wv = uint32_t(V->Wv);
     const float maxu = u23_to_float(Wv - 1), maxv = u23_to_float(uint32_t(V->Hv - 1));
     unsigned long long* __restrict__ keys = V->keys;
@@ -233,12 +233,13 @@ k_warp_splat(const ViewDesc* __restrict__ views, const FrameRef* __restrict__ fr
             const float X = __fadd_rn(__fmul_rn(a0, z), m3);
             const float Y = __fadd_rn(__fmul_rn(a1, z), m7);
             const float Z = __fadd_rn(__fmul_rn(a2, z), m11);
-            const float r = __fdiv_rn(1.0f, Z);
+            const float r = __frcp_rn(Z);          // 1 / Z, correctly rounded
             const float tu = floorf(__fadd_rn(__fmul_rn(X, r), 0.5f));
             const float tv = floorf(__fadd_rn(__fmul_rn(Y, r), 0.5f));
             // the bounds test also rejects NaN and +-inf, as a finiteness test would
-            const bool ok = dd != 0u && dd >= dlo && dd <= dhi && Z > zmin && tu >= 0.0f &&
-                            tu <= maxu && tv >= 0.0f && tv <= maxv;
+            // dd in [dlo, dhi] (dlo >= 1, so a code of 0 wraps above the span)
+            const bool ok = dd - dlo <= dspan && Z > zmin && tu >= 0.0f && tu <= maxu && tv >= 0.0f &&
+                            tv <= maxv;
             if (ok) {
                 const uint32_t pix = float_to_u23(tv) * Wv + float_to_u23(tu);
                 const unsigned long long key =
@@ -459,7 +460,7 @@ k_resolve(const ViewDesc* __restrict__ views, const FrameRef* __restrict__ frame
     const bool fill = (V->flags & kFlagFill) != 0;
     const float f1 = __fadd_rn(1.0f, V->tau_crack);
     const float tau_vis = V->tau_vis, zmin = V->z_min;
-    const uint32_t dlo = V->d_lo, dhi = V->d_hi;
+    const uint32_t dlo = V->d_lo, dspan = V->d_hi - V->d_lo;
     float* __restrict__ top3 = V->out_top3;
     unsigned long long* __restrict__ okeys = V->out_keys;
     const float4* g4 = reinterpret_cast<const float4*>(s_geom);
@@ -565,7 +566,7 @@ k_resolve(const ViewDesc* __restrict__ views, const FrameRef* __restrict__ frame
                     const float Xk = __fadd_rn(__fmul_rn(a0, Z), A.w);
                     const float Yk = __fadd_rn(__fmul_rn(a1, Z), Bq.w);
                     const float Zk = __fadd_rn(__fmul_rn(a2, Z), Cq.w);
-                    const float rk = __fdiv_rn(1.0f, Zk);
+                    const float rk = __frcp_rn(Zk);
                     const float tu = floorf(__fadd_rn(__fmul_rn(Xk, rk), 0.5f));
                     const float tv = floorf(__fadd_rn(__fmul_rn(Yk, rk), 0.5f));
                     // the bounds test also rejects NaN and +-inf, as a finiteness test would
@@ -598,7 +599,7 @@ k_resolve(const ViewDesc* __restrict__ views, const FrameRef* __restrict__ frame
                 for (int j = 0; j < 4; ++j) {
                     if (!ok[j])
                         continue;
-                    if (dk[j] == 0u || dk[j] < dlo || dk[j] > dhi)
+                    if (dk[j] - dlo > dspan)         // outside [dlo, dhi]; 0 wraps above
                         continue;
                     const float diff = fabsf(__fsub_rn(u23_to_float(dk[j]), zk[j]));
                     if (!(diff <= __fmul_rn(tau_vis, zk[j])))
@@ -621,7 +622,7 @@ k_resolve(const ViewDesc* __restrict__ views, const FrameRef* __restrict__ frame
                     }
                 }
             }
-            const float iw = __fdiv_rn(1.0f, wsum);
+            const float iw = __frcp_rn(wsum);
             s_rgb[x] = blend_channel(acc0, iw) | (blend_channel(acc1, iw) << 8) | (blend_channel(acc2, iw) << 16);
             s_dep[x] = Z;
             s_hole[x] = 0;
