@@ -20,9 +20,10 @@
 // template parameter, so the single-layer form carries none of it.
 //
 // Every FP32 operation of the warp, the filter and the blend is an explicit
-// round-to-nearest intrinsic (__fmul_rn / __fadd_rn / __fsub_rn / __fdiv_rn)
-// in a fixed order with no FMA contraction, so the results are exactly the
-// IEEE values of that operation sequence.
+// round-to-nearest intrinsic (__fmul_rn / __fadd_rn / __fsub_rn / __fmaf_rn /
+// __frcp_rn) in a fixed order -- a fused multiply-add only where the
+// operation sequence has one -- so the results are exactly the IEEE values of
+// that sequence.
 #include <climits>
 
 #include "fvv_internal.h"
@@ -215,7 +216,8 @@ k_warp_splat(const ViewDesc* __restrict__ views, const FrameRef* __restrict__ fr
         const float m4 = m[4], m6 = m[6], m7 = m[7];
         const float m8 = m[8], m10 = m[10], m11 = m[11];
         const float fv = u23_to_float(uint32_t(v));
-        const float r0 = __fmul_rn(m[1], fv), r1 = __fmul_rn(m[5], fv), r2 = __fmul_rn(m[9], fv);
+        // per-row terms fma(m1, v, m2), likewise for Y and Z
+        const float r0 = __fmaf_rn(m[1], fv, m2), r1 = __fmaf_rn(m[5], fv, m6), r2 = __fmaf_rn(m[9], fv, m10);
         const unsigned long long khi = static_cast<unsigned long long>(k) << kSrcBits;
         const uint32_t src0 = uint32_t(v) * uint32_t(F.W) + uint32_t(u0 + lane);
         const float fu0 = u23_to_float(uint32_t(u0 + lane));
@@ -227,12 +229,12 @@ k_warp_splat(const ViewDesc* __restrict__ views, const FrameRef* __restrict__ fr
             const uint32_t dd = d[j];
             const float fu = __fadd_rn(fu0, float(32 * j));  // exact: small integers
             const float z = u23_to_float(dd);
-            const float a0 = __fadd_rn(__fadd_rn(__fmul_rn(m0, fu), r0), m2);
-            const float a1 = __fadd_rn(__fadd_rn(__fmul_rn(m4, fu), r1), m6);
-            const float a2 = __fadd_rn(__fadd_rn(__fmul_rn(m8, fu), r2), m10);
-            const float X = __fadd_rn(__fmul_rn(a0, z), m3);
-            const float Y = __fadd_rn(__fmul_rn(a1, z), m7);
-            const float Z = __fadd_rn(__fmul_rn(a2, z), m11);
+            const float a0 = __fmaf_rn(m0, fu, r0);
+            const float a1 = __fmaf_rn(m4, fu, r1);
+            const float a2 = __fmaf_rn(m8, fu, r2);
+            const float X = __fmaf_rn(a0, z, m3);
+            const float Y = __fmaf_rn(a1, z, m7);
+            const float Z = __fmaf_rn(a2, z, m11);
             const float r = __frcp_rn(Z);          // 1 / Z, correctly rounded
             const float tu = floorf(__fadd_rn(__fmul_rn(X, r), 0.5f));
             const float tv = floorf(__fadd_rn(__fmul_rn(Y, r), 0.5f));
@@ -472,11 +474,11 @@ k_resolve(const ViewDesc* __restrict__ views, const FrameRef* __restrict__ frame
         if (y + 1 < y1)
             fetch_row(y + 2);
         cp_async_commit();
-        // per-row terms N1 y, N5 y, N9 y: the products the projection forms
+        // per-row terms fma(N1, y, N2), fma(N5, y, N6), fma(N9, y, N10)
         const float fy = u23_to_float(uint32_t(y));
         for (int i = tid; i < nc * 3; i += NT) {
             const int k = i / 3, j = i - k * 3;
-            s_rowt[4 * k + j] = __fmul_rn(s_geom[kGeomFloats * k + 1 + 4 * j], fy);
+            s_rowt[4 * k + j] = __fmaf_rn(s_geom[kGeomFloats * k + 1 + 4 * j], fy, s_geom[kGeomFloats * k + 2 + 4 * j]);
         }
         cp_async_wait<1>();                   // rows y-1 .. y+1 have landed
         __syncthreads();
@@ -560,12 +562,12 @@ k_resolve(const ViewDesc* __restrict__ views, const FrameRef* __restrict__ frame
                     const float4 A = g4[5 * k + 0], Bq = g4[5 * k + 1], Cq = g4[5 * k + 2],
                                  Eq = g4[5 * k + 4];
                     const float4 Rt = reinterpret_cast<const float4*>(s_rowt)[k];
-                    const float a0 = __fadd_rn(__fadd_rn(__fmul_rn(A.x, fx), Rt.x), A.z);
-                    const float a1 = __fadd_rn(__fadd_rn(__fmul_rn(Bq.x, fx), Rt.y), Bq.z);
-                    const float a2 = __fadd_rn(__fadd_rn(__fmul_rn(Cq.x, fx), Rt.z), Cq.z);
-                    const float Xk = __fadd_rn(__fmul_rn(a0, Z), A.w);
-                    const float Yk = __fadd_rn(__fmul_rn(a1, Z), Bq.w);
-                    const float Zk = __fadd_rn(__fmul_rn(a2, Z), Cq.w);
+                    const float a0 = __fmaf_rn(A.x, fx, Rt.x);
+                    const float a1 = __fmaf_rn(Bq.x, fx, Rt.y);
+                    const float a2 = __fmaf_rn(Cq.x, fx, Rt.z);
+                    const float Xk = __fmaf_rn(a0, Z, A.w);
+                    const float Yk = __fmaf_rn(a1, Z, Bq.w);
+                    const float Zk = __fmaf_rn(a2, Z, Cq.w);
                     const float rk = __frcp_rn(Zk);
                     const float tu = floorf(__fadd_rn(__fmul_rn(Xk, rk), 0.5f));
                     const float tv = floorf(__fadd_rn(__fmul_rn(Yk, rk), 0.5f));
@@ -607,9 +609,9 @@ k_resolve(const ViewDesc* __restrict__ views, const FrameRef* __restrict__ frame
                     const int k = kk[j];
                     const float wk = weight_of(k);
                     const uint32_t c = ck[j];
-                    acc0 = __fadd_rn(acc0, __fmul_rn(wk, u23_to_float(c & 255u)));
-                    acc1 = __fadd_rn(acc1, __fmul_rn(wk, u23_to_float((c >> 8) & 255u)));
-                    acc2 = __fadd_rn(acc2, __fmul_rn(wk, u23_to_float((c >> 16) & 255u)));
+                    acc0 = __fmaf_rn(wk, u23_to_float(c & 255u), acc0);
+                    acc1 = __fmaf_rn(wk, u23_to_float((c >> 8) & 255u), acc1);
+                    acc2 = __fmaf_rn(wk, u23_to_float((c >> 16) & 255u), acc2);
                     wsum = __fadd_rn(wsum, wk);
                     if (kTop3) {
                         if (w_before(wk, k, t0, k0)) {
