@@ -1133,6 +1133,17 @@ def run_fvv(args):
         n_sms = torch.cuda.get_device_properties(local).multi_processor_count
         roofline["issue"] = {k: issue_roofline(k, Bsz, timed[k][2] / timed[k][1] / 1e3, clk.get("sm_mhz"), n_sms)
                              for k in ("resolve", "warp_splat") if k in timed}
+        # the dominant kernel is bound by instruction issue, not by HBM: when
+        # its instruction count is known, that roofline is the headline one
+        # ("alu": warp instructions per second against SMs x 4 schedulers x
+        # the sampled SM clock) and the HBM figures stay beside it
+        iss = roofline["issue"].get(roofline["kernel"])
+        if iss is not None:
+            hbm = {k: roofline.pop(k) for k in ("achieved", "peak", "unit", "frac", "peak_source")}
+            hbm["bound"] = "hbm"
+            roofline = dict(roofline, bound="alu", achieved=iss["achieved"], peak=iss["peak"], unit=iss["unit"],
+                            frac=iss["frac"], peak_source=iss["peak_source"],
+                            warp_instructions_per_view=iss["warp_instructions_per_view"], hbm=hbm)
 
     if rank == 0:
         line = {

@@ -38,7 +38,7 @@ constexpr int kGeomFloats = 20;   // per-camera record of the resolve kernel
 constexpr int kRing = 4;          // key rows kept in shared memory (3 in use + 1 in flight)
 
 struct SmemLayout {
-    size_t ring, rgb, dep, hole, left, right, geom, rowt, frames, active, pos, scan, total;
+    size_t ring, rgb, dep, hole, geom, rowt, frames, active, pos, scan, total;
 };
 
 __host__ __device__ inline SmemLayout resolve_layout(int W, int n_cams, bool layered)
@@ -50,8 +50,8 @@ __host__ __device__ inline SmemLayout resolve_layout(int W, int n_cams, bool lay
     L.rgb = o;    o = align16(o + size_t(W) * 4);
     L.dep = o;    o = align16(o + size_t(W) * 4);
     L.hole = o;   o = align16(o + size_t(W));
-    L.left = o;   o = align16(o + size_t(W) * 2);
-    L.right = o;  o = align16(o + size_t(W) * 2);
+    // (the hole fill's nearest-left / nearest-right indices live in the key
+    // ring's slot of the row above, which no pixel reads any more by then)
     L.geom = o;   o = align16(o + size_t(n_cams) * kGeomFloats * sizeof(float));
     L.rowt = o;   o = align16(o + size_t(n_cams) * 4 * sizeof(float));
     L.frames = o; o = align16(o + size_t(n_cams) * sizeof(FrameRef));
@@ -381,8 +381,11 @@ __device__ __forceinline__ float pixel_weight(float cx, float cy, float cz, floa
 
 // kPixW: per-pixel angular weights (each contribution weighted by the angle
 // at its surface point) instead of the view's per-camera weights.
+// Four CTAs per SM in the single-layer forms (64 registers, under 56 KB of
+// shared memory up to 1280-pixel rows); the layered forms' two key rings
+// allow two.
 template <bool kTop3, bool kLayered, bool kPixW>
-__global__ void __launch_bounds__(kResolveThreads, 3)
+__global__ void __launch_bounds__(kResolveThreads, kLayered ? 2 : 4)
 k_resolve(const ViewDesc* __restrict__ views, const FrameRef* __restrict__ frames, int band)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -398,8 +401,6 @@ k_resolve(const ViewDesc* __restrict__ views, const FrameRef* __restrict__ frame
     uint32_t* s_rgb = reinterpret_cast<uint32_t*>(smem + L.rgb);
     float* s_dep = reinterpret_cast<float*>(smem + L.dep);
     uint8_t* s_hole = smem + L.hole;
-    int16_t* s_left = reinterpret_cast<int16_t*>(smem + L.left);
-    int16_t* s_right = reinterpret_cast<int16_t*>(smem + L.right);
     float* s_geom = reinterpret_cast<float*>(smem + L.geom);
     float* s_rowt = reinterpret_cast<float*>(smem + L.rowt);
     FrameRef* s_fr = reinterpret_cast<FrameRef*>(smem + L.frames);
@@ -637,6 +638,11 @@ k_resolve(const ViewDesc* __restrict__ views, const FrameRef* __restrict__ frame
         // (e) hole fill: nearest non-hole left / right, the deeper one wins
         const bool row_has_hole = __syncthreads_or(any_hole) != 0;
         if (fill && row_has_hole) {
+            // the ring slot of row y - 1: every thread has finished reading
+            // it (the barrier above), and row y + 3 lands in it only after
+            // the barrier that ends this row
+            int16_t* s_left = reinterpret_cast<int16_t*>(const_cast<unsigned long long*>(rU));
+            int16_t* s_right = s_left + Wv;
             const int seg = (Wv + NT - 1) / NT;
             const int x0 = min(tid * seg, Wv), x1 = min(x0 + seg, Wv);
             int last = -1;
@@ -763,6 +769,9 @@ cudaError_t launch_resolve(const ViewDesc* views, int n_views, int max_h, int ma
     dim3 grid(static_cast<unsigned>((max_h + band - 1) / band), static_cast<unsigned>(n_views));
     auto go = [&](auto kernel) {
         cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+        if (e != cudaSuccess) return e;
+        // the largest shared-memory carveout, so that four CTAs fit per SM
+        e = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
         if (e != cudaSuccess) return e;
         kernel<<<grid, kResolveThreads, smem, stream>>>(views, frames, band);
         return cudaGetLastError();
