@@ -381,11 +381,11 @@ __device__ __forceinline__ float pixel_weight(float cx, float cy, float cz, floa
 
 // kPixW: per-pixel angular weights (each contribution weighted by the angle
 // at its surface point) instead of the view's per-camera weights.
-// Four CTAs per SM in the single-layer forms (64 registers, under 56 KB of
-// shared memory up to 1280-pixel rows); the layered forms' two key rings
-// allow two.
+// Three CTAs per SM in the single-layer forms (a 64-register cap for four
+// cost more in the gathers' overlap than the extra warps gained); the
+// layered forms' two key rings allow two.
 template <bool kTop3, bool kLayered, bool kPixW>
-__global__ void __launch_bounds__(kResolveThreads, kLayered ? 2 : 4)
+__global__ void __launch_bounds__(kResolveThreads, kLayered ? 2 : 3)
 k_resolve(const ViewDesc* __restrict__ views, const FrameRef* __restrict__ frames, int band)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -770,7 +770,8 @@ cudaError_t launch_resolve(const ViewDesc* views, int n_views, int max_h, int ma
     auto go = [&](auto kernel) {
         cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
         if (e != cudaSuccess) return e;
-        // the largest shared-memory carveout, so that four CTAs fit per SM
+        // the largest shared-memory carveout, so that every CTA the
+        // registers allow also fits
         e = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
         if (e != cudaSuccess) return e;
         kernel<<<grid, kResolveThreads, smem, stream>>>(views, frames, band);
