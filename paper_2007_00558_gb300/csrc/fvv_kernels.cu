@@ -770,10 +770,6 @@ cudaError_t launch_resolve(const ViewDesc* views, int n_views, int max_h, int ma
     auto go = [&](auto kernel) {
         cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
         if (e != cudaSuccess) return e;
-        // the largest shared-memory carveout, so that every CTA the
-        // registers allow also fits
-        e = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-        if (e != cudaSuccess) return e;
         kernel<<<grid, kResolveThreads, smem, stream>>>(views, frames, band);
         return cudaGetLastError();
     };
