@@ -786,7 +786,7 @@ def adaptive_e2e_bench(F, wl, rgb_h, dep_h, slots, batch, steps, warmup, off=0):
             torch.cuda.synchronize()
             out_h = [torch.empty((H, W, 3), dtype=torch.uint8).pin_memory() for _ in range(batch)]
             out_d = [torch.empty((H, W * 3), dtype=torch.uint8, device="cuda") for _ in range(batch)]
-            up, syn = torch.cuda.Stream(), torch.cuda.Stream()
+            ups, syn = [torch.cuda.Stream(), torch.cuda.Stream()], torch.cuda.Stream()
             tick = [slots]
             h2d = [0]
 
@@ -797,10 +797,12 @@ def adaptive_e2e_bench(F, wl, rgb_h, dep_h, slots, batch, steps, warmup, off=0):
                     if mode == "adaptive":
                         m = masks[vi]
                         rp, dp = packed[m]
-                        F.fvv_upload_frames_subset(ctx, m, rp, H * W * 3, W * 3, dp, H * W * 2, W * 2, tick[0], up)
+                        F.fvv_upload_frames_subset(ctx, m, rp, H * W * 3, W * 3, dp, H * W * 2, W * 2, tick[0],
+                                                   ups[tick[0] % 2])
                         h2d[0] += rp.numel() + dp.numel() * 2
                     else:
-                        F.fvv_upload_frames(ctx, rgb_h, H * W * 3, W * 3, dep_h, H * W * 2, W * 2, tick[0], up)
+                        F.fvv_upload_frames(ctx, rgb_h, H * W * 3, W * 3, dep_h, H * W * 2, W * 2, tick[0],
+                                            ups[tick[0] % 2])
                         h2d[0] += rgb_h.numel() + dep_h.numel() * 2
                     ticks.append(tick[0])
                     tick[0] += 1
@@ -1041,20 +1043,23 @@ def run_fvv(args):
     # end to end through the C ABI with host buffers
     e2e = None
     if not args.no_e2e and not args.main_only:
-        # Two streams: every tick's upload (pinned host -> frame ring) on `up`,
-        # the batched synthesis and the read-back of its RGB results on `syn`.
-        # The frame ring's per-slot events order each synthesis after the
-        # uploads of its ticks and each upload after the syntheses still
-        # reading its slot, so step i+1's copies overlap step i's kernels.
+        # Three streams: ticks' uploads (pinned host -> frame ring) alternate
+        # between two upload streams, so one tick's host-to-device copy runs
+        # while the previous tick's packing kernel does; the batched
+        # synthesis and the read-back of its RGB results go on `syn`.  The
+        # frame ring's per-slot events order each synthesis after the uploads
+        # of its ticks and each upload after the syntheses still reading its
+        # slot, so step i+1's copies overlap step i's kernels.
         out_h = [torch.empty((H, W, 3), dtype=torch.uint8).pin_memory() for _ in range(Bsz)]
         out_d = [torch.empty((H, W * 3), dtype=torch.uint8, device="cuda") for _ in range(Bsz)]
-        up, syn = torch.cuda.Stream(), torch.cuda.Stream()
+        ups, syn = [torch.cuda.Stream(), torch.cuda.Stream()], torch.cuda.Stream()
         tick = [slots]
 
         def e2e_step(i):
             vs, ticks = [], []
             for j in range(Bsz):
-                F.fvv_upload_frames(ctx, rgb_h, H * W * 3, W * 3, dep_h, H * W * 2, W * 2, tick[0], up)
+                F.fvv_upload_frames(ctx, rgb_h, H * W * 3, W * 3, dep_h, H * W * 2, W * 2, tick[0],
+                                    ups[tick[0] % 2])
                 ticks.append(tick[0])
                 tick[0] += 1
                 vs.append(views[(off + i * Bsz + j) % 300])

@@ -445,30 +445,34 @@ static fvv_status upload_all(fvv_ctx* c, uint64_t mask, const uint8_t* rgb, size
         S.tick = tick;
         S.mask = 0;
     }
-    for (int r = 0; r < kMaxReaders; ++r)
-        if (S.read_pending[r]) FVV_CUDA(cudaStreamWaitEvent(s, S.read[r], 0));
     const uint8_t* r = rgb;
     const uint8_t* d = depth;
+    const int sb = c->stage_all_next;
     if (host) {
+        c->stage_all_next ^= 1;
         const size_t rspan = size_t(K - 1) * rcs + size_t(H - 1) * rp + size_t(W) * 3;
         const size_t dspan = size_t(K - 1) * dcs + size_t(H - 1) * dp + size_t(W) * 2;
         const size_t doff = align_up(rspan, 256);
-        if (c->stage_all_bytes < doff + dspan) {
-            FVV_CUDA(cudaEventSynchronize(c->stage_free));
-            dev_free(c, c->stage_all, c->stage_all_bytes);
-            c->stage_all = nullptr;
-            c->stage_all_bytes = 0;
+        if (c->stage_all_bytes[sb] < doff + dspan) {
+            FVV_CUDA(cudaEventSynchronize(c->stage_all_free[sb]));
+            dev_free(c, c->stage_all[sb], c->stage_all_bytes[sb]);
+            c->stage_all[sb] = nullptr;
+            c->stage_all_bytes[sb] = 0;
             void* p = nullptr;
             FVV_TRY(dev_alloc(c, &p, doff + dspan));
-            c->stage_all = static_cast<uint8_t*>(p);
-            c->stage_all_bytes = doff + dspan;
+            c->stage_all[sb] = static_cast<uint8_t*>(p);
+            c->stage_all_bytes[sb] = doff + dspan;
         }
-        FVV_CUDA(cudaStreamWaitEvent(s, c->stage_free, 0));    // a previous upload may still read it
-        FVV_CUDA(cudaMemcpyAsync(c->stage_all, rgb, rspan, cudaMemcpyHostToDevice, s));
-        FVV_CUDA(cudaMemcpyAsync(c->stage_all + doff, depth, dspan, cudaMemcpyHostToDevice, s));
-        r = c->stage_all;
-        d = c->stage_all + doff;
+        FVV_CUDA(cudaStreamWaitEvent(s, c->stage_all_free[sb], 0));   // an earlier upload may still read it
+        FVV_CUDA(cudaMemcpyAsync(c->stage_all[sb], rgb, rspan, cudaMemcpyHostToDevice, s));
+        FVV_CUDA(cudaMemcpyAsync(c->stage_all[sb] + doff, depth, dspan, cudaMemcpyHostToDevice, s));
+        r = c->stage_all[sb];
+        d = c->stage_all[sb] + doff;
     }
+    // only the writes into the slot wait for syntheses still reading it: the
+    // copies into the staging buffer above may already run
+    for (int rd = 0; rd < kMaxReaders; ++rd)
+        if (S.read_pending[rd]) FVV_CUDA(cudaStreamWaitEvent(s, S.read[rd], 0));
     UploadAll u{};
     u.rgb = r;
     u.rgb_cam_stride = rcs;
@@ -499,7 +503,7 @@ static fvv_status upload_all(fvv_ctx* c, uint64_t mask, const uint8_t* rgb, size
                               int64_t(c->dpitch[cams[i]])};
         FVV_TRY(run_kernel(c, kJbf, s, [&] { return launch_jbf(P, K, s); }));
     }
-    if (host) FVV_CUDA(cudaEventRecord(c->stage_free, s));
+    if (host) FVV_CUDA(cudaEventRecord(c->stage_all_free[sb], s));
     FVV_CUDA(cudaEventRecord(S.uploaded, s));
     S.mask |= mask;
     c->have_any = true;
@@ -884,7 +888,10 @@ fvv_status fvv_destroy(fvv_ctx* c)
         dev_free(c, c->jbf_tmp[k], size_t(c->cams[k].height) * c->dpitch[k] * 2);
     dev_free(c, c->frames_dev, sizeof(FrameRef) * size_t(c->slots) * c->n_cams);
     dev_free(c, c->arena, c->arena_bytes);
-    if (c->stage_all) dev_free(c, c->stage_all, c->stage_all_bytes);
+    for (int i = 0; i < 2; ++i) {
+        if (c->stage_all[i]) dev_free(c, c->stage_all[i], c->stage_all_bytes[i]);
+        if (c->stage_all_free[i]) cudaEventDestroy(c->stage_all_free[i]);
+    }
     if (c->stage_free) cudaEventDestroy(c->stage_free);
     if (c->own) cudaStreamDestroy(c->own);
     cudaGetLastError();
@@ -984,6 +991,10 @@ fvv_status fvv_create(const fvv_rig* rig, const fvv_options* opt, fvv_ctx** out)
     }
     FVV_CREATE_CUDA(cudaEventCreateWithFlags(&c->stage_free, cudaEventDisableTiming));
     FVV_CREATE_CUDA(cudaEventRecord(c->stage_free, c->own));
+    for (int i = 0; i < 2; ++i) {
+        FVV_CREATE_CUDA(cudaEventCreateWithFlags(&c->stage_all_free[i], cudaEventDisableTiming));
+        FVV_CREATE_CUDA(cudaEventRecord(c->stage_all_free[i], c->own));
+    }
     FVV_CREATE_TRY(fvv::scratch_alloc(c, c->main, 0, 0, o.max_batch, 4));
     c->main.growable = true;
     FVV_CREATE_CUDA(cudaStreamSynchronize(c->own));

@@ -149,9 +149,14 @@ struct fvv_ctx {
     std::vector<uint16_t*> bg;                  // per camera: static BG depth model [H][dpitch] or NULL
     std::vector<uint16_t*> jbf_tmp;             // per camera: unfiltered codes [H][dpitch] (depth pre-filter)
     std::vector<uint8_t*> stage_rgb;            // per camera, for host uploads
-    uint8_t* stage_all = nullptr;               // batched host uploads (all cameras)
-    size_t stage_all_bytes = 0;
-    cudaEvent_t stage_free = nullptr;           // last reader of the staging buffers
+    // batched host uploads: two staging buffers used in turn, so that a
+    // tick's host-to-device copy (on one stream) can run while the previous
+    // tick's packing kernel (on another) still reads the other buffer
+    uint8_t* stage_all[2] = {};
+    size_t stage_all_bytes[2] = {};
+    cudaEvent_t stage_all_free[2] = {};         // last reader of each
+    int stage_all_next = 0;
+    cudaEvent_t stage_free = nullptr;           // last reader of the per-camera staging buffers
     fvv::BatchScratch main;                     // scratch of fvv_synthesize(_batch)
 
     bool profiling = false;
