@@ -756,6 +756,65 @@ def jbf_bench(F, wl, stream, reps=20):
             "holes_before": float((wl["depth"] == 0).mean())}
 
 
+def yuv_e2e_bench(F, wl, rgb_h, dep_h, slots, batch, steps, warmup, off=0):
+    """End to end with the depth of every tick sent as YUV420 depth frames
+    (Sec. V-B: 12-bit disparity packed onto YUV420, 1.5 bytes per pixel
+    instead of 2), uploaded with fvv_upload_frames_yuv (decoded in the
+    upload kernel); otherwise the pipeline and views of the main e2e
+    measurement (all 9 cameras mixed)."""
+    import numpy as np
+    import torch
+    cams, views = wl["cams"], wl["views"]
+    K, H, W = len(cams), cams[0].height, cams[0].width
+    ctx = F.fvv_create(F.rig(cams, wl["look_at"]), F.fvv_default_options(frame_slots=slots, max_batch=batch))
+    try:
+        codec = F.fvv_depth_codec_default(z_near=0.3, z_far=10.0)
+        blk = H * W + 2 * (H // 2) * (W // 2)
+        yuv_d = torch.empty((K, blk), dtype=torch.uint8, device="cuda")
+        for k in range(K):
+            F.fvv_set_depth_codec(ctx, k, codec)
+            d = torch.from_numpy(np.ascontiguousarray(wl["depth"][k]).view(np.int16)).cuda()
+            y = yuv_d[k, :H * W].view(H, W)
+            u = yuv_d[k, H * W:H * W + (H // 2) * (W // 2)].view(H // 2, W // 2)
+            v = yuv_d[k, H * W + (H // 2) * (W // 2):].view(H // 2, W // 2)
+            F.fvv_depth_encode_yuv(ctx, k, d, W * 2, y, W, u, v, W // 2)
+        torch.cuda.synchronize()
+        yuv_h = yuv_d.cpu().pin_memory()
+        for t in range(slots):
+            F.fvv_upload_frames_yuv(ctx, rgb_h, H * W * 3, W * 3, yuv_h, blk, t, None)
+        torch.cuda.synchronize()
+        out_h = [torch.empty((H, W, 3), dtype=torch.uint8).pin_memory() for _ in range(batch)]
+        out_d = [torch.empty((H, W * 3), dtype=torch.uint8, device="cuda") for _ in range(batch)]
+        ups, syn = [torch.cuda.Stream(), torch.cuda.Stream()], torch.cuda.Stream()
+        tick = [slots]
+
+        def step(i):
+            vs, ticks = [], []
+            for j in range(batch):
+                F.fvv_upload_frames_yuv(ctx, rgb_h, H * W * 3, W * 3, yuv_h, blk, tick[0], ups[tick[0] % 2])
+                ticks.append(tick[0])
+                tick[0] += 1
+                vs.append(views[(off + i * batch + j) % len(views)])
+            F.fvv_synthesize_batch(ctx, vs, ticks, out_d, [W * 3] * batch, None, syn)
+            with torch.cuda.stream(syn):
+                for j in range(batch):
+                    out_h[j].view(-1).copy_(out_d[j].view(-1), non_blocking=True)
+
+        for i in range(warmup):
+            step(i)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for i in range(steps):
+            step(warmup + i)
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+    finally:
+        F.fvv_destroy(ctx)
+    return {"value": steps * batch / el, "unit": UNIT, "h2d_bytes_per_step": int(batch * (rgb_h.numel() + yuv_h.numel())),
+            "d2h_bytes_per_step": int(batch * H * W * 3),
+            "depth": "YUV420 depth frames (Eq. (2), (3)), z_near 0.3 m, z_far 10 m"}
+
+
 def adaptive_e2e_bench(F, wl, rgb_h, dep_h, slots, batch, steps, warmup, off=0):
     """End to end with adaptive view transmission (Sec. V-C) at the paper's
     settings: each view's tick carries only the N_Tx = 5 cameras nearest it
@@ -1081,9 +1140,10 @@ def run_fvv(args):
                "h2d_bytes_per_step": int(Bsz * (rgb_h.numel() + dep_h.numel() * 2)),
                "d2h_bytes_per_step": int(Bsz * H * W * 3)}
 
-    e2e_adaptive = None
+    e2e_adaptive = e2e_yuv = None
     if not args.no_e2e and world == 1 and not args.main_only:
         e2e_adaptive = adaptive_e2e_bench(F, wl, rgb_h, dep_h, slots, Bsz, args.steps, args.warmup)
+        e2e_yuv = yuv_e2e_bench(F, wl, rgb_h, dep_h, slots, Bsz, args.steps, args.warmup)
 
     serve = None
     if not args.no_serve and world == 1 and not args.main_only:
@@ -1161,7 +1221,7 @@ def run_fvv(args):
                              "resident" % (slots, K * H * W * 6 / 1e6),
                        "parallelism": "replicas" if world > 1 else "single"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "serve": serve, "refine": refine, "codec": codec,
-            "layered": layered, "jbf": jbf, "e2e_adaptive": e2e_adaptive, "pixel_weights": pixel_weights,
+            "layered": layered, "jbf": jbf, "e2e_adaptive": e2e_adaptive, "e2e_yuv": e2e_yuv, "pixel_weights": pixel_weights,
             "gpu_launches": int(launches), "clocks": clocks.summary(),
             "kernel_ms": {k: v[2] for k, v in stats.items()},
         }

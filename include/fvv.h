@@ -298,6 +298,17 @@ fvv_status fvv_upload_frame_yuv(fvv_ctx* ctx, int32_t cam, const uint8_t* rgb, s
                                 size_t y_pitch, const uint8_t* u, const uint8_t* v, size_t uv_pitch, uint64_t tick,
                                 void* stream);
 
+/* Every camera of one tick with YUV420 depth, in one batched upload: camera
+ * k's RGB8 rows at rgb + k * rgb_cam_stride (pitch rgb_pitch) and its depth
+ * as one dense planar YUV420 frame at yuv + k * yuv_cam_stride (Y: height
+ * rows of width bytes, then U and V: height/2 rows of width/2 bytes each).
+ * Cameras of one size, even width and height, each with a codec set; rgb and
+ * yuv both host or both device memory.  Decoded like fvv_upload_frame_yuv
+ * (and pre-filtered when jbf_radius > 0).  Errors: INVALID_ARG, STATE (a
+ * camera without codec, or a tick older than its slot's), CUDA. */
+fvv_status fvv_upload_frames_yuv(fvv_ctx* ctx, const uint8_t* rgb, size_t rgb_cam_stride, size_t rgb_pitch,
+                                 const uint8_t* yuv, size_t yuv_cam_stride, uint64_t tick, void* stream);
+
 /* ---- serving loop (continuous batching of many viewers' requests) ------
  * The paper serves one viewer whose viewpoint commands reach the edge server
  * and wait for the next synthesised frame (Sec. VIII, motion-to-photon

@@ -423,8 +423,11 @@ fvv_status fvv::upload_frame(fvv_ctx* c, int cam, const uint8_t* rgb, size_t rgb
 // The cameras of `mask` (all of one size) for one tick in one launch, after
 // at most two bulk host-to-device copies into the context's staging buffer;
 // camera blocks are packed in ascending camera order.
+// With yuv, each camera's depth block is a dense planar YUV420 depth frame
+// (Eq. (3)) decoded on the way in; dp is unused then.
 static fvv_status upload_all(fvv_ctx* c, uint64_t mask, const uint8_t* rgb, size_t rcs, size_t rp,
-                             const uint8_t* depth, size_t dcs, size_t dp, uint64_t tick, cudaStream_t s, bool host)
+                             const uint8_t* depth, size_t dcs, size_t dp, uint64_t tick, cudaStream_t s, bool host,
+                             bool yuv = false)
 {
     using namespace fvv;
     int cams[kMaxCams], K = 0;
@@ -433,8 +436,17 @@ static fvv_status upload_all(fvv_ctx* c, uint64_t mask, const uint8_t* rgb, size
     if (K == 0) return fail(FVV_ERR_INVALID_ARG, "camera mask selects no camera");
     const int W = c->cams[cams[0]].width, H = c->cams[cams[0]].height;
     if (rp < size_t(W) * 3) return fail(FVV_ERR_INVALID_ARG, "rgb_pitch < 3 * width");
-    if (dp < size_t(W) * 2 || dp % 2) return fail(FVV_ERR_INVALID_ARG, "depth_pitch < 2 * width or odd");
-    if (dcs % 2) return fail(FVV_ERR_INVALID_ARG, "depth camera stride must be even");
+    const size_t yuv_bytes = size_t(W) * H + 2 * (size_t(W / 2) * (H / 2));
+    if (yuv) {
+        if (W % 2 || H % 2) return fail(FVV_ERR_INVALID_ARG, "YUV420 depth needs even width and height");
+        if (dcs < yuv_bytes) return fail(FVV_ERR_INVALID_ARG, "depth camera stride < one YUV420 frame");
+        for (int i = 0; i < K; ++i)
+            if (!codec_decode_table(c, cams[i]))
+                return fail(FVV_ERR_STATE, "camera " + std::to_string(cams[i]) + " has no depth codec");
+    } else {
+        if (dp < size_t(W) * 2 || dp % 2) return fail(FVV_ERR_INVALID_ARG, "depth_pitch < 2 * width or odd");
+        if (dcs % 2) return fail(FVV_ERR_INVALID_ARG, "depth camera stride must be even");
+    }
     const int si = int(tick % uint64_t(c->slots));
     SlotState& S = c->slot[si];
     if (S.any && tick < S.tick)
@@ -451,7 +463,7 @@ static fvv_status upload_all(fvv_ctx* c, uint64_t mask, const uint8_t* rgb, size
     if (host) {
         c->stage_all_next ^= 1;
         const size_t rspan = size_t(K - 1) * rcs + size_t(H - 1) * rp + size_t(W) * 3;
-        const size_t dspan = size_t(K - 1) * dcs + size_t(H - 1) * dp + size_t(W) * 2;
+        const size_t dspan = size_t(K - 1) * dcs + (yuv ? yuv_bytes : size_t(H - 1) * dp + size_t(W) * 2);
         const size_t doff = align_up(rspan, 256);
         if (c->stage_all_bytes[sb] < doff + dspan) {
             FVV_CUDA(cudaEventSynchronize(c->stage_all_free[sb]));
@@ -486,9 +498,22 @@ static fvv_status upload_all(fvv_ctx* c, uint64_t mask, const uint8_t* rgb, size
     u.n_cams = K;
     u.dpitch = c->dpitch[cams[0]];
     u.rpitch = c->rpitch[cams[0]];
+    u.yuv = yuv ? 1 : 0;
+    const bool jbf = c->opt.jbf_radius > 0;
     for (int i = 0; i < K; ++i) {
         u.off_depth[i] = c->off_depth[cams[i]];
         u.off_rgba[i] = c->off_rgba[cams[i]];
+        u.lut[i] = yuv ? codec_decode_table(c, cams[i]) : nullptr;
+        u.ddst[i] = nullptr;
+        if (yuv && jbf) {
+            // the decoded codes go to the camera's unfiltered-code buffer;
+            // the pre-filter then writes the slot
+            const int k = cams[i];
+            if (!c->jbf_tmp[k])
+                FVV_TRY(dev_alloc(c, reinterpret_cast<void**>(&c->jbf_tmp[k]),
+                                  size_t(c->cams[k].height) * c->dpitch[k] * 2));
+            u.ddst[i] = c->jbf_tmp[k];
+        }
     }
     FVV_TRY(run_kernel(c, kPack, s, [&] { return launch_upload_all(u, s); }));
     if (c->opt.jbf_radius > 0) {
@@ -498,7 +523,8 @@ static fvv_status upload_all(fvv_ctx* c, uint64_t mask, const uint8_t* rgb, size
         jbf_params(c->opt, W, H, &P);
         for (int i = 0; i < K; ++i)
             P.cam[i] = JbfCam{r + size_t(i) * rcs, int64_t(rp),
-                              reinterpret_cast<const uint16_t*>(d + size_t(i) * dcs), int64_t(dp / 2),
+                              yuv ? u.ddst[i] : reinterpret_cast<const uint16_t*>(d + size_t(i) * dcs),
+                              yuv ? int64_t(c->dpitch[cams[i]]) : int64_t(dp / 2),
                               reinterpret_cast<uint16_t*>(u.slot + c->off_depth[cams[i]]),
                               int64_t(c->dpitch[cams[i]])};
         FVV_TRY(run_kernel(c, kJbf, s, [&] { return launch_jbf(P, K, s); }));
@@ -1080,6 +1106,22 @@ fvv_status fvv_upload_frames_subset(fvv_ctx* c, uint64_t cam_mask, const uint8_t
         ++i;
     }
     return FVV_OK;
+}
+
+fvv_status fvv_upload_frames_yuv(fvv_ctx* c, const uint8_t* rgb, size_t rgb_cam_stride, size_t rgb_pitch,
+                                 const uint8_t* yuv, size_t yuv_cam_stride, uint64_t tick, void* stream)
+{
+    if (!c) return fail(FVV_ERR_INVALID_ARG, "ctx is NULL");
+    if (!rgb || !yuv) return fail(FVV_ERR_INVALID_ARG, "rgb and yuv must be non-NULL");
+    cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : c->own;
+    std::lock_guard<std::recursive_mutex> lock(c->mu);
+    for (int k = 1; k < c->n_cams; ++k)
+        if (c->cams[k].width != c->cams[0].width || c->cams[k].height != c->cams[0].height)
+            return fail(FVV_ERR_INVALID_ARG, "fvv_upload_frames_yuv needs cameras of one size");
+    const fvv::MemKind kr = fvv::mem_kind(rgb), ky = fvv::mem_kind(yuv);
+    if (kr != ky) return fail(FVV_ERR_INVALID_ARG, "rgb and yuv must both be host or both device memory");
+    return upload_all(c, c->full_mask, rgb, rgb_cam_stride, rgb_pitch, yuv, yuv_cam_stride, 0, tick, s,
+                      kr == fvv::MemKind::Host, true);
 }
 
 fvv_status fvv_upload_frames(fvv_ctx* c, const uint8_t* rgb, size_t rgb_cam_stride, size_t rgb_pitch,

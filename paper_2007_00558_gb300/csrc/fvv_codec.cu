@@ -171,6 +171,13 @@ cudaError_t launch_yuv_decode(const YuvDepth& f, int width, int height, uint16_t
     return cudaGetLastError();
 }
 
+const uint16_t* codec_decode_table(fvv_ctx* c, int cam)
+{
+    CodecState* K = c->codec;
+    if (!K || cam < 0 || cam >= int(K->set.size()) || !K->set[cam]) return nullptr;
+    return K->dec[cam];
+}
+
 void codec_destroy(fvv_ctx* c)
 {
     CodecState* K = c->codec;

@@ -104,6 +104,10 @@ struct CodecState;
 // slot + off_rgba[k] (pitch rpitch texels), its uint16 depth rows at
 // depth + k * depth_cam_stride (pitch depth_pitch bytes) are copied to
 // slot + off_depth[k] (pitch dpitch elements).
+// With yuv set, camera i's depth is a dense planar YUV420 depth frame (Eq.
+// (3)) at depth + i * depth_cam_stride (Y rows of W bytes, then U and V rows
+// of W/2), decoded through lut[i]; ddst[i], when set, replaces the slot as
+// the destination of camera i's depth rows (pitch dpitch).
 struct UploadAll {
     const uint8_t* rgb;
     size_t rgb_cam_stride, rgb_pitch;
@@ -111,7 +115,10 @@ struct UploadAll {
     size_t depth_cam_stride, depth_pitch;
     uint8_t* slot;
     int W, H, n_cams, dpitch, rpitch;
+    int yuv;
     uint64_t off_depth[kMaxCams], off_rgba[kMaxCams];
+    const uint16_t* lut[kMaxCams];
+    uint16_t* ddst[kMaxCams];
 };
 cudaError_t launch_upload_all(const UploadAll& u, cudaStream_t stream);
 
@@ -182,6 +189,8 @@ fvv_status upload_frame(fvv_ctx* c, int cam, const uint8_t* rgb, size_t rgb_pitc
 cudaError_t launch_yuv_decode(const YuvDepth& f, int width, int height, uint16_t* out, size_t out_pitch,
                               cudaStream_t s);
 void codec_destroy(fvv_ctx* c);
+// Camera cam's decode table (4096 depth codes) or NULL when it has no codec.
+const uint16_t* codec_decode_table(fvv_ctx* c, int cam);
 // The refinement network for the serving loop: whether it is initialised, and
 // its forward pass on `s` without waiting (device batch; out_rgb is
 // [n][h][w][3] uint8).  A bounded-wait timeout leaves the device flag raised

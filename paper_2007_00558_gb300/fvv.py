@@ -129,6 +129,7 @@ def load() -> C.CDLL:
             "fvv_upload_frames": [P, P, S, S, P, S, S, U64, P],
             "fvv_set_bg_depth": [P, I, P, S],
             "fvv_upload_frames_subset": [P, U64, P, S, S, P, S, S, U64, P],
+            "fvv_upload_frames_yuv": [P, P, S, S, P, S, U64, P],
             "fvv_select_cameras": [C.POINTER(fvv_rig), I, C.POINTER(fvv_camera), I, C.POINTER(U64)],
             "fvv_depth_jbf": [P, S, P, S, P, S, I, I, C.POINTER(fvv_options), P],
             "fvv_latest_tick": [P, C.POINTER(U64)],
@@ -280,6 +281,13 @@ def fvv_upload_frames_subset(ctx: int, cam_mask: int, rgb, rgb_cam_stride: int, 
     _check(load().fvv_upload_frames_subset(ctx, cam_mask, ptr(rgb), rgb_cam_stride, rgb_pitch, ptr(depth),
                                            depth_cam_stride, depth_pitch, tick, stream_handle(stream)),
            "fvv_upload_frames_subset")
+
+
+def fvv_upload_frames_yuv(ctx: int, rgb, rgb_cam_stride: int, rgb_pitch: int, yuv, yuv_cam_stride: int, tick: int,
+                          stream=None) -> None:
+    """Every camera of one tick with dense planar YUV420 depth frames."""
+    _check(load().fvv_upload_frames_yuv(ctx, ptr(rgb), rgb_cam_stride, rgb_pitch, ptr(yuv), yuv_cam_stride, tick,
+                                        stream_handle(stream)), "fvv_upload_frames_yuv")
 
 
 def fvv_select_cameras(rig_: fvv_rig, views, n_tx: int) -> int:

@@ -127,3 +127,51 @@ def test_codec_errors(setup):
         assert e.value.code == F.FVV_ERR_INVALID_ARG
     finally:
         F.fvv_destroy(ctx)
+
+
+@pytest.mark.parametrize("mode", ["host", "device", "jbf", "layered"])
+def test_batched_yuv_tick_upload(setup, oracle_mod, mode):
+    """A whole tick with YUV420 depth in one call (dense planar frames, all
+    cameras): the z-buffer keys equal the oracle's on the oracle-decoded
+    depth (pre-filtered with the filter on; with background codes in the
+    layered form)."""
+    import torch
+    from oracle import jbf as J
+    F, ctx0, wl = setup
+    cams = wl["cams"]
+    H, W = cams[0].height, cams[0].width
+    lay = S.workload("layered_9cam_1280x720", scale=0.25) if mode == "layered" else None
+    src = lay if lay is not None else wl
+    opts = {"jbf": dict(jbf_radius=2), "layered": dict(layered=1)}.get(mode, {})
+    ctx = F.fvv_create(F.rig(src["cams"], src["look_at"]), F.fvv_default_options(**opts))
+    try:
+        blocks, dec = [], []
+        for k in range(len(cams)):
+            F.fvv_set_depth_codec(ctx, k, F.fvv_depth_codec_default(**CODEC))
+            if lay is not None:
+                F.fvv_set_bg_depth(ctx, k, np.ascontiguousarray(lay["bg"][k]), W * 2)
+            y, u, v = K.encode(np.asarray(src["depth"][k]), unit_m=0.001, **CODEC)
+            blocks.append(np.concatenate([y.reshape(-1), u.reshape(-1), v.reshape(-1)]))
+            dec.append(K.decode(y, u, v, CODEC["z_near"], CODEC["z_far"], 0.001))
+        yuv = np.ascontiguousarray(np.stack(blocks))
+        rgb = np.ascontiguousarray(src["rgb"])
+        if mode == "device":
+            yuv, rgb = torch.from_numpy(yuv).cuda(), torch.from_numpy(rgb).cuda()
+        F.fvv_upload_frames_yuv(ctx, rgb, H * W * 3, W * 3, yuv, blocks[0].size, 0)
+        dec = np.stack(dec)
+        if mode == "jbf":
+            dec = np.stack([J.jbf(dec[k], src["rgb"][k], radius=2) for k in range(len(cams))])
+        v = src["views"][33]
+        keys = torch.zeros((H, W), dtype=torch.int64, device="cuda")
+        out = torch.zeros((H, W * 3), dtype=torch.uint8, device="cuda")
+        F.fvv_synthesize(ctx, v, out, W * 3, F.aux(keys=keys))
+        torch.cuda.synchronize()
+        if lay is not None:
+            ref = oracle_mod.synthesize_layered(src["cams"], src["rgb"], dec, lay["bg"], v, src["look_at"])
+        else:
+            ref = oracle_mod.synthesize(src["cams"], src["rgb"], dec, v, src["look_at"])
+        assert np.array_equal(keys.cpu().numpy().view(np.uint64), ref["keys"])
+        d = np.abs(out.cpu().numpy().reshape(H, W, 3).astype(int) - ref["rgb"].astype(int))
+        assert (d <= 1).all(axis=-1).mean() >= 0.999
+    finally:
+        F.fvv_destroy(ctx)
