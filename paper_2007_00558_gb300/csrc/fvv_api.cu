@@ -584,7 +584,9 @@ void fvv::scratch_free(fvv_ctx* c, BatchScratch& S)
 
 size_t fvv::view_keys(const fvv_view& v, bool layered)
 {
-    return align_up(size_t(v.width) * v.height, 16) * (layered ? 2 : 1);
+    // layered: the FG z-buffer, the BG z-buffer and the BG layer after its
+    // crack filter
+    return align_up(size_t(v.width) * v.height, 16) * (layered ? 3 : 1);
 }
 
 size_t fvv::view_stage_bytes(const fvv_view& v, uint8_t* out_rgb, const fvv_aux* aux)
@@ -705,8 +707,11 @@ fvv_status fvv::run_batch(fvv_ctx* c, BatchScratch& S, int n, const fvv_view* vi
         D.keys = S.keys + koff;
         koff += align_up(np, 16);
         D.keys_bg = nullptr;
+        D.keys_bgf = nullptr;
         if (c->opt.layered) {
             D.keys_bg = S.keys + koff;
+            koff += align_up(np, 16);
+            D.keys_bgf = c->opt.crack_filter ? S.keys + koff : D.keys_bg;
             koff += align_up(np, 16);
         }
         CamGeom* g = gh + size_t(i) * c->n_cams;
@@ -778,6 +783,8 @@ fvv_status fvv::run_batch(fvv_ctx* c, BatchScratch& S, int n, const fvv_view* vi
     FVV_TRY(run_kernel(c, kSplat, s, [&] {
         return fvv::launch_warp_splat(vdev, n, max_chunks, c->frames_dev, s, c->opt.layered != 0);
     }));
+    if (c->opt.layered && c->opt.crack_filter)
+        FVV_TRY(run_kernel(c, kResolve, s, [&] { return fvv::launch_crack_bg(vdev, n, max_h, max_w, s); }));
     for (size_t r = 0; r < raw_copies.size(); ++r)
         FVV_CUDA(cudaMemcpyAsync(raw_copies[r].first, raw_copies[r].second, raw_bytes[r],
                                  cudaMemcpyDefault, s));

@@ -55,6 +55,7 @@ struct alignas(16) ViewDesc {
     float vk[4];                     // the view's cx, cy, 1/fx, 1/fy (per-pixel weights)
     unsigned long long* keys;        // scratch z-buffer [Hv * Wv] (the FG layer when layered)
     unsigned long long* keys_bg;     // layered: the BG layer's z-buffer [Hv * Wv], else NULL
+    unsigned long long* keys_bgf;    // layered: the BG layer after the crack filter (keys_bg without it)
     uint8_t* out_rgb;                // [Hv] rows of 3 * Wv bytes
     int64_t out_pitch;               // bytes
     float* out_depth;                // nullable [Hv * Wv]
@@ -71,6 +72,8 @@ cudaError_t launch_clear_keys(unsigned long long* keys, size_t n, cudaStream_t s
 // layered: FG/BG layers (each view's keys_bg set, frames' bg models used).
 cudaError_t launch_warp_splat(const ViewDesc* views, int n_views, int max_chunks,
                               const FrameRef* frames, cudaStream_t stream, bool layered = false);
+// Layered: the crack filter of the BG layer (keys_bg -> keys_bgf), one pass.
+cudaError_t launch_crack_bg(const ViewDesc* views, int n_views, int max_h, int max_w, cudaStream_t stream);
 cudaError_t launch_resolve(const ViewDesc* views, int n_views, int max_h, int max_w, int n_cams,
                            bool top3, const FrameRef* frames, cudaStream_t stream, bool layered = false,
                            bool pixel_weights = false);

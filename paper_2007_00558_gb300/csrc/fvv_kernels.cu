@@ -45,8 +45,8 @@ __host__ __device__ inline SmemLayout resolve_layout(int W, int n_cams, bool lay
 {
     SmemLayout L;
     size_t o = 0;
-    // layered: the BG layer's ring follows the FG layer's
-    L.ring = o;   o = align16(o + size_t(layered ? 2 : 1) * kRing * W * sizeof(unsigned long long));
+    (void)layered;                // the layered form reads its BG keys from the filtered z-buffer
+    L.ring = o;   o = align16(o + size_t(kRing) * W * sizeof(unsigned long long));
     L.rgb = o;    o = align16(o + size_t(W) * 4);
     L.dep = o;    o = align16(o + size_t(W) * 4);
     L.hole = o;   o = align16(o + size_t(W));
@@ -266,19 +266,16 @@ __device__ __forceinline__ unsigned long long nb_key(const unsigned long long* r
     return (x < 0 || x >= Wv) ? kKeyEmpty : row[x];
 }
 
-__device__ __forceinline__ unsigned long long crack_rule(const unsigned long long* up,
-                                                         const unsigned long long* mid,
-                                                         const unsigned long long* dn, int Wv, int x,
-                                                         unsigned long long kp, float f1)
+// The rule for a pixel whose neighbour at (dy, dx) is get(dy, dx).
+template <class Get>
+__device__ __forceinline__ unsigned long long crack_rule_at(Get get, unsigned long long kp, float f1)
 {
-    const unsigned long long* ra[4] = {mid, up, up, up};
-    const unsigned long long* rb[4] = {mid, dn, dn, dn};
-    const int ax[4] = {-1, 0, -1, 1};
-    const int bx[4] = {1, 0, 1, -1};
+    const int ady[4] = {0, -1, -1, -1}, adx[4] = {-1, 0, -1, 1};
+    const int bdy[4] = {0, 1, 1, 1}, bdx[4] = {1, 0, 1, -1};
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-        const unsigned long long a = nb_key(ra[q], Wv, x + ax[q]);
-        const unsigned long long b = nb_key(rb[q], Wv, x + bx[q]);
+        const unsigned long long a = get(ady[q], adx[q]);
+        const unsigned long long b = get(bdy[q], bdx[q]);
         if (a == kKeyEmpty || b == kKeyEmpty)
             continue;
         const float za = key_z(a), zb = key_z(b);
@@ -290,6 +287,33 @@ __device__ __forceinline__ unsigned long long crack_rule(const unsigned long lon
             return a < b ? a : b;
     }
     return kp;
+}
+
+__device__ __forceinline__ unsigned long long crack_rule(const unsigned long long* up,
+                                                         const unsigned long long* mid,
+                                                         const unsigned long long* dn, int Wv, int x,
+                                                         unsigned long long kp, float f1)
+{
+    const unsigned long long* rows[3] = {up, mid, dn};
+    return crack_rule_at([&](int dy, int dx) { return nb_key(rows[dy + 1], Wv, x + dx); }, kp, f1);
+}
+
+// Layered form: the BG layer's crack filter as its own pass, read straight
+// from the z-buffer (L1/L2), so the resolve stages one key ring only.
+__global__ void __launch_bounds__(256) k_crack_bg(const ViewDesc* __restrict__ views)
+{
+    const ViewDesc* V = views + blockIdx.z;
+    const int Wv = V->Wv, Hv = V->Hv;
+    const int x = blockIdx.x * 256 + threadIdx.x, y = blockIdx.y;
+    if (x >= Wv || y >= Hv)
+        return;
+    const unsigned long long* kb = V->keys_bg;
+    const float f1 = __fadd_rn(1.0f, V->tau_crack);
+    auto get = [&](int dy, int dx) {
+        const int yy = y + dy, xx = x + dx;
+        return (yy < 0 || yy >= Hv || xx < 0 || xx >= Wv) ? kKeyEmpty : __ldg(kb + size_t(yy) * Wv + xx);
+    };
+    V->keys_bgf[size_t(y) * Wv + x] = crack_rule_at(get, __ldg(kb + size_t(y) * Wv + x), f1);
 }
 
 __device__ __forceinline__ void cp_async8(void* smem_dst, const void* gsrc)
@@ -381,11 +405,10 @@ __device__ __forceinline__ float pixel_weight(float cx, float cy, float cz, floa
 
 // kPixW: per-pixel angular weights (each contribution weighted by the angle
 // at its surface point) instead of the view's per-camera weights.
-// Three CTAs per SM in the single-layer forms (a 64-register cap for four
-// cost more in the gathers' overlap than the extra warps gained); the
-// layered forms' two key rings allow two.
+// Three CTAs per SM (a 64-register cap for four cost more in the gathers'
+// overlap than the extra warps gained).
 template <bool kTop3, bool kLayered, bool kPixW>
-__global__ void __launch_bounds__(kResolveThreads, kLayered ? 2 : 3)
+__global__ void __launch_bounds__(kResolveThreads, 3)
 k_resolve(const ViewDesc* __restrict__ views, const FrameRef* __restrict__ frames, int band)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -411,25 +434,15 @@ k_resolve(const ViewDesc* __restrict__ views, const FrameRef* __restrict__ frame
     constexpr int NT = kResolveThreads;
     const unsigned long long* keys = V->keys;
 
-    const unsigned long long* keys_bg = V->keys_bg;
+    const unsigned long long* keys_bgf = V->keys_bgf;
     auto ring_row = [&](int yy) { return s_ring + size_t((yy + kRing) & (kRing - 1)) * Wv; };
-    auto ring_row_bg = [&](int yy) { return ring_row(yy) + size_t(kRing) * Wv; };
     auto fetch_row = [&](int yy) {           // async copy of key row yy (empty outside)
         unsigned long long* dst = ring_row(yy);
         if (yy >= 0 && yy < Hv) {
             const unsigned long long* src = keys + size_t(yy) * Wv;
             for (int x = tid; x < Wv; x += NT) cp_async8(dst + x, src + x);
-            if (kLayered) {
-                unsigned long long* dstb = ring_row_bg(yy);
-                const unsigned long long* srcb = keys_bg + size_t(yy) * Wv;
-                for (int x = tid; x < Wv; x += NT) cp_async8(dstb + x, srcb + x);
-            }
         } else {
             for (int x = tid; x < Wv; x += NT) dst[x] = kKeyEmpty;
-            if (kLayered) {
-                unsigned long long* dstb = ring_row_bg(yy);
-                for (int x = tid; x < Wv; x += NT) dstb[x] = kKeyEmpty;
-            }
         }
     };
     fetch_row(y0 - 1);
@@ -496,11 +509,7 @@ k_resolve(const ViewDesc* __restrict__ views, const FrameRef* __restrict__ frame
             // layer is resolved only where the filtered FG layer is empty
             bool bg_layer = false;
             if (kLayered && key == kKeyEmpty) {
-                const unsigned long long* bU = ring_row_bg(y - 1);
-                const unsigned long long* bC = ring_row_bg(y);
-                const unsigned long long* bD = ring_row_bg(y + 1);
-                const unsigned long long kb = bC[x];
-                key = crack ? crack_rule(bU, bC, bD, Wv, x, kb, f1) : kb;
+                key = keys_bgf[rowbase + x];          // filtered by k_crack_bg (raw without the filter)
                 bg_layer = true;
             }
             if (okeys) okeys[rowbase + x] = key;
@@ -754,6 +763,15 @@ cudaError_t launch_warp_splat(const ViewDesc* views, int n_views, int max_chunks
         k_warp_splat<true><<<grid, kSplatThreads, 0, stream>>>(views, frames);
     else
         k_warp_splat<false><<<grid, kSplatThreads, 0, stream>>>(views, frames);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_crack_bg(const ViewDesc* views, int n_views, int max_h, int max_w, cudaStream_t stream)
+{
+    if (n_views <= 0 || max_h <= 0 || max_w <= 0) return cudaSuccess;
+    dim3 grid(static_cast<unsigned>((max_w + 255) / 256), static_cast<unsigned>(max_h),
+              static_cast<unsigned>(n_views));
+    k_crack_bg<<<grid, 256, 0, stream>>>(views);
     return cudaGetLastError();
 }
 

@@ -408,8 +408,9 @@ fvv_status fvv_serve_start(fvv_ctx* c, const fvv_serve_cfg* cfg_in)
     const size_t room = per_lane - 2 * pb;
     size_t lane_px = 0;
     if (cfg.refine) {
-        // per lane and pixel: 8 bytes of keys per layer and the refinement buffers
-        const size_t layers = c->opt.layered ? 2 : 1;
+        // per lane and pixel: 8 bytes of keys per z-buffer (three when
+        // layered) and the refinement buffers
+        const size_t layers = c->opt.layered ? 3 : 1;
         lane_px = room / (8 * layers + fvv::kRefineBytesPerPixel) / 64 * 64;
         st->lane_keys = lane_px * layers;
         st->lane_stage = 0;
