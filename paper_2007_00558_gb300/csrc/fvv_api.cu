@@ -48,7 +48,7 @@ fvv_status fvv::fail(fvv_status code, const std::string& msg)
 }
 
 const char* const fvv::kKernelName[fvv::kNumKernels] = {"clear_keys", "warp_splat", "resolve",
-                                                        "pack_rgba", "yuv_decode", "jbf"};
+                                                        "pack_rgba", "yuv_decode", "jbf", "crack_bg"};
 
 fvv::MemKind fvv::mem_kind(const void* p)
 {
@@ -784,7 +784,7 @@ fvv_status fvv::run_batch(fvv_ctx* c, BatchScratch& S, int n, const fvv_view* vi
         return fvv::launch_warp_splat(vdev, n, max_chunks, c->frames_dev, s, c->opt.layered != 0);
     }));
     if (c->opt.layered && c->opt.crack_filter)
-        FVV_TRY(run_kernel(c, kResolve, s, [&] { return fvv::launch_crack_bg(vdev, n, max_h, max_w, s); }));
+        FVV_TRY(run_kernel(c, fvv::kCrackBg, s, [&] { return fvv::launch_crack_bg(vdev, n, max_h, max_w, s); }));
     for (size_t r = 0; r < raw_copies.size(); ++r)
         FVV_CUDA(cudaMemcpyAsync(raw_copies[r].first, raw_copies[r].second, raw_bytes[r],
                                  cudaMemcpyDefault, s));

@@ -51,7 +51,7 @@ struct ParamBlock {
     bool pending = false;
 };
 
-enum Kid { kClear = 0, kSplat, kResolve, kPack, kDecode, kJbf, kNumKernels };
+enum Kid { kClear = 0, kSplat, kResolve, kPack, kDecode, kJbf, kCrackBg, kNumKernels };
 extern const char* const kKernelName[kNumKernels];
 
 struct KernelStat {
