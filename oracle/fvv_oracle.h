@@ -14,7 +14,8 @@
  * them black) unless the optional row-wise hole fill is on.
  *
  * The paper prints no formula for any of these steps.  The readings taken
- * here (FMA-free FP32 warp, 64-bit z-buffer keys, the 3x3 crack rule, the
+ * here (FP32 warp in explicitly rounded operations, 64-bit z-buffer keys,
+ * the 3x3 crack rule, the
  * angular weights, the visibility test, the hole-fill rule) are stated
  * beside each function in fvv_oracle.c.
  *

@@ -13,8 +13,10 @@
 // Readings where the paper is silent: Eq. (2) rounds half up; bit i of the
 // first pixel's 4 MSBs goes to bit 2i of U (V), the second pixel's to bit
 // 2i + 1; the decoder inverts Eq. (2) as 1 / (1/z_far + (Y - 2)(1/z_near -
-// 1/z_far) / 4093); reserved codes 0 (background) and 1 (out of range or no
-// depth) decode to depth code 0, and depth code 0 encodes to 1.
+// 1/z_far) / 4093) and rounds to depth codes in [1, 65534]; reserved code 1
+// (out of range or no depth) decodes to depth code 0 and code 0 (background)
+// to the background signal 65535; depth code 0 encodes to 1 and the signal
+// to 0.
 #include <cmath>
 #include <cstring>
 #include <vector>
