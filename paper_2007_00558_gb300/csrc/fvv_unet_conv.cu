@@ -2,15 +2,18 @@
 // an implicit GEMM on the sm_103a tensor cores (tcgen05, TMEM, TMA).
 //
 // GEMM view: M = 128 consecutive output pixels of one image row, N = the
-// output channels, K = 9 taps x input channels.  A persistent CTA (one per
-// SM) walks the pixel tiles.  Input channels are taken in groups of one
+// output channels, K = 9 taps x input channels.  A tile is R such rows
+// (R = 4 for 32 output channels, 2 for up to 64, else 1).  A persistent CTA
+// (one per SM) walks the tiles.  Input channels are taken in groups of one
 // 64-byte row (32 bf16 or 64 e4m3 channels).  For each tile and group, ONE
-// TMA copy brings the halo -- rows y-1..y+1, pixels x0-1..x0+128, zero
+// TMA copy brings the halo -- rows y0-1..y0+R, pixels x0-1..x0+128, zero
 // outside the image (the convolution's padding) and beyond the last channel
-// -- into shared memory as 3 x 130 rows of 64 bytes with the 64-byte swizzle.
-// Operand A of tap (ky, kx) is that same halo seen through a descriptor
-// whose start lies 130 ky + kx rows further on: nine taps cost nine
-// descriptors, not nine copies.  The weights [cout][ky][kx][cin] stay
+// -- into shared memory as (R+2) x 130 rows of 64 bytes with the 64-byte
+// swizzle.  Operand A of output row r and tap (ky, kx) is that same halo
+// seen through a descriptor whose start lies 130 (r + ky) + kx rows further
+// on: nine taps cost nine descriptors, not nine copies, and the halo's two
+// extra rows are shared by the R output rows (narrow layers are bound by
+// moving the halo).  The weights [cout][ky][kx][cin] stay
 // resident in shared memory when they fit; otherwise they stream through a
 // ring of one-ky slices (three taps).  The fp32 accumulators live in TMEM,
 // double-buffered: four epilogue warps drain tile i (scale, bias, ReLU,
@@ -37,8 +40,6 @@ namespace {
 constexpr int kTileM = 128;
 constexpr int kHaloPx = kTileM + 2;                    // 130 halo pixels per row
 constexpr int kRow = 64;                               // bytes of one pixel row of a channel group
-constexpr int kHaloBytes = 3 * kHaloPx * kRow;         // 24,960
-constexpr int kHaloStage = 25 * 1024;                  // halo slot, 1024-aligned
 constexpr int kThreads = 192;
 constexpr int kMaxStages = 8;
 constexpr int kSmemLimit = 227 * 1024;
@@ -50,11 +51,17 @@ struct ConvCfg {
     static constexpr int kTap = COUT * kRow;           // B tile of one tap (COUT rows of 64 bytes)
     static constexpr int kSlice = 3 * kTap;            // the three taps of one ky
     static constexpr int kGroup = 9 * kTap;            // all taps of one channel group
-    static constexpr int kAcc = (COUT + 31) / 32 * 32; // TMEM columns between accumulators
-    static constexpr int kNumAcc = 4 * kAcc <= 512 ? 4 : 2;        // accumulator ring depth
-    static constexpr int kTmemCols = kNumAcc * kAcc <= 64 ? 64 : kNumAcc * kAcc <= 128 ? 128
-                                   : kNumAcc * kAcc <= 256 ? 256 : 512;
+    static constexpr int kAcc = (COUT + 31) / 32 * 32; // TMEM columns of one output row's accumulator
+    static constexpr int kRows = COUT <= 32 ? 4 : COUT <= 64 ? 2 : 1;   // output rows per tile
+    static constexpr int kTileAcc = kRows * kAcc;      // TMEM columns of one tile
+    static constexpr int kNumAcc = 4 * kTileAcc <= 512 ? 4 : 2;        // accumulator ring depth
+    static constexpr int kTmemCols = kNumAcc * kTileAcc <= 64 ? 64 : kNumAcc * kTileAcc <= 128 ? 128
+                                   : kNumAcc * kTileAcc <= 256 ? 256 : 512;
+    static constexpr int kHaloRows = kRows + 2;
+    static constexpr int kHaloBytes = kHaloRows * kHaloPx * kRow;
+    static constexpr int kHaloStage = (kHaloBytes + 1023) / 1024 * 1024;   // halo slot, 1024-aligned
     static_assert(kTap % 1024 == 0, "tap tiles stay 1024-byte aligned");
+    static_assert(kNumAcc * kTileAcc <= 512, "accumulators fit TMEM");
 };
 
 struct Plan {
@@ -67,16 +74,16 @@ Plan make_plan(int groups)
     using C = ConvCfg<COUT>;
     Plan p{};
     const int res = groups * C::kGroup;
-    if (kSmemFixed + res + 3 * kHaloStage <= kSmemLimit) {
+    if (kSmemFixed + res + 3 * C::kHaloStage <= kSmemLimit) {
         p.resident = 1;
-        p.hs = std::min(kMaxStages, (kSmemLimit - kSmemFixed - res) / kHaloStage);
+        p.hs = std::min(kMaxStages, (kSmemLimit - kSmemFixed - res) / C::kHaloStage);
         p.ws = 0;
-        p.smem = kSmemFixed + res + p.hs * kHaloStage;
+        p.smem = kSmemFixed + res + p.hs * C::kHaloStage;
     } else {
         p.resident = 0;
         p.hs = 3;
-        p.ws = std::min(kMaxStages, (kSmemLimit - kSmemFixed - p.hs * kHaloStage) / C::kSlice);
-        p.smem = kSmemFixed + p.hs * kHaloStage + p.ws * C::kSlice;
+        p.ws = std::min(kMaxStages, (kSmemLimit - kSmemFixed - p.hs * C::kHaloStage) / C::kSlice);
+        p.smem = kSmemFixed + p.hs * C::kHaloStage + p.ws * C::kSlice;
     }
     return p;
 }
@@ -164,7 +171,7 @@ k_conv3x3_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CU
     int* skip = reinterpret_cast<int*>(tmem_slot + 1);
     float* s_bias = reinterpret_cast<float*>(base + 512);          // [COUT] (<= 192 floats)
     uint8_t* sHalo = base + kHeader;
-    uint8_t* sW = sHalo + HS * kHaloStage;
+    uint8_t* sW = sHalo + HS * Cfg::kHaloStage;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) *skip = *reinterpret_cast<volatile int*>(P.err);
@@ -173,6 +180,8 @@ k_conv3x3_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CU
 
     const int Cin = P.Cin, H = P.H, Wd = P.W;
     const int G = (Cin + kPerGroup - 1) / kPerGroup;
+    constexpr int R = Cfg::kRows;
+    const int tiles_y = (H + R - 1) / R;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kMaxStages; ++s) {
@@ -211,8 +220,8 @@ k_conv3x3_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CU
             uint32_t qh = 0, qw = 0;
             bool ok = true;
             for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
-                const int xt = tile % P.tiles_x, row = tile / P.tiles_x;
-                const int y = row % H, n = row / H;
+                const int xt = tile % P.tiles_x, rb = tile / P.tiles_x;
+                const int y0 = (rb % tiles_y) * R, n = rb / tiles_y;
                 const int x0 = xt * kTileM;
                 for (int g = 0; g < G && ok; ++g) {
                     const int sh = int(qh % uint32_t(HS));
@@ -220,8 +229,9 @@ k_conv3x3_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CU
                         ok = false;
                         break;
                     }
-                    tc::mbar_arrive_expect_tx(&full_h[sh], kHaloBytes);
-                    tc::tma_load_4d(sHalo + sh * kHaloStage, &tmx, &full_h[sh], g * kPerGroup, x0 - 1, y - 1, n);
+                    tc::mbar_arrive_expect_tx(&full_h[sh], Cfg::kHaloBytes);
+                    tc::tma_load_4d(sHalo + sh * Cfg::kHaloStage, &tmx, &full_h[sh], g * kPerGroup, x0 - 1, y0 - 1,
+                                    n);
                     ++qh;
                     if (!resident) {
                         for (int ky = 0; ky < 3; ++ky, ++qw) {
@@ -257,7 +267,7 @@ k_conv3x3_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CU
                     break;
                 }
                 tc::fence_after_sync();
-                const uint32_t d = tmem + uint32_t(b * Cfg::kAcc);
+                const uint32_t d = tmem + uint32_t(b * Cfg::kTileAcc);
                 for (int g = 0; g < G; ++g) {
                     // TMA completion on the mbarrier orders the halo for the tensor
                     // cores (both async proxy): no tcgen05 fence here
@@ -265,15 +275,21 @@ k_conv3x3_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CU
                         ok = false;
                         break;
                     }
-                    const uint64_t da = dh0 + uint64_t((sh * kHaloStage) >> 4);
+                    const uint64_t da = dh0 + uint64_t((sh * Cfg::kHaloStage) >> 4);
                     const bool two = g < G - 1 || nks_last == 2;
                     const uint32_t acc0 = g != 0 ? 1u : 0u;
                     if (resident) {
                         const uint64_t db = dw0 + uint64_t((g * Cfg::kGroup) >> 4);
-                        if (two)
-                            mma_group<COUT, FP8, 2>(d, da, db, idesc, acc0);
-                        else
-                            mma_group<COUT, FP8, 1>(d, da, db, idesc, acc0);
+#pragma unroll
+                        for (int r = 0; r < R; ++r) {
+                            // output row r: its accumulator, the halo from row r on
+                            const uint32_t dr = d + uint32_t(r * Cfg::kAcc);
+                            const uint64_t dar = da + uint64_t((r * kHaloPx * kRow) >> 4);
+                            if (two)
+                                mma_group<COUT, FP8, 2>(dr, dar, db, idesc, acc0);
+                            else
+                                mma_group<COUT, FP8, 1>(dr, dar, db, idesc, acc0);
+                        }
                     } else {
                         for (int ky = 0; ky < 3; ++ky) {
                             if (!tc::mbar_wait(&full_w[sw], pw, P.err, 6)) {
@@ -281,12 +297,16 @@ k_conv3x3_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CU
                                 break;
                             }
                             const uint64_t db = dw0 + uint64_t((sw * Cfg::kSlice) >> 4);
-                            const uint64_t dak = da + uint64_t((ky * kHaloPx * kRow) >> 4);
                             const uint32_t a0 = acc0 | (ky != 0 ? 1u : 0u);
-                            if (two)
-                                mma_row<COUT, FP8, 2>(d, dak, db, idesc, a0);
-                            else
-                                mma_row<COUT, FP8, 1>(d, dak, db, idesc, a0);
+#pragma unroll
+                            for (int r = 0; r < R; ++r) {
+                                const uint32_t dr = d + uint32_t(r * Cfg::kAcc);
+                                const uint64_t dak = da + uint64_t(((r + ky) * kHaloPx * kRow) >> 4);
+                                if (two)
+                                    mma_row<COUT, FP8, 2>(dr, dak, db, idesc, a0);
+                                else
+                                    mma_row<COUT, FP8, 1>(dr, dak, db, idesc, a0);
+                            }
                             tc::mma_commit(&empty_w[sw]);      // the slice is free once these finish
                             if (++sw == WS) {
                                 sw = 0;
@@ -318,72 +338,76 @@ k_conv3x3_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CU
             const int b = tl % Cfg::kNumAcc;
             if (!tc::mbar_wait_sleep(&acc_full[b], (tl / Cfg::kNumAcc) & 1, P.err, 7)) break;
             tc::fence_after_sync();
-            const int xt = tile % P.tiles_x, row = tile / P.tiles_x;
+            const int xt = tile % P.tiles_x, rb = tile / P.tiles_x;
+            const int y0 = (rb % tiles_y) * R, n = rb / tiles_y;
             const int x = xt * kTileM + qd * 32 + lane;
-            size_t opix = size_t(row) * Wd + x;
-            if (P.up2) {                                       // top-left of the 2 x 2 block
-                const int n = row / H, y = row - n * H;
-                opix = (size_t(n) * 2 * H + 2 * y) * (2 * size_t(Wd)) + 2 * size_t(x);
-            }
-            const size_t rowstep = 2 * size_t(Wd);            // up2: the next output row
-            const uint32_t taddr = tmem + (uint32_t(qd * 32) << 16) + uint32_t(b * Cfg::kAcc);
-            // up to 64 columns per TMEM round trip, in units of 16
 #pragma unroll 1
-            for (int c0 = 0; c0 < COUT; c0 += 64) {
-                uint32_t r[4][16];
-                const int nu = min(4, (COUT - c0) / 16);
-#pragma unroll
-                for (int u = 0; u < 4; ++u)
-                    if (u < nu) tc::tmem_ld_x16(taddr + uint32_t(c0 + 16 * u), r[u]);
-                tc::tmem_ld_wait();
-                if (x < Wd) {
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        if (u >= nu) break;
-                        const int c = c0 + 16 * u;
-                        float v[16];
-#pragma unroll
-                        for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[u][j]) * P.acc_scale + s_bias[c + j];
-                        if (P.relu) {
-#pragma unroll
-                            for (int j = 0; j < 16; ++j) v[j] = fmaxf(v[j], 0.0f);
-                        }
-                        if (FP8) {
-                            uint8_t* dst = reinterpret_cast<uint8_t*>(P.y) + opix * P.ldy + P.coff + c;
-                            const float sc = P.out_inv_scale;
-                            const uint4 q =
-                                make_uint4(pack_e4m3x4(v[0] * sc, v[1] * sc, v[2] * sc, v[3] * sc),
-                                           pack_e4m3x4(v[4] * sc, v[5] * sc, v[6] * sc, v[7] * sc),
-                                           pack_e4m3x4(v[8] * sc, v[9] * sc, v[10] * sc, v[11] * sc),
-                                           pack_e4m3x4(v[12] * sc, v[13] * sc, v[14] * sc, v[15] * sc));
-                            *reinterpret_cast<uint4*>(dst) = q;
-                            if (P.up2) {
-                                const size_t ld = size_t(P.ldy);
-                                *reinterpret_cast<uint4*>(dst + ld) = q;
-                                *reinterpret_cast<uint4*>(dst + rowstep * ld) = q;
-                                *reinterpret_cast<uint4*>(dst + (rowstep + 1) * ld) = q;
+            for (int rr = 0; rr < R; ++rr) {
+                const int y = y0 + rr;
+                if (y >= H) break;                                 // rows past the image (last tile)
+                size_t opix = (size_t(n) * H + y) * Wd + x;
+                if (P.up2)                                         // top-left of the 2 x 2 block
+                    opix = (size_t(n) * 2 * H + 2 * y) * (2 * size_t(Wd)) + 2 * size_t(x);
+                const size_t rowstep = 2 * size_t(Wd);            // up2: the next output row
+                const uint32_t taddr = tmem + (uint32_t(qd * 32) << 16) + uint32_t(b * Cfg::kTileAcc + rr * Cfg::kAcc);
+                // up to 64 columns per TMEM round trip, in units of 16
+#pragma unroll 1
+                for (int c0 = 0; c0 < COUT; c0 += 64) {
+                    uint32_t r[4][16];
+                    const int nu = min(4, (COUT - c0) / 16);
+    #pragma unroll
+                    for (int u = 0; u < 4; ++u)
+                        if (u < nu) tc::tmem_ld_x16(taddr + uint32_t(c0 + 16 * u), r[u]);
+                    tc::tmem_ld_wait();
+                    if (x < Wd) {
+    #pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            if (u >= nu) break;
+                            const int c = c0 + 16 * u;
+                            float v[16];
+    #pragma unroll
+                            for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[u][j]) * P.acc_scale + s_bias[c + j];
+                            if (P.relu) {
+    #pragma unroll
+                                for (int j = 0; j < 16; ++j) v[j] = fmaxf(v[j], 0.0f);
                             }
-                        } else {
-                            if (P.mask) {
-                                const __nv_bfloat16* m = P.mask + opix * COUT + c;
-#pragma unroll
-                                for (int j = 0; j < 16; j += 2) {
-                                    const __nv_bfloat162 mm = *reinterpret_cast<const __nv_bfloat162*>(m + j);
-                                    if (!(__bfloat162float(mm.x) > 0.0f)) v[j] = 0.0f;
-                                    if (!(__bfloat162float(mm.y) > 0.0f)) v[j + 1] = 0.0f;
+                            if (FP8) {
+                                uint8_t* dst = reinterpret_cast<uint8_t*>(P.y) + opix * P.ldy + P.coff + c;
+                                const float sc = P.out_inv_scale;
+                                const uint4 q =
+                                    make_uint4(pack_e4m3x4(v[0] * sc, v[1] * sc, v[2] * sc, v[3] * sc),
+                                               pack_e4m3x4(v[4] * sc, v[5] * sc, v[6] * sc, v[7] * sc),
+                                               pack_e4m3x4(v[8] * sc, v[9] * sc, v[10] * sc, v[11] * sc),
+                                               pack_e4m3x4(v[12] * sc, v[13] * sc, v[14] * sc, v[15] * sc));
+                                *reinterpret_cast<uint4*>(dst) = q;
+                                if (P.up2) {
+                                    const size_t ld = size_t(P.ldy);
+                                    *reinterpret_cast<uint4*>(dst + ld) = q;
+                                    *reinterpret_cast<uint4*>(dst + rowstep * ld) = q;
+                                    *reinterpret_cast<uint4*>(dst + (rowstep + 1) * ld) = q;
                                 }
-                            }
-                            __nv_bfloat16* dst = P.y + opix * P.ldy + P.coff + c;
-                            const uint4 q0 = make_uint4(pack_bf16x2(v[0], v[1]), pack_bf16x2(v[2], v[3]),
-                                                        pack_bf16x2(v[4], v[5]), pack_bf16x2(v[6], v[7]));
-                            const uint4 q1 = make_uint4(pack_bf16x2(v[8], v[9]), pack_bf16x2(v[10], v[11]),
-                                                        pack_bf16x2(v[12], v[13]), pack_bf16x2(v[14], v[15]));
-                            const int nst = P.up2 ? 4 : 1;
-                            for (int k = 0; k < nst; ++k) {
-                                const size_t off = (k >> 1) * rowstep + (k & 1);     // pixels from the first
-                                uint4* d4 = reinterpret_cast<uint4*>(dst + off * P.ldy);
-                                d4[0] = q0;
-                                d4[1] = q1;
+                            } else {
+                                if (P.mask) {
+                                    const __nv_bfloat16* m = P.mask + opix * COUT + c;
+    #pragma unroll
+                                    for (int j = 0; j < 16; j += 2) {
+                                        const __nv_bfloat162 mm = *reinterpret_cast<const __nv_bfloat162*>(m + j);
+                                        if (!(__bfloat162float(mm.x) > 0.0f)) v[j] = 0.0f;
+                                        if (!(__bfloat162float(mm.y) > 0.0f)) v[j + 1] = 0.0f;
+                                    }
+                                }
+                                __nv_bfloat16* dst = P.y + opix * P.ldy + P.coff + c;
+                                const uint4 q0 = make_uint4(pack_bf16x2(v[0], v[1]), pack_bf16x2(v[2], v[3]),
+                                                            pack_bf16x2(v[4], v[5]), pack_bf16x2(v[6], v[7]));
+                                const uint4 q1 = make_uint4(pack_bf16x2(v[8], v[9]), pack_bf16x2(v[10], v[11]),
+                                                            pack_bf16x2(v[12], v[13]), pack_bf16x2(v[14], v[15]));
+                                const int nst = P.up2 ? 4 : 1;
+                                for (int k = 0; k < nst; ++k) {
+                                    const size_t off = (k >> 1) * rowstep + (k & 1);     // pixels from the first
+                                    uint4* d4 = reinterpret_cast<uint4*>(dst + off * P.ldy);
+                                    d4[0] = q0;
+                                    d4[1] = q1;
+                                }
                             }
                         }
                     }
@@ -416,15 +440,15 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
     return fn;
 }
 
-// x: [NB][H][W][C], halo box {one 64-byte channel group, 130 pixels, 3 rows, 1 image}
-cudaError_t make_halo_map(CUtensorMap* m, const void* x, int NB, int H, int W, int C, bool fp8)
+// x: [NB][H][W][C], halo box {one 64-byte channel group, 130 pixels, rows, 1 image}
+cudaError_t make_halo_map(CUtensorMap* m, const void* x, int NB, int H, int W, int C, bool fp8, int rows)
 {
     auto enc = encode_fn();
     if (!enc) return cudaErrorNotSupported;
     const cuuint64_t es = fp8 ? 1 : 2;
     const cuuint64_t dims[4] = {cuuint64_t(C), cuuint64_t(W), cuuint64_t(H), cuuint64_t(NB)};
     const cuuint64_t strides[3] = {cuuint64_t(C) * es, cuuint64_t(W) * C * es, cuuint64_t(H) * W * C * es};
-    const cuuint32_t box[4] = {cuuint32_t(kRow / es), cuuint32_t(kHaloPx), 3, 1};
+    const cuuint32_t box[4] = {cuuint32_t(kRow / es), cuuint32_t(kHaloPx), cuuint32_t(rows), 1};
     const cuuint32_t el[4] = {1, 1, 1, 1};
     CUresult r = enc(m, fp8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4,
                      const_cast<void*>(x), dims, strides, box, el, CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -470,13 +494,14 @@ cudaError_t launch_conv(const void* x, const void* w, const ConvArgs& a, cudaStr
     const Plan p = make_plan<COUT>(G);
     if (p.hs < 2 || (!p.resident && p.ws < 2)) return cudaErrorInvalidValue;
     CUtensorMap mx, mw;
-    cudaError_t e = make_halo_map(&mx, x, a.NB, a.H, a.W, a.xstride, FP8);
+    using C = ConvCfg<COUT>;
+    cudaError_t e = make_halo_map(&mx, x, a.NB, a.H, a.W, a.xstride, FP8, C::kHaloRows);
     if (e != cudaSuccess) return e;
     e = make_weight_map(&mw, w, COUT, a.Cin, FP8);
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(k_conv3x3_tc<COUT, FP8>, cudaFuncAttributeMaxDynamicSharedMemorySize, p.smem);
     if (e != cudaSuccess) return e;
-    const long long tiles = (long long)a.tiles_x * a.NB * a.H;
+    const long long tiles = (long long)a.tiles_x * a.NB * ((a.H + C::kRows - 1) / C::kRows);
     const int grid = int(std::min<long long>(tiles, num_sms()));
     k_conv3x3_tc<COUT, FP8><<<grid, kThreads, p.smem, s>>>(mx, mw, a, int(tiles), p.hs, p.ws, p.resident);
     return cudaGetLastError();
