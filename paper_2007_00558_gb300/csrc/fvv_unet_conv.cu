@@ -60,32 +60,59 @@ struct ConvCfg {
     static constexpr int kHaloRows = kRows + 2;
     static constexpr int kHaloBytes = kHaloRows * kHaloPx * kRow;
     static constexpr int kHaloStage = (kHaloBytes + 1023) / 1024 * 1024;   // halo slot, 1024-aligned
+    // Output staging for the TMA stores: each epilogue warp owns two buffers
+    // of 32 pixels x one chunk of up to 64 channels, 1024-byte aligned (the
+    // 128-byte swizzle's period).
+    static constexpr int kChunk = COUT < 64 ? COUT : 64;
+    __host__ __device__ static constexpr int out_buf(bool fp8) { return (32 * kChunk * (fp8 ? 1 : 2) + 1023) / 1024 * 1024; }
     static_assert(kTap % 1024 == 0, "tap tiles stay 1024-byte aligned");
     static_assert(kNumAcc * kTileAcc <= 512, "accumulators fit TMEM");
 };
 
 struct Plan {
-    int hs, ws, resident, smem;
+    int hs, ws, resident, out, smem;
 };
 
+// Shared memory: resident weights come first (they are read by every tile),
+// then the staged output, then the depth of the rings.  hs = 0: no plan fits.
 template <int COUT>
-Plan make_plan(int groups)
+Plan make_plan(int groups, bool fp8)
 {
     using C = ConvCfg<COUT>;
     Plan p{};
     const int res = groups * C::kGroup;
-    if (kSmemFixed + res + 3 * C::kHaloStage <= kSmemLimit) {
-        p.resident = 1;
-        p.hs = std::min(kMaxStages, (kSmemLimit - kSmemFixed - res) / C::kHaloStage);
-        p.ws = 0;
-        p.smem = kSmemFixed + res + p.hs * C::kHaloStage;
-    } else {
-        p.resident = 0;
-        p.hs = 3;
-        p.ws = std::min(kMaxStages, (kSmemLimit - kSmemFixed - p.hs * C::kHaloStage) / C::kSlice);
-        p.smem = kSmemFixed + p.hs * C::kHaloStage + p.ws * C::kSlice;
+    for (int out = 1; out >= 0; --out) {
+        const int fixed = kSmemFixed + (out ? 8 * C::out_buf(fp8) : 0);
+        if (fixed + res + 3 * C::kHaloStage <= kSmemLimit) {
+            p.resident = 1;
+            p.out = out;
+            p.hs = std::min(kMaxStages, (kSmemLimit - fixed - res) / C::kHaloStage);
+            p.ws = 0;
+            p.smem = fixed + res + p.hs * C::kHaloStage;
+            return p;
+        }
+    }
+    for (int out = 1; out >= 0; --out) {
+        const int fixed = kSmemFixed + (out ? 8 * C::out_buf(fp8) : 0);
+        const int ws = std::min(kMaxStages, (kSmemLimit - fixed - 3 * C::kHaloStage) / C::kSlice);
+        if (ws >= 2) {
+            p.resident = 0;
+            p.out = out;
+            p.hs = 3;
+            p.ws = ws;
+            p.smem = fixed + p.hs * C::kHaloStage + p.ws * C::kSlice;
+            return p;
+        }
     }
     return p;
+}
+
+// The 16-byte unit that logical unit j of staging row p occupies under the
+// tensor map's swizzle (the 128-, 64- and 32-byte modes XOR the unit index
+// with address bits 7 and up; rows of another length are not swizzled).
+__device__ __forceinline__ int out_swizzle(int row_bytes, int p)
+{
+    return row_bytes == 128 ? (p & 7) : row_bytes == 64 ? ((p >> 1) & 3) : row_bytes == 32 ? ((p >> 2) & 1) : 0;
 }
 
 __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b)
@@ -150,13 +177,15 @@ __device__ __forceinline__ void mma_group(uint32_t d, uint64_t da, uint64_t db, 
 // otherwise bf16 (K = 16, 32 per group).
 template <int COUT, bool FP8>
 __global__ void __launch_bounds__(kThreads, 1)
-k_conv3x3_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUtensorMap tmw, ConvArgs P,
-             int n_tiles, int HS, int WS, int resident)
+k_conv3x3_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUtensorMap tmw,
+             const __grid_constant__ CUtensorMap tmy, const __grid_constant__ CUtensorMap tmy2, ConvArgs P,
+             int n_tiles, int HS, int WS, int resident, int tma_out)
 {
     using Cfg = ConvCfg<COUT>;
     static_assert(512 + 4 * COUT <= kHeader, "bias fits the header");
     constexpr int kPerGroup = FP8 ? 64 : 32;           // channels in one 64-byte row
     constexpr int kEsize = FP8 ? 1 : 2;
+    constexpr int kOutBuf = Cfg::out_buf(FP8);
     extern __shared__ uint8_t smem_raw[];
     uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint64_t* full_h = reinterpret_cast<uint64_t*>(base);
@@ -170,7 +199,8 @@ k_conv3x3_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CU
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
     int* skip = reinterpret_cast<int*>(tmem_slot + 1);
     float* s_bias = reinterpret_cast<float*>(base + 512);          // [COUT] (<= 192 floats)
-    uint8_t* sHalo = base + kHeader;
+    uint8_t* sOut = base + kHeader;                                  // [4 warps][2][kOutBuf] when tma_out
+    uint8_t* sHalo = sOut + (tma_out ? 8 * kOutBuf : 0);
     uint8_t* sW = sHalo + HS * Cfg::kHaloStage;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -199,6 +229,10 @@ k_conv3x3_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CU
         tc::fence_mbar_init();
         tc::prefetch_tensormap(&tmx);
         tc::prefetch_tensormap(&tmw);
+        if (tma_out) {
+            tc::prefetch_tensormap(&tmy);
+            tc::prefetch_tensormap(&tmy2);
+        }
     }
     if (warp == 1) tc::tmem_alloc(tmem_slot, Cfg::kTmemCols);
     for (int i = threadIdx.x; i < COUT; i += kThreads) s_bias[i] = P.bias ? P.bias[i] : 0.0f;
@@ -332,15 +366,22 @@ k_conv3x3_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CU
         }
     } else {
         // ------------------------------------------------------------ epilogue
+        // Thread (warp w, lane l) owns output pixel x0 + 32 (w mod 4) + l of
+        // each row.  With tma_out the rounded values go, one chunk of up to
+        // 64 channels at a time, into one of the warp's two staging buffers
+        // (rows of 32 pixels, swizzled like the tensor map) and lane 0 stores
+        // the chunk with one TMA store (four with up2) while the warp moves
+        // on; otherwise every thread stores its pixel's channels itself.
         const int qd = warp & 3;
-        int tl = 0;
+        int tl = 0, nchunk = 0;
         for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++tl) {
             const int b = tl % Cfg::kNumAcc;
             if (!tc::mbar_wait_sleep(&acc_full[b], (tl / Cfg::kNumAcc) & 1, P.err, 7)) break;
             tc::fence_after_sync();
             const int xt = tile % P.tiles_x, rb = tile / P.tiles_x;
             const int y0 = (rb % tiles_y) * R, n = rb / tiles_y;
-            const int x = xt * kTileM + qd * 32 + lane;
+            const int xw = xt * kTileM + qd * 32, x = xw + lane;
+            const bool stage = tma_out && xw < Wd;                 // (uniform over the warp)
 #pragma unroll 1
             for (int rr = 0; rr < R; ++rr) {
                 const int y = y0 + rr;
@@ -355,30 +396,41 @@ k_conv3x3_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CU
                 for (int c0 = 0; c0 < COUT; c0 += 64) {
                     uint32_t r[4][16];
                     const int nu = min(4, (COUT - c0) / 16);
-    #pragma unroll
+                    const int row_bytes = nu * 16 * kEsize;
+                    uint8_t* ob = sOut + (qd * 2 + (nchunk & 1)) * kOutBuf + lane * row_bytes;
+                    const int swz = out_swizzle(row_bytes, lane);
+                    if (stage) {
+                        if (lane == 0) tc::bulk_wait_read<1>();    // this buffer's previous store has read it
+                        __syncwarp();
+                    }
+#pragma unroll
                     for (int u = 0; u < 4; ++u)
                         if (u < nu) tc::tmem_ld_x16(taddr + uint32_t(c0 + 16 * u), r[u]);
                     tc::tmem_ld_wait();
                     if (x < Wd) {
-    #pragma unroll
+#pragma unroll
                         for (int u = 0; u < 4; ++u) {
                             if (u >= nu) break;
                             const int c = c0 + 16 * u;
                             float v[16];
-    #pragma unroll
+#pragma unroll
                             for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[u][j]) * P.acc_scale + s_bias[c + j];
                             if (P.relu) {
-    #pragma unroll
+#pragma unroll
                                 for (int j = 0; j < 16; ++j) v[j] = fmaxf(v[j], 0.0f);
                             }
                             if (FP8) {
-                                uint8_t* dst = reinterpret_cast<uint8_t*>(P.y) + opix * P.ldy + P.coff + c;
                                 const float sc = P.out_inv_scale;
                                 const uint4 q =
                                     make_uint4(pack_e4m3x4(v[0] * sc, v[1] * sc, v[2] * sc, v[3] * sc),
                                                pack_e4m3x4(v[4] * sc, v[5] * sc, v[6] * sc, v[7] * sc),
                                                pack_e4m3x4(v[8] * sc, v[9] * sc, v[10] * sc, v[11] * sc),
                                                pack_e4m3x4(v[12] * sc, v[13] * sc, v[14] * sc, v[15] * sc));
+                                if (stage) {
+                                    *reinterpret_cast<uint4*>(ob + ((u ^ swz) << 4)) = q;
+                                    continue;
+                                }
+                                uint8_t* dst = reinterpret_cast<uint8_t*>(P.y) + opix * P.ldy + P.coff + c;
                                 *reinterpret_cast<uint4*>(dst) = q;
                                 if (P.up2) {
                                     const size_t ld = size_t(P.ldy);
@@ -389,18 +441,23 @@ k_conv3x3_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CU
                             } else {
                                 if (P.mask) {
                                     const __nv_bfloat16* m = P.mask + opix * COUT + c;
-    #pragma unroll
+#pragma unroll
                                     for (int j = 0; j < 16; j += 2) {
                                         const __nv_bfloat162 mm = *reinterpret_cast<const __nv_bfloat162*>(m + j);
                                         if (!(__bfloat162float(mm.x) > 0.0f)) v[j] = 0.0f;
                                         if (!(__bfloat162float(mm.y) > 0.0f)) v[j + 1] = 0.0f;
                                     }
                                 }
-                                __nv_bfloat16* dst = P.y + opix * P.ldy + P.coff + c;
                                 const uint4 q0 = make_uint4(pack_bf16x2(v[0], v[1]), pack_bf16x2(v[2], v[3]),
                                                             pack_bf16x2(v[4], v[5]), pack_bf16x2(v[6], v[7]));
                                 const uint4 q1 = make_uint4(pack_bf16x2(v[8], v[9]), pack_bf16x2(v[10], v[11]),
                                                             pack_bf16x2(v[12], v[13]), pack_bf16x2(v[14], v[15]));
+                                if (stage) {
+                                    *reinterpret_cast<uint4*>(ob + (((2 * u) ^ swz) << 4)) = q0;
+                                    *reinterpret_cast<uint4*>(ob + (((2 * u + 1) ^ swz) << 4)) = q1;
+                                    continue;
+                                }
+                                __nv_bfloat16* dst = P.y + opix * P.ldy + P.coff + c;
                                 const int nst = P.up2 ? 4 : 1;
                                 for (int k = 0; k < nst; ++k) {
                                     const size_t off = (k >> 1) * rowstep + (k & 1);     // pixels from the first
@@ -411,12 +468,29 @@ k_conv3x3_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CU
                             }
                         }
                     }
+                    if (stage) {
+                        tc::fence_proxy_async_smem();              // the staged rows, visible to the TMA unit
+                        __syncwarp();
+                        if (lane == 0) {                           // pixels past the image are clipped
+                            const CUtensorMap* m = (COUT <= 64 || c0 + 64 <= COUT) ? &tmy : &tmy2;
+                            const uint8_t* src = sOut + (qd * 2 + (nchunk & 1)) * kOutBuf;
+                            const int row = n * H + y;
+                            if (P.up2) {
+                                for (int k = 0; k < 4; ++k) tc::tma_store_5d(m, src, c0, k & 1, xw, k >> 1, row);
+                            } else {
+                                tc::tma_store_3d(m, src, c0, xw, row);
+                            }
+                            tc::bulk_commit();
+                        }
+                        ++nchunk;
+                    }
                 }
             }
             tc::fence_before_sync();
             __syncwarp();
             if (lane == 0) tc::mbar_arrive(&acc_empty[b]);
         }
+        if (tma_out && lane == 0) tc::bulk_wait<0>();          // the last stores are complete
     }
     if (warp == 1 && lane == 0) tc::mbar_wait_drain(drain, 0);  // before TMEM is released
     tc::fence_before_sync();
@@ -486,24 +560,72 @@ int num_sms()
     return n;
 }
 
+// y: channel c of output pixel p at y[p * ldy + coff + c]; box {chunk channels,
+// 32 pixels, 1 row}.  Plain: dims (cout, W, NB*H).  up2: the [NB][2H][2W]
+// tensor seen as (cout, dx, W, dy, NB*H), so that one box written at
+// (c, dx, x, dy, row) lands on the pixels (2 row + dy, 2 x + dx).
+cudaError_t make_out_map(CUtensorMap* m, void* y, int NB, int H, int W, int ldy, int coff, int cout, int chunk,
+                         bool fp8, bool up2)
+{
+    auto enc = encode_fn();
+    if (!enc) return cudaErrorNotSupported;
+    const cuuint64_t es = fp8 ? 1 : 2;
+    const cuuint64_t px = cuuint64_t(ldy) * es;
+    char* base = static_cast<char*>(y) + size_t(coff) * es;
+    if ((reinterpret_cast<uintptr_t>(base) & 15) || (px & 15)) return cudaErrorInvalidValue;
+    const int row_bytes = chunk * int(es);
+    const CUtensorMapSwizzle sw = row_bytes == 128 ? CU_TENSOR_MAP_SWIZZLE_128B
+                                  : row_bytes == 64 ? CU_TENSOR_MAP_SWIZZLE_64B
+                                  : row_bytes == 32 ? CU_TENSOR_MAP_SWIZZLE_32B : CU_TENSOR_MAP_SWIZZLE_NONE;
+    const CUtensorMapDataType dt = fp8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    CUresult r;
+    if (up2) {
+        const cuuint64_t dims[5] = {cuuint64_t(cout), 2, cuuint64_t(W), 2, cuuint64_t(NB) * H};
+        const cuuint64_t strides[4] = {px, 2 * px, 2 * cuuint64_t(W) * px, 4 * cuuint64_t(W) * px};
+        const cuuint32_t box[5] = {cuuint32_t(chunk), 1, 32, 1, 1};
+        const cuuint32_t el[5] = {1, 1, 1, 1, 1};
+        r = enc(m, dt, 5, base, dims, strides, box, el, CU_TENSOR_MAP_INTERLEAVE_NONE, sw,
+                CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    } else {
+        const cuuint64_t dims[3] = {cuuint64_t(cout), cuuint64_t(W), cuuint64_t(NB) * H};
+        const cuuint64_t strides[2] = {px, cuuint64_t(W) * px};
+        const cuuint32_t box[3] = {cuuint32_t(chunk), 32, 1};
+        const cuuint32_t el[3] = {1, 1, 1};
+        r = enc(m, dt, 3, base, dims, strides, box, el, CU_TENSOR_MAP_INTERLEAVE_NONE, sw,
+                CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    }
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
 template <int COUT, bool FP8>
 cudaError_t launch_conv(const void* x, const void* w, const ConvArgs& a, cudaStream_t s)
 {
     constexpr int kPerGroup = FP8 ? 64 : 32;
     const int G = (a.Cin + kPerGroup - 1) / kPerGroup;
-    const Plan p = make_plan<COUT>(G);
+    Plan p = make_plan<COUT>(G, FP8);
     if (p.hs < 2 || (!p.resident && p.ws < 2)) return cudaErrorInvalidValue;
-    CUtensorMap mx, mw;
+    CUtensorMap mx, mw, my, my2;
     using C = ConvCfg<COUT>;
     cudaError_t e = make_halo_map(&mx, x, a.NB, a.H, a.W, a.xstride, FP8, C::kHaloRows);
     if (e != cudaSuccess) return e;
     e = make_weight_map(&mw, w, COUT, a.Cin, FP8);
     if (e != cudaSuccess) return e;
+    my = mw;                                           // unused unless the output maps are made
+    my2 = mw;
+    if (p.out) {
+        // a layout the tensor maps cannot describe keeps the per-thread stores
+        const int tail = COUT > 64 ? COUT % 64 : 0;
+        if (make_out_map(&my, a.y, a.NB, a.H, a.W, a.ldy, a.coff, COUT, C::kChunk, FP8, a.up2 != 0) != cudaSuccess ||
+            (tail && make_out_map(&my2, a.y, a.NB, a.H, a.W, a.ldy, a.coff, COUT, tail, FP8, a.up2 != 0) !=
+                         cudaSuccess))
+            p.out = 0;
+    }
     e = cudaFuncSetAttribute(k_conv3x3_tc<COUT, FP8>, cudaFuncAttributeMaxDynamicSharedMemorySize, p.smem);
     if (e != cudaSuccess) return e;
     const long long tiles = (long long)a.tiles_x * a.NB * ((a.H + C::kRows - 1) / C::kRows);
     const int grid = int(std::min<long long>(tiles, num_sms()));
-    k_conv3x3_tc<COUT, FP8><<<grid, kThreads, p.smem, s>>>(mx, mw, a, int(tiles), p.hs, p.ws, p.resident);
+    k_conv3x3_tc<COUT, FP8><<<grid, kThreads, p.smem, s>>>(mx, mw, my, my2, a, int(tiles), p.hs, p.ws, p.resident,
+                                                             p.out);
     return cudaGetLastError();
 }
 
