@@ -440,6 +440,19 @@ fvv_status fvv_unet_conv3x3_e4m3(const void* x, int32_t n, int32_t h, int32_t w,
                                  const float* bias, int32_t cout, int32_t relu, float acc_scale,
                                  float out_inv_scale, void* y, void* stream);
 
+/* The convolution (ReLU on) with the network's 2x2 max pooling of its output
+ * fused into the same kernel, as the encoder uses it: y as
+ * fvv_unet_conv3x3 (bf16) or fvv_unet_conv3x3_e4m3 (e4m3 = 1; acc_scale,
+ * out_inv_scale as there), and pool_y[n][h/2][w/2][cout] (floors) the
+ * maximum of each 2x2 window of y (the stored values; -0 ties with +0).
+ * pool_arg (bf16 only, may be NULL): the window position 0..3 of each
+ * maximum in the order (0,0), (0,1), (1,0), (1,1), the first one winning a
+ * tie.  cout 32, 48 or 64.  Every pointer 16-byte aligned device memory.
+ * Waits for completion on `stream`.  Errors: INVALID_ARG, TIMEOUT, CUDA. */
+fvv_status fvv_unet_conv3x3_pool(const void* x, int32_t n, int32_t h, int32_t w, int32_t cin, const void* wt,
+                                 const float* bias, int32_t cout, int32_t e4m3, float acc_scale,
+                                 float out_inv_scale, void* y, void* pool_y, uint8_t* pool_arg, void* stream);
+
 /* ---- refinement network ---------------------------------------------------
  * A 3-level U-Net refines a plain synthesis (the paper has none; it leaves
  * disocclusions black, Sec. IX).  Input: the blended RGB / 255, depth / z_far,

@@ -289,10 +289,13 @@ fvv_status ensure_grads(fvv_ctx* c, RefineNet& N, size_t pixels)
     return FVV_OK;
 }
 
-// Where a conv writes: channel stride and offset of the output, and whether
-// it stores the 2x nearest upsampling (into a concatenation's first part).
+// Where a conv writes: channel stride and offset of the output, whether it
+// stores the 2x nearest upsampling (into a concatenation's first part), and
+// optionally the 2x2 max pooling of the output (and its window positions).
 struct Out {
     int ldy = 0, coff = 0, up2 = 0;
+    void* pool_y = nullptr;
+    uint8_t* pool_arg = nullptr;
 };
 
 fvv_status conv(const ConvLayer& l, const __nv_bfloat16* x, int B, int H, int W, __nv_bfloat16* y, int* err,
@@ -302,6 +305,8 @@ fvv_status conv(const ConvLayer& l, const __nv_bfloat16* x, int B, int H, int W,
     a.ldy = o.ldy;
     a.coff = o.coff;
     a.up2 = o.up2;
+    a.pool_y = static_cast<__nv_bfloat16*>(o.pool_y);
+    a.pool_arg = o.pool_arg;
     a.bias = l.b;
     a.y = y;
     a.relu = 1;
@@ -353,11 +358,14 @@ fvv_status forward(RefineNet& N, const fvv_refine_batch& b, int* err, cudaStream
     const int l1 = w2 + w1, l2 = w3 + w2;
     FVV_CUDA(launch_pack_features(npx, b.rgb, b.depth, b.hole, b.top3, N.z_far, N.x0, s));
     FVV_TRY(conv(N.L[0], N.x0, B, H, W, N.e1a, err, s, kX0Stride));
-    FVV_TRY(conv(N.L[1], N.e1a, B, H, W, N.cat1, err, s, 0, Out{l1, w2, 0}));
-    FVV_CUDA(launch_maxpool2(B, H, W, w1, N.cat1 + w2, l1, N.p1, N.arg1, s));
+    // the pooling runs in the epilogue of the conv before it where the tile
+    // shape allows (cout <= 64), else as a kernel of its own
+    const bool fp1 = conv_pool_supported(w1), fp2 = conv_pool_supported(w2);
+    FVV_TRY(conv(N.L[1], N.e1a, B, H, W, N.cat1, err, s, 0, Out{l1, w2, 0, fp1 ? N.p1 : nullptr, fp1 ? N.arg1 : nullptr}));
+    if (!fp1) FVV_CUDA(launch_maxpool2(B, H, W, w1, N.cat1 + w2, l1, N.p1, N.arg1, s));
     FVV_TRY(conv(N.L[2], N.p1, B, H2, W2, N.e2a, err, s));
-    FVV_TRY(conv(N.L[3], N.e2a, B, H2, W2, N.cat2, err, s, 0, Out{l2, w3, 0}));
-    FVV_CUDA(launch_maxpool2(B, H2, W2, w2, N.cat2 + w3, l2, N.p2, N.arg2, s));
+    FVV_TRY(conv(N.L[3], N.e2a, B, H2, W2, N.cat2, err, s, 0, Out{l2, w3, 0, fp2 ? N.p2 : nullptr, fp2 ? N.arg2 : nullptr}));
+    if (!fp2) FVV_CUDA(launch_maxpool2(B, H2, W2, w2, N.cat2 + w3, l2, N.p2, N.arg2, s));
     FVV_TRY(conv(N.L[4], N.p2, B, H4, W4, N.ba, err, s));
     FVV_TRY(conv(N.L[5], N.ba, B, H4, W4, N.cat2, err, s, 0, Out{l2, 0, 1}));
     FVV_TRY(conv(N.L[6], N.cat2, B, H2, W2, N.d2a, err, s));
@@ -430,6 +438,7 @@ fvv_status conv_e4m3(const ConvLayer& l, const uint8_t* x, int B, int H, int W, 
     a.ldy = o.ldy;
     a.coff = o.coff;
     a.up2 = o.up2;
+    a.pool_y = static_cast<__nv_bfloat16*>(o.pool_y);
     a.bias = l.b;
     a.y = reinterpret_cast<__nv_bfloat16*>(y);
     a.relu = 1;
@@ -453,11 +462,12 @@ fvv_status forward_e4m3(RefineNet& N, const fvv_refine_batch& b, int* err, cudaS
     FVV_CUDA(launch_pack_features_e4m3(npx, b.rgb, b.depth, b.hole, b.top3, N.z_far, N.s0, N.q_x0, s));
     const int l1 = w2 + w1, l2 = w3 + w2;                 // concatenations written in place
     FVV_TRY(conv_e4m3(N.L[0], N.q_x0, B, H, W, N.q_e1a, err, s, kX0StrideQ));
-    FVV_TRY(conv_e4m3(N.L[1], N.q_e1a, B, H, W, N.q_cat1, err, s, 0, Out{l1, w2, 0}));
-    FVV_CUDA(launch_maxpool2_e4m3(B, H, W, w1, N.q_cat1 + w2, l1, N.q_p1, s));
+    const bool fp1 = conv_pool_supported(w1), fp2 = conv_pool_supported(w2);
+    FVV_TRY(conv_e4m3(N.L[1], N.q_e1a, B, H, W, N.q_cat1, err, s, 0, Out{l1, w2, 0, fp1 ? N.q_p1 : nullptr}));
+    if (!fp1) FVV_CUDA(launch_maxpool2_e4m3(B, H, W, w1, N.q_cat1 + w2, l1, N.q_p1, s));
     FVV_TRY(conv_e4m3(N.L[2], N.q_p1, B, H2, W2, N.q_e2a, err, s));
-    FVV_TRY(conv_e4m3(N.L[3], N.q_e2a, B, H2, W2, N.q_cat2, err, s, 0, Out{l2, w3, 0}));
-    FVV_CUDA(launch_maxpool2_e4m3(B, H2, W2, w2, N.q_cat2 + w3, l2, N.q_p2, s));
+    FVV_TRY(conv_e4m3(N.L[3], N.q_e2a, B, H2, W2, N.q_cat2, err, s, 0, Out{l2, w3, 0, fp2 ? N.q_p2 : nullptr}));
+    if (!fp2) FVV_CUDA(launch_maxpool2_e4m3(B, H2, W2, w2, N.q_cat2 + w3, l2, N.q_p2, s));
     FVV_TRY(conv_e4m3(N.L[4], N.q_p2, B, H4, W4, N.q_ba, err, s));
     FVV_TRY(conv_e4m3(N.L[5], N.q_ba, B, H4, W4, N.q_cat2, err, s, 0, Out{l2, 0, 1}));
     FVV_TRY(conv_e4m3(N.L[6], N.q_cat2, B, H2, W2, N.q_d2a, err, s));
@@ -660,6 +670,48 @@ fvv_status fvv_unet_conv3x3_e4m3(const void* x, int32_t n, int32_t h, int32_t w,
     a.err = flag;
     FVV_CUDA(fvv::launch_conv3x3(x, n, h, w, cin, wt, cout, a, s));
     return fvv::check_flag(flag, s, "fvv_unet_conv3x3_e4m3");
+}
+
+fvv_status fvv_unet_conv3x3_pool(const void* x, int32_t n, int32_t h, int32_t w, int32_t cin, const void* wt,
+                                 const float* bias, int32_t cout, int32_t e4m3, float acc_scale,
+                                 float out_inv_scale, void* y, void* pool_y, uint8_t* pool_arg, void* stream)
+{
+    if (!fvv::on_device(x) || !fvv::on_device(wt) || !fvv::on_device(y) || !fvv::on_device(pool_y))
+        return fail(FVV_ERR_INVALID_ARG, "x, w, y and pool_y must be device memory");
+    if ((bias && !fvv::on_device(bias)) || (pool_arg && !fvv::on_device(pool_arg)))
+        return fail(FVV_ERR_INVALID_ARG, "bias and pool_arg must be device memory");
+    if ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(wt) | reinterpret_cast<uintptr_t>(y) |
+         reinterpret_cast<uintptr_t>(bias) | reinterpret_cast<uintptr_t>(pool_y) |
+         reinterpret_cast<uintptr_t>(pool_arg)) & 15u)
+        return fail(FVV_ERR_INVALID_ARG, "every pointer must be 16-byte aligned");
+    if (e4m3 != 0 && e4m3 != 1) return fail(FVV_ERR_INVALID_ARG, "e4m3 must be 0 or 1");
+    if (e4m3 && pool_arg) return fail(FVV_ERR_INVALID_ARG, "pool_arg is bf16 only");
+    const int q = e4m3 ? 16 : 8;
+    if (n < 1 || h < 1 || w < 1 || cin < q || cin % q || cin > 4096)
+        return fail(FVV_ERR_INVALID_ARG, "need n, h, w >= 1 and cin a multiple of 8 (e4m3: 16)");
+    if (!fvv::conv_pool_supported(cout)) return fail(FVV_ERR_INVALID_ARG, "cout must be 32, 48 or 64");
+    if (e4m3 && (!(acc_scale > 0.0f) || !(out_inv_scale > 0.0f) || !std::isfinite(acc_scale) ||
+                 !std::isfinite(out_inv_scale)))
+        return fail(FVV_ERR_INVALID_ARG, "scales must be finite and > 0");
+    if (uint64_t(n) * h * ((w + 127) / 128) >= (uint64_t(1) << 31))
+        return fail(FVV_ERR_INVALID_ARG, "too many pixel tiles");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int* flag = nullptr;
+    FVV_TRY(fvv::device_flag(&flag));
+    fvv::ConvArgs a{};
+    a.bias = bias;
+    a.y = static_cast<__nv_bfloat16*>(y);
+    a.relu = 1;
+    a.fp8 = e4m3;
+    if (e4m3) {
+        a.acc_scale = acc_scale;
+        a.out_inv_scale = out_inv_scale;
+    }
+    a.pool_y = static_cast<__nv_bfloat16*>(pool_y);
+    a.pool_arg = pool_arg;
+    a.err = flag;
+    FVV_CUDA(fvv::launch_conv3x3(x, n, h, w, cin, wt, cout, a, s));
+    return fvv::check_flag(flag, s, "fvv_unet_conv3x3_pool");
 }
 
 fvv_status fvv_refine_default_cfg(fvv_unet_cfg* cfg)

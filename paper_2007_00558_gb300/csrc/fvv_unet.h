@@ -24,9 +24,13 @@ struct ConvArgs {
     float acc_scale;                // accumulator multiplier before the bias (0: 1)
     float out_inv_scale;            // e4m3 output = value * out_inv_scale (0: 1)
     int* err;                       // device flag: a bounded wait ran out (never reset here)
+    __nv_bfloat16* pool_y;          // optional (relu, not up2/mask, conv_pool_supported): also the
+                                    // 2x2 max pooling [NB][H/2][W/2][Cout] of the output (e4m3: bytes)
+    uint8_t* pool_arg;              // optional with pool_y (bf16): the window position 0..3 of each max
 };
 
 bool conv_cout_supported(int cout);
+bool conv_pool_supported(int cout);
 // y = relu?(acc_scale conv3x3(x, w) + bias) [* (mask > 0)]; w is [Cout][3][3][Cin]
 // in the element type of x, Cout one of conv_cout_supported.
 cudaError_t launch_conv3x3(const void* x, int NB, int H, int W, int Cin, const void* w, int Cout, ConvArgs a,

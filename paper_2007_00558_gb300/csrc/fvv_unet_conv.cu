@@ -173,6 +173,39 @@ __device__ __forceinline__ void mma_group(uint32_t d, uint64_t da, uint64_t db, 
             }
 }
 
+// 2 x 2 max pooling of packed non-negative values (bf16 pairs or e4m3
+// quads; after the ReLU a value is +0, -0 or positive, so its magnitude bits
+// order it like the value and -0 ties with +0).  Candidates in window order
+// (0,0), (0,1), (1,0), (1,1); a later one wins only if strictly greater, as
+// in the separate pooling kernel.  *arg gets the winner's index per element.
+__device__ __forceinline__ uint32_t pool4_bf16(const uint32_t (&c)[4], uint32_t* arg)
+{
+    uint32_t best = c[0], bk = c[0] & 0x7FFF7FFFu, a = 0;
+#pragma unroll
+    for (int k = 1; k < 4; ++k) {
+        const uint32_t kk = c[k] & 0x7FFF7FFFu;
+        const uint32_t m = __vcmpgtu2(kk, bk);
+        best = (c[k] & m) | (best & ~m);
+        bk = (kk & m) | (bk & ~m);
+        a = ((uint32_t(k) * 0x00010001u) & m) | (a & ~m);
+    }
+    *arg = a;
+    return best;
+}
+
+__device__ __forceinline__ uint32_t pool4_e4m3(const uint32_t (&c)[4])
+{
+    uint32_t best = c[0], bk = c[0] & 0x7F7F7F7Fu;
+#pragma unroll
+    for (int k = 1; k < 4; ++k) {
+        const uint32_t kk = c[k] & 0x7F7F7F7Fu;
+        const uint32_t m = __vcmpgtu4(kk, bk);
+        best = (c[k] & m) | (best & ~m);
+        bk = (kk & m) | (bk & ~m);
+    }
+    return best;
+}
+
 // FP8: e4m3 operands and output (K = 32 channels per MMA, 64 per group);
 // otherwise bf16 (K = 16, 32 per group).
 template <int COUT, bool FP8>
@@ -373,6 +406,14 @@ k_conv3x3_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CU
         // the chunk with one TMA store (four with up2) while the warp moves
         // on; otherwise every thread stores its pixel's channels itself.
         const int qd = warp & 3;
+        // With pool_y (cout <= 64, an even number of rows per tile) the packed
+        // outputs of the top row of each row pair stay in registers until the
+        // bottom row is done; lanes 2i and 2i+1 then pool pixel pair i, each
+        // taking half of the channels.
+        constexpr int kPoolW = COUT <= 64 ? (FP8 ? COUT / 4 : COUT / 2) : 1;   // packed words per pixel
+        uint32_t ptop[kPoolW], pbot[kPoolW];
+#pragma unroll
+        for (int i = 0; i < kPoolW; ++i) ptop[i] = pbot[i] = 0u;
         int tl = 0, nchunk = 0;
         for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++tl) {
             const int b = tl % Cfg::kNumAcc;
@@ -395,7 +436,7 @@ k_conv3x3_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CU
 #pragma unroll 1
                 for (int c0 = 0; c0 < COUT; c0 += 64) {
                     uint32_t r[4][16];
-                    const int nu = min(4, (COUT - c0) / 16);
+                    const int nu = COUT <= 64 ? COUT / 16 : min(4, (COUT - c0) / 16);
                     const int row_bytes = nu * 16 * kEsize;
                     uint8_t* ob = sOut + (qd * 2 + (nchunk & 1)) * kOutBuf + lane * row_bytes;
                     const int swz = out_swizzle(row_bytes, lane);
@@ -426,6 +467,18 @@ k_conv3x3_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CU
                                                pack_e4m3x4(v[4] * sc, v[5] * sc, v[6] * sc, v[7] * sc),
                                                pack_e4m3x4(v[8] * sc, v[9] * sc, v[10] * sc, v[11] * sc),
                                                pack_e4m3x4(v[12] * sc, v[13] * sc, v[14] * sc, v[15] * sc));
+                                if constexpr (COUT <= 64) {
+                                    if (P.pool_y) {
+                                        const uint32_t w4[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+                                        for (int m = 0; m < 4; ++m) {
+                                            if (rr & 1)
+                                                pbot[4 * u + m] = w4[m];
+                                            else
+                                                ptop[4 * u + m] = w4[m];
+                                        }
+                                    }
+                                }
                                 if (stage) {
                                     *reinterpret_cast<uint4*>(ob + ((u ^ swz) << 4)) = q;
                                     continue;
@@ -452,6 +505,18 @@ k_conv3x3_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CU
                                                             pack_bf16x2(v[4], v[5]), pack_bf16x2(v[6], v[7]));
                                 const uint4 q1 = make_uint4(pack_bf16x2(v[8], v[9]), pack_bf16x2(v[10], v[11]),
                                                             pack_bf16x2(v[12], v[13]), pack_bf16x2(v[14], v[15]));
+                                if constexpr (COUT <= 64) {
+                                    if (P.pool_y) {
+                                        const uint32_t w8[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
+#pragma unroll
+                                        for (int m = 0; m < 8; ++m) {
+                                            if (rr & 1)
+                                                pbot[8 * u + m] = w8[m];
+                                            else
+                                                ptop[8 * u + m] = w8[m];
+                                        }
+                                    }
+                                }
                                 if (stage) {
                                     *reinterpret_cast<uint4*>(ob + (((2 * u) ^ swz) << 4)) = q0;
                                     *reinterpret_cast<uint4*>(ob + (((2 * u + 1) ^ swz) << 4)) = q1;
@@ -483,6 +548,44 @@ k_conv3x3_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CU
                             tc::bulk_commit();
                         }
                         ++nchunk;
+                    }
+                }
+                if constexpr (COUT <= 64) {
+                    if (P.pool_y && (rr & 1)) {
+                        // rows y - 1 and y, pixels xe and xe + 1; the even lane takes
+                        // the first half of the channels, the odd lane the second
+                        constexpr int kHalf = kPoolW / 2;
+                        const bool ev = (lane & 1) == 0;
+                        const int xe = x & ~1;
+                        uint32_t outw[kHalf], argw[kHalf];
+#pragma unroll
+                        for (int i = 0; i < kHalf; ++i) {
+                            const uint32_t ot = __shfl_xor_sync(~0u, ev ? ptop[kHalf + i] : ptop[i], 1);
+                            const uint32_t obt = __shfl_xor_sync(~0u, ev ? pbot[kHalf + i] : pbot[i], 1);
+                            const uint32_t mt = ev ? ptop[i] : ptop[kHalf + i];
+                            const uint32_t mb = ev ? pbot[i] : pbot[kHalf + i];
+                            const uint32_t c[4] = {ev ? mt : ot, ev ? ot : mt, ev ? mb : obt, ev ? obt : mb};
+                            argw[i] = 0u;
+                            outw[i] = FP8 ? pool4_e4m3(c) : pool4_bf16(c, &argw[i]);
+                        }
+                        if (xe + 1 < Wd) {
+                            const size_t pp = (size_t(n) * (H / 2) + (y >> 1)) * size_t(Wd / 2) + (xe >> 1);
+                            const int ch0 = ev ? 0 : COUT / 2;
+                            uint2* dst = reinterpret_cast<uint2*>(reinterpret_cast<uint8_t*>(P.pool_y) +
+                                                                  (pp * COUT + ch0) * kEsize);
+#pragma unroll
+                            for (int i = 0; i < kHalf / 2; ++i) dst[i] = make_uint2(outw[2 * i], outw[2 * i + 1]);
+                            if (!FP8 && P.pool_arg) {
+                                uint32_t ab[kHalf / 2];
+#pragma unroll
+                                for (int i = 0; i < kHalf / 2; ++i)
+                                    ab[i] = (argw[2 * i] & 0xFFu) | ((argw[2 * i] >> 16) << 8) |
+                                            ((argw[2 * i + 1] & 0xFFu) << 16) | ((argw[2 * i + 1] >> 16) << 24);
+                                uint2* da = reinterpret_cast<uint2*>(P.pool_arg + pp * COUT + ch0);
+#pragma unroll
+                                for (int i = 0; i < kHalf / 4; ++i) da[i] = make_uint2(ab[2 * i], ab[2 * i + 1]);
+                            }
+                        }
                     }
                 }
             }
@@ -650,6 +753,11 @@ bool conv_cout_supported(int cout)
     return cout == 32 || cout == 48 || cout == 64 || cout == 96 || cout == 128 || cout == 192;
 }
 
+bool conv_pool_supported(int cout)
+{
+    return cout == 32 || cout == 48 || cout == 64;                // an even number of rows per tile
+}
+
 cudaError_t launch_conv3x3(const void* x, int NB, int H, int W, int Cin, const void* w, int Cout, ConvArgs a,
                            cudaStream_t s)
 {
@@ -662,6 +770,9 @@ cudaError_t launch_conv3x3(const void* x, int NB, int H, int W, int Cin, const v
     a.Cin = Cin;
     if (a.xstride == 0) a.xstride = Cin;
     if (a.mask && (a.up2 || a.coff || (a.ldy && a.ldy != Cout))) return cudaErrorInvalidValue;
+    if ((a.pool_y || a.pool_arg) && (!conv_pool_supported(Cout) || !a.pool_y || !a.relu || a.up2 || a.mask))
+        return cudaErrorInvalidValue;
+    if (a.pool_arg && fp8) return cudaErrorInvalidValue;
     if (a.xstride < Cin || a.xstride % (fp8 ? 16 : 8)) return cudaErrorInvalidValue;
     a.tiles_x = (W + kTileM - 1) / kTileM;
     if (a.ldy == 0) a.ldy = Cout;

@@ -150,6 +150,7 @@ def load() -> C.CDLL:
             "fvv_unet_conv3x3": [P, I, I, I, I, P, P, I, I, P, P, P],
             "fvv_selftest_bounded_wait": [I, C.c_uint32, P],
             "fvv_unet_conv3x3_e4m3": [P, I, I, I, I, P, P, I, I, C.c_float, C.c_float, P, P],
+            "fvv_unet_conv3x3_pool": [P, I, I, I, I, P, P, I, I, C.c_float, C.c_float, P, P, P, P],
             "fvv_depth_codec_default": [C.POINTER(fvv_depth_codec)],
             "fvv_set_depth_codec": [P, I, C.POINTER(fvv_depth_codec)],
             "fvv_depth_encode_yuv": [P, I, P, S, P, S, P, P, S, P],
@@ -434,6 +435,14 @@ def fvv_unet_conv3x3_e4m3(x, n: int, h: int, w: int, cin: int, wt, bias, cout: i
     _check(load().fvv_unet_conv3x3_e4m3(ptr(x), n, h, w, cin, ptr(wt), ptr(bias), cout, 1 if relu else 0,
                                         acc_scale, out_inv_scale, ptr(y), stream_handle(stream)),
            "fvv_unet_conv3x3_e4m3")
+
+
+def fvv_unet_conv3x3_pool(x, n: int, h: int, w: int, cin: int, wt, bias, cout: int, y, pool_y, pool_arg=None,
+                          e4m3: bool = False, acc_scale: float = 1.0, out_inv_scale: float = 1.0,
+                          stream=None) -> None:
+    _check(load().fvv_unet_conv3x3_pool(ptr(x), n, h, w, cin, ptr(wt), ptr(bias), cout, 1 if e4m3 else 0,
+                                        acc_scale, out_inv_scale, ptr(y), ptr(pool_y), ptr(pool_arg),
+                                        stream_handle(stream)), "fvv_unet_conv3x3_pool")
 
 
 class fvv_depth_codec(C.Structure):
