@@ -15,13 +15,15 @@
 // extra rows are shared by the R output rows (narrow layers are bound by
 // moving the halo).  The weights [cout][ky][kx][cin] stay
 // resident in shared memory when they fit; otherwise they stream through a
-// ring of one-ky slices (three taps).  The fp32 accumulators live in TMEM,
-// double-buffered: four epilogue warps drain tile i (scale, bias, ReLU,
-// optional ReLU-derivative mask, rounding to bf16 or e4m3, NHWC store) while
-// the MMA thread accumulates tile i+1.
+// ring of one-ky slices (three taps).  The fp32 accumulators live in a TMEM
+// ring: the epilogue (scale, bias, ReLU, optional ReLU-derivative mask,
+// rounding to bf16 or e4m3, NHWC store, optional 2x2 max pooling) drains
+// tile i while the MMA thread accumulates the next ones.
 //
-// Warp roles (192 threads): 0 = TMA producer, 1 = TMEM owner and MMA issuer,
-// 2..5 = epilogue (warp w reads TMEM lanes 32 (w mod 4) .. +31).
+// Warp roles (320 threads): 0 = TMA producer, 1 = TMEM owner and MMA issuer,
+// 2..9 = epilogue in two groups of four, taking alternate tiles (warp w
+// reads TMEM lanes 32 (w mod 4) .. +31); two warps per sub-partition hide
+// each other's TMEM-load and store latency.
 #include <algorithm>
 
 #include <cuda.h>
@@ -40,7 +42,7 @@ namespace {
 constexpr int kTileM = 128;
 constexpr int kHaloPx = kTileM + 2;                    // 130 halo pixels per row
 constexpr int kRow = 64;                               // bytes of one pixel row of a channel group
-constexpr int kThreads = 192;
+constexpr int kThreads = 320;
 constexpr int kMaxStages = 8;
 constexpr int kSmemLimit = 227 * 1024;
 constexpr int kHeader = 2048;                          // barriers (bytes 0..511) and bias (512..1279)
@@ -60,9 +62,9 @@ struct ConvCfg {
     static constexpr int kHaloRows = kRows + 2;
     static constexpr int kHaloBytes = kHaloRows * kHaloPx * kRow;
     static constexpr int kHaloStage = (kHaloBytes + 1023) / 1024 * 1024;   // halo slot, 1024-aligned
-    // Output staging for the TMA stores: each epilogue warp owns two buffers
-    // of 32 pixels x one chunk of up to 64 channels, 1024-byte aligned (the
-    // 128-byte swizzle's period).
+    // Output staging for the TMA stores: each of the eight epilogue warps
+    // owns a buffer of 32 pixels x one chunk of up to 64 channels,
+    // 1024-byte aligned (the 128-byte swizzle's period).
     static constexpr int kChunk = COUT < 64 ? COUT : 64;
     __host__ __device__ static constexpr int out_buf(bool fp8) { return (32 * kChunk * (fp8 ? 1 : 2) + 1023) / 1024 * 1024; }
     static_assert(kTap % 1024 == 0, "tap tiles stay 1024-byte aligned");
@@ -76,12 +78,12 @@ struct Plan {
 // Shared memory: resident weights come first (they are read by every tile),
 // then the staged output, then the depth of the rings.  hs = 0: no plan fits.
 template <int COUT>
-Plan make_plan(int groups, bool fp8)
+Plan make_plan(int groups, bool fp8, bool want_out)
 {
     using C = ConvCfg<COUT>;
     Plan p{};
     const int res = groups * C::kGroup;
-    for (int out = 1; out >= 0; --out) {
+    for (int out = want_out ? 1 : 0; out >= 0; --out) {
         const int fixed = kSmemFixed + (out ? 8 * C::out_buf(fp8) : 0);
         if (fixed + res + 3 * C::kHaloStage <= kSmemLimit) {
             p.resident = 1;
@@ -92,7 +94,7 @@ Plan make_plan(int groups, bool fp8)
             return p;
         }
     }
-    for (int out = 1; out >= 0; --out) {
+    for (int out = want_out ? 1 : 0; out >= 0; --out) {
         const int fixed = kSmemFixed + (out ? 8 * C::out_buf(fp8) : 0);
         const int ws = std::min(kMaxStages, (kSmemLimit - fixed - 3 * C::kHaloStage) / C::kSlice);
         if (ws >= 2) {
@@ -232,7 +234,7 @@ k_conv3x3_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CU
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
     int* skip = reinterpret_cast<int*>(tmem_slot + 1);
     float* s_bias = reinterpret_cast<float*>(base + 512);          // [COUT] (<= 192 floats)
-    uint8_t* sOut = base + kHeader;                                  // [4 warps][2][kOutBuf] when tma_out
+    uint8_t* sOut = base + kHeader;                                  // [8 warps][kOutBuf] when tma_out
     uint8_t* sHalo = sOut + (tma_out ? 8 * kOutBuf : 0);
     uint8_t* sW = sHalo + HS * Cfg::kHaloStage;
 
@@ -399,13 +401,14 @@ k_conv3x3_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CU
         }
     } else {
         // ------------------------------------------------------------ epilogue
-        // Thread (warp w, lane l) owns output pixel x0 + 32 (w mod 4) + l of
-        // each row.  With tma_out the rounded values go, one chunk of up to
-        // 64 channels at a time, into one of the warp's two staging buffers
-        // (rows of 32 pixels, swizzled like the tensor map) and lane 0 stores
-        // the chunk with one TMA store (four with up2) while the warp moves
-        // on; otherwise every thread stores its pixel's channels itself.
-        const int qd = warp & 3;
+        // Group eg = (w - 2) / 4 takes the tiles tl = eg, eg + 2, ... of this
+        // CTA.  Thread (warp w, lane l) owns output pixel x0 + 32 (w mod 4) + l
+        // of each row.  With tma_out the rounded values go, one chunk of up
+        // to 64 channels at a time, into the warp's staging buffer (rows of 32
+        // pixels, swizzled like the tensor map) and lane 0 stores the chunk
+        // with one TMA store (four with up2) while the warp moves on;
+        // otherwise every thread stores its pixel's channels itself.
+        const int qd = warp & 3, ew = warp - 2, eg = ew >> 2;
         // With pool_y (cout <= 64, an even number of rows per tile) the packed
         // outputs of the top row of each row pair stay in registers until the
         // bottom row is done; lanes 2i and 2i+1 then pool pixel pair i, each
@@ -414,8 +417,7 @@ k_conv3x3_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CU
         uint32_t ptop[kPoolW], pbot[kPoolW];
 #pragma unroll
         for (int i = 0; i < kPoolW; ++i) ptop[i] = pbot[i] = 0u;
-        int tl = 0, nchunk = 0;
-        for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++tl) {
+        for (int tile = blockIdx.x + eg * gridDim.x, tl = eg; tile < n_tiles; tile += 2 * gridDim.x, tl += 2) {
             const int b = tl % Cfg::kNumAcc;
             if (!tc::mbar_wait_sleep(&acc_full[b], (tl / Cfg::kNumAcc) & 1, P.err, 7)) break;
             tc::fence_after_sync();
@@ -438,15 +440,27 @@ k_conv3x3_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CU
                     uint32_t r[4][16];
                     const int nu = COUT <= 64 ? COUT / 16 : min(4, (COUT - c0) / 16);
                     const int row_bytes = nu * 16 * kEsize;
-                    uint8_t* ob = sOut + (qd * 2 + (nchunk & 1)) * kOutBuf + lane * row_bytes;
+                    uint8_t* ob = sOut + ew * kOutBuf + lane * row_bytes;
                     const int swz = out_swizzle(row_bytes, lane);
                     if (stage) {
-                        if (lane == 0) tc::bulk_wait_read<1>();    // this buffer's previous store has read it
+                        if (lane == 0) tc::bulk_wait_read<0>();    // the buffer's previous store has read it
                         __syncwarp();
                     }
+                    // as few TMEM loads as the chunk allows (32 columns each, 16 for an odd unit)
 #pragma unroll
-                    for (int u = 0; u < 4; ++u)
-                        if (u < nu) tc::tmem_ld_x16(taddr + uint32_t(c0 + 16 * u), r[u]);
+                    for (int h = 0; h < 2; ++h) {
+                        if (2 * h + 1 < nu) {
+                            uint32_t t[32];
+                            tc::tmem_ld_x32(taddr + uint32_t(c0 + 32 * h), t);
+#pragma unroll
+                            for (int j = 0; j < 16; ++j) {
+                                r[2 * h][j] = t[j];
+                                r[2 * h + 1][j] = t[16 + j];
+                            }
+                        } else if (2 * h < nu) {
+                            tc::tmem_ld_x16(taddr + uint32_t(c0 + 32 * h), r[2 * h]);
+                        }
+                    }
                     tc::tmem_ld_wait();
                     if (x < Wd) {
 #pragma unroll
@@ -538,7 +552,7 @@ k_conv3x3_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CU
                         __syncwarp();
                         if (lane == 0) {                           // pixels past the image are clipped
                             const CUtensorMap* m = (COUT <= 64 || c0 + 64 <= COUT) ? &tmy : &tmy2;
-                            const uint8_t* src = sOut + (qd * 2 + (nchunk & 1)) * kOutBuf;
+                            const uint8_t* src = sOut + ew * kOutBuf;
                             const int row = n * H + y;
                             if (P.up2) {
                                 for (int k = 0; k < 4; ++k) tc::tma_store_5d(m, src, c0, k & 1, xw, k >> 1, row);
@@ -547,7 +561,6 @@ k_conv3x3_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CU
                             }
                             tc::bulk_commit();
                         }
-                        ++nchunk;
                     }
                 }
                 if constexpr (COUT <= 64) {
@@ -705,7 +718,11 @@ cudaError_t launch_conv(const void* x, const void* w, const ConvArgs& a, cudaStr
 {
     constexpr int kPerGroup = FP8 ? 64 : 32;
     const int G = (a.Cin + kPerGroup - 1) / kPerGroup;
-    Plan p = make_plan<COUT>(G, FP8);
+    // Staged TMA stores pay where a warp's own stores would scatter: into a
+    // channel slice of a wider tensor, or four times for the upsampling.  A
+    // dense output is already written in whole lines by the threads.
+    const bool want_out = a.up2 || a.ldy != COUT || a.coff != 0;
+    Plan p = make_plan<COUT>(G, FP8, want_out);
     if (p.hs < 2 || (!p.resident && p.ws < 2)) return cudaErrorInvalidValue;
     CUtensorMap mx, mw, my, my2;
     using C = ConvCfg<COUT>;
