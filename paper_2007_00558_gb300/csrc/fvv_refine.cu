@@ -298,10 +298,33 @@ struct Out {
     uint8_t* pool_arg = nullptr;
 };
 
+// The 1x1 head fused into the last convolution (inference only: the
+// activations d1 are then never stored).
+struct Head {
+    const float *w = nullptr, *b = nullptr;
+    float scale = 1.0f;
+    const uint8_t* rgb = nullptr;
+    uint8_t* out = nullptr;
+    size_t pitch = 0;
+    float* f32 = nullptr;
+};
+
+void set_head(ConvArgs& a, const Head& h)
+{
+    a.head_w = h.w;
+    a.head_b = h.b;
+    a.head_scale = h.scale;
+    a.head_rgb = h.rgb;
+    a.head_out = h.out;
+    a.head_pitch = h.pitch;
+    a.head_f32 = h.f32;
+}
+
 fvv_status conv(const ConvLayer& l, const __nv_bfloat16* x, int B, int H, int W, __nv_bfloat16* y, int* err,
-                cudaStream_t s, int xstride = 0, Out o = Out())
+                cudaStream_t s, int xstride = 0, Out o = Out(), Head h = Head())
 {
     ConvArgs a{};
+    set_head(a, h);
     a.ldy = o.ldy;
     a.coff = o.coff;
     a.up2 = o.up2;
@@ -371,6 +394,18 @@ fvv_status forward(RefineNet& N, const fvv_refine_batch& b, int* err, cudaStream
     FVV_TRY(conv(N.L[6], N.cat2, B, H2, W2, N.d2a, err, s));
     FVV_TRY(conv(N.L[7], N.d2a, B, H2, W2, N.cat1, err, s, 0, Out{l1, 0, 1}));
     FVV_TRY(conv(N.L[8], N.cat1, B, H, W, N.d1a, err, s));
+    if (out || out_f32) {
+        // inference: the head runs in d1b's epilogue (d1 and s are training state)
+        Head h;
+        h.w = N.wout;
+        h.b = N.bout;
+        h.rgb = b.rgb;
+        h.out = out;
+        h.pitch = out_pitch;
+        h.f32 = out_f32;
+        FVV_TRY(conv(N.L[9], N.d1a, B, H, W, N.d1, err, s, 0, Out(), h));
+        return FVV_OK;
+    }
     FVV_TRY(conv(N.L[9], N.d1a, B, H, W, N.d1, err, s));
     FVV_CUDA(launch_head_fwd(npx, w1, N.d1, N.wout, N.bout, b.rgb, N.s, out, W, out_pitch, out_f32, s));
     return FVV_OK;
@@ -432,9 +467,10 @@ fvv_status ensure_acts8(fvv_ctx* c, RefineNet& N, size_t pixels)
 }
 
 fvv_status conv_e4m3(const ConvLayer& l, const uint8_t* x, int B, int H, int W, uint8_t* y, int* err,
-                     cudaStream_t s, int xstride = 0, Out o = Out())
+                     cudaStream_t s, int xstride = 0, Out o = Out(), Head h = Head())
 {
     ConvArgs a{};
+    set_head(a, h);
     a.ldy = o.ldy;
     a.coff = o.coff;
     a.up2 = o.up2;
@@ -473,6 +509,18 @@ fvv_status forward_e4m3(RefineNet& N, const fvv_refine_batch& b, int* err, cudaS
     FVV_TRY(conv_e4m3(N.L[6], N.q_cat2, B, H2, W2, N.q_d2a, err, s));
     FVV_TRY(conv_e4m3(N.L[7], N.q_d2a, B, H2, W2, N.q_cat1, err, s, 0, Out{l1, 0, 1}));
     FVV_TRY(conv_e4m3(N.L[8], N.q_cat1, B, H, W, N.q_d1a, err, s));
+    if (out || out_f32) {
+        Head h;                                           // the head runs in d1b's epilogue
+        h.w = N.wout;
+        h.b = N.bout;
+        h.scale = N.s_act[9];
+        h.rgb = b.rgb;
+        h.out = out;
+        h.pitch = out_pitch;
+        h.f32 = out_f32;
+        FVV_TRY(conv_e4m3(N.L[9], N.q_d1a, B, H, W, N.q_d1, err, s, 0, Out(), h));
+        return FVV_OK;
+    }
     FVV_TRY(conv_e4m3(N.L[9], N.q_d1a, B, H, W, N.q_d1, err, s));
     FVV_CUDA(launch_head_fwd_e4m3(npx, w1, N.q_d1, N.s_act[9], N.wout, N.bout, b.rgb, out, W, out_pitch, out_f32,
                                   s));

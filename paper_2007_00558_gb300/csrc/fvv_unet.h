@@ -27,6 +27,18 @@ struct ConvArgs {
     __nv_bfloat16* pool_y;          // optional (relu, not up2/mask, conv_pool_supported): also the
                                     // 2x2 max pooling [NB][H/2][W/2][Cout] of the output (e4m3: bytes)
     uint8_t* pool_arg;              // optional with pool_y (bf16): the window position 0..3 of each max
+    // optional fused 1x1 head (relu, dense output, conv_pool_supported): y is not
+    // stored; per pixel p, s = rgb / 255 + head_w d1 + head_b (head_w [3][Cout],
+    // d1 the rounded outputs; e4m3: decoded codes times head_scale), then
+    // head_out[row * head_pitch + 3 x + k] = round(255 clamp(s_k, 0, 1)) and/or
+    // head_f32[3 p + k] = clamp(s_k, 0, 1) (rows of W pixels, images stacked)
+    const float* head_w;
+    const float* head_b;
+    float head_scale;
+    const uint8_t* head_rgb;        // [NB * H * W][3]
+    uint8_t* head_out;
+    size_t head_pitch;
+    float* head_f32;
 };
 
 bool conv_cout_supported(int cout);

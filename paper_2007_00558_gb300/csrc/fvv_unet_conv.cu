@@ -218,6 +218,7 @@ k_conv3x3_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CU
 {
     using Cfg = ConvCfg<COUT>;
     static_assert(512 + 4 * COUT <= kHeader, "bias fits the header");
+    static_assert(COUT > 64 || 768 + 4 * (3 * COUT + 3) <= kHeader, "head weights fit the header");
     constexpr int kPerGroup = FP8 ? 64 : 32;           // channels in one 64-byte row
     constexpr int kEsize = FP8 ? 1 : 2;
     constexpr int kOutBuf = Cfg::out_buf(FP8);
@@ -234,6 +235,7 @@ k_conv3x3_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CU
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
     int* skip = reinterpret_cast<int*>(tmem_slot + 1);
     float* s_bias = reinterpret_cast<float*>(base + 512);          // [COUT] (<= 192 floats)
+    float* s_head = reinterpret_cast<float*>(base + 768);          // fused head: [3][COUT] weights, [3] bias
     uint8_t* sOut = base + kHeader;                                  // [8 warps][kOutBuf] when tma_out
     uint8_t* sHalo = sOut + (tma_out ? 8 * kOutBuf : 0);
     uint8_t* sW = sHalo + HS * Cfg::kHaloStage;
@@ -271,6 +273,8 @@ k_conv3x3_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CU
     }
     if (warp == 1) tc::tmem_alloc(tmem_slot, Cfg::kTmemCols);
     for (int i = threadIdx.x; i < COUT; i += kThreads) s_bias[i] = P.bias ? P.bias[i] : 0.0f;
+    if (COUT <= 64 && P.head_w)
+        for (int i = threadIdx.x; i < 3 * COUT + 3; i += kThreads) s_head[i] = i < 3 * COUT ? P.head_w[i] : P.head_b[i - 3 * COUT];
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
@@ -403,20 +407,24 @@ k_conv3x3_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CU
         // ------------------------------------------------------------ epilogue
         // Group eg = (w - 2) / 4 takes the tiles tl = eg, eg + 2, ... of this
         // CTA.  Thread (warp w, lane l) owns output pixel x0 + 32 (w mod 4) + l
-        // of each row.  With tma_out the rounded values go, one chunk of up
-        // to 64 channels at a time, into the warp's staging buffer (rows of 32
+        // of each row; every lane runs the arithmetic (the shuffles of the
+        // pooling need the whole warp) and only lanes inside the image load
+        // or store.  With tma_out the rounded values go, one chunk of up to 64
+        // channels at a time, into the warp's staging buffer (rows of 32
         // pixels, swizzled like the tensor map) and lane 0 stores the chunk
         // with one TMA store (four with up2) while the warp moves on;
         // otherwise every thread stores its pixel's channels itself.
-        const int qd = warp & 3, ew = warp - 2, eg = ew >> 2;
+        //
         // With pool_y (cout <= 64, an even number of rows per tile) the packed
-        // outputs of the top row of each row pair stay in registers until the
-        // bottom row is done; lanes 2i and 2i+1 then pool pixel pair i, each
-        // taking half of the channels.
+        // outputs of the top row of each row pair stay in registers; at the
+        // bottom row lanes 2i and 2i+1 pool pixel pair i unit by unit, the
+        // even lane taking the first half of each unit's channels.
+        const int qd = warp & 3, ew = warp - 2, eg = ew >> 2;
         constexpr int kPoolW = COUT <= 64 ? (FP8 ? COUT / 4 : COUT / 2) : 1;   // packed words per pixel
-        uint32_t ptop[kPoolW], pbot[kPoolW];
+        uint32_t ptop[kPoolW];
 #pragma unroll
-        for (int i = 0; i < kPoolW; ++i) ptop[i] = pbot[i] = 0u;
+        for (int i = 0; i < kPoolW; ++i) ptop[i] = 0u;
+        const bool ev = (lane & 1) == 0;
         for (int tile = blockIdx.x + eg * gridDim.x, tl = eg; tile < n_tiles; tile += 2 * gridDim.x, tl += 2) {
             const int b = tl % Cfg::kNumAcc;
             if (!tc::mbar_wait_sleep(&acc_full[b], (tl / Cfg::kNumAcc) & 1, P.err, 7)) break;
@@ -424,6 +432,8 @@ k_conv3x3_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CU
             const int xt = tile % P.tiles_x, rb = tile / P.tiles_x;
             const int y0 = (rb % tiles_y) * R, n = rb / tiles_y;
             const int xw = xt * kTileM + qd * 32, x = xw + lane;
+            const bool xin = x < Wd;
+            const bool pair_in = (x | 1) < Wd;                     // both pixels of this lane's pooling pair
             const bool stage = tma_out && xw < Wd;                 // (uniform over the warp)
 #pragma unroll 1
             for (int rr = 0; rr < R; ++rr) {
@@ -433,6 +443,8 @@ k_conv3x3_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CU
                 if (P.up2)                                         // top-left of the 2 x 2 block
                     opix = (size_t(n) * 2 * H + 2 * y) * (2 * size_t(Wd)) + 2 * size_t(x);
                 const size_t rowstep = 2 * size_t(Wd);            // up2: the next output row
+                const size_t pp = (size_t(n) * (H / 2) + (y >> 1)) * size_t(Wd / 2) + (x >> 1);   // pooled pixel
+                const bool pool_row = COUT <= 64 && P.pool_y && (rr & 1);
                 const uint32_t taddr = tmem + (uint32_t(qd * 32) << 16) + uint32_t(b * Cfg::kTileAcc + rr * Cfg::kAcc);
                 // up to 64 columns per TMEM round trip, in units of 16
 #pragma unroll 1
@@ -462,88 +474,149 @@ k_conv3x3_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CU
                         }
                     }
                     tc::tmem_ld_wait();
-                    if (x < Wd) {
+                    // fused 1x1 head: one chain per output channel over the
+                    // rounded activations in channel order
+                    float hr[3] = {0.0f, 0.0f, 0.0f};
+                    if (COUT <= 64 && P.head_w)
+                        for (int k = 0; k < 3; ++k) hr[k] = s_head[3 * COUT + k];
 #pragma unroll
-                        for (int u = 0; u < 4; ++u) {
-                            if (u >= nu) break;
-                            const int c = c0 + 16 * u;
-                            float v[16];
+                    for (int u = 0; u < 4; ++u) {
+                        if (u >= nu) break;
+                        const int c = c0 + 16 * u;
+                        float v[16];
 #pragma unroll
-                            for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[u][j]) * P.acc_scale + s_bias[c + j];
-                            if (P.relu) {
+                        for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[u][j]) * P.acc_scale + s_bias[c + j];
+                        if (P.relu) {
 #pragma unroll
-                                for (int j = 0; j < 16; ++j) v[j] = fmaxf(v[j], 0.0f);
+                            for (int j = 0; j < 16; ++j) v[j] = fmaxf(v[j], 0.0f);
+                        }
+                        // the unit as packed words: 4 of 4 e4m3 codes or 8 of 2 bf16
+                        constexpr int kW = FP8 ? 4 : 8;
+                        uint32_t w[kW];
+                        if (FP8) {
+                            const float sc = P.out_inv_scale;
+#pragma unroll
+                            for (int m = 0; m < 4; ++m)
+                                w[m] = pack_e4m3x4(v[4 * m] * sc, v[4 * m + 1] * sc, v[4 * m + 2] * sc, v[4 * m + 3] * sc);
+                        } else {
+                            if (P.mask && xin) {
+                                const __nv_bfloat16* mk = P.mask + opix * COUT + c;
+#pragma unroll
+                                for (int j = 0; j < 16; j += 2) {
+                                    const __nv_bfloat162 mm = *reinterpret_cast<const __nv_bfloat162*>(mk + j);
+                                    if (!(__bfloat162float(mm.x) > 0.0f)) v[j] = 0.0f;
+                                    if (!(__bfloat162float(mm.y) > 0.0f)) v[j + 1] = 0.0f;
+                                }
                             }
+#pragma unroll
+                            for (int m = 0; m < kW; ++m) w[m % kW] = pack_bf16x2(v[2 * m], v[2 * m + 1]);
+                        }
+                        if constexpr (COUT <= 64) {
+                            if (P.head_w) {
+#pragma unroll
+                                for (int j = 0; j < 16; ++j) {
+                                    float a;
+                                    if (FP8) {
+                                        const __nv_fp8_storage_t b8 =
+                                            __nv_fp8_storage_t((w[(j >> 2) % kW] >> (8 * (j & 3))) & 0xFFu);
+                                        a = __half2float(__half(__nv_cvt_fp8_to_halfraw(b8, __NV_E4M3))) * P.head_scale;
+                                    } else {
+                                        const uint32_t wj = w[(j >> 1) % kW];
+                                        a = __uint_as_float((j & 1) ? (wj & 0xFFFF0000u) : (wj << 16));
+                                    }
+#pragma unroll
+                                    for (int k = 0; k < 3; ++k) hr[k] += s_head[k * COUT + c + j] * a;
+                                }
+                                continue;                          // the activations themselves are not stored
+                            }
+                            if (P.pool_y) {
+                                if (!pool_row) {
+#pragma unroll
+                                    for (int m = 0; m < kW; ++m) ptop[(kW * u + m) % kPoolW] = w[m];
+                                } else {
+                                    // candidates in window order: (top, even), (top, odd), (bottom, even), (bottom, odd)
+                                    constexpr int kH = kW / 2;
+                                    uint32_t pw[kH], pa[kH];
+#pragma unroll
+                                    for (int i = 0; i < kH; ++i) {
+                                        const uint32_t t_lo = ptop[(kW * u + i) % kPoolW], t_hi = ptop[(kW * u + kH + i) % kPoolW];
+                                        const uint32_t ot = __shfl_xor_sync(~0u, ev ? t_hi : t_lo, 1);
+                                        const uint32_t obm = __shfl_xor_sync(~0u, ev ? w[kH + i] : w[i], 1);
+                                        const uint32_t mt = ev ? t_lo : t_hi, mb = ev ? w[i] : w[kH + i];
+                                        const uint32_t cand[4] = {ev ? mt : ot, ev ? ot : mt, ev ? mb : obm, ev ? obm : mb};
+                                        pa[i] = 0u;
+                                        pw[i] = FP8 ? pool4_e4m3(cand) : pool4_bf16(cand, &pa[i]);
+                                    }
+                                    if (pair_in) {
+                                        // this lane's 8 channels of the unit: c + 8 (odd lane)
+                                        const size_t pc = pp * COUT + c + (ev ? 0 : 8);
+                                        if (FP8) {
+                                            *reinterpret_cast<uint2*>(reinterpret_cast<uint8_t*>(P.pool_y) + pc) =
+                                                make_uint2(pw[0], pw[1 % kH]);
+                                        } else {
+                                            *reinterpret_cast<uint4*>(P.pool_y + pc) =
+                                                make_uint4(pw[0], pw[1 % kH], pw[2 % kH], pw[3 % kH]);
+                                            if (P.pool_arg) {
+                                                uint32_t ab[2];
+#pragma unroll
+                                                for (int i = 0; i < 2; ++i) {
+                                                    const uint32_t a0 = pa[(2 * i) % kH], a1 = pa[(2 * i + 1) % kH];
+                                                    ab[i] = (a0 & 0xFFu) | ((a0 >> 16) << 8) | ((a1 & 0xFFu) << 16) |
+                                                            ((a1 >> 16) << 24);
+                                                }
+                                                *reinterpret_cast<uint2*>(P.pool_arg + pc) = make_uint2(ab[0], ab[1]);
+                                            }
+                                        }
+                                    }
+                                }
+                            }
+                        }
+                        if (stage) {
                             if (FP8) {
-                                const float sc = P.out_inv_scale;
-                                const uint4 q =
-                                    make_uint4(pack_e4m3x4(v[0] * sc, v[1] * sc, v[2] * sc, v[3] * sc),
-                                               pack_e4m3x4(v[4] * sc, v[5] * sc, v[6] * sc, v[7] * sc),
-                                               pack_e4m3x4(v[8] * sc, v[9] * sc, v[10] * sc, v[11] * sc),
-                                               pack_e4m3x4(v[12] * sc, v[13] * sc, v[14] * sc, v[15] * sc));
-                                if constexpr (COUT <= 64) {
-                                    if (P.pool_y) {
-                                        const uint32_t w4[4] = {q.x, q.y, q.z, q.w};
-#pragma unroll
-                                        for (int m = 0; m < 4; ++m) {
-                                            if (rr & 1)
-                                                pbot[4 * u + m] = w4[m];
-                                            else
-                                                ptop[4 * u + m] = w4[m];
-                                        }
-                                    }
-                                }
-                                if (stage) {
-                                    *reinterpret_cast<uint4*>(ob + ((u ^ swz) << 4)) = q;
-                                    continue;
-                                }
-                                uint8_t* dst = reinterpret_cast<uint8_t*>(P.y) + opix * P.ldy + P.coff + c;
-                                *reinterpret_cast<uint4*>(dst) = q;
-                                if (P.up2) {
-                                    const size_t ld = size_t(P.ldy);
-                                    *reinterpret_cast<uint4*>(dst + ld) = q;
-                                    *reinterpret_cast<uint4*>(dst + rowstep * ld) = q;
-                                    *reinterpret_cast<uint4*>(dst + (rowstep + 1) * ld) = q;
-                                }
+                                *reinterpret_cast<uint4*>(ob + ((u ^ swz) << 4)) = make_uint4(w[0], w[1], w[2], w[3]);
                             } else {
-                                if (P.mask) {
-                                    const __nv_bfloat16* m = P.mask + opix * COUT + c;
+                                *reinterpret_cast<uint4*>(ob + (((2 * u) ^ swz) << 4)) =
+                                    make_uint4(w[0], w[1], w[2], w[3]);
+                                *reinterpret_cast<uint4*>(ob + (((2 * u + 1) ^ swz) << 4)) =
+                                    make_uint4(w[4 % kW], w[5 % kW], w[6 % kW], w[7 % kW]);
+                            }
+                            continue;
+                        }
+                        if (!xin) continue;
+                        if (FP8) {
+                            uint8_t* dst = reinterpret_cast<uint8_t*>(P.y) + opix * P.ldy + P.coff + c;
+                            const uint4 q = make_uint4(w[0], w[1], w[2], w[3]);
+                            *reinterpret_cast<uint4*>(dst) = q;
+                            if (P.up2) {
+                                const size_t ld = size_t(P.ldy);
+                                *reinterpret_cast<uint4*>(dst + ld) = q;
+                                *reinterpret_cast<uint4*>(dst + rowstep * ld) = q;
+                                *reinterpret_cast<uint4*>(dst + (rowstep + 1) * ld) = q;
+                            }
+                        } else {
+                            __nv_bfloat16* dst = P.y + opix * P.ldy + P.coff + c;
+                            const uint4 q0 = make_uint4(w[0], w[1], w[2], w[3]);
+                            const uint4 q1 = make_uint4(w[4 % kW], w[5 % kW], w[6 % kW], w[7 % kW]);
+                            const int nst = P.up2 ? 4 : 1;
+                            for (int k = 0; k < nst; ++k) {
+                                const size_t off = (k >> 1) * rowstep + (k & 1);     // pixels from the first
+                                uint4* d4 = reinterpret_cast<uint4*>(dst + off * P.ldy);
+                                d4[0] = q0;
+                                d4[1] = q1;
+                            }
+                        }
+                    }
+                    if (COUT <= 64 && P.head_w && xin) {
+                        // s = rgb / 255 + (W d1 + b); out = round(255 clamp(s, 0, 1))
+                        const size_t p = (size_t(n) * H + y) * Wd + x;
 #pragma unroll
-                                    for (int j = 0; j < 16; j += 2) {
-                                        const __nv_bfloat162 mm = *reinterpret_cast<const __nv_bfloat162*>(m + j);
-                                        if (!(__bfloat162float(mm.x) > 0.0f)) v[j] = 0.0f;
-                                        if (!(__bfloat162float(mm.y) > 0.0f)) v[j + 1] = 0.0f;
-                                    }
-                                }
-                                const uint4 q0 = make_uint4(pack_bf16x2(v[0], v[1]), pack_bf16x2(v[2], v[3]),
-                                                            pack_bf16x2(v[4], v[5]), pack_bf16x2(v[6], v[7]));
-                                const uint4 q1 = make_uint4(pack_bf16x2(v[8], v[9]), pack_bf16x2(v[10], v[11]),
-                                                            pack_bf16x2(v[12], v[13]), pack_bf16x2(v[14], v[15]));
-                                if constexpr (COUT <= 64) {
-                                    if (P.pool_y) {
-                                        const uint32_t w8[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
-#pragma unroll
-                                        for (int m = 0; m < 8; ++m) {
-                                            if (rr & 1)
-                                                pbot[8 * u + m] = w8[m];
-                                            else
-                                                ptop[8 * u + m] = w8[m];
-                                        }
-                                    }
-                                }
-                                if (stage) {
-                                    *reinterpret_cast<uint4*>(ob + (((2 * u) ^ swz) << 4)) = q0;
-                                    *reinterpret_cast<uint4*>(ob + (((2 * u + 1) ^ swz) << 4)) = q1;
-                                    continue;
-                                }
-                                __nv_bfloat16* dst = P.y + opix * P.ldy + P.coff + c;
-                                const int nst = P.up2 ? 4 : 1;
-                                for (int k = 0; k < nst; ++k) {
-                                    const size_t off = (k >> 1) * rowstep + (k & 1);     // pixels from the first
-                                    uint4* d4 = reinterpret_cast<uint4*>(dst + off * P.ldy);
-                                    d4[0] = q0;
-                                    d4[1] = q1;
-                                }
+                        for (int k = 0; k < 3; ++k) {
+                            const float sv = float(P.head_rgb[3 * p + k]) * (1.0f / 255.0f) + hr[k];
+                            const float pr = fminf(fmaxf(sv, 0.0f), 1.0f);
+                            if (P.head_f32) P.head_f32[3 * p + k] = pr;
+                            if (P.head_out) {
+                                const size_t yy = p / size_t(Wd), xx = p % size_t(Wd);
+                                P.head_out[yy * P.head_pitch + 3 * xx + k] = uint8_t(floorf(pr * 255.0f + 0.5f));
                             }
                         }
                     }
@@ -560,44 +633,6 @@ k_conv3x3_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CU
                                 tc::tma_store_3d(m, src, c0, xw, row);
                             }
                             tc::bulk_commit();
-                        }
-                    }
-                }
-                if constexpr (COUT <= 64) {
-                    if (P.pool_y && (rr & 1)) {
-                        // rows y - 1 and y, pixels xe and xe + 1; the even lane takes
-                        // the first half of the channels, the odd lane the second
-                        constexpr int kHalf = kPoolW / 2;
-                        const bool ev = (lane & 1) == 0;
-                        const int xe = x & ~1;
-                        uint32_t outw[kHalf], argw[kHalf];
-#pragma unroll
-                        for (int i = 0; i < kHalf; ++i) {
-                            const uint32_t ot = __shfl_xor_sync(~0u, ev ? ptop[kHalf + i] : ptop[i], 1);
-                            const uint32_t obt = __shfl_xor_sync(~0u, ev ? pbot[kHalf + i] : pbot[i], 1);
-                            const uint32_t mt = ev ? ptop[i] : ptop[kHalf + i];
-                            const uint32_t mb = ev ? pbot[i] : pbot[kHalf + i];
-                            const uint32_t c[4] = {ev ? mt : ot, ev ? ot : mt, ev ? mb : obt, ev ? obt : mb};
-                            argw[i] = 0u;
-                            outw[i] = FP8 ? pool4_e4m3(c) : pool4_bf16(c, &argw[i]);
-                        }
-                        if (xe + 1 < Wd) {
-                            const size_t pp = (size_t(n) * (H / 2) + (y >> 1)) * size_t(Wd / 2) + (xe >> 1);
-                            const int ch0 = ev ? 0 : COUT / 2;
-                            uint2* dst = reinterpret_cast<uint2*>(reinterpret_cast<uint8_t*>(P.pool_y) +
-                                                                  (pp * COUT + ch0) * kEsize);
-#pragma unroll
-                            for (int i = 0; i < kHalf / 2; ++i) dst[i] = make_uint2(outw[2 * i], outw[2 * i + 1]);
-                            if (!FP8 && P.pool_arg) {
-                                uint32_t ab[kHalf / 2];
-#pragma unroll
-                                for (int i = 0; i < kHalf / 2; ++i)
-                                    ab[i] = (argw[2 * i] & 0xFFu) | ((argw[2 * i] >> 16) << 8) |
-                                            ((argw[2 * i + 1] & 0xFFu) << 16) | ((argw[2 * i + 1] >> 16) << 24);
-                                uint2* da = reinterpret_cast<uint2*>(P.pool_arg + pp * COUT + ch0);
-#pragma unroll
-                                for (int i = 0; i < kHalf / 4; ++i) da[i] = make_uint2(ab[2 * i], ab[2 * i + 1]);
-                            }
                         }
                     }
                 }
@@ -790,6 +825,10 @@ cudaError_t launch_conv3x3(const void* x, int NB, int H, int W, int Cin, const v
     if ((a.pool_y || a.pool_arg) && (!conv_pool_supported(Cout) || !a.pool_y || !a.relu || a.up2 || a.mask))
         return cudaErrorInvalidValue;
     if (a.pool_arg && fp8) return cudaErrorInvalidValue;
+    if (a.head_w && (!conv_pool_supported(Cout) || !a.head_b || !a.relu || a.up2 || a.mask || a.pool_y || a.coff ||
+                     (a.ldy && a.ldy != Cout) || !a.head_rgb || (!a.head_out && !a.head_f32)))
+        return cudaErrorInvalidValue;
+    if (a.head_w && fp8 && !(a.head_scale > 0.0f)) return cudaErrorInvalidValue;
     if (a.xstride < Cin || a.xstride % (fp8 ? 16 : 8)) return cudaErrorInvalidValue;
     a.tiles_x = (W + kTileM - 1) / kTileM;
     if (a.ldy == 0) a.ldy = Cout;
