@@ -672,7 +672,7 @@ fvv_status fvv_unet_conv3x3(const void* x, int32_t n, int32_t h, int32_t w, int3
         return fail(FVV_ERR_INVALID_ARG, "need n, h, w >= 1 and cin a multiple of 8");
     if (!fvv::conv_cout_supported(cout))
         return fail(FVV_ERR_INVALID_ARG, "cout must be 32, 48, 64, 96, 128 or 192");
-    if (uint64_t(n) * h * ((w + 127) / 128) >= (uint64_t(1) << 31))
+    if (uint64_t(n) * h * ((w + 119) / 120) >= (uint64_t(1) << 31))
         return fail(FVV_ERR_INVALID_ARG, "too many pixel tiles");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     int* flag = nullptr;
@@ -703,7 +703,7 @@ fvv_status fvv_unet_conv3x3_e4m3(const void* x, int32_t n, int32_t h, int32_t w,
         return fail(FVV_ERR_INVALID_ARG, "cout must be 32, 48, 64, 96, 128 or 192");
     if (!(acc_scale > 0.0f) || !(out_inv_scale > 0.0f) || !std::isfinite(acc_scale) || !std::isfinite(out_inv_scale))
         return fail(FVV_ERR_INVALID_ARG, "scales must be finite and > 0");
-    if (uint64_t(n) * h * ((w + 127) / 128) >= (uint64_t(1) << 31))
+    if (uint64_t(n) * h * ((w + 119) / 120) >= (uint64_t(1) << 31))
         return fail(FVV_ERR_INVALID_ARG, "too many pixel tiles");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     int* flag = nullptr;
@@ -741,7 +741,7 @@ fvv_status fvv_unet_conv3x3_pool(const void* x, int32_t n, int32_t h, int32_t w,
     if (e4m3 && (!(acc_scale > 0.0f) || !(out_inv_scale > 0.0f) || !std::isfinite(acc_scale) ||
                  !std::isfinite(out_inv_scale)))
         return fail(FVV_ERR_INVALID_ARG, "scales must be finite and > 0");
-    if (uint64_t(n) * h * ((w + 127) / 128) >= (uint64_t(1) << 31))
+    if (uint64_t(n) * h * ((w + 119) / 120) >= (uint64_t(1) << 31))
         return fail(FVV_ERR_INVALID_ARG, "too many pixel tiles");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     int* flag = nullptr;

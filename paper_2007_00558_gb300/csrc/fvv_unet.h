@@ -12,7 +12,7 @@ struct ConvArgs {
     int NB, H, W, Cin;              // input; Cin a multiple of 8 (bf16) or 16 (e4m3)
     int xstride;                    // input channels per pixel in memory (0: Cin); channels
                                     // Cin..xstride-1 are read but must hold zeros
-    int tiles_x;                    // ceil(W / 128), set by the launcher
+    int tiles_x;                    // tiles per image row, set by the launcher
     const float* bias;              // [Cout] or null (16-byte aligned)
     __nv_bfloat16* y;               // output pixel p, channel c at y[p * ldy + coff + c] (e4m3: bytes)
     int ldy, coff;                  // output channel stride (0: Cout) and offset

@@ -40,7 +40,6 @@ namespace fvv {
 namespace {
 
 constexpr int kTileM = 128;
-constexpr int kHaloPx = kTileM + 2;                    // 130 halo pixels per row
 constexpr int kRow = 64;                               // bytes of one pixel row of a channel group
 constexpr int kThreads = 320;
 constexpr int kMaxStages = 8;
@@ -48,13 +47,27 @@ constexpr int kSmemLimit = 227 * 1024;
 constexpr int kHeader = 2048;                          // barriers (bytes 0..511) and bias (512..1279)
 constexpr int kSmemFixed = 1024 + kHeader;             // alignment slack + header
 
-template <int COUT>
+// kFold (32 output channels, where a 128 x 32 MMA is bound by its issue
+// cost): the three kx taps of one ky run as ONE MMA of N = 96 against the
+// unshifted halo row, D[p][32 kx + c] = sum over ky of A_ky[p] W(ky, kx);
+// output pixel q is then D[q][c] + D[q+1][32+c] + D[q+2][64+c], summed in
+// the epilogue with warp shuffles.  Each TMEM lane quadrant (one epilogue
+// warp) holds its own window of 32 halo pixels, overlapping the next by 2,
+// so a warp finds all three terms of its first 30 pixels in its own lanes:
+// a tile covers 4 x 30 output pixels.
+template <int COUT, bool FOLD = false>
 struct ConvCfg {
+    static_assert(!FOLD || COUT == 32, "the folded form is for 32 output channels");
+    static constexpr bool kFold = FOLD;
     static constexpr int kTap = COUT * kRow;           // B tile of one tap (COUT rows of 64 bytes)
     static constexpr int kSlice = 3 * kTap;            // the three taps of one ky
     static constexpr int kGroup = 9 * kTap;            // all taps of one channel group
-    static constexpr int kAcc = (COUT + 31) / 32 * 32; // TMEM columns of one output row's accumulator
-    static constexpr int kRows = COUT <= 32 ? 4 : COUT <= 64 ? 2 : 1;   // output rows per tile
+    static constexpr int kN = kFold ? 3 * COUT : COUT; // MMA N
+    static constexpr int kAcc = (kN + 31) / 32 * 32;   // TMEM columns of one output row's accumulator
+    static constexpr int kRows = kFold ? 2 : COUT <= 32 ? 4 : COUT <= 64 ? 2 : 1;   // output rows per tile
+    static constexpr int kHaloPx = kFold ? 128 : kTileM + 2;           // halo pixels per halo row
+    static constexpr int kQuad = kFold ? 30 : 32;      // output pixels per lane quadrant
+    static constexpr int kTileOut = 4 * kQuad;         // output pixels per tile row
     static constexpr int kTileAcc = kRows * kAcc;      // TMEM columns of one tile
     static constexpr int kNumAcc = 4 * kTileAcc <= 512 ? 4 : 2;        // accumulator ring depth
     static constexpr int kTmemCols = kNumAcc * kTileAcc <= 64 ? 64 : kNumAcc * kTileAcc <= 128 ? 128
@@ -77,10 +90,10 @@ struct Plan {
 
 // Shared memory: resident weights come first (they are read by every tile),
 // then the staged output, then the depth of the rings.  hs = 0: no plan fits.
-template <int COUT>
+template <int COUT, bool FOLD>
 Plan make_plan(int groups, bool fp8, bool want_out)
 {
-    using C = ConvCfg<COUT>;
+    using C = ConvCfg<COUT, FOLD>;
     Plan p{};
     const int res = groups * C::kGroup;
     for (int out = want_out ? 1 : 0; out >= 0; --out) {
@@ -165,7 +178,7 @@ __device__ __forceinline__ void mma_group(uint32_t d, uint64_t da, uint64_t db, 
         for (int kx = 0; kx < 3; ++kx)
 #pragma unroll
             for (int ks = 0; ks < NKS; ++ks) {
-                const uint64_t a = da + uint64_t(((ky * kHaloPx + kx) * kRow) >> 4) + 2 * ks;
+                const uint64_t a = da + uint64_t(((ky * Cfg::kHaloPx + kx) * kRow) >> 4) + 2 * ks;
                 const uint64_t b = db + uint64_t((ky * Cfg::kSlice + kx * Cfg::kTap) >> 4) + 2 * ks;
                 const uint32_t acc = (ky | kx | ks) != 0 ? 1u : acc0;
                 if (FP8)
@@ -173,6 +186,28 @@ __device__ __forceinline__ void mma_group(uint32_t d, uint64_t da, uint64_t db, 
                 else
                     tc::mma_bf16(d, a, b, idesc, acc);
             }
+}
+
+// kFold: the MMAs of one output row and channel group, one per (ky, K-step)
+// with N = 96; A of ky starts ky halo rows further on, B of ky is the
+// contiguous slice of its three taps.  NKY: slices resident (3, ky from the
+// group's base) or one streamed slice (1, the caller passes its ky's A).
+template <bool FP8, int NKS, int NKY>
+__device__ __forceinline__ void mma_fold(uint32_t d, uint64_t da, uint64_t db, uint32_t idesc, uint32_t acc0)
+{
+    using Cfg = ConvCfg<32, true>;
+#pragma unroll
+    for (int ky = 0; ky < NKY; ++ky)
+#pragma unroll
+        for (int ks = 0; ks < NKS; ++ks) {
+            const uint64_t a = da + uint64_t((ky * Cfg::kHaloPx * kRow) >> 4) + 2 * ks;
+            const uint64_t b = db + uint64_t((ky * Cfg::kSlice) >> 4) + 2 * ks;
+            const uint32_t acc = (ky | ks) != 0 ? 1u : acc0;
+            if (FP8)
+                tc::mma_e4m3(d, a, b, idesc, acc);
+            else
+                tc::mma_bf16(d, a, b, idesc, acc);
+        }
 }
 
 // 2 x 2 max pooling of packed non-negative values (bf16 pairs or e4m3
@@ -210,13 +245,13 @@ __device__ __forceinline__ uint32_t pool4_e4m3(const uint32_t (&c)[4])
 
 // FP8: e4m3 operands and output (K = 32 channels per MMA, 64 per group);
 // otherwise bf16 (K = 16, 32 per group).
-template <int COUT, bool FP8>
+template <int COUT, bool FP8, bool FOLD>
 __global__ void __launch_bounds__(kThreads, 1)
 k_conv3x3_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUtensorMap tmw,
              const __grid_constant__ CUtensorMap tmy, const __grid_constant__ CUtensorMap tmy2, ConvArgs P,
              int n_tiles, int HS, int WS, int resident, int tma_out)
 {
-    using Cfg = ConvCfg<COUT>;
+    using Cfg = ConvCfg<COUT, FOLD>;
     static_assert(512 + 4 * COUT <= kHeader, "bias fits the header");
     static_assert(COUT > 64 || 768 + 4 * (3 * COUT + 3) <= kHeader, "head weights fit the header");
     constexpr int kPerGroup = FP8 ? 64 : 32;           // channels in one 64-byte row
@@ -295,7 +330,7 @@ k_conv3x3_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CU
             for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
                 const int xt = tile % P.tiles_x, rb = tile / P.tiles_x;
                 const int y0 = (rb % tiles_y) * R, n = rb / tiles_y;
-                const int x0 = xt * kTileM;
+                const int x0 = xt * Cfg::kTileOut;
                 for (int g = 0; g < G && ok; ++g) {
                     const int sh = int(qh % uint32_t(HS));
                     if (!tc::mbar_wait_sleep(&empty_h[sh], ((qh / uint32_t(HS)) & 1u) ^ 1u, P.err, 1)) {
@@ -303,8 +338,16 @@ k_conv3x3_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CU
                         break;
                     }
                     tc::mbar_arrive_expect_tx(&full_h[sh], Cfg::kHaloBytes);
-                    tc::tma_load_4d(sHalo + sh * Cfg::kHaloStage, &tmx, &full_h[sh], g * kPerGroup, x0 - 1, y0 - 1,
-                                    n);
+                    if constexpr (Cfg::kFold) {
+                        // one 32-pixel window per lane quadrant and halo row
+                        for (int h = 0; h < Cfg::kHaloRows; ++h)
+                            for (int k = 0; k < 4; ++k)
+                                tc::tma_load_4d(sHalo + sh * Cfg::kHaloStage + (h * Cfg::kHaloPx + 32 * k) * kRow, &tmx,
+                                                &full_h[sh], g * kPerGroup, x0 - 1 + Cfg::kQuad * k, y0 - 1 + h, n);
+                    } else {
+                        tc::tma_load_4d(sHalo + sh * Cfg::kHaloStage, &tmx, &full_h[sh], g * kPerGroup, x0 - 1, y0 - 1,
+                                        n);
+                    }
                     ++qh;
                     if (!resident) {
                         for (int ky = 0; ky < 3; ++ky, ++qw) {
@@ -327,7 +370,7 @@ k_conv3x3_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CU
         // group is one straight run of MMAs with compile-time descriptor
         // offsets (the issue loop is the critical path of the kernel).
         if (lane == 0) {
-            constexpr uint32_t idesc = FP8 ? tc::idesc_e4m3(kTileM, COUT) : tc::idesc_bf16(kTileM, COUT);
+            constexpr uint32_t idesc = FP8 ? tc::idesc_e4m3(kTileM, Cfg::kN) : tc::idesc_bf16(kTileM, Cfg::kN);
             bool ok = !resident || tc::mbar_wait(wready, 0, P.err, 3);
             const int nks_last = (min(kPerGroup, Cin - (G - 1) * kPerGroup) * kEsize + 31) / 32;
             const uint64_t dh0 = tc::desc_kmajor_sw64(tc::smem_u32(sHalo));
@@ -357,11 +400,18 @@ k_conv3x3_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CU
                         for (int r = 0; r < R; ++r) {
                             // output row r: its accumulator, the halo from row r on
                             const uint32_t dr = d + uint32_t(r * Cfg::kAcc);
-                            const uint64_t dar = da + uint64_t((r * kHaloPx * kRow) >> 4);
-                            if (two)
-                                mma_group<COUT, FP8, 2>(dr, dar, db, idesc, acc0);
-                            else
-                                mma_group<COUT, FP8, 1>(dr, dar, db, idesc, acc0);
+                            const uint64_t dar = da + uint64_t((r * Cfg::kHaloPx * kRow) >> 4);
+                            if constexpr (Cfg::kFold) {
+                                if (two)
+                                    mma_fold<FP8, 2, 3>(dr, dar, db, idesc, acc0);
+                                else
+                                    mma_fold<FP8, 1, 3>(dr, dar, db, idesc, acc0);
+                            } else {
+                                if (two)
+                                    mma_group<COUT, FP8, 2>(dr, dar, db, idesc, acc0);
+                                else
+                                    mma_group<COUT, FP8, 1>(dr, dar, db, idesc, acc0);
+                            }
                         }
                     } else {
                         for (int ky = 0; ky < 3; ++ky) {
@@ -374,11 +424,18 @@ k_conv3x3_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CU
 #pragma unroll
                             for (int r = 0; r < R; ++r) {
                                 const uint32_t dr = d + uint32_t(r * Cfg::kAcc);
-                                const uint64_t dak = da + uint64_t(((r + ky) * kHaloPx * kRow) >> 4);
-                                if (two)
-                                    mma_row<COUT, FP8, 2>(dr, dak, db, idesc, a0);
-                                else
-                                    mma_row<COUT, FP8, 1>(dr, dak, db, idesc, a0);
+                                const uint64_t dak = da + uint64_t(((r + ky) * Cfg::kHaloPx * kRow) >> 4);
+                                if constexpr (Cfg::kFold) {
+                                    if (two)
+                                        mma_fold<FP8, 2, 1>(dr, dak, db, idesc, a0);
+                                    else
+                                        mma_fold<FP8, 1, 1>(dr, dak, db, idesc, a0);
+                                } else {
+                                    if (two)
+                                        mma_row<COUT, FP8, 2>(dr, dak, db, idesc, a0);
+                                    else
+                                        mma_row<COUT, FP8, 1>(dr, dak, db, idesc, a0);
+                                }
                             }
                             tc::mma_commit(&empty_w[sw]);      // the slice is free once these finish
                             if (++sw == WS) {
@@ -431,9 +488,9 @@ k_conv3x3_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CU
             tc::fence_after_sync();
             const int xt = tile % P.tiles_x, rb = tile / P.tiles_x;
             const int y0 = (rb % tiles_y) * R, n = rb / tiles_y;
-            const int xw = xt * kTileM + qd * 32, x = xw + lane;
-            const bool xin = x < Wd;
-            const bool pair_in = (x | 1) < Wd;                     // both pixels of this lane's pooling pair
+            const int xw = xt * Cfg::kTileOut + qd * Cfg::kQuad, x = xw + lane;
+            const bool xin = lane < Cfg::kQuad && x < Wd;
+            const bool pair_in = lane < Cfg::kQuad && (x | 1) < Wd;   // both pixels of this lane's pooling pair
             const bool stage = tma_out && xw < Wd;                 // (uniform over the warp)
 #pragma unroll 1
             for (int rr = 0; rr < R; ++rr) {
@@ -458,9 +515,23 @@ k_conv3x3_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CU
                         if (lane == 0) tc::bulk_wait_read<0>();    // the buffer's previous store has read it
                         __syncwarp();
                     }
+                    if constexpr (Cfg::kFold) {
+                        // the three kx partial sums of output pixel x are in lanes l, l+1, l+2
+                        uint32_t t0[32], t1[32], t2[32];
+                        tc::tmem_ld_x32(taddr, t0);
+                        tc::tmem_ld_x32(taddr + 32u, t1);
+                        tc::tmem_ld_x32(taddr + 64u, t2);
+                        tc::tmem_ld_wait();
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) {
+                            const float s1 = __uint_as_float(__shfl_down_sync(~0u, t1[j], 1));
+                            const float s2 = __uint_as_float(__shfl_down_sync(~0u, t2[j], 2));
+                            r[j >> 4][j & 15] = __float_as_uint(__uint_as_float(t0[j]) + s1 + s2);
+                        }
+                    }
                     // as few TMEM loads as the chunk allows (32 columns each, 16 for an odd unit)
 #pragma unroll
-                    for (int h = 0; h < 2; ++h) {
+                    for (int h = 0; h < 2 && !Cfg::kFold; ++h) {
                         if (2 * h + 1 < nu) {
                             uint32_t t[32];
                             tc::tmem_ld_x32(taddr + uint32_t(c0 + 32 * h), t);
@@ -665,15 +736,15 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
     return fn;
 }
 
-// x: [NB][H][W][C], halo box {one 64-byte channel group, 130 pixels, rows, 1 image}
-cudaError_t make_halo_map(CUtensorMap* m, const void* x, int NB, int H, int W, int C, bool fp8, int rows)
+// x: [NB][H][W][C], halo box {one 64-byte channel group, px pixels, rows, 1 image}
+cudaError_t make_halo_map(CUtensorMap* m, const void* x, int NB, int H, int W, int C, bool fp8, int px, int rows)
 {
     auto enc = encode_fn();
     if (!enc) return cudaErrorNotSupported;
     const cuuint64_t es = fp8 ? 1 : 2;
     const cuuint64_t dims[4] = {cuuint64_t(C), cuuint64_t(W), cuuint64_t(H), cuuint64_t(NB)};
     const cuuint64_t strides[3] = {cuuint64_t(C) * es, cuuint64_t(W) * C * es, cuuint64_t(H) * W * C * es};
-    const cuuint32_t box[4] = {cuuint32_t(kRow / es), cuuint32_t(kHaloPx), cuuint32_t(rows), 1};
+    const cuuint32_t box[4] = {cuuint32_t(kRow / es), cuuint32_t(px), cuuint32_t(rows), 1};
     const cuuint32_t el[4] = {1, 1, 1, 1};
     CUresult r = enc(m, fp8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4,
                      const_cast<void*>(x), dims, strides, box, el, CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -716,7 +787,7 @@ int num_sms()
 // tensor seen as (cout, dx, W, dy, NB*H), so that one box written at
 // (c, dx, x, dy, row) lands on the pixels (2 row + dy, 2 x + dx).
 cudaError_t make_out_map(CUtensorMap* m, void* y, int NB, int H, int W, int ldy, int coff, int cout, int chunk,
-                         bool fp8, bool up2)
+                         int quad, bool fp8, bool up2)
 {
     auto enc = encode_fn();
     if (!enc) return cudaErrorNotSupported;
@@ -733,14 +804,14 @@ cudaError_t make_out_map(CUtensorMap* m, void* y, int NB, int H, int W, int ldy,
     if (up2) {
         const cuuint64_t dims[5] = {cuuint64_t(cout), 2, cuuint64_t(W), 2, cuuint64_t(NB) * H};
         const cuuint64_t strides[4] = {px, 2 * px, 2 * cuuint64_t(W) * px, 4 * cuuint64_t(W) * px};
-        const cuuint32_t box[5] = {cuuint32_t(chunk), 1, 32, 1, 1};
+        const cuuint32_t box[5] = {cuuint32_t(chunk), 1, cuuint32_t(quad), 1, 1};
         const cuuint32_t el[5] = {1, 1, 1, 1, 1};
         r = enc(m, dt, 5, base, dims, strides, box, el, CU_TENSOR_MAP_INTERLEAVE_NONE, sw,
                 CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     } else {
         const cuuint64_t dims[3] = {cuuint64_t(cout), cuuint64_t(W), cuuint64_t(NB) * H};
         const cuuint64_t strides[2] = {px, cuuint64_t(W) * px};
-        const cuuint32_t box[3] = {cuuint32_t(chunk), 32, 1};
+        const cuuint32_t box[3] = {cuuint32_t(chunk), cuuint32_t(quad), 1};
         const cuuint32_t el[3] = {1, 1, 1};
         r = enc(m, dt, 3, base, dims, strides, box, el, CU_TENSOR_MAP_INTERLEAVE_NONE, sw,
                 CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -748,8 +819,8 @@ cudaError_t make_out_map(CUtensorMap* m, void* y, int NB, int H, int W, int ldy,
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-template <int COUT, bool FP8>
-cudaError_t launch_conv(const void* x, const void* w, const ConvArgs& a, cudaStream_t s)
+template <int COUT, bool FP8, bool FOLD = false>
+cudaError_t launch_conv(const void* x, const void* w, ConvArgs a, cudaStream_t s)
 {
     constexpr int kPerGroup = FP8 ? 64 : 32;
     const int G = (a.Cin + kPerGroup - 1) / kPerGroup;
@@ -757,11 +828,13 @@ cudaError_t launch_conv(const void* x, const void* w, const ConvArgs& a, cudaStr
     // channel slice of a wider tensor, or four times for the upsampling.  A
     // dense output is already written in whole lines by the threads.
     const bool want_out = a.up2 || a.ldy != COUT || a.coff != 0;
-    Plan p = make_plan<COUT>(G, FP8, want_out);
+    Plan p = make_plan<COUT, FOLD>(G, FP8, want_out);
     if (p.hs < 2 || (!p.resident && p.ws < 2)) return cudaErrorInvalidValue;
     CUtensorMap mx, mw, my, my2;
-    using C = ConvCfg<COUT>;
-    cudaError_t e = make_halo_map(&mx, x, a.NB, a.H, a.W, a.xstride, FP8, C::kHaloRows);
+    using C = ConvCfg<COUT, FOLD>;
+    a.tiles_x = (a.W + C::kTileOut - 1) / C::kTileOut;
+    cudaError_t e = C::kFold ? make_halo_map(&mx, x, a.NB, a.H, a.W, a.xstride, FP8, 32, 1)
+                             : make_halo_map(&mx, x, a.NB, a.H, a.W, a.xstride, FP8, C::kHaloPx, C::kHaloRows);
     if (e != cudaSuccess) return e;
     e = make_weight_map(&mw, w, COUT, a.Cin, FP8);
     if (e != cudaSuccess) return e;
@@ -770,16 +843,17 @@ cudaError_t launch_conv(const void* x, const void* w, const ConvArgs& a, cudaStr
     if (p.out) {
         // a layout the tensor maps cannot describe keeps the per-thread stores
         const int tail = COUT > 64 ? COUT % 64 : 0;
-        if (make_out_map(&my, a.y, a.NB, a.H, a.W, a.ldy, a.coff, COUT, C::kChunk, FP8, a.up2 != 0) != cudaSuccess ||
-            (tail && make_out_map(&my2, a.y, a.NB, a.H, a.W, a.ldy, a.coff, COUT, tail, FP8, a.up2 != 0) !=
+        if (make_out_map(&my, a.y, a.NB, a.H, a.W, a.ldy, a.coff, COUT, C::kChunk, C::kQuad, FP8, a.up2 != 0) !=
+                cudaSuccess ||
+            (tail && make_out_map(&my2, a.y, a.NB, a.H, a.W, a.ldy, a.coff, COUT, tail, C::kQuad, FP8, a.up2 != 0) !=
                          cudaSuccess))
             p.out = 0;
     }
-    e = cudaFuncSetAttribute(k_conv3x3_tc<COUT, FP8>, cudaFuncAttributeMaxDynamicSharedMemorySize, p.smem);
+    e = cudaFuncSetAttribute(k_conv3x3_tc<COUT, FP8, FOLD>, cudaFuncAttributeMaxDynamicSharedMemorySize, p.smem);
     if (e != cudaSuccess) return e;
     const long long tiles = (long long)a.tiles_x * a.NB * ((a.H + C::kRows - 1) / C::kRows);
     const int grid = int(std::min<long long>(tiles, num_sms()));
-    k_conv3x3_tc<COUT, FP8><<<grid, kThreads, p.smem, s>>>(mx, mw, my, my2, a, int(tiles), p.hs, p.ws, p.resident,
+    k_conv3x3_tc<COUT, FP8, FOLD><<<grid, kThreads, p.smem, s>>>(mx, mw, my, my2, a, int(tiles), p.hs, p.ws, p.resident,
                                                              p.out);
     return cudaGetLastError();
 }
@@ -788,7 +862,11 @@ template <bool FP8>
 cudaError_t dispatch(const void* x, const void* w, int Cout, const ConvArgs& a, cudaStream_t s)
 {
     switch (Cout) {
-    case 32: return launch_conv<32, FP8>(x, w, a, s);
+    case 32:
+        // the folded form pays where the MMAs outweigh the epilogue: two or
+        // more channel groups per tile
+        if (a.Cin > (FP8 ? 64 : 32)) return launch_conv<32, FP8, true>(x, w, a, s);
+        return launch_conv<32, FP8>(x, w, a, s);
     case 48: return launch_conv<48, FP8>(x, w, a, s);
     case 64: return launch_conv<64, FP8>(x, w, a, s);
     case 96: return launch_conv<96, FP8>(x, w, a, s);
@@ -830,7 +908,6 @@ cudaError_t launch_conv3x3(const void* x, int NB, int H, int W, int Cin, const v
         return cudaErrorInvalidValue;
     if (a.head_w && fp8 && !(a.head_scale > 0.0f)) return cudaErrorInvalidValue;
     if (a.xstride < Cin || a.xstride % (fp8 ? 16 : 8)) return cudaErrorInvalidValue;
-    a.tiles_x = (W + kTileM - 1) / kTileM;
     if (a.ldy == 0) a.ldy = Cout;
     if (a.acc_scale == 0.0f) a.acc_scale = 1.0f;
     if (a.out_inv_scale == 0.0f) a.out_inv_scale = 1.0f;
