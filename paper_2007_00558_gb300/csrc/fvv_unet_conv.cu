@@ -96,8 +96,8 @@ Plan make_plan(int groups, bool fp8, bool want_out)
     using C = ConvCfg<COUT, FOLD>;
     Plan p{};
     const int res = groups * C::kGroup;
-    for (int out = want_out ? 1 : 0; out >= 0; --out) {
-        const int fixed = kSmemFixed + (out ? 8 * C::out_buf(fp8) : 0);
+    for (int out = want_out ? 2 : 0; out >= 0; --out) {
+        const int fixed = kSmemFixed + out * 8 * C::out_buf(fp8);
         if (fixed + res + 3 * C::kHaloStage <= kSmemLimit) {
             p.resident = 1;
             p.out = out;
@@ -107,8 +107,8 @@ Plan make_plan(int groups, bool fp8, bool want_out)
             return p;
         }
     }
-    for (int out = want_out ? 1 : 0; out >= 0; --out) {
-        const int fixed = kSmemFixed + (out ? 8 * C::out_buf(fp8) : 0);
+    for (int out = want_out ? 2 : 0; out >= 0; --out) {
+        const int fixed = kSmemFixed + out * 8 * C::out_buf(fp8);
         const int ws = std::min(kMaxStages, (kSmemLimit - fixed - 3 * C::kHaloStage) / C::kSlice);
         if (ws >= 2) {
             p.resident = 0;
@@ -271,8 +271,8 @@ k_conv3x3_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CU
     int* skip = reinterpret_cast<int*>(tmem_slot + 1);
     float* s_bias = reinterpret_cast<float*>(base + 512);          // [COUT] (<= 192 floats)
     float* s_head = reinterpret_cast<float*>(base + 768);          // fused head: [3][COUT] weights, [3] bias
-    uint8_t* sOut = base + kHeader;                                  // [8 warps][kOutBuf] when tma_out
-    uint8_t* sHalo = sOut + (tma_out ? 8 * kOutBuf : 0);
+    uint8_t* sOut = base + kHeader;                                  // [8 warps][tma_out][kOutBuf]
+    uint8_t* sHalo = sOut + tma_out * 8 * kOutBuf;
     uint8_t* sW = sHalo + HS * Cfg::kHaloStage;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -482,6 +482,7 @@ k_conv3x3_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CU
 #pragma unroll
         for (int i = 0; i < kPoolW; ++i) ptop[i] = 0u;
         const bool ev = (lane & 1) == 0;
+        int nst = 0;                                               // chunks this warp has staged
         for (int tile = blockIdx.x + eg * gridDim.x, tl = eg; tile < n_tiles; tile += 2 * gridDim.x, tl += 2) {
             const int b = tl % Cfg::kNumAcc;
             if (!tc::mbar_wait_sleep(&acc_full[b], (tl / Cfg::kNumAcc) & 1, P.err, 7)) break;
@@ -502,6 +503,13 @@ k_conv3x3_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CU
                 const size_t rowstep = 2 * size_t(Wd);            // up2: the next output row
                 const size_t pp = (size_t(n) * (H / 2) + (y >> 1)) * size_t(Wd / 2) + (x >> 1);   // pooled pixel
                 const bool pool_row = COUT <= 64 && P.pool_y && (rr & 1);
+                // the head's colour input, fetched before the accumulator is read
+                float hrgb[3] = {0.0f, 0.0f, 0.0f};
+                if (COUT <= 64 && P.head_w && xin) {
+                    const size_t p = (size_t(n) * H + y) * Wd + x;
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) hrgb[k] = float(P.head_rgb[3 * p + k]);
+                }
                 const uint32_t taddr = tmem + (uint32_t(qd * 32) << 16) + uint32_t(b * Cfg::kTileAcc + rr * Cfg::kAcc);
                 // up to 64 columns per TMEM round trip, in units of 16
 #pragma unroll 1
@@ -509,10 +517,16 @@ k_conv3x3_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CU
                     uint32_t r[4][16];
                     const int nu = COUT <= 64 ? COUT / 16 : min(4, (COUT - c0) / 16);
                     const int row_bytes = nu * 16 * kEsize;
-                    uint8_t* ob = sOut + ew * kOutBuf + lane * row_bytes;
+                    uint8_t* const obuf = sOut + (ew * tma_out + (tma_out == 2 ? (nst & 1) : 0)) * kOutBuf;
+                    uint8_t* ob = obuf + lane * row_bytes;
                     const int swz = out_swizzle(row_bytes, lane);
                     if (stage) {
-                        if (lane == 0) tc::bulk_wait_read<0>();    // the buffer's previous store has read it
+                        if (lane == 0) {                           // the buffer's previous store has read it
+                            if (tma_out == 2)
+                                tc::bulk_wait_read<1>();
+                            else
+                                tc::bulk_wait_read<0>();
+                        }
                         __syncwarp();
                     }
                     if constexpr (Cfg::kFold) {
@@ -596,7 +610,11 @@ k_conv3x3_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CU
                                         a = __uint_as_float((j & 1) ? (wj & 0xFFFF0000u) : (wj << 16));
                                     }
 #pragma unroll
-                                    for (int k = 0; k < 3; ++k) hr[k] += s_head[k * COUT + c + j] * a;
+                                    for (int k = 0; k < 3; ++k) {
+                                        const float4 w4 = reinterpret_cast<const float4*>(s_head + k * COUT + c)[j >> 2];
+                                        const float wk = (j & 3) == 0 ? w4.x : (j & 3) == 1 ? w4.y : (j & 3) == 2 ? w4.z : w4.w;
+                                        hr[k] += wk * a;
+                                    }
                                 }
                                 continue;                          // the activations themselves are not stored
                             }
@@ -682,7 +700,7 @@ k_conv3x3_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CU
                         const size_t p = (size_t(n) * H + y) * Wd + x;
 #pragma unroll
                         for (int k = 0; k < 3; ++k) {
-                            const float sv = float(P.head_rgb[3 * p + k]) * (1.0f / 255.0f) + hr[k];
+                            const float sv = hrgb[k] * (1.0f / 255.0f) + hr[k];
                             const float pr = fminf(fmaxf(sv, 0.0f), 1.0f);
                             if (P.head_f32) P.head_f32[3 * p + k] = pr;
                             if (P.head_out) {
@@ -696,7 +714,7 @@ k_conv3x3_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CU
                         __syncwarp();
                         if (lane == 0) {                           // pixels past the image are clipped
                             const CUtensorMap* m = (COUT <= 64 || c0 + 64 <= COUT) ? &tmy : &tmy2;
-                            const uint8_t* src = sOut + ew * kOutBuf;
+                            const uint8_t* src = obuf;
                             const int row = n * H + y;
                             if (P.up2) {
                                 for (int k = 0; k < 4; ++k) tc::tma_store_5d(m, src, c0, k & 1, xw, k >> 1, row);
@@ -705,6 +723,7 @@ k_conv3x3_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CU
                             }
                             tc::bulk_commit();
                         }
+                        ++nst;
                     }
                 }
             }
