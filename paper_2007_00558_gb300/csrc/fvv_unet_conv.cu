@@ -55,8 +55,12 @@ constexpr int kSmemFixed = 1024 + kHeader;             // alignment slack + head
 // warp) holds its own window of 32 halo pixels, overlapping the next by 2,
 // so a warp finds all three terms of its first 30 pixels in its own lanes:
 // a tile covers 4 x 30 output pixels.
-template <int COUT, bool FOLD = false>
+// WIDE (96 and 128 output channels with streamed weights): two output rows
+// per tile instead of one, so that every weight slice streamed from L2 feeds
+// twice the MMAs.
+template <int COUT, bool FOLD = false, bool WIDE = false>
 struct ConvCfg {
+    static_assert(!WIDE || (!FOLD && (COUT == 96 || COUT == 128)), "the wide form is for 96 or 128 channels");
     static_assert(!FOLD || COUT == 32, "the folded form is for 32 output channels");
     static constexpr bool kFold = FOLD;
     static constexpr int kTap = COUT * kRow;           // B tile of one tap (COUT rows of 64 bytes)
@@ -64,7 +68,7 @@ struct ConvCfg {
     static constexpr int kGroup = 9 * kTap;            // all taps of one channel group
     static constexpr int kN = kFold ? 3 * COUT : COUT; // MMA N
     static constexpr int kAcc = (kN + 31) / 32 * 32;   // TMEM columns of one output row's accumulator
-    static constexpr int kRows = kFold ? 2 : COUT <= 32 ? 4 : COUT <= 64 ? 2 : 1;   // output rows per tile
+    static constexpr int kRows = kFold ? 2 : WIDE ? 2 : COUT <= 32 ? 4 : COUT <= 64 ? 2 : 1;   // rows per tile
     static constexpr int kHaloPx = kFold ? 128 : kTileM + 2;           // halo pixels per halo row
     static constexpr int kQuad = kFold ? 30 : 32;      // output pixels per lane quadrant
     static constexpr int kTileOut = 4 * kQuad;         // output pixels per tile row
@@ -90,10 +94,10 @@ struct Plan {
 
 // Shared memory: resident weights come first (they are read by every tile),
 // then the staged output, then the depth of the rings.  hs = 0: no plan fits.
-template <int COUT, bool FOLD>
+template <int COUT, bool FOLD, bool WIDE = false>
 Plan make_plan(int groups, bool fp8, bool want_out)
 {
-    using C = ConvCfg<COUT, FOLD>;
+    using C = ConvCfg<COUT, FOLD, WIDE>;
     Plan p{};
     const int res = groups * C::kGroup;
     for (int out = want_out ? 2 : 0; out >= 0; --out) {
@@ -107,7 +111,7 @@ Plan make_plan(int groups, bool fp8, bool want_out)
             return p;
         }
     }
-    for (int out = want_out ? 2 : 0; out >= 0; --out) {
+    for (int out = want_out ? 1 : 0; out >= 0; --out) {       // streamed: weight slices before staging
         const int fixed = kSmemFixed + out * 8 * C::out_buf(fp8);
         const int ws = std::min(kMaxStages, (kSmemLimit - fixed - 3 * C::kHaloStage) / C::kSlice);
         if (ws >= 2) {
@@ -245,13 +249,13 @@ __device__ __forceinline__ uint32_t pool4_e4m3(const uint32_t (&c)[4])
 
 // FP8: e4m3 operands and output (K = 32 channels per MMA, 64 per group);
 // otherwise bf16 (K = 16, 32 per group).
-template <int COUT, bool FP8, bool FOLD>
+template <int COUT, bool FP8, bool FOLD, bool WIDE>
 __global__ void __launch_bounds__(kThreads, 1)
 k_conv3x3_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUtensorMap tmw,
              const __grid_constant__ CUtensorMap tmy, const __grid_constant__ CUtensorMap tmy2, ConvArgs P,
              int n_tiles, int HS, int WS, int resident, int tma_out)
 {
-    using Cfg = ConvCfg<COUT, FOLD>;
+    using Cfg = ConvCfg<COUT, FOLD, WIDE>;
     static_assert(512 + 4 * COUT <= kHeader, "bias fits the header");
     static_assert(COUT > 64 || 768 + 4 * (3 * COUT + 3) <= kHeader, "head weights fit the header");
     constexpr int kPerGroup = FP8 ? 64 : 32;           // channels in one 64-byte row
@@ -838,7 +842,7 @@ cudaError_t make_out_map(CUtensorMap* m, void* y, int NB, int H, int W, int ldy,
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-template <int COUT, bool FP8, bool FOLD = false>
+template <int COUT, bool FP8, bool FOLD = false, bool WIDE = false>
 cudaError_t launch_conv(const void* x, const void* w, ConvArgs a, cudaStream_t s)
 {
     constexpr int kPerGroup = FP8 ? 64 : 32;
@@ -847,10 +851,10 @@ cudaError_t launch_conv(const void* x, const void* w, ConvArgs a, cudaStream_t s
     // channel slice of a wider tensor, or four times for the upsampling.  A
     // dense output is already written in whole lines by the threads.
     const bool want_out = a.up2 || a.ldy != COUT || a.coff != 0;
-    Plan p = make_plan<COUT, FOLD>(G, FP8, want_out);
+    Plan p = make_plan<COUT, FOLD, WIDE>(G, FP8, want_out);
     if (p.hs < 2 || (!p.resident && p.ws < 2)) return cudaErrorInvalidValue;
     CUtensorMap mx, mw, my, my2;
-    using C = ConvCfg<COUT, FOLD>;
+    using C = ConvCfg<COUT, FOLD, WIDE>;
     a.tiles_x = (a.W + C::kTileOut - 1) / C::kTileOut;
     cudaError_t e = C::kFold ? make_halo_map(&mx, x, a.NB, a.H, a.W, a.xstride, FP8, 32, 1)
                              : make_halo_map(&mx, x, a.NB, a.H, a.W, a.xstride, FP8, C::kHaloPx, C::kHaloRows);
@@ -868,13 +872,23 @@ cudaError_t launch_conv(const void* x, const void* w, ConvArgs a, cudaStream_t s
                          cudaSuccess))
             p.out = 0;
     }
-    e = cudaFuncSetAttribute(k_conv3x3_tc<COUT, FP8, FOLD>, cudaFuncAttributeMaxDynamicSharedMemorySize, p.smem);
+    e = cudaFuncSetAttribute(k_conv3x3_tc<COUT, FP8, FOLD, WIDE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             p.smem);
     if (e != cudaSuccess) return e;
     const long long tiles = (long long)a.tiles_x * a.NB * ((a.H + C::kRows - 1) / C::kRows);
     const int grid = int(std::min<long long>(tiles, num_sms()));
-    k_conv3x3_tc<COUT, FP8, FOLD><<<grid, kThreads, p.smem, s>>>(mx, mw, my, my2, a, int(tiles), p.hs, p.ws, p.resident,
+    k_conv3x3_tc<COUT, FP8, FOLD, WIDE><<<grid, kThreads, p.smem, s>>>(mx, mw, my, my2, a, int(tiles), p.hs, p.ws, p.resident,
                                                              p.out);
     return cudaGetLastError();
+}
+
+// Whether the one-row plan of a layer streams its weights.
+template <int COUT>
+bool streamed(const ConvArgs& a, bool fp8)
+{
+    const int G = (a.Cin + (fp8 ? 64 : 32) - 1) / (fp8 ? 64 : 32);
+    const bool want_out = a.up2 || (a.ldy && a.ldy != COUT) || a.coff != 0;
+    return !make_plan<COUT, false>(G, fp8, want_out).resident;
 }
 
 template <bool FP8>
@@ -888,8 +902,12 @@ cudaError_t dispatch(const void* x, const void* w, int Cout, const ConvArgs& a, 
         return launch_conv<32, FP8>(x, w, a, s);
     case 48: return launch_conv<48, FP8>(x, w, a, s);
     case 64: return launch_conv<64, FP8>(x, w, a, s);
-    case 96: return launch_conv<96, FP8>(x, w, a, s);
-    case 128: return launch_conv<128, FP8>(x, w, a, s);
+    case 96:
+        if (streamed<96>(a, FP8)) return launch_conv<96, FP8, false, true>(x, w, a, s);
+        return launch_conv<96, FP8>(x, w, a, s);
+    case 128:
+        if (streamed<128>(a, FP8)) return launch_conv<128, FP8, false, true>(x, w, a, s);
+        return launch_conv<128, FP8>(x, w, a, s);
     case 192: return launch_conv<192, FP8>(x, w, a, s);
     default: return cudaErrorInvalidValue;
     }
