@@ -3,7 +3,8 @@
 //
 // GEMM view: M = 128 consecutive output pixels of one image row, N = the
 // output channels, K = 9 taps x input channels.  A tile is R such rows
-// (R = 4 for 32 output channels, 2 for up to 64, else 1).  A persistent CTA
+// (R = 4 for 32 output channels, 2 for up to 64, else 1; the folded and
+// wide forms below use 2).  A persistent CTA
 // (one per SM) walks the tiles.  Input channels are taken in groups of one
 // 64-byte row (32 bf16 or 64 e4m3 channels).  For each tile and group, ONE
 // TMA copy brings the halo -- rows y0-1..y0+R, pixels x0-1..x0+128, zero
@@ -17,8 +18,10 @@
 // resident in shared memory when they fit; otherwise they stream through a
 // ring of one-ky slices (three taps).  The fp32 accumulators live in a TMEM
 // ring: the epilogue (scale, bias, ReLU, optional ReLU-derivative mask,
-// rounding to bf16 or e4m3, NHWC store, optional 2x2 max pooling) drains
-// tile i while the MMA thread accumulates the next ones.
+// rounding to bf16 or e4m3, NHWC store -- staged through shared memory and
+// TMA where the output is strided or upsampled --, optional 2x2 max pooling
+// or 1x1 output head) drains tile i while the MMA thread accumulates the
+// next ones.
 //
 // Warp roles (320 threads): 0 = TMA producer, 1 = TMEM owner and MMA issuer,
 // 2..9 = epilogue in two groups of four, taking alternate tiles (warp w
