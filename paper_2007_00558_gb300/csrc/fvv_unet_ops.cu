@@ -60,12 +60,11 @@ __global__ void k_pack_features(size_t npx, const uint8_t* __restrict__ rgb, con
         const __nv_bfloat162 h = __floats2bfloat162_rn(f[2 * i], f[2 * i + 1]);
         w[i] = *reinterpret_cast<const uint32_t*>(&h);
     }
-    uint4* dst = reinterpret_cast<uint4*>(out) + 4 * p;          // 32 channels per pixel
-    dst[0] = make_uint4(w[0], w[1], w[2], w[3]);
-    dst[1] = dst[2] = dst[3] = make_uint4(0u, 0u, 0u, 0u);
+    // 32 channels per pixel; channels 8..31 stay zero from the allocation
+    reinterpret_cast<uint4*>(out)[4 * p] = make_uint4(w[0], w[1], w[2], w[3]);
 }
 
-// e4m3 codes of feature / s0 in bytes 0..7, zero in 8..63
+// e4m3 codes of feature / s0 in bytes 0..7, zero in 8..15 (16..63: zero already)
 __global__ void k_pack_features_e4m3(size_t npx, const uint8_t* __restrict__ rgb, const float* __restrict__ depth,
                                      const uint8_t* __restrict__ hole, const float* __restrict__ top3,
                                      float inv_zfar, float inv_s0, uint8_t* __restrict__ out)
@@ -83,9 +82,8 @@ __global__ void k_pack_features_e4m3(size_t npx, const uint8_t* __restrict__ rgb
             make_float2(f[4 * i + 2] * inv_s0, f[4 * i + 3] * inv_s0), __NV_SATFINITE, __NV_E4M3);
         w[i] = uint32_t(lo) | (uint32_t(hi) << 16);
     }
-    uint4* dst = reinterpret_cast<uint4*>(out) + 4 * p;          // 64 bytes per pixel
-    dst[0] = make_uint4(w[0], w[1], 0u, 0u);
-    dst[1] = dst[2] = dst[3] = make_uint4(0u, 0u, 0u, 0u);
+    // 64 bytes per pixel; bytes 16..63 stay zero from the allocation
+    reinterpret_cast<uint4*>(out)[4 * p] = make_uint4(w[0], w[1], 0u, 0u);
 }
 
 // ---- 8-channel vectors: every channel count here is a multiple of 8 ---------
