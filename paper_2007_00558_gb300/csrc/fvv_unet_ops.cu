@@ -449,6 +449,84 @@ __global__ void __launch_bounds__(BCO * BCI / 4) k_wgrad3x3(int B, int H, int W,
     atomicAdd(&dw[o0 + K + 1], a11);
 }
 
+// The same sum for 32 x 32 (co x ci) blocks with every thread owning 4 x 4
+// outputs: per staged pixel two 16-byte shared-memory reads feed 16 FMAs
+// (the 2 x 2 form above does one read per FMA).  64 threads per CTA; dz and
+// x rows are staged 64 pixels at a time as fp32 with 16-byte loads.
+constexpr int kWgPix4 = 64;
+__global__ void __launch_bounds__(64) k_wgrad3x3_r4(int B, int H, int W, int Cin, int xs_, int Cout,
+                                                    const __nv_bfloat16* __restrict__ x,
+                                                    const __nv_bfloat16* __restrict__ dz, float* __restrict__ dw,
+                                                    int rows_per_cta)
+{
+    __shared__ __align__(16) float sz[kWgPix4][32];
+    __shared__ __align__(16) float sx[kWgPix4][32];
+    const int co_blocks = Cout / 32, ci_blocks = Cin / 32;
+    int t = blockIdx.x;
+    const int cib = t % ci_blocks;
+    t /= ci_blocks;
+    const int cob = t % co_blocks;
+    const int tap = t / co_blocks;
+    const int ky = tap / 3, kx = tap - 3 * ky;
+    const int tid = threadIdx.x;
+    const int tco = (tid >> 3) * 4, tci = (tid & 7) * 4;
+    float acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.0f;
+    const long total_rows = long(B) * H;
+    const long r0 = long(blockIdx.y) * rows_per_cta;
+    const long r1 = min(total_rows, r0 + rows_per_cta);
+    for (long r = r0; r < r1; ++r) {
+        const int b = int(r / H), yy = int(r % H);
+        const int ys = yy + ky - 1;
+        for (int x0 = 0; x0 < W; x0 += kWgPix4) {
+            __syncthreads();
+            for (int i = tid; i < kWgPix4 * 4; i += 64) {
+                const int pp = i >> 2, q = i & 3;                 // pixel, 8-channel quarter
+                const int xx = x0 + pp, xs = xx + kx - 1;
+                float fz[8], fx[8];
+                if (xx < W) {
+                    unpack8(*reinterpret_cast<const uint4*>(dz + ((size_t(b) * H + yy) * W + xx) * Cout + cob * 32 + 8 * q), fz);
+                } else {
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) fz[k] = 0.0f;
+                }
+                if (xx < W && ys >= 0 && ys < H && xs >= 0 && xs < W) {
+                    unpack8(*reinterpret_cast<const uint4*>(x + ((size_t(b) * H + ys) * W + xs) * xs_ + cib * 32 + 8 * q), fx);
+                } else {
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) fx[k] = 0.0f;
+                }
+                float4* dzs = reinterpret_cast<float4*>(&sz[pp][8 * q]);
+                float4* dxs = reinterpret_cast<float4*>(&sx[pp][8 * q]);
+                dzs[0] = make_float4(fz[0], fz[1], fz[2], fz[3]);
+                dzs[1] = make_float4(fz[4], fz[5], fz[6], fz[7]);
+                dxs[0] = make_float4(fx[0], fx[1], fx[2], fx[3]);
+                dxs[1] = make_float4(fx[4], fx[5], fx[6], fx[7]);
+            }
+            __syncthreads();
+#pragma unroll 4
+            for (int pp = 0; pp < kWgPix4; ++pp) {
+                const float4 z = *reinterpret_cast<const float4*>(&sz[pp][tco]);
+                const float4 v = *reinterpret_cast<const float4*>(&sx[pp][tci]);
+                const float zz[4] = {z.x, z.y, z.z, z.w}, xv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) acc[i][j] += zz[i] * xv[j];
+            }
+        }
+    }
+    const size_t K = size_t(9) * Cin;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            atomicAdd(&dw[size_t(cob * 32 + tco + i) * K + size_t(tap) * Cin + cib * 32 + tci + j], acc[i][j]);
+}
+
 // db[co] += sum_p dz[p][co]
 __global__ void k_bias_grad(size_t npx, int C, const __nv_bfloat16* __restrict__ dz, float* __restrict__ db,
                             size_t px_per_cta)
@@ -633,6 +711,18 @@ cudaError_t launch_wgrad3x3(int B, int H, int W, int Cin, int xstride, int Cout,
                             const __nv_bfloat16* dz, float* dw, cudaStream_t s)
 {
     if (Cout % 16 || Cin % 8 || xstride < Cin) return cudaErrorInvalidValue;
+    if (Cout % 32 == 0 && Cin % 32 == 0 && xstride % 8 == 0 &&
+        ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(dz)) & 15) == 0) {
+        const int tiles = 9 * (Cout / 32) * (Cin / 32);
+        const long rows = long(B) * H;
+        long splits = (152L * 16 + tiles - 1) / tiles;       // about 16 CTAs of 64 threads per SM
+        if (splits > rows) splits = rows;
+        if (splits < 1) splits = 1;
+        const int rpc = int((rows + splits - 1) / splits);
+        dim3 grid(unsigned(tiles), unsigned((rows + rpc - 1) / rpc));
+        k_wgrad3x3_r4<<<grid, 64, 0, s>>>(B, H, W, Cin, xstride, Cout, x, dz, dw, rpc);
+        return cudaGetLastError();
+    }
     if (Cout % 32 == 0) {
         if (Cin % 32 == 0) return wgrad_blocks<32, 32>(B, H, W, Cin, xstride, Cout, x, dz, dw, s);
         if (Cin % 16 == 0) return wgrad_blocks<32, 16>(B, H, W, Cin, xstride, Cout, x, dz, dw, s);
