@@ -75,9 +75,53 @@ def parse_args():
     p.add_argument("--net-forward", type=int, default=0, metavar="REPS",
                    help="only time the refinement network: REPS forwards of a batch of 4 plain-like "
                         "1280x720 inputs after 2 untimed ones (0: the full benchmark); for profiling")
+    p.add_argument("--net-train", type=int, default=0, metavar="STEPS",
+                   help="only time the refinement network's training: STEPS Adam steps on 8 random "
+                        "128x128 crops after 3 untimed ones (0: the full benchmark); for profiling")
     p.add_argument("--net-widths", default="32,64,128")
     p.add_argument("--net-e4m3", action="store_true", help="with --net-forward: quantise to E4M3 first")
     return p.parse_args()
+
+
+def net_train(args):
+    """Refinement network training steps alone (forward, loss, backward,
+    Adam) on random crops: for kernel profiles of the training step.  The
+    FLOP figure counts the 3x3 convolutions three times (forward, input
+    gradient, weight gradient)."""
+    import torch
+    import synthetic as S
+    from paper_2007_00558_gb300 import fvv as F
+    F.load()
+    widths = tuple(int(v) for v in args.net_widths.split(","))
+    B, H, W = 8, 128, 128
+    g = torch.Generator(device="cuda").manual_seed(0)
+    rgb = torch.randint(0, 256, (B, H, W, 3), dtype=torch.uint8, device="cuda", generator=g)
+    depth = torch.rand((B, H, W), device="cuda", generator=g) * 6000 + 500
+    hole = (torch.rand((B, H, W), device="cuda", generator=g) < 0.05).to(torch.uint8)
+    top3 = torch.rand((B, H, W, 3), device="cuda", generator=g)
+    target = torch.randint(0, 256, (B, H, W, 3), dtype=torch.uint8, device="cuda", generator=g)
+    ctx = F.fvv_create(F.rig(S.rig_parallel(1, 16, 16, 10.0, 0.1), [0, 0, 1]))
+    try:
+        F.fvv_refine_init(ctx, F.fvv_refine_default_cfg(seed=1, widths=widths))
+        fb = F.refine_batch(B, H, W, rgb, depth, hole, top3, target)
+        s = torch.cuda.Stream()
+        torch.cuda.set_stream(s)
+        for _ in range(3):
+            F.fvv_refine_train_step(ctx, fb, 1e-4, s)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        for _ in range(args.net_train):
+            F.fvv_refine_train_step(ctx, fb, 1e-4, s)
+        e1.record(s)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / max(1, args.net_train)
+        fl = 3 * unet_flops(H, W, widths) * B
+        print(json.dumps({"widths": list(widths), "batch": [B, H, W], "ms_per_step": ms,
+                          "tflops": fl / (ms * 1e-3) / 1e12}))
+    finally:
+        F.fvv_destroy(ctx)
+    return 0
 
 
 def net_forward(args):
@@ -1237,6 +1281,8 @@ def main():
         return run_reference(args)
     if args.net_forward:
         return net_forward(args)
+    if args.net_train:
+        return net_train(args)
     if args.jbf_only:
         import torch
         import synthetic as S

@@ -528,18 +528,33 @@ __global__ void __launch_bounds__(64) k_wgrad3x3_r4(int B, int H, int W, int Cin
 }
 
 // db[co] += sum_p dz[p][co]
-__global__ void k_bias_grad(size_t npx, int C, const __nv_bfloat16* __restrict__ dz, float* __restrict__ db,
-                            size_t px_per_cta)
+__global__ void __launch_bounds__(256) k_bias_grad(size_t npx, int C, const __nv_bfloat16* __restrict__ dz,
+                                                   float* __restrict__ db, size_t px_per_cta)
 {
-    const int c = threadIdx.x % C;
-    const int lanes = blockDim.x / C;
-    const int l = threadIdx.x / C;
-    if (l >= lanes) return;
+    // thread = (pixel lane l, 8-channel group g): 16-byte loads, 8 partial
+    // sums; the lanes are summed in shared memory, one atomic per channel
+    __shared__ float part[256 * 8];
+    const int G = C / 8, R = 256 / G;
+    const int g = threadIdx.x % G, l = threadIdx.x / G;
+    float a[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     const size_t p0 = size_t(blockIdx.x) * px_per_cta;
     const size_t p1 = p0 + px_per_cta < npx ? p0 + px_per_cta : npx;
-    float a = 0.0f;
-    for (size_t p = p0 + l; p < p1; p += lanes) a += bf(dz[p * C + c]);
-    atomicAdd(&db[c], a);
+    if (l < R) {
+        for (size_t p = p0 + l; p < p1; p += R) {
+            float f[8];
+            unpack8(*reinterpret_cast<const uint4*>(dz + p * C + 8 * g), f);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) a[j] += f[j];
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j) part[l * C + 8 * g + j] = a[j];
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < C; c += blockDim.x) {
+        float t = 0.0f;
+        for (int k = 0; k < R; ++k) t += part[k * C + c];
+        atomicAdd(&db[c], t);
+    }
 }
 
 // wt[ci][ky][kx][co] = w[co][2-ky][2-kx][ci] (bf16), the weights of the
@@ -735,7 +750,10 @@ cudaError_t launch_wgrad3x3(int B, int H, int W, int Cin, int xstride, int Cout,
 
 cudaError_t launch_bias_grad(size_t npx, int C, const __nv_bfloat16* dz, float* db, cudaStream_t s)
 {
-    const size_t per = 4096;
+    if (C % 8 || C > 2048 || (reinterpret_cast<uintptr_t>(dz) & 15)) return cudaErrorInvalidValue;
+    // about eight CTAs per SM, at least 256 pixels each
+    size_t per = (npx + 152 * 8 - 1) / (152 * 8);
+    if (per < 256) per = 256;
     k_bias_grad<<<blocks(npx, int(per)), 256, 0, s>>>(npx, C, dz, db, per);
     return cudaGetLastError();
 }
