@@ -900,8 +900,10 @@ cudaError_t dispatch(const void* x, const void* w, int Cout, const ConvArgs& a, 
     switch (Cout) {
     case 32:
         // the folded form pays where the MMAs outweigh the epilogue: two or
-        // more channel groups per tile
-        if (a.Cin > (FP8 ? 64 : 32)) return launch_conv<32, FP8, true>(x, w, a, s);
+        // more channel groups per tile.  It is kept to dense outputs without
+        // the fused head (the network's uses of it)
+        if (a.Cin > (FP8 ? 64 : 32) && !a.up2 && a.ldy == 32 && a.coff == 0 && !a.head_w)
+            return launch_conv<32, FP8, true>(x, w, a, s);
         return launch_conv<32, FP8>(x, w, a, s);
     case 48: return launch_conv<48, FP8>(x, w, a, s);
     case 64: return launch_conv<64, FP8>(x, w, a, s);
