@@ -5,10 +5,9 @@
  *
  * Build: gcc -O2 -std=c11 -ffp-contract=off -fno-fast-math -shared -fPIC.
  * FP32 expressions are written one rounded operation at a time, with the
- * evaluation order spelled out by parentheses; the compiler forms no fused
- * multiply-add of its own, and where a reading uses one it is an explicit
- * fmaf() (correctly rounded), so every FP32 result is the IEEE
- * round-to-nearest value of that exact sequence of operations.
+ * evaluation order spelled out by parentheses, and contraction into FMA is
+ * disabled, so every FP32 result is the IEEE round-to-nearest value of that
+ * exact sequence of operations.
  *
  * Readings of the paper (it gives the method in prose only):
  *   R1  units: lengths in depth units (mm); poses in metres, FP64 on the host.
@@ -16,10 +15,9 @@
  *       the point z * K_k^-1 (u, v, 1); it is mapped to the virtual camera by
  *       K_v [R_v R_k^T | t_v - R_v R_k^T t_k] and the 3x4 product is rounded
  *       to FP32 once (M_k).  The backward map N_k swaps the roles.
- *   R3  forward projection with fused multiply-adds (one rounding each):
- *       a = fma(m0, u, fma(m1, v, m2)); X = fma(a, z, m3), likewise Y, Z;
- *       reject !(Z > z_min); r = 1 / Z,
- *       u' = X r, v' = Y r; target pixel floor(u' + 0.5) (ties round up).
+ *   R3  forward projection (FMA-free):  a = ((m0 u + m1 v) + m2);
+ *       X = a z + m3, likewise Y, Z; reject !(Z > z_min); u' = X / Z,
+ *       v' = Y / Z; target pixel floor(u' + 0.5) (ties round up).
  *   R4  z-buffer: the smallest 64-bit key  bits(Z) << 32 | k << 26 | src
  *       wins; positive floats order like their bit patterns, so the key
  *       orders by depth, then camera, then source pixel.
@@ -225,17 +223,16 @@ void oracle_warp_splat(int n_cams, const or_camera* cams,
                     continue;
                 const float fu = (float)u;
                 const float z = (float)d;
-                float a0 = fmaf(m[0], fu, fmaf(m[1], fv, m[2]));
-                float a1 = fmaf(m[4], fu, fmaf(m[5], fv, m[6]));
-                float a2 = fmaf(m[8], fu, fmaf(m[9], fv, m[10]));
-                float X = fmaf(a0, z, m[3]);
-                float Y = fmaf(a1, z, m[7]);
-                float Z = fmaf(a2, z, m[11]);
+                float a0 = ((m[0] * fu) + (m[1] * fv)) + m[2];
+                float a1 = ((m[4] * fu) + (m[5] * fv)) + m[6];
+                float a2 = ((m[8] * fu) + (m[9] * fv)) + m[10];
+                float X = (a0 * z) + m[3];
+                float Y = (a1 * z) + m[7];
+                float Z = (a2 * z) + m[11];
                 if (!(Z > opt->z_min))
                     continue;
-                const float r = 1.0f / Z;
-                float up = X * r;
-                float vp = Y * r;
+                float up = X / Z;
+                float vp = Y / Z;
                 if (!isfinite(up) || !isfinite(vp))
                     continue;
                 float tu = floorf(up + 0.5f);
@@ -331,10 +328,9 @@ static float pixel_weight(const or_xform* xk, float x, float y, float Z)
 /* ------------------------------------------------------------------------
  * Step d (R6, R7).  The winning key gives depth Z, camera w and source pixel
  * s.  acc = w_w * rgb_w[s]; then each other active camera k, in ascending
- * order, back-projects (x, y, Z) with N_k (the same fused order as R3),
- * takes the nearest pixel, and contributes acc = fma(w_k, rgb_k, acc) there
- * when visible.
- * Output channel = min(255, floor(acc (1 / wsum) + 0.5)).  Aux: Z, hole flag,
+ * order, back-projects (x, y, Z) with N_k (same FMA-free order as R3), takes
+ * the nearest pixel, and contributes w_k * rgb_k there when visible.
+ * Output channel = min(255, floor(acc / wsum + 0.5)).  Aux: Z, hole flag,
  * the three largest normalised contributing weights (descending, ties by
  * lower camera index), number of contributing cameras.
  * ---------------------------------------------------------------------- */
@@ -377,17 +373,16 @@ void oracle_fetch_blend(int n_cams, const or_camera* cams,
                 if (k == w || !(xf[k].w > 0.0f))
                     continue;
                 const float* n = xf[k].N;
-                float a0 = fmaf(n[0], fx, fmaf(n[1], fy, n[2]));
-                float a1 = fmaf(n[4], fx, fmaf(n[5], fy, n[6]));
-                float a2 = fmaf(n[8], fx, fmaf(n[9], fy, n[10]));
-                float Xk = fmaf(a0, Z, n[3]);
-                float Yk = fmaf(a1, Z, n[7]);
-                float Zk = fmaf(a2, Z, n[11]);
+                float a0 = ((n[0] * fx) + (n[1] * fy)) + n[2];
+                float a1 = ((n[4] * fx) + (n[5] * fy)) + n[6];
+                float a2 = ((n[8] * fx) + (n[9] * fy)) + n[10];
+                float Xk = (a0 * Z) + n[3];
+                float Yk = (a1 * Z) + n[7];
+                float Zk = (a2 * Z) + n[11];
                 if (!(Zk > opt->z_min))
                     continue;
-                const float rk = 1.0f / Zk;
-                float up = Xk * rk;
-                float vp = Yk * rk;
+                float up = Xk / Zk;
+                float vp = Yk / Zk;
                 if (!isfinite(up) || !isfinite(vp))
                     continue;
                 float tu = floorf(up + 0.5f);
@@ -406,14 +401,13 @@ void oracle_fetch_blend(int n_cams, const or_camera* cams,
                 const uint8_t* ckp = rgb[k] + (size_t)vk * rgb_pitch[k] + 3 * (size_t)uk;
                 const float wk = opt->pixel_weights ? pixel_weight(&xf[k], fx, fy, Z) : xf[k].w;
                 for (int ch = 0; ch < 3; ++ch)
-                    acc[ch] = fmaf(wk, (float)ckp[ch], acc[ch]);
+                    acc[ch] = acc[ch] + wk * (float)ckp[ch];
                 wsum = wsum + wk;
                 cw[nc] = wk;
                 ck[nc++] = k;
             }
-            const float iw = 1.0f / wsum;
             for (int ch = 0; ch < 3; ++ch) {
-                float val = floorf(acc[ch] * iw + 0.5f);
+                float val = floorf(acc[ch] / wsum + 0.5f);
                 o[ch] = (uint8_t)(val > 255.0f ? 255.0f : val);
             }
             if (out_depth) out_depth[p] = Z;
@@ -431,7 +425,7 @@ void oracle_fetch_blend(int n_cams, const or_camera* cams,
                         out_top3[3 * p + r] = 0.0f;
                     } else {
                         used[best] = 1;
-                        out_top3[3 * p + r] = cw[best] * iw;
+                        out_top3[3 * p + r] = cw[best] / wsum;
                     }
                 }
             }
