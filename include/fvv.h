@@ -91,7 +91,7 @@ typedef struct fvv_options {
     int32_t hole_fill;          /* 1 = apply step (e) */
     float tau_crack;            /* (c) relative depth tolerance, default 0.05 */
     float tau_vis;              /* (d) visibility tolerance |d - Z| <= tau_vis Z, default 0.03 */
-    float z_min;                /* smallest accepted projected depth (depth units), default 1 */
+    float z_min;                /* smallest accepted projected depth (depth units), >= 0, default 1 */
     uint32_t d_lo, d_hi;        /* accepted depth codes, default [1, 65534] (d_hi <= 65534:
                                    FVV_DEPTH_BG is never a depth) */
     int32_t frame_slots;        /* device-resident frame ticks kept (ring), default 2 */

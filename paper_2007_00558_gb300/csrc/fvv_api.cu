@@ -101,7 +101,8 @@ bool options_ok(const fvv_options& o, int n_cams, std::string* why)
     if (o.n_ref < 0 || o.n_ref > n_cams) { *why = "n_ref must be in [0, n_cams]"; return false; }
     if (!(o.tau_crack >= 0.0f) || !std::isfinite(o.tau_crack)) { *why = "tau_crack must be >= 0"; return false; }
     if (!(o.tau_vis >= 0.0f) || !std::isfinite(o.tau_vis)) { *why = "tau_vis must be >= 0"; return false; }
-    if (!std::isfinite(o.z_min)) { *why = "z_min must be finite"; return false; }
+    // Z > z_min >= 0 keeps every projected depth positive, so X / Z is never NaN
+    if (!(o.z_min >= 0.0f) || !std::isfinite(o.z_min)) { *why = "z_min must be finite and >= 0"; return false; }
     if (o.d_lo < 1 || o.d_hi > 65534 || o.d_lo > o.d_hi) {
         *why = "need 1 <= d_lo <= d_hi <= 65534 (65535 is the background signal)";
         return false;

@@ -20,10 +20,10 @@
 // template parameter, so the single-layer form carries none of it.
 //
 // Every FP32 operation of the warp, the filter and the blend is an explicit
-// round-to-nearest intrinsic (__fmul_rn / __fadd_rn / __fsub_rn / __fmaf_rn /
-// __frcp_rn) in a fixed order -- a fused multiply-add only where the
-// operation sequence has one -- so the results are exactly the IEEE values of
-// that sequence.
+// round-to-nearest intrinsic (__fmul_rn / __fadd_rn / __fsub_rn / __fdiv_rn)
+// in a fixed, FMA-free order -- each product and each sum rounded once, each
+// quotient a correctly rounded division -- so the results are exactly the
+// IEEE values of that sequence.
 #include <climits>
 
 #include "fvv_internal.h"
@@ -216,8 +216,8 @@ k_warp_splat(const ViewDesc* __restrict__ views, const FrameRef* __restrict__ fr
         const float m4 = m[4], m6 = m[6], m7 = m[7];
         const float m8 = m[8], m10 = m[10], m11 = m[11];
         const float fv = u23_to_float(uint32_t(v));
-        // per-row terms fma(m1, v, m2), likewise for Y and Z
-        const float r0 = __fmaf_rn(m[1], fv, m2), r1 = __fmaf_rn(m[5], fv, m6), r2 = __fmaf_rn(m[9], fv, m10);
+        // per-row products m1 v, m5 v, m9 v (the order stays ((m0 u + m1 v) + m2))
+        const float r0 = __fmul_rn(m[1], fv), r1 = __fmul_rn(m[5], fv), r2 = __fmul_rn(m[9], fv);
         const unsigned long long khi = static_cast<unsigned long long>(k) << kSrcBits;
         const uint32_t src0 = uint32_t(v) * uint32_t(F.W) + uint32_t(u0 + lane);
         const float fu0 = u23_to_float(uint32_t(u0 + lane));
@@ -229,15 +229,14 @@ k_warp_splat(const ViewDesc* __restrict__ views, const FrameRef* __restrict__ fr
             const uint32_t dd = d[j];
             const float fu = __fadd_rn(fu0, float(32 * j));  // exact: small integers
             const float z = u23_to_float(dd);
-            const float a0 = __fmaf_rn(m0, fu, r0);
-            const float a1 = __fmaf_rn(m4, fu, r1);
-            const float a2 = __fmaf_rn(m8, fu, r2);
-            const float X = __fmaf_rn(a0, z, m3);
-            const float Y = __fmaf_rn(a1, z, m7);
-            const float Z = __fmaf_rn(a2, z, m11);
-            const float r = __frcp_rn(Z);          // 1 / Z, correctly rounded
-            const float tu = floorf(__fadd_rn(__fmul_rn(X, r), 0.5f));
-            const float tv = floorf(__fadd_rn(__fmul_rn(Y, r), 0.5f));
+            const float a0 = __fadd_rn(__fadd_rn(__fmul_rn(m0, fu), r0), m2);
+            const float a1 = __fadd_rn(__fadd_rn(__fmul_rn(m4, fu), r1), m6);
+            const float a2 = __fadd_rn(__fadd_rn(__fmul_rn(m8, fu), r2), m10);
+            const float X = __fadd_rn(__fmul_rn(a0, z), m3);
+            const float Y = __fadd_rn(__fmul_rn(a1, z), m7);
+            const float Z = __fadd_rn(__fmul_rn(a2, z), m11);
+            const float tu = floorf(__fadd_rn(__fdiv_rn(X, Z), 0.5f));
+            const float tv = floorf(__fadd_rn(__fdiv_rn(Y, Z), 0.5f));
             // the bounds test also rejects NaN and +-inf, as a finiteness test would
             // dd in [dlo, dhi] (dlo >= 1, so a code of 0 wraps above the span)
             const bool ok = dd - dlo <= dspan && Z > zmin && tu >= 0.0f && tu <= maxu && tv >= 0.0f &&
@@ -332,9 +331,9 @@ __device__ __forceinline__ bool w_before(float wa, int ka, float wb, int kb)
     return wa > wb || (wa == wb && ka < kb);
 }
 
-__device__ __forceinline__ uint32_t blend_channel(float acc, float iw)    // iw = 1 / wsum
+__device__ __forceinline__ uint32_t blend_channel(float acc, float wsum)
 {
-    float v = floorf(__fadd_rn(__fmul_rn(acc, iw), 0.5f));
+    float v = floorf(__fadd_rn(__fdiv_rn(acc, wsum), 0.5f));
     v = v > 255.0f ? 255.0f : v;
     return uint32_t(v);
 }
@@ -488,11 +487,11 @@ k_resolve(const ViewDesc* __restrict__ views, const FrameRef* __restrict__ frame
         if (y + 1 < y1)
             fetch_row(y + 2);
         cp_async_commit();
-        // per-row terms fma(N1, y, N2), fma(N5, y, N6), fma(N9, y, N10)
+        // per-row products N1 y, N5 y, N9 y (the order stays ((N0 x + N1 y) + N2))
         const float fy = u23_to_float(uint32_t(y));
         for (int i = tid; i < nc * 3; i += NT) {
             const int k = i / 3, j = i - k * 3;
-            s_rowt[4 * k + j] = __fmaf_rn(s_geom[kGeomFloats * k + 1 + 4 * j], fy, s_geom[kGeomFloats * k + 2 + 4 * j]);
+            s_rowt[4 * k + j] = __fmul_rn(s_geom[kGeomFloats * k + 1 + 4 * j], fy);
         }
         cp_async_wait<1>();                   // rows y-1 .. y+1 have landed
         __syncthreads();
@@ -572,15 +571,14 @@ k_resolve(const ViewDesc* __restrict__ views, const FrameRef* __restrict__ frame
                     const float4 A = g4[5 * k + 0], Bq = g4[5 * k + 1], Cq = g4[5 * k + 2],
                                  Eq = g4[5 * k + 4];
                     const float4 Rt = reinterpret_cast<const float4*>(s_rowt)[k];
-                    const float a0 = __fmaf_rn(A.x, fx, Rt.x);
-                    const float a1 = __fmaf_rn(Bq.x, fx, Rt.y);
-                    const float a2 = __fmaf_rn(Cq.x, fx, Rt.z);
-                    const float Xk = __fmaf_rn(a0, Z, A.w);
-                    const float Yk = __fmaf_rn(a1, Z, Bq.w);
-                    const float Zk = __fmaf_rn(a2, Z, Cq.w);
-                    const float rk = __frcp_rn(Zk);
-                    const float tu = floorf(__fadd_rn(__fmul_rn(Xk, rk), 0.5f));
-                    const float tv = floorf(__fadd_rn(__fmul_rn(Yk, rk), 0.5f));
+                    const float a0 = __fadd_rn(__fadd_rn(__fmul_rn(A.x, fx), Rt.x), A.z);
+                    const float a1 = __fadd_rn(__fadd_rn(__fmul_rn(Bq.x, fx), Rt.y), Bq.z);
+                    const float a2 = __fadd_rn(__fadd_rn(__fmul_rn(Cq.x, fx), Rt.z), Cq.z);
+                    const float Xk = __fadd_rn(__fmul_rn(a0, Z), A.w);
+                    const float Yk = __fadd_rn(__fmul_rn(a1, Z), Bq.w);
+                    const float Zk = __fadd_rn(__fmul_rn(a2, Z), Cq.w);
+                    const float tu = floorf(__fadd_rn(__fdiv_rn(Xk, Zk), 0.5f));
+                    const float tv = floorf(__fadd_rn(__fdiv_rn(Yk, Zk), 0.5f));
                     // the bounds test also rejects NaN and +-inf, as a finiteness test would
                     ok[j] = g0 + j < nother && Zk > zmin && tu >= 0.0f && tu <= Eq.x &&
                             tv >= 0.0f && tv <= Eq.y;
@@ -619,9 +617,9 @@ k_resolve(const ViewDesc* __restrict__ views, const FrameRef* __restrict__ frame
                     const int k = kk[j];
                     const float wk = weight_of(k);
                     const uint32_t c = ck[j];
-                    acc0 = __fmaf_rn(wk, u23_to_float(c & 255u), acc0);
-                    acc1 = __fmaf_rn(wk, u23_to_float((c >> 8) & 255u), acc1);
-                    acc2 = __fmaf_rn(wk, u23_to_float((c >> 16) & 255u), acc2);
+                    acc0 = __fadd_rn(acc0, __fmul_rn(wk, u23_to_float(c & 255u)));
+                    acc1 = __fadd_rn(acc1, __fmul_rn(wk, u23_to_float((c >> 8) & 255u)));
+                    acc2 = __fadd_rn(acc2, __fmul_rn(wk, u23_to_float((c >> 16) & 255u)));
                     wsum = __fadd_rn(wsum, wk);
                     if (kTop3) {
                         if (w_before(wk, k, t0, k0)) {
@@ -634,14 +632,13 @@ k_resolve(const ViewDesc* __restrict__ views, const FrameRef* __restrict__ frame
                     }
                 }
             }
-            const float iw = __frcp_rn(wsum);
-            s_rgb[x] = blend_channel(acc0, iw) | (blend_channel(acc1, iw) << 8) | (blend_channel(acc2, iw) << 16);
+            s_rgb[x] = blend_channel(acc0, wsum) | (blend_channel(acc1, wsum) << 8) | (blend_channel(acc2, wsum) << 16);
             s_dep[x] = Z;
             s_hole[x] = 0;
             if (kTop3 && top3) {
-                top3[3 * (rowbase + x) + 0] = __fmul_rn(t0, iw);
-                top3[3 * (rowbase + x) + 1] = t1 >= 0.0f ? __fmul_rn(t1, iw) : 0.0f;
-                top3[3 * (rowbase + x) + 2] = t2 >= 0.0f ? __fmul_rn(t2, iw) : 0.0f;
+                top3[3 * (rowbase + x) + 0] = __fdiv_rn(t0, wsum);
+                top3[3 * (rowbase + x) + 1] = t1 >= 0.0f ? __fdiv_rn(t1, wsum) : 0.0f;
+                top3[3 * (rowbase + x) + 2] = t2 >= 0.0f ? __fdiv_rn(t2, wsum) : 0.0f;
             }
         }
         // (e) hole fill: nearest non-hole left / right, the deeper one wins

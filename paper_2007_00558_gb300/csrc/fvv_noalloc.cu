@@ -109,7 +109,7 @@ extern "C" fvv_status fvv_synthesize_noalloc(const fvv_rig* rig, const fvv_optio
         return fail(FVV_ERR_INVALID_ARG,
                     "fvv_synthesize_noalloc: layered synthesis needs a context (fvv_set_bg_depth)");
     if (o.n_ref < 0 || o.n_ref > rig->n_cams || o.d_lo < 1 || o.d_hi > 65534 || o.d_lo > o.d_hi ||
-        !(o.tau_crack >= 0.0f) || !(o.tau_vis >= 0.0f) || !std::isfinite(o.z_min))
+        !(o.tau_crack >= 0.0f) || !(o.tau_vis >= 0.0f) || !(o.z_min >= 0.0f) || !std::isfinite(o.z_min))
         return fail(FVV_ERR_INVALID_ARG, "fvv_synthesize_noalloc: invalid options");
     if (!camera_sane(*view))
         return fail(FVV_ERR_INVALID_ARG, "fvv_synthesize_noalloc: invalid view camera");
