@@ -209,6 +209,28 @@ def _worker_for(seconds, start):
     return n, time.perf_counter() - t0
 
 
+def oracle_single_thread_rates(wl, seconds=4.0):
+    """The oracle in this process, one thread: views/s on the 9-camera
+    1280x720 swing and on the 2-camera 320x240 midway view."""
+    import oracle
+    import synthetic as S
+    oracle.build()
+    out = {}
+    for key, w in (("single_thread", wl), ("config_2cam_320x240_single_thread", S.workload("plain_2cam_320x240"))):
+        views = w["views"]
+        t0 = time.perf_counter()
+        n = 0
+        while True:
+            oracle.synthesize(w["cams"], w["rgb"], w["depth"], views[n % len(views)], w["look_at"])
+            n += 1
+            el = time.perf_counter() - t0
+            if el >= seconds / 2:
+                break
+        out[key] = {"value": n / el, "unit": UNIT, "cores": 1,
+                    "sample": "%d views in %.2f s, one thread" % (n, el)}
+    return out
+
+
 class OraclePool:
     """Spawned worker processes, each running the single-threaded C oracle
     on frames shared through POSIX shared memory."""
@@ -1236,6 +1258,7 @@ def run_fvv(args):
         cpu = {"value": n / wall, "unit": UNIT, "cores": pool.procs, "kind": "oracle",
                "sample": "%d views of the 9-camera 1280x720 swing in %.1f s on %d worker processes "
                          "(one single-threaded oracle each)" % (n, wall, pool.procs)}
+        cpu.update(oracle_single_thread_rates(wl, seconds=min(4.0, args.cpu_seconds)))
 
     if roofline is not None:
         clk = clocks.summary() or {}

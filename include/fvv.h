@@ -556,6 +556,9 @@ fvv_status fvv_synthesize_refined(fvv_ctx* ctx, const fvv_view* view, uint8_t* o
  *                   bytes (even), 0 = no depth
  *   rgba[k]:        camera k's colour, one uint32 per pixel R | G << 8 | B << 16,
  *                   rows of pitch rgba_pitch[k] bytes (multiple of 4)
+ *                   (each pitch in elements, p, must keep (H - 1) * p + W
+ *                   below 2^32; depth, rgba and out_rgb must be memory of
+ *                   the current device)
  *   view:           the virtual camera, width * height <= FVV_NOALLOC_MAX_PIXELS
  *   out_rgb:        height rows of 3 * width bytes, row pitch out_pitch
  *   stream:         cudaStream_t as void* (NULL = the legacy default stream);
@@ -565,7 +568,9 @@ fvv_status fvv_synthesize_refined(fvv_ctx* ctx, const fvv_view* view, uint8_t* o
  * loads the library holds until the process exits.  Larger views are rejected
  * with FVV_ERR_INVALID_ARG.  The first call on a device looks up the device
  * address of that scratch (cudaGetSymbolAddress) with the device current;
- * make that first call before any stream capture.  Every call shares the
+ * make that first call before any stream capture.  The address is kept for
+ * the life of the process, so a device reset (cudaDeviceReset) after the
+ * first call is not supported.  Every call shares the
  * scratch and it keeps the last call's contents (the keys are reset at the
  * start of each call): calls whose GPU work overlaps, e.g. on two unordered
  * streams, race -- order them on one stream.  On success nothing is

@@ -15,7 +15,7 @@ constexpr uint16_t kDepthBg = 65535;   // depth code of a background pixel
 constexpr int kSplatSeg = 256;       // source pixels per splat warp (8 per lane, stride 32)
 constexpr int kSplatThreads = 256;
 constexpr int kResolveThreads = 256;
-constexpr int kResolveBand = 4;      // output rows per resolve CTA
+constexpr int kResolveBand = 2;      // output rows per resolve CTA
 
 constexpr int kFlagCrack = 1;
 constexpr int kFlagFill = 2;
@@ -80,6 +80,8 @@ cudaError_t launch_resolve(const ViewDesc* views, int n_views, int max_h, int ma
 cudaError_t launch_pack_rgba(const uint8_t* rgb, size_t rgb_pitch, uint32_t* rgba,
                              int rpitch, int W, int H, cudaStream_t stream);
 size_t resolve_smem_bytes(int max_w, int n_cams, bool layered = false);
+// The current device's streaming-multiprocessor count (1 if it cannot be read).
+int device_sms();
 
 }  // namespace fvv
 

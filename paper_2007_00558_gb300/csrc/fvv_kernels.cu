@@ -9,7 +9,7 @@
 //   k_clear_keys   reset the per-view z-buffers to the empty key
 //   k_warp_splat   (a) forward warp + (b) 64-bit atomicMin z-buffer splat
 //   k_resolve      (c) crack filter + (d) backward fetch and blend +
-//                  (e) row hole fill, fused: one CTA per output row
+//                  (e) row hole fill, fused: one CTA per band of output rows
 //   k_pack_rgba    upload: RGB8 rows -> RGBA8 (one aligned 32-bit gather per texel)
 //
 // Layered form (Sec. VI, per-camera FG and BG layers): a pixel signalled BG
@@ -25,6 +25,7 @@
 // quotient a correctly rounded division -- so the results are exactly the
 // IEEE values of that sequence.
 #include <climits>
+#include <cstdlib>
 
 #include "fvv_internal.h"
 
@@ -34,28 +35,50 @@ namespace {
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 
-constexpr int kGeomFloats = 20;   // per-camera record of the resolve kernel
 constexpr int kRing = 4;          // key rows kept in shared memory (3 in use + 1 in flight)
+constexpr int kGroup = 8;         // back-projections issued together per pixel
+
+// Per active camera of a view, staged in the resolve kernel's shared memory
+// and indexed by the camera's position in the view's active list.  The first
+// 80 bytes are what every back-projection reads.
+struct alignas(16) RCam {
+    float4 gx;                 // N0, N2, N3, N1 y   (the row product, rewritten per row)
+    float4 gy;                 // N4, N6, N7, N5 y
+    float4 gz;                 // N8, N10, N11, N9 y
+    const uint16_t* depth;     // the camera's frame in the view's slot
+    const uint32_t* rgba;
+    int32_t dpitch, rpitch;    // elements
+    uint32_t maxu, maxv;       // W - 1, H - 1
+    float w;                   // per-view blend weight
+    int32_t k;                 // camera index
+    uint32_t magic, shift;     // s / W == (s * magic) >> shift for every s < 2^26
+    const uint16_t* bg;        // layered: the static BG depth model, or NULL
+    float unused[2];
+    float4 rowc;               // N1, N5, N9 (coefficients of the row products)
+    float4 cen;                // the camera's centre in the view's frame (per-pixel weights)
+};
+static_assert(sizeof(RCam) == 144, "RCam layout");
 
 struct SmemLayout {
-    size_t ring, rgb, dep, hole, geom, rowt, frames, active, pos, scan, total;
+    size_t ring, rgb, dep, hole, cams, pos, scan, total;
 };
+
+// Key rows carry one EMPTY sentinel on each side (Wv + 2 entries), so the
+// crack filter reads x - 1 and x + 1 without bounds tests.
+__host__ __device__ inline size_t ring_pitch(int W) { return size_t(W) + 2; }
 
 __host__ __device__ inline SmemLayout resolve_layout(int W, int n_cams, bool layered)
 {
     SmemLayout L;
     size_t o = 0;
     (void)layered;                // the layered form reads its BG keys from the filtered z-buffer
-    L.ring = o;   o = align16(o + size_t(kRing) * W * sizeof(unsigned long long));
+    L.ring = o;   o = align16(o + size_t(kRing) * ring_pitch(W) * sizeof(unsigned long long));
     L.rgb = o;    o = align16(o + size_t(W) * 4);
     L.dep = o;    o = align16(o + size_t(W) * 4);
     L.hole = o;   o = align16(o + size_t(W));
     // (the hole fill's nearest-left / nearest-right indices live in the key
     // ring's slot of the row above, which no pixel reads any more by then)
-    L.geom = o;   o = align16(o + size_t(n_cams) * kGeomFloats * sizeof(float));
-    L.rowt = o;   o = align16(o + size_t(n_cams) * 4 * sizeof(float));
-    L.frames = o; o = align16(o + size_t(n_cams) * sizeof(FrameRef));
-    L.active = o; o = align16(o + size_t(kMaxCams) * sizeof(int));
+    L.cams = o;   o = align16(o + size_t(n_cams) * sizeof(RCam));
     L.pos = o;    o = align16(o + size_t(kMaxCams) * sizeof(int));
     L.scan = o;   o = align16(o + 64 * sizeof(int));
     L.total = o;
@@ -65,6 +88,11 @@ __host__ __device__ inline SmemLayout resolve_layout(int W, int n_cams, bool lay
 __device__ __forceinline__ float key_z(unsigned long long k)
 {
     return __uint_as_float(static_cast<uint32_t>(k >> 32));
+}
+
+__device__ __forceinline__ uint32_t key_zbits(unsigned long long k)
+{
+    return static_cast<uint32_t>(k >> 32);
 }
 
 }  // namespace
@@ -111,7 +139,7 @@ __device__ __forceinline__ void red_min_key(unsigned long long* ptr, unsigned lo
                  : "memory");
 }
 
-// streaming 2-byte load (read once)
+// streaming loads (read once)
 __device__ __forceinline__ uint32_t ld_stream_u16(const uint16_t* ptr, uint64_t pol)
 {
     unsigned short v;
@@ -120,49 +148,79 @@ __device__ __forceinline__ uint32_t ld_stream_u16(const uint16_t* ptr, uint64_t 
     return v;
 }
 
-// Exact integer <-> float conversions on the FP32/ALU pipes: for 0 <= d < 2^23,
+__device__ __forceinline__ uint4 ld_stream_v4(const void* ptr, uint64_t pol)
+{
+    uint4 v;
+    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(ptr), "l"(pol));
+    return v;
+}
+
+// Exact integer -> float conversion on the FP32/ALU pipes: for 0 <= d < 2^23,
 // 2^23 + d is exactly representable and its low mantissa bits are d.
 __device__ __forceinline__ float u23_to_float(uint32_t d)
 {
     return __fsub_rn(__uint_as_float(0x4B000000u | d), 8388608.0f);
 }
 
-__device__ __forceinline__ uint32_t float_to_u23(float f)   // f integral, 0 <= f < 2^23
+// R3's target pixel of a projected point: u' = X / Z and v' = Y / Z by
+// correctly rounded division, then floor(u' + 0.5) (ties up), and the bounds
+// test 0 <= t <= max as one unsigned compare per axis.  The float -> int
+// floor saturates, so +-inf and out-of-range values fail the test as in the
+// FP32 form; Z > z_min >= 0 (validated on the host) and a finite X, Y rule
+// out NaN.
+__device__ __forceinline__ bool target_pixel(float X, float Y, float Z, uint32_t maxu, uint32_t maxv,
+                                             uint32_t& ui, uint32_t& vi)
 {
-    return __float_as_uint(__fadd_rn(f, 8388608.0f)) & 0x7FFFFFu;
+    ui = static_cast<uint32_t>(__float2int_rd(__fadd_rn(__fdiv_rn(X, Z), 0.5f)));
+    vi = static_cast<uint32_t>(__float2int_rd(__fadd_rn(__fdiv_rn(Y, Z), 0.5f)));
+    return ui <= maxu && vi <= maxv;
 }
 
 // ---------------------------------------------------------------------------
 // (a) + (b): forward warp and z-buffer splat.
 // One warp = one segment of kSplatSeg consecutive source pixels of one row
-// of one active camera; lane l takes pixels l, l + 32, l + 64, ... so every
-// warp-wide load and atomic touches 32 consecutive source pixels, whose
-// targets are neighbours in the view (few L2 sectors per atomic).  Segments
-// of a view are numbered camera-major over the active cameras:
-// chunk_begin[a] .. chunk_begin[a+1).  Each CTA belongs to one view and
-// stages its maps and frame table in shared memory.
+// of one active camera.  kVec = false: lane l takes pixels l, l + 32, ...
+// (2-byte loads), so every warp-wide atomic touches 32 consecutive source
+// pixels, whose targets are neighbours in the view (few L2 sectors per
+// atomic).  kVec = true: lane l takes the 8 consecutive pixels 8l .. 8l+7
+// with one 16-byte load.  Segments of a view are numbered camera-major over
+// the active cameras: chunk_begin[a] .. chunk_begin[a+1).  Each CTA belongs
+// to one view and stages its maps and frame table in shared memory.
 // ---------------------------------------------------------------------------
-template <bool kLayered>
+template <bool kLayered, bool kVec>
 __global__ void __launch_bounds__(kSplatThreads, 5)
 k_warp_splat(const ViewDesc* __restrict__ views, const FrameRef* __restrict__ frames)
 {
-    __shared__ __align__(16) float s_M[kMaxCams][12];
+    // per active camera: (m0, m2, m3, m1), (m4, m6, m7, m5), (m8, m10, m11, m9)
+    __shared__ __align__(16) float4 s_M[kMaxCams][3];
     __shared__ __align__(16) FrameRef s_F[kMaxCams];
     __shared__ int s_cb[kMaxCams + 1];
     __shared__ int s_act[kMaxCams];
+    __shared__ uint2 s_div[kMaxCams];              // segment -> row: (magic, shift) of segments per row
     constexpr int kWarps = kSplatThreads / 32;
+    constexpr int kPer = kSplatSeg / 32;           // pixels per lane per segment
+    static_assert(kPer == 8, "a 16-byte load holds 8 depth codes");
     const ViewDesc* V = views + blockIdx.y;
     const int na = V->n_active;
     const int first = blockIdx.x * kWarps;
     if (first >= V->chunk_begin[na])
         return;                                   // uniform over the CTA
-    for (int i = threadIdx.x; i < na * 12; i += kSplatThreads) {
-        const int a = i / 12;
-        s_M[a][i - a * 12] = V->geom[V->active[a]].M[i - a * 12];
+    for (int i = threadIdx.x; i < na * 3; i += kSplatThreads) {
+        const int a = i / 3, r = i - a * 3;
+        const float* m = V->geom[V->active[a]].M + 4 * r;
+        s_M[a][r] = make_float4(m[0], m[2], m[3], m[1]);
     }
     for (int i = threadIdx.x; i < na; i += kSplatThreads) {
         s_act[i] = V->active[i];
-        s_F[i] = frames[V->slot * V->n_cams + V->active[i]];
+        const FrameRef F = frames[V->slot * V->n_cams + V->active[i]];
+        s_F[i] = F;
+        // local / spr for local < 2^26 as (local * magic) >> shift, with
+        // shift = 26 + ceil(log2 spr) and magic = ceil(2^shift / spr): the
+        // excess local * e / 2^shift stays below 1 / spr
+        const uint32_t spr = uint32_t((F.W + kSplatSeg - 1) / kSplatSeg);
+        const uint32_t lg = spr > 1 ? 32u - uint32_t(__clz(spr - 1)) : 0u;
+        s_div[i] = make_uint2(uint32_t(((1ull << (26u + lg)) + spr - 1) / spr), 26u + lg);
     }
     for (int i = threadIdx.x; i <= na; i += kSplatThreads)
         s_cb[i] = V->chunk_begin[i];
@@ -173,30 +231,48 @@ k_warp_splat(const ViewDesc* __restrict__ views, const FrameRef* __restrict__ fr
     const float zmin = V->z_min;
     const uint32_t dlo = V->d_lo, dspan = V->d_hi - V->d_lo;
     const uint32_t Wv = uint32_t(V->Wv);
-    const float maxu = u23_to_float(Wv - 1), maxv = u23_to_float(uint32_t(V->Hv - 1));
+    const uint32_t maxu = Wv - 1, maxv = uint32_t(V->Hv - 1);
     unsigned long long* __restrict__ keys = V->keys;
     unsigned long long* __restrict__ keys_bg = V->keys_bg;
     const uint64_t pol_stream = policy_evict_first();
     const uint64_t pol_keys = policy_evict_last();
 
-    // persistent warps: segment seg, seg + stride, ... of this view
+    // persistent warps: segment seg, seg + stride, ... of this view; the
+    // segments grow, so the camera search resumes where it stopped
+    int a = 0;
     for (int seg = first + int(threadIdx.x >> 5); seg < total; seg += gridDim.x * kWarps) {
-        int a = 0;
         while (seg >= s_cb[a + 1])
             ++a;
         const int k = s_act[a];
         const FrameRef& F = s_F[a];
         const int spr = (F.W + kSplatSeg - 1) / kSplatSeg;
-        const int local = seg - s_cb[a];
-        const int v = local / spr;
-        const int u0 = (local - v * spr) * kSplatSeg;
+        const uint32_t local = uint32_t(seg - s_cb[a]);
+        const uint2 dv = s_div[a];
+        const int v = int((static_cast<unsigned long long>(local) * dv.x) >> dv.y);
+        const int u0 = (int(local) - v * spr) * kSplatSeg;
         const uint16_t* row = F.depth + size_t(v) * F.dpitch;
+        // the lane's first pixel and the step between its pixels
+        const int ub = u0 + (kVec ? kPer * lane : lane);
+        constexpr int kStep = kVec ? 1 : 32;
 
-        uint32_t d[kSplatSeg / 32];
+        uint32_t d[kPer];
+        // 16-byte loads need 16-byte aligned rows; a vector lies wholly
+        // inside or wholly past the row's pitch (pitch and ub multiples of 8)
+        if (kVec && (F.dpitch & 7) == 0 && (reinterpret_cast<uintptr_t>(F.depth) & 15u) == 0) {
+            uint4 q = make_uint4(0u, 0u, 0u, 0u);
+            if (ub < F.dpitch)
+                q = ld_stream_v4(row + ub, pol_stream);
+            d[0] = q.x & 0xFFFFu; d[1] = q.x >> 16; d[2] = q.y & 0xFFFFu; d[3] = q.y >> 16;
+            d[4] = q.z & 0xFFFFu; d[5] = q.z >> 16; d[6] = q.w & 0xFFFFu; d[7] = q.w >> 16;
 #pragma unroll
-        for (int j = 0; j < kSplatSeg / 32; ++j) {
-            const int u = u0 + lane + 32 * j;
-            d[j] = u < F.W ? ld_stream_u16(row + u, pol_stream) : 0u;
+            for (int j = 0; j < kPer; ++j)
+                if (ub + j >= F.W) d[j] = 0u;
+        } else {
+#pragma unroll
+            for (int j = 0; j < kPer; ++j) {
+                const int u = ub + kStep * j;
+                d[j] = u < F.W ? ld_stream_u16(row + u, pol_stream) : 0u;
+            }
         }
         // layered: a BG-signalled pixel takes its depth from the model and
         // splats into the BG layer (bit j of bgm)
@@ -204,50 +280,43 @@ k_warp_splat(const ViewDesc* __restrict__ views, const FrameRef* __restrict__ fr
         if (kLayered) {
             const uint16_t* brow = F.bg ? F.bg + size_t(v) * F.dpitch : nullptr;
 #pragma unroll
-            for (int j = 0; j < kSplatSeg / 32; ++j)
+            for (int j = 0; j < kPer; ++j)
                 if (d[j] == kDepthBg) {
-                    d[j] = brow ? ld_stream_u16(brow + u0 + lane + 32 * j, pol_stream) : 0u;
+                    d[j] = brow ? ld_stream_u16(brow + ub + kStep * j, pol_stream) : 0u;
                     bgm |= 1u << j;
                 }
         }
 
-        const float* m = s_M[a];
-        const float m0 = m[0], m2 = m[2], m3 = m[3];
-        const float m4 = m[4], m6 = m[6], m7 = m[7];
-        const float m8 = m[8], m10 = m[10], m11 = m[11];
+        const float4 Mx = s_M[a][0], My = s_M[a][1], Mz = s_M[a][2];
         const float fv = u23_to_float(uint32_t(v));
         // per-row products m1 v, m5 v, m9 v (the order stays ((m0 u + m1 v) + m2))
-        const float r0 = __fmul_rn(m[1], fv), r1 = __fmul_rn(m[5], fv), r2 = __fmul_rn(m[9], fv);
+        const float rx = __fmul_rn(Mx.w, fv), ry = __fmul_rn(My.w, fv), rz = __fmul_rn(Mz.w, fv);
         const unsigned long long khi = static_cast<unsigned long long>(k) << kSrcBits;
-        const uint32_t src0 = uint32_t(v) * uint32_t(F.W) + uint32_t(u0 + lane);
-        const float fu0 = u23_to_float(uint32_t(u0 + lane));
+        const uint32_t src0 = uint32_t(v) * uint32_t(F.W) + uint32_t(ub);
+        const float fu0 = u23_to_float(uint32_t(ub));
 
         // branch-free per point (only the atomic is predicated), so the eight
         // independent projections and divisions of a lane can interleave
 #pragma unroll
-        for (int j = 0; j < kSplatSeg / 32; ++j) {
+        for (int j = 0; j < kPer; ++j) {
             const uint32_t dd = d[j];
-            const float fu = __fadd_rn(fu0, float(32 * j));  // exact: small integers
+            const float fu = __fadd_rn(fu0, float(kStep * j));   // exact: small integers
             const float z = u23_to_float(dd);
-            const float a0 = __fadd_rn(__fadd_rn(__fmul_rn(m0, fu), r0), m2);
-            const float a1 = __fadd_rn(__fadd_rn(__fmul_rn(m4, fu), r1), m6);
-            const float a2 = __fadd_rn(__fadd_rn(__fmul_rn(m8, fu), r2), m10);
-            const float X = __fadd_rn(__fmul_rn(a0, z), m3);
-            const float Y = __fadd_rn(__fmul_rn(a1, z), m7);
-            const float Z = __fadd_rn(__fmul_rn(a2, z), m11);
-            const float tu = floorf(__fadd_rn(__fdiv_rn(X, Z), 0.5f));
-            const float tv = floorf(__fadd_rn(__fdiv_rn(Y, Z), 0.5f));
-            // the bounds test also rejects NaN and +-inf, as a finiteness test would
+            const float a0 = __fadd_rn(__fadd_rn(__fmul_rn(Mx.x, fu), rx), Mx.y);
+            const float a1 = __fadd_rn(__fadd_rn(__fmul_rn(My.x, fu), ry), My.y);
+            const float a2 = __fadd_rn(__fadd_rn(__fmul_rn(Mz.x, fu), rz), Mz.y);
+            const float X = __fadd_rn(__fmul_rn(a0, z), Mx.z);
+            const float Y = __fadd_rn(__fmul_rn(a1, z), My.z);
+            const float Z = __fadd_rn(__fmul_rn(a2, z), Mz.z);
+            uint32_t tu, tv;
+            const bool hit = target_pixel(X, Y, Z, maxu, maxv, tu, tv);
             // dd in [dlo, dhi] (dlo >= 1, so a code of 0 wraps above the span)
-            const bool ok = dd - dlo <= dspan && Z > zmin && tu >= 0.0f && tu <= maxu && tv >= 0.0f &&
-                            tv <= maxv;
-            if (ok) {
-                const uint32_t pix = float_to_u23(tv) * Wv + float_to_u23(tu);
+            if (dd - dlo <= dspan && Z > zmin && hit) {
                 const unsigned long long key =
                     (static_cast<unsigned long long>(__float_as_uint(Z)) << 32) | khi |
-                    static_cast<unsigned long long>(src0 + uint32_t(32 * j));
+                    static_cast<unsigned long long>(src0 + uint32_t(kStep * j));
                 unsigned long long* dst = (kLayered && ((bgm >> j) & 1u)) ? keys_bg : keys;
-                red_min_key(dst + pix, key, pol_keys);
+                red_min_key(dst + (tv * Wv + tu), key, pol_keys);
             }
         }
     }
@@ -260,11 +329,6 @@ k_warp_splat(const ViewDesc* __restrict__ views, const FrameRef* __restrict__ fr
 // An empty pixel takes min(a, b) of the first consistent pair; a present
 // pixel takes it from the first consistent pair with z_p > (1+tau) zmax.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ unsigned long long nb_key(const unsigned long long* row, int Wv, int x)
-{
-    return (x < 0 || x >= Wv) ? kKeyEmpty : row[x];
-}
-
 // The rule for a pixel whose neighbour at (dy, dx) is get(dy, dx).
 template <class Get>
 __device__ __forceinline__ unsigned long long crack_rule_at(Get get, unsigned long long kp, float f1)
@@ -288,13 +352,29 @@ __device__ __forceinline__ unsigned long long crack_rule_at(Get get, unsigned lo
     return kp;
 }
 
-__device__ __forceinline__ unsigned long long crack_rule(const unsigned long long* up,
-                                                         const unsigned long long* mid,
-                                                         const unsigned long long* dn, int Wv, int x,
-                                                         unsigned long long kp, float f1)
+// The rule on padded shared-memory rows (index -1 and Wv hold EMPTY).  A
+// present pixel no deeper than (1+tau) times its nearest present neighbour
+// keeps its key without the pair walk: every consistent pair's far depth is
+// at least that neighbour's, and the rounded product is monotone, so no pair
+// can satisfy z_p > (1+tau) zmax.  With no present neighbour no pair is
+// consistent either.
+__device__ __forceinline__ unsigned long long crack_rule_rows(const unsigned long long* up,
+                                                              const unsigned long long* mid,
+                                                              const unsigned long long* dn, int x,
+                                                              unsigned long long kp, float f1)
 {
-    const unsigned long long* rows[3] = {up, mid, dn};
-    return crack_rule_at([&](int dy, int dx) { return nb_key(rows[dy + 1], Wv, x + dx); }, kp, f1);
+    const unsigned long long n[3][3] = {{up[x - 1], up[x], up[x + 1]},
+                                        {mid[x - 1], kp, mid[x + 1]},
+                                        {dn[x - 1], dn[x], dn[x + 1]}};
+    if (kp != kKeyEmpty) {
+        // positive depths order like their bit patterns; EMPTY's are the largest
+        const uint32_t zb =
+            min(min(min(key_zbits(n[0][0]), key_zbits(n[0][1])), min(key_zbits(n[0][2]), key_zbits(n[1][0]))),
+                min(min(key_zbits(n[1][2]), key_zbits(n[2][0])), min(key_zbits(n[2][1]), key_zbits(n[2][2]))));
+        if (zb == 0xFFFFFFFFu || !(key_z(kp) > __fmul_rn(f1, __uint_as_float(zb))))
+            return kp;
+    }
+    return crack_rule_at([&](int dy, int dx) { return n[dy + 1][dx + 1]; }, kp, f1);
 }
 
 // Layered form: the BG layer's crack filter as its own pass, read straight
@@ -338,54 +418,6 @@ __device__ __forceinline__ uint32_t blend_channel(float acc, float wsum)
     return uint32_t(v);
 }
 
-// Block-wide exclusive prefix max (over lower thread ids), -1 for thread 0.
-__device__ __forceinline__ int block_excl_prefix_max(int v, int* s_scan)
-{
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    int inc = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int t = __shfl_up_sync(0xffffffffu, inc, o);
-        if (lane >= o) inc = max(inc, t);
-    }
-    if (lane == 31) s_scan[wid] = inc;
-    __syncthreads();
-    int acc = -1;
-    for (int i = 0; i < wid; ++i) acc = max(acc, s_scan[i]);
-    int excl = __shfl_up_sync(0xffffffffu, inc, 1);
-    if (lane == 0) excl = -1;
-    __syncthreads();
-    return max(acc, excl);
-}
-
-// Block-wide exclusive suffix min (over higher thread ids), INT_MAX for the last.
-__device__ __forceinline__ int block_excl_suffix_min(int v, int* s_scan)
-{
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int nw = blockDim.x >> 5;
-    int inc = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int t = __shfl_down_sync(0xffffffffu, inc, o);
-        if (lane + o < 32) inc = min(inc, t);
-    }
-    if (lane == 0) s_scan[wid] = inc;
-    __syncthreads();
-    int acc = INT_MAX;
-    for (int i = wid + 1; i < nw; ++i) acc = min(acc, s_scan[i]);
-    int excl = __shfl_down_sync(0xffffffffu, inc, 1);
-    if (lane == 31) excl = INT_MAX;
-    __syncthreads();
-    return min(acc, excl);
-}
-
-// ---------------------------------------------------------------------------
-// (c) + (d) + (e).  One CTA walks a band of consecutive output rows of one
-// view.  The key rows y-1, y, y+1 sit in a 4-row ring in shared memory; row
-// y+2 is copied in asynchronously (cp.async) while row y is resolved.
-// kTop3: also track the three largest contributing weights (only when that
-// output is requested).
-// ---------------------------------------------------------------------------
 // Per-pixel angular weight of a camera whose centre in the view's frame is
 // (cx, cy, cz), at the surface point (px, py, pz) at distance lb from the
 // view's centre: 1 / (chord + 0.001) with chord = sqrt(2 (1 - cos)) of the
@@ -402,10 +434,20 @@ __device__ __forceinline__ float pixel_weight(float cx, float cy, float cz, floa
     return __fdiv_rn(1.0f, __fadd_rn(chord, 0.001f));
 }
 
-// kPixW: per-pixel angular weights (each contribution weighted by the angle
-// at its surface point) instead of the view's per-camera weights.
-// Three CTAs per SM (a 64-register cap for four cost more in the gathers'
-// overlap than the extra warps gained).
+// ---------------------------------------------------------------------------
+// (c) + (d) + (e).  One CTA walks a band of consecutive output rows of one
+// view (two rows, or one for small batches), launched view after view so
+// that the resident CTAs share one view's frames in L2.  The key rows y-1, y, y+1 sit in a 4-row ring in shared
+// memory; row y+2 is copied in asynchronously (cp.async) while row y is
+// resolved.  Each thread resolves the pixels x = tid, tid + 256, ... of a
+// row: the winner's colour, then the other active cameras in ascending
+// order, in groups of four whose projections and gathers are issued before
+// any is consumed.
+// kTop3: also track the three largest contributing weights (only when that
+// output is requested).  kPixW: per-pixel angular weights (each contribution
+// weighted by the angle at its surface point) instead of the view's
+// per-camera weights.
+// ---------------------------------------------------------------------------
 template <bool kTop3, bool kLayered, bool kPixW>
 __global__ void __launch_bounds__(kResolveThreads, 3)
 k_resolve(const ViewDesc* __restrict__ views, const FrameRef* __restrict__ frames, int band)
@@ -419,29 +461,29 @@ k_resolve(const ViewDesc* __restrict__ views, const FrameRef* __restrict__ frame
     const int y1 = min(Hv, y0 + band);
     const int nc = V->n_cams, na = V->n_active;
     const SmemLayout L = resolve_layout(Wv, nc, kLayered);
+    const size_t RP = ring_pitch(Wv);
     unsigned long long* s_ring = reinterpret_cast<unsigned long long*>(smem + L.ring);
     uint32_t* s_rgb = reinterpret_cast<uint32_t*>(smem + L.rgb);
     float* s_dep = reinterpret_cast<float*>(smem + L.dep);
     uint8_t* s_hole = smem + L.hole;
-    float* s_geom = reinterpret_cast<float*>(smem + L.geom);
-    float* s_rowt = reinterpret_cast<float*>(smem + L.rowt);
-    FrameRef* s_fr = reinterpret_cast<FrameRef*>(smem + L.frames);
-    int* s_act = reinterpret_cast<int*>(smem + L.active);
-    int* s_pos = reinterpret_cast<int*>(smem + L.pos);        // camera -> position in s_act
+    RCam* s_cam = reinterpret_cast<RCam*>(smem + L.cams);
+    int* s_pos = reinterpret_cast<int*>(smem + L.pos);        // camera -> position in the active list
     int* s_scan = reinterpret_cast<int*>(smem + L.scan);
     const int tid = threadIdx.x;
     constexpr int NT = kResolveThreads;
     const unsigned long long* keys = V->keys;
 
     const unsigned long long* keys_bgf = V->keys_bgf;
-    auto ring_row = [&](int yy) { return s_ring + size_t((yy + kRing) & (kRing - 1)) * Wv; };
-    auto fetch_row = [&](int yy) {           // async copy of key row yy (empty outside)
+    auto ring_row = [&](int yy) { return s_ring + size_t((yy + kRing) & (kRing - 1)) * RP; };
+    auto fetch_row = [&](int yy) {           // async copy of key row yy (empty outside), with sentinels
         unsigned long long* dst = ring_row(yy);
+        if (tid == 0) dst[0] = kKeyEmpty;
+        if (tid == NT - 1) dst[Wv + 1] = kKeyEmpty;
         if (yy >= 0 && yy < Hv) {
             const unsigned long long* src = keys + size_t(yy) * Wv;
-            for (int x = tid; x < Wv; x += NT) cp_async8(dst + x, src + x);
+            for (int x = tid; x < Wv; x += NT) cp_async8(dst + 1 + x, src + x);
         } else {
-            for (int x = tid; x < Wv; x += NT) dst[x] = kKeyEmpty;
+            for (int x = tid; x < Wv; x += NT) dst[1 + x] = kKeyEmpty;
         }
     };
     fetch_row(y0 - 1);
@@ -449,21 +491,35 @@ k_resolve(const ViewDesc* __restrict__ views, const FrameRef* __restrict__ frame
     fetch_row(y0 + 1);
     cp_async_commit();
 
-    // per camera, 20 floats: N[0..11], w, 3 unused, W - 1, H - 1, 2 unused
-    for (int i = tid; i < nc * kGeomFloats; i += NT) {
-        const int k = i / kGeomFloats, j = i - k * kGeomFloats;
-        float val = 0.0f;
-        if (j < 12) val = V->geom[k].N[j];
-        else if (j == 12) val = V->geom[k].w;
-        else if (j < 16) val = V->geom[k].pad[j - 13];     // centre in the view's frame (per-pixel weights)
-        else if (j == 16) val = float(frames[V->slot * nc + k].W - 1);
-        else if (j == 17) val = float(frames[V->slot * nc + k].H - 1);
-        s_geom[i] = val;
+    // the active cameras' records, in active order
+    for (int a = tid; a < na; a += NT) {
+        const int k = V->active[a];
+        const CamGeom& G = V->geom[k];
+        const FrameRef& F = frames[V->slot * nc + k];
+        RCam C;
+        C.gx = make_float4(G.N[0], G.N[2], G.N[3], 0.0f);
+        C.gy = make_float4(G.N[4], G.N[6], G.N[7], 0.0f);
+        C.gz = make_float4(G.N[8], G.N[10], G.N[11], 0.0f);
+        C.depth = F.depth;
+        C.rgba = F.rgba;
+        C.dpitch = F.dpitch;
+        C.rpitch = F.rpitch;
+        C.maxu = uint32_t(F.W - 1);
+        C.maxv = uint32_t(F.H - 1);
+        C.w = G.w;
+        C.k = k;
+        // s / W for s < 2^26: shift = 26 + ceil(log2 W), magic = ceil(2^shift / W);
+        // then s * magic / 2^shift = s / W + e with 0 <= e < s / 2^shift < 1 / W,
+        // which never carries past the next integer
+        const uint32_t lg = F.W > 1 ? 32u - uint32_t(__clz(uint32_t(F.W - 1))) : 0u;
+        C.shift = 26u + lg;
+        C.magic = uint32_t(((1ull << C.shift) + uint64_t(F.W) - 1) / uint64_t(F.W));
+        C.bg = F.bg;
+        C.unused[0] = C.unused[1] = 0.0f;
+        C.rowc = make_float4(G.N[1], G.N[5], G.N[9], 0.0f);
+        C.cen = make_float4(G.pad[0], G.pad[1], G.pad[2], 0.0f);
+        s_cam[a] = C;
     }
-    for (int i = tid; i < nc; i += NT)
-        s_fr[i] = frames[V->slot * nc + i];
-    for (int i = tid; i < na; i += NT)
-        s_act[i] = V->active[i];
     for (int k = tid; k < kMaxCams; k += NT) {     // 0 for inactive cameras keeps every index in range
         int p = 0;
         for (int i = 0; i < na; ++i)
@@ -478,8 +534,8 @@ k_resolve(const ViewDesc* __restrict__ views, const FrameRef* __restrict__ frame
     const uint32_t dlo = V->d_lo, dspan = V->d_hi - V->d_lo;
     float* __restrict__ top3 = V->out_top3;
     unsigned long long* __restrict__ okeys = V->out_keys;
-    const float4* g4 = reinterpret_cast<const float4*>(s_geom);
-    __syncthreads();                          // s_geom, s_fr, s_act staged
+    const int nother = na - 1;
+    __syncthreads();                          // s_cam, s_pos staged
 
     for (int y = y0; y < y1; ++y) {
         // the ring slot of row y+2 held row y-2, last read before the end of
@@ -489,21 +545,23 @@ k_resolve(const ViewDesc* __restrict__ views, const FrameRef* __restrict__ frame
         cp_async_commit();
         // per-row products N1 y, N5 y, N9 y (the order stays ((N0 x + N1 y) + N2))
         const float fy = u23_to_float(uint32_t(y));
-        for (int i = tid; i < nc * 3; i += NT) {
-            const int k = i / 3, j = i - k * 3;
-            s_rowt[4 * k + j] = __fmul_rn(s_geom[kGeomFloats * k + 1 + 4 * j], fy);
+        for (int a = tid; a < na; a += NT) {
+            const float4 rc = s_cam[a].rowc;
+            s_cam[a].gx.w = __fmul_rn(rc.x, fy);
+            s_cam[a].gy.w = __fmul_rn(rc.y, fy);
+            s_cam[a].gz.w = __fmul_rn(rc.z, fy);
         }
         cp_async_wait<1>();                   // rows y-1 .. y+1 have landed
         __syncthreads();
 
-        const unsigned long long* rU = ring_row(y - 1);
-        const unsigned long long* rC = ring_row(y);
-        const unsigned long long* rD = ring_row(y + 1);
+        const unsigned long long* rU = ring_row(y - 1) + 1;
+        const unsigned long long* rC = ring_row(y) + 1;
+        const unsigned long long* rD = ring_row(y + 1) + 1;
         const size_t rowbase = size_t(y) * Wv;
         bool any_hole = false;
         for (int x = tid; x < Wv; x += NT) {
             const unsigned long long kp = rC[x];
-            unsigned long long key = crack ? crack_rule(rU, rC, rD, Wv, x, kp, f1) : kp;
+            unsigned long long key = crack ? crack_rule_rows(rU, rC, rD, x, kp, f1) : kp;
             // layered: the FG layer is stacked over the BG layer, so the BG
             // layer is resolved only where the filtered FG layer is empty
             bool bg_layer = false;
@@ -527,10 +585,12 @@ k_resolve(const ViewDesc* __restrict__ views, const FrameRef* __restrict__ frame
             const float Z = key_z(key);
             const int w = int((key >> kSrcBits) & 63u);
             const uint32_t s = uint32_t(key & ((1u << kSrcBits) - 1u));
-            const FrameRef& Fw = s_fr[w];
-            const uint32_t sv = s / uint32_t(Fw.W);
-            const uint32_t su = s - sv * uint32_t(Fw.W);
-            const uint32_t cw = __ldg(Fw.rgba + sv * uint32_t(Fw.rpitch) + su);
+            // the winner is always active (only active cameras splat)
+            const int pw = s_pos[w];
+            const RCam& Cw = s_cam[pw];
+            const uint32_t sv = uint32_t((static_cast<unsigned long long>(s) * Cw.magic) >> Cw.shift);
+            const uint32_t su = s - sv * (Cw.maxu + 1u);
+            const uint32_t cw = __ldg(Cw.rgba + sv * uint32_t(Cw.rpitch) + su);
             const float fx = u23_to_float(uint32_t(x));
             // per-pixel weights: the surface point in the view's frame
             float px = 0.0f, py = 0.0f, lb = 0.0f;
@@ -539,74 +599,73 @@ k_resolve(const ViewDesc* __restrict__ views, const FrameRef* __restrict__ frame
                 py = __fmul_rn(__fmul_rn(__fsub_rn(fy, V->vk[1]), V->vk[3]), Z);
                 lb = __fsqrt_rn(__fadd_rn(__fadd_rn(__fmul_rn(px, px), __fmul_rn(py, py)), __fmul_rn(Z, Z)));
             }
-            auto weight_of = [&](int k) {
-                if (!kPixW) return s_geom[kGeomFloats * k + 12];
-                const float* gk = s_geom + kGeomFloats * k;
-                return pixel_weight(gk[13], gk[14], gk[15], px, py, Z, lb);
+            auto weight_of = [&](const RCam& C) {
+                if (!kPixW) return C.w;
+                const float4 c = C.cen;
+                return pixel_weight(c.x, c.y, c.z, px, py, Z, lb);
             };
-            const float ww = weight_of(w);
-            float acc0 = __fmul_rn(ww, u23_to_float(cw & 255u));
-            float acc1 = __fmul_rn(ww, u23_to_float((cw >> 8) & 255u));
-            float acc2 = __fmul_rn(ww, u23_to_float((cw >> 16) & 255u));
+            const float ww = weight_of(Cw);
+            // the winner's colour is consumed after the first group's gathers
+            // are in flight (its load latency overlaps their projections)
+            float acc0 = 0.0f, acc1 = 0.0f, acc2 = 0.0f;
+            auto init_acc = [&]() {
+                acc0 = __fmul_rn(ww, u23_to_float(cw & 255u));
+                acc1 = __fmul_rn(ww, u23_to_float((cw >> 8) & 255u));
+                acc2 = __fmul_rn(ww, u23_to_float((cw >> 16) & 255u));
+            };
+            if (nother <= 0)
+                init_acc();
             float wsum = ww;
             float t0 = ww, t1 = -1.0f, t2 = -1.0f;
             int k0 = w, k1 = INT_MAX, k2 = INT_MAX;
-            // the other active cameras (the winner is always active: only
-            // active cameras splat), in ascending order, in groups of four:
-            // project all four and issue their depth and colour gathers
-            // before any is consumed, then accumulate in order
-            const int pw = s_pos[w], nother = na - 1;
-            for (int g0 = 0; g0 < nother; g0 += 4) {
-                uint32_t dk[4], ck[4], di[4];
-                float zk[4];
-                int kk[4];
-                bool ok[4];
+            for (int g0 = 0; g0 < nother; g0 += kGroup) {
+                uint32_t dk[kGroup], ck[kGroup], di[kGroup];
+                float zk[kGroup];
+                int ak[kGroup];
+                bool ok[kGroup];
                 // branch-free projection of the group (only the gathers are
-                // predicated), so the four chains can interleave
+                // predicated), so the chains can interleave
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {
+                for (int j = 0; j < kGroup; ++j) {
                     const int ii = min(g0 + j, nother - 1);
-                    const int k = s_act[ii + (ii >= pw ? 1 : 0)];
-                    kk[j] = k;
-                    const float4 A = g4[5 * k + 0], Bq = g4[5 * k + 1], Cq = g4[5 * k + 2],
-                                 Eq = g4[5 * k + 4];
-                    const float4 Rt = reinterpret_cast<const float4*>(s_rowt)[k];
-                    const float a0 = __fadd_rn(__fadd_rn(__fmul_rn(A.x, fx), Rt.x), A.z);
-                    const float a1 = __fadd_rn(__fadd_rn(__fmul_rn(Bq.x, fx), Rt.y), Bq.z);
-                    const float a2 = __fadd_rn(__fadd_rn(__fmul_rn(Cq.x, fx), Rt.z), Cq.z);
-                    const float Xk = __fadd_rn(__fmul_rn(a0, Z), A.w);
-                    const float Yk = __fadd_rn(__fmul_rn(a1, Z), Bq.w);
-                    const float Zk = __fadd_rn(__fmul_rn(a2, Z), Cq.w);
-                    const float tu = floorf(__fadd_rn(__fdiv_rn(Xk, Zk), 0.5f));
-                    const float tv = floorf(__fadd_rn(__fdiv_rn(Yk, Zk), 0.5f));
-                    // the bounds test also rejects NaN and +-inf, as a finiteness test would
-                    ok[j] = g0 + j < nother && Zk > zmin && tu >= 0.0f && tu <= Eq.x &&
-                            tv >= 0.0f && tv <= Eq.y;
+                    const int a = ii + (ii >= pw ? 1 : 0);
+                    ak[j] = a;
+                    const RCam& C = s_cam[a];
+                    const float4 gx = C.gx, gy = C.gy, gz = C.gz;
+                    const float a0 = __fadd_rn(__fadd_rn(__fmul_rn(gx.x, fx), gx.w), gx.y);
+                    const float a1 = __fadd_rn(__fadd_rn(__fmul_rn(gy.x, fx), gy.w), gy.y);
+                    const float a2 = __fadd_rn(__fadd_rn(__fmul_rn(gz.x, fx), gz.w), gz.y);
+                    const float Xk = __fadd_rn(__fmul_rn(a0, Z), gx.z);
+                    const float Yk = __fadd_rn(__fmul_rn(a1, Z), gy.z);
+                    const float Zk = __fadd_rn(__fmul_rn(a2, Z), gz.z);
+                    uint32_t uk, vk;
+                    const bool hit = target_pixel(Xk, Yk, Zk, C.maxu, C.maxv, uk, vk);
+                    ok[j] = g0 + j < nother && Zk > zmin && hit;
                     zk[j] = Zk;
                     dk[j] = 0u;
                     ck[j] = 0u;
                     di[j] = 0u;
                     if (ok[j]) {
-                        const FrameRef& Fk = s_fr[k];
-                        const uint32_t uk = float_to_u23(tu), vk = float_to_u23(tv);
-                        di[j] = vk * uint32_t(Fk.dpitch) + uk;
-                        dk[j] = __ldg(Fk.depth + di[j]);
-                        ck[j] = __ldg(Fk.rgba + vk * uint32_t(Fk.rpitch) + uk);
+                        di[j] = vk * uint32_t(C.dpitch) + uk;
+                        dk[j] = __ldg(C.depth + di[j]);
+                        ck[j] = __ldg(C.rgba + vk * uint32_t(C.rpitch) + uk);
                     }
                 }
                 // the BG layer's depth in camera k: its model where camera k
                 // signals BG, none elsewhere (there camera k sees FG)
                 if (kLayered && bg_layer) {
 #pragma unroll
-                    for (int j = 0; j < 4; ++j) {
+                    for (int j = 0; j < kGroup; ++j) {
                         if (!ok[j])
                             continue;
-                        const FrameRef& Fk = s_fr[kk[j]];
-                        dk[j] = (dk[j] == kDepthBg && Fk.bg) ? uint32_t(__ldg(Fk.bg + di[j])) : 0u;
+                        const uint16_t* bgk = s_cam[ak[j]].bg;
+                        dk[j] = (dk[j] == kDepthBg && bgk) ? uint32_t(__ldg(bgk + di[j])) : 0u;
                     }
                 }
+                if (g0 == 0)
+                    init_acc();
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {
+                for (int j = 0; j < kGroup; ++j) {
                     if (!ok[j])
                         continue;
                     if (dk[j] - dlo > dspan)         // outside [dlo, dhi]; 0 wraps above
@@ -614,14 +673,15 @@ k_resolve(const ViewDesc* __restrict__ views, const FrameRef* __restrict__ frame
                     const float diff = fabsf(__fsub_rn(u23_to_float(dk[j]), zk[j]));
                     if (!(diff <= __fmul_rn(tau_vis, zk[j])))
                         continue;
-                    const int k = kk[j];
-                    const float wk = weight_of(k);
+                    const RCam& C = s_cam[ak[j]];
+                    const float wk = weight_of(C);
                     const uint32_t c = ck[j];
                     acc0 = __fadd_rn(acc0, __fmul_rn(wk, u23_to_float(c & 255u)));
                     acc1 = __fadd_rn(acc1, __fmul_rn(wk, u23_to_float((c >> 8) & 255u)));
                     acc2 = __fadd_rn(acc2, __fmul_rn(wk, u23_to_float((c >> 16) & 255u)));
                     wsum = __fadd_rn(wsum, wk);
                     if (kTop3) {
+                        const int k = C.k;
                         if (w_before(wk, k, t0, k0)) {
                             t2 = t1; k2 = k1; t1 = t0; k1 = k0; t0 = wk; k0 = k;
                         } else if (w_before(wk, k, t1, k1)) {
@@ -641,39 +701,63 @@ k_resolve(const ViewDesc* __restrict__ views, const FrameRef* __restrict__ frame
                 top3[3 * (rowbase + x) + 2] = t2 >= 0.0f ? __fdiv_rn(t2, wsum) : 0.0f;
             }
         }
-        // (e) hole fill: nearest non-hole left / right, the deeper one wins
+        // (e) hole fill: nearest non-hole left / right, the deeper one wins.
+        // The row is cut into 32-pixel chunks, a warp owning a run of them;
+        // a chunk's non-hole mask is one ballot, the nearest non-hole inside
+        // a chunk one bit search, and across chunks and warps a carry.
         const bool row_has_hole = __syncthreads_or(any_hole) != 0;
         if (fill && row_has_hole) {
+            constexpr int NW = NT / 32;
+            const int lane = tid & 31, wid = tid >> 5;
             // the ring slot of row y - 1: every thread has finished reading
             // it (the barrier above), and row y + 3 lands in it only after
-            // the barrier that ends this row
-            int16_t* s_left = reinterpret_cast<int16_t*>(const_cast<unsigned long long*>(rU));
-            int16_t* s_right = s_left + Wv;
-            const int seg = (Wv + NT - 1) / NT;
-            const int x0 = min(tid * seg, Wv), x1 = min(x0 + seg, Wv);
-            int last = -1;
-            for (int x = x0; x < x1; ++x)
-                if (!s_hole[x]) last = x;
-            int run = block_excl_prefix_max(last, s_scan);
-            for (int x = x0; x < x1; ++x) {
-                if (!s_hole[x]) run = x;
-                s_left[x] = int16_t(run);
+            // the barrier that ends this row (which also restores its sentinels)
+            int16_t* s_left = reinterpret_cast<int16_t*>(ring_row(y - 1));
+            uint32_t* s_mask = reinterpret_cast<uint32_t*>(s_left + ((Wv + 1) & ~1));
+            const int nch = (Wv + 31) >> 5;
+            const int cpw = (nch + NW - 1) / NW;
+            const int c0 = min(wid * cpw, nch), c1 = min(c0 + cpw, nch);
+            int last = -1, first = INT_MAX;
+            for (int c = c0; c < c1; ++c) {
+                const int x = (c << 5) + lane;
+                const uint32_t m = __ballot_sync(0xffffffffu, x < Wv && !s_hole[x]);
+                if (m) {
+                    last = (c << 5) + 31 - __clz(m);
+                    if (first == INT_MAX) first = (c << 5) + __ffs(m) - 1;
+                }
+                if (lane == 0) s_mask[c] = m;
             }
-            int first = INT_MAX;
-            for (int x = x1 - 1; x >= x0; --x)
-                if (!s_hole[x]) first = x;
-            run = block_excl_suffix_min(first, s_scan);
-            for (int x = x1 - 1; x >= x0; --x) {
-                if (!s_hole[x]) run = x;
-                s_right[x] = int16_t(run == INT_MAX ? -1 : run);
+            if (lane == 0) {
+                s_scan[wid] = last;
+                s_scan[NW + wid] = first;
             }
             __syncthreads();
-            for (int x = tid; x < Wv; x += NT) {
-                if (!s_hole[x])
+            int carry = -1;                          // nearest non-hole left of the chunk
+            for (int i = 0; i < wid; ++i) carry = max(carry, s_scan[i]);
+            const uint32_t upto = lane == 31 ? 0xffffffffu : ((2u << lane) - 1u);   // bits <= lane
+            for (int c = c0; c < c1; ++c) {
+                const uint32_t m = s_mask[c];
+                const uint32_t ml = m & upto;
+                const int x = (c << 5) + lane;
+                if (x < Wv) s_left[x] = int16_t(ml ? (c << 5) + 31 - __clz(ml) : carry);
+                if (m) carry = (c << 5) + 31 - __clz(m);
+            }
+            __syncwarp();
+            carry = INT_MAX;                         // nearest non-hole right of the chunk
+            for (int i = wid + 1; i < NW; ++i) carry = min(carry, s_scan[NW + i]);
+            const uint32_t from = ~((1u << lane) - 1u);                             // bits >= lane
+            for (int c = c1 - 1; c >= c0; --c) {
+                const uint32_t m = s_mask[c];
+                const uint32_t mr = m & from;
+                const int x = (c << 5) + lane;
+                const int r0 = mr ? (c << 5) + __ffs(mr) - 1 : carry;
+                if (m) carry = (c << 5) + __ffs(m) - 1;
+                if (x >= Wv || !s_hole[x])
                     continue;
-                const int l = s_left[x], r = s_right[x];
+                const int l = s_left[x], r = r0 == INT_MAX ? -1 : r0;
                 if (l < 0 && r < 0)
                     continue;
+                // only holes are written and only non-holes are read
                 const int src = l < 0 ? r : (r < 0 ? l : (s_dep[r] > s_dep[l] ? r : l));
                 s_rgb[x] = s_rgb[src];
                 s_dep[x] = s_dep[src];
@@ -681,25 +765,23 @@ k_resolve(const ViewDesc* __restrict__ views, const FrameRef* __restrict__ frame
             __syncthreads();
         }
 
+        // RGB8 row: four pixels -> three aligned 32-bit words where the row
+        // allows it, single bytes for the rest
         uint8_t* orow = V->out_rgb + size_t(y) * size_t(V->out_pitch);
-        const int nbytes = 3 * Wv;
-        int done = 0;
+        int xdone = 0;
         if ((reinterpret_cast<uintptr_t>(orow) & 3u) == 0) {
-            const int nw = nbytes >> 2;
+            const int nq = Wv >> 2;
             uint32_t* o32 = reinterpret_cast<uint32_t*>(orow);
-            for (int i = tid; i < nw; i += NT) {
-                uint32_t word = 0;
-#pragma unroll
-                for (int b = 0; b < 4; ++b) {
-                    const int byte = 4 * i + b;
-                    const int x = byte / 3;
-                    word |= ((s_rgb[x] >> (8 * (byte - 3 * x))) & 255u) << (8 * b);
-                }
-                o32[i] = word;
+            const uint4* p4 = reinterpret_cast<const uint4*>(s_rgb);
+            for (int q = tid; q < nq; q += NT) {
+                const uint4 p = p4[q];
+                o32[3 * q + 0] = __byte_perm(p.x, p.y, 0x4210);
+                o32[3 * q + 1] = __byte_perm(p.y, p.z, 0x5421);
+                o32[3 * q + 2] = __byte_perm(p.z, p.w, 0x6542);
             }
-            done = nw << 2;
+            xdone = nq << 2;
         }
-        for (int i = done + tid; i < nbytes; i += NT) {
+        for (int i = 3 * xdone + tid; i < 3 * Wv; i += NT) {
             const int x = i / 3;
             orow[i] = uint8_t(s_rgb[x] >> (8 * (i - 3 * x)));
         }
@@ -707,7 +789,7 @@ k_resolve(const ViewDesc* __restrict__ views, const FrameRef* __restrict__ frame
             for (int x = tid; x < Wv; x += NT) V->out_depth[rowbase + x] = s_dep[x];
         if (V->out_hole)
             for (int x = tid; x < Wv; x += NT) V->out_hole[rowbase + x] = s_hole[x];
-        __syncthreads();        // s_rgb / s_dep / s_hole / s_rowt are rewritten next row
+        __syncthreads();        // s_rgb / s_dep / s_hole / row products are rewritten next row
     }
 }
 
@@ -728,6 +810,32 @@ __global__ void __launch_bounds__(256) k_pack_rgba(const uint8_t* __restrict__ r
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
+int device_sms()
+{
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) {
+        cudaGetLastError();
+        sms = 1;
+    }
+    return sms;
+}
+
+namespace {
+
+// Splat depth loads: 16-byte vectors (8 pixels per lane) or 2-byte loads at
+// a stride of 32 pixels.  FVV_SPLAT_VEC=0/1 picks one for measurements.
+bool splat_vec()
+{
+    static const int v = [] {
+        const char* e = std::getenv("FVV_SPLAT_VEC");
+        return e ? (e[0] == '1' ? 1 : 0) : 0;
+    }();
+    return v != 0;
+}
+
+}  // namespace
+
 size_t resolve_smem_bytes(int max_w, int n_cams, bool layered)
 {
     return resolve_layout(max_w, n_cams, layered).total;
@@ -737,8 +845,9 @@ cudaError_t launch_clear_keys(unsigned long long* keys, size_t n, cudaStream_t s
 {
     if (n == 0) return cudaSuccess;
     size_t blocks = ((n >> 1) + 255) / 256;
+    const size_t cap = size_t(device_sms()) * 16;
     if (blocks < 1) blocks = 1;
-    if (blocks > 152 * 16) blocks = 152 * 16;
+    if (blocks > cap) blocks = cap;
     k_clear_keys<<<unsigned(blocks), 256, 0, stream>>>(keys, n);
     return cudaGetLastError();
 }
@@ -749,17 +858,19 @@ cudaError_t launch_warp_splat(const ViewDesc* views, int n_views, int max_chunks
     if (n_views <= 0 || max_chunks <= 0) return cudaSuccess;
     constexpr int kWarps = kSplatThreads / 32;      // one warp per segment at a time
     // persistent warps: about two resident waves over all views of the batch
-    int dev = 0, sms = 152;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int sms = device_sms();
     const int want = (2 * 5 * sms + n_views - 1) / n_views;
     const int need = (max_chunks + kWarps - 1) / kWarps;
     const int bx = need < want ? need : (want < 1 ? 1 : want);
     dim3 grid(static_cast<unsigned>(bx), static_cast<unsigned>(n_views));
-    if (layered)
-        k_warp_splat<true><<<grid, kSplatThreads, 0, stream>>>(views, frames);
-    else
-        k_warp_splat<false><<<grid, kSplatThreads, 0, stream>>>(views, frames);
+    const bool vec = splat_vec();
+    if (layered) {
+        if (vec) k_warp_splat<true, true><<<grid, kSplatThreads, 0, stream>>>(views, frames);
+        else k_warp_splat<true, false><<<grid, kSplatThreads, 0, stream>>>(views, frames);
+    } else {
+        if (vec) k_warp_splat<false, true><<<grid, kSplatThreads, 0, stream>>>(views, frames);
+        else k_warp_splat<false, false><<<grid, kSplatThreads, 0, stream>>>(views, frames);
+    }
     return cudaGetLastError();
 }
 
@@ -780,11 +891,21 @@ cudaError_t launch_resolve(const ViewDesc* views, int n_views, int max_h, int ma
     // the layout grows with the width and the camera count, so the widest
     // view of the batch bounds every CTA's shared memory
     const size_t smem = resolve_smem_bytes(max_w, n_cams, layered);
-    const int band = kResolveBand;
-    dim3 grid(static_cast<unsigned>((max_h + band - 1) / band), static_cast<unsigned>(n_views));
+    const int sms = device_sms();
     auto go = [&](auto kernel) {
         cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
         if (e != cudaSuccess) return e;
+        // Bands of two rows, launched view after view: the CTAs resident at
+        // one time then cover about one view, whose frames stay in L2 for
+        // its gathers (a single wave of all views' bands streams every
+        // view's frames at once and doubled the DRAM reads).  Single rows
+        // when two-row bands would not fill the resident slots.
+        int per_sm = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kResolveThreads, smem);
+        if (e != cudaSuccess) return e;
+        const long long slots = (long long)(per_sm > 0 ? per_sm : 1) * sms;
+        const int band = (long long)max_h * n_views >= 2 * kResolveBand * slots ? kResolveBand : 1;
+        dim3 grid(static_cast<unsigned>((max_h + band - 1) / band), static_cast<unsigned>(n_views));
         kernel<<<grid, kResolveThreads, smem, stream>>>(views, frames, band);
         return cudaGetLastError();
     };

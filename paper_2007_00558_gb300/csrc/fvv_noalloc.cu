@@ -16,6 +16,7 @@
 // them.  Calls whose GPU work overlaps (e.g. on two streams without ordering)
 // race on that scratch.  The clear kernel resets the keys at the start of
 // every call; the parameters are rewritten by every call.
+#include <climits>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -64,14 +65,24 @@ __global__ void k_store_params(const NoAllocParams p, NoAllocParams* dst)
         d[i] = src[i];
 }
 
-bool device_memory(const void* p)
+// Device (or managed) memory of device `dev`: the kernels run on the current
+// device and would otherwise dereference another GPU's memory.
+bool device_memory(const void* p, int dev)
 {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    return (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) && a.device == dev;
+}
+
+// The resolve kernel indexes a frame in 32 bits: (H - 1) * pitch + W must
+// stay below 2^32 elements.
+bool pitch_fits(size_t pitch_elems, int W, int H)
+{
+    return pitch_elems <= size_t(INT32_MAX) &&
+           uint64_t(H - 1) * uint64_t(pitch_elems) + uint64_t(W) < (uint64_t(1) << 32);
 }
 
 bool camera_sane(const fvv_camera& c)
@@ -124,28 +135,33 @@ extern "C" fvv_status fvv_synthesize_noalloc(const fvv_rig* rig, const fvv_optio
     }
     if (out_pitch < size_t(view->width) * 3)
         return fail(FVV_ERR_INVALID_ARG, "fvv_synthesize_noalloc: out_pitch < 3 * width");
-    if (!device_memory(out_rgb))
-        return fail(FVV_ERR_INVALID_ARG, "fvv_synthesize_noalloc: out_rgb must be device memory");
-    for (int k = 0; k < rig->n_cams; ++k) {
-        if (!camera_sane(rig->cams[k]))
-            return fail(FVV_ERR_INVALID_ARG, "fvv_synthesize_noalloc: invalid rig camera");
-        if (!depth[k] || !rgba[k] || !device_memory(depth[k]) || !device_memory(rgba[k]))
-            return fail(FVV_ERR_INVALID_ARG, "fvv_synthesize_noalloc: frames must be device memory");
-        if (depth_pitch[k] % 2 || depth_pitch[k] < size_t(rig->cams[k].width) * 2 ||
-            rgba_pitch[k] % 4 || rgba_pitch[k] < size_t(rig->cams[k].width) * 4 ||
-            (reinterpret_cast<uintptr_t>(depth[k]) & 1) || (reinterpret_cast<uintptr_t>(rgba[k]) & 3))
-            return fail(FVV_ERR_INVALID_ARG, "fvv_synthesize_noalloc: bad frame pitch or alignment");
-    }
-    if (fvv::resolve_smem_bytes(view->width, rig->n_cams) > size_t(227) * 1024)
-        return fail(FVV_ERR_INVALID_ARG, "fvv_synthesize_noalloc: view too wide");
-
-    // once per device, with that device current: device addresses of the
-    // scratch arrays
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
         cudaGetLastError();
         return fail(FVV_ERR_CUDA, "fvv_synthesize_noalloc: no usable current device");
     }
+    if (!device_memory(out_rgb, dev))
+        return fail(FVV_ERR_INVALID_ARG, "fvv_synthesize_noalloc: out_rgb must be memory of the current device");
+    for (int k = 0; k < rig->n_cams; ++k) {
+        if (!camera_sane(rig->cams[k]))
+            return fail(FVV_ERR_INVALID_ARG, "fvv_synthesize_noalloc: invalid rig camera");
+        if (!depth[k] || !rgba[k] || !device_memory(depth[k], dev) || !device_memory(rgba[k], dev))
+            return fail(FVV_ERR_INVALID_ARG, "fvv_synthesize_noalloc: frames must be memory of the current device");
+        const int W = rig->cams[k].width, H = rig->cams[k].height;
+        if (depth_pitch[k] % 2 || depth_pitch[k] < size_t(W) * 2 ||
+            rgba_pitch[k] % 4 || rgba_pitch[k] < size_t(W) * 4 ||
+            (reinterpret_cast<uintptr_t>(depth[k]) & 1) || (reinterpret_cast<uintptr_t>(rgba[k]) & 3))
+            return fail(FVV_ERR_INVALID_ARG, "fvv_synthesize_noalloc: bad frame pitch or alignment");
+        if (!pitch_fits(depth_pitch[k] / 2, W, H) || !pitch_fits(rgba_pitch[k] / 4, W, H))
+            return fail(FVV_ERR_INVALID_ARG,
+                        "fvv_synthesize_noalloc: frame pitch too large ((H - 1) * pitch + W must be below 2^32 elements)");
+    }
+    if (fvv::resolve_smem_bytes(view->width, rig->n_cams) > size_t(227) * 1024)
+        return fail(FVV_ERR_INVALID_ARG, "fvv_synthesize_noalloc: view too wide");
+
+    // once per device, with that device current: device addresses of the
+    // scratch arrays (a device reset after this point is not supported: the
+    // module may come back at other addresses)
     DeviceScratch S;
     {
         std::lock_guard<std::mutex> lock(g_scratch_mu);
@@ -178,7 +194,8 @@ extern "C" fvv_status fvv_synthesize_noalloc(const fvv_rig* rig, const fvv_optio
     D.Hv = view->height;
     D.n_cams = nc;
     D.slot = 0;
-    D.flags = (o.crack_filter ? fvv::kFlagCrack : 0) | (o.hole_fill ? fvv::kFlagFill : 0);
+    D.flags = (o.crack_filter ? fvv::kFlagCrack : 0) | (o.hole_fill ? fvv::kFlagFill : 0) |
+              (o.pixel_weights ? fvv::kFlagPixelWeights : 0);
     D.tau_crack = o.tau_crack;
     D.tau_vis = o.tau_vis;
     D.z_min = o.z_min;

@@ -7,6 +7,7 @@
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
 
+#include "fvv_internal.h"
 #include "fvv_unet.h"
 
 namespace fvv {
@@ -686,7 +687,8 @@ cudaError_t launch_head_bwd(size_t npx, int C1, const __nv_bfloat16* d1, const f
 cudaError_t launch_amax(size_t npix, int C, const __nv_bfloat16* x, int ld, float* out, cudaStream_t s)
 {
     unsigned g = blocks(npix * (C / 8), 256);
-    if (g > 152 * 8) g = 152 * 8;
+    const unsigned cap = unsigned(device_sms()) * 8;
+    if (g > cap) g = cap;
     if (g == 0) g = 1;
     k_amax<<<g, 256, 0, s>>>(npix, C, x, ld, out);
     return cudaGetLastError();
@@ -713,7 +715,7 @@ cudaError_t wgrad_blocks(int B, int H, int W, int Cin, int xst, int Cout, const 
     const int tiles = 9 * (Cout / BCO) * (Cin / BCI);
     const long rows = long(B) * H;
     // split the rows so that about 4 waves of CTAs cover the GPU
-    long splits = (4L * 152 * 4 * (1024 / (BCO * BCI)) + tiles - 1) / tiles;
+    long splits = (4L * device_sms() * 4 * (1024 / (BCO * BCI)) + tiles - 1) / tiles;
     if (splits > rows) splits = rows;
     if (splits < 1) splits = 1;
     const int rpc = int((rows + splits - 1) / splits);
@@ -730,7 +732,7 @@ cudaError_t launch_wgrad3x3(int B, int H, int W, int Cin, int xstride, int Cout,
         ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(dz)) & 15) == 0) {
         const int tiles = 9 * (Cout / 32) * (Cin / 32);
         const long rows = long(B) * H;
-        long splits = (152L * 16 + tiles - 1) / tiles;       // about 16 CTAs of 64 threads per SM
+        long splits = (long(device_sms()) * 16 + tiles - 1) / tiles;   // about 16 CTAs of 64 threads per SM
         if (splits > rows) splits = rows;
         if (splits < 1) splits = 1;
         const int rpc = int((rows + splits - 1) / splits);
@@ -752,7 +754,8 @@ cudaError_t launch_bias_grad(size_t npx, int C, const __nv_bfloat16* dz, float* 
 {
     if (C % 8 || C > 2048 || (reinterpret_cast<uintptr_t>(dz) & 15)) return cudaErrorInvalidValue;
     // about eight CTAs per SM, at least 256 pixels each
-    size_t per = (npx + 152 * 8 - 1) / (152 * 8);
+    const size_t nblk = size_t(device_sms()) * 8;
+    size_t per = (npx + nblk - 1) / nblk;
     if (per < 256) per = 256;
     k_bias_grad<<<blocks(npx, int(per)), 256, 0, s>>>(npx, C, dz, db, per);
     return cudaGetLastError();
