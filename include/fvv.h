@@ -425,6 +425,22 @@ fvv_status fvv_unet_conv3x3(const void* x, int32_t n, int32_t h, int32_t w, int3
                             const void* wt, const float* bias, int32_t cout, int32_t relu,
                             const void* mask, void* y, void* stream);
 
+/* Weight and bias gradients of that convolution on the tensor cores (the
+ * paper has no network; these are the training step's kernels):
+ *   dw[co][ky][kx][ci] = sum_p dz[p][co] x[p + (ky - 1, kx - 1)][ci],
+ *   db[co] = sum_p dz[p][co]   (zero padding outside the image)
+ *   x: [n][h][w] pixels of xstride bf16 channels, the first cin used
+ *      (xstride 0 = cin); dz: [n][h][w][cout] bf16; cin, xstride and cout
+ *      multiples of 8; x and dz 16-byte aligned
+ *   dw: float [cout][3][3][cin], db: float [cout] or NULL (overwritten)
+ * The pixels are split into fixed ranges whose fp32 partial sums are added
+ * in a fixed order, so the result is reproducible bit for bit.  Allocates
+ * its partial-sum scratch (cudaMalloc) for the call and waits for
+ * completion on `stream`.  Errors: INVALID_ARG, OUT_OF_MEMORY, TIMEOUT (a
+ * bounded wait inside the kernel ran out), CUDA. */
+fvv_status fvv_unet_wgrad3x3(const void* x, int32_t n, int32_t h, int32_t w, int32_t cin, int32_t xstride,
+                             const void* dz, int32_t cout, float* dw, float* db, void* stream);
+
 /* FP8 form of the same convolution.  x, wt and y hold OCP E4M3 bytes (1
  * sign, 4 exponent bits with bias 7, 3 mantissa bits; largest finite 448).
  * With per-tensor scales s_x, s_w, s_y (x = s_x X, w = s_w W, y = s_y Y for

@@ -102,6 +102,9 @@ struct RefineNet {
     __nv_bfloat16 *g_d1b, *g_d1a, *g_cat1, *g_skip1, *g_d2b, *g_d2a, *g_cat2, *g_skip2, *g_bb, *g_ba, *g_p2,
         *g_e2b, *g_e2a, *g_p1, *g_e1b, *g_e1a;
     float* loss = nullptr;
+    // per-split partial sums of the tensor-core weight gradients
+    float* wscratch = nullptr;
+    size_t wscratch_floats = 0;
     // e4m3 inference: per-tensor scales of the ten conv outputs, the input
     // scale, and e4m3 activations for (qB, qH, qW)
     int precision = FVV_PREC_BF16;
@@ -293,6 +296,33 @@ fvv_status ensure_grads(fvv_ctx* c, RefineNet& N, size_t pixels)
     return FVV_OK;
 }
 
+// Partial sums of the weight-gradient kernels for a batch of B images H x W:
+// the largest layer's full split count, capped at 64 MiB (the kernels then
+// use fewer splits).
+fvv_status ensure_wscratch(fvv_ctx* c, RefineNet& N, int B, int H, int W)
+{
+    size_t need = 0;
+    const int hs[10] = {H, H, H / 2, H / 2, H / 4, H / 4, H / 2, H / 2, H, H};
+    const int ws[10] = {W, W, W / 2, W / 2, W / 4, W / 4, W / 2, W / 2, W, W};
+    for (int i = 0; i < 10; ++i)
+        need = std::max(need, wgrad_scratch_floats(B, hs[i], ws[i], N.L[i].cin, N.L[i].cout));
+    need = std::min(need, size_t(16) << 20);             // 64 MiB
+    for (int i = 0; i < 10; ++i)                          // but one split of every layer
+        need = std::max(need, size_t(N.L[i].cout) * (9 * size_t(N.L[i].cin) + 1));
+    // the head's backward pass uses the same buffer first
+    need = std::max(need, head_bwd_scratch_floats(size_t(B) * H * W, N.L[9].cout));
+    if (need <= N.wscratch_floats) return FVV_OK;
+    FVV_CUDA(cudaDeviceSynchronize());
+    if (N.wscratch) dev_free(c, N.wscratch, N.wscratch_floats * 4);
+    N.wscratch = nullptr;
+    N.wscratch_floats = 0;
+    void* p = nullptr;
+    FVV_TRY(dev_alloc(c, &p, need * 4));
+    N.wscratch = static_cast<float*>(p);
+    N.wscratch_floats = need;
+    return FVV_OK;
+}
+
 // Where a conv writes: channel stride and offset of the output, whether it
 // stores the 2x nearest upsampling (into a concatenation's first part), and
 // optionally the 2x2 max pooling of the output (and its window positions).
@@ -343,16 +373,17 @@ fvv_status conv(const ConvLayer& l, const __nv_bfloat16* x, int B, int H, int W,
     return FVV_OK;
 }
 
-// weight and bias gradients of layer l, and its input gradient (masked).  The
-// input gradient is the convolution of dz with the flipped weights
-// wt[ci][ky][kx][co]; for a concatenated input (split > 0) it runs once per
-// part, ci in [0, split) and [split, cin), into channel slices of dx.
-fvv_status conv_bwd(const ConvLayer& l, const __nv_bfloat16* x, const __nv_bfloat16* dz, int B, int H, int W,
-                    __nv_bfloat16* dx, const __nv_bfloat16* mask, int* err, cudaStream_t s, int split = 0,
-                    int xstride = 0)
+// weight and bias gradients of layer l (tensor cores, written whole), and its
+// input gradient (masked).  The input gradient is the convolution of dz with
+// the flipped weights wt[ci][ky][kx][co]; for a concatenated input (split >
+// 0) it runs once per part, ci in [0, split) and [split, cin), into channel
+// slices of dx.
+fvv_status conv_bwd(const RefineNet& N, const ConvLayer& l, const __nv_bfloat16* x, const __nv_bfloat16* dz, int B,
+                    int H, int W, __nv_bfloat16* dx, const __nv_bfloat16* mask, int* err, cudaStream_t s,
+                    int split = 0, int xstride = 0)
 {
-    FVV_CUDA(launch_wgrad3x3(B, H, W, l.cin, xstride ? xstride : l.cin, l.cout, x, dz, l.gw, s));
-    FVV_CUDA(launch_bias_grad(size_t(B) * H * W, l.cout, dz, l.gb, s));
+    FVV_CUDA(launch_wgrad3x3_tc(B, H, W, l.cin, xstride ? xstride : l.cin, l.cout, x, dz, l.gw, l.gb, N.wscratch,
+                                N.wscratch_floats, err, s));
     if (dx) {
         const int parts = split > 0 ? 2 : 1;
         for (int p = 0; p < parts; ++p) {
@@ -421,28 +452,22 @@ fvv_status backward(RefineNet& N, const fvv_refine_batch& b, int* err, cudaStrea
     const size_t npx = size_t(B) * H * W;
     const int H2 = H / 2, W2 = W / 2, H4 = H / 4, W4 = W / 4;
     const int w1 = N.L[1].cout, w2 = N.L[3].cout, w3 = N.L[5].cout;
-    for (ConvLayer& l : N.L) {
-        FVV_CUDA(cudaMemsetAsync(l.gw, 0, l.nw() * 4, s));
-        FVV_CUDA(cudaMemsetAsync(l.gb, 0, size_t(l.cout) * 4, s));
-    }
-    FVV_CUDA(cudaMemsetAsync(N.gwout, 0, size_t(3) * N.w1 * 4, s));
-    FVV_CUDA(cudaMemsetAsync(N.gbout, 0, 3 * 4, s));
-    FVV_CUDA(cudaMemsetAsync(N.loss, 0, 4, s));
-    FVV_CUDA(launch_head_bwd(npx, w1, N.d1, N.wout, N.s, b.target, N.loss, N.gwout, N.gbout, N.g_d1b, s));
-    FVV_TRY(conv_bwd(N.L[9], N.d1a, N.g_d1b, B, H, W, N.g_d1a, N.d1a, err, s));
-    FVV_TRY(conv_bwd(N.L[8], N.cat1, N.g_d1a, B, H, W, N.g_cat1, nullptr, err, s, w2));
+    FVV_CUDA(launch_head_bwd(npx, w1, N.d1, N.wout, N.s, b.target, N.loss, N.gwout, N.gbout, N.g_d1b, N.wscratch,
+                             N.wscratch_floats, s));
+    FVV_TRY(conv_bwd(N, N.L[9], N.d1a, N.g_d1b, B, H, W, N.g_d1a, N.d1a, err, s));
+    FVV_TRY(conv_bwd(N, N.L[8], N.cat1, N.g_d1a, B, H, W, N.g_cat1, nullptr, err, s, w2));
     FVV_CUDA(launch_up2_concat_bwd(B, H, W, w2, w1, N.g_cat1, N.cat1, w2 + w1, N.g_d2b, N.g_skip1, s));
-    FVV_TRY(conv_bwd(N.L[7], N.d2a, N.g_d2b, B, H2, W2, N.g_d2a, N.d2a, err, s));
-    FVV_TRY(conv_bwd(N.L[6], N.cat2, N.g_d2a, B, H2, W2, N.g_cat2, nullptr, err, s, w3));
+    FVV_TRY(conv_bwd(N, N.L[7], N.d2a, N.g_d2b, B, H2, W2, N.g_d2a, N.d2a, err, s));
+    FVV_TRY(conv_bwd(N, N.L[6], N.cat2, N.g_d2a, B, H2, W2, N.g_cat2, nullptr, err, s, w3));
     FVV_CUDA(launch_up2_concat_bwd(B, H2, W2, w3, w2, N.g_cat2, N.cat2, w3 + w2, N.g_bb, N.g_skip2, s));
-    FVV_TRY(conv_bwd(N.L[5], N.ba, N.g_bb, B, H4, W4, N.g_ba, N.ba, err, s));
-    FVV_TRY(conv_bwd(N.L[4], N.p2, N.g_ba, B, H4, W4, N.g_p2, nullptr, err, s));
+    FVV_TRY(conv_bwd(N, N.L[5], N.ba, N.g_bb, B, H4, W4, N.g_ba, N.ba, err, s));
+    FVV_TRY(conv_bwd(N, N.L[4], N.p2, N.g_ba, B, H4, W4, N.g_p2, nullptr, err, s));
     FVV_CUDA(launch_maxpool2_bwd(B, H2, W2, w2, N.g_p2, N.arg2, N.g_skip2, N.cat2 + w3, w3 + w2, N.g_e2b, s));
-    FVV_TRY(conv_bwd(N.L[3], N.e2a, N.g_e2b, B, H2, W2, N.g_e2a, N.e2a, err, s));
-    FVV_TRY(conv_bwd(N.L[2], N.p1, N.g_e2a, B, H2, W2, N.g_p1, nullptr, err, s));
+    FVV_TRY(conv_bwd(N, N.L[3], N.e2a, N.g_e2b, B, H2, W2, N.g_e2a, N.e2a, err, s));
+    FVV_TRY(conv_bwd(N, N.L[2], N.p1, N.g_e2a, B, H2, W2, N.g_p1, nullptr, err, s));
     FVV_CUDA(launch_maxpool2_bwd(B, H, W, w1, N.g_p1, N.arg1, N.g_skip1, N.cat1 + w2, w2 + w1, N.g_e1b, s));
-    FVV_TRY(conv_bwd(N.L[1], N.e1a, N.g_e1b, B, H, W, N.g_e1a, N.e1a, err, s));
-    FVV_TRY(conv_bwd(N.L[0], N.x0, N.g_e1a, B, H, W, nullptr, nullptr, err, s, 0, kX0Stride));
+    FVV_TRY(conv_bwd(N, N.L[1], N.e1a, N.g_e1b, B, H, W, N.g_e1a, N.e1a, err, s));
+    FVV_TRY(conv_bwd(N, N.L[0], N.x0, N.g_e1a, B, H, W, nullptr, nullptr, err, s, 0, kX0Stride));
     return FVV_OK;
 }
 
@@ -626,6 +651,7 @@ void refine_destroy(fvv_ctx* c)
     free_list(c, N->acts8);
     free_list(c, N->syn);
     free_list(c, N->params);
+    if (N->wscratch) dev_free(c, N->wscratch, N->wscratch_floats * 4);
     delete N;
     c->refine = nullptr;
 }
@@ -691,6 +717,33 @@ fvv_status fvv_unet_conv3x3(const void* x, int32_t n, int32_t h, int32_t w, int3
     a.err = flag;
     FVV_CUDA(fvv::launch_conv3x3(x, n, h, w, cin, wt, cout, a, s));
     return fvv::check_flag(flag, s, "fvv_unet_conv3x3");
+}
+
+fvv_status fvv_unet_wgrad3x3(const void* x, int32_t n, int32_t h, int32_t w, int32_t cin, int32_t xstride,
+                            const void* dz, int32_t cout, float* dw, float* db, void* stream)
+{
+    if (!fvv::on_device(x) || !fvv::on_device(dz) || !fvv::on_device(dw) || (db && !fvv::on_device(db)))
+        return fail(FVV_ERR_INVALID_ARG, "x, dz, dw and db must be device memory");
+    if ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(dz)) & 15u)
+        return fail(FVV_ERR_INVALID_ARG, "x and dz must be 16-byte aligned");
+    if (xstride == 0) xstride = cin;
+    if (n < 1 || h < 1 || w < 1 || cin < 8 || cin % 8 || cin > 4096 || xstride < cin || xstride % 8 ||
+        cout < 8 || cout % 8 || cout > 4096)
+        return fail(FVV_ERR_INVALID_ARG, "need n, h, w >= 1, cin, xstride >= cin and cout multiples of 8");
+    if (uint64_t(n) * h * w >= (uint64_t(1) << 31))
+        return fail(FVV_ERR_INVALID_ARG, "too many pixels");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int* flag = nullptr;
+    FVV_TRY(fvv::device_flag(&flag));
+    const size_t nf = fvv::wgrad_scratch_floats(n, h, w, cin, cout);
+    float* scratch = nullptr;
+    FVV_CUDA(cudaMalloc(&scratch, nf * sizeof(float)));
+    cudaError_t e = fvv::launch_wgrad3x3_tc(n, h, w, cin, xstride, cout, static_cast<const __nv_bfloat16*>(x),
+                                            static_cast<const __nv_bfloat16*>(dz), dw, db, scratch, nf, flag, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(scratch);
+    FVV_CUDA(e);
+    return fvv::check_flag(flag, s, "fvv_unet_wgrad3x3");
 }
 
 fvv_status fvv_unet_conv3x3_e4m3(const void* x, int32_t n, int32_t h, int32_t w, int32_t cin, const void* wt,
@@ -988,6 +1041,7 @@ fvv_status fvv_refine_train_step(fvv_ctx* c, const fvv_refine_batch* b, float lr
     FVV_TRY(fvv::device_flag(&err));
     FVV_TRY(fvv::ensure_acts(c, *N, size_t(b->n) * b->height * b->width));
     FVV_TRY(fvv::ensure_grads(c, *N, size_t(b->n) * b->height * b->width));
+    FVV_TRY(fvv::ensure_wscratch(c, *N, b->n, b->height, b->width));
     FVV_TRY(fvv::forward(*N, *b, err, s, nullptr, 0, nullptr));
     FVV_TRY(fvv::backward(*N, *b, err, s));
     if (lr > 0.0f) FVV_TRY(fvv::adam(*N, lr, s));

@@ -4,6 +4,7 @@
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
 
 namespace fvv {
 
@@ -41,6 +42,9 @@ struct ConvArgs {
     float* head_f32;
 };
 
+// cuTensorMapEncodeTiled from the driver (NULL when it cannot be found).
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder();
+
 bool conv_cout_supported(int cout);
 bool conv_pool_supported(int cout);
 // y = relu?(acc_scale conv3x3(x, w) + bias) [* (mask > 0)]; w is [Cout][3][3][Cin]
@@ -71,9 +75,13 @@ bool head_width_supported(int c1);              // w1 of the 1x1 head: 32, 48 or
 cudaError_t launch_head_fwd(size_t npx, int C1, const __nv_bfloat16* d1, const float* wout, const float* bout,
                             const uint8_t* rgb, float* sbuf, uint8_t* out, int W, size_t out_pitch,
                             float* out_f32, cudaStream_t s);
+// Loss, head gradients (overwritten) and dd1, deterministic: scratch holds
+// head_bwd_scratch_floats() per-warp partial sums.
+constexpr int kHeadPixelsPerWarp = 256;
+size_t head_bwd_scratch_floats(size_t npx, int C1);
 cudaError_t launch_head_bwd(size_t npx, int C1, const __nv_bfloat16* d1, const float* wout, const float* sbuf,
                             const uint8_t* target, float* loss, float* dwout, float* dbout, __nv_bfloat16* dd1,
-                            cudaStream_t s);
+                            float* scratch, size_t scratch_floats, cudaStream_t s);
 // e4m3 inference forms: activations are e4m3 codes with per-tensor scales
 cudaError_t launch_pack_features_e4m3(size_t npx, const uint8_t* rgb, const float* depth, const uint8_t* hole,
                                       const float* top3, float z_far, float s0, uint8_t* out, cudaStream_t s);
@@ -83,9 +91,19 @@ cudaError_t launch_head_fwd_e4m3(size_t npx, int C1, const uint8_t* d1, float s_
                                  float* out_f32, cudaStream_t s);
 // out = max(out, max |x|) over npix pixels of C channels, pixel stride ld
 cudaError_t launch_amax(size_t npix, int C, const __nv_bfloat16* x, int ld, float* out, cudaStream_t s);
-cudaError_t launch_wgrad3x3(int B, int H, int W, int Cin, int xstride, int Cout, const __nv_bfloat16* x,
-                            const __nv_bfloat16* dz, float* dw, cudaStream_t s);
-cudaError_t launch_bias_grad(size_t npx, int C, const __nv_bfloat16* dz, float* db, cudaStream_t s);
+
+// fvv_unet_wgrad.cu (tensor cores): dw[co][3][3][ci] and db[co] (both
+// overwritten, fp32) of a 3x3 convolution from its input x ([B][H][W] pixels
+// of xstride channels, the first Cin used) and output gradient dz
+// ([B][H][W][Cout]).  Cin, xstride and Cout multiples of 8; x, dz 16-byte
+// aligned.  scratch holds the per-split partial sums: wgrad_scratch_floats()
+// floats give the full split count, fewer give fewer splits (at least
+// Cout * (9 Cin + 1) floats).  err: device flag raised when a bounded wait
+// runs out.  db may be NULL.
+size_t wgrad_scratch_floats(int B, int H, int W, int Cin, int Cout);
+cudaError_t launch_wgrad3x3_tc(int B, int H, int W, int Cin, int xstride, int Cout, const __nv_bfloat16* x,
+                               const __nv_bfloat16* dz, float* dw, float* db, float* scratch,
+                               size_t scratch_floats, int* err, cudaStream_t s);
 cudaError_t launch_flip_weights(int Cout, int Cin, const float* w, __nv_bfloat16* wbf, __nv_bfloat16* wt,
                                 cudaStream_t s);
 cudaError_t launch_adam(size_t n, float* w, const float* g, float* m, float* v, float lr, int t, cudaStream_t s);

@@ -920,6 +920,8 @@ cudaError_t dispatch(const void* x, const void* w, int Cout, const ConvArgs& a, 
 
 }  // namespace
 
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() { return encode_fn(); }
+
 bool conv_cout_supported(int cout)
 {
     return cout == 32 || cout == 48 || cout == 64 || cout == 96 || cout == 128 || cout == 192;

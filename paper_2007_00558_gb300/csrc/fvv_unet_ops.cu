@@ -16,19 +16,6 @@ namespace {
 
 __device__ __forceinline__ float bf(const __nv_bfloat16 v) { return __bfloat162float(v); }
 
-__device__ __forceinline__ float block_sum(float v, float* red)
-{
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    __syncthreads();
-    if (lane == 0) red[wid] = v;
-    __syncthreads();
-    float s = 0.0f;
-    if (threadIdx.x == 0)
-        for (int i = 0; i < int(blockDim.x >> 5); ++i) s += red[i];
-    return s;                                   // valid in thread 0
-}
-
 // ---- input features ----------------------------------------------------------
 // 8 channels: RGB / 255, depth / z_far, hole, top-3 weights, stored in one
 // 64-byte row per pixel (bf16: channels 8..31 zero; e4m3: bytes 8..63 zero) so
@@ -332,230 +319,100 @@ __global__ void k_head_fwd(size_t npx, const T* __restrict__ d1, float s_d1, con
 }
 
 // Loss and the head's backward pass.  diff = clamp(s) - target / 255;
-// loss += sum diff^2 (scaled by inv_count); ds = 2 diff inv_count on 0 < s < 1;
-// dW += ds d1^T; db += ds; dd1 = (W^T ds) * (d1 > 0).
+// loss = sum diff^2 inv_count; ds = 2 diff inv_count on 0 < s < 1;
+// dW = ds d1^T; db = ds; dd1 = (W^T ds) * (d1 > 0).  Deterministic: warp g
+// reduces the fixed pixel range [g ppw, (g + 1) ppw) in pixel order (lane k
+// owns output channels k and k + 32 of d1) and writes its partial sums to
+// part[g][3 C1 + 4] (dW, db, loss); k_head_reduce adds them in warp order.
 template <int C1>
-__global__ void k_head_bwd(size_t npx, const __nv_bfloat16* __restrict__ d1, const float* __restrict__ wout,
-                           const float* __restrict__ s, const uint8_t* __restrict__ target, float inv_count,
-                           float* __restrict__ loss, float* __restrict__ dwout, float* __restrict__ dbout,
-                           __nv_bfloat16* __restrict__ dd1)
+__global__ void __launch_bounds__(128) k_head_bwd(size_t npx, const __nv_bfloat16* __restrict__ d1,
+                                                  const float* __restrict__ wout, const float* __restrict__ s,
+                                                  const uint8_t* __restrict__ target, float inv_count, size_t ppw,
+                                                  float* __restrict__ part, __nv_bfloat16* __restrict__ dd1)
 {
+    constexpr int KPL = (C1 + 31) / 32;                 // d1 channels per lane
     __shared__ float sw[3 * C1];
-    __shared__ float acc[3 * C1 + 3 + 1];
-    __shared__ float red[32];
     for (int i = threadIdx.x; i < 3 * C1; i += blockDim.x) sw[i] = wout[i];
-    for (int i = threadIdx.x; i < 3 * C1 + 4; i += blockDim.x) acc[i] = 0.0f;
     __syncthreads();
-    const size_t p = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    float l = 0.0f;
-    if (p < npx) {
-        float a[C1];
-        load_d1<C1>(d1, p, a);
-        float ds[3];
+    const int lane = threadIdx.x & 31;
+    const size_t gw = (size_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const size_t p0 = gw * ppw;
+    if (p0 >= npx) return;                              // whole warps leave together
+    const size_t p1 = min(npx, p0 + ppw);
+    float aw[3][KPL] = {}, ab[3] = {0.0f, 0.0f, 0.0f}, l = 0.0f;
+    for (size_t base = p0; base < p1; base += 32) {
+        const size_t p = base + lane;
+        float ds[3] = {0.0f, 0.0f, 0.0f};
+        if (p < p1) {
+            float a[C1];
+            load_d1<C1>(d1, p, a);
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            const float sv = s[3 * p + c];
-            const float d = fminf(fmaxf(sv, 0.0f), 1.0f) - float(target[3 * p + c]) * (1.0f / 255.0f);
-            l += d * d;
-            ds[c] = (sv > 0.0f && sv < 1.0f) ? 2.0f * d * inv_count : 0.0f;
-            atomicAdd(&acc[3 * C1 + c], ds[c]);
-        }
-        float g[C1];
-#pragma unroll
-        for (int k = 0; k < C1; ++k) {
-            const float v = sw[k] * ds[0] + sw[C1 + k] * ds[1] + sw[2 * C1 + k] * ds[2];
-            g[k] = a[k] > 0.0f ? v : 0.0f;
-        }
-        uint4* dst = reinterpret_cast<uint4*>(dd1 + size_t(C1) * p);
-#pragma unroll
-        for (int v = 0; v < C1 / 8; ++v) dst[v] = pack8(g + 8 * v);
-#pragma unroll
-        for (int c = 0; c < 3; ++c)
-            if (ds[c] != 0.0f)
-#pragma unroll 4
-                for (int k = 0; k < C1; ++k) atomicAdd(&acc[C1 * c + k], ds[c] * a[k]);
-    }
-    const float bl = block_sum(l, red);
-    __syncthreads();
-    if (threadIdx.x == 0) atomicAdd(loss, bl * inv_count);
-    for (int i = threadIdx.x; i < 3 * C1 + 3; i += blockDim.x) {
-        const float v = acc[i];
-        if (v != 0.0f) atomicAdd(i < 3 * C1 ? &dwout[i] : &dbout[i - 3 * C1], v);
-    }
-}
-
-// ---- weight gradients of a 3x3 convolution --------------------------------------
-// dw[co][ky][kx][ci] += sum_p dz[p][co] * x[p + (ky-1, kx-1)][ci]  (zero outside).
-// CTA = a BCO (co) x BCI (ci) block of one tap over a slice of pixel rows;
-// each thread owns 2 x 2 outputs; 64 pixels are staged in shared memory at a
-// time.  BCO, BCI in {32, 16, 8} divide Cout and Cin.
-constexpr int kWgPix = 64;
-template <int BCO, int BCI>
-__global__ void __launch_bounds__(BCO * BCI / 4) k_wgrad3x3(int B, int H, int W, int Cin, int xs_, int Cout,
-                                                           const __nv_bfloat16* __restrict__ x,
-                                                           const __nv_bfloat16* __restrict__ dz,
-                                                           float* __restrict__ dw, int rows_per_cta)
-{
-    constexpr int NT = BCO * BCI / 4;
-    __shared__ float sz[kWgPix][BCO + 1];
-    __shared__ float sx[kWgPix][BCI + 1];
-    const int co_blocks = Cout / BCO, ci_blocks = Cin / BCI;
-    int t = blockIdx.x;
-    const int cib = t % ci_blocks;
-    t /= ci_blocks;
-    const int cob = t % co_blocks;
-    const int tap = t / co_blocks;
-    const int ky = tap / 3, kx = tap - 3 * ky;
-    const int tid = threadIdx.x;
-    const int tco = (tid / (BCI / 2)) * 2, tci = (tid % (BCI / 2)) * 2;
-    float a00 = 0.f, a01 = 0.f, a10 = 0.f, a11 = 0.f;
-    const long total_rows = long(B) * H;
-    const long r0 = long(blockIdx.y) * rows_per_cta;
-    const long r1 = min(total_rows, r0 + rows_per_cta);
-    for (long r = r0; r < r1; ++r) {
-        const int b = int(r / H), yy = int(r % H);
-        const int ys = yy + ky - 1;
-        for (int x0 = 0; x0 < W; x0 += kWgPix) {
-            __syncthreads();
-            for (int i = tid; i < kWgPix * BCO; i += NT) {
-                const int pp = i / BCO, c = i % BCO;
-                const int xx = x0 + pp;
-                sz[pp][c] = xx < W ? bf(dz[((size_t(b) * H + yy) * W + xx) * Cout + cob * BCO + c]) : 0.0f;
+            for (int c = 0; c < 3; ++c) {
+                const float sv = s[3 * p + c];
+                const float d = fminf(fmaxf(sv, 0.0f), 1.0f) - float(target[3 * p + c]) * (1.0f / 255.0f);
+                l += d * d;
+                ds[c] = (sv > 0.0f && sv < 1.0f) ? 2.0f * d * inv_count : 0.0f;
             }
-            for (int i = tid; i < kWgPix * BCI; i += NT) {
-                const int pp = i / BCI, c = i % BCI;
-                const int xx = x0 + pp, xs = xx + kx - 1;
-                float xv = 0.0f;
-                if (xx < W && ys >= 0 && ys < H && xs >= 0 && xs < W)
-                    xv = bf(x[((size_t(b) * H + ys) * W + xs) * xs_ + cib * BCI + c]);
-                sx[pp][c] = xv;
+            float g[C1];
+#pragma unroll
+            for (int k = 0; k < C1; ++k) {
+                const float v = sw[k] * ds[0] + sw[C1 + k] * ds[1] + sw[2 * C1 + k] * ds[2];
+                g[k] = a[k] > 0.0f ? v : 0.0f;
             }
-            __syncthreads();
-#pragma unroll 8
-            for (int pp = 0; pp < kWgPix; ++pp) {
-                const float z0 = sz[pp][tco], z1 = sz[pp][tco + 1];
-                const float x0v = sx[pp][tci], x1v = sx[pp][tci + 1];
-                a00 += z0 * x0v;
-                a01 += z0 * x1v;
-                a10 += z1 * x0v;
-                a11 += z1 * x1v;
-            }
+            uint4* dst = reinterpret_cast<uint4*>(dd1 + size_t(C1) * p);
+#pragma unroll
+            for (int v = 0; v < C1 / 8; ++v) dst[v] = pack8(g + 8 * v);
         }
-    }
-    const size_t K = size_t(9) * Cin;
-    const size_t o0 = size_t(cob * BCO + tco) * K + size_t(tap) * Cin + cib * BCI + tci;
-    atomicAdd(&dw[o0], a00);
-    atomicAdd(&dw[o0 + 1], a01);
-    atomicAdd(&dw[o0 + K], a10);
-    atomicAdd(&dw[o0 + K + 1], a11);
-}
-
-// The same sum for 32 x 32 (co x ci) blocks with every thread owning 4 x 4
-// outputs: per staged pixel two 16-byte shared-memory reads feed 16 FMAs
-// (the 2 x 2 form above does one read per FMA).  64 threads per CTA; dz and
-// x rows are staged 64 pixels at a time as fp32 with 16-byte loads.
-constexpr int kWgPix4 = 64;
-__global__ void __launch_bounds__(64) k_wgrad3x3_r4(int B, int H, int W, int Cin, int xs_, int Cout,
-                                                    const __nv_bfloat16* __restrict__ x,
-                                                    const __nv_bfloat16* __restrict__ dz, float* __restrict__ dw,
-                                                    int rows_per_cta)
-{
-    __shared__ __align__(16) float sz[kWgPix4][32];
-    __shared__ __align__(16) float sx[kWgPix4][32];
-    const int co_blocks = Cout / 32, ci_blocks = Cin / 32;
-    int t = blockIdx.x;
-    const int cib = t % ci_blocks;
-    t /= ci_blocks;
-    const int cob = t % co_blocks;
-    const int tap = t / co_blocks;
-    const int ky = tap / 3, kx = tap - 3 * ky;
-    const int tid = threadIdx.x;
-    const int tco = (tid >> 3) * 4, tci = (tid & 7) * 4;
-    float acc[4][4];
+        const int nj = int(min(size_t(32), p1 - base));
+        for (int j = 0; j < nj; ++j) {
+            const float e0 = __shfl_sync(0xffffffffu, ds[0], j);
+            const float e1 = __shfl_sync(0xffffffffu, ds[1], j);
+            const float e2 = __shfl_sync(0xffffffffu, ds[2], j);
+            const __nv_bfloat16* row = d1 + size_t(C1) * (base + j);
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = 0.0f;
-    const long total_rows = long(B) * H;
-    const long r0 = long(blockIdx.y) * rows_per_cta;
-    const long r1 = min(total_rows, r0 + rows_per_cta);
-    for (long r = r0; r < r1; ++r) {
-        const int b = int(r / H), yy = int(r % H);
-        const int ys = yy + ky - 1;
-        for (int x0 = 0; x0 < W; x0 += kWgPix4) {
-            __syncthreads();
-            for (int i = tid; i < kWgPix4 * 4; i += 64) {
-                const int pp = i >> 2, q = i & 3;                 // pixel, 8-channel quarter
-                const int xx = x0 + pp, xs = xx + kx - 1;
-                float fz[8], fx[8];
-                if (xx < W) {
-                    unpack8(*reinterpret_cast<const uint4*>(dz + ((size_t(b) * H + yy) * W + xx) * Cout + cob * 32 + 8 * q), fz);
-                } else {
-#pragma unroll
-                    for (int k = 0; k < 8; ++k) fz[k] = 0.0f;
+            for (int q = 0; q < KPL; ++q) {
+                const int k = lane + 32 * q;
+                if (k < C1) {
+                    const float a = __bfloat162float(row[k]);
+                    aw[0][q] += e0 * a;
+                    aw[1][q] += e1 * a;
+                    aw[2][q] += e2 * a;
                 }
-                if (xx < W && ys >= 0 && ys < H && xs >= 0 && xs < W) {
-                    unpack8(*reinterpret_cast<const uint4*>(x + ((size_t(b) * H + ys) * W + xs) * xs_ + cib * 32 + 8 * q), fx);
-                } else {
-#pragma unroll
-                    for (int k = 0; k < 8; ++k) fx[k] = 0.0f;
-                }
-                float4* dzs = reinterpret_cast<float4*>(&sz[pp][8 * q]);
-                float4* dxs = reinterpret_cast<float4*>(&sx[pp][8 * q]);
-                dzs[0] = make_float4(fz[0], fz[1], fz[2], fz[3]);
-                dzs[1] = make_float4(fz[4], fz[5], fz[6], fz[7]);
-                dxs[0] = make_float4(fx[0], fx[1], fx[2], fx[3]);
-                dxs[1] = make_float4(fx[4], fx[5], fx[6], fx[7]);
             }
-            __syncthreads();
-#pragma unroll 4
-            for (int pp = 0; pp < kWgPix4; ++pp) {
-                const float4 z = *reinterpret_cast<const float4*>(&sz[pp][tco]);
-                const float4 v = *reinterpret_cast<const float4*>(&sx[pp][tci]);
-                const float zz[4] = {z.x, z.y, z.z, z.w}, xv[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-                for (int i = 0; i < 4; ++i)
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) acc[i][j] += zz[i] * xv[j];
-            }
+            ab[0] += e0;
+            ab[1] += e1;
+            ab[2] += e2;
         }
     }
-    const size_t K = size_t(9) * Cin;
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
+    float* out = part + gw * (3 * C1 + 4);
 #pragma unroll
-        for (int j = 0; j < 4; ++j)
-            atomicAdd(&dw[size_t(cob * 32 + tco + i) * K + size_t(tap) * Cin + cib * 32 + tci + j], acc[i][j]);
+    for (int q = 0; q < KPL; ++q) {
+        const int k = lane + 32 * q;
+        if (k < C1)
+            for (int c = 0; c < 3; ++c) out[C1 * c + k] = aw[c][q];
+    }
+    if (lane == 0) {
+        out[3 * C1 + 0] = ab[0];
+        out[3 * C1 + 1] = ab[1];
+        out[3 * C1 + 2] = ab[2];
+        out[3 * C1 + 3] = l * inv_count;
+    }
 }
 
-// db[co] += sum_p dz[p][co]
-__global__ void __launch_bounds__(256) k_bias_grad(size_t npx, int C, const __nv_bfloat16* __restrict__ dz,
-                                                   float* __restrict__ db, size_t px_per_cta)
+// dwout[3 C1], dbout[3], loss = the sums of the warps' partials, in warp order
+__global__ void k_head_reduce(const float* __restrict__ part, size_t nwarps, int C1, float* __restrict__ dwout,
+                              float* __restrict__ dbout, float* __restrict__ loss)
 {
-    // thread = (pixel lane l, 8-channel group g): 16-byte loads, 8 partial
-    // sums; the lanes are summed in shared memory, one atomic per channel
-    __shared__ float part[256 * 8];
-    const int G = C / 8, R = 256 / G;
-    const int g = threadIdx.x % G, l = threadIdx.x / G;
-    float a[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    const size_t p0 = size_t(blockIdx.x) * px_per_cta;
-    const size_t p1 = p0 + px_per_cta < npx ? p0 + px_per_cta : npx;
-    if (l < R) {
-        for (size_t p = p0 + l; p < p1; p += R) {
-            float f[8];
-            unpack8(*reinterpret_cast<const uint4*>(dz + p * C + 8 * g), f);
-#pragma unroll
-            for (int j = 0; j < 8; ++j) a[j] += f[j];
-        }
-#pragma unroll
-        for (int j = 0; j < 8; ++j) part[l * C + 8 * g + j] = a[j];
-    }
-    __syncthreads();
-    for (int c = threadIdx.x; c < C; c += blockDim.x) {
-        float t = 0.0f;
-        for (int k = 0; k < R; ++k) t += part[k * C + c];
-        atomicAdd(&db[c], t);
-    }
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int nv = 3 * C1 + 4;
+    if (i >= nv) return;
+    float a = 0.0f;
+    for (size_t g = 0; g < nwarps; ++g) a += part[g * nv + i];
+    if (i < 3 * C1) dwout[i] = a;
+    else if (i < 3 * C1 + 3) dbout[i - 3 * C1] = a;
+    else *loss = a;
 }
 
 // wt[ci][ky][kx][co] = w[co][2-ky][2-kx][ci] (bf16), the weights of the
@@ -670,17 +527,30 @@ cudaError_t launch_head_fwd_e4m3(size_t npx, int C1, const uint8_t* d1, float s_
     return cudaGetLastError();
 }
 
+size_t head_bwd_scratch_floats(size_t npx, int C1)
+{
+    const size_t nwarps = (npx + kHeadPixelsPerWarp - 1) / kHeadPixelsPerWarp;
+    return nwarps * size_t(3 * C1 + 4);
+}
+
 cudaError_t launch_head_bwd(size_t npx, int C1, const __nv_bfloat16* d1, const float* wout, const float* sbuf,
                             const uint8_t* target, float* loss, float* dwout, float* dbout, __nv_bfloat16* dd1,
-                            cudaStream_t s)
+                            float* scratch, size_t scratch_floats, cudaStream_t s)
 {
+    if (npx == 0 || !scratch || scratch_floats < head_bwd_scratch_floats(npx, C1)) return cudaErrorInvalidValue;
     const float inv = 1.0f / float(npx * 3);
+    const size_t ppw = kHeadPixelsPerWarp;
+    const size_t nwarps = (npx + ppw - 1) / ppw;
+    const unsigned grid = unsigned((nwarps + 3) / 4);
     switch (C1) {
-    case 32: k_head_bwd<32><<<blocks(npx, 128), 128, 0, s>>>(npx, d1, wout, sbuf, target, inv, loss, dwout, dbout, dd1); break;
-    case 48: k_head_bwd<48><<<blocks(npx, 128), 128, 0, s>>>(npx, d1, wout, sbuf, target, inv, loss, dwout, dbout, dd1); break;
-    case 64: k_head_bwd<64><<<blocks(npx, 128), 128, 0, s>>>(npx, d1, wout, sbuf, target, inv, loss, dwout, dbout, dd1); break;
+    case 32: k_head_bwd<32><<<grid, 128, 0, s>>>(npx, d1, wout, sbuf, target, inv, ppw, scratch, dd1); break;
+    case 48: k_head_bwd<48><<<grid, 128, 0, s>>>(npx, d1, wout, sbuf, target, inv, ppw, scratch, dd1); break;
+    case 64: k_head_bwd<64><<<grid, 128, 0, s>>>(npx, d1, wout, sbuf, target, inv, ppw, scratch, dd1); break;
     default: return cudaErrorInvalidValue;
     }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_head_reduce<<<unsigned((3 * C1 + 4 + 127) / 128), 128, 0, s>>>(scratch, nwarps, C1, dwout, dbout, loss);
     return cudaGetLastError();
 }
 
@@ -705,59 +575,6 @@ cudaError_t launch_maxpool2_e4m3(int B, int H, int W, int C, const uint8_t* x, i
 {
     const size_t n = size_t(B) * (H / 2) * (W / 2) * (C / 16);
     k_maxpool2_e4m3<<<blocks(n, 256), 256, 0, s>>>(B, H, W, C, x, ldx, y);
-    return cudaGetLastError();
-}
-
-template <int BCO, int BCI>
-cudaError_t wgrad_blocks(int B, int H, int W, int Cin, int xst, int Cout, const __nv_bfloat16* x,
-                         const __nv_bfloat16* dz, float* dw, cudaStream_t s)
-{
-    const int tiles = 9 * (Cout / BCO) * (Cin / BCI);
-    const long rows = long(B) * H;
-    // split the rows so that about 4 waves of CTAs cover the GPU
-    long splits = (4L * device_sms() * 4 * (1024 / (BCO * BCI)) + tiles - 1) / tiles;
-    if (splits > rows) splits = rows;
-    if (splits < 1) splits = 1;
-    const int rpc = int((rows + splits - 1) / splits);
-    dim3 grid(unsigned(tiles), unsigned((rows + rpc - 1) / rpc));
-    k_wgrad3x3<BCO, BCI><<<grid, BCO * BCI / 4, 0, s>>>(B, H, W, Cin, xst, Cout, x, dz, dw, rpc);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_wgrad3x3(int B, int H, int W, int Cin, int xstride, int Cout, const __nv_bfloat16* x,
-                            const __nv_bfloat16* dz, float* dw, cudaStream_t s)
-{
-    if (Cout % 16 || Cin % 8 || xstride < Cin) return cudaErrorInvalidValue;
-    if (Cout % 32 == 0 && Cin % 32 == 0 && xstride % 8 == 0 &&
-        ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(dz)) & 15) == 0) {
-        const int tiles = 9 * (Cout / 32) * (Cin / 32);
-        const long rows = long(B) * H;
-        long splits = (long(device_sms()) * 16 + tiles - 1) / tiles;   // about 16 CTAs of 64 threads per SM
-        if (splits > rows) splits = rows;
-        if (splits < 1) splits = 1;
-        const int rpc = int((rows + splits - 1) / splits);
-        dim3 grid(unsigned(tiles), unsigned((rows + rpc - 1) / rpc));
-        k_wgrad3x3_r4<<<grid, 64, 0, s>>>(B, H, W, Cin, xstride, Cout, x, dz, dw, rpc);
-        return cudaGetLastError();
-    }
-    if (Cout % 32 == 0) {
-        if (Cin % 32 == 0) return wgrad_blocks<32, 32>(B, H, W, Cin, xstride, Cout, x, dz, dw, s);
-        if (Cin % 16 == 0) return wgrad_blocks<32, 16>(B, H, W, Cin, xstride, Cout, x, dz, dw, s);
-        return wgrad_blocks<32, 8>(B, H, W, Cin, xstride, Cout, x, dz, dw, s);
-    }
-    if (Cin % 32 == 0) return wgrad_blocks<16, 32>(B, H, W, Cin, xstride, Cout, x, dz, dw, s);
-    if (Cin % 16 == 0) return wgrad_blocks<16, 16>(B, H, W, Cin, xstride, Cout, x, dz, dw, s);
-    return wgrad_blocks<16, 8>(B, H, W, Cin, xstride, Cout, x, dz, dw, s);
-}
-
-cudaError_t launch_bias_grad(size_t npx, int C, const __nv_bfloat16* dz, float* db, cudaStream_t s)
-{
-    if (C % 8 || C > 2048 || (reinterpret_cast<uintptr_t>(dz) & 15)) return cudaErrorInvalidValue;
-    // about eight CTAs per SM, at least 256 pixels each
-    const size_t nblk = size_t(device_sms()) * 8;
-    size_t per = (npx + nblk - 1) / nblk;
-    if (per < 256) per = 256;
-    k_bias_grad<<<blocks(npx, int(per)), 256, 0, s>>>(npx, C, dz, db, per);
     return cudaGetLastError();
 }
 

@@ -148,6 +148,7 @@ def load() -> C.CDLL:
             "fvv_serve_stats": [P, C.POINTER(fvv_serve_report), I],
             "fvv_serve_stop": [P],
             "fvv_unet_conv3x3": [P, I, I, I, I, P, P, I, I, P, P, P],
+            "fvv_unet_wgrad3x3": [P, I, I, I, I, I, P, I, P, P, P],
             "fvv_selftest_bounded_wait": [I, C.c_uint32, P],
             "fvv_unet_conv3x3_e4m3": [P, I, I, I, I, P, P, I, I, C.c_float, C.c_float, P, P],
             "fvv_unet_conv3x3_pool": [P, I, I, I, I, P, P, I, I, C.c_float, C.c_float, P, P, P, P],
@@ -422,6 +423,13 @@ def fvv_serve_stats(ctx: int, reset: bool = False) -> dict:
 
 def fvv_serve_stop(ctx: int) -> None:
     _check(load().fvv_serve_stop(ctx), "fvv_serve_stop")
+
+
+def fvv_unet_wgrad3x3(x, n: int, h: int, w: int, cin: int, xstride: int, dz, cout: int, dw, db,
+                      stream=None) -> None:
+    """Weight (and bias) gradients of a 3x3 convolution on the tensor cores."""
+    _check(load().fvv_unet_wgrad3x3(ptr(x), n, h, w, cin, xstride, ptr(dz), cout, ptr(dw), ptr(db),
+                                    stream_handle(stream)), "fvv_unet_wgrad3x3")
 
 
 def fvv_unet_conv3x3(x, n: int, h: int, w: int, cin: int, wt, bias, cout: int, relu: bool, mask, y,
