@@ -616,13 +616,26 @@ fvv_status quantize_weights(RefineNet& N, cudaStream_t s)
 fvv_status adam(RefineNet& N, float lr, cudaStream_t s)
 {
     const int t = ++N.step;
+    // every tensor in one launch; the 3x3 weights refresh their bf16 copies
+    // (and the flipped transposes of the input gradients) as they update
+    AdamList L{};
+    auto add = [&](float* w, const float* g, float* m, float* v, size_t n, __nv_bfloat16* wbf,
+                   __nv_bfloat16* wt, int cout, int cin) {
+        AdamTensor& T = L.t[L.count];
+        T = AdamTensor{w, g, m, v, wbf, wt, cout, cin};
+        L.off[L.count + 1] = L.off[L.count] + n;
+        ++L.count;
+    };
     for (ConvLayer& l : N.L) {
-        FVV_CUDA(launch_adam(l.nw(), l.w, l.gw, l.mw, l.vw, lr, t, s));
-        FVV_CUDA(launch_adam(size_t(l.cout), l.b, l.gb, l.mb, l.vb, lr, t, s));
+        add(l.w, l.gw, l.mw, l.vw, l.nw(), l.wbf, l.wt, l.cout, l.cin);
+        add(l.b, l.gb, l.mb, l.vb, size_t(l.cout), nullptr, nullptr, 0, 1);
     }
-    FVV_CUDA(launch_adam(size_t(3) * N.w1, N.wout, N.gwout, N.mwo, N.vwo, lr, t, s));
-    FVV_CUDA(launch_adam(3, N.bout, N.gbout, N.mbo, N.vbo, lr, t, s));
-    return refresh_weights(N, s);
+    add(N.wout, N.gwout, N.mwo, N.vwo, size_t(3) * N.w1, nullptr, nullptr, 0, 1);
+    add(N.bout, N.gbout, N.mbo, N.vbo, 3, nullptr, nullptr, 0, 1);
+    FVV_CUDA(launch_adam_multi(L, lr, t, s));
+    N.q_ready = false;                        // e4m3 weights are stale
+    N.precision = FVV_PREC_BF16;
+    return FVV_OK;
 }
 
 fvv_status check_batch(const RefineNet& N, const fvv_refine_batch* b, bool need_target)

@@ -106,6 +106,28 @@ cudaError_t launch_wgrad3x3_tc(int B, int H, int W, int Cin, int xstride, int Co
                                size_t scratch_floats, int* err, cudaStream_t s);
 cudaError_t launch_flip_weights(int Cout, int Cin, const float* w, __nv_bfloat16* wbf, __nv_bfloat16* wt,
                                 cudaStream_t s);
-cudaError_t launch_adam(size_t n, float* w, const float* g, float* m, float* v, float lr, int t, cudaStream_t s);
+// out = sum over splits of part[split][n] in a fixed order (see fvv_unet_ops.cu);
+// element i goes to out0[i] (i < n0), out1[i - n0] (i < n0 + n1), else out2.
+cudaError_t launch_sum_splits(const float* part, int splits, size_t n, float* out0, size_t n0, float* out1,
+                              size_t n1, float* out2, cudaStream_t s);
+
+// Adam over several tensors in one launch (weights of 3x3 layers also
+// refresh their bf16 copy wbf and flipped transpose wt when those are set).
+constexpr int kAdamMaxTensors = 24;
+struct AdamTensor {
+    float* w;
+    const float* g;
+    float* m;
+    float* v;
+    __nv_bfloat16* wbf;      // or NULL
+    __nv_bfloat16* wt;       // or NULL
+    int cout, cin;
+};
+struct AdamList {
+    AdamTensor t[kAdamMaxTensors];
+    size_t off[kAdamMaxTensors + 1];  // prefix sums of the element counts
+    int count;
+};
+cudaError_t launch_adam_multi(const AdamList& L, float lr, int t, cudaStream_t s);
 
 }  // namespace fvv

@@ -323,7 +323,7 @@ __global__ void k_head_fwd(size_t npx, const T* __restrict__ d1, float s_d1, con
 // dW = ds d1^T; db = ds; dd1 = (W^T ds) * (d1 > 0).  Deterministic: warp g
 // reduces the fixed pixel range [g ppw, (g + 1) ppw) in pixel order (lane k
 // owns output channels k and k + 32 of d1) and writes its partial sums to
-// part[g][3 C1 + 4] (dW, db, loss); k_head_reduce adds them in warp order.
+// part[g][3 C1 + 4] (dW, db, loss); launch_sum_splits adds them in warp order.
 template <int C1>
 __global__ void __launch_bounds__(128) k_head_bwd(size_t npx, const __nv_bfloat16* __restrict__ d1,
                                                   const float* __restrict__ wout, const float* __restrict__ s,
@@ -401,18 +401,33 @@ __global__ void __launch_bounds__(128) k_head_bwd(size_t npx, const __nv_bfloat1
     }
 }
 
-// dwout[3 C1], dbout[3], loss = the sums of the warps' partials, in warp order
-__global__ void k_head_reduce(const float* __restrict__ part, size_t nwarps, int C1, float* __restrict__ dwout,
-                              float* __restrict__ dbout, float* __restrict__ loss)
+// Deterministic sum over splits: out[i] = sum_s part[s][i] (i < n), with a
+// fixed association: warp g of a block sums the splits g, g + 8, ... in
+// order for 32 consecutive elements, then the eight warp sums are added in
+// warp order.  Element i goes to out0[i] (i < n0), out1[i - n0] (i < n0 + n1)
+// or out2[i - n0 - n1]; a NULL output is skipped.
+__global__ void __launch_bounds__(256) k_sum_splits(const float* __restrict__ part, int splits, size_t n,
+                                                    float* out0, size_t n0, float* out1, size_t n1, float* out2)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int nv = 3 * C1 + 4;
-    if (i >= nv) return;
+    __shared__ float red[8][32];
+    const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
+    const size_t i = size_t(blockIdx.x) * 32 + lane;
     float a = 0.0f;
-    for (size_t g = 0; g < nwarps; ++g) a += part[g * nv + i];
-    if (i < 3 * C1) dwout[i] = a;
-    else if (i < 3 * C1 + 3) dbout[i - 3 * C1] = a;
-    else *loss = a;
+    if (i < n)
+        for (int sp = g; sp < splits; sp += 8) a += part[size_t(sp) * n + i];
+    red[g][lane] = a;
+    __syncthreads();
+    if (g != 0 || i >= n) return;
+    float t = red[0][lane];
+#pragma unroll
+    for (int w = 1; w < 8; ++w) t += red[w][lane];
+    if (i < n0) {
+        if (out0) out0[i] = t;
+    } else if (i < n0 + n1) {
+        if (out1) out1[i - n0] = t;
+    } else if (out2) {
+        out2[i - n0 - n1] = t;
+    }
 }
 
 // wt[ci][ky][kx][co] = w[co][2-ky][2-kx][ci] (bf16), the weights of the
@@ -431,17 +446,37 @@ __global__ void k_flip_weights(int Cout, int Cin, const float* __restrict__ w, _
     if (wt) wt[(size_t(ci) * 9 + (8 - tap)) * Cout + co] = v;
 }
 
-__global__ void k_adam(size_t n, float* __restrict__ w, const float* __restrict__ g, float* __restrict__ m,
-                       float* __restrict__ v, float lr, float b1, float b2, float eps, float c1, float c2)
+// Adam over every parameter tensor of the network in one launch; for a 3x3
+// layer's weights also the bf16 copy and its flipped transpose (as
+// k_flip_weights).  Element e of the concatenation lies in the tensor k with
+// off[k] <= e < off[k + 1].
+__global__ void k_adam_multi(AdamList L, float lr, float b1, float b2, float eps, float c1, float c2)
 {
-    const size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const float gi = g[i];
-    const float mi = b1 * m[i] + (1.0f - b1) * gi;
-    const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
-    m[i] = mi;
-    v[i] = vi;
-    w[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    const size_t stride = size_t(gridDim.x) * blockDim.x;
+    for (size_t e = size_t(blockIdx.x) * blockDim.x + threadIdx.x; e < L.off[L.count]; e += stride) {
+        int lo = 0, hi = L.count - 1;                    // the last k with off[k] <= e
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (L.off[mid] <= e) lo = mid; else hi = mid - 1;
+        }
+        const AdamTensor& T = L.t[lo];
+        const size_t i = e - L.off[lo];
+        const float gi = T.g[i];
+        const float mi = b1 * T.m[i] + (1.0f - b1) * gi;
+        const float vi = b2 * T.v[i] + (1.0f - b2) * gi * gi;
+        T.m[i] = mi;
+        T.v[i] = vi;
+        const float w = T.w[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+        T.w[i] = w;
+        if (T.wbf) {
+            const int ci = int(i % T.cin);
+            const int tap = int((i / T.cin) % 9);
+            const int co = int(i / (size_t(9) * T.cin));
+            const __nv_bfloat16 v = __float2bfloat16_rn(w);
+            T.wbf[i] = v;
+            if (T.wt) T.wt[(size_t(ci) * 9 + (8 - tap)) * T.cout + co] = v;
+        }
+    }
 }
 
 // out = max(out, max |x|) over npix pixels of C channels at pixel stride ld
@@ -550,8 +585,7 @@ cudaError_t launch_head_bwd(size_t npx, int C1, const __nv_bfloat16* d1, const f
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_head_reduce<<<unsigned((3 * C1 + 4 + 127) / 128), 128, 0, s>>>(scratch, nwarps, C1, dwout, dbout, loss);
-    return cudaGetLastError();
+    return launch_sum_splits(scratch, int(nwarps), size_t(3 * C1 + 4), dwout, size_t(3 * C1), dbout, 3, loss, s);
 }
 
 cudaError_t launch_amax(size_t npix, int C, const __nv_bfloat16* x, int ld, float* out, cudaStream_t s)
@@ -586,11 +620,24 @@ cudaError_t launch_flip_weights(int Cout, int Cin, const float* w, __nv_bfloat16
     return cudaGetLastError();
 }
 
-cudaError_t launch_adam(size_t n, float* w, const float* g, float* m, float* v, float lr, int t, cudaStream_t s)
+cudaError_t launch_sum_splits(const float* part, int splits, size_t n, float* out0, size_t n0, float* out1,
+                              size_t n1, float* out2, cudaStream_t s)
 {
+    if (n == 0 || splits < 1) return cudaSuccess;
+    k_sum_splits<<<unsigned((n + 31) / 32), 256, 0, s>>>(part, splits, n, out0, n0, out1, n1, out2);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adam_multi(const AdamList& L, float lr, int t, cudaStream_t s)
+{
+    if (L.count < 1 || L.count > kAdamMaxTensors) return cudaErrorInvalidValue;
     const float b1 = 0.9f, b2 = 0.999f;
     const float c1 = 1.0f - powf(b1, float(t)), c2 = 1.0f - powf(b2, float(t));
-    k_adam<<<blocks(n, 256), 256, 0, s>>>(n, w, g, m, v, lr, b1, b2, 1e-8f, c1, c2);
+    const size_t n = L.off[L.count];
+    unsigned g = blocks(n, 256);
+    const unsigned cap = unsigned(device_sms()) * 8;
+    if (g > cap) g = cap;
+    k_adam_multi<<<g, 256, 0, s>>>(L, lr, b1, b2, 1e-8f, c1, c2);
     return cudaGetLastError();
 }
 

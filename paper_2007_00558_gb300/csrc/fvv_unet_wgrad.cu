@@ -50,8 +50,7 @@ struct WgradArgs {
     int n_chunks;
     int cps;                                    // chunks per split
     int nb;                                     // output-channel boxes per CTA
-    float* part;                                // [splits][Cout][9][Cin]
-    float* bpart;                               // [splits][Cout]
+    float* part;                                // [splits][Cout * 9 * Cin + Cout]: dW, then db
     int* err;
 };
 
@@ -172,6 +171,7 @@ k_wgrad3x3_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ C
     ok = __all_sync(0xffffffffu, ok && nk > 0 && *reinterpret_cast<volatile int*>(P.err) == 0);
     if (ok) {
         const int ci = ci0 + lane;
+        const size_t nw = size_t(P.Cout) * 9 * P.Cin, nper = nw + size_t(P.Cout);
         for (int g = 0; g < 3; ++g) {
             const int slot = 4 * g + warp;
             if (slot > kWgOnes) continue;
@@ -182,7 +182,7 @@ k_wgrad3x3_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ C
                 const int cb = co0 + 32 * c32;
                 if (slot < 9) {
                     if (ci < P.Cin) {
-                        float* dst = P.part + ((size_t(split) * P.Cout + cb) * 9 + slot) * P.Cin + ci;
+                        float* dst = P.part + size_t(split) * nper + (size_t(cb) * 9 + slot) * P.Cin + ci;
 #pragma unroll
                         for (int j = 0; j < 32; ++j)
                             if (cb + j < P.Cout) dst[size_t(j) * 9 * P.Cin] = __uint_as_float(r[j]);
@@ -190,7 +190,7 @@ k_wgrad3x3_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ C
                 } else if (ci0 == 0 && lane == 0) {
 #pragma unroll
                     for (int j = 0; j < 32; ++j)
-                        if (cb + j < P.Cout) P.bpart[size_t(split) * P.Cout + cb + j] = __uint_as_float(r[j]);
+                        if (cb + j < P.Cout) P.part[size_t(split) * nper + nw + cb + j] = __uint_as_float(r[j]);
                 }
             }
         }
@@ -198,25 +198,6 @@ k_wgrad3x3_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ C
     tc::fence_before_sync();
     __syncthreads();
     if (warp == 0) tc::tmem_dealloc(tmem, cols);
-}
-
-// dw[i] = sum over splits of part[s][i] (i over Cout * 9 * Cin), db likewise,
-// in split order.
-__global__ void __launch_bounds__(256) k_wgrad_reduce(const float* __restrict__ part, const float* __restrict__ bpart,
-                                                      int splits, size_t nw, int nbias, float* __restrict__ dw,
-                                                      float* __restrict__ db)
-{
-    const size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (i < nw) {
-        float a = 0.0f;
-        for (int s = 0; s < splits; ++s) a += part[size_t(s) * nw + i];
-        dw[i] = a;
-    } else if (i < nw + size_t(nbias) && db) {
-        const size_t j = i - nw;
-        float a = 0.0f;
-        for (int s = 0; s < splits; ++s) a += bpart[size_t(s) * nbias + j];
-        db[j] = a;
-    }
 }
 
 }  // namespace
@@ -242,11 +223,11 @@ WgradPlan wgrad_plan(int B, int H, int W, int Cin, int Cout)
     return p;
 }
 
-// Splits of the chunk range: about two CTAs per SM over all tiles, at least
-// four chunks per CTA.
+// Splits of the chunk range: one resident wave (one CTA per SM) over all
+// tiles, at least four chunks per CTA.
 int wgrad_splits(const WgradPlan& p)
 {
-    const int want = (2 * device_sms() + p.tiles - 1) / p.tiles;
+    const int want = (device_sms() + p.tiles - 1) / p.tiles;
     const int most = (p.n_chunks + 3) / 4;
     return std::max(1, std::min(want, most));
 }
@@ -307,17 +288,14 @@ cudaError_t launch_wgrad3x3_tc(int B, int H, int W, int Cin, int xstride, int Co
     a.cps = cps;
     a.nb = p.nb;
     a.part = scratch;
-    const size_t nw = size_t(Cout) * 9 * Cin;
-    a.bpart = scratch + size_t(splits) * nw;
     a.err = err;
     e = cudaFuncSetAttribute(k_wgrad3x3_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kWgSmem);
     if (e != cudaSuccess) return e;
     k_wgrad3x3_tc<<<dim3(unsigned(p.tiles), unsigned(splits)), kWgThreads, kWgSmem, s>>>(mx, mdz, a);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    const size_t n = nw + size_t(Cout);
-    k_wgrad_reduce<<<unsigned((n + 255) / 256), 256, 0, s>>>(scratch, a.bpart, splits, nw, Cout, dw, db);
-    return cudaGetLastError();
+    const size_t nw = size_t(Cout) * 9 * Cin;
+    return launch_sum_splits(scratch, splits, nw + size_t(Cout), dw, nw, db, size_t(Cout), nullptr, s);
 }
 
 }  // namespace fvv
