@@ -34,14 +34,38 @@ namespace fvv {
 namespace {
 
 constexpr int kWgThreads = 128;
-constexpr int kWgStages = 3;
 constexpr int kWgBox = 4096;                    // 64 pixels x 32 channels x 2 bytes
-constexpr int kWgSlots = 12;                    // 9 taps, the ones tile, 2 unused (3 MMAs of 4 slots)
-constexpr int kWgOnes = 9;
 constexpr int kWgMaxNb = 4;                     // output-channel boxes of 32 per CTA
-constexpr int kWgStage = (kWgSlots + kWgMaxNb) * kWgBox;
 constexpr int kWgHeader = 1024;
-constexpr int kWgSmem = kWgHeader + kWgStages * kWgStage + 1024;   // + alignment slack
+constexpr int kWgHaloPx = 66;                   // a one-row chunk and its two neighbours
+constexpr int kWgHaloBox = 5120;                // room for 80 rows of 64 bytes, 1024-aligned
+
+// Two layouts of the shifted x windows in a pipeline stage.
+//  Nine windows (any chunk shape): tap t = 3 ky + kx at slot t (4 KiB each),
+//    the ones tile at slot 9; MMA g reads slots 4g .. 4g + 3.
+//  Row halos (one-row chunks, images at least 64 wide): for each ky one box
+//    of the 66 pixels x0 - 1 .. x0 + 64 of row y0 + ky - 1, the ones tile as
+//    a fourth box; MMA g = kx starts kx rows (64 bytes) into every box, so
+//    its slots are (ky = 0, 1, 2, ones).  A third of the TMA traffic of the
+//    nine windows.  (The 64-byte swizzle follows absolute shared-memory
+//    address bits, so a start moved by whole rows reads the shifted window.)
+template <bool kHalo>
+struct WgLayout {
+    static constexpr int kLbo = kHalo ? kWgHaloBox : kWgBox;          // between the slots of an MMA
+    static constexpr int kABytes = kHalo ? 4 * kWgHaloBox : 12 * kWgBox;
+    static constexpr int kOnes = kHalo ? 3 * kWgHaloBox : 9 * kWgBox;  // the ones tile
+    static constexpr int kOnesBytes = kHalo ? kWgHaloBox : kWgBox;
+    static constexpr int kStage = kABytes + kWgMaxNb * kWgBox;
+    static constexpr int kStages = kHalo ? 5 : 3;
+    static constexpr int kSmem = kWgHeader + kStages * kStage + 1024;  // + alignment slack
+    // the tap (0..8) of slot w of MMA g, 9 for the ones slot, -1 unused
+    __device__ static int tap(int g, int w)
+    {
+        if (kHalo) return w < 3 ? 3 * w + g : (g == 0 ? 9 : -1);
+        const int s = 4 * g + w;
+        return s <= 9 ? s : -1;
+    }
+};
 
 struct WgradArgs {
     int B, H, W, Cin, Cout;
@@ -69,9 +93,13 @@ __device__ __forceinline__ uint64_t desc_mn_sw64(uint32_t saddr, uint32_t lbo)
     return d;
 }
 
+template <bool kHalo>
 __global__ void __launch_bounds__(kWgThreads, 1)
 k_wgrad3x3_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUtensorMap tmdz, WgradArgs P)
 {
+    using Lay = WgLayout<kHalo>;
+    constexpr int kWgStages = Lay::kStages;
+    constexpr int kWgStage = Lay::kStage;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint64_t* full = reinterpret_cast<uint64_t*>(base);
@@ -106,8 +134,8 @@ k_wgrad3x3_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ C
     }
     // the ones tile of every stage (bf16 1.0; the swizzle does not matter)
     for (int s = 0; s < kWgStages; ++s) {
-        uint4* o = reinterpret_cast<uint4*>(stages + s * kWgStage + kWgOnes * kWgBox);
-        for (int i = threadIdx.x; i < kWgBox / 16; i += kWgThreads)
+        uint4* o = reinterpret_cast<uint4*>(stages + s * kWgStage + Lay::kOnes);
+        for (int i = threadIdx.x; i < Lay::kOnesBytes / 16; i += kWgThreads)
             o[i] = make_uint4(0x3F803F80u, 0x3F803F80u, 0x3F803F80u, 0x3F803F80u);
     }
     tc::fence_proxy_async_smem();
@@ -120,7 +148,7 @@ k_wgrad3x3_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ C
     const int nk = c_end - c_begin;
     if (warp == 0 && lane == 0) {
         // ---------------------------------------------------------------- TMA
-        const uint32_t bytes = uint32_t(9 + nb) * kWgBox;
+        const uint32_t bytes = (kHalo ? 3u * kWgHaloPx * 64u : 9u * kWgBox) + uint32_t(nb) * kWgBox;
         int it = 0;
         for (; it < nk; ++it) {
             const int s = it % kWgStages;
@@ -135,10 +163,15 @@ k_wgrad3x3_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ C
             const int x0 = tx * P.wbox, y0 = ty * P.hbox;
             uint8_t* st = stages + s * kWgStage;
             tc::mbar_arrive_expect_tx(&full[s], bytes);
-            for (int t = 0; t < 9; ++t)
-                tc::tma_load_4d(st + t * kWgBox, &tmx, &full[s], ci0, x0 + (t % 3) - 1, y0 + (t / 3) - 1, b);
+            if (kHalo) {
+                for (int ky = 0; ky < 3; ++ky)
+                    tc::tma_load_4d(st + ky * kWgHaloBox, &tmx, &full[s], ci0, x0 - 1, y0 + ky - 1, b);
+            } else {
+                for (int t = 0; t < 9; ++t)
+                    tc::tma_load_4d(st + t * kWgBox, &tmx, &full[s], ci0, x0 + (t % 3) - 1, y0 + (t / 3) - 1, b);
+            }
             for (int j = 0; j < nb; ++j)
-                tc::tma_load_4d(st + (kWgSlots + j) * kWgBox, &tmdz, &full[s], co0 + 32 * j, x0, y0, b);
+                tc::tma_load_4d(st + Lay::kABytes + j * kWgBox, &tmdz, &full[s], co0 + 32 * j, x0, y0, b);
         }
         // the copies of the last stages have landed before the CTA exits
         for (int k = max(0, it - kWgStages); k < it; ++k)
@@ -151,12 +184,13 @@ k_wgrad3x3_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ C
             if (!tc::mbar_wait(&full[s], uint32_t((it / kWgStages) & 1), P.err, 2)) break;
             tc::fence_after_sync();
             const uint32_t a0 = tc::smem_u32(stages + s * kWgStage);
-            const uint32_t b0 = a0 + kWgSlots * kWgBox;
+            const uint32_t b0 = a0 + Lay::kABytes;
 #pragma unroll
             for (int ks = 0; ks < 4; ++ks)
 #pragma unroll
                 for (int g = 0; g < 3; ++g)
-                    tc::mma_bf16(tmem + uint32_t(g * N), desc_mn_sw64(a0 + g * 4 * kWgBox + ks * 1024, kWgBox),
+                    tc::mma_bf16(tmem + uint32_t(g * N),
+                                 desc_mn_sw64(a0 + (kHalo ? g * 64 : g * 4 * kWgBox) + ks * 1024, Lay::kLbo),
                                  desc_mn_sw64(b0 + ks * 1024, kWgBox), idesc, (it > 0 || ks > 0) ? 1u : 0u);
             tc::mma_commit(&empty[s]);
         }
@@ -173,8 +207,8 @@ k_wgrad3x3_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ C
         const int ci = ci0 + lane;
         const size_t nw = size_t(P.Cout) * 9 * P.Cin, nper = nw + size_t(P.Cout);
         for (int g = 0; g < 3; ++g) {
-            const int slot = 4 * g + warp;
-            if (slot > kWgOnes) continue;
+            const int slot = Lay::tap(g, warp);
+            if (slot < 0) continue;
             for (int c32 = 0; c32 < nb; ++c32) {
                 uint32_t r[32];
                 tc::tmem_ld_x32(tmem + (uint32_t(32 * warp) << 16) + uint32_t(g * N + 32 * c32), r);
@@ -270,7 +304,8 @@ cudaError_t launch_wgrad3x3_tc(int B, int H, int W, int Cin, int xstride, int Co
     const int cps = (p.n_chunks + splits - 1) / splits;
     splits = (p.n_chunks + cps - 1) / cps;                 // every split holds at least one chunk
     CUtensorMap mx, mdz;
-    cudaError_t e = make_map(&mx, x, B, H, W, Cin, xstride, p.wbox, p.hbox);
+    const bool halo = p.hbox == 1;                       // one-row chunks: row halos
+    cudaError_t e = make_map(&mx, x, B, H, W, Cin, xstride, halo ? kWgHaloPx : p.wbox, p.hbox);
     if (e != cudaSuccess) return e;
     e = make_map(&mdz, dz, B, H, W, Cout, Cout, p.wbox, p.hbox);
     if (e != cudaSuccess) return e;
@@ -289,9 +324,17 @@ cudaError_t launch_wgrad3x3_tc(int B, int H, int W, int Cin, int xstride, int Co
     a.nb = p.nb;
     a.part = scratch;
     a.err = err;
-    e = cudaFuncSetAttribute(k_wgrad3x3_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kWgSmem);
-    if (e != cudaSuccess) return e;
-    k_wgrad3x3_tc<<<dim3(unsigned(p.tiles), unsigned(splits)), kWgThreads, kWgSmem, s>>>(mx, mdz, a);
+    const dim3 grid(unsigned(p.tiles), unsigned(splits));
+    if (halo) {
+        e = cudaFuncSetAttribute(k_wgrad3x3_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, WgLayout<true>::kSmem);
+        if (e != cudaSuccess) return e;
+        k_wgrad3x3_tc<true><<<grid, kWgThreads, WgLayout<true>::kSmem, s>>>(mx, mdz, a);
+    } else {
+        e = cudaFuncSetAttribute(k_wgrad3x3_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 WgLayout<false>::kSmem);
+        if (e != cudaSuccess) return e;
+        k_wgrad3x3_tc<false><<<grid, kWgThreads, WgLayout<false>::kSmem, s>>>(mx, mdz, a);
+    }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const size_t nw = size_t(Cout) * 9 * Cin;
