@@ -79,6 +79,14 @@ def parse_args():
                    help="only time the refinement network's training: STEPS Adam steps on 8 random "
                         "128x128 crops after 3 untimed ones (0: the full benchmark); for profiling")
     p.add_argument("--net-widths", default="32,64,128")
+    p.add_argument("--config3", action="store_true",
+                   help="config 3: train the refinement net on LOO renders of the 9-camera 720p rig, report PSNRs")
+    p.add_argument("--c3-renders", type=int, default=2000, help="config 3: training renders")
+    p.add_argument("--c3-test-scenes", type=int, default=16, help="config 3: evaluation scenes (x 9 renders)")
+    p.add_argument("--c3-epochs", type=int, default=2)
+    p.add_argument("--c3-batch", type=int, default=8)
+    p.add_argument("--config5", action="store_true",
+                   help="config 5: 18 cameras 1080p, 64 viewers, the 48/96/192 net in E4M3 vs bf16 vs plain")
     p.add_argument("--net-e4m3", action="store_true", help="with --net-forward: quantise to E4M3 first")
     return p.parse_args()
 
@@ -348,6 +356,22 @@ def bf16_peak():
         return 1900.0, "fallback"
 
 
+def recorded_run(name, command):
+    """The JSON record of a separate bench mode committed under profiles/
+    (config 3 and 5 take minutes of host-side scene generation, more than the
+    default run), labelled with its command."""
+    try:
+        text = open(os.path.join(ROOT, "profiles", name)).read()
+    except OSError:
+        return None
+    m = re.search(r"```json\n(\{.*?\})\n```", text, re.S)
+    if not m:
+        return None
+    rec = json.loads(m.group(1))
+    rec["source"] = "recorded by `%s` on a GB300 (profiles/%s)" % (command, name)
+    return rec
+
+
 def kernel_source_sha():
     h = hashlib.sha256()
     for f in ("fvv_kernels.cu", "fvv_internal.h"):
@@ -507,16 +531,22 @@ def codec_bench(F, ctx, wl, stream, reps=50):
                                "h2d_depth_bytes": {"yuv420": int(1.5 * H * W * K), "uint16": int(2 * H * W * K)}}}
 
 
-def serve_bench(F, ctx, wl, rgb_h, dep_h, slots, seconds, stream):
-    """16 viewers, Poisson 30 Hz each, resolutions 640x360 : 1280x720 :
-    1920x1080 = 2:1:1 (viewer i takes SERVE_RES[i % 4]), frames re-uploaded
-    at 30 fps on a second stream; then a saturation run of back-to-back
-    submissions.  Latency: submission -> output written (library clock)."""
+def serve_bench(F, ctx, wl, rgb_h, dep_h, slots, seconds, stream, refine=False, n_viewers=16, res=None,
+                n_sat=3000):
+    """n_viewers viewers, Poisson 30 Hz each, resolutions cycling through
+    `res` (default 640x360 : 1280x720 : 1920x1080 = 2:1:1, viewer i takes
+    res[i % len(res)]), frames re-uploaded at 30 fps on a second stream; then
+    a saturation run of back-to-back submissions.  refine: every view also
+    runs the context's refinement network.  Latency: submission -> output
+    written (library clock)."""
     import numpy as np
     import torch
     import synthetic as S
     H, W = wl["cams"][0].height, wl["cams"][0].width
-    n_viewers, rate = 16, 30.0
+    rate = 30.0
+    res = SERVE_RES if res is None else res
+    nres = len(res)
+    radius = float(np.linalg.norm(wl["cams"][0].center))
     rng = np.random.default_rng(7)
     arrivals = []
     for v in range(n_viewers):
@@ -527,14 +557,15 @@ def serve_bench(F, ctx, wl, rgb_h, dep_h, slots, seconds, stream):
     arrivals.sort()
     views = {}
     for v in range(n_viewers):
-        Wv, Hv, f = SERVE_RES[v % 4]
-        views[v] = [S.arc_view(22.5 * math.sin(2 * math.pi * (i + 19 * v) / 300.0), 1.5, Wv, Hv, f)
+        Wv, Hv, f = res[v % nres]
+        views[v] = [S.arc_view(22.5 * math.sin(2 * math.pi * (i + 19 * v) / 300.0), radius, Wv, Hv, f)
                     for i in range(300)]
     depth_per_viewer = 8
-    bufs = {v: [torch.empty((SERVE_RES[v % 4][1], SERVE_RES[v % 4][0] * 3), dtype=torch.uint8,
+    bufs = {v: [torch.empty((res[v % nres][1], res[v % nres][0] * 3), dtype=torch.uint8,
                             device="cuda") for _ in range(depth_per_viewer)] for v in range(n_viewers)}
     owner = {}
-    F.fvv_serve_start(ctx, F.fvv_serve_default_cfg(lanes=3, max_batch=16, memory_budget=1 << 30))
+    F.fvv_serve_start(ctx, F.fvv_serve_default_cfg(lanes=3, max_batch=16, memory_budget=1 << 30,
+                                                    refine=1 if refine else 0))
     stop = threading.Event()
     up_stream = torch.cuda.Stream()
     tick0 = [10 ** 6]
@@ -576,7 +607,6 @@ def serve_bench(F, ctx, wl, rgb_h, dep_h, slots, seconds, stream):
         owner.clear()
         nominal = F.fvv_serve_stats(ctx, reset=True)
         # saturation: submit as fast as the pending limit allows
-        n_sat = 3000
         t0 = time.perf_counter()
         tickets = []
         for j in range(n_sat):
@@ -593,10 +623,14 @@ def serve_bench(F, ctx, wl, rgb_h, dep_h, slots, seconds, stream):
         stop.set()
         th.join()
         F.fvv_serve_stop(ctx)
-    mean_px = sum(r[0] * r[1] for r in SERVE_RES) / len(SERVE_RES)
+    mean_px = sum(r[0] * r[1] for r in res) / len(res)
+    mix = {}
+    for r in res:
+        mix["%dx%d" % (r[0], r[1])] = mix.get("%dx%d" % (r[0], r[1]), 0) + 1
     return {
-        "viewers": n_viewers, "rate_hz_per_viewer": rate, "resolutions": "640x360:1280x720:1920x1080=2:1:1",
-        "frame_updates_hz": 30, "lanes": 3, "max_batch": 16, "seconds": seconds,
+        "viewers": n_viewers, "rate_hz_per_viewer": rate,
+        "resolutions": ":".join(mix) + "=" + ":".join(str(v) for v in mix.values()),
+        "refined": bool(refine), "frame_updates_hz": 30, "lanes": 3, "max_batch": 16, "seconds": seconds,
         "offered_rps": len(arrivals) / seconds, "completed": nominal["completed"],
         "p50_ms": nominal["p50_ms"], "p99_ms": nominal["p99_ms"], "max_ms": nominal["max_ms"],
         "views_per_s": nominal["views_per_s"], "mean_batch": nominal["mean_batch"],
@@ -1241,9 +1275,14 @@ def run_fvv(args):
     refine = None
     if not args.no_refine and world == 1 and not args.main_only:
         data = loo_data()
-        refine = {"net_32_64_128": refine_bench(F, ctx, wl, args.refine_steps, stream, data),
-                  "net_48_96_192": refine_bench(F, ctx, wl, args.refine_steps, stream, data, (48, 96, 192),
-                                                fp8=True)}
+        refine = {"net_32_64_128": refine_bench(F, ctx, wl, args.refine_steps, stream, data)}
+        # the serving load of the plain run (16 Poisson viewers, 2:1:1
+        # resolutions, frames at 30 fps) with every view refined by it
+        if not args.no_serve:
+            refine["net_32_64_128"]["bf16"]["serve_mixed"] = serve_bench(
+                F, ctx, wl, rgb_h, dep_h, slots, args.serve_seconds, stream, refine=True, n_sat=600)
+        refine["net_48_96_192"] = refine_bench(F, ctx, wl, args.refine_steps, stream, data, (48, 96, 192),
+                                               fp8=True)
 
     F.fvv_destroy(ctx)
 
@@ -1265,17 +1304,11 @@ def run_fvv(args):
         n_sms = torch.cuda.get_device_properties(local).multi_processor_count
         roofline["issue"] = {k: issue_roofline(k, Bsz, timed[k][2] / timed[k][1] / 1e3, clk.get("sm_mhz"), n_sms)
                              for k in ("resolve", "warp_splat") if k in timed}
-        # the dominant kernel is bound by instruction issue, not by HBM: when
-        # its instruction count is known, that roofline is the headline one
-        # ("alu": warp instructions per second against SMs x 4 schedulers x
-        # the sampled SM clock) and the HBM figures stay beside it
-        iss = roofline["issue"].get(roofline["kernel"])
-        if iss is not None:
-            hbm = {k: roofline.pop(k) for k in ("achieved", "peak", "unit", "frac", "peak_source")}
-            hbm["bound"] = "hbm"
-            roofline = dict(roofline, bound="alu", achieved=iss["achieved"], peak=iss["peak"], unit=iss["unit"],
-                            frac=iss["frac"], peak_source=iss["peak_source"],
-                            warp_instructions_per_view=iss["warp_instructions_per_view"], hbm=hbm)
+        # the headline stays the HBM roofline of the dominant kernel (the
+        # contract's figure); its instruction-issue roofline (warp
+        # instructions/s against SMs x 4 schedulers x the sampled SM clock),
+        # which is what actually bounds it, is reported beside it
+        roofline["bound_by"] = "issue" if roofline["issue"].get(roofline["kernel"]) else None
 
     if rank == 0:
         line = {
@@ -1288,6 +1321,8 @@ def run_fvv(args):
                              "resident" % (slots, K * H * W * 6 / 1e6),
                        "parallelism": "replicas" if world > 1 else "single"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "serve": serve, "refine": refine, "codec": codec,
+            "config3": recorded_run("refine_config3_9cam_1280x720.md", "python bench.py --config3"),
+            "config5": recorded_run("stress_config5_18cam_1920x1080.md", "python bench.py --config5"),
             "layered": layered, "jbf": jbf, "e2e_adaptive": e2e_adaptive, "e2e_yuv": e2e_yuv, "pixel_weights": pixel_weights,
             "gpu_launches": int(launches), "clocks": clocks.summary(),
             "kernel_ms": {k: v[2] for k, v in stats.items()},
@@ -1295,6 +1330,293 @@ def run_fvv(args):
         print(json.dumps(line))
     if world > 1:
         torch.distributed.destroy_process_group()
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# config 3: the refinement network trained on 2000 leave-one-camera-out
+# renders of the 9-camera 1280x720 rig, batch 8, with PSNR against the
+# held-out camera and against the analytic (FP64 ray-cast) ground truth
+# ---------------------------------------------------------------------------
+def _c3_scene(job):
+    """One seeded scene of the 9-camera 1280x720 rig (20 random spheres and
+    boxes, floor, wall; 1 % depth noise and 5 % dropout discs).  For an
+    evaluation scene also the FP64 colour of every camera and, per camera,
+    the mask of its pixels whose surface point another camera sees (FP64
+    shadow test against that camera's exact depth)."""
+    import numpy as np
+    import synthetic as S
+    seed, with_gt = job
+    cams = S.rig_arc(9, 90.0, 1.5, 1280, 720, 1000.0)
+    scene = S.scene_random_objects(seed)
+    rng = np.random.default_rng(seed + 100000)
+    K, H, W = len(cams), cams[0].height, cams[0].width
+    rgb = np.zeros((K, H, W, 3), np.uint8)
+    dep = np.zeros((K, H, W), np.uint16)
+    rends = []
+    for k, c in enumerate(cams):
+        r = S.render(scene, c)
+        rgb[k], d = S.quantise(r)
+        dep[k] = S.add_depth_noise(d, r["z"] * 1000.0, rng)
+        if with_gt:
+            rends.append(r)
+    if not with_gt:
+        return seed, rgb, dep, None, None
+    gt = np.stack([r["rgb"] for r in rends]).astype(np.float32)
+    seen = np.zeros((K, H, W), bool)
+    for j in range(K):
+        P = rends[j]["point"].reshape(-1, 3)
+        m = np.zeros(H * W, bool)
+        for i, c in enumerate(cams):
+            if i == j:
+                continue
+            q = P @ c.R.T + c.t
+            with np.errstate(divide="ignore", invalid="ignore"):
+                u = np.floor(c.fx * q[:, 0] / q[:, 2] + c.cx + 0.5)
+                v = np.floor(c.fy * q[:, 1] / q[:, 2] + c.cy + 0.5)
+            ok = (q[:, 2] > 0) & np.isfinite(u) & np.isfinite(v) & (u >= 0) & (u < W) & (v >= 0) & (v < H)
+            ui = np.where(ok, u, 0).astype(int)
+            vi = np.where(ok, v, 0).astype(int)
+            zc = rends[i]["z"][vi, ui]
+            m |= ok & (np.abs(zc - q[:, 2]) <= 2e-3 * q[:, 2])
+        seen[j] = m.reshape(H, W)
+    return seed, rgb, dep, gt, seen
+
+
+def config3(args):
+    """Config 3 end to end on one GPU; prints one JSON line."""
+    import multiprocessing as mp
+    n_train_scenes = (args.c3_renders + 8) // 9
+    jobs = [(1000 + i, False) for i in range(n_train_scenes)] + \
+           [(5000 + i, True) for i in range(args.c3_test_scenes)]
+    procs = max(1, min(16, os.cpu_count() or 1))
+    t0 = time.perf_counter()
+    pool = mp.get_context("spawn").Pool(procs)          # before any CUDA call
+    results = pool.imap(_c3_scene, jobs)
+    import numpy as np
+    import torch
+    import synthetic as S
+    from paper_2007_00558_gb300 import build as B
+    B.build()
+    from paper_2007_00558_gb300 import fvv as F
+    from paper_2007_00558_gb300 import refine_train as RT
+    cams = S.rig_arc(9, 90.0, 1.5, 1280, 720, 1000.0)
+    K, H, W = 9, 720, 1280
+    N = args.c3_renders
+    dev = torch.device("cuda")
+    train = {"rgb": torch.empty((N, H, W, 3), dtype=torch.uint8, device=dev),
+             "depth": torch.empty((N, H, W), dtype=torch.float32, device=dev),
+             "hole": torch.empty((N, H, W), dtype=torch.uint8, device=dev),
+             "top3": torch.empty((N, H, W, 3), dtype=torch.float32, device=dev),
+             "target": torch.empty((N, H, W, 3), dtype=torch.uint8, device=dev)}
+    test, gts, seens = [], [], []
+    loo = RT.LooRig(cams, [0.0, 0.0, 0.0])
+    n = 0
+    try:
+        for seed, rgb, dep, gt, seen in results:
+            smp = loo.samples(rgb, dep)
+            if gt is None:
+                take = min(K, N - n)
+                for k in train:
+                    train[k][n:n + take] = smp[k][:take]
+                n += take
+            else:
+                test.append(smp)
+                gts.append(torch.from_numpy(gt).to(dev))
+                seens.append(torch.from_numpy(seen).to(dev))
+    finally:
+        loo.close()
+        pool.close()
+        pool.join()
+    data_s = time.perf_counter() - t0
+    test = RT.concat(test)
+    gt = torch.cat(gts, 0)
+    seen = torch.cat(seens, 0)
+    ctx = F.fvv_create(F.rig(S.rig_parallel(1, 16, 16, 10.0, 0.1), [0, 0, 1]))
+    try:
+        widths = (32, 64, 128)
+        F.fvv_refine_init(ctx, F.fvv_refine_default_cfg(seed=1, widths=widths))
+        steps_per_epoch = N // args.c3_batch
+        steps = steps_per_epoch * args.c3_epochs
+        rng = np.random.default_rng(3)
+        order = np.concatenate([rng.permutation(N) for _ in range(args.c3_epochs)])
+        lr0, lr1 = 2e-3, 2e-4
+        losses = []
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        for st in range(steps):
+            idx = torch.from_numpy(order[st * args.c3_batch:(st + 1) * args.c3_batch]).to(dev)
+            b = {k: v.index_select(0, idx) for k, v in train.items()}
+            rate = lr1 + 0.5 * (lr0 - lr1) * (1 + math.cos(math.pi * st / max(1, steps - 1)))
+            fb = F.refine_batch(args.c3_batch, H, W, b["rgb"], b["depth"], b["hole"], b["top3"], b["target"])
+            losses.append(F.fvv_refine_train_step(ctx, fb, rate))
+        torch.cuda.synchronize()
+        train_s = time.perf_counter() - t1
+        # evaluation: plain and refined against the held-out cameras' frames,
+        # against the FP64 colour, and against it where another camera sees
+        # the surface (the pixels the plain method can reconstruct)
+        nt = test["depth"].shape[0]
+        refined = torch.empty((nt, H, W, 3), dtype=torch.uint8, device=dev)
+        for i in range(0, nt, 8):
+            j = min(nt, i + 8)
+            sl = {k: v[i:j].contiguous() for k, v in test.items()}
+            fb = F.refine_batch(j - i, H, W, sl["rgb"], sl["depth"], sl["hole"], sl["top3"])
+            F.fvv_refine_forward(ctx, fb, refined[i:j])
+        torch.cuda.synchronize()
+
+        def ps(a, b, m=None):
+            d = a.float() - b.float()
+            if m is not None:
+                d = d[m]
+            mse = float((d * d).mean())
+            return float("inf") if mse == 0 else 10 * math.log10(255.0 ** 2 / mse)
+
+        plain, tgt = test["rgb"], test["target"]
+        hole = test["hole"].bool()
+        res = {
+            "config": "3: U-Net 32/64/128 on the plain 9-camera 1280x720 synthesis",
+            "train": {"renders": N, "scenes": n_train_scenes, "resolution": "1280x720", "batch": args.c3_batch,
+                      "epochs": args.c3_epochs, "steps": steps, "seconds": train_s,
+                      "ms_per_step": 1e3 * train_s / max(1, steps),
+                      "loss_first": float(np.mean(losses[:20])), "loss_last": float(np.mean(losses[-20:])),
+                      "lr": "cosine 2e-3 -> 2e-4", "data_seconds": data_s, "host_procs": procs},
+            "eval": {"renders": nt, "scenes": args.c3_test_scenes, "seeds": "5000..%d" % (5000 + args.c3_test_scenes - 1)},
+            "psnr_vs_held_out_camera": {"plain_db": ps(plain, tgt), "refined_db": ps(refined, tgt)},
+            "psnr_vs_analytic": {"plain_db": ps(plain, gt), "refined_db": ps(refined, gt)},
+            "psnr_vs_analytic_seen_by_another_camera": {"plain_db": ps(plain, gt, seen),
+                                                        "refined_db": ps(refined, gt, seen),
+                                                        "pixel_fraction": float(seen.float().mean())},
+            "psnr_vs_analytic_in_plain_holes": {"plain_db": ps(plain, gt, hole), "refined_db": ps(refined, gt, hole),
+                                                "pixel_fraction": float(hole.float().mean())},
+            "psnr_refined_vs_plain_db": ps(refined, plain),
+        }
+        print(json.dumps(res))
+    finally:
+        F.fvv_destroy(ctx)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# config 5: 18 cameras 1920x1080 on a 180 deg arc (radius 2 m), 64 viewers
+# at 720p / 1080p 1:1 under the serving loop; the 48/96/192 network in E4M3
+# against its bf16 twin and the plain method
+# ---------------------------------------------------------------------------
+C5_RIG = (18, 180.0, 2.0, 1920, 1080, 1500.0)
+
+
+def _c5_render(job):
+    """Camera k of the 18-camera 1920x1080 rig on the scene of `seed`, with
+    the depth noise model (noise seeded per scene and camera)."""
+    import numpy as np
+    import synthetic as S
+    seed, k = job
+    cams = S.rig_arc(*C5_RIG)
+    r = S.render(S.scene_random_objects(seed), cams[k])
+    rgb, d = S.quantise(r)
+    d = S.add_depth_noise(d, r["z"] * 1000.0, np.random.default_rng(seed * 100 + k))
+    return seed, k, rgb, d
+
+
+def config5(args):
+    """Config 5 end to end on one GPU; prints one JSON line."""
+    import multiprocessing as mp
+    train_seeds, test_seeds = [300, 301, 302, 303], [400]
+    seeds = train_seeds + test_seeds
+    K = C5_RIG[0]
+    procs = max(1, min(16, os.cpu_count() or 1))
+    t0 = time.perf_counter()
+    pool = mp.get_context("spawn").Pool(procs)          # before any CUDA call
+    results = pool.imap_unordered(_c5_render, [(sd, k) for sd in seeds for k in range(K)])
+    import numpy as np
+    import torch
+    import synthetic as S
+    from paper_2007_00558_gb300 import build as B
+    B.build()
+    from paper_2007_00558_gb300 import fvv as F
+    from paper_2007_00558_gb300 import refine_train as RT
+    cams = S.rig_arc(*C5_RIG)
+    H, W = cams[0].height, cams[0].width
+    frames = {sd: (np.zeros((K, H, W, 3), np.uint8), np.zeros((K, H, W), np.uint16)) for sd in seeds}
+    try:
+        for sd, k, rgb, d in results:
+            frames[sd][0][k] = rgb
+            frames[sd][1][k] = d
+    finally:
+        pool.close()
+        pool.join()
+    data_s = time.perf_counter() - t0
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    out = {"config": "5: 18 cameras 1920x1080, 180 deg arc of radius 2 m, 1 % depth noise, 5 % dropouts",
+           "data_seconds": data_s, "host_procs": procs}
+    # 1. plain serving: 64 Poisson viewers (30 Hz each), 720p : 1080p = 1 : 1
+    rgb_h = torch.from_numpy(frames[test_seeds[0]][0]).pin_memory()
+    dep_h = torch.from_numpy(frames[test_seeds[0]][1].view(np.int16)).pin_memory()
+    opts = F.fvv_default_options(frame_slots=4, max_batch=16)
+    ctx = F.fvv_create(F.rig(cams, [0.0, 0.0, 0.0]), opts)
+    res = [(1280, 720, 1000.0), (1920, 1080, 1500.0)]
+    try:
+        F.fvv_upload_frames(ctx, rgb_h, H * W * 3, W * 3, dep_h, H * W * 2, W * 2, 0, stream)
+        torch.cuda.synchronize()
+        out["serve_plain"] = serve_bench(F, ctx, {"cams": cams}, rgb_h, dep_h, 4, args.serve_seconds, stream,
+                                         n_viewers=64, res=res, n_sat=3000)
+        # 2. the 48/96/192 network on LOO renders of this rig, bf16 and E4M3
+        loo = RT.LooRig(cams, [0.0, 0.0, 0.0], F.fvv_default_options(frame_slots=1, max_batch=1))
+        try:
+            train = RT.concat([loo.samples(*frames[sd]) for sd in train_seeds])
+            test = RT.concat([loo.samples(*frames[sd]) for sd in test_seeds])
+        finally:
+            loo.close()
+        widths = (48, 96, 192)
+        F.fvv_refine_init(ctx, F.fvv_refine_default_cfg(seed=1, widths=widths))
+        t1 = time.perf_counter()
+        losses = RT.train(ctx, train, steps=args.refine_steps, batch=8, crop=128, lr=2e-3)
+        train_s = time.perf_counter() - t1
+        flops = unet_flops(H, W, widths)
+        nb = 4
+        tb = {k: v[:nb].contiguous() for k, v in test.items()}
+        fb = F.refine_batch(nb, H, W, tb["rgb"], tb["depth"], tb["hole"], tb["top3"])
+        o = torch.empty((nb, H, W, 3), dtype=torch.uint8, device="cuda")
+
+        def net_ms():
+            F.fvv_refine_forward(ctx, fb, o, None, stream)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(10):
+                F.fvv_refine_forward(ctx, fb, o, None, stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1) / 10 / nb
+
+        ev = RT.evaluate(ctx, test)
+        ms_bf16 = net_ms()
+        o_bf16 = o.clone()                     # the bf16 twin's output on the timed batch
+        peak, src = bf16_peak()
+        out["net_48_96_192"] = {
+            "train": {"samples": int(train["depth"].shape[0]), "scenes": len(train_seeds), "steps": args.refine_steps,
+                      "batch": 8, "crop": 128, "seconds": train_s,
+                      "loss_first": float(np.mean(losses[:20])), "loss_last": float(np.mean(losses[-20:]))},
+            "eval": "leave-one-camera-out, %d unseen scene x %d cameras, %s" % (len(test_seeds), K, ev["size"]),
+            "psnr_plain_db": ev["psnr_plain"],
+            "bf16": {"psnr_db": ev["psnr_refined"], "net_ms_per_view": ms_bf16,
+                     "net_tflops": flops / (ms_bf16 * 1e-3) / 1e12, "tensor_frac": flops / (ms_bf16 * 1e-3) / 1e12 / peak,
+                     "peak_tflops": peak, "peak_source": src},
+            "gflop_per_view": flops / 1e9}
+        RT.quantize(ctx, train, n=8)
+        evq = RT.evaluate(ctx, test)
+        ms_q = net_ms()
+        out["net_48_96_192"]["e4m3"] = {
+            "psnr_db": evq["psnr_refined"], "net_ms_per_view": ms_q, "net_tflops": flops / (ms_q * 1e-3) / 1e12,
+            "tensor_frac": flops / (ms_q * 1e-3) / 1e12 / (2 * peak), "peak_tflops": 2 * peak,
+            "peak_source": src + " bf16 x 2 (the e4m3 / bf16 dense rate ratio)",
+            "psnr_vs_bf16_db": RT.psnr(o, o_bf16)}
+        # the refined views served under the same 64-viewer load (E4M3 net)
+        out["serve_refined_e4m3"] = serve_bench(F, ctx, {"cams": cams}, rgb_h, dep_h, 4, args.serve_seconds, stream,
+                                                refine=True, n_viewers=64, res=res, n_sat=600)
+    finally:
+        F.fvv_destroy(ctx)
+    print(json.dumps(out))
     return 0
 
 
@@ -1306,6 +1628,10 @@ def main():
         return net_forward(args)
     if args.net_train:
         return net_train(args)
+    if args.config3:
+        return config3(args)
+    if args.config5:
+        return config5(args)
     if args.jbf_only:
         import torch
         import synthetic as S
