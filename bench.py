@@ -532,13 +532,14 @@ def codec_bench(F, ctx, wl, stream, reps=50):
 
 
 def serve_bench(F, ctx, wl, rgb_h, dep_h, slots, seconds, stream, refine=False, n_viewers=16, res=None,
-                n_sat=3000):
+                n_sat=3000, persistent=False):
     """n_viewers viewers, Poisson 30 Hz each, resolutions cycling through
     `res` (default 640x360 : 1280x720 : 1920x1080 = 2:1:1, viewer i takes
     res[i % len(res)]), frames re-uploaded at 30 fps on a second stream; then
     a saturation run of back-to-back submissions.  refine: every view also
-    runs the context's refinement network.  Latency: submission -> output
-    written (library clock)."""
+    runs the context's refinement network; persistent: the batches run in the
+    library's persistent kernel.  Latency: submission -> output written
+    (library clock)."""
     import numpy as np
     import torch
     import synthetic as S
@@ -565,7 +566,8 @@ def serve_bench(F, ctx, wl, rgb_h, dep_h, slots, seconds, stream, refine=False, 
                             device="cuda") for _ in range(depth_per_viewer)] for v in range(n_viewers)}
     owner = {}
     F.fvv_serve_start(ctx, F.fvv_serve_default_cfg(lanes=3, max_batch=16, memory_budget=1 << 30,
-                                                    refine=1 if refine else 0))
+                                                    refine=1 if refine else 0, persistent=1 if persistent else 0,
+                                                    max_width=max(r[0] for r in res)))
     stop = threading.Event()
     up_stream = torch.cuda.Stream()
     tick0 = [10 ** 6]
@@ -630,7 +632,8 @@ def serve_bench(F, ctx, wl, rgb_h, dep_h, slots, seconds, stream, refine=False, 
     return {
         "viewers": n_viewers, "rate_hz_per_viewer": rate,
         "resolutions": ":".join(mix) + "=" + ":".join(str(v) for v in mix.values()),
-        "refined": bool(refine), "frame_updates_hz": 30, "lanes": 3, "max_batch": 16, "seconds": seconds,
+        "refined": bool(refine), "persistent_kernel": bool(persistent), "frame_updates_hz": 30, "lanes": 3,
+        "max_batch": 16, "seconds": seconds,
         "offered_rps": len(arrivals) / seconds, "completed": nominal["completed"],
         "p50_ms": nominal["p50_ms"], "p99_ms": nominal["p99_ms"], "max_ms": nominal["max_ms"],
         "views_per_s": nominal["views_per_s"], "mean_batch": nominal["mean_batch"],
@@ -1248,6 +1251,9 @@ def run_fvv(args):
     serve = None
     if not args.no_serve and world == 1 and not args.main_only:
         serve = serve_bench(F, ctx, wl, rgb_h, dep_h, slots, args.serve_seconds, stream)
+        # the same load with the batches in the persistent kernel
+        serve["persistent"] = serve_bench(F, ctx, wl, rgb_h, dep_h, slots, args.serve_seconds, stream,
+                                          persistent=True)
 
     codec = None
     if world == 1 and not args.main_only:

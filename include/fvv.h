@@ -330,12 +330,28 @@ fvv_status fvv_upload_frames_yuv(fvv_ctx* ctx, const uint8_t* rgb, size_t rgb_ca
  * width and height multiples of 4.  The network's own activations are not
  * part of memory_budget.  While such a session runs, the fvv_refine_* calls
  * that use or change the network return FVV_ERR_BUSY. */
+/* With persistent = 1 (plain views only: refine 0, no layered context) the
+ * batches do not become kernel launches: one cooperative kernel, resident on
+ * every SM, takes them from a ring of batch descriptors in pinned host
+ * memory that the scheduler writes, runs steps (a)-(e) of each (grid
+ * barriers between the steps), and publishes each batch's completion in
+ * that memory, where a poller thread of the library sees it.  The kernel
+ * returns after idle_us without work and is launched again for the next
+ * batch.  It leaves room on every SM (registers for a small kernel) so
+ * that frame uploads run beside it.  Views may be at most max_width wide (it sizes the kernel's shared
+ * memory) and outputs must be device memory.  Every wait of the kernel is
+ * bounded; a grid barrier that runs out ends the kernel and fails its
+ * batches with FVV_ERR_TIMEOUT.  An upload into a frame slot that a posted
+ * batch still reads waits (up to 2 s) for that batch. */
 typedef struct fvv_serve_cfg {
     int32_t lanes;              /* batches in flight on the GPU, 1..16, default 3 */
     int32_t max_batch;          /* views per batched launch, default 16 */
     int32_t max_pending;        /* submitted and not yet polled, default 4096 */
     uint64_t memory_budget;     /* device bytes of serving scratch (all lanes), default 768 MiB */
     int32_t refine;             /* 1: every view also runs the refinement network (see below) */
+    int32_t persistent;         /* 1: batches run in one persistent kernel (see above), default 0 */
+    int32_t max_width;          /* persistent: widest view, default 1920 */
+    uint32_t idle_us;           /* persistent: the kernel returns after this long without work, default 20000 */
 } fvv_serve_cfg;
 
 typedef struct fvv_serve_report {
@@ -405,6 +421,16 @@ fvv_status fvv_profile_read(fvv_ctx* ctx, fvv_kernel_stats* out, int32_t* n, int
  * Returns OK when the phase completed, TIMEOUT when the wait ran out,
  * INVALID_ARG for a limit outside the range, CUDA on a launch failure. */
 fvv_status fvv_selftest_bounded_wait(int32_t arrive, uint32_t limit_us, void* stream);
+
+/* Diagnostic of the persistent serving kernel's bounded waits, on an empty
+ * ring of batches (a context with an n_cams-camera rig is not needed).
+ * barrier = 0: the kernel waits for work that never comes and returns after
+ * idle_us.  barrier = 1: work is posted but the grid barrier's count is set
+ * so that it never completes; every CTA gives up after limit_us.  Waits on
+ * `stream`.  Returns TIMEOUT with the kernel's code in the message when the
+ * limit ran out as intended (the wait for work: "idle", the barrier:
+ * "barrier"), INVALID_ARG for limits outside [1, 2000000] us, CUDA. */
+fvv_status fvv_selftest_persistent_wait(int32_t barrier, uint32_t limit_us, void* stream);
 
 /* ---- refinement network: layer operations -------------------------------
  * The learned refinement (a U-Net; the paper has none) runs on the sm_103a

@@ -353,6 +353,7 @@ fvv_status fvv::upload_frame(fvv_ctx* c, int cam, const uint8_t* rgb, size_t rgb
         S.tick = tick;
         S.mask = 0;
     }
+    FVV_TRY(fvv::serve_wait_slot(c, S));
     for (int r = 0; r < fvv::kMaxReaders; ++r)
         if (S.read_pending[r]) FVV_CUDA(cudaStreamWaitEvent(s, S.read[r], 0));
     uint8_t* base = c->arena + size_t(si) * c->slot_bytes;
@@ -484,6 +485,7 @@ static fvv_status upload_all(fvv_ctx* c, uint64_t mask, const uint8_t* rgb, size
     }
     // only the writes into the slot wait for syntheses still reading it: the
     // copies into the staging buffer above may already run
+    FVV_TRY(fvv::serve_wait_slot(c, S));
     for (int rd = 0; rd < kMaxReaders; ++rd)
         if (S.read_pending[rd]) FVV_CUDA(cudaStreamWaitEvent(s, S.read[rd], 0));
     UploadAll u{};
@@ -606,7 +608,7 @@ size_t fvv::view_stage_bytes(const fvv_view& v, uint8_t* out_rgb, const fvv_aux*
 
 fvv_status fvv::run_batch(fvv_ctx* c, BatchScratch& S, int n, const fvv_view* views,
                           const uint64_t* ticks, uint8_t* const* out_rgb, const size_t* out_pitch,
-                          const fvv_aux* aux, cudaStream_t s, bool sync_host)
+                          const fvv_aux* aux, cudaStream_t s, bool sync_host, PersistPost* post)
 {
     if (n < 1 || n > S.max_batch)
         return fail(FVV_ERR_INVALID_ARG, "batch size must be in [1, max_batch]");
@@ -780,6 +782,20 @@ fvv_status fvv::run_batch(fvv_ctx* c, BatchScratch& S, int n, const fvv_view* vi
     // the z-buffer scratch and output staging are shared by all batches using
     // S: a batch on another stream waits for the previous one
     if (S.pending) FVV_CUDA(cudaStreamWaitEvent(s, S.done, 0));
+    if (post) {
+        if (c->opt.layered || any_host || want_top3 || aux)
+            return fail(FVV_ERR_INVALID_ARG, "persistent batches take device outputs and no aux outputs");
+        int band = 1, sbx = 1;
+        fvv::persist_batch_shape(n, max_h, max_chunks, post->ctas, &band, &sbx);
+        post->batch = PersistBatch{vdev, c->frames_dev, S.keys, koff, n, max_h, band, sbx,
+                                   c->opt.pixel_weights != 0 ? 1 : 0, {0, 0, 0}};
+        post->slots.clear();
+        for (int si = 0; si < c->slots; ++si)
+            if (used[si]) post->slots.push_back(si);
+        FVV_CUDA(cudaEventRecord(P.done, s));
+        P.pending = true;
+        return FVV_OK;
+    }
     FVV_TRY(run_kernel(c, kClear, s, [&] { return fvv::launch_clear_keys(S.keys, koff, s); }));
     FVV_TRY(run_kernel(c, kSplat, s, [&] {
         return fvv::launch_warp_splat(vdev, n, max_chunks, c->frames_dev, s, c->opt.layered != 0);

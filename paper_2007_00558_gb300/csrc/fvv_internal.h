@@ -67,6 +67,45 @@ struct alignas(16) ViewDesc {
     int32_t chunk_begin[kMaxCams + 1];  // prefix of splat warp segments over `active`
 };
 
+// Persistent serving kernel (fvv_kernels.cu): one cooperative launch that
+// takes batches of views from a ring the host writes, and runs steps a-e of
+// each (clear, splat, resolve, separated by grid barriers).  The ring lives
+// in pinned, mapped host memory; the kernel reads it through its device
+// alias.  Every wait of the kernel is bounded by %globaltimer.
+struct PersistBatch {
+    const ViewDesc* views;             // device: the batch's parameter block
+    const FrameRef* frames;            // device: the frame ring's table
+    unsigned long long* keys;          // the batch's z-buffers, cleared first
+    unsigned long long n_keys;
+    int32_t n_views, max_h, band, splat_bx;
+    int32_t pixel_weights, pad[3];
+};
+constexpr int kPersistRing = 16;
+struct PersistQueue {
+    PersistBatch batch[kPersistRing];   // batch b at b % kPersistRing
+    volatile uint32_t posted;           // batches written so far (set after the batch)
+    volatile uint32_t stop;             // 1: return at the next wait for work
+    volatile uint32_t done;             // batches completed (set after their outputs)
+    volatile int32_t err;               // 0, or the code of the wait that ran out
+};
+// Device memory of the kernel's grid barrier; zeroed before every launch.
+struct PersistSync {
+    unsigned int count, gen;
+    int cmd;                            // 0: run the batch, 1: return
+    int err;
+};
+constexpr int kPersistErrBarrier = 11;  // a grid barrier ran out
+// Launch the kernel on `stream` (cooperative, every CTA resident) to take
+// batches first, first + 1, ...; it returns after idle_ns without work, on
+// q->stop, or when a grid barrier waits longer than wait_ns.  max_w, n_cams
+// size its shared memory.  *ctas: the grid size.
+cudaError_t launch_serve_persistent(PersistQueue* q_dev, PersistSync* sync, uint32_t first, int max_w, int n_cams,
+                                    uint64_t idle_ns, uint64_t wait_ns, cudaStream_t stream, int* ctas);
+// The grid of that kernel for views up to max_w wide (0: none fits).
+int persist_grid(int max_w, int n_cams);
+// The band and the splat's CTAs per view the kernel uses for a batch.
+void persist_batch_shape(int n_views, int max_h, int max_chunks, int ctas, int* band, int* splat_bx);
+
 // Launchers (fvv_kernels.cu).  All asynchronous on `stream`.
 cudaError_t launch_clear_keys(unsigned long long* keys, size_t n, cudaStream_t stream);
 // layered: FG/BG layers (each view's keys_bg set, frames' bg models used).

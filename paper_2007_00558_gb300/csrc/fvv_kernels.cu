@@ -24,6 +24,7 @@
 // in a fixed, FMA-free order -- each product and each sum rounded once, each
 // quotient a correctly rounded division -- so the results are exactly the
 // IEEE values of that sequence.
+#include <algorithm>
 #include <climits>
 #include <cstdlib>
 
@@ -156,6 +157,24 @@ __device__ __forceinline__ uint4 ld_stream_v4(const void* ptr, uint64_t pol)
     return v;
 }
 
+// Loads of frame data.  kCoh = false: the read-only (non-coherent) paths,
+// for kernels during whose life the frames do not change.  kCoh = true
+// (the persistent serving kernel, which outlives frame uploads): weak loads,
+// which a gpu-scope acquire fence makes observe the latest writes.
+template <bool kCoh, class T>
+__device__ __forceinline__ T ld_frame(const T* p)
+{
+    if constexpr (kCoh) return *p;
+    else return __ldg(p);
+}
+
+template <bool kCoh>
+__device__ __forceinline__ uint32_t ld_depth_stream(const uint16_t* ptr, uint64_t pol)
+{
+    if constexpr (kCoh) return *ptr;
+    else return ld_stream_u16(ptr, pol);
+}
+
 // Exact integer -> float conversion on the FP32/ALU pipes: for 0 <= d < 2^23,
 // 2^23 + d is exactly representable and its low mantissa bits are d.
 __device__ __forceinline__ float u23_to_float(uint32_t d)
@@ -188,9 +207,12 @@ __device__ __forceinline__ bool target_pixel(float X, float Y, float Z, uint32_t
 // the active cameras: chunk_begin[a] .. chunk_begin[a+1).  Each CTA belongs
 // to one view and stages its maps and frame table in shared memory.
 // ---------------------------------------------------------------------------
-template <bool kLayered, bool kVec>
-__global__ void __launch_bounds__(kSplatThreads, 5)
-k_warp_splat(const ViewDesc* __restrict__ views, const FrameRef* __restrict__ frames)
+// The work of one CTA (bx, by) of a grid of gdx x (views) CTAs; the kernel
+// below is its one-launch form, the persistent serving kernel calls it for
+// virtual CTAs in turn (kCoh: coherent frame loads, see ld_frame).
+template <bool kLayered, bool kVec, bool kCoh>
+__device__ __forceinline__ void splat_cta(const ViewDesc* __restrict__ views, const FrameRef* __restrict__ frames,
+                                          int bx, int by, int gdx)
 {
     // per active camera: (m0, m2, m3, m1), (m4, m6, m7, m5), (m8, m10, m11, m9)
     __shared__ __align__(16) float4 s_M[kMaxCams][3];
@@ -201,9 +223,10 @@ k_warp_splat(const ViewDesc* __restrict__ views, const FrameRef* __restrict__ fr
     constexpr int kWarps = kSplatThreads / 32;
     constexpr int kPer = kSplatSeg / 32;           // pixels per lane per segment
     static_assert(kPer == 8, "a 16-byte load holds 8 depth codes");
-    const ViewDesc* V = views + blockIdx.y;
+    if (kCoh) __syncthreads();                     // the previous virtual CTA's reads of the staging are done
+    const ViewDesc* V = views + by;
     const int na = V->n_active;
-    const int first = blockIdx.x * kWarps;
+    const int first = bx * kWarps;
     if (first >= V->chunk_begin[na])
         return;                                   // uniform over the CTA
     for (int i = threadIdx.x; i < na * 3; i += kSplatThreads) {
@@ -240,7 +263,7 @@ k_warp_splat(const ViewDesc* __restrict__ views, const FrameRef* __restrict__ fr
     // persistent warps: segment seg, seg + stride, ... of this view; the
     // segments grow, so the camera search resumes where it stopped
     int a = 0;
-    for (int seg = first + int(threadIdx.x >> 5); seg < total; seg += gridDim.x * kWarps) {
+    for (int seg = first + int(threadIdx.x >> 5); seg < total; seg += gdx * kWarps) {
         while (seg >= s_cb[a + 1])
             ++a;
         const int k = s_act[a];
@@ -258,7 +281,7 @@ k_warp_splat(const ViewDesc* __restrict__ views, const FrameRef* __restrict__ fr
         uint32_t d[kPer];
         // 16-byte loads need 16-byte aligned rows; a vector lies wholly
         // inside or wholly past the row's pitch (pitch and ub multiples of 8)
-        if (kVec && (F.dpitch & 7) == 0 && (reinterpret_cast<uintptr_t>(F.depth) & 15u) == 0) {
+        if (kVec && !kCoh && (F.dpitch & 7) == 0 && (reinterpret_cast<uintptr_t>(F.depth) & 15u) == 0) {
             uint4 q = make_uint4(0u, 0u, 0u, 0u);
             if (ub < F.dpitch)
                 q = ld_stream_v4(row + ub, pol_stream);
@@ -271,7 +294,7 @@ k_warp_splat(const ViewDesc* __restrict__ views, const FrameRef* __restrict__ fr
 #pragma unroll
             for (int j = 0; j < kPer; ++j) {
                 const int u = ub + kStep * j;
-                d[j] = u < F.W ? ld_stream_u16(row + u, pol_stream) : 0u;
+                d[j] = u < F.W ? ld_depth_stream<kCoh>(row + u, pol_stream) : 0u;
             }
         }
         // layered: a BG-signalled pixel takes its depth from the model and
@@ -282,7 +305,7 @@ k_warp_splat(const ViewDesc* __restrict__ views, const FrameRef* __restrict__ fr
 #pragma unroll
             for (int j = 0; j < kPer; ++j)
                 if (d[j] == kDepthBg) {
-                    d[j] = brow ? ld_stream_u16(brow + ub + kStep * j, pol_stream) : 0u;
+                    d[j] = brow ? ld_depth_stream<kCoh>(brow + ub + kStep * j, pol_stream) : 0u;
                     bgm |= 1u << j;
                 }
         }
@@ -320,6 +343,13 @@ k_warp_splat(const ViewDesc* __restrict__ views, const FrameRef* __restrict__ fr
             }
         }
     }
+}
+
+template <bool kLayered, bool kVec>
+__global__ void __launch_bounds__(kSplatThreads, 5)
+k_warp_splat(const ViewDesc* __restrict__ views, const FrameRef* __restrict__ frames)
+{
+    splat_cta<kLayered, kVec, false>(views, frames, int(blockIdx.x), int(blockIdx.y), int(gridDim.x));
 }
 
 // ---------------------------------------------------------------------------
@@ -448,14 +478,14 @@ __device__ __forceinline__ float pixel_weight(float cx, float cy, float cz, floa
 // weighted by the angle at its surface point) instead of the view's
 // per-camera weights.
 // ---------------------------------------------------------------------------
-template <bool kTop3, bool kLayered, bool kPixW>
-__global__ void __launch_bounds__(kResolveThreads, 3)
-k_resolve(const ViewDesc* __restrict__ views, const FrameRef* __restrict__ frames, int band)
+template <bool kTop3, bool kLayered, bool kPixW, bool kCoh>
+__device__ __forceinline__ void resolve_cta(const ViewDesc* __restrict__ views, const FrameRef* __restrict__ frames,
+                                            int band, int bx, int by, unsigned char* smem)
 {
-    extern __shared__ __align__(16) unsigned char smem[];
-    const ViewDesc* V = views + blockIdx.y;
+    if (kCoh) __syncthreads();                     // the previous virtual CTA is done with the shared memory
+    const ViewDesc* V = views + by;
     const int Wv = V->Wv, Hv = V->Hv;
-    const int y0 = blockIdx.x * band;
+    const int y0 = bx * band;
     if (y0 >= Hv)
         return;                                    // uniform over the CTA
     const int y1 = min(Hv, y0 + band);
@@ -481,7 +511,12 @@ k_resolve(const ViewDesc* __restrict__ views, const FrameRef* __restrict__ frame
         if (tid == NT - 1) dst[Wv + 1] = kKeyEmpty;
         if (yy >= 0 && yy < Hv) {
             const unsigned long long* src = keys + size_t(yy) * Wv;
-            for (int x = tid; x < Wv; x += NT) cp_async8(dst + 1 + x, src + x);
+            if (kCoh) {
+                // written by other CTAs of the same kernel: L2 loads
+                for (int x = tid; x < Wv; x += NT) dst[1 + x] = __ldcg(src + x);
+            } else {
+                for (int x = tid; x < Wv; x += NT) cp_async8(dst + 1 + x, src + x);
+            }
         } else {
             for (int x = tid; x < Wv; x += NT) dst[1 + x] = kKeyEmpty;
         }
@@ -590,7 +625,7 @@ k_resolve(const ViewDesc* __restrict__ views, const FrameRef* __restrict__ frame
             const RCam& Cw = s_cam[pw];
             const uint32_t sv = uint32_t((static_cast<unsigned long long>(s) * Cw.magic) >> Cw.shift);
             const uint32_t su = s - sv * (Cw.maxu + 1u);
-            const uint32_t cw = __ldg(Cw.rgba + sv * uint32_t(Cw.rpitch) + su);
+            const uint32_t cw = ld_frame<kCoh>(Cw.rgba + sv * uint32_t(Cw.rpitch) + su);
             const float fx = u23_to_float(uint32_t(x));
             // per-pixel weights: the surface point in the view's frame
             float px = 0.0f, py = 0.0f, lb = 0.0f;
@@ -647,8 +682,8 @@ k_resolve(const ViewDesc* __restrict__ views, const FrameRef* __restrict__ frame
                     di[j] = 0u;
                     if (ok[j]) {
                         di[j] = vk * uint32_t(C.dpitch) + uk;
-                        dk[j] = __ldg(C.depth + di[j]);
-                        ck[j] = __ldg(C.rgba + vk * uint32_t(C.rpitch) + uk);
+                        dk[j] = ld_frame<kCoh>(C.depth + di[j]);
+                        ck[j] = ld_frame<kCoh>(C.rgba + vk * uint32_t(C.rpitch) + uk);
                     }
                 }
                 // the BG layer's depth in camera k: its model where camera k
@@ -659,7 +694,7 @@ k_resolve(const ViewDesc* __restrict__ views, const FrameRef* __restrict__ frame
                         if (!ok[j])
                             continue;
                         const uint16_t* bgk = s_cam[ak[j]].bg;
-                        dk[j] = (dk[j] == kDepthBg && bgk) ? uint32_t(__ldg(bgk + di[j])) : 0u;
+                        dk[j] = (dk[j] == kDepthBg && bgk) ? uint32_t(ld_frame<kCoh>(bgk + di[j])) : 0u;
                     }
                 }
                 if (g0 == 0)
@@ -793,6 +828,139 @@ k_resolve(const ViewDesc* __restrict__ views, const FrameRef* __restrict__ frame
     }
 }
 
+template <bool kTop3, bool kLayered, bool kPixW>
+__global__ void __launch_bounds__(kResolveThreads, 3)
+k_resolve(const ViewDesc* __restrict__ views, const FrameRef* __restrict__ frames, int band)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    resolve_cta<kTop3, kLayered, kPixW, false>(views, frames, band, int(blockIdx.x), int(blockIdx.y), smem);
+}
+
+// ---------------------------------------------------------------------------
+// Persistent serving kernel.  One cooperative launch (every CTA resident)
+// loops: CTA 0 waits for the next posted batch, then all CTAs run its clear,
+// splat and resolve as virtual CTAs, with a grid barrier between the steps
+// and a gpu-scope fence after each barrier (so weak loads see the other
+// CTAs' writes and the frames uploaded before the batch was posted), and
+// CTA 0 publishes the batch's completion.  It returns when no batch comes
+// for idle_ns, on q->stop, or when a barrier runs out (sync->err, then
+// q->err).
+// ---------------------------------------------------------------------------
+namespace {
+
+__device__ __forceinline__ uint64_t gtimer()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Sense-counting grid barrier with a bounded wait (limit_ns); false once any
+// CTA gave up.
+__device__ bool persist_barrier(PersistSync* sync, unsigned int& gen, uint64_t limit_ns)
+{
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned int g = gen;
+        __threadfence();
+        if (atomicAdd(&sync->count, 1u) == gridDim.x - 1) {
+            atomicExch(&sync->count, 0u);
+            __threadfence();
+            atomicExch(&sync->gen, g + 1);
+        } else {
+            const uint64_t t0 = gtimer();
+            while (*reinterpret_cast<volatile unsigned int*>(&sync->gen) == g) {
+                if (*reinterpret_cast<volatile int*>(&sync->err) != 0) break;
+                if (gtimer() - t0 > limit_ns) {
+                    atomicCAS(&sync->err, 0, kPersistErrBarrier);
+                    break;
+                }
+                __nanosleep(256);
+            }
+        }
+        __threadfence();                      // acquire: later loads see the writes before the barrier
+        gen = g + 1;
+        s_ok = *reinterpret_cast<volatile int*>(&sync->err) == 0;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+}  // namespace
+
+__global__ void __launch_bounds__(kResolveThreads, 3)
+k_serve_persistent(PersistQueue* q, PersistSync* sync, uint32_t first, uint64_t idle_ns, uint64_t wait_ns)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ PersistBatch s_b;
+    __shared__ int s_cmd;
+    unsigned int gen = 0;                     // the host zeroes *sync before the launch
+    for (uint32_t b = first;; ++b) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            int cmd = 1;
+            const uint64_t t0 = gtimer();
+            for (;;) {
+                if (q->stop) break;
+                if (q->posted > b) {
+                    cmd = 0;
+                    break;
+                }
+                if (gtimer() - t0 > idle_ns) break;
+                __nanosleep(1000);
+            }
+            sync->cmd = cmd;
+        }
+        if (!persist_barrier(sync, gen, wait_ns)) break;
+        if (threadIdx.x == 0) {
+            s_cmd = *reinterpret_cast<volatile int*>(&sync->cmd);
+            if (!s_cmd) {
+                // field by field through volatile reads: the host wrote it
+                const volatile PersistBatch& src = q->batch[b % kPersistRing];
+                s_b.views = src.views;
+                s_b.frames = src.frames;
+                s_b.keys = src.keys;
+                s_b.n_keys = src.n_keys;
+                s_b.n_views = src.n_views;
+                s_b.max_h = src.max_h;
+                s_b.band = src.band;
+                s_b.splat_bx = src.splat_bx;
+                s_b.pixel_weights = src.pixel_weights;
+            }
+        }
+        __syncthreads();
+        if (s_cmd) break;
+        const PersistBatch B = s_b;
+        // (a0) the batch's z-buffers
+        const size_t stride = size_t(gridDim.x) * blockDim.x;
+        for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < B.n_keys; i += stride)
+            B.keys[i] = kKeyEmpty;
+        if (!persist_barrier(sync, gen, wait_ns)) break;
+        // (a) + (b)
+        for (int v = int(blockIdx.x); v < B.splat_bx * B.n_views; v += int(gridDim.x))
+            splat_cta<false, false, true>(B.views, B.frames, v % B.splat_bx, v / B.splat_bx, B.splat_bx);
+        if (!persist_barrier(sync, gen, wait_ns)) break;
+        // (c) + (d) + (e)
+        const int nb = (B.max_h + B.band - 1) / B.band;
+        for (int v = int(blockIdx.x); v < nb * B.n_views; v += int(gridDim.x)) {
+            if (B.pixel_weights)
+                resolve_cta<false, false, true, true>(B.views, B.frames, B.band, v % nb, v / nb, smem);
+            else
+                resolve_cta<false, false, false, true>(B.views, B.frames, B.band, v % nb, v / nb, smem);
+        }
+        if (!persist_barrier(sync, gen, wait_ns)) break;
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            __threadfence_system();           // the batch's outputs before its completion
+            q->done = b + 1;
+            __threadfence_system();
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        q->err = *reinterpret_cast<volatile int*>(&sync->err);
+        __threadfence_system();
+    }
+}
+
 // ---------------------------------------------------------------------------
 // upload: RGB8 rows -> RGBA8 rows (R | G << 8 | B << 16)
 // ---------------------------------------------------------------------------
@@ -915,6 +1083,57 @@ cudaError_t launch_resolve(const ViewDesc* views, int n_views, int max_h, int ma
     }
     if (layered) return top3 ? go(k_resolve<true, true, false>) : go(k_resolve<false, true, false>);
     return top3 ? go(k_resolve<true, false, false>) : go(k_resolve<false, false, false>);
+}
+
+void persist_batch_shape(int n_views, int max_h, int max_chunks, int ctas, int* band, int* splat_bx)
+{
+    // two-row bands when they fill the CTAs, else single rows; the splat's
+    // segments spread over about one virtual CTA per real one
+    *band = (long long)max_h * n_views >= 2LL * kResolveBand * ctas ? kResolveBand : 1;
+    constexpr int kWarps = kSplatThreads / 32;
+    const int need = (max_chunks + kWarps - 1) / kWarps;
+    const int want = (ctas + n_views - 1) / n_views;
+    *splat_bx = std::max(1, std::min(need, want));
+}
+
+int persist_grid(int max_w, int n_cams)
+{
+    const size_t smem = resolve_smem_bytes(max_w, n_cams, false);
+    int per_sm = 0;
+    if (cudaFuncSetAttribute(k_serve_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) !=
+            cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_serve_persistent, kResolveThreads, smem) !=
+            cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    // other kernels (the frame uploads: 256 threads of at most 32 registers)
+    // must fit beside the persistent one instead of waiting for it to idle:
+    // when its CTAs leave fewer registers than that, one CTA per SM less
+    cudaFuncAttributes fa{};
+    int regs_sm = 65536;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaFuncGetAttributes(&fa, k_serve_persistent) != cudaSuccess ||
+        cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return (per_sm > 1 ? per_sm - 1 : 1) * device_sms();
+    }
+    const int free_regs = regs_sm - per_sm * kResolveThreads * fa.numRegs;
+    if (free_regs < 256 * 32 && per_sm > 1) --per_sm;
+    return per_sm * device_sms();
+}
+
+cudaError_t launch_serve_persistent(PersistQueue* q_dev, PersistSync* sync, uint32_t first, int max_w, int n_cams,
+                                    uint64_t idle_ns, uint64_t wait_ns, cudaStream_t stream, int* ctas)
+{
+    const size_t smem = resolve_smem_bytes(max_w, n_cams, false);
+    const int grid = persist_grid(max_w, n_cams);
+    if (grid < 1) return cudaErrorInvalidValue;
+    *ctas = grid;
+    void* args[] = {&q_dev, &sync, &first, &idle_ns, &wait_ns};
+    return cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(k_serve_persistent), dim3(unsigned(grid)),
+                                       dim3(kResolveThreads), args, smem, stream);
 }
 
 cudaError_t launch_pack_rgba(const uint8_t* rgb, size_t rgb_pitch, uint32_t* rgba, int rpitch,

@@ -72,6 +72,7 @@ struct SlotState {
     cudaEvent_t uploaded = nullptr;            // after the last upload into this slot
     cudaEvent_t read[kMaxReaders] = {};        // after each reader's last synthesis of it
     bool read_pending[kMaxReaders] = {};
+    uint32_t persist_reads = 0;                // persistent serving: batch index + 1 of its last reader
 };
 
 // Device scratch of batched launches: the z-buffer keys, the staging area
@@ -247,13 +248,29 @@ void scratch_free(fvv_ctx* c, BatchScratch& S);
 size_t view_keys(const fvv_view& v, bool layered = false);
 size_t view_stage_bytes(const fvv_view& v, uint8_t* out_rgb, const fvv_aux* aux);
 
+// A batch for the persistent serving kernel: what run_batch fills instead
+// of launching (ctas: the kernel's grid, set by the caller).
+struct PersistPost {
+    int ctas = 0;
+    PersistBatch batch{};
+    std::vector<int> slots;                    // frame-ring slots the batch reads
+};
+
 // One batched launch of steps a-e for n views on stream s, with scratch S.
 // ticks[i] selects view i's tick (NULL = newest complete).  With sync_host
 // the call waits for host outputs; without, the caller orders on the stream.
+// With post (device outputs, no aux, single-layer context) nothing is
+// launched: the parameter copy and the waits for the frames' uploads are
+// queued on s and *post describes the batch for the persistent kernel.
 // The caller holds c->mu.
 fvv_status run_batch(fvv_ctx* c, BatchScratch& S, int n, const fvv_view* views,
                      const uint64_t* ticks, uint8_t* const* out_rgb, const size_t* out_pitch,
-                     const fvv_aux* aux, cudaStream_t s, bool sync_host);
+                     const fvv_aux* aux, cudaStream_t s, bool sync_host, PersistPost* post = nullptr);
+
+// Persistent serving: before an upload overwrites `slot`, wait (up to 2 s,
+// relaunching the kernel if it returned with the batch pending) until the
+// batches that read it are done.  The caller holds c->mu.
+fvv_status serve_wait_slot(fvv_ctx* c, const SlotState& slot);
 
 // fvv_serve.cu: stop a running serving loop (fvv_destroy calls it).
 void serve_shutdown(fvv_ctx* c);

@@ -22,6 +22,7 @@
 // of one lane overlaps the network pass of another.  The network's
 // activations are sized once, at start, for the largest batch a lane holds.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -96,6 +97,20 @@ struct ServeState {
     std::vector<double> lat_ms;
     double t_first = -1.0, t_last = -1.0;
     std::string error;
+    // persistent mode: the batch ring (pinned, mapped), its device alias, the
+    // kernel's barrier state, its stream and an event recorded after its
+    // launch (complete once it returned), and the poller thread
+    PersistQueue* pq = nullptr;
+    PersistQueue* pq_dev = nullptr;
+    PersistSync* psync = nullptr;
+    cudaStream_t pstream = nullptr;
+    cudaEvent_t pexit = nullptr;
+    bool plaunched = false;
+    int pctas = 0;
+    uint32_t pposted = 0;                  // batches posted (host's count; pq->posted mirrors it)
+    ServeLane* pslot[kPersistRing] = {};   // the lane of posted batch b at b % kPersistRing
+    std::thread poller;
+    bool poller_stop = false;
 };
 
 namespace {
@@ -103,6 +118,128 @@ namespace {
 // network inputs (depth 4 + top-3 weights 12 + colour 3 + hole 1) and the
 // refined colour (3), bytes per pixel of a lane
 constexpr size_t kRefineBytesPerPixel = 23;
+
+// persistent mode: a grid barrier of the kernel gives up after 2 s
+constexpr uint64_t kPersistBarrierNs = 2000000000ull;
+
+// Whether the persistent kernel is (still) running; caller holds c->mu.
+bool persist_running(ServeState* st)
+{
+    if (!st->plaunched) return false;
+    const cudaError_t e = cudaEventQuery(st->pexit);
+    if (e == cudaErrorNotReady) return true;
+    if (e != cudaSuccess) cudaGetLastError();
+    return false;
+}
+
+// Launch the persistent kernel for the batches from pq->done on, unless it
+// runs; caller holds c->mu.
+fvv_status persist_launch(fvv_ctx* c, ServeState* st)
+{
+    if (persist_running(st)) return FVV_OK;
+    st->plaunched = false;
+    FVV_CUDA(cudaMemsetAsync(st->psync, 0, sizeof(PersistSync), st->pstream));
+    st->pq->err = 0;
+    int ctas = 0;
+    // the other CTAs wait at a grid barrier while CTA 0 waits for work: the
+    // barrier's limit stays above the idle limit
+    const uint64_t idle_ns = uint64_t(st->cfg.idle_us) * 1000ull;
+    const uint64_t wait_ns = std::max<uint64_t>(kPersistBarrierNs, idle_ns + 1000000000ull);
+    const cudaError_t e = launch_serve_persistent(st->pq_dev, st->psync, st->pq->done, st->cfg.max_width, c->n_cams,
+                                                  idle_ns, wait_ns, st->pstream, &ctas);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(FVV_ERR_CUDA, std::string("persistent serving kernel: ") + cudaGetErrorString(e));
+    }
+    FVV_CUDA(cudaEventRecord(st->pexit, st->pstream));
+    st->plaunched = true;
+    return FVV_OK;
+}
+
+// Batches [from, to) completed at time t (ok) or failed; caller holds st->mu.
+void persist_finish(ServeState* st, uint32_t from, uint32_t to, double t, bool ok)
+{
+    for (uint32_t b = from; b < to; ++b) {
+        ServeLane* L = st->pslot[b % kPersistRing];
+        st->pslot[b % kPersistRing] = nullptr;
+        if (!L) continue;
+        for (uint64_t tk : L->tickets) {
+            auto it = st->recs.find(tk);
+            if (it == st->recs.end()) continue;
+            if (!ok) {
+                it->second.state = ReqState::Failed;
+                ++st->failed;
+                continue;
+            }
+            it->second.state = ReqState::Done;
+            it->second.t_done = t;
+            st->lat_ms.push_back(1e3 * (t - it->second.t_submit));
+            ++st->completed;
+        }
+        L->tickets.clear();
+        L->busy = false;
+    }
+    if (ok) st->t_last = t;
+}
+
+// Poller: publishes the batches the kernel completed (their requests Done,
+// their lanes free), and relaunches the kernel when it returned (idle) with
+// batches still posted, or fails those batches when it returned because a
+// wait ran out.
+void persist_poller(ServeState* st)
+{
+    fvv_ctx* c = st->ctx;
+    cudaSetDevice(c->device);
+    uint32_t seen = st->pq->done;
+    for (;;) {
+        const uint32_t d = st->pq->done;
+        if (d != seen) {
+            const double t = now_s();
+            {
+                std::lock_guard<std::mutex> lk(st->mu);
+                persist_finish(st, seen, d, t, true);
+            }
+            st->cv.notify_all();
+            seen = d;
+            continue;
+        }
+        uint32_t posted;
+        {
+            std::lock_guard<std::mutex> lk(st->mu);
+            if (st->poller_stop) break;
+            posted = st->pposted;
+        }
+        if (posted != d) {
+            std::lock_guard<std::recursive_mutex> g(c->mu);
+            if (!persist_running(st) && st->pq->done == d) {
+                if (st->pq->err != 0) {
+                    // a wait of the kernel ran out: its pending batches fail
+                    {
+                        std::lock_guard<std::mutex> lk(st->mu);
+                        st->error = "a bounded wait of the persistent serving kernel ran out (code " +
+                                    std::to_string(st->pq->err) + ")";
+                        persist_finish(st, d, posted, now_s(), false);
+                    }
+                    st->pq->done = posted;
+                    seen = posted;
+                    st->cv.notify_all();
+                } else if (persist_launch(c, st) != FVV_OK) {
+                    std::lock_guard<std::mutex> lk(st->mu);
+                    st->error = fvv_last_error();
+                    persist_finish(st, d, posted, now_s(), false);
+                    st->pq->done = posted;
+                    seen = posted;
+                    st->cv.notify_all();
+                }
+            }
+        }
+        // a batch outstanding: poll again at once (latency); idle: sleep
+        if (posted != st->pq->done)
+            std::this_thread::yield();
+        else
+            std::this_thread::sleep_for(std::chrono::microseconds(50));
+    }
+}
 
 void CUDART_CB lane_done(void* p)
 {
@@ -175,6 +312,40 @@ fvv_status run_refined(fvv_ctx* c, ServeState* st, ServeLane* L, const std::vect
     FVV_TRY(refine_error_flag(&flag));
     FVV_CUDA(cudaMemcpyAsync(L->flag_host, flag, sizeof(int), cudaMemcpyDeviceToHost, st->refine_stream));
     return FVV_OK;
+}
+
+// Persistent mode: prepare the batch (parameters copied, waits for the
+// frames' uploads queued on the lane's stream), wait for that on the host,
+// then post it to the kernel's ring and make sure the kernel runs.  Its
+// completion comes through the poller.
+fvv_status persist_submit(fvv_ctx* c, ServeState* st, ServeLane* L, const std::vector<fvv_view>& views,
+                          std::vector<uint8_t*>& outs, std::vector<size_t>& pitches)
+{
+    PersistPost P;
+    P.ctas = st->pctas;
+    {
+        std::lock_guard<std::recursive_mutex> g(c->mu);
+        FVV_TRY(run_batch(c, L->S, int(views.size()), views.data(), nullptr, outs.data(), pitches.data(), nullptr,
+                          L->stream, false, &P));
+        FVV_CUDA(cudaEventRecord(L->plain_done, L->stream));
+    }
+    FVV_CUDA(cudaEventSynchronize(L->plain_done));
+    std::lock_guard<std::recursive_mutex> g(c->mu);
+    uint32_t b;
+    {
+        std::lock_guard<std::mutex> lk(st->mu);
+        b = st->pposted;
+        st->pslot[b % kPersistRing] = L;
+    }
+    st->pq->batch[b % kPersistRing] = P.batch;
+    for (int si : P.slots) c->slot[si].persist_reads = b + 1;
+    std::atomic_thread_fence(std::memory_order_seq_cst);      // the batch before its index
+    st->pq->posted = b + 1;
+    {
+        std::lock_guard<std::mutex> lk(st->mu);
+        st->pposted = b + 1;
+    }
+    return persist_launch(c, st);
 }
 
 void scheduler(ServeState* st)
@@ -266,7 +437,10 @@ void scheduler(ServeState* st)
             lk.unlock();
             fvv_status rc;
             std::string err;
-            {
+            if (st->cfg.persistent) {
+                rc = persist_submit(c, st, L, views, outs, pitches);
+                if (rc != FVV_OK) err = fvv_last_error();
+            } else {
                 std::lock_guard<std::recursive_mutex> g(c->mu);
                 cudaStream_t done_on = L->stream;
                 if (st->cfg.refine) {
@@ -343,6 +517,20 @@ fvv_status lane_refine_alloc(fvv_ctx* c, ServeLane& L, size_t px)
 
 bool serve_refining(fvv_ctx* c) { return c && c->serve && c->serve->cfg.refine; }
 
+fvv_status serve_wait_slot(fvv_ctx* c, const SlotState& slot)
+{
+    ServeState* st = c->serve;
+    if (!st || !st->pq || slot.persist_reads == 0) return FVV_OK;
+    const double t0 = now_s();
+    while (st->pq->done < slot.persist_reads) {
+        if (st->pq->err == 0 && !persist_running(st)) FVV_TRY(persist_launch(c, st));   // it returned, idle
+        if (now_s() - t0 > 2.0)
+            return fail(FVV_ERR_TIMEOUT, "a persistent serving batch still reads this frame slot after 2 s");
+        std::this_thread::sleep_for(std::chrono::microseconds(20));
+    }
+    return FVV_OK;
+}
+
 void serve_shutdown(fvv_ctx* c)
 {
     ServeState* st = c->serve;
@@ -353,8 +541,27 @@ void serve_shutdown(fvv_ctx* c)
     }
     st->cv.notify_all();
     if (st->thread.joinable()) st->thread.join();
+    if (st->pq) {
+        // every request finished; the kernel returns at its next wait for work
+        st->pq->stop = 1;
+        std::atomic_thread_fence(std::memory_order_seq_cst);
+        if (st->pstream) cudaStreamSynchronize(st->pstream);
+        {
+            std::lock_guard<std::mutex> lk(st->mu);
+            st->poller_stop = true;
+        }
+        if (st->poller.joinable()) st->poller.join();
+    }
     {
         std::lock_guard<std::recursive_mutex> g(c->mu);
+        if (st->pq) {
+            for (int si = 0; si < c->slots; ++si) c->slot[si].persist_reads = 0;
+            cudaFreeHost(st->pq);
+            st->pq = nullptr;
+            dev_free(c, st->psync, sizeof(PersistSync));
+            if (st->pexit) cudaEventDestroy(st->pexit);
+            if (st->pstream) cudaStreamDestroy(st->pstream);
+        }
         if (st->refine_stream) cudaStreamSynchronize(st->refine_stream);
         for (auto& L : st->lanes) lane_free(c, *L);
         if (st->refine_stream) cudaStreamDestroy(st->refine_stream);
@@ -379,6 +586,9 @@ fvv_status fvv_serve_default_cfg(fvv_serve_cfg* cfg)
     cfg->max_pending = 4096;
     cfg->memory_budget = uint64_t(768) << 20;
     cfg->refine = 0;
+    cfg->persistent = 0;
+    cfg->max_width = 1920;
+    cfg->idle_us = 20000;
     return FVV_OK;
 }
 
@@ -392,6 +602,16 @@ fvv_status fvv_serve_start(fvv_ctx* c, const fvv_serve_cfg* cfg_in)
     if (cfg.max_batch < 1 || cfg.max_batch > 4096 || cfg.max_pending < 1)
         return fail(FVV_ERR_INVALID_ARG, "max_batch must be in [1, 4096], max_pending >= 1");
     if (cfg.refine != 0 && cfg.refine != 1) return fail(FVV_ERR_INVALID_ARG, "refine must be 0 or 1");
+    if (cfg.persistent != 0 && cfg.persistent != 1) return fail(FVV_ERR_INVALID_ARG, "persistent must be 0 or 1");
+    if (cfg.persistent) {
+        if (cfg.refine) return fail(FVV_ERR_INVALID_ARG, "persistent serving renders plain views (refine = 0)");
+        if (c->opt.layered) return fail(FVV_ERR_INVALID_ARG, "persistent serving needs a single-layer context");
+        if (cfg.lanes > fvv::kPersistRing) return fail(FVV_ERR_INVALID_ARG, "persistent serving: at most 16 lanes");
+        if (cfg.idle_us < 100 || cfg.idle_us > 10000000)
+            return fail(FVV_ERR_INVALID_ARG, "idle_us must be in [100, 10000000]");
+        if (cfg.max_width < 1 || fvv::resolve_smem_bytes(cfg.max_width, c->n_cams, false) > c->smem_optin)
+            return fail(FVV_ERR_INVALID_ARG, "max_width must be >= 1 and fit the shared memory");
+    }
     if (c->serve) return fail(FVV_ERR_STATE, "serving loop already running");
     std::lock_guard<std::recursive_mutex> g(c->mu);
     if (cfg.refine && !fvv::refine_ready(c))
@@ -423,6 +643,8 @@ fvv_status fvv_serve_start(fvv_ctx* c, const fvv_serve_cfg* cfg_in)
         if (st->refine_stream) cudaStreamSynchronize(st->refine_stream);
         for (auto& l : st->lanes) fvv::lane_free(c, *l);
         if (st->refine_stream) cudaStreamDestroy(st->refine_stream);
+        if (st->pexit) cudaEventDestroy(st->pexit);
+        if (st->pstream) cudaStreamDestroy(st->pstream);
         return fail(rc, msg);
     };
     if (cfg.refine) {
@@ -440,15 +662,50 @@ fvv_status fvv_serve_start(fvv_ctx* c, const fvv_serve_cfg* cfg_in)
         if (rc == FVV_OK)
             rc = fvv::scratch_alloc(c, L->S, st->lane_keys, st->lane_stage, cfg.max_batch, 2);
         if (rc == FVV_OK && cfg.refine) rc = fvv::lane_refine_alloc(c, *L, lane_px);
+        if (rc == FVV_OK && cfg.persistent) {
+            e = cudaEventCreateWithFlags(&L->plain_done, cudaEventDisableTiming);
+            if (e != cudaSuccess) rc = FVV_ERR_CUDA;
+        }
         L->S.reader = 1 + i;
         st->lanes.push_back(std::move(L));
         if (rc != FVV_OK)
             return unwind(rc, e != cudaSuccess ? std::string("cudaStreamCreate: ") + cudaGetErrorString(e)
                                                : std::string(fvv_last_error()));
     }
+    if (cfg.persistent) {
+        void* q = nullptr;
+        cudaError_t e = cudaHostAlloc(&q, sizeof(fvv::PersistQueue), cudaHostAllocMapped);
+        if (e == cudaSuccess) {
+            std::memset(q, 0, sizeof(fvv::PersistQueue));
+            st->pq = static_cast<fvv::PersistQueue*>(q);
+            e = cudaHostGetDevicePointer(reinterpret_cast<void**>(&st->pq_dev), q, 0);
+        }
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&st->pstream, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&st->pexit, cudaEventDisableTiming);
+        if (e != cudaSuccess) {
+            if (st->pq) cudaFreeHost(st->pq);
+            st->pq = nullptr;
+            return unwind(FVV_ERR_CUDA, std::string("persistent serving setup: ") + cudaGetErrorString(e));
+        }
+        void* ps = nullptr;
+        if (fvv::dev_alloc(c, &ps, sizeof(fvv::PersistSync)) != FVV_OK) {
+            cudaFreeHost(st->pq);
+            st->pq = nullptr;
+            return unwind(FVV_ERR_OUT_OF_MEMORY, fvv_last_error());
+        }
+        st->psync = static_cast<fvv::PersistSync*>(ps);
+        st->pctas = fvv::persist_grid(cfg.max_width, c->n_cams);
+        if (st->pctas < 1) {
+            cudaFreeHost(st->pq);
+            st->pq = nullptr;
+            fvv::dev_free(c, ps, sizeof(fvv::PersistSync));
+            return unwind(FVV_ERR_CUDA, "persistent serving kernel: no resident CTA fits");
+        }
+    }
     ServeState* raw = st.release();
     c->serve = raw;
     raw->thread = std::thread(fvv::scheduler, raw);
+    if (raw->pq) raw->poller = std::thread(fvv::persist_poller, raw);
     return FVV_OK;
 }
 
@@ -463,6 +720,12 @@ fvv_status fvv_serve_submit(fvv_ctx* c, uint32_t viewer, const fvv_view* view, u
     if (fvv::resolve_smem_bytes(view->width, c->n_cams, c->opt.layered != 0) > c->smem_optin)
         return fail(FVV_ERR_INVALID_ARG, "view: width too large");
     if (pitch < size_t(view->width) * 3) return fail(FVV_ERR_INVALID_ARG, "pitch < 3 * width");
+    if (st->cfg.persistent) {
+        if (view->width > st->cfg.max_width)
+            return fail(FVV_ERR_INVALID_ARG, "view wider than the persistent kernel's max_width");
+        if (fvv::mem_kind(out) != fvv::MemKind::Device)
+            return fail(FVV_ERR_INVALID_ARG, "persistent serving writes device outputs only");
+    }
     if (st->cfg.refine) {
         if (view->width % 4 || view->height % 4)
             return fail(FVV_ERR_INVALID_ARG, "refined views need width and height multiples of 4");

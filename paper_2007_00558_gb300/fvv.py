@@ -72,7 +72,8 @@ class fvv_aux(C.Structure):
 
 class fvv_serve_cfg(C.Structure):
     _fields_ = [("lanes", C.c_int32), ("max_batch", C.c_int32), ("max_pending", C.c_int32),
-                ("memory_budget", C.c_uint64), ("refine", C.c_int32)]
+                ("memory_budget", C.c_uint64), ("refine", C.c_int32), ("persistent", C.c_int32),
+                ("max_width", C.c_int32), ("idle_us", C.c_uint32)]
 
 
 class fvv_serve_report(C.Structure):
@@ -150,6 +151,7 @@ def load() -> C.CDLL:
             "fvv_unet_conv3x3": [P, I, I, I, I, P, P, I, I, P, P, P],
             "fvv_unet_wgrad3x3": [P, I, I, I, I, I, P, I, P, P, P],
             "fvv_selftest_bounded_wait": [I, C.c_uint32, P],
+            "fvv_selftest_persistent_wait": [I, C.c_uint32, P],
             "fvv_unet_conv3x3_e4m3": [P, I, I, I, I, P, P, I, I, C.c_float, C.c_float, P, P],
             "fvv_unet_conv3x3_pool": [P, I, I, I, I, P, P, I, I, C.c_float, C.c_float, P, P, P, P],
             "fvv_depth_codec_default": [C.POINTER(fvv_depth_codec)],
@@ -520,6 +522,15 @@ def fvv_selftest_bounded_wait(arrive: bool, limit_us: int, stream=None) -> int:
     st = load().fvv_selftest_bounded_wait(1 if arrive else 0, limit_us, stream_handle(stream))
     if st not in (FVV_OK, FVV_ERR_TIMEOUT):
         _check(st, "fvv_selftest_bounded_wait")
+    return st
+
+
+def fvv_selftest_persistent_wait(barrier: bool, limit_us: int, stream=None) -> int:
+    """Returns the raw status (FVV_ERR_TIMEOUT is the expected outcome);
+    other failures raise."""
+    st = load().fvv_selftest_persistent_wait(1 if barrier else 0, limit_us, stream_handle(stream))
+    if st != FVV_ERR_TIMEOUT:
+        _check(st, "fvv_selftest_persistent_wait")
     return st
 
 

@@ -239,3 +239,93 @@ def test_serve_refined_equals_alone(rig_small, precision):
         assert changed == len(reqs)                              # the network did run
     finally:
         F.fvv_destroy(ctx)
+
+
+# ---- persistent serving kernel ---------------------------------------------
+def test_persistent_kernel_waits_run_out_cleanly(rig_small):
+    """The persistent kernel's wait for work returns after its idle limit, and
+    a grid barrier that cannot complete gives up after its limit and reports
+    it; the CUDA context keeps working (a synthesis still matches)."""
+    import torch
+    F = lib()
+    t0 = time.perf_counter()
+    assert F.fvv_selftest_persistent_wait(False, 30000) == F.FVV_ERR_TIMEOUT
+    assert "idle" in F.fvv_last_error()
+    assert time.perf_counter() - t0 < 1.5
+    t0 = time.perf_counter()
+    assert F.fvv_selftest_persistent_wait(True, 40000) == F.FVV_ERR_TIMEOUT
+    assert "barrier" in F.fvv_last_error()
+    assert 0.03 <= time.perf_counter() - t0 < 1.5
+    wl = rig_small
+    ctx = _ctx_with_frames(F, wl)
+    try:
+        v = wl["views"][5]
+        a = torch.zeros((v.height, v.width * 3), dtype=torch.uint8, device="cuda")
+        F.fvv_synthesize(ctx, v, a, v.width * 3)
+        torch.cuda.synchronize()
+        assert int(a.float().sum().item()) > 0
+    finally:
+        F.fvv_destroy(ctx)
+
+
+def test_persistent_serve_equals_alone_and_relaunches_after_idle(rig_small):
+    """Mixed resolutions served through the persistent kernel equal the same
+    views synthesised alone byte for byte; a request after the kernel went
+    idle (and returned) relaunches it; an upload while batches run waits for
+    the batches that read its slot."""
+    import torch
+    F = lib()
+    wl = rig_small
+    rng = np.random.default_rng(11)
+    sizes = [(640, 360, 250.0), (640, 360, 250.0), (1280, 720, 500.0), (1920, 1080, 750.0)]
+    reqs = []
+    for i in range(40):
+        W, H, f = sizes[rng.integers(0, 4)]
+        reqs.append((i % 4, _view(wl["views"][int(rng.integers(0, 300))], W, H, f)))
+    ctx = _ctx_with_frames(F, wl, frame_slots=2)
+    H0, W0 = wl["cams"][0].height, wl["cams"][0].width
+    try:
+        F.fvv_serve_start(ctx, F.fvv_serve_default_cfg(lanes=3, max_batch=4, memory_budget=512 << 20,
+                                                        persistent=1, max_width=1920, idle_us=20000))
+        # a host output is refused in this mode
+        with pytest.raises(F.FvvError) as e:
+            F.fvv_serve_submit(ctx, 0, reqs[0][1], np.zeros((reqs[0][1].height, reqs[0][1].width * 3), np.uint8),
+                               reqs[0][1].width * 3)
+        assert e.value.code == F.FVV_ERR_INVALID_ARG
+        outs = [torch.zeros((v.height, v.width * 3), dtype=torch.uint8, device="cuda") for _, v in reqs]
+        torch.cuda.synchronize()
+        tickets = []
+        for i, ((viewer, v), o) in enumerate(zip(reqs, outs)):
+            tickets.append(F.fvv_serve_submit(ctx, viewer, v, o, v.width * 3))
+            if i == 19:
+                time.sleep(0.002)
+        for t in tickets:
+            F.fvv_serve_poll(ctx, t, 5_000_000)
+        st = F.fvv_serve_stats(ctx)
+        assert st["completed"] == 40 and st["failed"] == 0
+        # idle longer than the kernel's limit: it returns; the next request relaunches it
+        time.sleep(0.1)
+        v = reqs[0][1]
+        late = torch.zeros_like(outs[0])
+        F.fvv_serve_poll(ctx, F.fvv_serve_submit(ctx, 9, v, late, v.width * 3), 5_000_000)
+        assert torch.equal(late, outs[0])
+        # uploads of new ticks into the two-slot ring while requests run
+        more = []
+        for k in range(6):
+            for cam in range(len(wl["cams"])):
+                F.fvv_upload_frame(ctx, cam, np.ascontiguousarray(wl["rgb"][cam]), W0 * 3,
+                                   np.ascontiguousarray(wl["depth"][cam]), W0 * 2, 1 + k)
+            o = torch.zeros_like(outs[k])
+            more.append((o, F.fvv_serve_submit(ctx, k, reqs[k][1], o, reqs[k][1].width * 3)))
+        for o, t in more:
+            F.fvv_serve_poll(ctx, t, 5_000_000)
+        F.fvv_serve_stop(ctx)
+        for k, (o, _) in enumerate(more):          # the same frames in every tick: the same views
+            assert torch.equal(o, outs[k])
+        for (viewer, v), o in zip(reqs, outs):
+            ref = torch.zeros((v.height, v.width * 3), dtype=torch.uint8, device="cuda")
+            F.fvv_synthesize(ctx, v, ref, v.width * 3)
+            torch.cuda.synchronize()
+            assert torch.equal(o, ref)
+    finally:
+        F.fvv_destroy(ctx)
