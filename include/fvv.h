@@ -291,6 +291,19 @@ fvv_status fvv_depth_encode_yuv(fvv_ctx* ctx, int32_t cam, const uint16_t* depth
 fvv_status fvv_depth_decode_yuv(fvv_ctx* ctx, int32_t cam, const uint8_t* y, size_t y_pitch, const uint8_t* u,
                                 const uint8_t* v, size_t uv_pitch, uint16_t* depth, size_t depth_pitch,
                                 void* stream);
+/* The decoder over every camera 0 .. n_cams-1 of one tick in one launch:
+ * camera k's depth as one dense planar YUV420 frame at yuv + k *
+ * yuv_cam_stride (Y: height rows of width bytes, then U and V: height/2 rows
+ * of width/2 bytes each, the layout fvv_upload_frames_yuv takes), its codes
+ * at depth + k * depth_cam_stride (height rows, pitch depth_pitch bytes).
+ * Cameras of one size, even width and height, each with a codec set; device
+ * memory; asynchronous on `stream`.  With width a multiple of 16 and 16-byte
+ * aligned frames, strides and pitches the kernel moves 16 bytes per access;
+ * otherwise it decodes frame after frame like fvv_depth_decode_yuv.  Errors:
+ * INVALID_ARG (sizes, strides, pitches, host memory), STATE (a camera without
+ * codec), CUDA. */
+fvv_status fvv_depth_decode_yuv_frames(fvv_ctx* ctx, int32_t n_cams, const uint8_t* yuv, size_t yuv_cam_stride,
+                                       uint16_t* depth, size_t depth_cam_stride, size_t depth_pitch, void* stream);
 /* fvv_upload_frame with the depth given as a YUV420 depth frame: the decode
  * runs fused into the upload and writes the frame ring directly.  rgb and
  * the planes may be host or device memory (the three planes alike). */

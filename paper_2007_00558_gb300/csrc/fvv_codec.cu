@@ -117,6 +117,117 @@ __global__ void __launch_bounds__(512) k_yuv_decode(YuvDepth f, int bw, int bh, 
         decode_block(f, f.lut, int(i % bw), int(i / bw), out, opitch);
 }
 
+// 16 x 2 pixels (eight 2x2 blocks) per thread with 16-byte accesses: two
+// 16-byte Y row pieces, 8 bytes of U and of V, four 16-byte stores of codes.
+// The 4 MSBs of a pixel are the even (left pixel) or odd (right pixel) bits
+// of its block's U (top row) or V (bottom row) byte, gathered by two
+// mask-and-shift steps.
+__device__ __forceinline__ uint32_t msb_of(uint32_t uvbyte, uint32_t right)
+{
+    uint32_t m = (uvbyte >> right) & 0x55u;
+    m = (m | (m >> 1)) & 0x33u;
+    return (m | (m >> 2)) & 0x0Fu;
+}
+
+__device__ __forceinline__ void decode_16x2(const uint8_t* y0, const uint8_t* y1, const uint8_t* u, const uint8_t* v,
+                                            const uint16_t* __restrict__ lut, uint16_t* o0, uint16_t* o1)
+{
+    const uint4 Y0 = *reinterpret_cast<const uint4*>(y0);
+    const uint4 Y1 = *reinterpret_cast<const uint4*>(y1);
+    const uint2 U = *reinterpret_cast<const uint2*>(u);
+    const uint2 V = *reinterpret_cast<const uint2*>(v);
+    const uint32_t yw[2][4] = {{Y0.x, Y0.y, Y0.z, Y0.w}, {Y1.x, Y1.y, Y1.z, Y1.w}};
+    const uint32_t cw[2][2] = {{U.x, U.y}, {V.x, V.y}};
+    uint32_t out[2][8];
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {                 // pixels 4q .. 4q + 3: blocks 2q, 2q + 1
+            const uint32_t cb = cw[r][q >> 1] >> (16 * (q & 1));
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {             // block 2q + h: pixels 4q + 2h (left), 4q + 2h + 1 (right)
+                const uint32_t byte = (cb >> (8 * h)) & 0xFFu;
+                uint32_t codes = 0;
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    const uint32_t yb = (yw[r][q] >> (8 * (2 * h + e))) & 0xFFu;
+                    const uint32_t m = msb_of(byte, uint32_t(e));
+                    const uint32_t y12 = (m << 8) | ((m & 1u) ? 255u - yb : yb);
+                    codes |= uint32_t(__ldg(lut + y12)) << (16 * e);
+                }
+                out[r][2 * q + h] = codes;
+            }
+        }
+    }
+    uint4* d0 = reinterpret_cast<uint4*>(o0);
+    uint4* d1 = reinterpret_cast<uint4*>(o1);
+    d0[0] = make_uint4(out[0][0], out[0][1], out[0][2], out[0][3]);
+    d0[1] = make_uint4(out[0][4], out[0][5], out[0][6], out[0][7]);
+    d1[0] = make_uint4(out[1][0], out[1][1], out[1][2], out[1][3]);
+    d1[1] = make_uint4(out[1][4], out[1][5], out[1][6], out[1][7]);
+}
+
+// Frames of cameras 0 .. n-1 of one size: camera k's planes at y/u/v + k *
+// cam_stride, its codes at out + k * out_cam_stride.  Work item = (camera,
+// block row, 16-pixel column group), grid-stride.
+struct YuvFrames {
+    const uint8_t *y, *u, *v;
+    size_t y_pitch, uv_pitch, cam_stride;
+    uint16_t* out;
+    size_t out_pitch, out_cam_stride;
+    int groups, block_rows, n;
+    const uint16_t* lut[kMaxCams];
+};
+
+__global__ void __launch_bounds__(256) k_yuv_decode16(const __grid_constant__ YuvFrames f)
+{
+    const size_t per_cam = size_t(f.groups) * f.block_rows;
+    const size_t n = per_cam * f.n;
+    for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += size_t(gridDim.x) * blockDim.x) {
+        const int k = int(i / per_cam);
+        const size_t r = i - size_t(k) * per_cam;
+        const int by = int(r / f.groups), g = int(r - size_t(by) * f.groups);
+        const size_t cs = size_t(k) * f.cam_stride;
+        const uint8_t* y0 = f.y + cs + size_t(2 * by) * f.y_pitch + 16 * g;
+        const size_t uvo = cs + size_t(by) * f.uv_pitch + 8 * g;
+        uint16_t* o0 = reinterpret_cast<uint16_t*>(reinterpret_cast<uint8_t*>(f.out) + size_t(k) * f.out_cam_stride +
+                                                   size_t(2 * by) * f.out_pitch) + 16 * g;
+        uint16_t* o1 = reinterpret_cast<uint16_t*>(reinterpret_cast<uint8_t*>(o0) + f.out_pitch);
+        decode_16x2(y0, y0 + f.y_pitch, f.u + uvo, f.v + uvo, f.lut[k], o0, o1);
+    }
+}
+
+bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+// The 16-byte form applies when every access it makes is aligned.
+bool vec16_ok(const YuvFrames& f, int width)
+{
+    return width % 16 == 0 && aligned(f.y, 16) && f.y_pitch % 16 == 0 && aligned(f.u, 8) && aligned(f.v, 8) &&
+           f.uv_pitch % 8 == 0 && f.cam_stride % 16 == 0 && aligned(f.out, 16) && f.out_pitch % 16 == 0 &&
+           f.out_cam_stride % 16 == 0;
+}
+
+int device_sm_count()
+{
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
+            sms = 1;
+    }
+    return sms;
+}
+
+cudaError_t launch_decode16(const YuvFrames& f, cudaStream_t s)
+{
+    const size_t n = size_t(f.groups) * f.block_rows * f.n;
+    if (n == 0) return cudaSuccess;
+    const size_t want = (n + 255) / 256, cap = size_t(device_sm_count()) * 8;
+    k_yuv_decode16<<<unsigned(want < cap ? want : cap), 256, 0, s>>>(f);
+    return cudaGetLastError();
+}
+
 __global__ void __launch_bounds__(256) k_yuv_encode(const uint16_t* __restrict__ depth, size_t dpitch, int bw,
                                                     int bh, const uint16_t* __restrict__ lut, uint8_t* __restrict__ y,
                                                     size_t ypitch, uint8_t* __restrict__ u, uint8_t* __restrict__ v,
@@ -160,13 +271,22 @@ cudaError_t launch_yuv_decode(const YuvDepth& f, int width, int height, uint16_t
     const int bw = width / 2, bh = height / 2;
     const size_t n = size_t(bw) * bh;
     if (n == 0) return cudaSuccess;
-    static int sms = 0;
-    if (!sms) {
-        int dev = 0;
-        if (cudaGetDevice(&dev) != cudaSuccess ||
-            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
-            sms = 1;
-    }
+    YuvFrames v{};
+    v.y = f.y;
+    v.u = f.u;
+    v.v = f.v;
+    v.y_pitch = f.y_pitch;
+    v.uv_pitch = f.uv_pitch;
+    v.cam_stride = 0;
+    v.out = out;
+    v.out_pitch = out_pitch;
+    v.out_cam_stride = 0;
+    v.groups = width / 16;
+    v.block_rows = bh;
+    v.n = 1;
+    v.lut[0] = f.lut;
+    if (vec16_ok(v, width)) return launch_decode16(v, s);
+    const int sms = device_sm_count();
     const size_t want = (n + 511) / 512;
     const unsigned grid = unsigned(want < size_t(2 * sms) ? want : size_t(2 * sms));
     k_yuv_decode<<<grid, 512, 0, s>>>(f, bw, bh, out, out_pitch);
@@ -276,6 +396,55 @@ fvv_status fvv_depth_decode_yuv(fvv_ctx* c, int32_t cam, const uint8_t* y, size_
     const fvv::YuvDepth f{y, u, v, y_pitch, uv_pitch, c->codec->dec[cam]};
     std::lock_guard<std::recursive_mutex> g(c->mu);
     return fvv::run_kernel(c, fvv::kDecode, s, [&] { return fvv::launch_yuv_decode(f, W, H, depth, depth_pitch, s); });
+}
+
+fvv_status fvv_depth_decode_yuv_frames(fvv_ctx* c, int32_t n_cams, const uint8_t* yuv, size_t yuv_cam_stride,
+                                       uint16_t* depth, size_t depth_cam_stride, size_t depth_pitch, void* stream)
+{
+    if (!c) return fail(FVV_ERR_INVALID_ARG, "ctx is NULL");
+    if (n_cams < 1 || n_cams > c->n_cams) return fail(FVV_ERR_INVALID_ARG, "n_cams out of range");
+    for (int k = 0; k < n_cams; ++k) {
+        FVV_TRY(fvv::check_cam(c, k));
+        if (c->cams[k].width != c->cams[0].width || c->cams[k].height != c->cams[0].height)
+            return fail(FVV_ERR_INVALID_ARG, "cameras of one size only");
+    }
+    const int W = c->cams[0].width, H = c->cams[0].height;
+    const size_t frame = size_t(W) * H + 2 * size_t(W / 2) * (H / 2);
+    if (!fvv::on_dev(yuv) || !fvv::on_dev(depth))
+        return fail(FVV_ERR_INVALID_ARG, "yuv and depth must be device memory");
+    if (yuv_cam_stride < frame || depth_pitch < size_t(W) * 2 || depth_cam_stride < depth_pitch * size_t(H) ||
+        depth_pitch % 4 || depth_cam_stride % 4 || reinterpret_cast<uintptr_t>(depth) % 4)
+        return fail(FVV_ERR_INVALID_ARG, "stride or pitch too small, or depth not 4-byte aligned");
+    cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : c->own;
+    fvv::YuvFrames f{};
+    f.y = yuv;
+    f.u = yuv + size_t(W) * H;
+    f.v = f.u + size_t(W / 2) * (H / 2);
+    f.y_pitch = size_t(W);
+    f.uv_pitch = size_t(W / 2);
+    f.cam_stride = yuv_cam_stride;
+    f.out = depth;
+    f.out_pitch = depth_pitch;
+    f.out_cam_stride = depth_cam_stride;
+    f.groups = W / 16;
+    f.block_rows = H / 2;
+    f.n = n_cams;
+    for (int k = 0; k < n_cams; ++k) f.lut[k] = c->codec->dec[k];
+    std::lock_guard<std::recursive_mutex> g(c->mu);
+    if (fvv::vec16_ok(f, W))
+        return fvv::run_kernel(c, fvv::kDecode, s, [&] { return fvv::launch_decode16(f, s); });
+    // unaligned or ragged: the per-frame form, camera after camera
+    return fvv::run_kernel(c, fvv::kDecode, s, [&] {
+        for (int k = 0; k < n_cams; ++k) {
+            const uint8_t* y = yuv + size_t(k) * yuv_cam_stride;
+            const fvv::YuvDepth d{y, y + size_t(W) * H, y + size_t(W) * H + size_t(W / 2) * (H / 2), size_t(W),
+                                  size_t(W / 2), c->codec->dec[k]};
+            uint16_t* o = reinterpret_cast<uint16_t*>(reinterpret_cast<uint8_t*>(depth) + size_t(k) * depth_cam_stride);
+            const cudaError_t e = fvv::launch_yuv_decode(d, W, H, o, depth_pitch, s);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    });
 }
 
 fvv_status fvv_upload_frame_yuv(fvv_ctx* c, int32_t cam, const uint8_t* rgb, size_t rgb_pitch, const uint8_t* y,

@@ -158,6 +158,7 @@ def load() -> C.CDLL:
             "fvv_set_depth_codec": [P, I, C.POINTER(fvv_depth_codec)],
             "fvv_depth_encode_yuv": [P, I, P, S, P, S, P, P, S, P],
             "fvv_depth_decode_yuv": [P, I, P, S, P, P, S, P, S, P],
+            "fvv_depth_decode_yuv_frames": [P, I, P, S, P, S, S, P],
             "fvv_upload_frame_yuv": [P, I, P, S, P, S, P, P, S, U64, P],
             "fvv_refine_quantize": [P, C.POINTER(fvv_refine_batch), P, P],
             "fvv_refine_set_precision": [P, I],
@@ -481,6 +482,12 @@ def fvv_depth_decode_yuv(ctx: int, cam: int, y, y_pitch: int, u, v, uv_pitch: in
                          stream=None) -> None:
     _check(load().fvv_depth_decode_yuv(ctx, cam, ptr(y), y_pitch, ptr(u), ptr(v), uv_pitch, ptr(depth),
                                        depth_pitch, stream_handle(stream)), "fvv_depth_decode_yuv")
+
+
+def fvv_depth_decode_yuv_frames(ctx: int, n_cams: int, yuv, yuv_cam_stride: int, depth, depth_cam_stride: int,
+                                depth_pitch: int, stream=None) -> None:
+    _check(load().fvv_depth_decode_yuv_frames(ctx, n_cams, ptr(yuv), yuv_cam_stride, ptr(depth), depth_cam_stride,
+                                              depth_pitch, stream_handle(stream)), "fvv_depth_decode_yuv_frames")
 
 
 def fvv_upload_frame_yuv(ctx: int, cam: int, rgb, rgb_pitch: int, y, y_pitch: int, u, v, uv_pitch: int,

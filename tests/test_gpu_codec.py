@@ -175,3 +175,62 @@ def test_batched_yuv_tick_upload(setup, oracle_mod, mode):
         assert (d <= 1).all(axis=-1).mean() >= 0.999
     finally:
         F.fvv_destroy(ctx)
+
+
+@pytest.mark.parametrize("width,height,pad", [(320, 180, 0), (336, 40, 64), (330, 18, 0), (320, 20, 4)])
+def test_decode_tick_in_one_call(width, height, pad):
+    """fvv_depth_decode_yuv_frames over four cameras of one tick equals the
+    oracle's decode of each frame: the 16-byte form (width a multiple of 16,
+    aligned strides; also with padded depth rows) and the frame-by-frame
+    form (width 330, or a depth pitch that is not a multiple of 16)."""
+    import torch
+    F = lib()
+    base = S.workload("plain_2cam_320x240")["cams"][0]
+    cams = []
+    for k in range(4):
+        c = base.copy()
+        c.width, c.height = width, height
+        c.t = c.t + np.array([0.05 * k, 0.0, 0.0])
+        cams.append(c)
+    ctx = F.fvv_create(F.rig(cams, np.zeros(3)))
+    try:
+        codecs = [dict(z_near=0.3 + 0.1 * k, z_far=6.0 + k, alpha=0.0, beta=1.0) for k in range(4)]
+        for k in range(4):
+            F.fvv_set_depth_codec(ctx, k, F.fvv_depth_codec_default(**codecs[k]))
+        rng = np.random.default_rng(width + height + pad)
+        H, W = height, width
+        frame = H * W + 2 * (H // 2) * (W // 2)
+        stride = (frame + 15) // 16 * 16
+        yuv = rng.integers(0, 256, (4, stride), dtype=np.uint8)
+        pitch = W * 2 + pad
+        out = torch.full((4, H, pitch // 2), -7, dtype=torch.int16, device="cuda")
+        F.fvv_depth_decode_yuv_frames(ctx, 4, torch.from_numpy(yuv).cuda(), stride, out, H * pitch, pitch)
+        torch.cuda.synchronize()
+        got = out.cpu().numpy().view(np.uint16)
+        for k in range(4):
+            b = yuv[k]
+            Y = b[:H * W].reshape(H, W)
+            U = b[H * W:H * W + (H // 2) * (W // 2)].reshape(H // 2, W // 2)
+            V = b[H * W + (H // 2) * (W // 2):frame].reshape(H // 2, W // 2)
+            ref = K.decode(Y, U, V, codecs[k]["z_near"], codecs[k]["z_far"], 0.001)
+            assert np.array_equal(got[k, :, :W], ref), k
+            assert (got[k, :, W:] == np.uint16(0xFFF9)).all()              # padding untouched
+    finally:
+        F.fvv_destroy(ctx)
+
+
+def test_decode_tick_errors(setup):
+    import torch
+    F, ctx, wl = setup
+    H, W = wl["depth"][0].shape
+    frame = H * W + 2 * (H // 2) * (W // 2)
+    yuv = torch.zeros((9, frame), dtype=torch.uint8, device="cuda")
+    out = torch.zeros((9, H, W), dtype=torch.int16, device="cuda")
+    for args in ((0, yuv, frame, out, H * W * 2, W * 2),          # no camera
+                 (10, yuv, frame, out, H * W * 2, W * 2),         # more cameras than the rig
+                 (9, yuv, frame - 1, out, H * W * 2, W * 2),      # overlapping frames
+                 (9, yuv, frame, out, H * W * 2, W * 2 - 2),      # pitch too small
+                 (9, yuv.cpu(), frame, out, H * W * 2, W * 2)):   # host memory
+        with pytest.raises(F.FvvError) as e:
+            F.fvv_depth_decode_yuv_frames(ctx, *args)
+        assert e.value.code == F.FVV_ERR_INVALID_ARG
