@@ -64,9 +64,9 @@ fvv_status check_flag(int* flag, cudaStream_t s, const char* what)
 
 bool on_device(const void* p) { return p && mem_kind(p) == MemKind::Device; }
 
-// the 8 input features occupy one 64-byte row per pixel (zeros after them)
-constexpr int kX0Stride = 32;     // bf16 channels
-constexpr int kX0StrideQ = 64;    // e4m3 bytes
+// the 8 input features: 16 bytes per pixel (e4m3: 8 codes, 8 zero bytes)
+constexpr int kX0Stride = 8;      // bf16 channels
+constexpr int kX0StrideQ = 16;    // e4m3 bytes
 
 
 }  // namespace
@@ -258,9 +258,6 @@ fvv_status ensure_acts(fvv_ctx* c, RefineNet& N, size_t pixels)
     FVV_TRY(alloc_t(c, N.acts, &N.arg1, p2 * w1));
     FVV_TRY(alloc_t(c, N.acts, &N.arg2, p3 * w2));
     FVV_TRY(alloc_t(c, N.acts, &N.s, p1 * 3));
-    // the feature rows' padding channels are written once, here; the packing
-    // kernel writes only the eight features of each row
-    FVV_CUDA(cudaMemset(N.x0, 0, p1 * kX0Stride * sizeof(__nv_bfloat16)));
     FVV_CUDA(cudaDeviceSynchronize());
     N.cap = pixels;
     return FVV_OK;
@@ -481,8 +478,6 @@ fvv_status ensure_acts8(fvv_ctx* c, RefineNet& N, size_t pixels)
     const int w1 = N.L[1].cout, w2 = N.L[3].cout, w3 = N.L[5].cout;
     auto A = [&](uint8_t** p, size_t n) { return alloc_t(c, N.acts8, p, n); };
     FVV_TRY(A(&N.q_x0, p1 * kX0StrideQ));
-    FVV_CUDA(cudaMemset(N.q_x0, 0, p1 * kX0StrideQ));             // padding bytes, written once
-    FVV_CUDA(cudaDeviceSynchronize());
     FVV_TRY(A(&N.q_e1a, p1 * w1));
     FVV_TRY(A(&N.q_p1, p2 * w1));
     FVV_TRY(A(&N.q_e2a, p2 * w2));

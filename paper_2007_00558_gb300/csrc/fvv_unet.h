@@ -14,6 +14,7 @@ struct ConvArgs {
     int xstride;                    // input channels per pixel in memory (0: Cin); channels
                                     // Cin..xstride-1 are read but must hold zeros
     int tiles_x;                    // tiles per image row, set by the launcher
+    int x_quads;                    // set by the launcher: 16-byte pixels copied four to a row
     const float* bias;              // [Cout] or null (16-byte aligned)
     __nv_bfloat16* y;               // output pixel p, channel c at y[p * ldy + coff + c] (e4m3: bytes)
     int ldy, coff;                  // output channel stride (0: Cout) and offset

@@ -23,6 +23,17 @@
 // or 1x1 output head) drains tile i while the MMA thread accumulates the
 // next ones.
 //
+// C8 (the first layer: 8 input features in 16 bytes per pixel, bf16, or 8
+// e4m3 codes and 8 zero bytes): the halo is copied as rows of 16 bytes, one
+// per pixel, without swizzle, and each MMA (K = 16 bytes x 2) takes two taps
+// at once -- the descriptor's second K core matrix is the next pixel (tap
+// kx + 1) or the next halo row (tap ky + 1) -- against a weight tile stored
+// tap by tap: five MMAs per output row instead of nine, and a quarter of the
+// halo bytes.  A tenth, zero weight tap pads the odd ninth.  Where the image
+// width is a multiple of 4 the copy sees four pixels as one 64-byte row (a
+// TMA copy costs per row): the halo then starts at pixel x0 - 4, three
+// pixels before the window, and the descriptors start three pixels on.
+//
 // Warp roles (320 threads): 0 = TMA producer, 1 = TMEM owner and MMA issuer,
 // 2..9 = epilogue in two groups of four, taking alternate tiles (warp w
 // reads TMEM lanes 32 (w mod 4) .. +31); two warps per sub-partition hide
@@ -123,6 +134,36 @@ Plan make_plan(int groups, bool fp8, bool want_out)
             p.hs = 3;
             p.ws = ws;
             p.smem = fixed + p.hs * C::kHaloStage + p.ws * C::kSlice;
+            return p;
+        }
+    }
+    return p;
+}
+
+// C8: halo rows of kC8Px pixels x 16 bytes; weights as 10 tap tiles of COUT x 16 bytes
+constexpr int kC8Px = 136;
+template <int COUT>
+struct C8Cfg {
+    static constexpr int kHaloRows = ConvCfg<COUT>::kHaloRows;
+    static constexpr int kHaloBytes = kHaloRows * kC8Px * 16;
+    static constexpr int kHaloStage = (kHaloBytes + 1023) / 1024 * 1024;
+    static constexpr int kTap = COUT * 16;
+    static constexpr int kWBytes = (10 * kTap + 1023) / 1024 * 1024;
+};
+
+template <int COUT>
+Plan make_plan_c8(bool fp8, bool want_out)
+{
+    using C = C8Cfg<COUT>;
+    Plan p{};
+    for (int out = want_out ? 2 : 0; out >= 0; --out) {
+        const int fixed = kSmemFixed + out * 8 * ConvCfg<COUT>::out_buf(fp8);
+        if (fixed + C::kWBytes + 2 * C::kHaloStage <= kSmemLimit) {
+            p.resident = 1;
+            p.out = out;
+            p.hs = std::min(kMaxStages, (kSmemLimit - fixed - C::kWBytes) / C::kHaloStage);
+            p.ws = 0;
+            p.smem = fixed + C::kWBytes + p.hs * C::kHaloStage;
             return p;
         }
     }
@@ -252,13 +293,17 @@ __device__ __forceinline__ uint32_t pool4_e4m3(const uint32_t (&c)[4])
 
 // FP8: e4m3 operands and output (K = 32 channels per MMA, 64 per group);
 // otherwise bf16 (K = 16, 32 per group).
-template <int COUT, bool FP8, bool FOLD, bool WIDE>
+template <int COUT, bool FP8, bool FOLD, bool WIDE, bool C8>
 __global__ void __launch_bounds__(kThreads, 1)
 k_conv3x3_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUtensorMap tmw,
              const __grid_constant__ CUtensorMap tmy, const __grid_constant__ CUtensorMap tmy2, ConvArgs P,
              int n_tiles, int HS, int WS, int resident, int tma_out)
 {
     using Cfg = ConvCfg<COUT, FOLD, WIDE>;
+    static_assert(!C8 || (!FOLD && !WIDE && COUT <= 64), "the 16-byte-pixel form is for the first layer");
+    // halo stage size and bytes per copy (C8: 16-byte pixel rows)
+    constexpr int kStage = C8 ? C8Cfg<COUT>::kHaloStage : Cfg::kHaloStage;
+    constexpr int kHaloTx = C8 ? C8Cfg<COUT>::kHaloBytes : Cfg::kHaloBytes;
     static_assert(512 + 4 * COUT <= kHeader, "bias fits the header");
     static_assert(COUT > 64 || 768 + 4 * (3 * COUT + 3) <= kHeader, "head weights fit the header");
     constexpr int kPerGroup = FP8 ? 64 : 32;           // channels in one 64-byte row
@@ -280,7 +325,7 @@ k_conv3x3_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CU
     float* s_head = reinterpret_cast<float*>(base + 768);          // fused head: [3][COUT] weights, [3] bias
     uint8_t* sOut = base + kHeader;                                  // [8 warps][tma_out][kOutBuf]
     uint8_t* sHalo = sOut + tma_out * 8 * kOutBuf;
-    uint8_t* sW = sHalo + HS * Cfg::kHaloStage;
+    uint8_t* sW = sHalo + HS * kStage;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) *skip = *reinterpret_cast<volatile int*>(P.err);
@@ -288,7 +333,7 @@ k_conv3x3_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CU
     if (*skip) return;                                 // an earlier CTA gave up
 
     const int Cin = P.Cin, H = P.H, Wd = P.W;
-    const int G = (Cin + kPerGroup - 1) / kPerGroup;
+    const int G = C8 ? 1 : (Cin + kPerGroup - 1) / kPerGroup;
     constexpr int R = Cfg::kRows;
     const int tiles_y = (H + R - 1) / R;
 
@@ -317,6 +362,12 @@ k_conv3x3_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CU
     for (int i = threadIdx.x; i < COUT; i += kThreads) s_bias[i] = P.bias ? P.bias[i] : 0.0f;
     if (COUT <= 64 && P.head_w)
         for (int i = threadIdx.x; i < 3 * COUT + 3; i += kThreads) s_head[i] = i < 3 * COUT ? P.head_w[i] : P.head_b[i - 3 * COUT];
+    if (C8) {
+        // the zero tenth tap, visible to the tensor cores (async proxy)
+        uint4* z = reinterpret_cast<uint4*>(sW + 9 * C8Cfg<COUT>::kTap);
+        for (int i = threadIdx.x; i < COUT; i += kThreads) z[i] = make_uint4(0u, 0u, 0u, 0u);
+        tc::fence_proxy_async_smem();
+    }
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
@@ -325,7 +376,10 @@ k_conv3x3_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CU
     if (warp == 0) {
         // ------------------------------------------------------------ TMA producer
         if (lane == 0) {
-            if (resident) {
+            if (C8) {
+                tc::mbar_arrive_expect_tx(wready, uint32_t(9 * C8Cfg<COUT>::kTap));
+                tc::tma_load_3d(sW, &tmw, wready, 0, 0, 0);
+            } else if (resident) {
                 tc::mbar_arrive_expect_tx(wready, uint32_t(G * Cfg::kGroup));
                 for (int g = 0; g < G; ++g)
                     for (int ky = 0; ky < 3; ++ky)
@@ -344,19 +398,21 @@ k_conv3x3_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CU
                         ok = false;
                         break;
                     }
-                    tc::mbar_arrive_expect_tx(&full_h[sh], Cfg::kHaloBytes);
-                    if constexpr (Cfg::kFold) {
+                    tc::mbar_arrive_expect_tx(&full_h[sh], kHaloTx);
+                    if constexpr (C8) {
+                        tc::tma_load_4d(sHalo + sh * kStage, &tmx, &full_h[sh], 0, P.x_quads ? x0 / 4 - 1 : x0 - 1,
+                                        y0 - 1, n);
+                    } else if constexpr (Cfg::kFold) {
                         // one 32-pixel window per lane quadrant and halo row
                         for (int h = 0; h < Cfg::kHaloRows; ++h)
                             for (int k = 0; k < 4; ++k)
-                                tc::tma_load_4d(sHalo + sh * Cfg::kHaloStage + (h * Cfg::kHaloPx + 32 * k) * kRow, &tmx,
+                                tc::tma_load_4d(sHalo + sh * kStage + (h * Cfg::kHaloPx + 32 * k) * kRow, &tmx,
                                                 &full_h[sh], g * kPerGroup, x0 - 1 + Cfg::kQuad * k, y0 - 1 + h, n);
                     } else {
-                        tc::tma_load_4d(sHalo + sh * Cfg::kHaloStage, &tmx, &full_h[sh], g * kPerGroup, x0 - 1, y0 - 1,
-                                        n);
+                        tc::tma_load_4d(sHalo + sh * kStage, &tmx, &full_h[sh], g * kPerGroup, x0 - 1, y0 - 1, n);
                     }
                     ++qh;
-                    if (!resident) {
+                    if (!resident && !C8) {
                         for (int ky = 0; ky < 3; ++ky, ++qw) {
                             const int sw = int(qw % uint32_t(WS));
                             if (!tc::mbar_wait_sleep(&empty_w[sw], ((qw / uint32_t(WS)) & 1u) ^ 1u, P.err, 2)) {
@@ -378,7 +434,7 @@ k_conv3x3_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CU
         // offsets (the issue loop is the critical path of the kernel).
         if (lane == 0) {
             constexpr uint32_t idesc = FP8 ? tc::idesc_e4m3(kTileM, Cfg::kN) : tc::idesc_bf16(kTileM, Cfg::kN);
-            bool ok = !resident || tc::mbar_wait(wready, 0, P.err, 3);
+            bool ok = (!resident && !C8) || tc::mbar_wait(wready, 0, P.err, 3);
             const int nks_last = (min(kPerGroup, Cin - (G - 1) * kPerGroup) * kEsize + 31) / 32;
             const uint64_t dh0 = tc::desc_kmajor_sw64(tc::smem_u32(sHalo));
             const uint64_t dw0 = tc::desc_kmajor_sw64(tc::smem_u32(sW));
@@ -398,10 +454,39 @@ k_conv3x3_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CU
                         ok = false;
                         break;
                     }
-                    const uint64_t da = dh0 + uint64_t((sh * Cfg::kHaloStage) >> 4);
+                    const uint64_t da = dh0 + uint64_t((sh * kStage) >> 4);
                     const bool two = g < G - 1 || nks_last == 2;
                     const uint32_t acc0 = g != 0 ? 1u : 0u;
-                    if (resident) {
+                    if constexpr (C8) {
+                        // per output row: (ky, 0) + (ky, 1) for ky = 0..2 (second K core
+                        // matrix = the next pixel, the next weight tap), (0, 2) + (1, 2)
+                        // (the next halo row, three taps on), (2, 2) + the zero tap
+                        constexpr uint32_t kHR = kC8Px * 16, kT = C8Cfg<COUT>::kTap;
+                        const uint32_t h0 = tc::smem_u32(sHalo + sh * kStage) + (P.x_quads ? 3u * 16u : 0u);
+                        const uint32_t w0 = tc::smem_u32(sW);
+#pragma unroll
+                        for (int r = 0; r < R; ++r) {
+                            const uint32_t dr = d + uint32_t(r * Cfg::kAcc);
+                            const uint32_t hr = h0 + uint32_t(r) * kHR;
+                            uint64_t a[5], bw[5];
+#pragma unroll
+                            for (int ky = 0; ky < 3; ++ky) {
+                                a[ky] = tc::desc_kmajor_plain(hr + ky * kHR, 16, 128);
+                                bw[ky] = tc::desc_kmajor_plain(w0 + 3 * ky * kT, kT, 128);
+                            }
+                            a[3] = tc::desc_kmajor_plain(hr + 2 * 16, kHR, 128);
+                            bw[3] = tc::desc_kmajor_plain(w0 + 2 * kT, 3 * kT, 128);
+                            a[4] = tc::desc_kmajor_plain(hr + 2 * kHR + 2 * 16, 16, 128);
+                            bw[4] = tc::desc_kmajor_plain(w0 + 8 * kT, kT, 128);
+#pragma unroll
+                            for (int i = 0; i < 5; ++i) {
+                                if (FP8)
+                                    tc::mma_e4m3(dr, a[i], bw[i], idesc, i != 0 ? 1u : acc0);
+                                else
+                                    tc::mma_bf16(dr, a[i], bw[i], idesc, i != 0 ? 1u : acc0);
+                            }
+                        }
+                    } else if (resident) {
                         const uint64_t db = dw0 + uint64_t((g * Cfg::kGroup) >> 4);
 #pragma unroll
                         for (int r = 0; r < R; ++r) {
@@ -794,6 +879,43 @@ cudaError_t make_weight_map(CUtensorMap* m, const void* w, int cout, int cin, bo
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
+// C8: x [NB][H][W] pixels of 16 bytes (8 bf16 channels, or 16 e4m3 bytes),
+// halo box {16 bytes, kC8Px pixels, rows, 1 image}, no swizzle; quads (W a
+// multiple of 4): the same bytes as rows of four pixels, box {64 bytes,
+// kC8Px / 4 quads, rows, 1}
+cudaError_t make_halo_map_c8(CUtensorMap* m, const void* x, int NB, int H, int W, bool fp8, int rows, bool quads)
+{
+    auto enc = encode_fn();
+    if (!enc) return cudaErrorNotSupported;
+    const cuuint64_t px = quads ? 4 : 1;                          // pixels per copied row
+    const cuuint64_t ch = (fp8 ? 16 : 8) * px;
+    const cuuint64_t dims[4] = {ch, cuuint64_t(W) / px, cuuint64_t(H), cuuint64_t(NB)};
+    const cuuint64_t strides[3] = {16 * px, cuuint64_t(W) * 16, cuuint64_t(H) * W * 16};
+    const cuuint32_t box[4] = {cuuint32_t(ch), cuuint32_t(kC8Px / px), cuuint32_t(rows), 1};
+    const cuuint32_t el[4] = {1, 1, 1, 1};
+    CUresult r = enc(m, fp8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4,
+                     const_cast<void*>(x), dims, strides, box, el, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                     CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+// C8: w [cout][9][16 bytes] seen as (16 bytes, cout, tap); one box of all nine
+// taps lands tap by tap, each tap a COUT x 16-byte tile
+cudaError_t make_weight_map_c8(CUtensorMap* m, const void* w, int cout, bool fp8)
+{
+    auto enc = encode_fn();
+    if (!enc) return cudaErrorNotSupported;
+    const cuuint64_t ch = fp8 ? 16 : 8;
+    const cuuint64_t dims[3] = {ch, cuuint64_t(cout), 9};
+    const cuuint64_t strides[2] = {9 * 16, 16};
+    const cuuint32_t box[3] = {cuuint32_t(ch), cuuint32_t(cout), 9};
+    const cuuint32_t el[3] = {1, 1, 1};
+    CUresult r = enc(m, fp8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3,
+                     const_cast<void*>(w), dims, strides, box, el, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                     CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
 int num_sms()
 {
     static int n = 0;
@@ -845,7 +967,7 @@ cudaError_t make_out_map(CUtensorMap* m, void* y, int NB, int H, int W, int ldy,
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-template <int COUT, bool FP8, bool FOLD = false, bool WIDE = false>
+template <int COUT, bool FP8, bool FOLD = false, bool WIDE = false, bool C8 = false>
 cudaError_t launch_conv(const void* x, const void* w, ConvArgs a, cudaStream_t s)
 {
     constexpr int kPerGroup = FP8 ? 64 : 32;
@@ -854,15 +976,17 @@ cudaError_t launch_conv(const void* x, const void* w, ConvArgs a, cudaStream_t s
     // channel slice of a wider tensor, or four times for the upsampling.  A
     // dense output is already written in whole lines by the threads.
     const bool want_out = a.up2 || a.ldy != COUT || a.coff != 0;
-    Plan p = make_plan<COUT, FOLD, WIDE>(G, FP8, want_out);
+    Plan p = C8 ? make_plan_c8<COUT>(FP8, want_out) : make_plan<COUT, FOLD, WIDE>(G, FP8, want_out);
     if (p.hs < 2 || (!p.resident && p.ws < 2)) return cudaErrorInvalidValue;
     CUtensorMap mx, mw, my, my2;
     using C = ConvCfg<COUT, FOLD, WIDE>;
     a.tiles_x = (a.W + C::kTileOut - 1) / C::kTileOut;
-    cudaError_t e = C::kFold ? make_halo_map(&mx, x, a.NB, a.H, a.W, a.xstride, FP8, 32, 1)
-                             : make_halo_map(&mx, x, a.NB, a.H, a.W, a.xstride, FP8, C::kHaloPx, C::kHaloRows);
+    a.x_quads = C8 && a.W % 4 == 0;
+    cudaError_t e = C8         ? make_halo_map_c8(&mx, x, a.NB, a.H, a.W, FP8, C::kHaloRows, a.x_quads != 0)
+                    : C::kFold ? make_halo_map(&mx, x, a.NB, a.H, a.W, a.xstride, FP8, 32, 1)
+                               : make_halo_map(&mx, x, a.NB, a.H, a.W, a.xstride, FP8, C::kHaloPx, C::kHaloRows);
     if (e != cudaSuccess) return e;
-    e = make_weight_map(&mw, w, COUT, a.Cin, FP8);
+    e = C8 ? make_weight_map_c8(&mw, w, COUT, FP8) : make_weight_map(&mw, w, COUT, a.Cin, FP8);
     if (e != cudaSuccess) return e;
     my = mw;                                           // unused unless the output maps are made
     my2 = mw;
@@ -875,13 +999,13 @@ cudaError_t launch_conv(const void* x, const void* w, ConvArgs a, cudaStream_t s
                          cudaSuccess))
             p.out = 0;
     }
-    e = cudaFuncSetAttribute(k_conv3x3_tc<COUT, FP8, FOLD, WIDE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(k_conv3x3_tc<COUT, FP8, FOLD, WIDE, C8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              p.smem);
     if (e != cudaSuccess) return e;
     const long long tiles = (long long)a.tiles_x * a.NB * ((a.H + C::kRows - 1) / C::kRows);
     const int grid = int(std::min<long long>(tiles, num_sms()));
-    k_conv3x3_tc<COUT, FP8, FOLD, WIDE><<<grid, kThreads, p.smem, s>>>(mx, mw, my, my2, a, int(tiles), p.hs, p.ws, p.resident,
-                                                             p.out);
+    k_conv3x3_tc<COUT, FP8, FOLD, WIDE, C8><<<grid, kThreads, p.smem, s>>>(mx, mw, my, my2, a, int(tiles), p.hs, p.ws,
+                                                                      p.resident, p.out);
     return cudaGetLastError();
 }
 
@@ -897,15 +1021,20 @@ bool streamed(const ConvArgs& a, bool fp8)
 template <bool FP8>
 cudaError_t dispatch(const void* x, const void* w, int Cout, const ConvArgs& a, cudaStream_t s)
 {
+    // 16-byte pixels (the network's input features): two taps per MMA
+    const bool c8 = a.xstride * (FP8 ? 1 : 2) == 16;
     switch (Cout) {
     case 32:
+        if (c8) return launch_conv<32, FP8, false, false, true>(x, w, a, s);
         // the folded form pays where the MMAs outweigh the epilogue: two or
         // more channel groups per tile.  It is kept to dense outputs without
         // the fused head (the network's uses of it)
         if (a.Cin > (FP8 ? 64 : 32) && !a.up2 && a.ldy == 32 && a.coff == 0 && !a.head_w)
             return launch_conv<32, FP8, true>(x, w, a, s);
         return launch_conv<32, FP8>(x, w, a, s);
-    case 48: return launch_conv<48, FP8>(x, w, a, s);
+    case 48:
+        if (c8) return launch_conv<48, FP8, false, false, true>(x, w, a, s);
+        return launch_conv<48, FP8>(x, w, a, s);
     case 64: return launch_conv<64, FP8>(x, w, a, s);
     case 96:
         if (streamed<96>(a, FP8)) return launch_conv<96, FP8, false, true>(x, w, a, s);

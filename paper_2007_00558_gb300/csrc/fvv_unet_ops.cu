@@ -17,9 +17,11 @@ namespace {
 __device__ __forceinline__ float bf(const __nv_bfloat16 v) { return __bfloat162float(v); }
 
 // ---- input features ----------------------------------------------------------
-// 8 channels: RGB / 255, depth / z_far, hole, top-3 weights, stored in one
-// 64-byte row per pixel (bf16: channels 8..31 zero; e4m3: bytes 8..63 zero) so
-// that the convolution's halo copies move whole contiguous rows.
+// 8 channels: RGB / 255, depth / z_far, hole, top-3 weights, stored densely
+// in 16 bytes per pixel (bf16: the 8 channels; e4m3: 8 codes and 8 zero
+// bytes, the smallest row a tensor map takes).  The convolution's halo copy
+// reads these 16 bytes and fills the rest of its 64-byte rows with zeros
+// (channels past the tensor's extent), so no padding lives in memory.
 __device__ __forceinline__ void features(size_t p, const uint8_t* __restrict__ rgb, const float* __restrict__ depth,
                                          const uint8_t* __restrict__ hole, const float* __restrict__ top3,
                                          float inv_zfar, float f[8])
@@ -48,11 +50,10 @@ __global__ void k_pack_features(size_t npx, const uint8_t* __restrict__ rgb, con
         const __nv_bfloat162 h = __floats2bfloat162_rn(f[2 * i], f[2 * i + 1]);
         w[i] = *reinterpret_cast<const uint32_t*>(&h);
     }
-    // 32 channels per pixel; channels 8..31 stay zero from the allocation
-    reinterpret_cast<uint4*>(out)[4 * p] = make_uint4(w[0], w[1], w[2], w[3]);
+    reinterpret_cast<uint4*>(out)[p] = make_uint4(w[0], w[1], w[2], w[3]);
 }
 
-// e4m3 codes of feature / s0 in bytes 0..7, zero in 8..15 (16..63: zero already)
+// e4m3 codes of feature / s0 in bytes 0..7, zero in 8..15
 __global__ void k_pack_features_e4m3(size_t npx, const uint8_t* __restrict__ rgb, const float* __restrict__ depth,
                                      const uint8_t* __restrict__ hole, const float* __restrict__ top3,
                                      float inv_zfar, float inv_s0, uint8_t* __restrict__ out)
@@ -70,8 +71,7 @@ __global__ void k_pack_features_e4m3(size_t npx, const uint8_t* __restrict__ rgb
             make_float2(f[4 * i + 2] * inv_s0, f[4 * i + 3] * inv_s0), __NV_SATFINITE, __NV_E4M3);
         w[i] = uint32_t(lo) | (uint32_t(hi) << 16);
     }
-    // 64 bytes per pixel; bytes 16..63 stay zero from the allocation
-    reinterpret_cast<uint4*>(out)[4 * p] = make_uint4(w[0], w[1], 0u, 0u);
+    reinterpret_cast<uint4*>(out)[p] = make_uint4(w[0], w[1], 0u, 0u);
 }
 
 // ---- 8-channel vectors: every channel count here is a multiple of 8 ---------

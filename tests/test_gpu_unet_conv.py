@@ -31,7 +31,7 @@ def test_conv3x3_matches_oracle(cin, cout, h, w, relu):
 # stage ring wrap several times; resident and streamed weights
 @pytest.mark.parametrize("cin,cout,n,h,w", [(32, 32, 3, 64, 300), (64, 128, 2, 48, 256),
                                             (128, 128, 2, 40, 256), (192, 64, 2, 60, 130),
-                                            (48, 96, 2, 50, 640)])
+                                            (48, 96, 2, 50, 640), (8, 32, 3, 64, 300), (8, 48, 2, 50, 200)])
 def test_conv3x3_many_tiles(cin, cout, n, h, w):
     _check_conv(cin, cout, n, h, w, 1)
 
@@ -90,7 +90,7 @@ def _e4m3_ulp(v):
     return np.ldexp(1.0, np.clip(ex - 1, -6, 8) - 3)
 
 
-@pytest.mark.parametrize("cin,cout,h,w", [(16, 32, 3, 130), (32, 48, 2, 200), (48, 96, 2, 140),
+@pytest.mark.parametrize("cin,cout,h,w", [(16, 32, 3, 130), (16, 32, 2, 256), (16, 48, 4, 70), (32, 48, 2, 200), (48, 96, 2, 140),
                                           (64, 64, 3, 100), (96, 192, 2, 64), (144, 48, 2, 130),
                                           (288, 96, 2, 128), (192, 192, 1, 140), (64, 128, 40, 256)])
 @pytest.mark.parametrize("relu", [0, 1])

@@ -23,7 +23,8 @@ def _bf16(rng, shape):
 
 # (n, h, w, cin, xstride, cout)
 CASES = [
-    (2, 5, 40, 8, 32, 32),          # input features: 8 of 32 channels per pixel, 32-wide boxes
+    (2, 5, 40, 8, 8, 32),           # input features: 8 channels in 16 bytes per pixel
+    (2, 5, 40, 8, 32, 32),          # 8 of 32 channels per pixel, 32-wide boxes
     (2, 4, 130, 32, 32, 32),        # ragged 64-pixel boxes along a row
     (1, 3, 64, 32, 40, 64),         # pixel stride of 40 channels
     (2, 6, 20, 64, 64, 128),        # narrow image: 16 x 4 pixel boxes
