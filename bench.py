@@ -550,7 +550,7 @@ def codec_bench(F, ctx, wl, stream, reps=50):
 
 
 def serve_bench(F, ctx, wl, rgb_h, dep_h, slots, seconds, stream, refine=False, n_viewers=16, res=None,
-                n_sat=3000, persistent=False):
+                n_sat=3000, persistent=False, window_us=0):
     """n_viewers viewers, Poisson 30 Hz each, resolutions cycling through
     `res` (default 640x360 : 1280x720 : 1920x1080 = 2:1:1, viewer i takes
     res[i % len(res)]), frames re-uploaded at 30 fps on a second stream; then
@@ -585,7 +585,7 @@ def serve_bench(F, ctx, wl, rgb_h, dep_h, slots, seconds, stream, refine=False, 
     owner = {}
     F.fvv_serve_start(ctx, F.fvv_serve_default_cfg(lanes=3, max_batch=16, memory_budget=1 << 30,
                                                     refine=1 if refine else 0, persistent=1 if persistent else 0,
-                                                    max_width=max(r[0] for r in res)))
+                                                    max_width=max(r[0] for r in res), batch_window_us=window_us))
     stop = threading.Event()
     up_stream = torch.cuda.Stream()
     tick0 = [10 ** 6]
@@ -650,7 +650,8 @@ def serve_bench(F, ctx, wl, rgb_h, dep_h, slots, seconds, stream, refine=False, 
     return {
         "viewers": n_viewers, "rate_hz_per_viewer": rate,
         "resolutions": ":".join(mix) + "=" + ":".join(str(v) for v in mix.values()),
-        "refined": bool(refine), "persistent_kernel": bool(persistent), "frame_updates_hz": 30, "lanes": 3,
+        "refined": bool(refine), "persistent_kernel": bool(persistent), "batch_window_us": window_us,
+        "frame_updates_hz": 30, "lanes": 3,
         "max_batch": 16, "seconds": seconds,
         "offered_rps": len(arrivals) / seconds, "completed": nominal["completed"],
         "p50_ms": nominal["p50_ms"], "p99_ms": nominal["p99_ms"], "max_ms": nominal["max_ms"],
@@ -1272,6 +1273,9 @@ def run_fvv(args):
         # the same load with the batches in the persistent kernel
         serve["persistent"] = serve_bench(F, ctx, wl, rgb_h, dep_h, slots, args.serve_seconds, stream,
                                           persistent=True)
+        # the same load with a 4 ms coalescing window (batch size for latency)
+        serve["window_4ms"] = serve_bench(F, ctx, wl, rgb_h, dep_h, slots, args.serve_seconds, stream,
+                                          window_us=4000)
 
     codec = None
     if world == 1 and not args.main_only:

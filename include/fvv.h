@@ -365,6 +365,7 @@ typedef struct fvv_serve_cfg {
     int32_t persistent;         /* 1: batches run in one persistent kernel (see above), default 0 */
     int32_t max_width;          /* persistent: widest view, default 1920 */
     uint32_t idle_us;           /* persistent: the kernel returns after this long without work, default 20000 */
+    uint32_t batch_window_us;   /* coalescing window, default 0 (see below) */
 } fvv_serve_cfg;
 
 typedef struct fvv_serve_report {
@@ -376,6 +377,10 @@ typedef struct fvv_serve_report {
     int32_t in_flight;          /* submitted, not yet finished */
 } fvv_serve_report;
 
+/* batch_window_us > 0 trades latency for batch size: while fewer than
+ * max_batch requests are queued, a batch waits until its oldest request has
+ * been queued for batch_window_us (at most 1 s) before it leaves.  At light
+ * load (each request finds the GPU idle) the default 0 gives batches of one. */
 fvv_status fvv_serve_default_cfg(fvv_serve_cfg* cfg);
 
 /* Start the scheduler thread and allocate the lanes' scratch.  Errors:

@@ -374,6 +374,18 @@ void scheduler(ServeState* st)
                    (!st->queue.empty() && free_lane() != nullptr);
         });
         if (st->stopping && st->queue.empty() && idle()) break;
+        // coalescing window: a short queue waits for its oldest request to
+        // age batch_window_us (stopping sends it at once)
+        if (st->cfg.batch_window_us && !st->stopping && !st->queue.empty() &&
+            int(st->queue.size()) < st->cfg.max_batch) {
+            const double due = st->recs[st->queue.front().ticket].t_submit + 1e-6 * st->cfg.batch_window_us;
+            const double wait = due - now_s();
+            if (wait > 0.0) {
+                st->cv.wait_for(lk, std::chrono::duration<double>(wait),
+                                [&] { return st->stopping || int(st->queue.size()) >= st->cfg.max_batch; });
+                continue;
+            }
+        }
         if (st->reset_flag) {
             // a network wait ran out: clear the flag before the next batch
             st->reset_flag = false;
@@ -589,6 +601,7 @@ fvv_status fvv_serve_default_cfg(fvv_serve_cfg* cfg)
     cfg->persistent = 0;
     cfg->max_width = 1920;
     cfg->idle_us = 20000;
+    cfg->batch_window_us = 0;
     return FVV_OK;
 }
 
@@ -602,6 +615,7 @@ fvv_status fvv_serve_start(fvv_ctx* c, const fvv_serve_cfg* cfg_in)
     if (cfg.max_batch < 1 || cfg.max_batch > 4096 || cfg.max_pending < 1)
         return fail(FVV_ERR_INVALID_ARG, "max_batch must be in [1, 4096], max_pending >= 1");
     if (cfg.refine != 0 && cfg.refine != 1) return fail(FVV_ERR_INVALID_ARG, "refine must be 0 or 1");
+    if (cfg.batch_window_us > 1000000) return fail(FVV_ERR_INVALID_ARG, "batch_window_us must be at most 1 s");
     if (cfg.persistent != 0 && cfg.persistent != 1) return fail(FVV_ERR_INVALID_ARG, "persistent must be 0 or 1");
     if (cfg.persistent) {
         if (cfg.refine) return fail(FVV_ERR_INVALID_ARG, "persistent serving renders plain views (refine = 0)");

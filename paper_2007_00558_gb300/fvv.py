@@ -73,7 +73,7 @@ class fvv_aux(C.Structure):
 class fvv_serve_cfg(C.Structure):
     _fields_ = [("lanes", C.c_int32), ("max_batch", C.c_int32), ("max_pending", C.c_int32),
                 ("memory_budget", C.c_uint64), ("refine", C.c_int32), ("persistent", C.c_int32),
-                ("max_width", C.c_int32), ("idle_us", C.c_uint32)]
+                ("max_width", C.c_int32), ("idle_us", C.c_uint32), ("batch_window_us", C.c_uint32)]
 
 
 class fvv_serve_report(C.Structure):

@@ -329,3 +329,52 @@ def test_persistent_serve_equals_alone_and_relaunches_after_idle(rig_small):
             assert torch.equal(o, ref)
     finally:
         F.fvv_destroy(ctx)
+
+
+@pytest.mark.parametrize("persistent", [0, 1])
+def test_batch_window_coalesces_sparse_requests(rig_small, persistent):
+    """Requests 1 ms apart find the GPU idle, so without a window every batch
+    holds one view; with a 40 ms window they leave together.  The results
+    still equal the views rendered alone, and no request waits much beyond
+    the window."""
+    import torch
+    F = lib()
+    wl = rig_small
+    views = [_view(wl["views"][17 * i], 320, 180, 125.0) for i in range(12)]
+    ctx = _ctx_with_frames(F, wl)
+    try:
+        stats = {}
+        for window in (0, 40_000):
+            F.fvv_serve_start(ctx, F.fvv_serve_default_cfg(lanes=2, max_batch=16, batch_window_us=window,
+                                                            persistent=persistent))
+            outs = [torch.zeros((v.height, v.width * 3), dtype=torch.uint8, device="cuda") for v in views]
+            torch.cuda.synchronize()
+            tickets = []
+            for i, (v, o) in enumerate(zip(views, outs)):
+                tickets.append(F.fvv_serve_submit(ctx, i, F.camera(v), o, v.width * 3))
+                time.sleep(0.001)
+            for t in tickets:
+                F.fvv_serve_poll(ctx, t, 5_000_000)
+            stats[window] = F.fvv_serve_stats(ctx)
+            F.fvv_serve_stop(ctx)
+            for v, o in zip(views, outs):
+                ref = torch.zeros_like(o)
+                F.fvv_synthesize(ctx, v, ref, v.width * 3)
+                torch.cuda.synchronize()
+                assert torch.equal(o, ref)
+        assert stats[0]["completed"] == 12 and stats[40_000]["completed"] == 12
+        assert stats[40_000]["mean_batch"] >= 4.0 > stats[0]["mean_batch"]
+        assert stats[40_000]["max_ms"] < 40.0 + 200.0
+    finally:
+        F.fvv_destroy(ctx)
+
+
+def test_batch_window_is_bounded(rig_small):
+    F = lib()
+    ctx = _ctx_with_frames(F, rig_small)
+    try:
+        with pytest.raises(F.FvvError) as e:
+            F.fvv_serve_start(ctx, F.fvv_serve_default_cfg(batch_window_us=2_000_000))
+        assert e.value.code == F.FVV_ERR_INVALID_ARG
+    finally:
+        F.fvv_destroy(ctx)
