@@ -452,10 +452,12 @@ def algorithmic_bytes(K, Ns, Nd, rho, n_ref):
     """Per-view algorithmic bytes of each kernel (RGB counted as 3 bytes):
     clear: 8 Nd; splat: depth 2 K Ns + one 8-byte atomicMin per valid source
     pixel 8 rho K Ns; resolve: keys 8 Nd + backward depth and colour gathers
-    (2 + 3)(n_ref - 1) Nd + winner colour 3 Nd + output 3 Nd."""
+    (2 + 3)(n_ref - 1) Nd + winner colour 3 Nd + output 3 Nd + the next
+    batch's z-buffer emptied 8 Nd (batches of an unchanged layout need no
+    clear launch, so the clear's bytes move into the resolve)."""
     return {"clear_keys": 8.0 * Nd,
             "warp_splat": 2.0 * K * Ns + 8.0 * rho * K * Ns,
-            "resolve": 8.0 * Nd + 5.0 * (n_ref - 1) * Nd + 3.0 * Nd + 3.0 * Nd}
+            "resolve": 8.0 * Nd + 5.0 * (n_ref - 1) * Nd + 3.0 * Nd + 3.0 * Nd + 8.0 * Nd}
 
 
 # ---------------------------------------------------------------------------
@@ -1218,8 +1220,9 @@ def run_fvv(args):
                     "traffic": profiled_traffic(dom, Bsz),
                     "alg_bytes_per_launch": alg[dom] * Bsz, "avg_launch_us": avg_s * 1e6,
                     "kernel_share": {k: v[2] / sum(x[2] for x in timed.values()) for k, v in timed.items()},
-                    "step_alg_bytes_per_view": sum(alg.values()),
-                    "step_frac": sum(alg.values()) * n_views / world / (el_ms / 1e3) / 1e9 / peak}
+                    "step_alg_bytes_per_view": alg["warp_splat"] + alg["resolve"],
+                    "step_frac": (alg["warp_splat"] + alg["resolve"]) * n_views / world / (el_ms / 1e3) / 1e9
+                                 / peak}
 
     # end to end through the C ABI with host buffers
     e2e = None

@@ -300,12 +300,18 @@ fvv_status ensure_keys(fvv_ctx* c, BatchScratch& S, size_t n)
     if (S.keys) {
         FVV_CUDA(cudaDeviceSynchronize());
         dev_free(c, S.keys, S.keys_cap * 8);
+        dev_free(c, S.keys2, S.keys_cap * 8);
         S.keys = nullptr;
+        S.keys2 = nullptr;
         S.keys_cap = 0;
     }
+    S.clean[0].clear();
+    S.clean[1].clear();
+    S.cur = 0;
     const size_t cap = align_up(n, 1 << 16);
     FVV_TRY(dev_alloc(c, reinterpret_cast<void**>(&S.keys), cap * 8));
     S.keys_cap = cap;
+    FVV_TRY(dev_alloc(c, reinterpret_cast<void**>(&S.keys2), cap * 8));
     return FVV_OK;
 }
 
@@ -577,7 +583,11 @@ void fvv::scratch_free(fvv_ctx* c, BatchScratch& S)
     }
     S.pring.clear();
     dev_free(c, S.keys, S.keys_cap * 8);
+    dev_free(c, S.keys2, S.keys_cap * 8);
     dev_free(c, S.out_stage, S.out_stage_cap);
+    S.keys2 = nullptr;
+    S.clean[0].clear();
+    S.clean[1].clear();
     S.keys = nullptr;
     S.out_stage = nullptr;
     S.keys_cap = S.out_stage_cap = 0;
@@ -680,6 +690,12 @@ fvv_status fvv::run_batch(fvv_ctx* c, BatchScratch& S, int n, const fvv_view* vi
     CamGeom* gh = reinterpret_cast<CamGeom*>(P.host + geom_off);
     const CamGeom* gd = reinterpret_cast<const CamGeom*>(P.dev + geom_off);
 
+    // the z-buffer this batch splats into, and the one its resolve empties
+    const bool ahead = S.keys2 != nullptr && !c->opt.layered && !post;
+    unsigned long long* const kx = ahead && S.cur ? S.keys2 : S.keys;
+    unsigned long long* const ky = ahead ? (S.cur ? S.keys : S.keys2) : nullptr;
+    std::vector<size_t> layout;
+
     struct HostCopy { void* dst; size_t dpitch; const void* src; size_t spitch, width, height; };
     std::vector<HostCopy> d2h;
     std::vector<std::pair<void*, const void*>> raw_copies;   // keys_raw
@@ -707,7 +723,9 @@ fvv_status fvv::run_batch(fvv_ctx* c, BatchScratch& S, int n, const fvv_view* vi
         D.z_min = c->opt.z_min;
         D.d_lo = c->opt.d_lo;
         D.d_hi = c->opt.d_hi;
-        D.keys = S.keys + koff;
+        D.keys = kx + koff;
+        D.keys_next = ky ? ky + koff : nullptr;
+        layout.push_back(align_up(np, 16));
         koff += align_up(np, 16);
         D.keys_bg = nullptr;
         D.keys_bgf = nullptr;
@@ -796,7 +814,11 @@ fvv_status fvv::run_batch(fvv_ctx* c, BatchScratch& S, int n, const fvv_view* vi
         P.pending = true;
         return FVV_OK;
     }
-    FVV_TRY(run_kernel(c, kClear, s, [&] { return fvv::launch_clear_keys(S.keys, koff, s); }));
+    // a buffer whose view regions an earlier resolve emptied for this layout needs no clear
+    const bool clean = ahead && S.clean[S.cur] == layout;
+    S.clean[0].clear();
+    S.clean[1].clear();
+    if (!clean) FVV_TRY(run_kernel(c, kClear, s, [&] { return fvv::launch_clear_keys(kx, koff, s); }));
     FVV_TRY(run_kernel(c, kSplat, s, [&] {
         return fvv::launch_warp_splat(vdev, n, max_chunks, c->frames_dev, s, c->opt.layered != 0);
     }));
@@ -809,6 +831,10 @@ fvv_status fvv::run_batch(fvv_ctx* c, BatchScratch& S, int n, const fvv_view* vi
         return fvv::launch_resolve(vdev, n, max_h, max_w, c->n_cams, want_top3, c->frames_dev, s,
                                    c->opt.layered != 0, c->opt.pixel_weights != 0);
     }));
+    if (ahead) {
+        S.clean[1 - S.cur] = layout;
+        S.cur ^= 1;
+    }
     for (const HostCopy& h : d2h)
         FVV_CUDA(cudaMemcpy2DAsync(h.dst, h.dpitch, h.src, h.spitch, h.width, h.height,
                                    cudaMemcpyDeviceToHost, s));

@@ -56,6 +56,8 @@ struct alignas(16) ViewDesc {
     unsigned long long* keys;        // scratch z-buffer [Hv * Wv] (the FG layer when layered)
     unsigned long long* keys_bg;     // layered: the BG layer's z-buffer [Hv * Wv], else NULL
     unsigned long long* keys_bgf;    // layered: the BG layer after the crack filter (keys_bg without it)
+    unsigned long long* keys_next;   // nullable [Hv * Wv]: set to the empty key by the resolve (the
+                                     // next batch's z-buffer, so that it needs no clear; single layer)
     uint8_t* out_rgb;                // [Hv] rows of 3 * Wv bytes
     int64_t out_pitch;               // bytes
     float* out_depth;                // nullable [Hv * Wv]

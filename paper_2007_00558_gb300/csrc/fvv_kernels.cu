@@ -489,6 +489,16 @@ __device__ __forceinline__ void resolve_cta(const ViewDesc* __restrict__ views, 
     if (y0 >= Hv)
         return;                                    // uniform over the CTA
     const int y1 = min(Hv, y0 + band);
+    if (!kLayered && V->keys_next) {
+        // the next batch's z-buffer rows of this band, emptied while the key
+        // rows below are in flight (kept in L2 for that batch's splat)
+        const uint64_t pol = policy_evict_last();
+        unsigned long long* kn = V->keys_next + size_t(y0) * Wv;
+        const int m = (y1 - y0) * Wv;
+        for (int i = threadIdx.x; i < m; i += kResolveThreads)
+            asm volatile("st.global.L2::cache_hint.u64 [%0], %1, %2;" ::"l"(kn + i), "l"(kKeyEmpty), "l"(pol)
+                         : "memory");
+    }
     const int nc = V->n_cams, na = V->n_active;
     const SmemLayout L = resolve_layout(Wv, nc, kLayered);
     const size_t RP = ring_pitch(Wv);

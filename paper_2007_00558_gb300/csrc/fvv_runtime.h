@@ -81,6 +81,14 @@ struct SlotState {
 struct BatchScratch {
     unsigned long long* keys = nullptr;
     size_t keys_cap = 0;                  // elements
+    // A growable scratch holds two z-buffers: a single-layer batch splats
+    // into keys_buf(cur) while its resolve empties the same view regions of
+    // the other one, so a next batch of the same layout starts without a
+    // clear.  clean[b]: the per-view key counts whose regions buffer b is
+    // known to hold empty (none: clear before use).
+    unsigned long long* keys2 = nullptr;
+    int cur = 0;
+    std::vector<size_t> clean[2];
     uint8_t* out_stage = nullptr;
     size_t out_stage_cap = 0;             // bytes
     std::vector<ParamBlock> pring;
