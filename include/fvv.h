@@ -96,7 +96,10 @@ typedef struct fvv_options {
                                    FVV_DEPTH_BG is never a depth) */
     int32_t frame_slots;        /* device-resident frame ticks kept (ring), default 2 */
     int32_t max_batch;          /* most views per batched call, default 64 */
-    uint64_t memory_budget;     /* device bytes the context may hold, 0 = unlimited */
+    uint64_t memory_budget;     /* device bytes the context may hold, 0 = unlimited.  Within it
+                                   the batch z-buffer is held twice (a batch's resolve empties
+                                   the other copy, so the next batch of the same view sizes
+                                   needs no clear); without room for that, once. */
     int32_t layered;            /* 1 = layered FG/BG synthesis (see fvv_set_bg_depth), default 0 */
     /* joint bilateral depth pre-filter on upload (see fvv_depth_jbf) */
     int32_t jbf_radius;         /* window radius 0..7, 0 = off (default) */

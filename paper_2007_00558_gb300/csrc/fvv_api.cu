@@ -311,7 +311,10 @@ fvv_status ensure_keys(fvv_ctx* c, BatchScratch& S, size_t n)
     const size_t cap = align_up(n, 1 << 16);
     FVV_TRY(dev_alloc(c, reinterpret_cast<void**>(&S.keys), cap * 8));
     S.keys_cap = cap;
-    FVV_TRY(dev_alloc(c, reinterpret_cast<void**>(&S.keys2), cap * 8));
+    // the second z-buffer only where the memory budget leaves room for it
+    // (without it every batch clears its z-buffer first)
+    if (!c->opt.memory_budget || c->held + cap * 8 <= c->opt.memory_budget)
+        FVV_TRY(dev_alloc(c, reinterpret_cast<void**>(&S.keys2), cap * 8));
     return FVV_OK;
 }
 
