@@ -10,9 +10,10 @@
 // when a lane and its memory are free, and batches on different lanes overlap
 // on the GPU.  Requests that arrive while batches run join the next batch as
 // soon as a lane frees up (continuous batching).  Every batch renders from
-// the newest complete frame tick at the moment it is formed.  A host callback
-// on the lane's stream stamps each request's completion; latency is
-// submission to completion of its output write.
+// the newest complete frame tick at the moment it is formed.  An event
+// recorded after each batch's last work is polled by a completion thread,
+// which stamps each request's completion; latency is submission to
+// completion of its output write.
 //
 // With refinement on, a lane renders its batch (all requests of one size)
 // into its own device buffers of network inputs (colour, depth, hole mask,
@@ -77,6 +78,8 @@ struct ServeLane {
     uint8_t *rgb = nullptr, *hole = nullptr, *refined = nullptr;
     cudaEvent_t plain_done = nullptr;
     int* flag_host = nullptr;             // pinned copy of the network's error flag
+    cudaEvent_t done_ev = nullptr;        // recorded after a batch's last work (stream lanes)
+    bool ev_pending = false;              // done_ev recorded, its requests not yet completed
 };
 
 struct ServeState {
@@ -111,6 +114,9 @@ struct ServeState {
     ServeLane* pslot[kPersistRing] = {};   // the lane of posted batch b at b % kPersistRing
     std::thread poller;
     bool poller_stop = false;
+    // stream lanes: the thread that polls the lanes' done events
+    std::thread completer;
+    bool completer_stop = false;
 };
 
 namespace {
@@ -241,15 +247,24 @@ void persist_poller(ServeState* st)
     }
 }
 
-void CUDART_CB lane_done(void* p)
+// Complete lane L's batch at time t (its work has finished, or failed with
+// `cuda_err`); caller holds st->mu.
+void lane_finish(ServeState* st, ServeLane* L, double t, cudaError_t cuda_err)
 {
-    // runs on a CUDA callback thread: no CUDA calls here
-    ServeLane* L = static_cast<ServeLane*>(p);
-    ServeState* st = L->owner;
-    const double t = now_s();
     {
-        std::lock_guard<std::mutex> lk(st->mu);
-        const bool timed_out = L->flag_host && *L->flag_host != 0;
+        const bool timed_out = cuda_err == cudaSuccess && L->flag_host && *L->flag_host != 0;
+        if (cuda_err != cudaSuccess) {
+            st->error = std::string("a serving batch failed: ") + cudaGetErrorString(cuda_err);
+            for (uint64_t tk : L->tickets) {
+                auto it = st->recs.find(tk);
+                if (it == st->recs.end()) continue;
+                it->second.state = ReqState::Failed;
+                ++st->failed;
+            }
+            L->tickets.clear();
+            L->busy = false;
+            return;
+        }
         if (timed_out) {
             st->reset_flag = true;
             st->error = "a bounded wait of the refinement network ran out";
@@ -271,7 +286,40 @@ void CUDART_CB lane_done(void* p)
         L->tickets.clear();
         L->busy = false;
     }
-    st->cv.notify_all();
+}
+
+// Stream lanes: completes a lane's requests as soon as its done event is
+// reached.  It polls (yielding) while any batch is in flight and sleeps on
+// the condition variable otherwise, which answers faster than a host
+// callback enqueued on the stream.
+void lane_completer(ServeState* st)
+{
+    cudaSetDevice(st->ctx->device);
+    std::unique_lock<std::mutex> lk(st->mu);
+    for (;;) {
+        bool any = false;
+        for (auto& Lp : st->lanes) {
+            ServeLane* L = Lp.get();
+            if (!L->ev_pending) continue;
+            any = true;
+            lk.unlock();
+            const cudaError_t q = cudaEventQuery(L->done_ev);
+            lk.lock();
+            if (q == cudaErrorNotReady) continue;
+            if (q != cudaSuccess) cudaGetLastError();
+            L->ev_pending = false;
+            lane_finish(st, L, now_s(), q);
+            st->cv.notify_all();
+        }
+        if (!any) {
+            if (st->completer_stop) break;
+            st->cv.wait_for(lk, std::chrono::milliseconds(2));
+            continue;
+        }
+        lk.unlock();
+        std::this_thread::yield();
+        lk.lock();
+    }
 }
 
 // One refined batch of same-size views on lane L: plain steps a-e into the
@@ -463,11 +511,11 @@ void scheduler(ServeState* st)
                                    pitches.data(), nullptr, L->stream, false);
                 }
                 if (rc == FVV_OK) {
-                    cudaError_t e = cudaLaunchHostFunc(done_on, lane_done, L);
+                    cudaError_t e = cudaEventRecord(L->done_ev, done_on);
                     if (e != cudaSuccess) {
                         cudaGetLastError();
                         rc = FVV_ERR_CUDA;
-                        err = std::string("cudaLaunchHostFunc: ") + cudaGetErrorString(e);
+                        err = std::string("cudaEventRecord: ") + cudaGetErrorString(e);
                     }
                 } else {
                     err = fvv_last_error();
@@ -480,6 +528,10 @@ void scheduler(ServeState* st)
                 }
             }
             lk.lock();
+            if (rc == FVV_OK && !st->cfg.persistent) {
+                L->ev_pending = true;              // the completer takes it from here
+                st->cv.notify_all();
+            }
             if (rc != FVV_OK) {
                 for (uint64_t tk : L->tickets) {
                     st->recs[tk].state = ReqState::Failed;
@@ -505,6 +557,8 @@ void lane_free(fvv_ctx* c, ServeLane& L)
     L.flag_host = nullptr;
     if (L.plain_done) cudaEventDestroy(L.plain_done);
     L.plain_done = nullptr;
+    if (L.done_ev) cudaEventDestroy(L.done_ev);
+    L.done_ev = nullptr;
     if (L.stream) cudaStreamDestroy(L.stream);
     L.stream = nullptr;
 }
@@ -553,6 +607,12 @@ void serve_shutdown(fvv_ctx* c)
     }
     st->cv.notify_all();
     if (st->thread.joinable()) st->thread.join();
+    {
+        std::lock_guard<std::mutex> lk(st->mu);
+        st->completer_stop = true;           // the scheduler left only when every lane was idle
+    }
+    st->cv.notify_all();
+    if (st->completer.joinable()) st->completer.join();
     if (st->pq) {
         // every request finished; the kernel returns at its next wait for work
         st->pq->stop = 1;
@@ -680,6 +740,10 @@ fvv_status fvv_serve_start(fvv_ctx* c, const fvv_serve_cfg* cfg_in)
             e = cudaEventCreateWithFlags(&L->plain_done, cudaEventDisableTiming);
             if (e != cudaSuccess) rc = FVV_ERR_CUDA;
         }
+        if (rc == FVV_OK) {
+            e = cudaEventCreateWithFlags(&L->done_ev, cudaEventDisableTiming);
+            if (e != cudaSuccess) rc = FVV_ERR_CUDA;
+        }
         L->S.reader = 1 + i;
         st->lanes.push_back(std::move(L));
         if (rc != FVV_OK)
@@ -720,6 +784,7 @@ fvv_status fvv_serve_start(fvv_ctx* c, const fvv_serve_cfg* cfg_in)
     c->serve = raw;
     raw->thread = std::thread(fvv::scheduler, raw);
     if (raw->pq) raw->poller = std::thread(fvv::persist_poller, raw);
+    else raw->completer = std::thread(fvv::lane_completer, raw);
     return FVV_OK;
 }
 
