@@ -197,6 +197,10 @@ void persist_poller(ServeState* st)
     fvv_ctx* c = st->ctx;
     cudaSetDevice(c->device);
     uint32_t seen = st->pq->done;
+    // whether the kernel still runs is asked only after 100 us without
+    // progress, and never waits for the context lock (an upload may hold
+    // it): the completion count alone answers the common case
+    double t_progress = now_s();
     for (;;) {
         const uint32_t d = st->pq->done;
         if (d != seen) {
@@ -207,6 +211,7 @@ void persist_poller(ServeState* st)
             }
             st->cv.notify_all();
             seen = d;
+            t_progress = t;
             continue;
         }
         uint32_t posted;
@@ -215,8 +220,14 @@ void persist_poller(ServeState* st)
             if (st->poller_stop) break;
             posted = st->pposted;
         }
-        if (posted != d) {
-            std::lock_guard<std::recursive_mutex> g(c->mu);
+        if (posted == d) t_progress = now_s();
+        if (posted != d && now_s() - t_progress > 1e-4) {
+            std::unique_lock<std::recursive_mutex> g(c->mu, std::try_to_lock);
+            if (!g.owns_lock()) {
+                std::this_thread::yield();
+                continue;
+            }
+            t_progress = now_s();
             if (!persist_running(st) && st->pq->done == d) {
                 if (st->pq->err != 0) {
                     // a wait of the kernel ran out: its pending batches fail
