@@ -6,18 +6,19 @@ radius 1.5 m, 1 % depth noise and 5 % dropout discs, one 1280x720 virtual view
 per frame along the swing trajectory phi(t) = 22.5 deg sin(2 pi t / 300).
 Synthetic, seeded inputs (the paper's captured sequences are not available).
 
-A step is one batch of ``--batch`` views synthesised by one
-``fvv_synthesize_batch`` call (steps a-e of the hot path: three kernel
-launches).  Each view of a step reads its own frame tick from a ring of
-``--slots`` device-resident ticks, so consecutive reads of a tick are
-separated by more frame data than the 129 MB L2 holds.
+A step is one batch of ``--batch`` views (default 32) synthesised by one
+``fvv_synthesize_batch`` call (steps a-e of the hot path: a splat and a
+resolve launch; the z-buffer is emptied by the previous step's resolve).
+Each view of a step reads its own frame tick from a ring of
+``max(--slots, --batch)`` device-resident ticks, so consecutive reads of a
+tick are separated by more frame data than the 129 MB L2 holds.
 
 ``value``: views/s over all ranks with inputs resident in HBM.
-``e2e``: the same metric through the C ABI with host buffers: every view
-uploads its tick's frames from pinned host memory (one stream) and every
-step's RGB8 results are read back to pinned host memory (on the synthesis
-stream), all inside the timed region; uploads of the next step overlap the
-synthesis of the current one.
+``e2e``: the same metric through the C ABI with host buffers, in steps of
+``--e2e-batch`` views (default 8): every view uploads its tick's frames from
+pinned host memory and every step's RGB8 results are read back to pinned
+host memory, all inside the timed region; uploads of the next step overlap
+the synthesis of the current one.
 ``--impl reference``: the CPU oracle on the host cores, same workload.
 
 Under torchrun each rank renders its own share of views (replicas: the path
@@ -52,7 +53,9 @@ def parse_args():
     p.add_argument("--steps", type=int, default=200)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", choices=["fvv", "reference"], default="fvv")
-    p.add_argument("--batch", type=int, default=8, help="views per step (one batched call)")
+    p.add_argument("--batch", type=int, default=32, help="views per step (one batched call)")
+    p.add_argument("--e2e-batch", type=int, default=8,
+                   help="views per step of the end-to-end legs (host uploads of every view's tick)")
     p.add_argument("--slots", type=int, default=16, help="device-resident frame ticks")
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU-baseline sample length")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -1234,22 +1237,26 @@ def run_fvv(args):
         # frame ring's per-slot events order each synthesis after the uploads
         # of its ticks and each upload after the syntheses still reading its
         # slot, so step i+1's copies overlap step i's kernels.
-        out_h = [torch.empty((H, W, 3), dtype=torch.uint8).pin_memory() for _ in range(Bsz)]
-        out_d = [torch.empty((H, W * 3), dtype=torch.uint8, device="cuda") for _ in range(Bsz)]
+        # The end-to-end leg takes its own, smaller batch: a step's synthesis
+        # waits for all of its ticks, so with fewer views per step the next
+        # step's uploads overlap it sooner (the host link is the bound)
+        Be = min(args.e2e_batch, slots // 2) if slots >= 2 else 1
+        out_h = [torch.empty((H, W, 3), dtype=torch.uint8).pin_memory() for _ in range(Be)]
+        out_d = [torch.empty((H, W * 3), dtype=torch.uint8, device="cuda") for _ in range(Be)]
         ups, syn = [torch.cuda.Stream(), torch.cuda.Stream()], torch.cuda.Stream()
         tick = [slots]
 
         def e2e_step(i):
             vs, ticks = [], []
-            for j in range(Bsz):
+            for j in range(Be):
                 F.fvv_upload_frames(ctx, rgb_h, H * W * 3, W * 3, dep_h, H * W * 2, W * 2, tick[0],
                                     ups[tick[0] % 2])
                 ticks.append(tick[0])
                 tick[0] += 1
-                vs.append(views[(off + i * Bsz + j) % 300])
-            F.fvv_synthesize_batch(ctx, vs, ticks, out_d, pitches, None, syn)
+                vs.append(views[(off + i * Be + j) % 300])
+            F.fvv_synthesize_batch(ctx, vs, ticks, out_d, pitches[:Be], None, syn)
             with torch.cuda.stream(syn):
-                for j in range(Bsz):
+                for j in range(Be):
                     out_h[j].view(-1).copy_(out_d[j].view(-1), non_blocking=True)
 
         for i in range(args.warmup):
@@ -1261,14 +1268,17 @@ def run_fvv(args):
             e2e_step(args.warmup + i)
         torch.cuda.synchronize()
         el = max_over_ranks(time.perf_counter() - t0, "cuda")
-        e2e = {"value": aggregate_views_per_s(args.steps, Bsz, world, el), "unit": UNIT,
-               "h2d_bytes_per_step": int(Bsz * (rgb_h.numel() + dep_h.numel() * 2)),
-               "d2h_bytes_per_step": int(Bsz * H * W * 3)}
+        e2e = {"value": aggregate_views_per_s(args.steps, Be, world, el), "unit": UNIT,
+               "h2d_bytes_per_step": int(Be * (rgb_h.numel() + dep_h.numel() * 2)),
+               "d2h_bytes_per_step": int(Be * H * W * 3), "views_per_step": Be}
 
     e2e_adaptive = e2e_yuv = None
     if not args.no_e2e and world == 1 and not args.main_only:
-        e2e_adaptive = adaptive_e2e_bench(F, wl, rgb_h, dep_h, slots, Bsz, args.steps, args.warmup)
-        e2e_yuv = yuv_e2e_bench(F, wl, rgb_h, dep_h, slots, Bsz, args.steps, args.warmup)
+        # their own contexts: a ring of twice the end-to-end batch (at least --slots)
+        Be = max(1, args.e2e_batch)
+        es = max(args.slots, 2 * Be)
+        e2e_adaptive = adaptive_e2e_bench(F, wl, rgb_h, dep_h, es, Be, args.steps, args.warmup)
+        e2e_yuv = yuv_e2e_bench(F, wl, rgb_h, dep_h, es, Be, args.steps, args.warmup)
 
     serve = None
     if not args.no_serve and world == 1 and not args.main_only:
