@@ -1,5 +1,5 @@
 """The headline measurement's own launch configuration, checked against the
-oracle: nine 1280x720 cameras, a 16-tick frame ring, batches of eight
+oracle: nine 1280x720 cameras, a 32-tick frame ring, batches of 32
 1280x720 views each naming its own tick (two-row bands of the resolve), two
 steps in a row on one context (the second runs on the z-buffer the first
 resolve emptied, without a clear).  The ticks carry different colours, so a
@@ -24,18 +24,19 @@ def test_bench_batches_match_the_oracle(oracle_mod):
     wl = S.workload("plain_9cam_1280x720")
     cams = wl["cams"]
     K, H, W = len(cams), cams[0].height, cams[0].width
-    ctx = F.fvv_create(F.rig(cams, wl["look_at"]), F.fvv_default_options(frame_slots=16))
+    ctx = F.fvv_create(F.rig(cams, wl["look_at"]), F.fvv_default_options(frame_slots=32, max_batch=32))
     try:
         dep = torch.from_numpy(np.ascontiguousarray(np.stack(wl["depth"])).view(np.int16)).cuda()
         variants = [torch.from_numpy(np.ascontiguousarray(_tick_rgb(np.stack(wl["rgb"]), t))).cuda()
                     for t in range(4)]
-        for t in range(16):
+        for t in range(32):
             F.fvv_upload_frames(ctx, variants[t % 4], H * W * 3, W * 3, dep, H * W * 2, W * 2, t)
         torch.cuda.synchronize()
-        steps = [([3, 9, 14, 0, 7, 12, 5, 2], [11, 47, 93, 140, 185, 222, 260, 299]),
-                 ([6, 1, 15, 8, 13, 4, 10, 3], [5, 66, 121, 150, 203, 248, 271, 290])]
+        rng = np.random.default_rng(11)
+        steps = [(list(rng.permutation(32)), list(rng.choice(300, 32, replace=False))) for _ in range(2)]
         for s, (ticks, vi) in enumerate(steps):
-            views = [wl["views"][i] for i in vi]
+            views = [wl["views"][int(i)] for i in vi]
+            ticks = [int(t) for t in ticks]
             outs = [torch.zeros((H, W * 3), dtype=torch.uint8, device="cuda") for _ in views]
             got = [{"depth": torch.zeros((H, W), dtype=torch.float32, device="cuda"),
                     "hole": torch.zeros((H, W), dtype=torch.uint8, device="cuda"),
