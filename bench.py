@@ -463,6 +463,13 @@ def algorithmic_bytes(K, Ns, Nd, rho, n_ref):
             "resolve": 8.0 * Nd + 5.0 * (n_ref - 1) * Nd + 3.0 * Nd + 3.0 * Nd + 8.0 * Nd}
 
 
+def compulsory_bytes(K, Ns, Nd):
+    """Per-view bytes no implementation can avoid: every camera's depth and
+    colour read once (2 + 3 bytes per source pixel) and the RGB8 view written
+    once; the z-buffer, its atomics and the repeated gathers left out."""
+    return 5.0 * K * Ns + 3.0 * Nd
+
+
 # ---------------------------------------------------------------------------
 # serving loop: many viewers, Poisson arrivals, mixed resolutions
 # ---------------------------------------------------------------------------
@@ -1225,7 +1232,10 @@ def run_fvv(args):
                     "kernel_share": {k: v[2] / sum(x[2] for x in timed.values()) for k, v in timed.items()},
                     "step_alg_bytes_per_view": alg["warp_splat"] + alg["resolve"],
                     "step_frac": (alg["warp_splat"] + alg["resolve"]) * n_views / world / (el_ms / 1e3) / 1e9
-                                 / peak}
+                                 / peak,
+                    "compulsory_bytes_per_view": compulsory_bytes(K, Ns, Nd),
+                    "compulsory_frac": compulsory_bytes(K, Ns, Nd) * n_views / world / (el_ms / 1e3) / 1e9 / peak,
+                    "atomics_per_view": rho * K * Ns}
 
     # end to end through the C ABI with host buffers
     e2e = None

@@ -94,6 +94,17 @@ def test_step_bytes_count_every_kernel_once():
     assert step / 1e6 == pytest.approx(136.76, abs=0.01)
 
 
+def test_compulsory_bytes_are_the_frames_read_once_and_the_view_written_once():
+    """5 K Ns + 3 Nd: 9 cameras' uint16 depth and RGB8 colour at 1280x720,
+    one RGB8 view, 44.2 MB; below the algorithmic bytes of the step."""
+    K, Ns, Nd = 9, 921600, 921600
+    c = bench.compulsory_bytes(K, Ns, Nd)
+    assert c == 9 * 921600 * (2 + 3) + 921600 * 3
+    assert c / 1e6 == pytest.approx(44.24, abs=0.01)
+    a = bench.algorithmic_bytes(K, Ns, Nd, 0.95, K)
+    assert c < a["warp_splat"] + a["resolve"]
+
+
 def test_recorded_runs_are_read_from_their_json_block(tmp_path, monkeypatch):
     (tmp_path / "profiles").mkdir()
     (tmp_path / "profiles" / "x.md").write_text("# t\n\n```json\n{\"a\": 1, \"b\": [2, 3]}\n```\n")
