@@ -116,6 +116,38 @@ def test_mixed_view_sizes_in_one_batch(oracle_mod, arc_small):
                       "%dx%d" % (v.width, v.height))
 
 
+def test_widest_views(oracle_mod, arc_small):
+    """The resolve stages key rows in shared memory, so the view width is
+    bounded by the per-CTA limit: a 5000-pixel-wide view (about 205 KB of
+    shared memory at nine cameras) matches the oracle, and an 8192-wide one is
+    refused as too wide before anything is launched."""
+    import torch
+    wl = arc_small
+    base = wl["views"][120]
+    wide = base.copy()
+    W, H, f = 5000, 6, 260.0
+    wide.width, wide.height, wide.fx, wide.fy, wide.cx, wide.cy = W, H, f, f, (W - 1) / 2, (H - 1) / 2
+    g = gpu_run(wl["cams"], wl["rgb"], wl["depth"], [wide], wl["look_at"])[0]
+    ref = _oracle(oracle_mod, wl["cams"], wl["rgb"], wl["depth"], wide, wl["look_at"])
+    assert_parity(g, ref, "5000 wide")
+    assert (ref["hole"] == 0).any() and (ref["hole"] == 1).any()
+    F = lib()
+    too = base.copy()
+    too.width, too.height, too.fx, too.fy, too.cx, too.cy = 8192, 2, f, f, 4095.5, 0.5
+    ctx = F.fvv_create(F.rig(wl["cams"], wl["look_at"]), None)
+    try:
+        for k, c in enumerate(wl["cams"]):
+            F.fvv_upload_frame(ctx, k, np.ascontiguousarray(wl["rgb"][k]), c.width * 3,
+                               np.ascontiguousarray(wl["depth"][k]), c.width * 2, 0)
+        out = torch.zeros((2, 8192 * 3), dtype=torch.uint8, device="cuda")
+        with pytest.raises(F.FvvError) as e:
+            F.fvv_synthesize_batch(ctx, [too], [0], [out], [8192 * 3])
+        assert e.value.code == F.FVV_ERR_INVALID_ARG
+        assert "width" in str(e.value)
+    finally:
+        F.fvv_destroy(ctx)
+
+
 def test_sixty_four_cameras(oracle_mod):
     """The 6-bit camera field at its limit: 64 cameras on a full circle."""
     cams = S.rig_arc(64, 354.375, 1.5, 24, 16, 20.0)
