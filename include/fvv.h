@@ -7,15 +7,15 @@
  * plus depth frames.  Every step runs in the library's CUDA kernels for
  * sm_103a:
  *   (a) per-camera unproject/reproject warp of every pixel with depth
- *       (Sec. VI: "each pixel ... corresponds to a line in 3D space, and
- *       depth information constrains that line to a single point");
+ *       (Sec. VI: a pixel of a calibrated camera is a ray, and its depth
+ *       fixes the 3D point on that ray);
  *   (b) z-buffer splat with 64-bit atomicMin on packed keys
  *       bits(Z) << 32 | camera << 26 | source pixel;
  *   (c) crack / outlier filter on the key image (Sec. VI: cracks from
  *       magnification, handled by backward warping plus filtering);
- *   (d) backward fetch and blend weighted by the angular distance of each
- *       reference camera to the virtual camera (Sec. VI: contributions are
- *       mixed according to that distance);
+ *   (d) backward fetch and blend, each camera weighted by its angular
+ *       distance from the virtual camera (Sec. VI weighs the cameras'
+ *       contributions by that distance);
  *   (e) row-wise hole filling from the background side (Sec. VI names
  *       disocclusions; the paper leaves them black, Sec. IX, fig. of test
  *       screenshots -- the fill can be switched off).
@@ -30,8 +30,13 @@
  *   - Every call returns an fvv_status; on failure fvv_last_error() holds a
  *     message for the calling thread.
  *   - Buffers passed in may be host memory (pageable or pinned) or device
- *     memory of the current device; the kind is detected per pointer.
- *     The library keeps no pointer to a caller buffer after a call returns.
+ *     memory of the context's device (the device current at fvv_create);
+ *     the kind is detected per pointer.  Device memory of another GPU is
+ *     refused with FVV_ERR_INVALID_ARG wherever a kernel would read or
+ *     write it.  A call on a context makes the context's device current for
+ *     its duration and gives the caller's current device back on return;
+ *     calls without a context use the current device.  The library keeps
+ *     no pointer to a caller buffer after a call returns.
  *   - `stream` is a cudaStream_t passed as void* (NULL = the library's own
  *     stream).  Calls enqueue their GPU work on that stream; a call that
  *     writes host memory returns after that data is written.  Calls on one
@@ -210,8 +215,8 @@ fvv_status fvv_select_cameras(const fvv_rig* rig, int32_t n_views, const fvv_vie
 fvv_status fvv_set_bg_depth(fvv_ctx* ctx, int32_t cam, const uint16_t* depth, size_t pitch);
 
 /* ---- joint bilateral depth pre-filter (Sec. VI) ------------------------
- * Live depth is pre-processed to close small holes and gaps around object
- * edges with a joint bilateral filter guided by the colour frame.  A pixel
+ * A joint bilateral filter guided by the colour frame fills small gaps in
+ * the live depth, in particular along object boundaries.  A pixel
  * without depth (0) takes the weighted mean of the valid codes (in [d_lo,
  * d_hi], not FVV_DEPTH_BG) of its (2 jbf_radius + 1)^2 window, visited in
  * row-major order; the weight is s(dx, dy) c(|dR|) c(|dG|) c(|dB|) with

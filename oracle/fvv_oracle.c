@@ -23,8 +23,8 @@
  *       orders by depth, then camera, then source pixel.
  *   R5  crack/outlier filter (Sec. VI names cracks and "backward warping
  *       combined with filtering" but gives no rule): see oracle_crack_filter.
- *   R6  mixing "according to the distance of each reference camera to the
- *       virtual camera" (Sec. VI) read as angular distance about the rig's
+ *   R6  Sec. VI weights each reference camera by its distance from the
+ *       virtual camera; read as the angular distance about the rig's
  *       look-at point: w_k = 1 / (theta_k + 1e-3) for the n_ref nearest
  *       cameras, 0 for the rest; one-hot when the view sits on a camera.
  *   R7  backward fetch: a non-winning camera contributes when the

@@ -1,6 +1,6 @@
 """CPU oracle of the joint bilateral depth pre-filter of the view-synthesis
-side (Sec. VI: live depth is pre-processed to close small holes and gaps
-around object edges with a joint bilateral filter guided by the colour).
+side (Sec. VI: a colour-guided joint bilateral filter fills small gaps in
+the live depth, in particular along object boundaries).
 
 TEST INFRASTRUCTURE ONLY (tests, smoke check, benchmark CPU leg).  numpy,
 FP32 arithmetic in the order stated below.

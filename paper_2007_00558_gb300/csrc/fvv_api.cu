@@ -57,8 +57,14 @@ fvv::MemKind fvv::mem_kind(const void* p)
         cudaGetLastError();
         return MemKind::Host;
     }
-    return (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) ? MemKind::Device
-                                                                               : MemKind::Host;
+    if (a.type == cudaMemoryTypeManaged) return MemKind::Device;
+    if (a.type != cudaMemoryTypeDevice) return MemKind::Host;
+    int cur = -1;
+    if (cudaGetDevice(&cur) != cudaSuccess) {
+        cudaGetLastError();
+        return MemKind::Foreign;
+    }
+    return a.device == cur ? MemKind::Device : MemKind::Foreign;
 }
 
 namespace {
@@ -162,8 +168,8 @@ void centre_of(const fvv_camera& c, double C[3])
         C[j] = -(c.R[0 + j] * c.t[0] + c.R[3 + j] * c.t[1] + c.R[6 + j] * c.t[2]);
 }
 
-// Mixing by "the distance of each reference camera to the virtual camera"
-// (Sec. VI), read as the angle between the two viewing directions from the
+// Sec. VI weights a reference camera by its distance from the virtual
+// camera, read as the angle between the two viewing directions from the
 // rig's look-at point: theta = atan2(|a x b|, a . b).
 double angle_about(const double Cv[3], const double Ck[3], const double O[3])
 {
@@ -350,6 +356,8 @@ fvv_status fvv::upload_frame(fvv_ctx* c, int cam, const uint8_t* rgb, size_t rgb
 {
     const fvv_camera& C = c->cams[cam];
     if (!rgb || (!depth && !yuv)) return fail(FVV_ERR_INVALID_ARG, "rgb and depth must be non-NULL");
+    if (foreign(rgb) || foreign(depth) || (yuv && (foreign(yuv->y) || foreign(yuv->u) || foreign(yuv->v))))
+        return fail(FVV_ERR_INVALID_ARG, "frame buffers must be host memory or the context's device memory");
     if (rgb_pitch < size_t(C.width) * 3) return fail(FVV_ERR_INVALID_ARG, "rgb_pitch < 3 * width");
     if (!yuv && depth_pitch < size_t(C.width) * 2) return fail(FVV_ERR_INVALID_ARG, "depth_pitch < 2 * width");
     const int si = int(tick % uint64_t(c->slots));
@@ -642,6 +650,10 @@ fvv_status fvv::run_batch(fvv_ctx* c, BatchScratch& S, int n, const fvv_view* vi
         if (fvv::resolve_smem_bytes(V.width, c->n_cams, c->opt.layered != 0) > c->smem_optin)
             return fail(FVV_ERR_INVALID_ARG, "view " + std::to_string(i) + ": width too large");
         if (!out_rgb[i]) return fail(FVV_ERR_INVALID_ARG, "out_rgb[" + std::to_string(i) + "] is NULL");
+        if (foreign(out_rgb[i]) ||
+            (aux && (foreign(aux[i].depth) || foreign(aux[i].hole) || foreign(aux[i].top3) || foreign(aux[i].keys))))
+            return fail(FVV_ERR_INVALID_ARG, "view " + std::to_string(i) +
+                                                 ": outputs must be host memory or the context's device memory");
         if (out_pitch[i] < size_t(V.width) * 3) return fail(FVV_ERR_INVALID_ARG, "out_pitch < 3 * width");
         CamGeom* g = geom.data() + size_t(i) * c->n_cams;
         compose_view(c->n_cams, c->cams.data(), c->look_at, c->depth_unit_m, c->opt.n_ref, V, g);
@@ -864,6 +876,7 @@ fvv_status fvv_synthesize_batch(fvv_ctx* c, int32_t n, const fvv_view* views, co
     if (!c) return fail(FVV_ERR_INVALID_ARG, "ctx is NULL");
     if (n < 1 || n > c->opt.max_batch)
         return fail(FVV_ERR_INVALID_ARG, "batch size must be in [1, max_batch]");
+    fvv::DeviceScope dev_scope(c->device);
     cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : c->own;
     std::lock_guard<std::recursive_mutex> lock(c->mu);
     return fvv::run_batch(c, c->main, n, views, ticks, out_rgb, out_pitch, aux, s, true);
@@ -938,43 +951,42 @@ fvv_status fvv_view_params(const fvv_rig* rig, const fvv_options* opt, const fvv
 fvv_status fvv_destroy(fvv_ctx* c)
 {
     if (!c) return FVV_OK;
-    fvv::serve_shutdown(c);
-    fvv::refine_destroy(c);
-    fvv::codec_destroy(c);
-    int cur = 0;
-    cudaGetDevice(&cur);
-    cudaSetDevice(c->device);
-    if (c->own) cudaStreamSynchronize(c->own);
-    cudaDeviceSynchronize();
-    fvv::scratch_free(c, c->main);
-    for (auto& S : c->slot) {
-        if (S.uploaded) cudaEventDestroy(S.uploaded);
-        for (cudaEvent_t e : S.read)
-            if (e) cudaEventDestroy(e);
+    {   // the context's device for the teardown, the caller's again after it
+        fvv::DeviceScope dev_scope(c->device);
+        fvv::serve_shutdown(c);
+        fvv::refine_destroy(c);
+        fvv::codec_destroy(c);
+        if (c->own) cudaStreamSynchronize(c->own);
+        cudaDeviceSynchronize();
+        fvv::scratch_free(c, c->main);
+        for (auto& S : c->slot) {
+            if (S.uploaded) cudaEventDestroy(S.uploaded);
+            for (cudaEvent_t e : S.read)
+                if (e) cudaEventDestroy(e);
+        }
+        for (auto& K : c->kstat)
+            for (auto& ev : K.pending) c->event_pool.push_back(ev);
+        for (auto& ev : c->event_pool) {
+            cudaEventDestroy(ev.first);
+            cudaEventDestroy(ev.second);
+        }
+        for (int k = 0; k < c->n_cams; ++k)
+            if (c->stage_rgb[k])
+                dev_free(c, c->stage_rgb[k], size_t(c->cams[k].width) * 3 * size_t(c->cams[k].height));
+        for (size_t k = 0; k < c->bg.size(); ++k)
+            dev_free(c, c->bg[k], size_t(c->cams[k].height) * c->dpitch[k] * 2);
+        for (size_t k = 0; k < c->jbf_tmp.size(); ++k)
+            dev_free(c, c->jbf_tmp[k], size_t(c->cams[k].height) * c->dpitch[k] * 2);
+        dev_free(c, c->frames_dev, sizeof(FrameRef) * size_t(c->slots) * c->n_cams);
+        dev_free(c, c->arena, c->arena_bytes);
+        for (int i = 0; i < 2; ++i) {
+            if (c->stage_all[i]) dev_free(c, c->stage_all[i], c->stage_all_bytes[i]);
+            if (c->stage_all_free[i]) cudaEventDestroy(c->stage_all_free[i]);
+        }
+        if (c->stage_free) cudaEventDestroy(c->stage_free);
+        if (c->own) cudaStreamDestroy(c->own);
+        cudaGetLastError();
     }
-    for (auto& K : c->kstat)
-        for (auto& ev : K.pending) c->event_pool.push_back(ev);
-    for (auto& ev : c->event_pool) {
-        cudaEventDestroy(ev.first);
-        cudaEventDestroy(ev.second);
-    }
-    for (int k = 0; k < c->n_cams; ++k)
-        if (c->stage_rgb[k])
-            dev_free(c, c->stage_rgb[k], size_t(c->cams[k].width) * 3 * size_t(c->cams[k].height));
-    for (size_t k = 0; k < c->bg.size(); ++k)
-        dev_free(c, c->bg[k], size_t(c->cams[k].height) * c->dpitch[k] * 2);
-    for (size_t k = 0; k < c->jbf_tmp.size(); ++k)
-        dev_free(c, c->jbf_tmp[k], size_t(c->cams[k].height) * c->dpitch[k] * 2);
-    dev_free(c, c->frames_dev, sizeof(FrameRef) * size_t(c->slots) * c->n_cams);
-    dev_free(c, c->arena, c->arena_bytes);
-    for (int i = 0; i < 2; ++i) {
-        if (c->stage_all[i]) dev_free(c, c->stage_all[i], c->stage_all_bytes[i]);
-        if (c->stage_all_free[i]) cudaEventDestroy(c->stage_all_free[i]);
-    }
-    if (c->stage_free) cudaEventDestroy(c->stage_free);
-    if (c->own) cudaStreamDestroy(c->own);
-    cudaGetLastError();
-    cudaSetDevice(cur);
     delete c;
     return FVV_OK;
 }
@@ -1088,6 +1100,7 @@ fvv_status fvv_upload_frame(fvv_ctx* c, int32_t cam, const uint8_t* rgb, size_t 
 {
     if (!c) return fail(FVV_ERR_INVALID_ARG, "ctx is NULL");
     if (cam < 0 || cam >= c->n_cams) return fail(FVV_ERR_INVALID_ARG, "camera index out of range");
+    fvv::DeviceScope dev_scope(c->device);
     cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : c->own;
     std::lock_guard<std::recursive_mutex> lock(c->mu);
     return upload_one(c, cam, rgb, rgb_pitch, depth, depth_pitch, tick, s);
@@ -1101,7 +1114,7 @@ fvv_status fvv_set_bg_depth(fvv_ctx* c, int32_t cam, const uint16_t* depth, size
     if (depth && (pitch < size_t(C.width) * 2 || pitch % 2))
         return fail(FVV_ERR_INVALID_ARG, "pitch must be even and >= 2 * width");
     std::lock_guard<std::recursive_mutex> lock(c->mu);
-    FVV_CUDA(cudaSetDevice(c->device));
+    fvv::DeviceScope dev_scope(c->device);
     // kernels in flight may read the model: replace it only when they are done
     FVV_CUDA(cudaDeviceSynchronize());
     const size_t bytes = size_t(C.height) * c->dpitch[cam] * 2;
@@ -1132,6 +1145,7 @@ fvv_status fvv_upload_frames_subset(fvv_ctx* c, uint64_t cam_mask, const uint8_t
     if (!rgb || !depth) return fail(FVV_ERR_INVALID_ARG, "rgb and depth must be non-NULL");
     if (cam_mask == 0 || (cam_mask & ~c->full_mask) != 0)
         return fail(FVV_ERR_INVALID_ARG, "camera mask empty or naming cameras the rig does not have");
+    fvv::DeviceScope dev_scope(c->device);
     cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : c->own;
     std::lock_guard<std::recursive_mutex> lock(c->mu);
     int first = -1;
@@ -1143,6 +1157,8 @@ fvv_status fvv_upload_frames_subset(fvv_ctx* c, uint64_t cam_mask, const uint8_t
                   c->cams[k].height == c->cams[first].height;
     }
     const fvv::MemKind kr = fvv::mem_kind(rgb), kd = fvv::mem_kind(depth);
+    if (kr == fvv::MemKind::Foreign || kd == fvv::MemKind::Foreign)
+        return fail(FVV_ERR_INVALID_ARG, "frame buffers must be host memory or the context's device memory");
     // the batched kernel reads depth as uint16: device rows must be 2-byte aligned
     const bool aligned = depth_pitch % 2 == 0 && depth_cam_stride % 2 == 0 &&
                          (kd == fvv::MemKind::Host || (reinterpret_cast<uintptr_t>(depth) & 1) == 0);
@@ -1166,12 +1182,15 @@ fvv_status fvv_upload_frames_yuv(fvv_ctx* c, const uint8_t* rgb, size_t rgb_cam_
 {
     if (!c) return fail(FVV_ERR_INVALID_ARG, "ctx is NULL");
     if (!rgb || !yuv) return fail(FVV_ERR_INVALID_ARG, "rgb and yuv must be non-NULL");
+    fvv::DeviceScope dev_scope(c->device);
     cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : c->own;
     std::lock_guard<std::recursive_mutex> lock(c->mu);
     for (int k = 1; k < c->n_cams; ++k)
         if (c->cams[k].width != c->cams[0].width || c->cams[k].height != c->cams[0].height)
             return fail(FVV_ERR_INVALID_ARG, "fvv_upload_frames_yuv needs cameras of one size");
     const fvv::MemKind kr = fvv::mem_kind(rgb), ky = fvv::mem_kind(yuv);
+    if (kr == fvv::MemKind::Foreign || ky == fvv::MemKind::Foreign)
+        return fail(FVV_ERR_INVALID_ARG, "frame buffers must be host memory or the context's device memory");
     if (kr != ky) return fail(FVV_ERR_INVALID_ARG, "rgb and yuv must both be host or both device memory");
     return upload_all(c, c->full_mask, rgb, rgb_cam_stride, rgb_pitch, yuv, yuv_cam_stride, 0, tick, s,
                       kr == fvv::MemKind::Host, true);
@@ -1222,6 +1241,7 @@ fvv_status fvv_profile_enable(fvv_ctx* c, int32_t on)
 fvv_status fvv_profile_read(fvv_ctx* c, fvv_kernel_stats* out, int32_t* n, int32_t reset)
 {
     if (!c || !n) return fail(FVV_ERR_INVALID_ARG, "NULL argument");
+    fvv::DeviceScope dev_scope(c->device);
     std::lock_guard<std::recursive_mutex> lock(c->mu);
     for (auto& K : c->kstat) {
         for (auto& ev : K.pending) {

@@ -337,7 +337,7 @@ fvv_status fvv_set_depth_codec(fvv_ctx* c, int32_t cam, const fvv_depth_codec* p
         !std::isfinite(p->beta))
         return fail(FVV_ERR_INVALID_ARG, "need 0 < z_near < z_far and finite alpha, beta");
     std::lock_guard<std::recursive_mutex> g(c->mu);
-    FVV_CUDA(cudaSetDevice(c->device));
+    fvv::DeviceScope dev_scope(c->device);
     if (!c->codec) {
         auto* K = new fvv::CodecState();
         K->set.assign(c->n_cams, 0);
@@ -367,6 +367,7 @@ fvv_status fvv_depth_encode_yuv(fvv_ctx* c, int32_t cam, const uint16_t* depth, 
                                 size_t y_pitch, uint8_t* u, uint8_t* v, size_t uv_pitch, void* stream)
 {
     FVV_TRY(fvv::check_cam(c, cam));
+    fvv::DeviceScope dev_scope(c->device);
     const int W = c->cams[cam].width, H = c->cams[cam].height;
     if (!fvv::on_dev(depth) || !fvv::on_dev(y) || !fvv::on_dev(u) || !fvv::on_dev(v))
         return fail(FVV_ERR_INVALID_ARG, "depth and the Y, U, V planes must be device memory");
@@ -386,6 +387,7 @@ fvv_status fvv_depth_decode_yuv(fvv_ctx* c, int32_t cam, const uint8_t* y, size_
                                 const uint8_t* v, size_t uv_pitch, uint16_t* depth, size_t depth_pitch, void* stream)
 {
     FVV_TRY(fvv::check_cam(c, cam));
+    fvv::DeviceScope dev_scope(c->device);
     const int W = c->cams[cam].width, H = c->cams[cam].height;
     if (!fvv::on_dev(depth) || !fvv::on_dev(y) || !fvv::on_dev(u) || !fvv::on_dev(v))
         return fail(FVV_ERR_INVALID_ARG, "depth and the Y, U, V planes must be device memory");
@@ -403,6 +405,7 @@ fvv_status fvv_depth_decode_yuv_frames(fvv_ctx* c, int32_t n_cams, const uint8_t
 {
     if (!c) return fail(FVV_ERR_INVALID_ARG, "ctx is NULL");
     if (n_cams < 1 || n_cams > c->n_cams) return fail(FVV_ERR_INVALID_ARG, "n_cams out of range");
+    fvv::DeviceScope dev_scope(c->device);
     for (int k = 0; k < n_cams; ++k) {
         FVV_TRY(fvv::check_cam(c, k));
         if (c->cams[k].width != c->cams[0].width || c->cams[k].height != c->cams[0].height)
@@ -452,9 +455,12 @@ fvv_status fvv_upload_frame_yuv(fvv_ctx* c, int32_t cam, const uint8_t* rgb, siz
                                 void* stream)
 {
     FVV_TRY(fvv::check_cam(c, cam));
+    fvv::DeviceScope dev_scope(c->device);
     if (!y || !u || !v) return fail(FVV_ERR_INVALID_ARG, "Y, U and V must be non-NULL");
     const int W = c->cams[cam].width, H = c->cams[cam].height;
     if (y_pitch < size_t(W) || uv_pitch < size_t(W / 2)) return fail(FVV_ERR_INVALID_ARG, "pitch too small");
+    if (fvv::foreign(rgb) || fvv::foreign(y) || fvv::foreign(u) || fvv::foreign(v))
+        return fail(FVV_ERR_INVALID_ARG, "frame buffers must be host memory or the context's device memory");
     const bool dy = fvv::on_dev(y), du = fvv::on_dev(u), dv = fvv::on_dev(v);
     if (dy != du || dy != dv) return fail(FVV_ERR_INVALID_ARG, "Y, U, V must all be host or all device memory");
     cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : c->own;

@@ -1,6 +1,6 @@
-// fvv_jbf.cu -- joint bilateral depth pre-filter (Sec. VI: live depth is
-// pre-processed to close small holes and gaps around object edges with a
-// joint bilateral filter guided by the colour frame).
+// fvv_jbf.cu -- joint bilateral depth pre-filter (Sec. VI: a colour-guided
+// joint bilateral filter fills small gaps in the live depth, in particular
+// along object boundaries).
 //
 // A pixel without depth (code 0) takes the weighted mean of the valid codes
 // in its (2r+1) x (2r+1) window; every other pixel keeps its code.  The

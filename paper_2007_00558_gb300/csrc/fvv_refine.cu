@@ -670,6 +670,7 @@ fvv_status refine_reserve(fvv_ctx* c, size_t pixels)
 {
     RefineNet* N = c->refine;
     if (!N) return fail(FVV_ERR_STATE, "refinement network not initialised");
+    fvv::DeviceScope dev_scope(c->device);
     return N->precision == FVV_PREC_E4M3 ? ensure_acts8(c, *N, pixels) : ensure_acts(c, *N, pixels);
 }
 
@@ -677,6 +678,7 @@ fvv_status refine_forward_async(fvv_ctx* c, const fvv_refine_batch& b, uint8_t* 
 {
     RefineNet* N = c->refine;
     if (!N) return fail(FVV_ERR_STATE, "refinement network not initialised");
+    fvv::DeviceScope dev_scope(c->device);
     int* err = nullptr;
     FVV_TRY(device_flag(&err));
     const size_t px = size_t(b.n) * b.height * b.width;
@@ -843,6 +845,7 @@ fvv_status fvv_refine_default_cfg(fvv_unet_cfg* cfg)
 fvv_status fvv_refine_init(fvv_ctx* c, const fvv_unet_cfg* cfg_in)
 {
     if (!c) return fail(FVV_ERR_INVALID_ARG, "ctx is NULL");
+    fvv::DeviceScope dev_scope(c->device);
     fvv_unet_cfg cfg;
     if (cfg_in) cfg = *cfg_in; else fvv_refine_default_cfg(&cfg);
     // every forward output width and every part of every input gradient is a
@@ -924,6 +927,7 @@ fvv_status fvv_refine_get(fvv_ctx* c, int32_t which, float* out)
 {
     RefineNet* N = fvv::net_of(c);
     if (!N) return fail(FVV_ERR_STATE, "refinement network not initialised");
+    fvv::DeviceScope dev_scope(c->device);
     if (!out || which < 0 || which > 3) return fail(FVV_ERR_INVALID_ARG, "bad buffer selector or NULL");
     std::lock_guard<std::recursive_mutex> g(c->mu);
     FVV_CUDA(cudaDeviceSynchronize());
@@ -934,6 +938,7 @@ fvv_status fvv_refine_set(fvv_ctx* c, int32_t which, const float* in)
 {
     RefineNet* N = fvv::net_of(c);
     if (!N) return fail(FVV_ERR_STATE, "refinement network not initialised");
+    fvv::DeviceScope dev_scope(c->device);
     if (!in || which < 0 || which > 3) return fail(FVV_ERR_INVALID_ARG, "bad buffer selector or NULL");
     std::lock_guard<std::recursive_mutex> g(c->mu);
     if (fvv::serve_refining(c)) return fail(FVV_ERR_BUSY, "the serving loop is running the refinement network");
@@ -948,6 +953,7 @@ fvv_status fvv_refine_forward(fvv_ctx* c, const fvv_refine_batch* b, uint8_t* ou
 {
     RefineNet* N = fvv::net_of(c);
     if (!N) return fail(FVV_ERR_STATE, "refinement network not initialised");
+    fvv::DeviceScope dev_scope(c->device);
     FVV_TRY(fvv::check_batch(*N, b, false));
     if ((out_rgb && !fvv::on_device(out_rgb)) || (out_f32 && !fvv::on_device(out_f32)))
         return fail(FVV_ERR_INVALID_ARG, "outputs must be device memory");
@@ -970,6 +976,7 @@ fvv_status fvv_refine_quantize(fvv_ctx* c, const fvv_refine_batch* calib, const 
 {
     RefineNet* N = fvv::net_of(c);
     if (!N) return fail(FVV_ERR_STATE, "refinement network not initialised");
+    fvv::DeviceScope dev_scope(c->device);
     cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : c->own;
     std::lock_guard<std::recursive_mutex> g(c->mu);
     if (fvv::serve_refining(c)) return fail(FVV_ERR_BUSY, "the serving loop is running the refinement network");
@@ -1014,6 +1021,7 @@ fvv_status fvv_refine_set_precision(fvv_ctx* c, int32_t precision)
 {
     RefineNet* N = fvv::net_of(c);
     if (!N) return fail(FVV_ERR_STATE, "refinement network not initialised");
+    fvv::DeviceScope dev_scope(c->device);
     if (precision != FVV_PREC_BF16 && precision != FVV_PREC_E4M3)
         return fail(FVV_ERR_INVALID_ARG, "precision must be FVV_PREC_BF16 or FVV_PREC_E4M3");
     std::lock_guard<std::recursive_mutex> g(c->mu);
@@ -1028,6 +1036,7 @@ fvv_status fvv_refine_get_precision(fvv_ctx* c, int32_t* precision, float* act_s
 {
     RefineNet* N = fvv::net_of(c);
     if (!N) return fail(FVV_ERR_STATE, "refinement network not initialised");
+    fvv::DeviceScope dev_scope(c->device);
     if (!precision) return fail(FVV_ERR_INVALID_ARG, "precision is NULL");
     std::lock_guard<std::recursive_mutex> g(c->mu);
     *precision = N->precision;
@@ -1040,6 +1049,7 @@ fvv_status fvv_refine_train_step(fvv_ctx* c, const fvv_refine_batch* b, float lr
 {
     RefineNet* N = fvv::net_of(c);
     if (!N) return fail(FVV_ERR_STATE, "refinement network not initialised");
+    fvv::DeviceScope dev_scope(c->device);
     FVV_TRY(fvv::check_batch(*N, b, true));
     if (!(lr >= 0.0f) || !std::isfinite(lr)) return fail(FVV_ERR_INVALID_ARG, "lr must be >= 0");
     cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : c->own;
@@ -1064,6 +1074,7 @@ fvv_status fvv_refine_save(fvv_ctx* c, const char* path)
 {
     RefineNet* N = fvv::net_of(c);
     if (!N) return fail(FVV_ERR_STATE, "refinement network not initialised");
+    fvv::DeviceScope dev_scope(c->device);
     if (!path) return fail(FVV_ERR_INVALID_ARG, "path is NULL");
     std::lock_guard<std::recursive_mutex> g(c->mu);
     FVV_CUDA(cudaDeviceSynchronize());
@@ -1088,6 +1099,7 @@ fvv_status fvv_refine_save(fvv_ctx* c, const char* path)
 fvv_status fvv_refine_load(fvv_ctx* c, const char* path)
 {
     if (!c || !path) return fail(FVV_ERR_INVALID_ARG, "NULL argument");
+    fvv::DeviceScope dev_scope(c->device);
     FILE* f = std::fopen(path, "rb");
     if (!f) return fail(FVV_ERR_INVALID_ARG, std::string("cannot open ") + path);
     char magic[8];
@@ -1129,6 +1141,7 @@ fvv_status fvv_synthesize_refined(fvv_ctx* c, const fvv_view* view, uint8_t* out
 {
     RefineNet* N = fvv::net_of(c);
     if (!N) return fail(FVV_ERR_STATE, "refinement network not initialised");
+    fvv::DeviceScope dev_scope(c->device);
     if (!view || !out_rgb) return fail(FVV_ERR_INVALID_ARG, "NULL argument");
     const int H = view->height, W = view->width;
     if (H % 4 || W % 4) return fail(FVV_ERR_INVALID_ARG, "refined views need width and height multiples of 4");
@@ -1166,6 +1179,8 @@ fvv_status fvv_synthesize_refined(fvv_ctx* c, const fvv_view* view, uint8_t* out
     b.top3 = N->syn_top3;
     int* err = nullptr;
     FVV_TRY(fvv::device_flag(&err));
+    if (fvv::foreign(out_rgb))
+        return fail(FVV_ERR_INVALID_ARG, "out_rgb must be host memory or the context's device memory");
     const bool dev_out = fvv::mem_kind(out_rgb) == fvv::MemKind::Device;
     if (N->precision == FVV_PREC_E4M3) {
         FVV_TRY(fvv::ensure_acts8(c, *N, size_t(H) * W));

@@ -37,8 +37,39 @@ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
         if (s_ != FVV_OK) return s_;       \
     } while (0)
 
-enum class MemKind { Device, Host };
+// Where a caller's buffer lives: device memory that the current device's
+// kernels may use (its own, or managed), host memory (pageable or pinned),
+// or device memory of another GPU.  Entry points refuse the last kind for
+// buffers their kernels read or write: the kernels would dereference the
+// pointer on the wrong device.
+enum class MemKind { Device, Host, Foreign };
 MemKind mem_kind(const void* p);
+inline bool foreign(const void* p) { return p && mem_kind(p) == MemKind::Foreign; }
+
+// Makes a context's device current for the rest of an entry point (its
+// launches, allocations and pointer checks) and gives the caller's current
+// device back on return.
+class DeviceScope {
+public:
+    explicit DeviceScope(int dev)
+    {
+        if (cudaGetDevice(&prev_) != cudaSuccess) {
+            cudaGetLastError();
+            prev_ = -1;
+        }
+        if (prev_ != dev) cudaSetDevice(dev);
+    }
+    ~DeviceScope()
+    {
+        int cur = -1;
+        if (prev_ >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev_) cudaSetDevice(prev_);
+    }
+    DeviceScope(const DeviceScope&) = delete;
+    DeviceScope& operator=(const DeviceScope&) = delete;
+
+private:
+    int prev_ = -1;
+};
 
 // Valid pinhole camera (also used for views); `why` gets the reason.
 bool camera_ok(const fvv_camera& c, std::string* why);

@@ -679,6 +679,7 @@ fvv_status fvv_serve_default_cfg(fvv_serve_cfg* cfg)
 fvv_status fvv_serve_start(fvv_ctx* c, const fvv_serve_cfg* cfg_in)
 {
     if (!c) return fail(FVV_ERR_INVALID_ARG, "ctx is NULL");
+    fvv::DeviceScope dev_scope(c->device);
     fvv_serve_cfg cfg;
     if (cfg_in) cfg = *cfg_in; else fvv_serve_default_cfg(&cfg);
     if (cfg.lanes < 1 || cfg.lanes > fvv::kMaxReaders - 1)
@@ -805,6 +806,8 @@ fvv_status fvv_serve_submit(fvv_ctx* c, uint32_t viewer, const fvv_view* view, u
     if (!c || !view || !out || !ticket) return fail(FVV_ERR_INVALID_ARG, "NULL argument");
     ServeState* st = c->serve;
     if (!st) return fail(FVV_ERR_STATE, "serving loop not running");
+    fvv::DeviceScope dev_scope(c->device);
+    if (fvv::foreign(out)) return fail(FVV_ERR_INVALID_ARG, "out must be host memory or the context's device memory");
     std::string why;
     if (!fvv::camera_ok(*view, &why)) return fail(FVV_ERR_INVALID_ARG, "view: " + why);
     if (fvv::resolve_smem_bytes(view->width, c->n_cams, c->opt.layered != 0) > c->smem_optin)
@@ -914,6 +917,7 @@ fvv_status fvv_serve_stop(fvv_ctx* c)
 {
     if (!c) return fail(FVV_ERR_INVALID_ARG, "ctx is NULL");
     if (!c->serve) return fail(FVV_ERR_STATE, "serving loop not running");
+    fvv::DeviceScope dev_scope(c->device);
     fvv::serve_shutdown(c);
     return FVV_OK;
 }

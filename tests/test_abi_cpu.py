@@ -105,3 +105,50 @@ def test_selftest_limit_checked_on_host(F):
     so = F.load()
     for lim in (0, 2000001):
         assert so.fvv_selftest_bounded_wait(0, lim, None) == F.FVV_ERR_INVALID_ARG
+
+
+# Entry points that forward to another entry point (which holds the scope).
+_FORWARDERS = {"fvv_synthesize": "fvv_synthesize_batch", "fvv_upload_frames": "fvv_upload_frames_subset"}
+
+
+def test_context_entry_points_select_the_context_device():
+    """Every C-ABI call on a context that touches the GPU makes the context's
+    device current for the call (a DeviceScope, which also gives the
+    caller's device back), so its launches, allocations and the check that
+    caller buffers are this device's memory never follow whatever device
+    the calling thread had current.  A static check over the sources: each
+    such function's body holds a DeviceScope before its first CUDA call."""
+    import os
+    import re
+    csrc = os.path.join(os.path.dirname(__file__), "..", "paper_2007_00558_gb300", "csrc")
+    found = {}
+    for fn in sorted(os.listdir(csrc)):
+        if not fn.endswith(".cu"):
+            continue
+        src = open(os.path.join(csrc, fn)).read()
+        for m in re.finditer(r"\nfvv_status (fvv_\w+)\(fvv_ctx\* c[,)]", src):
+            name = m.group(1)
+            start = src.index("{", m.end())
+            depth, i = 0, start
+            while True:
+                if src[i] == "{":
+                    depth += 1
+                elif src[i] == "}":
+                    depth -= 1
+                    if depth == 0:
+                        break
+                i += 1
+            found[name] = src[start:i]
+    assert len(found) >= 30, sorted(found)
+    missing = []
+    for name, body in found.items():
+        if name in _FORWARDERS:
+            assert _FORWARDERS[name] + "(" in body and "cuda" not in body, name
+            continue
+        scope = body.find("DeviceScope")
+        calls = [body.find(t) for t in ("cuda", "run_batch", "upload_", "launch_", "dev_alloc", "serve_shutdown",
+                                        "refine_", "ensure_")]
+        calls = [c for c in calls if c >= 0]
+        if calls and (scope < 0 or min(calls) < scope):
+            missing.append(name)
+    assert not missing, "entry points without a device scope before their first CUDA call: %s" % missing

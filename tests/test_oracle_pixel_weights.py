@@ -1,6 +1,6 @@
 """Pins of the per-pixel angular weights (oracle R9, the per-pixel form of
-Sec. VI's mixing by the distance of each reference camera to the virtual
-camera) against an independent FP64 computation and the geometry."""
+Sec. VI's weighting of each camera by its distance from the virtual one)
+against an independent FP64 computation and the geometry."""
 import math
 
 import numpy as np
