@@ -747,9 +747,16 @@ def refine_bench(F, ctx, wl, steps, stream, data, widths=(32, 64, 128), fp8=Fals
     import torch
     from paper_2007_00558_gb300 import refine_train as RT
     train, test = data
+    # two throwaway steps take the first launches' module loading and
+    # allocations out of the timed run; the timed run starts from fresh
+    # weights of the same seed
     F.fvv_refine_init(ctx, F.fvv_refine_default_cfg(seed=1, widths=widths))
+    RT.train(ctx, train, steps=2, batch=8, crop=128, lr=2e-3)
+    F.fvv_refine_init(ctx, F.fvv_refine_default_cfg(seed=1, widths=widths))
+    torch.cuda.synchronize()
     t0 = time.perf_counter()
     losses = RT.train(ctx, train, steps=steps, batch=8, crop=128, lr=2e-3)
+    torch.cuda.synchronize()
     train_s = time.perf_counter() - t0
     ev = RT.evaluate(ctx, test)
     ev_q = None
