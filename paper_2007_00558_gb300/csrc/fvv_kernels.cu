@@ -471,8 +471,8 @@ __device__ __forceinline__ float pixel_weight(float cx, float cy, float cz, floa
 // memory; row y+2 is copied in asynchronously (cp.async) while row y is
 // resolved.  Each thread resolves the pixels x = tid, tid + 256, ... of a
 // row: the winner's colour, then the other active cameras in ascending
-// order, in groups of four whose projections and gathers are issued before
-// any is consumed.
+// order, in groups of eight (kGroup) whose projections and gathers are
+// issued before any is consumed.
 // kTop3: also track the three largest contributing weights (only when that
 // output is requested).  kPixW: per-pixel angular weights (each contribution
 // weighted by the angle at its surface point) instead of the view's
