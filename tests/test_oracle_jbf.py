@@ -144,3 +144,21 @@ def test_filter_closes_holes_of_the_synthesised_view(oracle_mod):
     ea = np.median(np.abs(a["depth"][both] - z[both]) / z[both])
     eb = np.median(np.abs(b["depth"][both] - z[both]) / z[both])
     assert eb <= ea * 1.05
+
+
+@pytest.mark.parametrize("channel", [0, 1, 2])
+def test_each_colour_channel_guides_alone(channel):
+    """Two depth regions whose colours differ in one channel only, a column
+    of holes between them whose colour is the right region's: every colour
+    channel enters the weight on its own, so the holes take the right
+    region's depth (the left neighbours' weight carries c(200) ~ e^-200 of
+    that channel's colour Gaussian, sigma_c = 10)."""
+    H, W = 9, 21
+    d = np.zeros((H, W), np.uint16)
+    d[:, :10] = 1000
+    d[:, 11:] = 3000
+    rgb = np.full((H, W, 3), 100, np.uint8)
+    rgb[:, :10, channel] = 0
+    rgb[:, 10:, channel] = 200
+    out = J.jbf(d, rgb, radius=2, sigma_s=2.0, sigma_c=10.0, min_valid=3)
+    assert np.all(out[:, 10] == 3000), out[:, 10]

@@ -80,3 +80,29 @@ def test_single_active_camera_is_unaffected(oracle_mod):
         a = oracle_mod.synthesize(wl["cams"], wl["rgb"], wl["depth"], v, wl["look_at"], **kw)
         b = oracle_mod.synthesize(wl["cams"], wl["rgb"], wl["depth"], v, wl["look_at"], pixel_weights=1, **kw)
         assert np.array_equal(a["rgb"], b["rgb"]) and np.array_equal(a["keys"], b["keys"])
+
+
+def test_weights_of_unequal_angles_match_fp64(oracle_mod):
+    """The view 15 mm from camera 0 and 585 mm from camera 1 (both parallel,
+    a fronto-parallel plane at 1.5 m): at the point the two rays meet camera
+    0's at ~0.01 rad and camera 1's at ~0.4 rad, so the 1e-3 in
+    w = 1 / (chord + 1e-3) weighs differently on the two and the shares pin
+    the chord's absolute scale, sqrt(2 (1 - cos)) = 2 sin(t / 2), not only
+    the ratio of the angles.  Bound as above: 1 - cos ~ 5e-5 for camera 0
+    carries ~2e-3 relative FP32 error, ~1e-3 in its chord and weight, ~3e-5
+    in camera 1's share of ~0.03."""
+    W, H, f = 160, 120, 150.0
+    cams = [S.Camera(W, H, f, f, (W - 1) / 2, (H - 1) / 2, np.eye(3), -np.array([x, 0.0, 0.0]))
+            for x in (0.0, 0.6)]
+    view = S.Camera(W, H, f, f, (W - 1) / 2, (H - 1) / 2, np.eye(3), -np.array([0.015, 0.0, 0.0]))
+    rgb, dep = S.frames_for(S.scene_fronto_plane(1.5), cams)
+    out = oracle_mod.synthesize(cams, rgb, dep, view, [0.3, 0.0, 1.5], pixel_weights=1, crack_filter=0,
+                                hole_fill=0)
+    both = (out["top3"][..., 1] > 0) & (out["hole"] == 0)
+    assert both.mean() > 0.3
+    ys, xs = np.nonzero(both)
+    for y, x in list(zip(ys, xs))[::53]:
+        w = _fp64_weights(cams, view, float(out["depth"][y, x]), x, y, [0, 1])
+        ref = np.sort(w / w.sum())[::-1]
+        assert ref[1] < 0.05
+        assert np.allclose(out["top3"][y, x, :2], ref, rtol=0, atol=1.5e-4)
