@@ -187,3 +187,16 @@ def test_forward_e4m3_without_rounding_is_the_network(monkeypatch):
         # and with rounding it stays close (3 mantissa bits per tensor)
         q8 = U.forward_e4m3(p, x, rgb, U.activation_scales(cache))
         assert np.abs(q8 - pred).max() < 0.1
+
+
+def test_features_follow_the_stated_input_layout():
+    """The network's 8 input channels are, in this order, the blended RGB,
+    the depth, the hole mask and the three largest view weights (the
+    refinement's stated input), scaled to [0, 1]: RGB / 255, depth / z_far."""
+    rgb = np.array([[[[255, 0, 51]]]], np.uint8)
+    depth = np.array([[[2500.0]]], np.float32)
+    hole = np.array([[[1]]], np.uint8)
+    top3 = np.array([[[[0.5, 0.3, 0.2]]]], np.float32)
+    f = U.features(rgb, depth, hole, top3, z_far=10000.0)
+    assert f.shape == (1, 1, 1, 8)
+    assert np.allclose(f[0, 0, 0], [1.0, 0.0, 0.2, 0.25, 1.0, 0.5, 0.3, 0.2], rtol=0, atol=1e-7)
