@@ -1626,9 +1626,15 @@ def config5(args):
         finally:
             loo.close()
         widths = (48, 96, 192)
+        # two throwaway steps first (module loading, allocations), then the
+        # timed run from fresh weights of the same seed
         F.fvv_refine_init(ctx, F.fvv_refine_default_cfg(seed=1, widths=widths))
+        RT.train(ctx, train, steps=2, batch=8, crop=128, lr=2e-3)
+        F.fvv_refine_init(ctx, F.fvv_refine_default_cfg(seed=1, widths=widths))
+        torch.cuda.synchronize()
         t1 = time.perf_counter()
         losses = RT.train(ctx, train, steps=args.refine_steps, batch=8, crop=128, lr=2e-3)
+        torch.cuda.synchronize()
         train_s = time.perf_counter() - t1
         flops = unet_flops(H, W, widths)
         nb = 4
