@@ -4,6 +4,7 @@ against an independent FP64 computation and the geometry."""
 import math
 
 import numpy as np
+import pytest
 
 import synthetic as S
 
@@ -82,7 +83,8 @@ def test_single_active_camera_is_unaffected(oracle_mod):
         assert np.array_equal(a["rgb"], b["rgb"]) and np.array_equal(a["keys"], b["keys"])
 
 
-def test_weights_of_unequal_angles_match_fp64(oracle_mod):
+@pytest.mark.parametrize("fy_scale", [1.0, 1.3])
+def test_weights_of_unequal_angles_match_fp64(oracle_mod, fy_scale):
     """The view 15 mm from camera 0 and 585 mm from camera 1 (both parallel,
     a fronto-parallel plane at 1.5 m): at the point the two rays meet camera
     0's at ~0.01 rad and camera 1's at ~0.4 rad, so the 1e-3 in
@@ -90,11 +92,13 @@ def test_weights_of_unequal_angles_match_fp64(oracle_mod):
     the chord's absolute scale, sqrt(2 (1 - cos)) = 2 sin(t / 2), not only
     the ratio of the angles.  Bound as above: 1 - cos ~ 5e-5 for camera 0
     carries ~2e-3 relative FP32 error, ~1e-3 in its chord and weight, ~3e-5
-    in camera 1's share of ~0.03."""
+    in camera 1's share of ~0.03.  The view's pixels are square or 1.3
+    times taller than wide (fy = 1.3 fx), so x and y scale by their own
+    focal lengths."""
     W, H, f = 160, 120, 150.0
     cams = [S.Camera(W, H, f, f, (W - 1) / 2, (H - 1) / 2, np.eye(3), -np.array([x, 0.0, 0.0]))
             for x in (0.0, 0.6)]
-    view = S.Camera(W, H, f, f, (W - 1) / 2, (H - 1) / 2, np.eye(3), -np.array([0.015, 0.0, 0.0]))
+    view = S.Camera(W, H, f, f * fy_scale, (W - 1) / 2, (H - 1) / 2, np.eye(3), -np.array([0.015, 0.0, 0.0]))
     rgb, dep = S.frames_for(S.scene_fronto_plane(1.5), cams)
     out = oracle_mod.synthesize(cams, rgb, dep, view, [0.3, 0.0, 1.5], pixel_weights=1, crack_filter=0,
                                 hole_fill=0)

@@ -73,3 +73,15 @@ def test_library_selection_equals_oracle(oracle_mod):
         F.fvv_select_cameras(r, views, 0)
     with pytest.raises(F.FvvError):
         F.fvv_select_cameras(r, views, 10)
+
+
+def test_ties_go_to_the_lower_camera(oracle_mod):
+    """A view exactly midway between two cameras of a mirror-symmetric pair
+    (angles equal to the last bit): one camera to send is the lower index,
+    two are both; the same with the pair's indices swapped."""
+    cams = S.rig_parallel(2, 64, 36, 50.0, 0.2)
+    O = np.array([0.0, 0.0, 1.5])
+    view = S.rig_parallel(1, 64, 36, 50.0, 0.2)[0]
+    assert oracle_mod.select_cameras(cams, [view], O, 1) == 0b01
+    assert oracle_mod.select_cameras(cams, [view], O, 2) == 0b11
+    assert oracle_mod.select_cameras(cams[::-1], [view], O, 1) == 0b01

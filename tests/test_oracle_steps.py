@@ -147,6 +147,12 @@ def test_weights_n_ref_and_onehot(oracle_mod):
     assert set(np.nonzero(w3)[0]) == set(np.argsort(th, kind="stable")[:3])
     _, _, w1 = oracle_mod.compose(cams, cams[6].copy(), [0, 0, 0])
     assert list(w1) == [0, 0, 0, 0, 0, 0, 1, 0, 0]
+    # half a millimetre beside camera 6 (same orientation) the view is not
+    # on it: every camera keeps its angular weight, camera 6 the largest
+    near = cams[6].copy()
+    near.t = near.t - near.R @ np.array([0.0005, 0.0, 0.0])
+    _, _, wn = oracle_mod.compose(cams, near, [0, 0, 0])
+    assert np.count_nonzero(wn) == 9 and int(np.argmax(wn)) == 6
     # midway between two cameras: equal weights
     mid = S.arc_view(-45 + 11.25 * 2.5, 1.5, 64, 36, 50.0)
     _, _, wm = oracle_mod.compose(cams, mid, [0, 0, 0], n_ref=2)
