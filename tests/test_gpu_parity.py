@@ -148,6 +148,24 @@ def test_widest_views(oracle_mod, arc_small):
         F.fvv_destroy(ctx)
 
 
+@pytest.mark.parametrize("pixel_weights", [0, 1])
+def test_non_square_view_pixels(oracle_mod, pixel_weights):
+    """A view whose pixels are 1.3 times taller than wide (fy = 1.3 fx), 15
+    mm from one camera and 585 mm from the other, over a plane at 1.5 m:
+    the warp's maps and the per-pixel weights' (x - cx) / fx, (y - cy) / fy
+    scale each axis by its own focal length."""
+    W, H, f = 160, 120, 150.0
+    cams = [S.Camera(W, H, f, f, (W - 1) / 2, (H - 1) / 2, np.eye(3), -np.array([x, 0.0, 0.0]))
+            for x in (0.0, 0.6)]
+    view = S.Camera(W, H, f, 1.3 * f, (W - 1) / 2, (H - 1) / 2, np.eye(3), -np.array([0.015, 0.0, 0.0]))
+    rgb, dep = S.frames_for(S.scene_fronto_plane(1.5), cams)
+    O = [0.3, 0.0, 1.5]
+    g = gpu_run(cams, rgb, dep, [view], O, opts=_opts(pixel_weights=pixel_weights))[0]
+    ref = _oracle(oracle_mod, cams, rgb, dep, view, O, pixel_weights=pixel_weights)
+    assert_parity(g, ref, "fy = 1.3 fx")
+    assert (ref["top3"][..., 1] > 0).mean() > 0.3
+
+
 def test_sixty_four_cameras(oracle_mod):
     """The 6-bit camera field at its limit: 64 cameras on a full circle."""
     cams = S.rig_arc(64, 354.375, 1.5, 24, 16, 20.0)

@@ -85,3 +85,8 @@ def test_ties_go_to_the_lower_camera(oracle_mod):
     assert oracle_mod.select_cameras(cams, [view], O, 1) == 0b01
     assert oracle_mod.select_cameras(cams, [view], O, 2) == 0b11
     assert oracle_mod.select_cameras(cams[::-1], [view], O, 1) == 0b01
+    # the library's host selection takes the same tie rule
+    from fvv_helpers import lib
+    F = lib()
+    for cs in (cams, cams[::-1]):
+        assert F.fvv_select_cameras(F.rig(cs, O), [view], 1) == 0b01
