@@ -63,13 +63,32 @@ def test_nine_camera_arc_full_size(oracle_mod, arc_full):
 @pytest.mark.parametrize("kw", [dict(n_ref=3), dict(n_ref=1), dict(crack_filter=0),
                                 dict(hole_fill=0), dict(crack_filter=0, hole_fill=0, n_ref=2),
                                 dict(tau_vis=0.0), dict(d_lo=1500, d_hi=3000), dict(pixel_weights=1),
-                                dict(pixel_weights=1, n_ref=3, crack_filter=0)])
+                                dict(pixel_weights=1, n_ref=3, crack_filter=0), dict(z_min=1200.0)])
 def test_options(oracle_mod, arc_small, kw):
     wl = arc_small
     v = wl["views"][40]
     g = gpu_run(wl["cams"], wl["rgb"], wl["depth"], [v], wl["look_at"], opts=_opts(**kw))[0]
     ref = _oracle(oracle_mod, wl["cams"], wl["rgb"], wl["depth"], v, wl["look_at"], **kw)
     assert_parity(g, ref, str(kw))
+
+
+@pytest.mark.parametrize("z_min", [0.0, 1800.0])
+def test_cameras_at_other_depths(oracle_mod, z_min):
+    """Camera 1 0.4 m nearer a plane at 2 m than camera 0 and the view: a
+    point lies 1600 mm from camera 1 and 2000 mm from the view, so the
+    visibility test must use the depth in camera 1, and with z_min = 1800 mm
+    camera 1's back-projections are rejected while both cameras splat."""
+    W, H, f = 96, 64, 120.0
+    cams = [S.Camera(W, H, f, f, (W - 1) / 2, (H - 1) / 2, np.eye(3), -np.array(c))
+            for c in ((0.0, 0.0, 0.0), (0.05, 0.0, 0.4))]
+    view = S.Camera(W, H, f, f, (W - 1) / 2, (H - 1) / 2, np.eye(3), -np.array([0.02, 0.0, 0.0]))
+    rgb = np.stack([np.full((H, W, 3), c, np.uint8) for c in ((200, 20, 40), (10, 100, 250))])
+    dep = np.stack([np.full((H, W), 2000, np.uint16), np.full((H, W), 1600, np.uint16)])
+    g = gpu_run(cams, rgb, dep, [view], [0, 0, 2.0], opts=_opts(z_min=z_min, hole_fill=0))[0]
+    ref = _oracle(oracle_mod, cams, rgb, dep, view, [0, 0, 2.0], z_min=z_min, hole_fill=0)
+    assert_parity(g, ref, "z_min %g" % z_min)
+    two = (ref["top3"][16:48, 24:72, 1] > 0)
+    assert two.all() if z_min == 0.0 else not two.any()
 
 
 def test_empty_input_all_holes(oracle_mod):

@@ -225,6 +225,48 @@ def test_blend_visibility_rejects_inconsistent_fetch(oracle_mod):
     assert np.all(out["top3"][mixed][:, 1] > 0)
 
 
+def _depth_offset_pair():
+    """Camera 0 at the origin, camera 1 0.4 m nearer a plane at 2 m (both
+    looking along +z), the view beside camera 0: a point on the plane lies
+    at 2000 mm in the view and in camera 0, at 1600 mm in camera 1."""
+    W, H, f = 96, 64, 120.0
+    cams = [S.Camera(W, H, f, f, (W - 1) / 2, (H - 1) / 2, np.eye(3), -np.array(c))
+            for c in ((0.0, 0.0, 0.0), (0.05, 0.0, 0.4))]
+    view = S.Camera(W, H, f, f, (W - 1) / 2, (H - 1) / 2, np.eye(3), -np.array([0.02, 0.0, 0.0]))
+    rgb = np.stack([np.full((H, W, 3), c, np.uint8) for c in ((200, 20, 40), (10, 100, 250))])
+    dep = np.stack([np.full((H, W), 2000, np.uint16), np.full((H, W), 1600, np.uint16)])
+    return cams, view, rgb, dep
+
+
+def test_blend_visibility_uses_the_depth_in_that_camera(oracle_mod):
+    """R7 compares camera k's depth at the back-projected pixel with the
+    point's depth in camera k (Z_k = 1600 mm), not in the view (2000 mm):
+    camera 1, nearer the plane, sees the points and contributes."""
+    cams, view, rgb, dep = _depth_offset_pair()
+    out = oracle_mod.synthesize(cams, rgb, dep, view, [0, 0, 2.0], hole_fill=0)
+    z, cam, src = oracle_mod.key_fields(out["keys"])
+    mid = np.zeros_like(cam, dtype=bool)
+    mid[16:48, 24:72] = True
+    assert np.all(cam[mid] == 0) and np.all(z[mid] == 2000.0)
+    assert np.all(out["top3"][mid][:, 1] > 0)
+    assert np.all(np.any(out["rgb"][mid] != rgb[0, 0, 0], axis=-1))
+
+
+def test_blend_back_projection_respects_z_min(oracle_mod):
+    """A back-projected point nearer camera k than z_min is rejected like a
+    warped one (R3, R7): with z_min = 1800 mm camera 1 (Z_k = 1600 mm) no
+    longer contributes, while both cameras still splat (Z = 2000 mm in the
+    view) and camera 0 wins the ties."""
+    cams, view, rgb, dep = _depth_offset_pair()
+    out = oracle_mod.synthesize(cams, rgb, dep, view, [0, 0, 2.0], hole_fill=0, z_min=1800.0)
+    z, cam, src = oracle_mod.key_fields(out["keys"])
+    mid = np.zeros_like(cam, dtype=bool)
+    mid[16:48, 24:72] = True
+    assert np.all(cam[mid] == 0)
+    assert np.all(out["top3"][mid][:, 1] == 0)
+    assert np.all(out["rgb"][mid] == rgb[0, 0, 0])
+
+
 def test_blend_rounding_and_single_camera(oracle_mod):
     """One active camera: the blend returns its colour exactly (acc / w)."""
     cams, view, rgb, dep = _two_cam_plane(0.0)
