@@ -43,6 +43,21 @@ def _rigs():
     for _ in range(3):
         out.append((cams18, S.arc_view(rng.uniform(-80, 80), rng.uniform(1.5, 2.5), 1920, 1080,
                                        rng.uniform(1200, 1800)), [0, 0, 0]))
+    # non-square pixels (sources fy = 1.2 fx, the view fy = 0.9 fx), and the
+    # rig moved off the origin with its look-at point
+    sq = S.rig_arc(5, 60.0, 1.5, 640, 360, 500.0)
+    for c in sq:
+        c.fy = 1.2 * c.fx
+    v = S.arc_view(7.0, 1.6, 640, 360, 520.0)
+    v.fy = 0.9 * v.fx
+    out.append((sq, v, [0, 0, 0]))
+    off = np.array([1.0, -2.0, 3.0])
+    mv = []
+    for c in sq + [v]:
+        m = c.copy()
+        m.t = c.t - c.R @ off
+        mv.append(m)
+    out.append((mv[:-1], mv[-1], list(off)))
     return out
 
 

@@ -147,14 +147,17 @@ def test_zoom_intrinsics(oracle_mod):
             assert int(si) not in got
 
 
-@pytest.mark.parametrize("seed", [0, 1, 2])
-def test_general_pose_matches_fp64_projection(oracle_mod, seed):
+@pytest.mark.parametrize("seed,fy_scale", [(0, 1.0), (1, 1.0), (2, 1.0), (3, 1.2)])
+def test_general_pose_matches_fp64_projection(oracle_mod, seed, fy_scale):
     """Arbitrary poses on the nine-camera arc: each splatted sparse source
     point lands on the pixel an independent FP64 projection predicts (away
-    from rounding ties) with its target-camera depth."""
+    from rounding ties) with its target-camera depth.  The last case gives
+    the source cameras pixels 1.2 times taller than wide (fy = 1.2 fx)."""
     rng = np.random.default_rng(seed)
     W, H, f = 160, 90, 125.0
     cams = S.rig_arc(9, 90.0, 1.5, W, H, f)
+    for c in cams:
+        c.fy = c.fx * fy_scale
     view = S.arc_view(rng.uniform(-40, 40), 1.5 + rng.uniform(-0.3, 0.3), W, H,
                       f * rng.uniform(0.8, 1.25))
     M, N, _ = oracle_mod.compose(cams, view, [0, 0, 0])

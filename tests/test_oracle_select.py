@@ -90,3 +90,27 @@ def test_ties_go_to_the_lower_camera(oracle_mod):
     F = lib()
     for cs in (cams, cams[::-1]):
         assert F.fvv_select_cameras(F.rig(cs, O), [view], 1) == 0b01
+
+
+def test_selection_is_invariant_to_moving_the_whole_rig(oracle_mod):
+    """Closeness is the angle about the rig's look-at point, so translating
+    the cameras, the views and that point together changes no selection
+    (the rig's centre is not the world origin in general)."""
+    wl = _rig()
+    off = np.array([1.0, -2.0, 3.0])
+
+    def moved(c):
+        m = c.copy()
+        m.t = c.t - c.R @ off                 # centre C + off
+        return m
+    cams = [moved(c) for c in wl["cams"]]
+    for vi in (10, 90, 170, 250):
+        v = wl["views"][vi]
+        for n in (1, 3, 5):
+            assert (oracle_mod.select_cameras(cams, [moved(v)], off, n) ==
+                    oracle_mod.select_cameras(wl["cams"], [v], np.zeros(3), n))
+    from fvv_helpers import lib
+    F = lib()
+    r = F.rig(cams, off)
+    vs = [moved(wl["views"][i]) for i in (10, 90)]
+    assert F.fvv_select_cameras(r, vs, 3) == oracle_mod.select_cameras(cams, vs, off, 3)
