@@ -91,6 +91,23 @@ def test_cameras_at_other_depths(oracle_mod, z_min):
     assert two.all() if z_min == 0.0 else not two.any()
 
 
+def test_non_square_source_pixels(oracle_mod):
+    """Five arc cameras with pixels 1.2 times taller than wide and a view
+    with pixels 0.9 times as tall: the composed maps scale each axis by its
+    own focal length, on both sides of the warp and the back-projection."""
+    cams = S.rig_arc(5, 60.0, 1.5, 200, 120, 160.0)
+    for c in cams:
+        c.fy = 1.2 * c.fx
+    scene = S.scene_random_objects(21, n_objects=10)
+    rgb, dep = S.frames_for(scene, cams, noise_seed=3)
+    view = S.arc_view(9.0, 1.55, 200, 120, 170.0)
+    view.fy = 0.9 * view.fx
+    g = gpu_run(cams, rgb, dep, [view], [0, 0, 0])[0]
+    ref = _oracle(oracle_mod, cams, rgb, dep, view, [0, 0, 0])
+    assert_parity(g, ref, "non-square sources")
+    assert (ref["hole"] == 0).mean() > 0.5
+
+
 def test_empty_input_all_holes(oracle_mod):
     cams = S.rig_arc(3, 30.0, 1.5, 40, 30, 40.0)
     rgb = np.full((3, 30, 40, 3), 200, np.uint8)
