@@ -153,6 +153,17 @@ def test_weights_n_ref_and_onehot(oracle_mod):
     near.t = near.t - near.R @ np.array([0.0005, 0.0, 0.0])
     _, _, wn = oracle_mod.compose(cams, near, [0, 0, 0])
     assert np.count_nonzero(wn) == 9 and int(np.argmax(wn)) == 6
+    # on camera 6's centre but turned 5 degrees about the vertical axis: not
+    # on the camera either (its optical axis differs), so angular weights,
+    # camera 6's the largest (its angle is 0: weight 1 / 1e-3)
+    a = math.radians(5.0)
+    turn = np.array([[math.cos(a), 0.0, -math.sin(a)], [0.0, 1.0, 0.0], [math.sin(a), 0.0, math.cos(a)]])
+    rot = cams[6].copy()
+    rot.R = turn @ cams[6].R
+    rot.t = turn @ cams[6].t                  # the same centre
+    _, _, wr = oracle_mod.compose(cams, rot, [0, 0, 0])
+    assert np.count_nonzero(wr) == 9 and int(np.argmax(wr)) == 6
+    assert wr[6] == np.float32(1.0 / 1e-3)
     # midway between two cameras: equal weights
     mid = S.arc_view(-45 + 11.25 * 2.5, 1.5, 64, 36, 50.0)
     _, _, wm = oracle_mod.compose(cams, mid, [0, 0, 0], n_ref=2)
