@@ -38,6 +38,12 @@ def _rigs():
     for i in (0, 37, 150, 299):
         out.append((cams, S.trajectory_arc(300, 22.5, 1.5, 1280, 720, 1000.0)[i], [0, 0, 0]))
     out.append((cams, cams[3].copy(), [0, 0, 0]))
+    # on camera 3's centre, turned 5 degrees about the vertical axis (not on it)
+    a = np.radians(5.0)
+    turn = np.array([[np.cos(a), 0.0, -np.sin(a)], [0.0, 1.0, 0.0], [np.sin(a), 0.0, np.cos(a)]])
+    rot = cams[3].copy()
+    rot.R, rot.t = turn @ cams[3].R, turn @ cams[3].t
+    out.append((cams, rot, [0, 0, 0]))
     rng = np.random.default_rng(4)
     cams18 = S.rig_arc(18, 180.0, 2.0, 1920, 1080, 1500.0)
     for _ in range(3):
