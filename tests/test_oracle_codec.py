@@ -104,3 +104,16 @@ def test_background_signal_is_code_zero():
     # a near z_far that reaches the top of the 16-bit range clamps below the signal
     dec_far = K.decode_table(0.5, 70.0, 0.001)
     assert dec_far[2] == K.DEPTH_BG - 1
+
+
+def test_encoder_applies_the_eq1_correction():
+    """The encoder quantises the corrected depth of Eq. (1), not the raw one:
+    with alpha = 0 and beta = 2 (corrected z = 2 z) a code d is encoded as
+    the uncorrected encoder encodes 2 d; with beta = 1 the two encoders are
+    the same."""
+    unit = 0.001
+    d = np.arange(1, 30000)
+    doubled = K.encode_table(ZN, ZF, 0.0, 2.0, unit)
+    plain = K.encode_table(ZN, ZF, 0.0, 1.0, unit)
+    assert np.array_equal(doubled[d], plain[2 * d])
+    assert np.array_equal(K.encode_table(ZN, ZF, 0.0, 1.0, unit), plain)

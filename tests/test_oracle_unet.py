@@ -200,3 +200,22 @@ def test_features_follow_the_stated_input_layout():
     f = U.features(rgb, depth, hole, top3, z_far=10000.0)
     assert f.shape == (1, 1, 1, 8)
     assert np.allclose(f[0, 0, 0], [1.0, 0.0, 0.2, 0.25, 1.0, 0.5, 0.3, 0.2], rtol=0, atol=1e-7)
+
+
+def test_activation_scales_map_each_maximum_to_448():
+    """Per-tensor scaling to the E4M3 range: the largest ReLU output of each
+    conv tensor divided by its scale is 448, the largest finite E4M3 value
+    (so it is kept, and nothing saturates); an all-zero tensor keeps scale 1."""
+    rng = np.random.default_rng(3)
+    cache = {}
+    amax = {}
+    for i, name in enumerate(U.CONV_OUTPUTS):
+        z = rng.normal(0.0, 1.0 + i, (2, 4, 4, 8))
+        cache[name + ".z"] = z
+        amax[name] = np.maximum(z, 0.0).max()
+    cache["e1a.z"] = -np.abs(cache["e1a.z"])          # all zero after the ReLU
+    s = U.activation_scales(cache)
+    assert s[0] == 1.0
+    for name, sc in zip(U.CONV_OUTPUTS[1:], s[1:]):
+        assert amax[name] / sc == pytest.approx(448.0, rel=1e-12)
+        assert U.e4m3_round(amax[name] / sc) == 448.0
