@@ -899,7 +899,7 @@ def jbf_bench(F, wl, stream, reps=20):
 
 def yuv_e2e_bench(F, wl, rgb_h, dep_h, slots, batch, steps, warmup, off=0):
     """End to end with the depth of every tick sent as YUV420 depth frames
-    (Sec. V-B: 12-bit disparity packed onto YUV420, 1.5 bytes per pixel
+    (Sec. V-A: 12-bit disparity packed onto YUV420, 1.5 bytes per pixel
     instead of 2), uploaded with fvv_upload_frames_yuv (decoded in the
     upload kernel); otherwise the pipeline and views of the main e2e
     measurement (all 9 cameras mixed)."""

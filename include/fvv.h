@@ -24,7 +24,8 @@
  *   - Cameras: pinhole, pixel (u, v) has its centre at integer (u, v);
  *     x right, y down, z forward; R, t map world -> camera; t in metres.
  *   - Depth frames: uint16 codes, 0 = no depth, FVV_DEPTH_BG = a background
- *     pixel (Sec. V-B: code 0 of the 12-bit map; BG depth is not sent);
+ *     pixel (Sec. V-A reserves the 12-bit code 0 for it; Sec. IV-B: its
+ *     depth is not sent);
  *     other codes * depth_unit_m metres of camera-space z.  Colour frames:
  *     RGB8 interleaved.
  *   - Every call returns an fvv_status; on failure fvv_last_error() holds a
@@ -262,7 +263,7 @@ fvv_status fvv_synthesize_batch(fvv_ctx* ctx, int32_t n, const fvv_view* views,
 fvv_status fvv_view_params(const fvv_rig* rig, const fvv_options* opt,
                            const fvv_view* view, float* M, float* N, float* w);
 
-/* ---- depth codec of the transmission chain (Sec. V-B, Eq. (1)-(3)) -------
+/* ---- depth codec of the transmission chain (Sec. IV-A Eq. (1), Sec. V-A Eq. (2), (3))
  * The capture side corrects depth (Eq. (1): z_post = (alpha z + beta) z, z in
  * metres), quantises it to 12-bit disparity (Eq. (2): Y = (2^12 - 3)(1/z -
  * 1/z_far) / (1/z_near - 1/z_far) + 2, rounded half up, for z in [z_near,

@@ -29,7 +29,7 @@ _lib = None
 
 KEY_EMPTY = np.uint64(0xFFFFFFFFFFFFFFFF)
 SRC_BITS = 26
-DEPTH_BG = 65535      # depth code signalling a background pixel (Sec. V-B, 12-bit code 0)
+DEPTH_BG = 65535      # depth code signalling a background pixel (Sec. V-A, 12-bit code 0)
 
 CFLAGS = ["-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
           "-shared", "-Wall", "-Wextra"]

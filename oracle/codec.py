@@ -1,4 +1,4 @@
-"""CPU oracle of the depth codec of the transmission chain (Sec. V-B).
+"""CPU oracle of the depth codec of the transmission chain (Sec. IV-A, V-A).
 
 TEST INFRASTRUCTURE ONLY (tests, smoke check, benchmark CPU leg).  FP64
 numpy, each step written from the paper:

@@ -56,7 +56,7 @@ void oracle_default_options(or_options* o)
     o->tau_vis = 0.03f;
     o->z_min = 1.0f;
     o->d_lo = 1;
-    o->d_hi = 65534;   /* 65535 signals a background pixel (Sec. V-B, code 0) */
+    o->d_hi = 65534;   /* 65535 signals a background pixel (Sec. V-A, code 0) */
     o->pixel_weights = 0;
 }
 

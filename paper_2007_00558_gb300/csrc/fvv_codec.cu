@@ -1,4 +1,4 @@
-// fvv_codec.cu -- the depth codec of the transmission chain (Sec. V-B):
+// fvv_codec.cu -- the depth codec of the transmission chain (Sec. IV-A, V-A):
 // 16-bit depth -> Eq. (1) correction -> Eq. (2) 12-bit disparity -> Eq. (3)
 // and the bit re-arrangement onto an 8-bit YUV420 frame, and back.
 //

@@ -1,4 +1,4 @@
-"""The depth codec (Sec. V-B, Eq. (1)-(3)) on the GPU against the oracle
+"""The depth codec (Sec. IV-A, V-A, Eq. (1)-(3)) on the GPU against the oracle
 (oracle/codec.py): encoding, decoding and the fused YUV upload are integer
 work decided by tables both sides build in FP64, so every byte and every
 depth code must match exactly."""

@@ -1,5 +1,5 @@
 """Pins of the depth-codec oracle (oracle/codec.py) to what the paper and
-the arithmetic fix (Sec. V-B, Eq. (1)-(3))."""
+the arithmetic fix (Sec. IV-A, V-A, Eq. (1)-(3))."""
 import numpy as np
 import pytest
 
