@@ -48,6 +48,26 @@ def test_all_background_with_exact_model_reduces_to_plain(oracle_mod, layered_sm
         assert not np.any(b["layer"] == 0)
 
 
+def test_background_without_a_model_has_no_depth(oracle_mod, layered_small):
+    """A camera without a BG model: its BG-signalled pixels carry no depth
+    at all (they are neither FG nor BG points), so with no model for any
+    camera the BG layer is empty and the output is the FG layer alone."""
+    wl = layered_small
+    assert any(np.any(np.asarray(d) == BG) for d in wl["depth"])
+    # a view of the swing, and one 0.5 m behind camera 4 looking the same
+    # way (a point just in front of camera 4 would land inside that view)
+    behind = wl["cams"][4].copy()
+    behind.t = behind.t + np.array([0.0, 0.0, 0.5])
+    zero = [np.zeros_like(d) for d in wl["depth"]]
+    for v in (wl["views"][60], behind):
+        none = oracle_mod.synthesize_layered(wl["cams"], wl["rgb"], wl["depth"], None, v, wl["look_at"])
+        empty = oracle_mod.synthesize_layered(wl["cams"], wl["rgb"], wl["depth"], zero, v, wl["look_at"])
+        assert np.all(none["keys_raw_bg"] == oracle_mod.KEY_EMPTY)
+        assert not np.any(none["layer"] == 1)
+        for f in ("rgb", "depth", "hole", "keys", "keys_raw"):
+            assert np.array_equal(none[f], empty[f]), f
+
+
 def test_identity_view_shows_each_pixel_in_its_layer(oracle_mod, layered_small):
     """The view at camera 0's pose (camera 0 alone has weight): each pixel
     maps to itself, so an actor pixel shows its live colour at its live

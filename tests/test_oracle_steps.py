@@ -82,6 +82,13 @@ def test_crack_removes_background_through_foreground(oracle_mod):
     assert oracle_mod.crack_filter(g4, 0.05)[1, 1] == g4[1, 1]
     g4[1, 1] = key(1093.0, 1, 4)
     assert oracle_mod.crack_filter(g4, 0.05)[1, 1] == g4[1, 0]
+    # the pairs are visited in order until one replaces the pixel: the first
+    # consistent pair (L, R) lies at the pixel's own depth and leaves it, the
+    # next one (U, D) lies far in front and replaces it
+    g5 = grid([[None, 1000, None],
+               [2950, 3000, 2960],
+               [None, 1010, None]])
+    assert oracle_mod.crack_filter(g5, 0.05)[1, 1] == min(g5[0, 1], g5[2, 1])
     # a foreground point on background is kept (the rule only pulls forward)
     g3 = grid([[2000, 2000, 2000],
                [2000, 1000, 2000],
