@@ -307,6 +307,8 @@ def test_hole_fill_rows(oracle_mod):
                     [0, 0, 3, 0, 7, 1, 0]], np.float32)
     rgb = np.zeros((4, 7, 3), np.uint8)
     rgb[..., 0] = np.arange(7)[None, :] * 10 + np.arange(4)[:, None]
+    rgb[..., 1] = 100 + rgb[..., 0]          # every channel carries the source
+    rgb[..., 2] = 200 - rgb[..., 0]
     rgb[hole == 1] = 0                       # the blend leaves holes black
     r, d = oracle_mod.hole_fill(hole, rgb, dep)
     # row 0: x1,x2 between A(5) and B(9) -> B; x4 between B(9) and C(2) -> B;
@@ -319,6 +321,10 @@ def test_hole_fill_rows(oracle_mod):
     assert list(r[2, :, 0]) == [2, 2, 22, 22, 22, 22, 22]
     # row 3: x0,x1 only right -> x2; x3 between 3 and 7 -> x4; x6 -> x5
     assert list(r[3, :, 0]) == [23, 23, 23, 43, 43, 53, 53]
+    # all three channels of a filled pixel come from its source pixel
+    filled = (hole == 1) & (r[..., 0] > 0)
+    assert np.array_equal(r[..., 1][filled], 100 + r[..., 0][filled])
+    assert np.array_equal(r[..., 2][filled], 200 - r[..., 0][filled])
 
 
 # ------------------------------------------------------------------ analytic ground truth

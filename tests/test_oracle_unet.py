@@ -126,6 +126,11 @@ def test_adam_single_step_closed_form():
     U.adam_step(p, g, st, lr=0.1)
     # first bias-corrected step moves by lr * g / (|g| + eps) = lr * sign(g)
     assert np.allclose(p["a"], [1.0 - 0.1, -2.0 + 0.1], atol=1e-6)
+    # with a gradient of the order of eps the epsilon shows: the first step
+    # is lr g / (sqrt(v) + eps) (eps added after the root), not lr g / sqrt(v + eps)
+    p = {"a": np.array([0.0])}
+    U.adam_step(p, {"a": np.array([1e-6])}, {}, lr=0.1)
+    assert p["a"][0] == pytest.approx(-0.1 * 1e-6 / (1e-6 + 1e-8), rel=1e-9)
 
 
 def test_e4m3_closed_forms():
