@@ -285,6 +285,48 @@ def test_blend_back_projection_respects_z_min(oracle_mod):
     assert np.all(out["rgb"][mid] == rgb[0, 0, 0])
 
 
+def test_depth_code_range_is_inclusive_at_both_ends(oracle_mod):
+    """Valid depth codes are [d_lo, d_hi], both ends included, for the points
+    that splat (R3) and for the depths the blend fetches (R7): camera 0's
+    codes at d_lo, d_hi and just outside them; camera 1 0.4 m nearer the
+    plane fetches 1600, outside [1700, 2100], so it does not contribute."""
+    cams, view, rgb, dep = _depth_offset_pair()
+    W = cams[0].width
+    d0 = np.zeros_like(dep[0])
+    d0[10, 20], d0[10, 30], d0[10, 40], d0[10, 50] = 1699, 1700, 2100, 2101
+    w = np.array([1.0, 0.0], np.float32)
+    M, N, _ = oracle_mod.compose(cams, view, [0, 0, 2.0])
+    keys = oracle_mod.warp_splat(cams, [d0, np.zeros_like(d0)], M, w, view.width, view.height,
+                                 oracle_mod.options(d_lo=1700, d_hi=2100))
+    z, cam, src = oracle_mod.key_fields(keys)
+    got = sorted(int(s) for s in src[src >= 0])
+    assert got == [10 * W + 30, 10 * W + 40]
+    out = oracle_mod.synthesize(cams, rgb, dep, view, [0, 0, 2.0], hole_fill=0, d_lo=1700, d_hi=2100)
+    zz, cc, _ = oracle_mod.key_fields(out["keys"])
+    mid = np.zeros_like(cc, dtype=bool)
+    mid[16:48, 24:72] = True
+    assert np.all(cc[mid] == 0)
+    assert np.all(out["top3"][mid][:, 1] == 0)
+    assert np.all(out["rgb"][mid] == rgb[0, 0, 0])
+
+
+def test_holes_stay_black_without_the_fill(oracle_mod):
+    """With hole_fill = 0 a pixel no camera reaches is black with depth 0
+    (the paper shows disocclusions black); with the fill it takes a
+    neighbour's colour and depth."""
+    wl = S.workload("plain_9cam_1280x720", scale=0.2)      # depth dropouts leave holes
+    kw = dict(crack_filter=0, n_ref=2)
+    off = oracle_mod.synthesize(wl["cams"], wl["rgb"], wl["depth"], wl["views"][50], wl["look_at"],
+                                hole_fill=0, **kw)
+    on = oracle_mod.synthesize(wl["cams"], wl["rgb"], wl["depth"], wl["views"][50], wl["look_at"],
+                               hole_fill=1, **kw)
+    h = off["hole"] == 1
+    assert h.sum() > 20
+    assert np.all(off["rgb"][h] == 0) and np.all(off["depth"][h] == 0)
+    assert np.array_equal(on["hole"], off["hole"])
+    assert np.any(on["rgb"][h] != 0) and np.all(on["depth"][h] > 0)
+
+
 def test_blend_rounding_and_single_camera(oracle_mod):
     """One active camera: the blend returns its colour exactly (acc / w)."""
     cams, view, rgb, dep = _two_cam_plane(0.0)
