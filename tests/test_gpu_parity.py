@@ -108,6 +108,23 @@ def test_non_square_source_pixels(oracle_mod):
     assert (ref["hole"] == 0).mean() > 0.5
 
 
+def test_depth_code_range_ends(oracle_mod):
+    """Codes d_lo - 1, d_lo, d_hi, d_hi + 1 in camera 0 (only the middle two
+    splat) and camera 1's fetched codes below d_lo (it does not
+    contribute): the kernels' unsigned range tests against the oracle."""
+    W, H, f = 96, 64, 120.0
+    cams = [S.Camera(W, H, f, f, (W - 1) / 2, (H - 1) / 2, np.eye(3), -np.array(c))
+            for c in ((0.0, 0.0, 0.0), (0.05, 0.0, 0.4))]
+    view = S.Camera(W, H, f, f, (W - 1) / 2, (H - 1) / 2, np.eye(3), -np.array([0.02, 0.0, 0.0]))
+    rgb = np.stack([np.full((H, W, 3), c, np.uint8) for c in ((200, 20, 40), (10, 100, 250))])
+    dep = np.stack([np.full((H, W), 2000, np.uint16), np.full((H, W), 1600, np.uint16)])
+    dep[0, 10, 20], dep[0, 10, 30], dep[0, 10, 40], dep[0, 10, 50] = 1699, 1700, 2100, 2101
+    kw = dict(d_lo=1700, d_hi=2100, hole_fill=0)
+    g = gpu_run(cams, rgb, dep, [view], [0, 0, 2.0], opts=_opts(**kw))[0]
+    ref = _oracle(oracle_mod, cams, rgb, dep, view, [0, 0, 2.0], **kw)
+    assert_parity(g, ref, "code range ends")
+
+
 def test_empty_input_all_holes(oracle_mod):
     cams = S.rig_arc(3, 30.0, 1.5, 40, 30, 40.0)
     rgb = np.full((3, 30, 40, 3), 200, np.uint8)
